@@ -1,0 +1,634 @@
+"""Explicit-state model checker for the synchronization algorithms (oracle; test infra only).
+
+Each algorithm runs as one step machine per block.  One step makes at most one shared-memory
+access, and every access is atomic as a whole (sequential consistency, interleaving
+semantics).  The checker enumerates every reachable state of `nproc` blocks that each perform
+`ops` operations (lock/unlock pairs, wait/post pairs or barrier crossings), and reports:
+
+  * safety: at most one block in a mutex's critical section, at most n in a semaphore's,
+    no block past barrier round r before every block has arrived at round r, and, for the
+    fair kinds, grants in ticket order;
+  * progress: from every reachable state some state with all blocks done stays reachable
+    (no deadlock, and no livelock that no schedule can escape).
+
+Words are uint32 and wrap; ticket and epoch comparisons use the signed difference, so a run
+can start its counters just below 2^32 to exercise wrap-around.
+
+The algorithms follow Section 5 ("Design") and the pseudocode of the Appendix:
+  SpinMutex     spin-lock mutex with optional backoff (Algorithm 1; "Spin-Lock Mutex")
+  TicketMutex   fetch-and-add mutex ("FA Mutex"; Section 5, "Fetch-and-Add Mutex")
+  QueueMutex    sleep-waiting queue lock: each waiter polls its own slot of a ring of flags
+  RingMutex     the paper's ring-buffer sleeping mutex (Section 5, "design alternative")
+  SpinSem       spin-lock semaphore with optional backoff ("Spin-Lock Semaphore")
+  SleepSem      sleeping (FA) semaphore ("Sleeping Semaphore")
+  AtomicBarrier two-stage atomic-counter barrier (Section 5, "Barrier")
+  FlagBarrier   decentralized XF flag barrier (Section 5, "Barrier")
+  TreeBarrier   combining-tree barrier (Section 2, hierarchical barriers)
+  ClusterBarrier  barrier inside groups of c blocks, then one leader per group globally
+Mutation variants with a planted mistake (`broken=...`) exist so that tests can show the
+checker catches each kind of error.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+M32 = 0xFFFFFFFF
+DONE = -1
+
+
+def s_gt(a: int, b: int) -> bool:
+    """a > b for wrapping uint32 counters: the signed 32-bit difference is positive."""
+    d = (a - b) & M32
+    return d != 0 and d < 0x80000000
+
+
+def s_ge(a: int, b: int) -> bool:
+    return ((a - b) & M32) < 0x80000000
+
+
+def inc(x: int, k: int = 1) -> int:
+    return (x + k) & M32
+
+
+@dataclass
+class Result:
+    states: int = 0
+    violation: str | None = None
+    trace: list = field(default_factory=list)
+    stuck_state: tuple | None = None
+
+    @property
+    def ok(self) -> bool:
+        return self.violation is None
+
+
+def _set(t: tuple, i: int, v) -> tuple:
+    return t[:i] + (v,) + t[i + 1:]
+
+
+# --------------------------------------------------------------------------------------------
+# Mutexes
+# --------------------------------------------------------------------------------------------
+# Local state: (pc, ops_done, reg_a, reg_b).  Events: ("enter", ticket|None), ("exit",).
+PC_ENTER, PC_EXIT = 50, 51
+
+
+class SpinMutex:
+    """Spin-lock mutex (Algorithm 1 and the Appendix's spin-lock mutex).
+
+    lock: repeat OldVal <- atomicExch(M, 1) until OldVal = 0, with Backoff() after each
+    failure when UseBackoff; unlock: M <- 0 (plain store; Algorithm 1 uses atomicExch(M, 0),
+    selected with atomic_unlock).  cas=True replaces the exchange by atomicCAS(M, 0, 1).
+    broken="test_then_set" splits the atomic into a load and a later store.
+    """
+    kind, capacity, fifo = "mutex", 1, False
+
+    def __init__(self, backoff=False, cas=False, atomic_unlock=False, broken=None):
+        self.backoff, self.cas, self.atomic_unlock, self.broken = backoff, cas, atomic_unlock, broken
+
+    def init(self, nproc, ops):
+        return (0,), tuple((0, 0, 0, 0) for _ in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, a, b = loc
+        M = sh[0]
+        if pc == 0:
+            if self.broken == "test_then_set":
+                return ((9, k, a, b) if M == 0 else (0, k, a, b)), sh, None
+            old = M
+            if self.cas:
+                if M == 0:
+                    sh = (1,)
+            else:
+                sh = (1,)
+            if old == 0:
+                return (PC_ENTER, k, a, b), sh, None
+            return ((1 if self.backoff else 0), k, a, b), sh, None
+        if pc == 9:  # second half of the broken test-then-set
+            return (PC_ENTER, k, a, b), (1,), None
+        if pc == 1:  # Backoff(): no memory access
+            return (0, k, a, b), sh, None
+        if pc == PC_ENTER:
+            return (PC_EXIT, k, a, b), sh, ("enter", None)
+        if pc == PC_EXIT:
+            return (2, k, a, b), sh, ("exit",)
+        if pc == 2:  # unlock
+            k += 1
+            return ((0 if k < ops else DONE), k, a, b), (0,), None
+        raise AssertionError(pc)
+
+
+class TicketMutex:
+    """Fetch-and-add (ticket) mutex.
+
+    lock: TicketNumber <- fetch-and-add(ticket, 1); wait until turn = TicketNumber.
+    unlock (literal=True): turn <- turn + 1 as a plain read then write (the Appendix's FA
+    mutex); literal=False stores TicketNumber + 1, which is the same value because only the
+    holder writes turn.  broken="no_advance" stores TicketNumber (the turn never moves on).
+    """
+    kind, capacity, fifo = "mutex", 1, True
+
+    def __init__(self, literal=False, base=0, broken=None):
+        self.literal, self.base, self.broken = literal, base & M32, broken
+
+    def init(self, nproc, ops):
+        return (self.base, self.base), tuple((0, 0, 0, 0) for _ in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, t, r = loc
+        ticket, turn = sh
+        if pc == 0:
+            return (1, k, ticket, r), (inc(ticket), turn), None
+        if pc == 1:
+            return ((PC_ENTER if turn == t else 1), k, t, r), sh, None
+        if pc == PC_ENTER:
+            return (PC_EXIT, k, t, r), sh, ("enter", t)
+        if pc == PC_EXIT:
+            return (2, k, t, r), sh, ("exit",)
+        if pc == 2:
+            if self.literal:
+                return (3, k, t, turn), sh, None
+            new = t if self.broken == "no_advance" else inc(t)
+            k += 1
+            return ((0 if k < ops else DONE), k, t, r), (ticket, new), None
+        if pc == 3:
+            k += 1
+            return ((0 if k < ops else DONE), k, t, r), (ticket, inc(r)), None
+        raise AssertionError(pc)
+
+
+class QueueMutex:
+    """Sleep-waiting queue lock with one flag slot per waiter (ring of Q slots, Q a power of 2).
+
+    lock: t <- fetch-and-add(tail, 1); wait until flag[t mod Q] = t.
+    unlock: flag[(t + 1) mod Q] <- t + 1.  Every waiter polls its own slot, so one unlock is
+    seen by exactly one waiter.  Initial state for a first ticket `base`: tail = base,
+    flag[base mod Q] = base, and every other slot holds the latest ticket below base that
+    maps to it, which no pending waiter can equal.
+    """
+    kind, capacity, fifo = "mutex", 1, True
+
+    def __init__(self, q=4, base=0):
+        assert q & (q - 1) == 0
+        self.q, self.base = q, base & M32
+
+    def init(self, nproc, ops):
+        assert self.q >= nproc
+        flags = []
+        for i in range(self.q):
+            back = (self.base - i) % self.q
+            flags.append((self.base - back) & M32)
+        return (self.base,) + tuple(flags), tuple((0, 0, 0, 0) for _ in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, t, r = loc
+        q = self.q
+        if pc == 0:
+            return (1, k, sh[0], r), _set(sh, 0, inc(sh[0])), None
+        if pc == 1:
+            return ((PC_ENTER if sh[1 + (t % q)] == t else 1), k, t, r), sh, None
+        if pc == PC_ENTER:
+            return (PC_EXIT, k, t, r), sh, ("enter", t)
+        if pc == PC_EXIT:
+            return (2, k, t, r), sh, ("exit",)
+        if pc == 2:
+            k += 1
+            n = inc(t)
+            return ((0 if k < ops else DONE), k, t, r), _set(sh, 1 + (n % q), n), None
+        raise AssertionError(pc)
+
+
+class RingMutex:
+    """The paper's ring-buffer sleeping mutex (Section 5, design alternative to FA).
+
+    An arriving block places itself at the end of a ring buffer and keeps checking whether the
+    entry at the front is itself; unlock increments the head pointer.  Here the end slot is
+    claimed with fetch-and-add on `tail` and then written with the block id; a waiter reads
+    `head`, then ring[head mod Q], and enters when that entry is its own id.  Unlock clears the
+    holder's entry before advancing `head`: without the clear (broken="no_clear") a block can
+    match its own stale entry from an earlier lap of the ring.
+    """
+    kind, capacity, fifo = "mutex", 1, True
+    EMPTY = M32
+
+    def __init__(self, q=4, broken=None):
+        self.q, self.broken = q, broken
+
+    def init(self, nproc, ops):
+        return (0, 0) + tuple([self.EMPTY] * self.q), tuple((0, 0, 0, 0) for _ in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, t, h = loc
+        q = self.q
+        head, tail = sh[0], sh[1]
+        if pc == 0:      # claim the end slot
+            return (3, k, tail, h), _set(sh, 1, inc(tail)), None
+        if pc == 3:      # place itself in the ring
+            return (1, k, t, h), _set(sh, 2 + (t % q), p), None
+        if pc == 1:      # read the head pointer
+            return (4, k, t, head), sh, None
+        if pc == 4:      # is the front entry this block?
+            return ((PC_ENTER if sh[2 + (h % q)] == p else 1), k, t, h), sh, None
+        if pc == PC_ENTER:
+            return (PC_EXIT, k, t, h), sh, ("enter", t)
+        if pc == PC_EXIT:
+            return ((5 if self.broken == "no_clear" else 2), k, t, h), sh, ("exit",)
+        if pc == 2:      # clear own entry
+            return (5, k, t, h), _set(sh, 2 + (t % q), self.EMPTY), None
+        if pc == 5:      # advance the head
+            k += 1
+            return ((0 if k < ops else DONE), k, t, h), _set(sh, 0, inc(t)), None
+        raise AssertionError(pc)
+
+
+# --------------------------------------------------------------------------------------------
+# Semaphores
+# --------------------------------------------------------------------------------------------
+
+
+class SpinSem:
+    """Spin-lock semaphore (Section 5 and the Appendix's spin-lock semaphore).
+
+    S starts at X + 1; 0 means another block holds the internal lock.  wait: V <- exch(S, 0);
+    V > 1: exch(S, V - 1) and enter; V = 1 (at capacity): exch(S, 1) and retry; V = 0: retry.
+    post: repeat V <- exch(S, 0) until V > 0, then exch(S, V + 1).  Backoff() after a failed
+    wait attempt when UseBackoff (never in post).
+    """
+    kind, fifo = "sem", False
+
+    def __init__(self, n=1, backoff=False):
+        self.capacity, self.backoff = n, backoff
+
+    def init(self, nproc, ops):
+        return (self.capacity + 1,), tuple((0, 0, 0, 0) for _ in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, v, r = loc
+        S = sh[0]
+        retry = 7 if self.backoff else 0
+        if pc == 0:
+            if S > 1:
+                return (1, k, S, r), (0,), None
+            if S == 1:
+                return (2, k, S, r), (0,), None
+            return (retry, k, S, r), (0,), None
+        if pc == 1:
+            return (PC_ENTER, k, v, r), (v - 1,), None
+        if pc == 2:
+            return (retry, k, v, r), (1,), None
+        if pc == 7:  # Backoff()
+            return (0, k, v, r), sh, None
+        if pc == PC_ENTER:
+            return (PC_EXIT, k, v, r), sh, ("enter", None)
+        if pc == PC_EXIT:
+            return (3, k, v, r), sh, ("exit",)
+        if pc == 3:
+            if S > 0:
+                return (4, k, S, r), (0,), None
+            return (3, k, S, r), (0,), None
+        if pc == 4:
+            k += 1
+            return ((0 if k < ops else DONE), k, v, r), (v + 1,), None
+        raise AssertionError(pc)
+
+
+class SleepSem:
+    """Sleeping (FA) semaphore (Section 5 and the Appendix's sleeping semaphore).
+
+    wait: OldCount <- fetch-and-add(count, 1); if OldCount < maxCount enter; otherwise
+    WaitIndex <- fetch-and-add(ticket, 1) and wait until turn > WaitIndex.
+    post: OldCount <- fetch-and-add(count, -1); if OldCount > maxCount, fetch-and-add(turn, 1).
+    The count is a signed 32-bit value; turn and WaitIndex compare by signed difference.
+    broken="turn_ge" waits for turn >= WaitIndex instead (one grant too many).
+    """
+    kind, fifo = "sem", False
+
+    def __init__(self, n=1, base=0, broken=None):
+        self.capacity, self.base, self.broken = n, base & M32, broken
+
+    def init(self, nproc, ops):
+        return (0, self.base, self.base), tuple((0, 0, 0, 0) for _ in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, w, r = loc
+        count, ticket, turn = sh
+        N = self.capacity
+        if pc == 0:
+            if count < N:
+                return (PC_ENTER, k, w, r), (count + 1, ticket, turn), None
+            return (1, k, w, r), (count + 1, ticket, turn), None
+        if pc == 1:
+            return (2, k, ticket, r), (count, inc(ticket), turn), None
+        if pc == 2:
+            ok = s_ge(turn, w) if self.broken == "turn_ge" else s_gt(turn, w)
+            return ((PC_ENTER if ok else 2), k, w, r), sh, None
+        if pc == PC_ENTER:
+            return (PC_EXIT, k, w, r), sh, ("enter", None)
+        if pc == PC_EXIT:
+            return (3, k, w, r), sh, ("exit",)
+        if pc == 3:
+            k += 1
+            nxt = 0 if k < ops else DONE
+            if count > N:
+                return (4, k, w, r), (count - 1, ticket, turn), None
+            return (nxt, k, w, r), (count - 1, ticket, turn), None
+        if pc == 4:
+            return ((0 if k < ops else DONE), k, w, r), (count, ticket, inc(turn)), None
+        raise AssertionError(pc)
+
+
+# --------------------------------------------------------------------------------------------
+# Barriers.  Events: ("arrive",) when a block arrives, ("pass",) when it leaves the barrier.
+# --------------------------------------------------------------------------------------------
+
+
+class AtomicBarrier:
+    """Two-stage atomic barrier: stage 1 counts arrivals with fetch-and-add; the last arriver
+    resets the counter and advances the release epoch; stage 2 polls the epoch.  Each block
+    keeps its expected epoch locally.  broken="no_wait": non-last arrivers leave at once."""
+    kind = "barrier"
+
+    def __init__(self, base=0, broken=None):
+        self.base, self.broken = base & M32, broken
+
+    def init(self, nproc, ops):
+        return (0, self.base), tuple((0, 0, self.base, 0) for _ in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, e, r = loc
+        count, release = sh
+        if pc == 0:
+            last = count + 1 == nproc
+            return ((1 if last else 3), k, e, r), (count + 1, release), ("arrive",)
+        if pc == 1:
+            return (2, k, e, r), (0, release), None
+        if pc == 2:
+            k += 1
+            return ((0 if k < ops else DONE), k, inc(e), r), (count, inc(e)), ("pass",)
+        if pc == 3:
+            if release == inc(e) or self.broken == "no_wait":
+                k += 1
+                return ((0 if k < ops else DONE), k, inc(e), r), sh, ("pass",)
+            return loc, sh, None
+        raise AssertionError(pc)
+
+
+class FlagBarrier:
+    """Decentralized flag barrier of Xiao and Feng (Section 5, "Barrier").
+
+    Each block writes its arrival flag; the master block (block 0) checks every flag, then
+    writes the release flags, one per block (broadcast=True: one shared release word).
+    Flags hold increasing epoch values, so no reset phase is needed.
+    broken="skip_last": the master never checks the last block's flag.
+    """
+    kind = "barrier"
+
+    def __init__(self, broadcast=False, base=0, broken=None):
+        self.broadcast, self.base, self.broken = broadcast, base & M32, broken
+
+    def init(self, nproc, ops):
+        nrel = 1 if self.broadcast else nproc
+        sh = tuple([self.base] * nproc) + tuple([self.base] * nrel)
+        return sh, tuple((0, 0, self.base, 0) for _ in range(nproc))
+
+    def _rel(self, p, nproc):
+        return nproc + (0 if self.broadcast else p)
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, e, j = loc
+        ne = inc(e)
+        if p != 0:
+            if pc == 0:
+                return (1, k, e, j), _set(sh, p, ne), ("arrive",)
+            if pc == 1:
+                if sh[self._rel(p, nproc)] == ne:
+                    k += 1
+                    return ((0 if k < ops else DONE), k, ne, j), sh, ("pass",)
+                return loc, sh, None
+            raise AssertionError(pc)
+        last = nproc - 1 if self.broken == "skip_last" else nproc
+        if pc == 0:
+            return (1, k, e, 1), _set(sh, 0, ne), ("arrive",)
+        if pc == 1:  # check arrival flags 1..n-1, one load per step
+            if j >= last:
+                return (2, k, e, 1), sh, None
+            if sh[j] == ne:
+                return (1, k, e, j + 1), sh, None
+            return loc, sh, None
+        if pc == 2:  # write release flags, one store per step
+            if self.broadcast:
+                k += 1
+                return ((0 if k < ops else DONE), k, ne, 0), _set(sh, nproc, ne), ("pass",)
+            if j >= nproc:
+                k += 1
+                return ((0 if k < ops else DONE), k, ne, 0), sh, ("pass",)
+            return (2, k, e, j + 1), _set(sh, nproc + j, ne), None
+        raise AssertionError(pc)
+
+
+class TreeBarrier:
+    """Combining-tree barrier with fan-in `fan`: a block counts itself in at its leaf; the
+    last arriver at a node resets that node and counts itself in at the parent; the last
+    arriver at the root advances the release epoch, which every block polls."""
+    kind = "barrier"
+
+    def __init__(self, fan=2, base=0):
+        self.fan, self.base = fan, base & M32
+
+    def _tree(self, nproc):
+        # nodes listed level by level: (size, parent index)
+        nodes, level, width = [], [], nproc
+        first = 0
+        sizes = [min(self.fan, width - i) for i in range(0, width, self.fan)]
+        levels = [sizes]
+        while len(levels[-1]) > 1:
+            w = len(levels[-1])
+            levels.append([min(self.fan, w - i) for i in range(0, w, self.fan)])
+        offs, off = [], 0
+        for lv in levels:
+            offs.append(off)
+            off += len(lv)
+        size, parent = [], []
+        for li, lv in enumerate(levels):
+            for i, s in enumerate(lv):
+                size.append(s)
+                parent.append(offs[li + 1] + i // self.fan if li + 1 < len(levels) else -1)
+        return size, parent
+
+    def init(self, nproc, ops):
+        size, _ = self._tree(nproc)
+        return tuple([0] * len(size)) + (self.base,), tuple((0, 0, self.base, p // self.fan) for p in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        size, parent = self._tree(nproc)
+        pc, k, e, nd = loc
+        rel = len(size)
+        if pc in (0, 4):  # arrive at node nd (pc 0: the leaf, a block's own arrival)
+            c = sh[nd] + 1
+            ev = ("arrive",) if pc == 0 else None
+            return ((1 if c == size[nd] else 3), k, e, nd), _set(sh, nd, c), ev
+        if pc == 1:  # last arriver at nd: reset it, go up or release
+            sh = _set(sh, nd, 0)
+            if parent[nd] < 0:
+                return (2, k, e, nd), sh, None
+            return (4, k, e, parent[nd]), sh, None
+        if pc == 2:
+            k += 1
+            return ((0 if k < ops else DONE), k, inc(e), p // self.fan), _set(sh, rel, inc(e)), ("pass",)
+        if pc == 3:
+            if sh[rel] == inc(e):
+                k += 1
+                return ((0 if k < ops else DONE), k, inc(e), p // self.fan), sh, ("pass",)
+            return loc, sh, None
+        raise AssertionError(pc)
+
+
+class ClusterBarrier:
+    """Hierarchical barrier over groups ("clusters") of c consecutive blocks.
+
+    Phase 1 is a barrier inside the cluster (the hardware cluster barrier; modelled as a
+    counter with a cluster epoch).  Phase 2: the cluster's leader (rank 0) arrives at a
+    global two-stage atomic barrier of nproc / c leaders; every block polls the global release
+    epoch.
+    """
+    kind = "barrier"
+
+    def __init__(self, c=2, base=0):
+        self.c, self.base = c, base & M32
+
+    def init(self, nproc, ops):
+        assert nproc % self.c == 0
+        ncl = nproc // self.c
+        sh = tuple([0] * ncl) + tuple([0] * ncl) + (0, self.base)
+        return sh, tuple((0, 0, self.base, 0) for _ in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        c = self.c
+        ncl = nproc // c
+        cl, rank = p // c, p % c
+        pc, k, e, ce = loc
+        CC, CE, GC, REL = cl, ncl + cl, 2 * ncl, 2 * ncl + 1
+        if pc == 0:
+            n = sh[CC] + 1
+            return ((1 if n == c else 2), k, e, ce), _set(sh, CC, n), ("arrive",)
+        if pc == 1:
+            sh = _set(sh, CC, 0)
+            return (2, k, e, ce), _set(sh, CE, inc(sh[CE])), None
+        if pc == 2:
+            if sh[CE] == inc(ce):
+                return ((3 if rank == 0 else 6), k, e, inc(ce)), sh, None
+            return loc, sh, None
+        if pc == 3:
+            n = sh[GC] + 1
+            return ((4 if n == ncl else 6), k, e, ce), _set(sh, GC, n), None
+        if pc == 4:
+            return (5, k, e, ce), _set(sh, GC, 0), None
+        if pc == 5:
+            k += 1
+            return ((0 if k < ops else DONE), k, inc(e), ce), _set(sh, REL, inc(e)), ("pass",)
+        if pc == 6:
+            if sh[REL] == inc(e):
+                k += 1
+                return ((0 if k < ops else DONE), k, inc(e), ce), sh, ("pass",)
+            return loc, sh, None
+        raise AssertionError(pc)
+
+
+# --------------------------------------------------------------------------------------------
+# Explorer
+# --------------------------------------------------------------------------------------------
+
+
+def _ghost0(model, nproc):
+    if model.kind == "barrier":
+        return (tuple([0] * nproc), tuple([0] * nproc))
+    return (0, 0)  # (blocks inside, grants so far)
+
+
+def _apply(model, ghost, p, ev, nproc):
+    """Updates the ghost bookkeeping for an event; returns (ghost, violation or None)."""
+    if ev is None:
+        return ghost, None
+    if model.kind == "barrier":
+        arrived, passed = ghost
+        if ev[0] == "arrive":
+            return (_set(arrived, p, arrived[p] + 1), passed), None
+        r = passed[p]  # the round p is leaving
+        if min(arrived) < r + 1:
+            return ghost, f"block {p} passed round {r} before every block arrived"
+        return (arrived, _set(passed, p, r + 1)), None
+    inside, grants = ghost
+    if ev[0] == "enter":
+        inside += 1
+        if inside > model.capacity:
+            return ghost, f"{inside} blocks inside a critical section of capacity {model.capacity}"
+        if model.fifo and ev[1] is not None:
+            want = (getattr(model, "base", 0) + grants) & M32
+            if ev[1] != want:
+                return ghost, f"grant {grants} went to ticket {ev[1]:#x}, expected {want:#x}"
+        return (inside, grants + 1), None
+    return (inside - 1, grants), None
+
+
+def check(model, nproc: int, ops: int, max_states: int = 2_000_000) -> Result:
+    """Explores every interleaving of `nproc` blocks doing `ops` operations each."""
+    sh0, loc0 = model.init(nproc, ops)
+    s0 = (sh0, loc0, _ghost0(model, nproc))
+    index = {s0: 0}
+    states = [s0]
+    parent = [-1]
+    succ: list[list[int]] = [[]]
+    stack = [0]
+    res = Result()
+    while stack:
+        i = stack.pop()
+        sh, locs, g = states[i]
+        for p in range(nproc):
+            if locs[p][0] == DONE:
+                continue
+            loc2, sh2, ev = model.step(p, locs[p], sh, nproc, ops)
+            g2, bad = _apply(model, g, p, ev, nproc)
+            s2 = (sh2, _set(locs, p, loc2), g2)
+            if bad:
+                res.violation = bad
+                res.states = len(states)
+                tr, j = [s2], i
+                while j >= 0:
+                    tr.append(states[j])
+                    j = parent[j]
+                res.trace = tr[::-1]
+                return res
+            j = index.get(s2)
+            if j is None:
+                j = len(states)
+                index[s2] = j
+                states.append(s2)
+                parent.append(i)
+                succ.append([])
+                stack.append(j)
+                if len(states) > max_states:
+                    raise RuntimeError("state space larger than max_states")
+            succ[i].append(j)
+    res.states = len(states)
+    # progress: every state must reach a final state (all blocks done)
+    pred: list[list[int]] = [[] for _ in states]
+    for i, ss in enumerate(succ):
+        for j in ss:
+            pred[j].append(i)
+    final = [i for i, (_, locs, _) in enumerate(states) if all(l[0] == DONE for l in locs)]
+    if not final:
+        res.violation = "no final state is reachable"
+        return res
+    reach = set(final)
+    work = list(final)
+    while work:
+        j = work.pop()
+        for i in pred[j]:
+            if i not in reach:
+                reach.add(i)
+                work.append(i)
+    if len(reach) != len(states):
+        stuck = next(i for i in range(len(states)) if i not in reach)
+        res.violation = "a reachable state cannot reach completion (deadlock or livelock)"
+        res.stuck_state = states[stuck]
+    return res

@@ -1,0 +1,71 @@
+"""Model checker: every algorithm passes on all interleavings of tiny inputs, and every
+planted mistake (in the oracle's models, on the CPU) is caught."""
+import pytest
+
+from oracle import model_check as mc
+
+W = 2 ** 32 - 3  # counters start just below 2^32 so that they wrap during the run
+
+CORRECT = [
+    ("spin_exch", mc.SpinMutex(), 3, 2),
+    ("spin_exch_atomic_unlock", mc.SpinMutex(atomic_unlock=True), 3, 2),
+    ("spin_backoff", mc.SpinMutex(backoff=True), 3, 2),
+    ("spin_cas", mc.SpinMutex(cas=True), 3, 2),
+    ("ticket", mc.TicketMutex(), 3, 2),
+    ("ticket_literal_unlock", mc.TicketMutex(literal=True), 3, 2),
+    ("ticket_wrap", mc.TicketMutex(base=W), 3, 2),
+    ("queue", mc.QueueMutex(q=4), 3, 2),
+    ("queue_wrap", mc.QueueMutex(q=4, base=W), 3, 2),
+    ("queue_exact_fit", mc.QueueMutex(q=2, base=W), 2, 3),
+    ("ring", mc.RingMutex(q=4), 3, 2),
+    ("spin_sem_1", mc.SpinSem(n=1), 3, 2),
+    ("spin_sem_2", mc.SpinSem(n=2), 3, 2),
+    ("spin_sem_2_backoff", mc.SpinSem(n=2, backoff=True), 3, 2),
+    ("sleep_sem_1", mc.SleepSem(n=1), 3, 2),
+    ("sleep_sem_2", mc.SleepSem(n=2), 3, 2),
+    ("sleep_sem_wrap", mc.SleepSem(n=1, base=W), 3, 2),
+    ("atomic_barrier", mc.AtomicBarrier(), 3, 2),
+    ("atomic_barrier_wrap", mc.AtomicBarrier(base=2 ** 32 - 1), 3, 3),
+    ("flag_barrier", mc.FlagBarrier(), 3, 2),
+    ("flag_barrier_broadcast", mc.FlagBarrier(broadcast=True), 3, 2),
+    ("flag_barrier_wrap", mc.FlagBarrier(base=2 ** 32 - 1), 3, 3),
+    ("tree_barrier_3", mc.TreeBarrier(fan=2), 3, 2),
+    ("tree_barrier_4", mc.TreeBarrier(fan=2), 4, 2),
+    ("cluster_barrier", mc.ClusterBarrier(c=2), 4, 2),
+]
+
+
+@pytest.mark.parametrize("name,model,nproc,ops", CORRECT, ids=[c[0] for c in CORRECT])
+def test_algorithm_is_safe_and_live(name, model, nproc, ops):
+    r = mc.check(model, nproc, ops)
+    assert r.ok, (r.violation, r.trace[-3:] if r.trace else r.stuck_state)
+    assert r.states > 10
+
+
+BROKEN = [
+    ("test_then_set", mc.SpinMutex(broken="test_then_set"), 2, 1, "critical section"),
+    ("ticket_no_advance", mc.TicketMutex(broken="no_advance"), 2, 2, "final state"),
+    ("ring_no_clear", mc.RingMutex(q=2, broken="no_clear"), 2, 3, "grant"),
+    ("sleep_sem_turn_ge", mc.SleepSem(n=1, broken="turn_ge"), 3, 1, "critical section"),
+    ("barrier_no_wait", mc.AtomicBarrier(broken="no_wait"), 3, 1, "passed round"),
+    ("flag_skip_last", mc.FlagBarrier(broken="skip_last"), 3, 1, "passed round"),
+]
+
+
+@pytest.mark.parametrize("name,model,nproc,ops,msg", BROKEN, ids=[b[0] for b in BROKEN])
+def test_planted_mistake_is_caught(name, model, nproc, ops, msg):
+    r = mc.check(model, nproc, ops)
+    assert not r.ok
+    assert msg in r.violation
+
+
+def test_queue_lock_rejects_ring_smaller_than_waiters():
+    # Q must be at least the number of blocks that can wait at once.
+    with pytest.raises(AssertionError):
+        mc.QueueMutex(q=2).init(3, 1)
+
+
+def test_wrap_safe_compare():
+    assert mc.s_gt(0, 2 ** 32 - 1)
+    assert not mc.s_gt(2 ** 32 - 1, 0)
+    assert mc.s_ge(5, 5) and not mc.s_gt(5, 5)
