@@ -1,0 +1,408 @@
+"""Benchmark of the inter-block synchronization hot path on GB300.
+
+One step = one pass over every row of the hot path at 1184 blocks:
+  * mutex contention (4 kinds x critical sections of 0/64/1024 words, 256 threads per block,
+    100 acquisitions per block, seeded delays U{0..2000} cycles),
+  * grid barriers (atomic, flag, tree, cluster 2/4/8; 128 threads, 1000 rounds each),
+  * counting semaphores (sleeping FA kind, n in {1, 4, 16, 64}; 128 threads, 200 pairs each,
+    hold U{100..5000} cycles).
+`value` is lock acquisitions per second of the library's default mutex kind over its three
+critical-section sizes; the other rows are reported beside it (barrier ns per crossing,
+semaphore ops/s).  The roofline terms (hand-off latency between SMs, critical-section time,
+same-word atomic throughput, atomic round trip) are measured by the probe kernels in the same
+run.  `--impl reference` times the CPU oracle (threaded C execution of the same workload on the
+host cores).  Under torchrun every rank runs the same workload on its own GPU (replicas).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NBLOCKS = 1184
+MUTEX_THREADS, MUTEX_ACQ, CS_SIZES = 256, 100, (0, 64, 1024)
+BAR_THREADS, BAR_ROUNDS = 128, 1000
+SEM_THREADS, SEM_PAIRS, SEM_COUNTS = 128, 200, (1, 4, 16, 64)
+DEFAULT_MUTEX = "sleep_queue"
+DEFAULT_BARRIER = ("flag", 0)
+BARRIERS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("cluster", 2), ("cluster", 4), ("cluster", 8)]
+MUTEX_BACKOFF = {"cas_backoff": (32, 2048)}
+METRIC = "lock acquires/s & barrier ns at 1184 blocks vs L2-atomic roofline; p99 latency"
+TIMEOUT_NS = 10_000_000_000
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gsync", choices=["gsync", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+
+def measure_roofline_terms(runner, G):
+    """L_handoff, T_cs(K), R_same and L_rt from the probe kernels (medians)."""
+    sms = runner.sm_count()
+    pairs = [(0, 1), (0, sms // 2), (0, sms - 1), (sms // 4, 3 * sms // 4), (2, sms - 3)]
+    hand = [runner.probe_pingpong(a, b, 4000) for a, b in pairs if a != b and 0 <= a < sms and 0 <= b < sms]
+    hand_ns = [h["handoff_ns"] for h in hand if h["status"] == 0]
+    L_handoff = float(np.median(hand_ns))
+    T_cs = {K: float(np.median([runner.probe_cs(K, MUTEX_THREADS, 20000)["ns_per_cs"] for _ in range(3)]))
+            for K in CS_SIZES}
+    rs = [runner.probe_throughput("red_add", True, False, NBLOCKS, 128, 2000)["ops_per_s"] for _ in range(3)]
+    ra = [runner.probe_throughput("atomic_read", True, False, NBLOCKS, 128, 1000)["ops_per_s"] for _ in range(3)]
+    L_rt = float(np.median([runner.probe_latency("atomic_read", 4000)["ns_per_op"] for _ in range(3)]))
+    return {"sms": sms, "L_handoff_ns": L_handoff, "L_handoff_pairs_ns": hand_ns, "T_cs_ns": T_cs,
+            "R_same_red_ops_s": float(np.median(rs)), "R_same_atom_ops_s": float(np.median(ra)), "L_rt_ns": L_rt}
+
+
+def mutex_roof_acq_s(terms, K):
+    return min(terms["R_same_atom_ops_s"] / 2.0, 1e9 / (terms["L_handoff_ns"] + terms["T_cs_ns"][K]))
+
+
+def barrier_roof_ns(terms, kind, param, B):
+    b_eff = B / param if kind == "cluster" else B
+    return terms["L_rt_ns"] + terms["L_handoff_ns"] + b_eff / terms["R_same_atom_ops_s"] * 1e9
+
+
+class GpuStep:
+    """All buffers of one step, allocated once; launch() enqueues the whole step."""
+
+    def __init__(self, runner, G, inputs):
+        import torch
+        self.torch = torch
+        self.mutex = {}
+        for kind in G.MUTEX_KINDS:
+            for K in CS_SIZES:
+                delay, add = inputs.mutex_inputs(NBLOCKS, MUTEX_ACQ, inputs.mutex_seed(G.MUTEX_KINDS[kind], NBLOCKS, K))
+                bo = runner.backoff(min_ns=MUTEX_BACKOFF[kind][0], max_ns=MUTEX_BACKOFF[kind][1]) \
+                    if kind in MUTEX_BACKOFF else None
+                self.mutex[(kind, K)] = (runner.MutexRun(kind, NBLOCKS, MUTEX_THREADS, MUTEX_ACQ, K, delay, add, bo=bo,
+                                                         timeout_ns=TIMEOUT_NS), add)
+        self.barrier = {(k, p): runner.BarrierRun(k, NBLOCKS, BAR_THREADS, BAR_ROUNDS, full=False, param=p,
+                                                  timeout_ns=TIMEOUT_NS) for k, p in BARRIERS}
+        self.sem = {}
+        for n in SEM_COUNTS:
+            hold, add = inputs.sem_inputs(NBLOCKS, SEM_PAIRS, inputs.SEED_SEM ^ (n << 16) ^ NBLOCKS)
+            self.sem[n] = (runner.SemRun("ticket", NBLOCKS, SEM_THREADS, SEM_PAIRS, n, hold, add,
+                                         timeout_ns=TIMEOUT_NS), add)
+        ev = lambda: torch.cuda.Event(enable_timing=True)
+        self.ev = {key: (ev(), ev()) for key in list(self.mutex) + list(self.barrier) + [("sem", n) for n in SEM_COUNTS]}
+        self.launches = 0
+
+    def launch(self):
+        """Enqueues one step; per-launch events on the launching (current) stream."""
+        launches = 0
+        for key, (mr, _) in self.mutex.items():
+            mr.reset()
+            a, b = self.ev[key]
+            a.record()
+            rc = mr.launch()
+            b.record()
+            assert rc == 0, (key, rc)
+            launches += 1
+        for key, br in self.barrier.items():
+            br.status.zero_()
+            a, b = self.ev[key]
+            a.record()
+            rc = br.launch()
+            b.record()
+            assert rc == 0, (key, rc)
+            launches += 1
+        for n, (sr, _) in self.sem.items():
+            sr.reset()
+            a, b = self.ev[("sem", n)]
+            a.record()
+            rc = sr.launch()
+            b.record()
+            assert rc == 0, (n, rc)
+            launches += 1
+        self.launches = launches
+
+    def times_ms(self):
+        return {k: a.elapsed_time(b) for k, (a, b) in self.ev.items()}
+
+    def verify(self, calc):
+        """Checks every workload's final state against the oracle (after a step)."""
+        bad = []
+        for (kind, K), (mr, add) in self.mutex.items():
+            got = mr.results()
+            want = calc.mutex_final(NBLOCKS, MUTEX_ACQ, K, add)
+            if got["status"] or got["total"] != want["total"] or not np.array_equal(got["data"], want["data"]):
+                bad.append(f"mutex {kind} K={K}")
+        for key, br in self.barrier.items():
+            st = int(br.status.cpu()[0])
+            mix = br.mix.cpu().numpy().view(np.uint32)
+            if st or br.bad.cpu().numpy().any() or not np.array_equal(mix, calc.barrier_sampled(NBLOCKS, BAR_ROUNDS)["mix"]):
+                bad.append(f"barrier {key}")
+        for n, (sr, add) in self.sem.items():
+            got = sr.results()
+            want = calc.sem_final(NBLOCKS, SEM_PAIRS, n, add)
+            if got["status"] or got["tally"] != want["tally"] or got["max_occ"] > n:
+                bad.append(f"sem n={n}")
+        return bad
+
+
+def flush_l2(torch, buf):
+    buf.zero_()  # 512 MiB write: larger than the 129 MB L2
+
+
+def e2e_mutex(G, inputs, kind, reps=3):
+    """Default-kind mutex workload through gsync_bench_mutex_host with pinned host buffers."""
+    import torch
+    total_acq, total_s = 0, 0.0
+    h2d = d2h = 0
+    for K in CS_SIZES:
+        n = NBLOCKS * MUTEX_ACQ
+        delay, add = inputs.mutex_inputs(NBLOCKS, MUTEX_ACQ, inputs.mutex_seed(G.MUTEX_KINDS[kind], NBLOCKS, K))
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).pin_memory()
+        hd, ha = pin(delay), pin(add)
+        outs = {nm: torch.zeros(sz, dtype=torch.int32).pin_memory()
+                for nm, sz in (("data", max(K, 1)), ("total", 1), ("log", n), ("ticket", n), ("count", NBLOCKS),
+                               ("status", 1))}
+        w = G.gsync_mutex_work(G.MUTEX_KINDS[kind], NBLOCKS, MUTEX_THREADS, MUTEX_ACQ, K, 0, hd.data_ptr(),
+                               ha.data_ptr(), outs["data"].data_ptr(), outs["total"].data_ptr(),
+                               outs["log"].data_ptr(), outs["ticket"].data_ptr(), outs["count"].data_ptr(),
+                               outs["status"].data_ptr())
+        nbytes = G.gsync_bench_mutex_workspace_bytes(w.kind, NBLOCKS, MUTEX_ACQ, K)
+        ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        bo = None
+        G.check("gsync_bench_mutex_host", G.gsync_bench_mutex_host(w, bo, ws, nbytes))  # warm-up
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            G.check("gsync_bench_mutex_host", G.gsync_bench_mutex_host(w, bo, ws, nbytes))
+            total_s += time.perf_counter() - t0
+            total_acq += n
+            assert int(outs["status"][0]) == 0 and int(outs["total"][0]) == n
+        h2d += 8 * n
+        d2h += 4 * (max(K, 0) + 1 + 2 * n + NBLOCKS + 1)
+    return {"value": total_acq / total_s, "unit": "acq/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "kind": kind}
+
+
+def cpu_baseline(inputs, kind):
+    """The CPU oracle (threaded C execution) on the host cores, same workload, one pass."""
+    from oracle import cpu
+    from paper_1110_4623_gb300 import gsync as G
+    acq, secs, threads = 0, 0.0, 0
+    for K in CS_SIZES:
+        delay, add = inputs.mutex_inputs(NBLOCKS, MUTEX_ACQ, inputs.mutex_seed(G.MUTEX_KINDS[kind], NBLOCKS, K))
+        r = cpu.mutex_run(kind, NBLOCKS, MUTEX_ACQ, K, add, delay)
+        acq += NBLOCKS * MUTEX_ACQ
+        secs += r["seconds"]
+        threads = r["threads"]
+    return {"value": acq / secs, "unit": "acq/s", "cores": threads, "kind": "oracle",
+            "sample": f"{kind} mutex, {NBLOCKS} blocks x {MUTEX_ACQ} acquisitions x CS {list(CS_SIZES)} words "
+                      f"(the full step's mutex workload of the default kind), blocks round-robin on {threads} threads"}
+
+
+def run_gpu(args):
+    import torch
+    from oracle import calc
+    from paper_1110_4623_gb300 import gsync as G, inputs, runner
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    G.lib()
+    terms = measure_roofline_terms(runner, G)
+    step = GpuStep(runner, G, inputs)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        step.launch()
+        torch.cuda.synchronize()
+    bad = step.verify(calc)
+    if bad:
+        raise SystemExit(f"parity failure after warm-up: {bad}")
+
+    per_step, per_kernel = [], []
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush_l2(torch, flush)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        step.launch()
+        s1.record()
+        torch.cuda.synchronize()
+        per_step.append(s0.elapsed_time(s1))
+        per_kernel.append(step.times_ms())
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    bad = step.verify(calc)
+
+    step_ms = float(np.mean(per_step))
+    if world > 1:
+        t = torch.tensor([step_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms = float(t.item())
+
+    med = {k: float(np.median([pk[k] for pk in per_kernel])) for k in per_kernel[0]}
+    mutex = {}
+    for (kind, K) in step.mutex:
+        ms = med[(kind, K)]
+        mutex.setdefault(kind, {})[K] = {"ms": ms, "acq_per_s": NBLOCKS * MUTEX_ACQ / (ms * 1e-3),
+                                         "roof_acq_per_s": mutex_roof_acq_s(terms, K)}
+    def_ms = sum(med[(DEFAULT_MUTEX, K)] for K in CS_SIZES)
+    def_acq = NBLOCKS * MUTEX_ACQ * len(CS_SIZES)
+    value = def_acq / (def_ms * 1e-3) * world
+    roof_ms = sum(NBLOCKS * MUTEX_ACQ / mutex_roof_acq_s(terms, K) * 1e3 for K in CS_SIZES)
+    peak = def_acq / (roof_ms * 1e-3)
+    barrier = {}
+    for (k, p) in step.barrier:
+        ns = med[(k, p)] * 1e6 / BAR_ROUNDS
+        roof = barrier_roof_ns(terms, k, max(p, 1), NBLOCKS)
+        barrier[f"{k}{p if k in ('tree', 'cluster') else ('_broadcast' if p else '')}"] = {
+            "ns_per_crossing": ns, "roof_ns": roof, "frac": roof / ns}
+    dk, dp = DEFAULT_BARRIER
+    bkey = f"{dk}{'_broadcast' if dp else ''}"
+    sem = {}
+    for n in SEM_COUNTS:
+        ms = med[("sem", n)]
+        sem[n] = {"ops_per_s": NBLOCKS * SEM_PAIRS / (ms * 1e-3)}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "acq/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded SplitMix64 delays/addends/hold times)",
+        "config": {"workload": f"mutex contention, {NBLOCKS} blocks x {MUTEX_THREADS} threads, {MUTEX_ACQ} "
+                               f"acquisitions/block, CS {list(CS_SIZES)} int32 words, delays U{{0..2000}} cycles; "
+                               f"+ barriers ({BAR_ROUNDS} rounds) and semaphores ({SEM_PAIRS} pairs) at {NBLOCKS} blocks",
+                   "default_mutex": DEFAULT_MUTEX, "default_barrier": bkey, "nblocks": NBLOCKS,
+                   "l2": "flushed (512 MiB write) before every timed step", "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "l2_handoff_latency", "achieved": value / world, "peak": peak, "unit": "acq/s",
+                     "frac": (value / world) / peak, "traffic": None,
+                     "peak_source": "measured live: 1e9 / (L_handoff + T_cs(K)) per CS size, from the ping-pong and "
+                                    "critical-section probe kernels of this run (min with R_same/2)"},
+        "barrier": {"default": bkey, "ns_per_crossing": barrier[bkey]["ns_per_crossing"], "kinds": barrier},
+        "mutex": {k: {str(K): v for K, v in d.items()} for k, d in mutex.items()},
+        "semaphore": {"kind": "ticket", "ops_per_s": {str(n): v["ops_per_s"] for n, v in sem.items()}},
+        "roofline_terms": terms,
+        "clocks": clk,
+        "gpu_launches": step.launches * args.steps,
+        "wall_s_timed_loop": wall,
+        "parity_after_timing": "ok" if not bad else bad,
+    }
+    if rank == 0:
+        out["e2e"] = e2e_mutex(G, inputs, DEFAULT_MUTEX)
+        out["e2e"]["value"] *= world
+        if not args.no_cpu_baseline and world == 1:
+            out["cpu_baseline"] = cpu_baseline(inputs, DEFAULT_MUTEX)
+        print(json.dumps(out, default=float))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1110_4623_gb300 import inputs
+    vals, secs_total = [], 0.0
+    base = None
+    t_all = time.perf_counter()
+    for _ in range(args.warmup):
+        cpu_baseline(inputs, DEFAULT_MUTEX)
+    for _ in range(args.steps):
+        base = cpu_baseline(inputs, DEFAULT_MUTEX)
+        vals.append(base["value"])
+    value = float(np.median(vals))
+    step_ms = NBLOCKS * MUTEX_ACQ * len(CS_SIZES) / value * 1e3
+    out = {"metric": METRIC, "impl": "reference", "value": value, "unit": "acq/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+           "config": {"workload": f"mutex contention, {NBLOCKS} blocks, {MUTEX_ACQ} acquisitions/block, CS "
+                                  f"{list(CS_SIZES)} words ({DEFAULT_MUTEX})", "nblocks": NBLOCKS},
+           "cpu_baseline": {"value": value, "unit": "acq/s", "cores": base["cores"], "kind": "oracle",
+                            "sample": base["sample"]},
+           "e2e": {"value": value, "unit": "acq/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "wall_s": time.perf_counter() - t_all}
+    print(json.dumps(out, default=float))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,261 @@
+/*
+ * gsync.h -- C ABI of the inter-block GPU synchronization library (sm_103a).
+ *
+ * Implements the primitives of Stuart & Owens, "Efficient Synchronization Primitives for
+ * GPUs": the grid barrier, the mutex (spin lock, spin lock with backoff, fetch-and-add
+ * ticket lock, sleep-waiting queue lock) and the counting semaphore (sleeping FA semaphore,
+ * spin-lock semaphore with and without backoff), plus the memory-system probes that
+ * classify a GPU under the paper's machine abstraction.  Device-side calls are in
+ * gsync_device.cuh; this header holds the host entry points.
+ *
+ * Conventions shared by every entry point:
+ *  - Memory: the library never allocates.  Every pointer named "device" is caller-owned
+ *    device memory; "host" pointers are caller-owned host memory.  Objects (the `state`
+ *    buffers) must be 128-byte aligned and sized with the matching gsync_*_bytes().
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Entry points enqueue work and return without synchronizing, except the *_host
+ *    variants, which copy host buffers in and out and synchronize `stream`.
+ *  - Errors: every entry point returns a gsync_status; nothing throws or exits.  Device
+ *    waits are bounded by the object's timeout; a timed-out or aborted wait is reported in
+ *    the caller's `status` word (bit GSYNC_STATUS_TIMEOUT / GSYNC_STATUS_ABORTED) and in
+ *    the object's abort word, and the kernel returns instead of hanging.
+ *  - Block semantics (Section 3): one request per block; every thread of a block calls the
+ *    device function, thread 0 acts, __syncthreads arbitrates inside the block.
+ */
+#ifndef GSYNC_H
+#define GSYNC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gsync_status {
+  GSYNC_OK = 0,
+  GSYNC_EINVAL = 1,        /* bad argument: size, alignment, kind, or a buffer too small */
+  GSYNC_ENOTRESIDENT = 2,  /* the grid cannot be co-resident, so a barrier could deadlock */
+  GSYNC_ETIMEDOUT = 3,     /* a device wait exceeded the object's timeout */
+  GSYNC_ECUDA = 4,         /* a CUDA runtime call failed (see gsync_last_cuda_error) */
+  GSYNC_EABORTED = 5       /* a device wait gave up because another wait timed out */
+} gsync_status;
+
+/* Bits of the device `status` word that the workload kernels OR in. */
+enum {
+  GSYNC_STATUS_TIMEOUT = 1u,
+  GSYNC_STATUS_ABORTED = 2u,
+  GSYNC_STATUS_VIOLATION = 4u, /* a workload saw an impossible state (e.g. a grant index past the end) */
+  GSYNC_STATUS_CONFIG = 8u     /* launch shape does not match the object (e.g. grid != nblocks) */
+};
+
+/* Mutex kinds (Section 5, "Mutex"; Appendix, spin-lock and FA mutex pseudocode). */
+typedef enum gsync_mutex_kind {
+  GSYNC_MUTEX_CAS_SPIN = 0,    /* spin on atomicCAS(0 -> 1); unlock = release store 0 */
+  GSYNC_MUTEX_CAS_BACKOFF = 1, /* the same with __nanosleep backoff after each failure */
+  GSYNC_MUTEX_TICKET = 2,      /* fetch-and-add ticket; poll turn; unlock stores turn + 1 */
+  GSYNC_MUTEX_SLEEP_QUEUE = 3  /* queue lock: each waiter polls its own padded flag slot */
+} gsync_mutex_kind;
+
+/* Barrier kinds (Section 5, "Barrier"). */
+typedef enum gsync_barrier_kind {
+  GSYNC_BAR_ATOMIC = 0,  /* two-stage atomic counter + release epoch */
+  GSYNC_BAR_FLAG = 1,    /* decentralized flag barrier of Xiao and Feng (XF) */
+  GSYNC_BAR_TREE = 2,    /* combining tree of atomic counters, fan-in = param */
+  GSYNC_BAR_CLUSTER = 3  /* hardware cluster barrier, then one leader per cluster on a counter */
+} gsync_barrier_kind;
+
+/* Semaphore kinds (Section 5, "Semaphore"; Appendix, spin-lock and sleeping semaphores). */
+typedef enum gsync_sem_kind {
+  GSYNC_SEM_TICKET = 0,       /* sleeping FA semaphore: <= 2 atomics per wait and per post */
+  GSYNC_SEM_SPIN = 1,         /* spin-lock semaphore: S = X + 1, swap with 0 to update */
+  GSYNC_SEM_SPIN_BACKOFF = 2  /* the same with backoff in wait (not in post) */
+} gsync_sem_kind;
+
+/* Backoff policy (Section 5: "Backoff"; the paper's counter I runs from Imin to Imax by +1
+ * and wraps; exponential doubling is the other common policy). */
+enum { GSYNC_BACKOFF_EXPONENTIAL = 0, GSYNC_BACKOFF_LINEAR_CYCLIC = 1 };
+
+typedef struct gsync_backoff {
+  uint32_t policy; /* GSYNC_BACKOFF_* */
+  uint32_t min_ns; /* first sleep (and, for ticket locks, sleep per waiter ahead); 0 = no sleeping */
+  uint32_t max_ns; /* cap */
+  uint32_t reserved;
+} gsync_backoff;
+
+/* ------------------------------------------------------------------------------------ */
+/* Objects: size query and initialisation (Algorithm 1: CreateSpinLock allocates a word  */
+/* and zeroes it; here the caller allocates and the library writes the initial state).   */
+/* ------------------------------------------------------------------------------------ */
+
+/* Bytes of a mutex for at most `max_waiters` blocks waiting at once; 0 if invalid. */
+size_t gsync_mutex_bytes(int kind, int max_waiters);
+/* Writes the initial state of a mutex into `state` (device) on `stream`.  `backoff` (host,
+ * may be NULL for no sleeping) is copied; timeout_ns = 0 selects 2 s. */
+int gsync_mutex_init(void* state, size_t bytes, int kind, int max_waiters,
+                     const gsync_backoff* backoff, uint64_t timeout_ns, void* stream);
+
+/* Bytes of a barrier for `nblocks` blocks.  param: fan-in (TREE, >= 2), cluster size
+ * (CLUSTER, 1..8, divides nblocks), release mode (FLAG: 0 one flag per block, 1 one word). */
+size_t gsync_barrier_bytes(int kind, int nblocks, int param);
+int gsync_barrier_init(void* state, size_t bytes, int kind, int nblocks, int param,
+                       uint64_t timeout_ns, void* stream);
+
+/* Bytes of a counting semaphore. */
+size_t gsync_sem_bytes(int kind);
+/* Initial count n >= 1 (Section 5: at most n blocks inside at once). */
+int gsync_sem_init(void* state, size_t bytes, int kind, int initial_count,
+                   const gsync_backoff* backoff, uint64_t timeout_ns, void* stream);
+
+/* Reads an object's abort word (device -> host, synchronous on `stream`): 0 when no wait
+ * on the object has timed out. */
+int gsync_object_abort_flag(const void* state, uint32_t* flag_out, void* stream);
+
+/* ------------------------------------------------------------------------------------ */
+/* Co-residency (Section 5: the barrier needs every block resident, "persistent threads") */
+/* ------------------------------------------------------------------------------------ */
+
+/* Largest grid of the given workload kernel that is co-resident on the current device
+ * with `block_threads` threads per block (and `cluster` blocks per cluster when > 1).
+ * workload: 0 barrier, 1 mutex, 2 semaphore; kind: that workload's kind enum. */
+int gsync_max_coresident_blocks(int workload, int kind, int block_threads, int cluster,
+                                int* max_blocks_out);
+
+/* Number of SMs of the current device. */
+int gsync_device_sm_count(int* sms_out);
+
+/* Last CUDA error code seen by the library on this thread (cudaError_t as int). */
+int gsync_last_cuda_error(void);
+
+/* ------------------------------------------------------------------------------------ */
+/* Workloads (Section 6, "Results": one kernel, a loop of operations per block).          */
+/* All launches are cooperative (or occupancy-checked cluster launches): a grid that     */
+/* cannot be co-resident returns GSYNC_ENOTRESIDENT before anything runs.                */
+/* ------------------------------------------------------------------------------------ */
+
+/* Barrier workload.  Round r: block b writes slots[(r&1)*nblocks + b] = r*nblocks + b,
+ * crosses the barrier, then reads slots of the same half:
+ *   full = 1: every slot j; chk[r*nblocks + b] = XOR_j slot_j; mix[b] = rotl(mix[b],5) ^
+ *             (sum_j lowbias32(slot_j)); bad[b] += #(slot_j != r*nblocks + j)
+ *   full = 0: partner p = (b + r + 1) mod nblocks; mix[b] = rotl(mix[b],5) ^ lowbias32(slot_p);
+ *             bad[b] += (slot_p != r*nblocks + p)
+ * Buffers (device): slots [2*nblocks] (scratch), chk [rounds*nblocks] (full only, else NULL),
+ * mix [nblocks], bad [nblocks], status [1] (OR of GSYNC_STATUS_*; caller zeroes).
+ * `state` must be a barrier initialised for nblocks (and `cluster` for CLUSTER). */
+typedef struct gsync_barrier_work {
+  int32_t kind, nblocks, block_threads, rounds, full, cluster;
+  uint32_t* slots;
+  uint32_t* chk;
+  uint32_t* mix;
+  uint32_t* bad;
+  uint32_t* status;
+} gsync_barrier_work;
+int gsync_bench_barrier(void* state, const gsync_barrier_work* w, void* stream);
+
+/* Mutex workload.  Block b makes `acq` acquisitions (id = b*acq + a): it waits delay[id]
+ * SM cycles, locks, and inside the critical section its thread 0 appends id to
+ * grant_log[total] and increments total (plain load/store), records the lock ticket in
+ * ticket[id] (0xFFFFFFFF for the CAS kinds), and its threads add addend[id] XOR
+ * (i * 0x9E3779B1) to data[i] for every i < cs_words (plain loads/stores); then it unlocks.
+ * count[b] receives the number of completed acquisitions.
+ * Buffers (device): delay, addend, grant_log, ticket [nblocks*acq]; data [cs_words];
+ * total [1]; count [nblocks]; status [1].  data, total and status must start at zero. */
+typedef struct gsync_mutex_work {
+  int32_t kind, nblocks, block_threads, acq, cs_words, reserved;
+  const uint32_t* delay;
+  const uint32_t* addend;
+  uint32_t* data;
+  uint32_t* total;
+  uint32_t* grant_log;
+  uint32_t* ticket;
+  uint32_t* count;
+  uint32_t* status;
+} gsync_mutex_work;
+int gsync_bench_mutex(void* state, const gsync_mutex_work* w, void* stream);
+
+/* The mutex workload from host buffers: copies delay and addend (host) into `workspace`
+ * (device, >= gsync_bench_mutex_workspace_bytes bytes), initialises the mutex there, runs
+ * the workload, and copies data, total, grant_log, ticket, count and status back into the
+ * host buffers of `w` (whose pointers are host pointers here), then synchronizes `stream`. */
+size_t gsync_bench_mutex_workspace_bytes(int kind, int nblocks, int acq, int cs_words);
+int gsync_bench_mutex_host(const gsync_mutex_work* w, const gsync_backoff* backoff,
+                           void* workspace, size_t workspace_bytes, void* stream);
+
+/* Semaphore workload.  Block b makes `pairs` wait/post pairs (id = b*pairs + p); inside,
+ * thread 0 counts itself into `occupancy` (atomic), raises max_occupancy, increments total
+ * with a plain load/store when the initial count is 1, holds for hold[id] SM cycles, adds
+ * addend[id] to tally (atomic) and counts itself out before posting.
+ * Buffers (device): hold, addend [nblocks*pairs]; occupancy, max_occupancy, total, tally,
+ * status [1] (zeroed by the caller); count [nblocks]. */
+typedef struct gsync_sem_work {
+  int32_t kind, nblocks, block_threads, pairs, initial_count, reserved;
+  const uint32_t* hold;
+  const uint32_t* addend;
+  uint32_t* occupancy;
+  uint32_t* max_occupancy;
+  uint32_t* total;
+  uint32_t* tally;
+  uint32_t* count;
+  uint32_t* status;
+} gsync_sem_work;
+int gsync_bench_sem(void* state, const gsync_sem_work* w, void* stream);
+
+/* ------------------------------------------------------------------------------------ */
+/* Memory-system probes (Section 3, "Benchmarks"; Section 4 machine abstraction).        */
+/* ------------------------------------------------------------------------------------ */
+
+/* Access patterns of the paper's twelve + four probes and of the GB300 additions. */
+typedef enum gsync_probe_op {
+  GSYNC_PROBE_VOLATILE_LOAD = 0,   /* ld.volatile                          (paper: volatile read) */
+  GSYNC_PROBE_VOLATILE_STORE = 1,  /* st.volatile                          (paper: volatile write) */
+  GSYNC_PROBE_ATOMIC_READ = 2,     /* atomicAdd(p, 0)                      (paper: atomic read) */
+  GSYNC_PROBE_ATOMIC_WRITE = 3,    /* atomicExch(p, 0)                     (paper: atomic write) */
+  GSYNC_PROBE_LOAD_ACQUIRE = 4,    /* ld.acquire.gpu */
+  GSYNC_PROBE_LOAD_RELAXED = 5,    /* ld.relaxed.gpu */
+  GSYNC_PROBE_STORE_RELEASE = 6,   /* st.release.gpu */
+  GSYNC_PROBE_RED_ADD = 7,         /* red.relaxed.gpu.add (no return) */
+  GSYNC_PROBE_ATOMIC_ADD64 = 8,    /* atom.add.u64 */
+  GSYNC_PROBE_ATOMIC_ACQREL = 9    /* atom.acq_rel.gpu.add */
+} gsync_probe_op;
+
+/* Throughput probe: `nblocks` blocks of `block_threads` threads; the master thread of each
+ * block performs `iters` accesses of `op` to one shared word (contentious = 1) or to its own
+ * word 256 bytes from the next block's (contentious = 0); pre_atomic = 1 issues one atomic
+ * on the word first (the paper's "volatile preceded by atomic").  Each block writes its
+ * start and end %globaltimer to times[2*b], times[2*b+1].  scratch (device) needs
+ * 256 * nblocks bytes and is overwritten. */
+int gsync_probe_throughput(int op, int contentious, int pre_atomic, int nblocks,
+                           int block_threads, int iters, void* scratch, uint64_t* times,
+                           void* stream);
+
+/* Latency probe: one thread performs `iters` dependent accesses (each address depends on
+ * the previous result): op = ATOMIC_READ (atom.add round trip, L_rt) or LOAD_RELAXED (L2
+ * load round trip).  out[0] = elapsed ns, out[1] = elapsed SM cycles. */
+int gsync_probe_latency(int op, int iters, void* scratch, uint64_t* out, void* stream);
+
+/* Ping-pong probe: the blocks on SMs sm_a and sm_b pass a token back and forth `iters`
+ * times through release stores and acquire loads on separate lines; out[0] = elapsed ns
+ * for the whole exchange (a hand-off is out[0] / (2 * iters)), out[1] = the SM of side A,
+ * out[2] = the SM of side B, out[3] = status (0 ok).  Launches one block per SM.
+ * scratch needs 512 bytes. */
+int gsync_probe_pingpong(int sm_a, int sm_b, int iters, void* scratch, uint64_t* out,
+                         void* stream);
+
+/* Sleep probe: for each requested duration req_ns[i] (device, n entries) one thread calls
+ * __nanosleep `iters` times and writes the mean measured ns per call to out_ns[i]. */
+int gsync_probe_nanosleep(const uint32_t* req_ns, int n, int iters, uint64_t* out_ns,
+                          void* stream);
+
+/* Critical-section probe (T_cs): one block runs the mutex workload's critical-section body
+ * (with the release store that ends it) `iters` times with no lock and no delay, timed with
+ * CUDA events; out[0] = elapsed ns.  Synchronizes `stream`.  scratch (device, 256-byte
+ * aligned) needs gsync_probe_cs_scratch_bytes(cs_words, iters) bytes. */
+int gsync_probe_cs(int cs_words, int block_threads, int iters, void* scratch, uint64_t* out,
+                   void* stream);
+size_t gsync_probe_cs_scratch_bytes(int cs_words, int iters);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSYNC_H */

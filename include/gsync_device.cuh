@@ -1,0 +1,533 @@
+// gsync_device.cuh -- device-side inter-block synchronization primitives for sm_103a.
+//
+// Stuart & Owens, "Efficient Synchronization Primitives for GPUs": barriers, mutexes and
+// counting semaphores with *block semantics* (Section 3: one request per block, made by a
+// master thread, with __syncthreads arbitrating inside the block).  The API follows the
+// paper's listing (Section 5, "API"): Barrier(), Mutex Lock()/Unlock(), Semaphore
+// Wait()/Post(), with no non-blocking variants.
+//
+// Every object lives in caller-owned device memory, laid out by gsync_*_init() (gsync.h):
+// line 0 is a read-only header, and every word that blocks contend on sits on its own
+// 128-byte line.  A kernel attaches once (gsync::*_attach reads the header into registers)
+// and then calls the block-level functions, which all threads of the block must reach.
+//
+// Memory model (PTX ISA): the paper's "volatile" polls become ld.acquire.gpu, its plain
+// release stores become st.release.gpu, and its atomics become atom.{relaxed,acquire,
+// acq_rel}.gpu, which make the critical-section data of a block (plain loads and stores by
+// any of its threads) visible to the next holder: __syncthreads orders the block's accesses
+// before the master's gpu-scope release, and the acquiring master's __syncthreads orders
+// them before its threads' accesses.
+//
+// Every wait is bounded: a wait that sees no progress for the object's timeout (globaltimer
+// nanoseconds) sets the object's abort word and returns GSYNC_ETIMEDOUT; waits that see the
+// abort word set return GSYNC_EABORTED.  Nothing traps, asserts or spins forever.
+#pragma once
+#include <stdint.h>
+
+#include "gsync.h"
+
+namespace gsync {
+
+// ---------------------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------------------
+namespace ptx {
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.volatile.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_volatile(uint32_t* p, uint32_t v) {
+  asm volatile("st.volatile.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t atom_add_relaxed(uint32_t* p, uint32_t v) {
+  uint32_t r;
+  asm volatile("atom.relaxed.gpu.global.add.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
+  return r;
+}
+__device__ __forceinline__ uint32_t atom_add_acquire(uint32_t* p, uint32_t v) {
+  uint32_t r;
+  asm volatile("atom.acquire.gpu.global.add.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
+  return r;
+}
+__device__ __forceinline__ uint32_t atom_add_release(uint32_t* p, uint32_t v) {
+  uint32_t r;
+  asm volatile("atom.release.gpu.global.add.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
+  return r;
+}
+__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t* p, uint32_t v) {
+  uint32_t r;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
+  return r;
+}
+__device__ __forceinline__ void red_add_relaxed(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_release(uint32_t* p, uint32_t v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t atom_cas_acquire(uint32_t* p, uint32_t cmp, uint32_t v) {
+  uint32_t r;
+  asm volatile("atom.acquire.gpu.global.cas.b32 %0, [%1], %2, %3;" : "=r"(r) : "l"(p), "r"(cmp), "r"(v) : "memory");
+  return r;
+}
+__device__ __forceinline__ uint32_t atom_exch_acquire(uint32_t* p, uint32_t v) {
+  uint32_t r;
+  asm volatile("atom.acquire.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
+  return r;
+}
+__device__ __forceinline__ uint32_t atom_exch_release(uint32_t* p, uint32_t v) {
+  uint32_t r;
+  asm volatile("atom.release.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
+  return r;
+}
+__device__ __forceinline__ uint32_t atom_exch_relaxed(uint32_t* p, uint32_t v) {
+  uint32_t r;
+  asm volatile("atom.relaxed.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
+  return r;
+}
+__device__ __forceinline__ void atom_or_relaxed(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void atom_max_relaxed(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.max.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ uint32_t smid() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_nctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+// Hardware barrier over every thread of every block of the cluster.
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+}  // namespace ptx
+
+// Wrap-safe "a is after b" for uint32 tickets and epochs (fewer than 2^31 outstanding).
+__device__ __forceinline__ bool after(uint32_t a, uint32_t b) { return (int32_t)(a - b) > 0; }
+
+// ---------------------------------------------------------------------------------------
+// State layout (words; a line is 32 words = 128 bytes)
+// ---------------------------------------------------------------------------------------
+enum : uint32_t { kLineWords = 32 };
+enum HeaderWord : uint32_t {
+  kHdrMagic = 0, kHdrN = 1, kHdrParam = 2, kHdrPolicy = 3, kHdrMinNs = 4, kHdrMaxNs = 5,
+  kHdrTimeoutLo = 6, kHdrTimeoutHi = 7, kHdrAbort = 8, kHdrMode = 9,
+};
+
+// Bounded polling: every 32 polls it checks the deadline (set lazily at the first check,
+// so an uncontended call never reads the timer) and the object's abort word.
+struct Waiter {
+  uint64_t deadline = 0;
+  uint32_t polls = 0;
+  __device__ __forceinline__ int tick(uint64_t timeout_ns, uint32_t* abort_word) {
+    if ((++polls & 31u) != 0) return GSYNC_OK;
+    const uint64_t now = ptx::globaltimer();
+    if (deadline == 0) deadline = now + timeout_ns;
+    if (ptx::ld_relaxed(abort_word) != 0) return GSYNC_EABORTED;
+    if (now > deadline) {
+      ptx::atom_or_relaxed(abort_word, 1u);
+      return GSYNC_ETIMEDOUT;
+    }
+    return GSYNC_OK;
+  }
+};
+
+struct Backoff {
+  uint32_t policy, min_ns, max_ns;
+  // Next sleep after `cur`: doubling up to max_ns (exponential), or the paper's cyclic
+  // policy that adds min_ns after each failure and wraps back to min_ns past max_ns.
+  __device__ __forceinline__ uint32_t next(uint32_t cur) const {
+    if (policy == GSYNC_BACKOFF_LINEAR_CYCLIC) {
+      const uint32_t n = cur + min_ns;
+      return n > max_ns ? min_ns : n;
+    }
+    const uint32_t n = cur * 2u;
+    return n > max_ns ? max_ns : n;
+  }
+};
+
+__device__ __forceinline__ uint64_t header_timeout(const uint32_t* s) {
+  uint64_t t = ((uint64_t)s[kHdrTimeoutHi] << 32) | s[kHdrTimeoutLo];
+  return t ? t : 2000000000ull;
+}
+
+// ---------------------------------------------------------------------------------------
+// Mutex (Section 5 "Mutex"; Appendix: spin-lock mutex, FA mutex)
+// ---------------------------------------------------------------------------------------
+// line 1: lock word (CAS kinds) or ticket counter (TICKET, SLEEP_QUEUE)
+// line 2: turn (TICKET)
+// lines 3 .. 3+Q-1: one flag per queue slot (SLEEP_QUEUE), Q = power of two >= waiters
+struct MutexRef {
+  uint32_t* s;
+  uint32_t kind, qmask;
+  Backoff bo;
+  uint64_t timeout_ns;
+  __device__ __forceinline__ uint32_t* lockw() const { return s + 1 * kLineWords; }
+  __device__ __forceinline__ uint32_t* turn() const { return s + 2 * kLineWords; }
+  __device__ __forceinline__ uint32_t* flag(uint32_t t) const { return s + (3 + (t & qmask)) * kLineWords; }
+  __device__ __forceinline__ uint32_t* abort_word() const { return s + kHdrAbort; }
+};
+
+__device__ __forceinline__ MutexRef mutex_attach(void* state) {
+  MutexRef m;
+  m.s = (uint32_t*)state;
+  m.kind = m.s[kHdrMagic] & 0xFFu;
+  m.qmask = m.s[kHdrParam] ? m.s[kHdrParam] - 1u : 0u;
+  m.bo.policy = m.s[kHdrPolicy];
+  m.bo.min_ns = m.s[kHdrMinNs];
+  m.bo.max_ns = m.s[kHdrMaxNs];
+  m.timeout_ns = header_timeout(m.s);
+  return m;
+}
+
+// Result of a lock: the status and the ticket the holder needs to unlock.
+struct Token {
+  int status;
+  uint32_t ticket;
+};
+
+// Master-thread lock.  Returns the ticket (ticket kinds) in tok.ticket.
+template <int KIND>
+__device__ __forceinline__ Token mutex_lock_thread(const MutexRef& m) {
+  Waiter w;
+  if (KIND == GSYNC_MUTEX_CAS_SPIN || KIND == GSYNC_MUTEX_CAS_BACKOFF) {
+    // Algorithm 1 / spin-lock mutex: swap 1 in until the old value was 0 (atomicCAS form).
+    uint32_t sleep_ns = m.bo.min_ns;
+    while (ptx::atom_cas_acquire(m.lockw(), 0u, 1u) != 0u) {
+      if (int rc = w.tick(m.timeout_ns, m.abort_word())) return {rc, 0u};
+      if (KIND == GSYNC_MUTEX_CAS_BACKOFF) {
+        __nanosleep(sleep_ns);
+        sleep_ns = m.bo.next(sleep_ns);
+      }
+    }
+    return {GSYNC_OK, 0xFFFFFFFFu};
+  } else if (KIND == GSYNC_MUTEX_TICKET) {
+    // FA mutex: take a ticket, poll the turn; sleep in proportion to the queue ahead.
+    const uint32_t t = ptx::atom_add_relaxed(m.lockw(), 1u);
+    uint32_t cur;
+    while ((cur = ptx::ld_acquire(m.turn())) != t) {
+      if (int rc = w.tick(m.timeout_ns, m.abort_word())) return {rc, t};
+      const uint32_t ahead = t - cur;
+      if (m.bo.min_ns && ahead > 1u && ahead < 0x80000000u) {
+        const uint32_t ns = (ahead - 1u) * m.bo.min_ns;
+        __nanosleep(ns < m.bo.max_ns ? ns : m.bo.max_ns);
+      }
+    }
+    return {GSYNC_OK, t};
+  } else {
+    // Queue lock: take a slot, poll the slot's own flag until it holds this ticket.
+    const uint32_t t = ptx::atom_add_relaxed(m.lockw(), 1u);
+    uint32_t* f = m.flag(t);
+    while (ptx::ld_acquire(f) != t) {
+      if (int rc = w.tick(m.timeout_ns, m.abort_word())) return {rc, t};
+      if (m.bo.min_ns) __nanosleep(m.bo.min_ns);
+    }
+    return {GSYNC_OK, t};
+  }
+}
+
+template <int KIND>
+__device__ __forceinline__ void mutex_unlock_thread(const MutexRef& m, uint32_t ticket) {
+  if (KIND == GSYNC_MUTEX_CAS_SPIN || KIND == GSYNC_MUTEX_CAS_BACKOFF) {
+    ptx::st_release(m.lockw(), 0u);
+  } else if (KIND == GSYNC_MUTEX_TICKET) {
+    ptx::st_release(m.turn(), ticket + 1u);  // only the holder writes turn: no atomic
+  } else {
+    ptx::st_release(m.flag(ticket + 1u), ticket + 1u);
+  }
+}
+
+// Block-level lock (all threads): thread 0 acquires, the block then proceeds together.
+template <int KIND>
+__device__ __forceinline__ Token mutex_lock(const MutexRef& m) {
+  __shared__ Token s_tok;
+  if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) s_tok = mutex_lock_thread<KIND>(m);
+  __syncthreads();
+  const Token t = s_tok;
+  return t;
+}
+
+// Block-level unlock: the block's critical-section accesses complete before the release.
+template <int KIND>
+__device__ __forceinline__ void mutex_unlock(const MutexRef& m, Token t) {
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) mutex_unlock_thread<KIND>(m, t.ticket);
+}
+
+// ---------------------------------------------------------------------------------------
+// Counting semaphore (Section 5 "Semaphore"; Appendix: spin-lock and sleeping semaphores)
+// ---------------------------------------------------------------------------------------
+// TICKET (sleeping): line 1 count, line 2 ticket, line 3 turn; header N = max count.
+// SPIN / SPIN_BACKOFF: line 1 S (initially N + 1; 0 while a block updates it).
+struct SemRef {
+  uint32_t* s;
+  uint32_t kind, n;
+  Backoff bo;
+  uint64_t timeout_ns;
+  __device__ __forceinline__ uint32_t* word(int line) const { return s + line * kLineWords; }
+  __device__ __forceinline__ uint32_t* abort_word() const { return s + kHdrAbort; }
+};
+
+__device__ __forceinline__ SemRef sem_attach(void* state) {
+  SemRef r;
+  r.s = (uint32_t*)state;
+  r.kind = r.s[kHdrMagic] & 0xFFu;
+  r.n = r.s[kHdrN];
+  r.bo.policy = r.s[kHdrPolicy];
+  r.bo.min_ns = r.s[kHdrMinNs];
+  r.bo.max_ns = r.s[kHdrMaxNs];
+  r.timeout_ns = header_timeout(r.s);
+  return r;
+}
+
+template <int KIND>
+__device__ __forceinline__ int sem_wait_thread(const SemRef& s) {
+  Waiter w;
+  if (KIND == GSYNC_SEM_TICKET) {
+    // One atomic when under capacity; otherwise take a wait ticket and poll the turn.
+    const uint32_t old = ptx::atom_add_acquire(s.word(1), 1u);
+    if ((int32_t)old < (int32_t)s.n) return GSYNC_OK;
+    const uint32_t wi = ptx::atom_add_relaxed(s.word(2), 1u);
+    while (!after(ptx::ld_acquire(s.word(3)), wi)) {
+      if (int rc = w.tick(s.timeout_ns, s.abort_word())) return rc;
+      if (s.bo.min_ns) __nanosleep(s.bo.min_ns);
+    }
+    return GSYNC_OK;
+  } else {
+    uint32_t sleep_ns = s.bo.min_ns;
+    for (;;) {
+      const uint32_t v = ptx::atom_exch_acquire(s.word(1), 0u);
+      if (v > 1u) {
+        ptx::atom_exch_relaxed(s.word(1), v - 1u);
+        return GSYNC_OK;
+      }
+      if (v == 1u) ptx::atom_exch_relaxed(s.word(1), 1u);
+      if (int rc = w.tick(s.timeout_ns, s.abort_word())) return rc;
+      if (KIND == GSYNC_SEM_SPIN_BACKOFF) {
+        __nanosleep(sleep_ns);
+        sleep_ns = s.bo.next(sleep_ns);
+      }
+    }
+  }
+}
+
+template <int KIND>
+__device__ __forceinline__ int sem_post_thread(const SemRef& s) {
+  if (KIND == GSYNC_SEM_TICKET) {
+    const uint32_t old = ptx::atom_add_release(s.word(1), 0xFFFFFFFFu);
+    if ((int32_t)old > (int32_t)s.n) ptx::red_add_release(s.word(3), 1u);
+    return GSYNC_OK;
+  } else {
+    Waiter w;
+    for (;;) {
+      const uint32_t v = ptx::atom_exch_acquire(s.word(1), 0u);
+      if (v > 0u) {
+        ptx::atom_exch_release(s.word(1), v + 1u);
+        return GSYNC_OK;
+      }
+      if (int rc = w.tick(s.timeout_ns, s.abort_word())) return rc;
+    }
+  }
+}
+
+template <int KIND>
+__device__ __forceinline__ int sem_wait(const SemRef& s) {
+  __shared__ int s_rc;
+  if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) s_rc = sem_wait_thread<KIND>(s);
+  __syncthreads();
+  const int rc = s_rc;
+  return rc;
+}
+
+template <int KIND>
+__device__ __forceinline__ int sem_post(const SemRef& s) {
+  __shared__ int s_rc;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) s_rc = sem_post_thread<KIND>(s);
+  __syncthreads();
+  const int rc = s_rc;
+  return rc;
+}
+
+// ---------------------------------------------------------------------------------------
+// Grid barrier (Section 5 "Barrier"): every block of the grid participates.
+// ---------------------------------------------------------------------------------------
+// ATOMIC : line 1 arrival counter, line 2 release epoch.
+// FLAG   : lines 1.. arrival flags (one word per block, packed), then release flags (one
+//          word per block, packed; mode 1: a single release word on its own line).
+// TREE   : line 1 release epoch, lines 2.. one counter line per tree node (fan-in = param).
+// CLUSTER: like ATOMIC over the cluster leaders; param = cluster size.
+// Epochs increase by one per crossing and are compared for equality, so no phase resets.
+struct BarrierRef {
+  uint32_t* s;
+  uint32_t kind, n, param, mode;
+  uint32_t epoch;  // epoch of the last crossing, kept by each block
+  uint64_t timeout_ns;
+  __device__ __forceinline__ uint32_t* line(uint32_t i) const { return s + i * kLineWords; }
+  __device__ __forceinline__ uint32_t* abort_word() const { return s + kHdrAbort; }
+  __device__ __forceinline__ uint32_t flag_lines() const { return (n + kLineWords - 1) / kLineWords; }
+  __device__ __forceinline__ uint32_t* arrive_flags() const { return line(1); }
+  __device__ __forceinline__ uint32_t* release_flags() const { return line(1 + flag_lines()); }
+};
+
+// Reads the header and the current epoch.  All blocks must attach between the same two
+// crossings (normally at kernel start).
+__device__ __forceinline__ BarrierRef barrier_attach(void* state) {
+  BarrierRef b;
+  b.s = (uint32_t*)state;
+  b.kind = b.s[kHdrMagic] & 0xFFu;
+  b.n = b.s[kHdrN];
+  b.param = b.s[kHdrParam];
+  b.mode = b.s[kHdrMode];
+  b.timeout_ns = header_timeout(b.s);
+  if (b.kind == GSYNC_BAR_FLAG) {
+    // A block's own release flag always holds the epoch of the last crossing.
+    b.epoch = b.mode ? ptx::ld_relaxed(b.release_flags()) : ptx::ld_relaxed(b.release_flags() + blockIdx.x);
+  } else if (b.kind == GSYNC_BAR_TREE) {
+    b.epoch = ptx::ld_relaxed(b.line(1));
+  } else {
+    b.epoch = ptx::ld_relaxed(b.line(2));
+  }
+  return b;
+}
+
+// Master-thread arrival on a two-stage atomic counter of `parties` participants.
+__device__ __forceinline__ int counter_arrive_wait(const BarrierRef& b, uint32_t parties, uint32_t e1) {
+  const uint32_t old = ptx::atom_add_acq_rel(b.line(1), 1u);
+  if (old == parties - 1u) {
+    ptx::st_relaxed(b.line(1), 0u);
+    ptx::st_release(b.line(2), e1);
+    return GSYNC_OK;
+  }
+  Waiter w;
+  while (ptx::ld_acquire(b.line(2)) != e1)
+    if (int rc = w.tick(b.timeout_ns, b.abort_word())) return rc;
+  return GSYNC_OK;
+}
+
+template <int KIND>
+__device__ __forceinline__ int barrier_wait(BarrierRef& b) {
+  __shared__ int s_rc;
+  const bool master = threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0;
+  const uint32_t e1 = b.epoch + 1u;
+  if (KIND == GSYNC_BAR_CLUSTER) {
+    ptx::cluster_sync();  // every block of the cluster has arrived (release/acquire, cluster)
+  } else {
+    __syncthreads();
+  }
+  if (KIND == GSYNC_BAR_ATOMIC) {
+    if (master) s_rc = counter_arrive_wait(b, b.n, e1);
+  } else if (KIND == GSYNC_BAR_CLUSTER) {
+    if (master) {
+      int rc = GSYNC_OK;
+      if (ptx::cluster_ctarank() == 0) {
+        rc = counter_arrive_wait(b, b.n / b.param, e1);
+      } else {
+        Waiter w;
+        while (ptx::ld_acquire(b.line(2)) != e1)
+          if ((rc = w.tick(b.timeout_ns, b.abort_word())) != GSYNC_OK) break;
+      }
+      s_rc = rc;
+    }
+  } else if (KIND == GSYNC_BAR_TREE) {
+    if (master) {
+      // Combining tree: count in at the leaf; the last arriver at a node resets it and
+      // counts in at the parent; the last arriver at the root advances the epoch.
+      const uint32_t fan = b.param;
+      uint32_t width = b.n, node = blockIdx.x / fan, off = 0;
+      int rc = GSYNC_OK;
+      for (;;) {
+        const uint32_t nodes = (width + fan - 1) / fan;
+        const uint32_t size = min(fan, width - node * fan);
+        uint32_t* c = b.line(2 + off + node);
+        const uint32_t old = ptx::atom_add_acq_rel(c, 1u);
+        if (old + 1u < size) {
+          Waiter w;
+          while (ptx::ld_acquire(b.line(1)) != e1)
+            if ((rc = w.tick(b.timeout_ns, b.abort_word())) != GSYNC_OK) break;
+          break;
+        }
+        ptx::st_relaxed(c, 0u);
+        if (nodes == 1u) {
+          ptx::st_release(b.line(1), e1);
+          break;
+        }
+        off += nodes;
+        width = nodes;
+        node /= fan;
+      }
+      s_rc = rc;
+    }
+  } else {  // GSYNC_BAR_FLAG: decentralized XF barrier, block 0 is the master block
+    const uint32_t tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const uint32_t nthr = blockDim.x * blockDim.y * blockDim.z;
+    if (blockIdx.x == 0) {
+      __shared__ int s_bad;
+      if (master) s_bad = GSYNC_OK;
+      __syncthreads();
+      Waiter w;
+      int rc = GSYNC_OK;
+      for (uint32_t j = 1 + tid; j < b.n && rc == GSYNC_OK; j += nthr)
+        while (ptx::ld_acquire(b.arrive_flags() + j) != e1)
+          if ((rc = w.tick(b.timeout_ns, b.abort_word())) != GSYNC_OK) break;
+      if (rc != GSYNC_OK) s_bad = rc;
+      __syncthreads();
+      if (s_bad == GSYNC_OK) {
+        ptx::fence_acq_rel();
+        if (b.mode) {
+          if (master) ptx::st_relaxed(b.release_flags(), e1);
+        } else {
+          for (uint32_t j = tid; j < b.n; j += nthr) ptx::st_relaxed(b.release_flags() + j, e1);
+        }
+      }
+      if (master) s_rc = s_bad;
+    } else if (master) {
+      ptx::st_release(b.arrive_flags() + blockIdx.x, e1);
+      uint32_t* rel = b.mode ? b.release_flags() : b.release_flags() + blockIdx.x;
+      Waiter w;
+      int rc = GSYNC_OK;
+      while (ptx::ld_acquire(rel) != e1)
+        if ((rc = w.tick(b.timeout_ns, b.abort_word())) != GSYNC_OK) break;
+      s_rc = rc;
+    }
+  }
+  __syncthreads();
+  const int rc = s_rc;
+  b.epoch = e1;
+  return rc;
+}
+
+}  // namespace gsync

@@ -7,6 +7,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 
 import numpy as np
@@ -25,11 +26,17 @@ _lib = None
 
 def build(force: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
+    stamp = os.path.join(OUT_DIR, "HOST_ARCH")
+    arch = platform.machine()
+    if not os.path.exists(stamp) or open(stamp).read().strip() != arch:
+        force = True
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
                                "-Wall", "-o", tmp, SRC])
         os.replace(tmp, LIB)
+        with open(stamp, "w") as f:
+            f.write(arch + "\n")
     return LIB
 
 

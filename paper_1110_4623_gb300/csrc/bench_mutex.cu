@@ -1,0 +1,214 @@
+// Mutex workload (Section 6, "Results": each block runs a loop of lock/unlock pairs).
+//
+// Block b makes `acq` acquisitions (id = b * acq + a).  Before each lock its master thread
+// waits delay[id] SM cycles; inside the critical section thread 0 appends id to the grant
+// log at position `total` and increments `total` with a plain load and store, and the
+// block's threads add addend[id] ^ (i * 0x9E3779B1) to data[i] for i < cs_words with plain
+// loads and stores.  Broken exclusion loses updates to total/data or corrupts the log; the
+// fair kinds also record their ticket so the host can check grants follow ticket order.
+#include "common.cuh"
+
+using namespace gsync_impl;
+
+namespace {
+
+constexpr int kMaxThreads = 256;
+constexpr int kNoLock = -1;  // no mutex at all: the critical-section probe (T_cs)
+constexpr uint32_t kGolden = 0x9E3779B1u;
+
+template <int KIND>
+__global__ void __launch_bounds__(kMaxThreads, 8)
+    mutex_workload_kernel(uint32_t* state, int acq, int cs_words, const uint32_t* __restrict__ delay,
+                          const uint32_t* __restrict__ addend, uint32_t* data, uint32_t* total, uint32_t* grant_log,
+                          uint32_t* ticket_out, uint32_t* count, uint32_t* status) {
+  const uint32_t b = blockIdx.x, tid = threadIdx.x;
+  const uint32_t n = gridDim.x * (uint32_t)acq;
+  gsync::MutexRef m;
+  if (KIND != kNoLock) {
+    m = gsync::mutex_attach(state);
+    const bool bad_queue = KIND == GSYNC_MUTEX_SLEEP_QUEUE && gridDim.x > m.qmask + 1u;
+    if (m.kind != (uint32_t)KIND || bad_queue) {
+      if (tid == 0) gsync::ptx::atom_or_relaxed(status, GSYNC_STATUS_CONFIG);
+      return;
+    }
+  }
+  uint32_t done = 0;
+  for (int a = 0; a < acq; ++a) {
+    const uint32_t id = b * (uint32_t)acq + (uint32_t)a;
+    const uint32_t v = addend[id];
+    if (tid == 0 && delay) spin_cycles(delay[id]);
+    gsync::Token t{GSYNC_OK, 0xFFFFFFFFu};
+    if (KIND != kNoLock) {
+      t = gsync::mutex_lock<KIND>(m);
+      if (t.status != GSYNC_OK) {
+        if (tid == 0) record_status(status, t.status);
+        break;
+      }
+    }
+    // ---- critical section ----
+    if (tid == 0) {
+      const uint32_t seq = *total;
+      *total = seq + 1u;
+      if (seq < n) {
+        grant_log[seq] = id;
+      } else {
+        gsync::ptx::atom_or_relaxed(status, GSYNC_STATUS_VIOLATION);
+      }
+      ticket_out[id] = t.ticket;
+    }
+    for (uint32_t i = tid; i < (uint32_t)cs_words; i += blockDim.x) data[i] += v ^ (i * kGolden);
+    // ---- end of critical section ----
+    if (KIND != kNoLock) {
+      gsync::mutex_unlock<KIND>(m, t);
+    } else {
+      __syncthreads();
+      if (tid == 0) gsync::ptx::st_release(status + 32, id);  // the release store of an unlock
+    }
+    ++done;
+  }
+  if (tid == 0) count[b] = done;
+}
+
+using KernelFn = void (*)(uint32_t*, int, int, const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*,
+                          uint32_t*, uint32_t*, uint32_t*);
+
+KernelFn pick(int kind) {
+  switch (kind) {
+    case GSYNC_MUTEX_CAS_SPIN: return mutex_workload_kernel<GSYNC_MUTEX_CAS_SPIN>;
+    case GSYNC_MUTEX_CAS_BACKOFF: return mutex_workload_kernel<GSYNC_MUTEX_CAS_BACKOFF>;
+    case GSYNC_MUTEX_TICKET: return mutex_workload_kernel<GSYNC_MUTEX_TICKET>;
+    case GSYNC_MUTEX_SLEEP_QUEUE: return mutex_workload_kernel<GSYNC_MUTEX_SLEEP_QUEUE>;
+  }
+  return nullptr;
+}
+
+int check_work(const gsync_mutex_work* w) {
+  if (!w || w->nblocks < 1 || w->acq < 0 || w->cs_words < 0 || w->block_threads < 32 ||
+      w->block_threads > kMaxThreads || w->block_threads % 32)
+    return GSYNC_EINVAL;
+  if ((uint64_t)w->nblocks * (uint64_t)w->acq >= (1ull << 31)) return GSYNC_EINVAL;
+  return GSYNC_OK;
+}
+
+size_t round_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+namespace gsync_impl {
+int max_blocks_mutex(int kind, int block_threads, int* out) {
+  KernelFn k = pick(kind);
+  if (!k) return GSYNC_EINVAL;
+  return max_coresident(k, block_threads, 1, 0, out);
+}
+}  // namespace gsync_impl
+
+extern "C" int gsync_bench_mutex(void* state, const gsync_mutex_work* w, void* stream) {
+  if (int rc = check_work(w)) return rc;
+  if (!state || !aligned(state, 128)) return GSYNC_EINVAL;
+  if (!w->addend || !w->total || !w->grant_log || !w->ticket || !w->count || !w->status ||
+      (w->cs_words > 0 && !w->data))
+    return GSYNC_EINVAL;
+  KernelFn k = pick(w->kind);
+  if (!k) return GSYNC_EINVAL;
+  return launch_coresident(k, w->nblocks, w->block_threads, 1, 0, (cudaStream_t)stream, (uint32_t*)state, w->acq,
+                           w->cs_words, w->delay, w->addend, w->data, w->total, w->grant_log, w->ticket, w->count,
+                           w->status);
+}
+
+extern "C" size_t gsync_bench_mutex_workspace_bytes(int kind, int nblocks, int acq, int cs_words) {
+  const size_t sb = gsync_mutex_bytes(kind, nblocks);
+  if (sb == 0 || nblocks < 1 || acq < 0 || cs_words < 0) return 0;
+  const size_t n = (size_t)nblocks * (size_t)acq;
+  return round_up(sb) + 4 * round_up(4 * n) + round_up(4 * (size_t)cs_words) + round_up(4 * (size_t)nblocks) +
+         2 * round_up(4);
+}
+
+extern "C" int gsync_bench_mutex_host(const gsync_mutex_work* w, const gsync_backoff* backoff, void* workspace,
+                                      size_t workspace_bytes, void* stream) {
+  if (int rc = check_work(w)) return rc;
+  const size_t need = gsync_bench_mutex_workspace_bytes(w->kind, w->nblocks, w->acq, w->cs_words);
+  if (need == 0 || !workspace || workspace_bytes < need || !aligned(workspace, 256)) return GSYNC_EINVAL;
+  if (!w->addend || !w->total || !w->grant_log || !w->ticket || !w->count || !w->status ||
+      (w->cs_words > 0 && !w->data))
+    return GSYNC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n = (size_t)w->nblocks * (size_t)w->acq;
+  char* p = (char*)workspace;
+  const size_t sb = gsync_mutex_bytes(w->kind, w->nblocks);
+  void* state = p;                 p += round_up(sb);
+  uint32_t* d_delay = (uint32_t*)p;  p += round_up(4 * n);
+  uint32_t* d_add = (uint32_t*)p;    p += round_up(4 * n);
+  uint32_t* d_log = (uint32_t*)p;    p += round_up(4 * n);
+  uint32_t* d_tick = (uint32_t*)p;   p += round_up(4 * n);
+  uint32_t* d_data = (uint32_t*)p;   p += round_up(4 * (size_t)w->cs_words);
+  uint32_t* d_count = (uint32_t*)p;  p += round_up(4 * (size_t)w->nblocks);
+  uint32_t* d_total = (uint32_t*)p;  p += round_up(4);
+  uint32_t* d_status = (uint32_t*)p; p += round_up(4);
+
+  if (w->delay) GSYNC_CUDA(cudaMemcpyAsync(d_delay, w->delay, 4 * n, cudaMemcpyHostToDevice, st));
+  GSYNC_CUDA(cudaMemcpyAsync(d_add, w->addend, 4 * n, cudaMemcpyHostToDevice, st));
+  if (w->cs_words) GSYNC_CUDA(cudaMemsetAsync(d_data, 0, 4 * (size_t)w->cs_words, st));
+  GSYNC_CUDA(cudaMemsetAsync(d_total, 0, 4, st));
+  GSYNC_CUDA(cudaMemsetAsync(d_status, 0, 4, st));
+  if (int rc = gsync_mutex_init(state, sb, w->kind, w->nblocks, backoff, 0, stream)) return rc;
+  gsync_mutex_work dw = *w;
+  dw.delay = w->delay ? d_delay : nullptr;
+  dw.addend = d_add;
+  dw.data = d_data;
+  dw.total = d_total;
+  dw.grant_log = d_log;
+  dw.ticket = d_tick;
+  dw.count = d_count;
+  dw.status = d_status;
+  if (int rc = gsync_bench_mutex(state, &dw, stream)) return rc;
+  if (w->cs_words) GSYNC_CUDA(cudaMemcpyAsync(w->data, d_data, 4 * (size_t)w->cs_words, cudaMemcpyDeviceToHost, st));
+  GSYNC_CUDA(cudaMemcpyAsync(w->total, d_total, 4, cudaMemcpyDeviceToHost, st));
+  GSYNC_CUDA(cudaMemcpyAsync(w->grant_log, d_log, 4 * n, cudaMemcpyDeviceToHost, st));
+  GSYNC_CUDA(cudaMemcpyAsync(w->ticket, d_tick, 4 * n, cudaMemcpyDeviceToHost, st));
+  GSYNC_CUDA(cudaMemcpyAsync(w->count, d_count, 4 * (size_t)w->nblocks, cudaMemcpyDeviceToHost, st));
+  GSYNC_CUDA(cudaMemcpyAsync(w->status, d_status, 4, cudaMemcpyDeviceToHost, st));
+  GSYNC_CUDA(cudaStreamSynchronize(st));
+  return GSYNC_OK;
+}
+
+// T_cs probe: one block runs the critical-section body, including the release store that
+// ends it, `iters` times with no lock and no delays.  scratch: [0, 128) status and the
+// release word (status + 32), then total, data, count, grant log.
+extern "C" int gsync_probe_cs(int cs_words, int block_threads, int iters, void* scratch, uint64_t* out,
+                              void* stream) {
+  if (!scratch || !out || cs_words < 0 || iters < 1 || block_threads < 32 || block_threads > kMaxThreads ||
+      block_threads % 32 || !aligned(scratch, 256))
+    return GSYNC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* p = (char*)scratch;
+  uint32_t* status = (uint32_t*)p;   p += 256;
+  uint32_t* total = (uint32_t*)p;    p += 256;
+  uint32_t* count = (uint32_t*)p;    p += 256;
+  uint32_t* data = (uint32_t*)p;     p += round_up(4 * (size_t)cs_words);
+  uint32_t* log = (uint32_t*)p;      p += round_up(4 * (size_t)iters);
+  uint32_t* tick = (uint32_t*)p;     p += round_up(4 * (size_t)iters);
+  uint32_t* add = (uint32_t*)p;      p += round_up(4 * (size_t)iters);
+  const size_t bytes = (size_t)(p - (char*)scratch);
+  GSYNC_CUDA(cudaMemsetAsync(scratch, 0, bytes, st));
+  cudaEvent_t e0, e1;
+  GSYNC_CUDA(cudaEventCreate(&e0));
+  GSYNC_CUDA(cudaEventCreate(&e1));
+  GSYNC_CUDA(cudaEventRecord(e0, st));
+  mutex_workload_kernel<kNoLock><<<1, block_threads, 0, st>>>(nullptr, iters, cs_words, nullptr, add, data, total, log,
+                                                             tick, count, status);
+  GSYNC_CUDA(cudaGetLastError());
+  GSYNC_CUDA(cudaEventRecord(e1, st));
+  GSYNC_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  GSYNC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  out[0] = (uint64_t)(ms * 1e6);
+  return GSYNC_OK;
+}
+
+// Size of the scratch buffer gsync_probe_cs needs.
+extern "C" size_t gsync_probe_cs_scratch_bytes(int cs_words, int iters) {
+  if (cs_words < 0 || iters < 1) return 0;
+  return 3 * 256 + round_up(4 * (size_t)cs_words) + 3 * round_up(4 * (size_t)iters);
+}

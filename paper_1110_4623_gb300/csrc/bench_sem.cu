@@ -1,0 +1,91 @@
+// Counting-semaphore workload (Section 6, "Results": each block runs a loop of wait/post
+// pairs; Section 5: at most n blocks inside the critical section at once).
+//
+// Block b makes `pairs` wait/post pairs (id = b * pairs + p).  Inside, thread 0 counts itself
+// into `occupancy` with an atomic add and raises `max_occupancy` (the capacity invariant,
+// checked on the host), increments `total` with a plain load/store when n == 1 (exclusion
+// makes it exact), holds for hold[id] SM cycles, adds addend[id] to `tally` atomically and
+// counts itself out of `occupancy` before posting.
+#include "common.cuh"
+
+using namespace gsync_impl;
+
+namespace {
+
+constexpr int kMaxThreads = 256;
+
+template <int KIND>
+__global__ void __launch_bounds__(kMaxThreads, 8)
+    sem_workload_kernel(uint32_t* state, int pairs, const uint32_t* __restrict__ hold,
+                        const uint32_t* __restrict__ addend, uint32_t* occupancy, uint32_t* max_occupancy,
+                        uint32_t* total, uint32_t* tally, uint32_t* count, uint32_t* status) {
+  const gsync::SemRef s = gsync::sem_attach(state);
+  const uint32_t b = blockIdx.x, tid = threadIdx.x;
+  if (s.kind != (uint32_t)KIND) {
+    if (tid == 0) gsync::ptx::atom_or_relaxed(status, GSYNC_STATUS_CONFIG);
+    return;
+  }
+  uint32_t done = 0;
+  for (int p = 0; p < pairs; ++p) {
+    const uint32_t id = b * (uint32_t)pairs + (uint32_t)p;
+    const int rc = gsync::sem_wait<KIND>(s);
+    if (rc != GSYNC_OK) {
+      if (tid == 0) record_status(status, rc);
+      break;
+    }
+    if (tid == 0) {
+      const uint32_t o = gsync::ptx::atom_add_relaxed(occupancy, 1u) + 1u;
+      gsync::ptx::atom_max_relaxed(max_occupancy, o);
+      if (s.n == 1u) {
+        const uint32_t t = *total;
+        *total = t + 1u;
+      }
+      if (hold) spin_cycles(hold[id]);
+      gsync::ptx::red_add_relaxed(tally, addend[id]);
+      gsync::ptx::atom_add_relaxed(occupancy, 0xFFFFFFFFu);
+    }
+    const int rc2 = gsync::sem_post<KIND>(s);
+    if (rc2 != GSYNC_OK) {
+      if (tid == 0) record_status(status, rc2);
+      break;
+    }
+    ++done;
+  }
+  if (tid == 0) count[b] = done;
+}
+
+using KernelFn = void (*)(uint32_t*, int, const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*,
+                          uint32_t*, uint32_t*, uint32_t*);
+
+KernelFn pick(int kind) {
+  switch (kind) {
+    case GSYNC_SEM_TICKET: return sem_workload_kernel<GSYNC_SEM_TICKET>;
+    case GSYNC_SEM_SPIN: return sem_workload_kernel<GSYNC_SEM_SPIN>;
+    case GSYNC_SEM_SPIN_BACKOFF: return sem_workload_kernel<GSYNC_SEM_SPIN_BACKOFF>;
+  }
+  return nullptr;
+}
+
+}  // namespace
+
+namespace gsync_impl {
+int max_blocks_sem(int kind, int block_threads, int* out) {
+  KernelFn k = pick(kind);
+  if (!k) return GSYNC_EINVAL;
+  return max_coresident(k, block_threads, 1, 0, out);
+}
+}  // namespace gsync_impl
+
+extern "C" int gsync_bench_sem(void* state, const gsync_sem_work* w, void* stream) {
+  if (!state || !w || !aligned(state, 128)) return GSYNC_EINVAL;
+  if (w->nblocks < 1 || w->pairs < 0 || w->block_threads < 32 || w->block_threads > kMaxThreads ||
+      w->block_threads % 32 || w->initial_count < 1)
+    return GSYNC_EINVAL;
+  if (!w->addend || !w->occupancy || !w->max_occupancy || !w->total || !w->tally || !w->count || !w->status)
+    return GSYNC_EINVAL;
+  KernelFn k = pick(w->kind);
+  if (!k) return GSYNC_EINVAL;
+  return launch_coresident(k, w->nblocks, w->block_threads, 1, 0, (cudaStream_t)stream, (uint32_t*)state, w->pairs,
+                           w->hold, w->addend, w->occupancy, w->max_occupancy, w->total, w->tally, w->count,
+                           w->status);
+}

@@ -1,0 +1,192 @@
+// Object sizing and initialisation, co-residency queries and error reporting of the C ABI.
+// Algorithm 1 ("CreateSpinLock") allocates one word on the GPU and zeroes it from the CPU;
+// here the caller owns the memory and gsync_*_init writes each object's initial state with
+// one small kernel on the caller's stream.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include "common.cuh"
+
+namespace gsync_impl {
+thread_local int g_last_cuda_error = 0;
+}
+using namespace gsync_impl;
+
+namespace {
+
+constexpr uint32_t kLine = 128;
+constexpr uint32_t kMagic = 0x6B5C0000u;
+enum : uint32_t { kPrimMutex = 1, kPrimBarrier = 2, kPrimSem = 3 };
+
+struct InitSpec {
+  uint32_t header[16];
+  uint32_t nwords;
+  uint32_t queue_slots;  // SLEEP_QUEUE: flag lines start at line 3
+  uint32_t spin_sem_s;   // spin semaphores: initial S (line 1), else 0
+};
+
+__global__ void init_state_kernel(uint32_t* s, InitSpec spec) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < spec.nwords; i += gridDim.x * blockDim.x) {
+    uint32_t v = 0;
+    if (i < 16) v = spec.header[i];
+    const uint32_t line = i / 32, word = i % 32;
+    if (spec.queue_slots && word == 0 && line >= 3 && line < 3 + spec.queue_slots) {
+      // Slot k first serves ticket k; before that it holds k - Q, the ticket of the previous
+      // lap, which no waiter can be waiting for.  Slot 0 holds ticket 0: the lock is free.
+      const uint32_t k = line - 3;
+      v = k == 0 ? 0u : k - spec.queue_slots;
+    }
+    if (spec.spin_sem_s && line == 1 && word == 0) v = spec.spin_sem_s;
+    s[i] = v;
+  }
+}
+
+int launch_init(void* state, size_t bytes, const InitSpec& spec, cudaStream_t st) {
+  if (!state || !aligned(state, kLine)) return GSYNC_EINVAL;
+  if ((size_t)spec.nwords * 4 > bytes) return GSYNC_EINVAL;
+  const uint32_t threads = 256;
+  uint32_t blocks = (spec.nwords + threads - 1) / threads;
+  if (blocks > 1024) blocks = 1024;
+  init_state_kernel<<<blocks, threads, 0, st>>>((uint32_t*)state, spec);
+  GSYNC_CUDA(cudaGetLastError());
+  return GSYNC_OK;
+}
+
+void fill_header(InitSpec& spec, uint32_t prim, uint32_t kind, uint32_t n, uint32_t param,
+                 const gsync_backoff* bo, uint64_t timeout_ns, uint32_t mode) {
+  memset(&spec, 0, sizeof spec);
+  spec.header[gsync::kHdrMagic] = kMagic | (prim << 8) | kind;
+  spec.header[gsync::kHdrN] = n;
+  spec.header[gsync::kHdrParam] = param;
+  if (bo) {
+    spec.header[gsync::kHdrPolicy] = bo->policy;
+    spec.header[gsync::kHdrMinNs] = bo->min_ns;
+    spec.header[gsync::kHdrMaxNs] = bo->max_ns;
+  }
+  spec.header[gsync::kHdrTimeoutLo] = (uint32_t)timeout_ns;
+  spec.header[gsync::kHdrTimeoutHi] = (uint32_t)(timeout_ns >> 32);
+  spec.header[gsync::kHdrMode] = mode;
+}
+
+uint32_t pow2_at_least(uint32_t n) {
+  uint32_t q = 1;
+  while (q < n) q <<= 1;
+  return q;
+}
+
+uint32_t tree_nodes(uint32_t n, uint32_t fan) {
+  uint32_t total = 0, width = n;
+  for (;;) {
+    const uint32_t nodes = (width + fan - 1) / fan;
+    total += nodes;
+    if (nodes == 1) break;
+    width = nodes;
+  }
+  return total;
+}
+
+uint32_t barrier_lines(int kind, uint32_t n, uint32_t param) {
+  switch (kind) {
+    case GSYNC_BAR_ATOMIC:
+    case GSYNC_BAR_CLUSTER:
+      return 3;
+    case GSYNC_BAR_FLAG: {
+      const uint32_t fl = (n + 31) / 32;
+      return 1 + fl + (param ? 1 : fl);
+    }
+    case GSYNC_BAR_TREE:
+      return 2 + tree_nodes(n, param);
+  }
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gsync_last_cuda_error(void) { return g_last_cuda_error; }
+
+size_t gsync_mutex_bytes(int kind, int max_waiters) {
+  if (kind < GSYNC_MUTEX_CAS_SPIN || kind > GSYNC_MUTEX_SLEEP_QUEUE || max_waiters < 1) return 0;
+  if (max_waiters > (1 << 24)) return 0;
+  const uint32_t q = kind == GSYNC_MUTEX_SLEEP_QUEUE ? pow2_at_least((uint32_t)max_waiters) : 0;
+  return (size_t)(3 + q) * kLine;
+}
+
+int gsync_mutex_init(void* state, size_t bytes, int kind, int max_waiters, const gsync_backoff* backoff,
+                     uint64_t timeout_ns, void* stream) {
+  const size_t need = gsync_mutex_bytes(kind, max_waiters);
+  if (need == 0 || bytes < need) return GSYNC_EINVAL;
+  if (backoff && backoff->policy > GSYNC_BACKOFF_LINEAR_CYCLIC) return GSYNC_EINVAL;
+  const uint32_t q = kind == GSYNC_MUTEX_SLEEP_QUEUE ? pow2_at_least((uint32_t)max_waiters) : 0;
+  InitSpec spec;
+  fill_header(spec, kPrimMutex, (uint32_t)kind, (uint32_t)max_waiters, q, backoff, timeout_ns, 0);
+  spec.nwords = (uint32_t)(need / 4);
+  spec.queue_slots = q;
+  return launch_init(state, bytes, spec, (cudaStream_t)stream);
+}
+
+size_t gsync_barrier_bytes(int kind, int nblocks, int param) {
+  if (nblocks < 1 || nblocks > (1 << 20)) return 0;
+  switch (kind) {
+    case GSYNC_BAR_ATOMIC: break;
+    case GSYNC_BAR_FLAG: if (param != 0 && param != 1) return 0; break;
+    case GSYNC_BAR_TREE: if (param < 2 || param > 1024) return 0; break;
+    case GSYNC_BAR_CLUSTER: if (param < 1 || param > 8 || nblocks % param) return 0; break;
+    default: return 0;
+  }
+  return (size_t)barrier_lines(kind, (uint32_t)nblocks, (uint32_t)param) * kLine;
+}
+
+int gsync_barrier_init(void* state, size_t bytes, int kind, int nblocks, int param, uint64_t timeout_ns,
+                       void* stream) {
+  const size_t need = gsync_barrier_bytes(kind, nblocks, param);
+  if (need == 0 || bytes < need) return GSYNC_EINVAL;
+  InitSpec spec;
+  const uint32_t mode = kind == GSYNC_BAR_FLAG ? (uint32_t)param : 0u;
+  fill_header(spec, kPrimBarrier, (uint32_t)kind, (uint32_t)nblocks, (uint32_t)param, nullptr, timeout_ns, mode);
+  spec.nwords = (uint32_t)(need / 4);
+  return launch_init(state, bytes, spec, (cudaStream_t)stream);
+}
+
+size_t gsync_sem_bytes(int kind) {
+  if (kind < GSYNC_SEM_TICKET || kind > GSYNC_SEM_SPIN_BACKOFF) return 0;
+  return 4 * kLine;
+}
+
+int gsync_sem_init(void* state, size_t bytes, int kind, int initial_count, const gsync_backoff* backoff,
+                   uint64_t timeout_ns, void* stream) {
+  const size_t need = gsync_sem_bytes(kind);
+  if (need == 0 || bytes < need || initial_count < 1 || initial_count > (1 << 30)) return GSYNC_EINVAL;
+  if (backoff && backoff->policy > GSYNC_BACKOFF_LINEAR_CYCLIC) return GSYNC_EINVAL;
+  InitSpec spec;
+  fill_header(spec, kPrimSem, (uint32_t)kind, (uint32_t)initial_count, 0, backoff, timeout_ns, 0);
+  spec.nwords = (uint32_t)(need / 4);
+  spec.spin_sem_s = kind == GSYNC_SEM_TICKET ? 0u : (uint32_t)initial_count + 1u;
+  return launch_init(state, bytes, spec, (cudaStream_t)stream);
+}
+
+int gsync_object_abort_flag(const void* state, uint32_t* flag_out, void* stream) {
+  if (!state || !flag_out || !aligned(state, kLine)) return GSYNC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  GSYNC_CUDA(cudaMemcpyAsync(flag_out, (const uint32_t*)state + gsync::kHdrAbort, 4, cudaMemcpyDeviceToHost, st));
+  GSYNC_CUDA(cudaStreamSynchronize(st));
+  return GSYNC_OK;
+}
+
+int gsync_device_sm_count(int* sms_out) {
+  if (!sms_out) return GSYNC_EINVAL;
+  return device_sms(sms_out);
+}
+
+int gsync_max_coresident_blocks(int workload, int kind, int block_threads, int cluster, int* max_blocks_out) {
+  if (!max_blocks_out || block_threads < 32 || block_threads > 256 || block_threads % 32) return GSYNC_EINVAL;
+  switch (workload) {
+    case 0: return max_blocks_barrier(kind, block_threads, cluster, max_blocks_out);
+    case 1: return max_blocks_mutex(kind, block_threads, max_blocks_out);
+    case 2: return max_blocks_sem(kind, block_threads, max_blocks_out);
+  }
+  return GSYNC_EINVAL;
+}
+
+}  // extern "C"

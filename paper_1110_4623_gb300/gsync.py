@@ -1,0 +1,238 @@
+"""Python binding of the gsync C ABI (include/gsync.h): the same entry-point names, argument
+marshalling only.  Every operation runs in the CUDA library; if libgsync.so is missing or
+fails to load, every call raises -- there is no fallback.
+
+Pointer arguments accept a torch tensor (its data_ptr), a ctypes object, an int address or
+None; `stream` accepts a torch.cuda.Stream, an int handle or None (the current torch stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgsync.so")
+
+# Enums of gsync.h
+GSYNC_OK, GSYNC_EINVAL, GSYNC_ENOTRESIDENT, GSYNC_ETIMEDOUT, GSYNC_ECUDA, GSYNC_EABORTED = range(6)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOTRESIDENT", 3: "ETIMEDOUT", 4: "ECUDA", 5: "EABORTED"}
+GSYNC_STATUS_TIMEOUT, GSYNC_STATUS_ABORTED, GSYNC_STATUS_VIOLATION, GSYNC_STATUS_CONFIG = 1, 2, 4, 8
+
+MUTEX_KINDS = {"cas_spin": 0, "cas_backoff": 1, "ticket": 2, "sleep_queue": 3}
+BARRIER_KINDS = {"atomic": 0, "flag": 1, "tree": 2, "cluster": 3}
+SEM_KINDS = {"ticket": 0, "spin": 1, "spin_backoff": 2}
+BACKOFF_EXPONENTIAL, BACKOFF_LINEAR_CYCLIC = 0, 1
+PROBE_OPS = {"volatile_load": 0, "volatile_store": 1, "atomic_read": 2, "atomic_write": 3,
+             "load_acquire": 4, "load_relaxed": 5, "store_release": 6, "red_add": 7,
+             "atomic_add64": 8, "atomic_acqrel": 9}
+
+u32p = ctypes.c_void_p
+
+
+class gsync_backoff(ctypes.Structure):
+    _fields_ = [("policy", ctypes.c_uint32), ("min_ns", ctypes.c_uint32),
+                ("max_ns", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class gsync_barrier_work(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("nblocks", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("rounds", ctypes.c_int32), ("full", ctypes.c_int32), ("cluster", ctypes.c_int32),
+                ("slots", u32p), ("chk", u32p), ("mix", u32p), ("bad", u32p), ("status", u32p)]
+
+
+class gsync_mutex_work(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("nblocks", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("acq", ctypes.c_int32), ("cs_words", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("delay", u32p), ("addend", u32p), ("data", u32p), ("total", u32p), ("grant_log", u32p),
+                ("ticket", u32p), ("count", u32p), ("status", u32p)]
+
+
+class gsync_sem_work(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("nblocks", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("pairs", ctypes.c_int32), ("initial_count", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("hold", u32p), ("addend", u32p), ("occupancy", u32p), ("max_occupancy", u32p),
+                ("total", u32p), ("tally", u32p), ("count", u32p), ("status", u32p)]
+
+
+# name -> (restype, argtypes)
+_SIG = {
+    "gsync_mutex_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
+    "gsync_mutex_init": (ctypes.c_int, [u32p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(gsync_backoff), ctypes.c_uint64, u32p]),
+    "gsync_barrier_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "gsync_barrier_init": (ctypes.c_int, [u32p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_uint64, u32p]),
+    "gsync_sem_bytes": (ctypes.c_size_t, [ctypes.c_int]),
+    "gsync_sem_init": (ctypes.c_int, [u32p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(gsync_backoff), ctypes.c_uint64, u32p]),
+    "gsync_object_abort_flag": (ctypes.c_int, [u32p, ctypes.POINTER(ctypes.c_uint32), u32p]),
+    "gsync_max_coresident_blocks": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.POINTER(ctypes.c_int)]),
+    "gsync_device_sm_count": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
+    "gsync_last_cuda_error": (ctypes.c_int, []),
+    "gsync_bench_barrier": (ctypes.c_int, [u32p, ctypes.POINTER(gsync_barrier_work), u32p]),
+    "gsync_bench_mutex": (ctypes.c_int, [u32p, ctypes.POINTER(gsync_mutex_work), u32p]),
+    "gsync_bench_mutex_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "gsync_bench_mutex_host": (ctypes.c_int, [ctypes.POINTER(gsync_mutex_work), ctypes.POINTER(gsync_backoff),
+                                              u32p, ctypes.c_size_t, u32p]),
+    "gsync_bench_sem": (ctypes.c_int, [u32p, ctypes.POINTER(gsync_sem_work), u32p]),
+    "gsync_probe_throughput": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, u32p, u32p, u32p]),
+    "gsync_probe_latency": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, u32p, u32p, u32p]),
+    "gsync_probe_pingpong": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, u32p, u32p, u32p]),
+    "gsync_probe_nanosleep": (ctypes.c_int, [u32p, ctypes.c_int, ctypes.c_int, u32p, u32p]),
+    "gsync_probe_cs": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, u32p, u32p, u32p]),
+    "gsync_probe_cs_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
+}
+
+_lib = None
+
+
+def lib():
+    """Loads libgsync.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1110_4623_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIG.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def ptr(x):
+    """Address of a torch tensor / int / ctypes object / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return ctypes.addressof(x)
+
+
+def stream_handle(stream=None):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class GsyncError(RuntimeError):
+    def __init__(self, fn, rc):
+        extra = f" (cudaError {lib().gsync_last_cuda_error()})" if rc == GSYNC_ECUDA else ""
+        super().__init__(f"{fn} returned {STATUS_NAMES.get(rc, rc)}{extra}")
+        self.rc = rc
+
+
+def check(fn, rc):
+    if rc != GSYNC_OK:
+        raise GsyncError(fn, rc)
+    return rc
+
+
+# ---- objects --------------------------------------------------------------------------
+
+def gsync_mutex_bytes(kind: int, max_waiters: int) -> int:
+    return lib().gsync_mutex_bytes(kind, max_waiters)
+
+
+def gsync_mutex_init(state, nbytes, kind, max_waiters, backoff=None, timeout_ns=0, stream=None) -> int:
+    bo = ctypes.byref(backoff) if backoff is not None else None
+    return lib().gsync_mutex_init(ptr(state), nbytes, kind, max_waiters, bo, timeout_ns, stream_handle(stream))
+
+
+def gsync_barrier_bytes(kind: int, nblocks: int, param: int) -> int:
+    return lib().gsync_barrier_bytes(kind, nblocks, param)
+
+
+def gsync_barrier_init(state, nbytes, kind, nblocks, param, timeout_ns=0, stream=None) -> int:
+    return lib().gsync_barrier_init(ptr(state), nbytes, kind, nblocks, param, timeout_ns, stream_handle(stream))
+
+
+def gsync_sem_bytes(kind: int) -> int:
+    return lib().gsync_sem_bytes(kind)
+
+
+def gsync_sem_init(state, nbytes, kind, initial_count, backoff=None, timeout_ns=0, stream=None) -> int:
+    bo = ctypes.byref(backoff) if backoff is not None else None
+    return lib().gsync_sem_init(ptr(state), nbytes, kind, initial_count, bo, timeout_ns, stream_handle(stream))
+
+
+def gsync_object_abort_flag(state, stream=None) -> tuple[int, int]:
+    v = ctypes.c_uint32(0)
+    rc = lib().gsync_object_abort_flag(ptr(state), ctypes.byref(v), stream_handle(stream))
+    return rc, v.value
+
+
+def gsync_max_coresident_blocks(workload: int, kind: int, block_threads: int, cluster: int = 1) -> tuple[int, int]:
+    v = ctypes.c_int(0)
+    rc = lib().gsync_max_coresident_blocks(workload, kind, block_threads, cluster, ctypes.byref(v))
+    return rc, v.value
+
+
+def gsync_device_sm_count() -> tuple[int, int]:
+    v = ctypes.c_int(0)
+    rc = lib().gsync_device_sm_count(ctypes.byref(v))
+    return rc, v.value
+
+
+def gsync_last_cuda_error() -> int:
+    return lib().gsync_last_cuda_error()
+
+
+# ---- workloads ------------------------------------------------------------------------
+
+def gsync_bench_barrier(state, work: gsync_barrier_work, stream=None) -> int:
+    return lib().gsync_bench_barrier(ptr(state), ctypes.byref(work), stream_handle(stream))
+
+
+def gsync_bench_mutex(state, work: gsync_mutex_work, stream=None) -> int:
+    return lib().gsync_bench_mutex(ptr(state), ctypes.byref(work), stream_handle(stream))
+
+
+def gsync_bench_mutex_workspace_bytes(kind, nblocks, acq, cs_words) -> int:
+    return lib().gsync_bench_mutex_workspace_bytes(kind, nblocks, acq, cs_words)
+
+
+def gsync_bench_mutex_host(work: gsync_mutex_work, backoff, workspace, workspace_bytes, stream=None) -> int:
+    bo = ctypes.byref(backoff) if backoff is not None else None
+    return lib().gsync_bench_mutex_host(ctypes.byref(work), bo, ptr(workspace), workspace_bytes,
+                                        stream_handle(stream))
+
+
+def gsync_bench_sem(state, work: gsync_sem_work, stream=None) -> int:
+    return lib().gsync_bench_sem(ptr(state), ctypes.byref(work), stream_handle(stream))
+
+
+# ---- probes ---------------------------------------------------------------------------
+
+def gsync_probe_throughput(op, contentious, pre_atomic, nblocks, block_threads, iters, scratch, times,
+                           stream=None) -> int:
+    return lib().gsync_probe_throughput(op, contentious, pre_atomic, nblocks, block_threads, iters, ptr(scratch),
+                                        ptr(times), stream_handle(stream))
+
+
+def gsync_probe_latency(op, iters, scratch, out, stream=None) -> int:
+    return lib().gsync_probe_latency(op, iters, ptr(scratch), ptr(out), stream_handle(stream))
+
+
+def gsync_probe_pingpong(sm_a, sm_b, iters, scratch, out, stream=None) -> int:
+    return lib().gsync_probe_pingpong(sm_a, sm_b, iters, ptr(scratch), ptr(out), stream_handle(stream))
+
+
+def gsync_probe_nanosleep(req_ns, n, iters, out_ns, stream=None) -> int:
+    return lib().gsync_probe_nanosleep(ptr(req_ns), n, iters, ptr(out_ns), stream_handle(stream))
+
+
+def gsync_probe_cs(cs_words, block_threads, iters, scratch, out, stream=None) -> int:
+    return lib().gsync_probe_cs(cs_words, block_threads, iters, ptr(scratch), ptr(out), stream_handle(stream))
+
+
+def gsync_probe_cs_scratch_bytes(cs_words, iters) -> int:
+    return lib().gsync_probe_cs_scratch_bytes(cs_words, iters)

@@ -1,0 +1,232 @@
+"""Device-memory plumbing around the C ABI: allocates the objects and the workload buffers
+as torch tensors, calls the entry points and copies results back as numpy arrays.  Every
+synchronization step runs in the CUDA library (gsync.py raises if it is not built).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import gsync as G
+
+
+def _u32(a) -> torch.Tensor:
+    """Host uint32 array -> int32 device tensor with the same bits."""
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).cuda()
+
+
+def _zeros(n: int) -> torch.Tensor:
+    return torch.zeros(max(int(n), 1), dtype=torch.int32, device="cuda")
+
+
+def _np(t: torch.Tensor, n: int | None = None) -> np.ndarray:
+    a = t.cpu().numpy().view(np.uint32)
+    return a if n is None else a[:n]
+
+
+def _state(nbytes: int) -> torch.Tensor:
+    if nbytes <= 0:
+        raise G.GsyncError("size query", G.GSYNC_EINVAL)
+    t = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    assert t.data_ptr() % 256 == 0
+    return t
+
+
+def backoff(policy: int = G.BACKOFF_EXPONENTIAL, min_ns: int = 0, max_ns: int = 0) -> G.gsync_backoff:
+    return G.gsync_backoff(policy, min_ns, max_ns, 0)
+
+
+@dataclass
+class StatusView:
+    rc: int
+    bits: int
+
+    @property
+    def ok(self) -> bool:
+        return self.rc == G.GSYNC_OK and self.bits == 0
+
+
+# ---------------------------------------------------------------------------------------
+
+class BarrierRun:
+    """A barrier object plus the buffers of the barrier workload (gsync_bench_barrier)."""
+
+    def __init__(self, kind: str, nblocks: int, block_threads: int, rounds: int, full: bool,
+                 param: int = 0, timeout_ns: int = 0):
+        self.kind, self.k = kind, G.BARRIER_KINDS[kind]
+        self.nblocks, self.rounds, self.full = nblocks, rounds, full
+        if kind == "tree" and param == 0:
+            param = 8
+        if kind == "cluster" and param == 0:
+            param = 2
+        self.param = param
+        nbytes = G.gsync_barrier_bytes(self.k, nblocks, param)
+        self.state = _state(nbytes)
+        G.check("gsync_barrier_init", G.gsync_barrier_init(self.state, nbytes, self.k, nblocks, param, timeout_ns))
+        self.slots = _zeros(2 * nblocks)
+        self.chk = _zeros(rounds * nblocks) if full else None
+        self.mix = _zeros(nblocks)
+        self.bad = _zeros(nblocks)
+        self.status = _zeros(1)
+        self.work = G.gsync_barrier_work(self.k, nblocks, block_threads, rounds, int(full),
+                                         param if kind == "cluster" else 1,
+                                         G.ptr(self.slots), G.ptr(self.chk), G.ptr(self.mix), G.ptr(self.bad),
+                                         G.ptr(self.status))
+
+    def launch(self, stream=None) -> int:
+        return G.gsync_bench_barrier(self.state, self.work, stream)
+
+    def run(self) -> dict:
+        self.status.zero_()
+        rc = self.launch()
+        torch.cuda.synchronize()
+        out = {"rc": rc, "status": int(_np(self.status)[0]), "mix": _np(self.mix), "bad": _np(self.bad)}
+        if self.full:
+            out["chk"] = _np(self.chk).reshape(self.rounds, self.nblocks)
+        return out
+
+
+class MutexRun:
+    """A mutex object plus the buffers of the mutex workload (gsync_bench_mutex)."""
+
+    def __init__(self, kind: str, nblocks: int, block_threads: int, acq: int, cs_words: int,
+                 delay: np.ndarray | None, addend: np.ndarray, bo: G.gsync_backoff | None = None,
+                 timeout_ns: int = 0):
+        self.kind, self.k = kind, G.MUTEX_KINDS[kind]
+        self.nblocks, self.acq, self.cs_words = nblocks, acq, cs_words
+        self.bo = bo
+        n = nblocks * acq
+        self.nbytes = G.gsync_mutex_bytes(self.k, nblocks)
+        self.state = _state(self.nbytes)
+        G.check("gsync_mutex_init", G.gsync_mutex_init(self.state, self.nbytes, self.k, nblocks, bo, timeout_ns))
+        self.delay = _u32(delay) if delay is not None else None
+        self.addend = _u32(addend)
+        self.data = _zeros(cs_words)
+        self.total = _zeros(1)
+        self.log = _zeros(n)
+        self.ticket = _zeros(n)
+        self.count = _zeros(nblocks)
+        self.status = _zeros(1)
+        self.work = G.gsync_mutex_work(self.k, nblocks, block_threads, acq, cs_words, 0,
+                                       G.ptr(self.delay), G.ptr(self.addend), G.ptr(self.data), G.ptr(self.total),
+                                       G.ptr(self.log), G.ptr(self.ticket), G.ptr(self.count), G.ptr(self.status))
+
+    def reset(self):
+        self.data.zero_()
+        self.total.zero_()
+        self.status.zero_()
+
+    def launch(self, stream=None) -> int:
+        return G.gsync_bench_mutex(self.state, self.work, stream)
+
+    def results(self) -> dict:
+        torch.cuda.synchronize()
+        n = self.nblocks * self.acq
+        return {"status": int(_np(self.status)[0]), "data": _np(self.data, self.cs_words),
+                "total": _np(self.total)[0], "log": _np(self.log, n), "ticket": _np(self.ticket, n),
+                "count": _np(self.count)}
+
+    def run(self) -> dict:
+        self.reset()
+        rc = self.launch()
+        out = self.results()
+        out["rc"] = rc
+        return out
+
+
+class SemRun:
+    """A counting semaphore plus the buffers of the semaphore workload (gsync_bench_sem)."""
+
+    def __init__(self, kind: str, nblocks: int, block_threads: int, pairs: int, initial_count: int,
+                 hold: np.ndarray | None, addend: np.ndarray, bo: G.gsync_backoff | None = None,
+                 timeout_ns: int = 0):
+        self.kind, self.k = kind, G.SEM_KINDS[kind]
+        self.nblocks, self.pairs, self.n = nblocks, pairs, initial_count
+        nbytes = G.gsync_sem_bytes(self.k)
+        self.state = _state(nbytes)
+        G.check("gsync_sem_init", G.gsync_sem_init(self.state, nbytes, self.k, initial_count, bo, timeout_ns))
+        self.hold = _u32(hold) if hold is not None else None
+        self.addend = _u32(addend)
+        self.scalars = _zeros(5 * 32)  # occupancy, max_occupancy, total, tally, status on separate lines
+        self.count = _zeros(nblocks)
+        s = self.scalars
+        self.work = G.gsync_sem_work(self.k, nblocks, block_threads, pairs, initial_count, 0,
+                                     G.ptr(self.hold), G.ptr(self.addend), s.data_ptr(), s.data_ptr() + 128,
+                                     s.data_ptr() + 256, s.data_ptr() + 384, G.ptr(self.count), s.data_ptr() + 512)
+
+    def reset(self):
+        self.scalars.zero_()
+
+    def launch(self, stream=None) -> int:
+        return G.gsync_bench_sem(self.state, self.work, stream)
+
+    def results(self) -> dict:
+        torch.cuda.synchronize()
+        s = _np(self.scalars)
+        return {"occupancy": int(s[0]), "max_occ": int(s[32]), "total": s[64], "tally": s[96],
+                "status": int(s[128]), "count": _np(self.count)}
+
+    def run(self) -> dict:
+        self.reset()
+        rc = self.launch()
+        out = self.results()
+        out["rc"] = rc
+        return out
+
+
+# ---- probes ---------------------------------------------------------------------------
+
+def probe_throughput(op: str, contentious: bool, pre_atomic: bool, nblocks: int, block_threads: int = 128,
+                     iters: int = 1000) -> dict:
+    """Runs one probe; returns the span of the blocks' globaltimer windows (ns) and ops/s."""
+    scratch = _state(256 * nblocks)
+    times = torch.zeros(2 * nblocks, dtype=torch.int64, device="cuda")
+    G.check("gsync_probe_throughput", G.gsync_probe_throughput(G.PROBE_OPS[op], int(contentious), int(pre_atomic),
+                                                               nblocks, block_threads, iters, scratch, times))
+    torch.cuda.synchronize()
+    t = times.cpu().numpy().reshape(nblocks, 2)
+    span = int(t[:, 1].max() - t[:, 0].min())
+    return {"ns": span, "ops_per_s": nblocks * iters / (span * 1e-9) if span > 0 else float("inf"),
+            "mean_block_ns": float((t[:, 1] - t[:, 0]).mean())}
+
+
+def probe_latency(op: str, iters: int = 4096) -> dict:
+    scratch = _state(256)
+    out = torch.zeros(2, dtype=torch.int64, device="cuda")
+    G.check("gsync_probe_latency", G.gsync_probe_latency(G.PROBE_OPS[op], iters, scratch, out))
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    return {"ns_per_op": o[0] / iters, "cycles_per_op": o[1] / iters}
+
+
+def probe_pingpong(sm_a: int, sm_b: int, iters: int = 2000) -> dict:
+    scratch = _state(512)
+    out = torch.zeros(4, dtype=torch.int64, device="cuda")
+    G.check("gsync_probe_pingpong", G.gsync_probe_pingpong(sm_a, sm_b, iters, scratch, out))
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    return {"handoff_ns": o[0] / (2 * iters), "status": int(o[3]), "sm_a": int(o[1]), "sm_b": int(o[2])}
+
+
+def probe_nanosleep(req_ns, iters: int = 64) -> np.ndarray:
+    req = _u32(np.asarray(req_ns, dtype=np.uint32))
+    out = torch.zeros(len(req_ns), dtype=torch.int64, device="cuda")
+    G.check("gsync_probe_nanosleep", G.gsync_probe_nanosleep(req, len(req_ns), iters, out))
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def probe_cs(cs_words: int, block_threads: int = 256, iters: int = 20000) -> dict:
+    nbytes = G.gsync_probe_cs_scratch_bytes(cs_words, iters)
+    scratch = _state(nbytes)
+    out = (G.ctypes.c_uint64 * 1)()
+    G.check("gsync_probe_cs", G.gsync_probe_cs(cs_words, block_threads, iters, scratch, out))
+    return {"ns_per_cs": out[0] / iters}
+
+
+def sm_count() -> int:
+    rc, n = G.gsync_device_sm_count()
+    G.check("gsync_device_sm_count", rc)
+    return n

@@ -1,0 +1,79 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports every function that
+include/gsync.h declares (no compute calls: this runs on the CPU-only machine too)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", h) for h in os.listdir(os.path.join(ROOT, "include")) if h.endswith(".h")]
+
+
+def declared_functions():
+    names = set()
+    for h in HEADERS:
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:int|size_t|void|uint32_t|uint64_t)\s+\**\s*(gsync_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_1110_4623_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["gsync_mutex_bytes", "gsync_mutex_init", "gsync_barrier_bytes", "gsync_barrier_init",
+                     "gsync_sem_bytes", "gsync_sem_init", "gsync_bench_barrier", "gsync_bench_mutex",
+                     "gsync_bench_sem", "gsync_probe_throughput", "gsync_max_coresident_blocks"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_binding_signatures_match(lib_path):
+    from paper_1110_4623_gb300 import gsync
+    lib = gsync.lib()
+    for name in declared_functions():
+        assert hasattr(lib, name)
+        assert name in gsync._SIG, f"binding has no signature for {name}"
+
+
+def test_size_queries_without_gpu(lib_path):
+    from paper_1110_4623_gb300 import gsync as G
+    # Pure host arithmetic: no CUDA call is made.
+    assert G.gsync_mutex_bytes(G.MUTEX_KINDS["cas_spin"], 1184) == 3 * 128
+    assert G.gsync_mutex_bytes(G.MUTEX_KINDS["sleep_queue"], 1184) == (3 + 2048) * 128
+    assert G.gsync_mutex_bytes(9, 4) == 0 and G.gsync_mutex_bytes(0, 0) == 0
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["atomic"], 1184, 0) == 3 * 128
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["flag"], 1184, 0) == (1 + 37 + 37) * 128
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["flag"], 1184, 1) == (1 + 37 + 1) * 128
+    # fan-in 8 over 1184 blocks: 148 + 19 + 3 + 1 nodes
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["tree"], 1184, 8) == (2 + 148 + 19 + 3 + 1) * 128
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["tree"], 16, 1) == 0
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["cluster"], 1184, 8) == 3 * 128
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["cluster"], 1183, 8) == 0
+    assert G.gsync_sem_bytes(0) == 4 * 128 and G.gsync_sem_bytes(3) == 0
+    assert G.gsync_bench_mutex_workspace_bytes(2, 1184, 100, 1024) > 4 * 1184 * 100 * 4
+    assert G.gsync_probe_cs_scratch_bytes(64, 1000) > 0
+
+
+def test_invalid_arguments_rejected_without_gpu(lib_path):
+    from paper_1110_4623_gb300 import gsync as G
+    # Null / misaligned state is rejected before any CUDA call.
+    assert G.lib().gsync_mutex_init(None, 384, 0, 4, None, 0, None) == G.GSYNC_EINVAL
+    assert G.lib().gsync_mutex_init(0x1001, 384, 0, 4, None, 0, None) == G.GSYNC_EINVAL
+    assert G.lib().gsync_barrier_init(0x1000, 10, 0, 4, 0, 0, None) == G.GSYNC_EINVAL  # too small
+    w = G.gsync_mutex_work(0, 0, 256, 1, 1, 0, None, None, None, None, None, None, None, None)
+    assert G.lib().gsync_bench_mutex(0x1000, ctypes.byref(w), None) == G.GSYNC_EINVAL

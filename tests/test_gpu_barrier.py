@@ -1,0 +1,89 @@
+"""Barrier workload on the GPU against the oracle, bit-exact (Section 5, "Barrier")."""
+import numpy as np
+import pytest
+
+from gpu_util import require_gpu
+from oracle import calc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+KINDS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("tree", 2), ("cluster", 2), ("cluster", 4),
+         ("cluster", 8)]
+
+
+@pytest.mark.parametrize("kind,param", KINDS)
+def test_config1_full_fold_10000_rounds(kind, param):
+    # 16 blocks x 128 threads, 10,000 rounds; per-round XOR checksum of all 16 slots.
+    from paper_1110_4623_gb300 import runner
+    got = runner.BarrierRun(kind, 16, 128, 10_000, full=True, param=param).run()
+    want = calc.barrier_full(16, 10_000)
+    assert got["rc"] == 0 and got["status"] == 0, got["status"]
+    assert np.array_equal(got["chk"], want["chk"])
+    assert np.array_equal(got["mix"], want["mix"])
+    assert not got["bad"].any()
+
+
+@pytest.mark.parametrize("kind,param", KINDS)
+@pytest.mark.parametrize("nblocks", [148, 296, 592, 1184])
+def test_sampled_sweep_1000_rounds(kind, param, nblocks):
+    # A cluster launch needs the grid to be a multiple of the cluster size: 148 blocks run as
+    # 144 with clusters of 8.
+    from paper_1110_4623_gb300 import runner
+    if kind == "cluster":
+        nblocks -= nblocks % param
+    got = runner.BarrierRun(kind, nblocks, 128, 1000, full=False, param=param).run()
+    want = calc.barrier_sampled(nblocks, 1000)
+    assert got["rc"] == 0 and got["status"] == 0, got["status"]
+    assert not got["bad"].any(), int(got["bad"].sum())
+    assert np.array_equal(got["mix"], want["mix"])
+
+
+@pytest.mark.parametrize("kind,param", [("atomic", 0), ("flag", 0), ("tree", 3), ("cluster", 1)])
+@pytest.mark.parametrize("nblocks,threads", [(1, 32), (2, 64), (37, 96), (151, 256)])
+def test_ragged_grids_full_fold(kind, param, nblocks, threads):
+    from paper_1110_4623_gb300 import runner
+    got = runner.BarrierRun(kind, nblocks, threads, 300, full=True, param=param).run()
+    want = calc.barrier_full(nblocks, 300)
+    assert got["rc"] == 0 and got["status"] == 0
+    assert np.array_equal(got["chk"], want["chk"]) and np.array_equal(got["mix"], want["mix"])
+    assert not got["bad"].any()
+
+
+def test_zero_rounds():
+    from paper_1110_4623_gb300 import runner
+    got = runner.BarrierRun("atomic", 8, 128, 0, full=False).run()
+    assert got["rc"] == 0 and got["status"] == 0 and not got["mix"].any()
+
+
+def test_repeated_launches_continue_epochs():
+    # The object keeps its epoch across launches: a second launch attaches at the new epoch.
+    from paper_1110_4623_gb300 import runner
+    br = runner.BarrierRun("flag", 64, 128, 501, full=False)
+    for _ in range(3):
+        got = br.run()
+        assert got["status"] == 0 and not got["bad"].any()
+        assert np.array_equal(got["mix"], calc.barrier_sampled(64, 501)["mix"])
+
+
+def test_max_coresident_grid_runs():
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    rc, maxb = G.gsync_max_coresident_blocks(0, G.BARRIER_KINDS["atomic"], 128, 1)
+    assert rc == 0 and maxb >= 1184
+    got = runner.BarrierRun("atomic", maxb, 128, 200, full=False).run()
+    assert got["status"] == 0 and np.array_equal(got["mix"], calc.barrier_sampled(maxb, 200)["mix"])
+
+
+def test_grid_beyond_coresidency_is_refused():
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    rc, maxb = G.gsync_max_coresident_blocks(0, G.BARRIER_KINDS["atomic"], 256, 1)
+    assert rc == 0
+    br = runner.BarrierRun("atomic", maxb + 1, 256, 10, full=False)
+    assert br.launch() == G.GSYNC_ENOTRESIDENT

@@ -1,0 +1,64 @@
+"""Failure detection without a GPU fault: waits that can never succeed (a lock word that
+nothing releases, a barrier counter that can never reach its target) end at the object's
+timeout, report it in the status word, and leave the context usable."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import require_gpu
+from oracle import calc
+from paper_1110_4623_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+# Lock word held by nobody (CAS kinds); a turn no ticket reaches (ticket); the first queue
+# slot holding a ticket nobody has (queue lock).
+@pytest.mark.parametrize("kind,line,value", [("cas_spin", 1, 1), ("cas_backoff", 1, 1), ("ticket", 2, 0x40000000),
+                                             ("sleep_queue", 3, 99)])
+def test_lock_that_is_never_released_times_out(kind, line, value):
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    delay, add = inputs.mutex_inputs(64, 4, 1, max_delay=0)
+    mr = runner.MutexRun(kind, 64, 128, 4, 8, delay, add, bo=runner.backoff(min_ns=100, max_ns=1000),
+                         timeout_ns=200_000_000)
+    words = mr.state.view(torch.int32)
+    words[line * 32] = value  # held by nobody / a turn that is never reached
+    got = mr.run()
+    assert got["rc"] == 0
+    assert got["status"] & (G.GSYNC_STATUS_TIMEOUT | G.GSYNC_STATUS_ABORTED)
+    assert got["status"] & G.GSYNC_STATUS_TIMEOUT
+    assert got["total"] == 0 and not got["count"].any()
+    assert G.gsync_object_abort_flag(mr.state)[1] != 0
+    # The context is still usable: a fresh object runs to completion.
+    ok = runner.MutexRun(kind, 64, 128, 4, 8, delay, add).run()
+    assert ok["status"] == 0 and ok["total"] == 256
+
+
+@pytest.mark.parametrize("kind", ["atomic", "cluster"])
+def test_barrier_that_can_never_complete_times_out(kind):
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    br = runner.BarrierRun(kind, 64, 128, 10, full=False, param=2 if kind == "cluster" else 0,
+                           timeout_ns=200_000_000)
+    words = br.state.view(torch.int32)
+    words[32] = 1_000_000  # arrival counter already past every target: nobody is last
+    got = br.run()
+    assert got["rc"] == 0 and got["status"] & G.GSYNC_STATUS_TIMEOUT
+    ok = runner.BarrierRun(kind, 64, 128, 10, full=False, param=2 if kind == "cluster" else 0).run()
+    assert ok["status"] == 0 and np.array_equal(ok["mix"], calc.barrier_sampled(64, 10)["mix"])
+
+
+def test_semaphore_with_no_free_slot_times_out():
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    hold, add = inputs.sem_inputs(32, 2, 5, 0, 10)
+    sr = runner.SemRun("ticket", 32, 128, 2, 1, hold, add, timeout_ns=200_000_000)
+    sr.state.view(torch.int32)[32] = 1000  # count says 1000 holders: every wait must queue
+    got = sr.run()
+    assert got["status"] & G.GSYNC_STATUS_TIMEOUT

@@ -1,0 +1,98 @@
+"""Mutex workload on the GPU against the oracle (Section 5, "Mutex"): exact final counters
+and data words, a valid grant log, and ticket-order grants for the fair kinds."""
+import numpy as np
+import pytest
+
+from gpu_util import require_gpu
+from oracle import calc
+from paper_1110_4623_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+KINDS = ["cas_spin", "cas_backoff", "ticket", "sleep_queue"]
+FAIR = {"ticket", "sleep_queue"}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def backoff_for(kind):
+    from paper_1110_4623_gb300 import runner
+    return runner.backoff(min_ns=32, max_ns=2048) if kind == "cas_backoff" else None
+
+
+def check(kind, nblocks, threads, acq, cs_words, max_delay=2000):
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    seed = inputs.mutex_seed(G.MUTEX_KINDS[kind], nblocks, cs_words)
+    delay, add = inputs.mutex_inputs(nblocks, acq, seed, max_delay=max_delay)
+    got = runner.MutexRun(kind, nblocks, threads, acq, cs_words, delay, add, bo=backoff_for(kind),
+                          timeout_ns=10_000_000_000).run()
+    want = calc.mutex_final(nblocks, acq, cs_words, add)
+    assert got["rc"] == 0 and got["status"] == 0, got["status"]
+    assert got["total"] == want["total"]
+    assert np.array_equal(got["count"], want["count"])
+    assert np.array_equal(got["data"], want["data"])
+    fifo = kind in FAIR
+    assert calc.check_grant_log(got["log"], got["ticket"] if fifo else None, nblocks, acq, fifo) == []
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("nblocks", [148, 296, 592, 1184])
+@pytest.mark.parametrize("cs_words", [0, 64, 1024])
+def test_contention_sweep_full_size(kind, nblocks, cs_words):
+    # 256 threads per block, 100 acquisitions per block, delays U{0..2000} cycles.
+    check(kind, nblocks, 256, 100, cs_words)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("nblocks,threads,acq,cs_words", [(1, 32, 50, 7), (3, 64, 17, 33), (37, 96, 9, 1000),
+                                                            (151, 256, 5, 1025)])
+def test_ragged_shapes(kind, nblocks, threads, acq, cs_words):
+    check(kind, nblocks, threads, acq, cs_words, max_delay=300)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_no_acquisitions(kind):
+    from paper_1110_4623_gb300 import runner
+    got = runner.MutexRun(kind, 8, 128, 0, 16, None, np.zeros(0, np.uint32)).run()
+    assert got["status"] == 0 and got["total"] == 0 and not got["count"].any() and not got["data"].any()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_state_reused_across_launches(kind):
+    # After a launch every lock is free again (ticket == turn, queue flag advanced), so the
+    # same object serves the next launch.
+    from paper_1110_4623_gb300 import runner
+    delay, add = inputs.mutex_inputs(296, 20, 77, max_delay=100)
+    mr = runner.MutexRun(kind, 296, 256, 20, 64, delay, add, bo=backoff_for(kind))
+    want = calc.mutex_final(296, 20, 64, add)
+    for rep in range(3):
+        got = mr.run()
+        assert got["status"] == 0 and np.array_equal(got["data"], want["data"])
+        base = rep * 296 * 20 if kind in FAIR else 0
+        fifo = kind in FAIR
+        assert calc.check_grant_log(got["log"], got["ticket"] if fifo else None, 296, 20, fifo, ticket_base=base) == []
+
+
+def test_host_buffer_entry_point():
+    import ctypes
+    import torch
+    from paper_1110_4623_gb300 import gsync as G
+    B, A, K = 592, 30, 64
+    delay, add = inputs.mutex_inputs(B, A, 12345)
+    n = B * A
+    data = np.zeros(K, np.uint32); total = np.zeros(1, np.uint32); log = np.zeros(n, np.uint32)
+    tick = np.zeros(n, np.uint32); count = np.zeros(B, np.uint32); status = np.zeros(1, np.uint32)
+    p = lambda a: a.ctypes.data
+    w = G.gsync_mutex_work(G.MUTEX_KINDS["ticket"], B, 256, A, K, 0, p(delay), p(add), p(data), p(total), p(log),
+                           p(tick), p(count), p(status))
+    nbytes = G.gsync_bench_mutex_workspace_bytes(w.kind, B, A, K)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    rc = G.gsync_bench_mutex_host(w, None, ws, nbytes)
+    assert rc == 0 and status[0] == 0
+    want = calc.mutex_final(B, A, K, add)
+    assert total[0] == want["total"] and np.array_equal(data, want["data"])
+    assert calc.check_grant_log(log, tick, B, A, fifo=True) == []
