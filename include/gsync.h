@@ -152,6 +152,27 @@ typedef struct gsync_barrier_work {
 } gsync_barrier_work;
 int gsync_bench_barrier(void* state, const gsync_barrier_work* w, void* stream);
 
+/* The barrier workload for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this is a library convenience.  Some callers cannot call cudaMalloc: code
+ * running where a device allocation is not allowed or would stall (a host callback, a loop
+ * that must not take cudaMalloc's implicit device synchronization, a plugin whose framework
+ * owns all device memory).  This variant allocates nothing.  The barrier object and the
+ * slot buffers live in one 128 KiB file-scope device array inside the library, which every
+ * GPU that loads the library holds until the process exits.  The caller still passes the
+ * outputs in `w` (chk, mix, bad, status; w->slots is ignored).
+ *  - Limits: nblocks <= GSYNC_STATIC_MAX_BLOCKS (4096), and the object for (kind, nblocks,
+ *    param) must fit in 96 KiB (gsync_barrier_bytes); anything larger returns GSYNC_EINVAL.
+ *    `param` is the TREE fan-in or the FLAG release mode; CLUSTER takes w->cluster.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current and caches it; make that first call
+ *    before any stream capture.
+ *  - Every call shares the one array and each call rewrites the object and clears the
+ *    slots, so calls whose work overlaps on the GPU (other streams, other threads) race and
+ *    must be serialized by the caller. */
+#define GSYNC_STATIC_MAX_BLOCKS 4096
+int gsync_bench_barrier_static(const gsync_barrier_work* w, int param, uint64_t timeout_ns,
+                               void* stream);
+
 /* Mutex workload.  Block b makes `acq` acquisitions (id = b*acq + a): it waits delay[id]
  * SM cycles, locks, and inside the critical section its thread 0 appends id to
  * grant_log[total] and increments total (plain load/store), records the lock ticket in

@@ -10,6 +10,8 @@
 //   sampled : thread 0 reads partner p = (b + r + 1) mod B only, folds lowbias32(slot_p) into
 //             mix and counts a stale read in bad.  This keeps the per-round work O(1) so the
 //             kernel time measures the barrier itself at large grids.
+#include <mutex>
+
 #include "common.cuh"
 
 using namespace gsync_impl;
@@ -124,4 +126,62 @@ extern "C" int gsync_bench_barrier(void* state, const gsync_barrier_work* w, voi
   }
   return launch_coresident(k, w->nblocks, w->block_threads, cluster, 0, (cudaStream_t)stream, (uint32_t*)state,
                            w->rounds, w->slots, w->chk, w->mix, w->bad, w->status);
+}
+
+// ---------------------------------------------------------------------------------------
+// Barrier workload without allocation.  Some callers cannot call cudaMalloc: code that runs
+// where a device allocation is not allowed or would stall (a host callback, a loop that
+// must not take the implicit device synchronization of cudaMalloc/cudaFree, or a plugin
+// whose host framework owns all device memory).  This entry point keeps the barrier object
+// and the slot buffers in one file-scope device array instead of caller memory.  The array
+// is part of the loaded module, so every GPU that loads the library holds it until exit.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticScratchBytes = 128 * 1024;
+constexpr size_t kStaticSlotBytes = 2 * (size_t)GSYNC_STATIC_MAX_BLOCKS * 4;  // 32 KiB
+constexpr size_t kStaticStateBytes = kStaticScratchBytes - kStaticSlotBytes;  // 96 KiB
+static_assert(kStaticStateBytes % 256 == 0, "slot buffers start on a 256-byte boundary");
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mutex;
+void* g_static_address[256] = {};  // device address of g_static_scratch, per device ordinal
+
+// In host code the name g_static_scratch is only a stand-in; the kernel needs the device
+// address, looked up once per device with that device current.
+int static_scratch_address(void** out) {
+  int dev = 0;
+  GSYNC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return GSYNC_EINVAL;
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (g_static_address[dev] == nullptr) {
+    void* p = nullptr;
+    GSYNC_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
+    g_static_address[dev] = p;
+  }
+  *out = g_static_address[dev];
+  return GSYNC_OK;
+}
+
+}  // namespace
+
+extern "C" int gsync_bench_barrier_static(const gsync_barrier_work* w, int param, uint64_t timeout_ns,
+                                          void* stream) {
+  if (!w || w->nblocks < 1 || w->nblocks > GSYNC_STATIC_MAX_BLOCKS) return GSYNC_EINVAL;
+  if (!w->mix || !w->bad || !w->status || (w->full && !w->chk)) return GSYNC_EINVAL;
+  const int p = w->kind == GSYNC_BAR_CLUSTER ? w->cluster : param;
+  const size_t state_bytes = gsync_barrier_bytes(w->kind, w->nblocks, p);
+  if (state_bytes == 0 || state_bytes > kStaticStateBytes) return GSYNC_EINVAL;
+  void* base = nullptr;
+  if (int rc = static_scratch_address(&base)) return rc;
+  void* state = base;
+  uint32_t* slots = (uint32_t*)((unsigned char*)base + kStaticStateBytes);
+  cudaStream_t st = (cudaStream_t)stream;
+  // The array keeps the previous call's contents: rewrite the whole object and clear the slots.
+  if (int rc = gsync_barrier_init(state, state_bytes, w->kind, w->nblocks, p, timeout_ns, stream)) return rc;
+  GSYNC_CUDA(cudaMemsetAsync(slots, 0, 2 * (size_t)w->nblocks * 4, st));
+  gsync_barrier_work dw = *w;
+  dw.slots = slots;
+  return gsync_bench_barrier(state, &dw, stream);
 }

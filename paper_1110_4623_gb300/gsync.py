@@ -71,6 +71,8 @@ _SIG = {
     "gsync_device_sm_count": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
     "gsync_last_cuda_error": (ctypes.c_int, []),
     "gsync_bench_barrier": (ctypes.c_int, [u32p, ctypes.POINTER(gsync_barrier_work), u32p]),
+    "gsync_bench_barrier_static": (ctypes.c_int, [ctypes.POINTER(gsync_barrier_work), ctypes.c_int, ctypes.c_uint64,
+                                                  u32p]),
     "gsync_bench_mutex": (ctypes.c_int, [u32p, ctypes.POINTER(gsync_mutex_work), u32p]),
     "gsync_bench_mutex_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "gsync_bench_mutex_host": (ctypes.c_int, [ctypes.POINTER(gsync_mutex_work), ctypes.POINTER(gsync_backoff),
@@ -190,6 +192,11 @@ def gsync_last_cuda_error() -> int:
 
 def gsync_bench_barrier(state, work: gsync_barrier_work, stream=None) -> int:
     return lib().gsync_bench_barrier(ptr(state), ctypes.byref(work), stream_handle(stream))
+
+
+def gsync_bench_barrier_static(work: gsync_barrier_work, param: int = 0, timeout_ns: int = 0, stream=None) -> int:
+    """The barrier workload in the library's own static device scratch (no allocation)."""
+    return lib().gsync_bench_barrier_static(ctypes.byref(work), param, timeout_ns, stream_handle(stream))
 
 
 def gsync_bench_mutex(state, work: gsync_mutex_work, stream=None) -> int:
