@@ -1,0 +1,64 @@
+"""Runs one named workload launch once, for capturing it under a profiler.
+
+    python -m paper_1110_4623_gb300.profile_cases <case> [<case> ...]
+
+Each case launches a single workload kernel at the bench's grid (1184 blocks) with fewer
+operations per block than the bench, so that a multi-pass profiler capture stays short.
+The result is checked against nothing; the parity tests do that.
+"""
+from __future__ import annotations
+
+import sys
+
+import torch
+
+from . import gsync as G
+from . import inputs, runner
+
+NB = 1184
+
+
+def _mutex(kind, K, acq=20):
+    delay, add = inputs.mutex_inputs(NB, acq, inputs.mutex_seed(G.MUTEX_KINDS[kind], NB, K))
+    bo = runner.backoff(min_ns=32, max_ns=2048) if kind == "cas_backoff" else None
+    r = runner.MutexRun(kind, NB, 256, acq, K, delay, add, bo=bo, timeout_ns=10_000_000_000)
+    return lambda: G.check("gsync_bench_mutex", r.launch())
+
+
+def _barrier(kind, param, rounds=200):
+    r = runner.BarrierRun(kind, NB, 128, rounds, full=False, param=param, timeout_ns=10_000_000_000)
+    return lambda: G.check("gsync_bench_barrier", r.launch())
+
+
+def _sem(n, pairs=20):
+    hold, add = inputs.sem_inputs(NB, pairs, inputs.SEED_SEM ^ (n << 16) ^ NB)
+    r = runner.SemRun("ticket", NB, 128, pairs, n, hold, add, timeout_ns=10_000_000_000)
+    return lambda: G.check("gsync_bench_sem", r.launch())
+
+
+CASES = {
+    "mutex_sleep_queue": lambda: _mutex("sleep_queue", 64),
+    "mutex_ticket": lambda: _mutex("ticket", 64),
+    "mutex_cas_spin": lambda: _mutex("cas_spin", 64),
+    "mutex_cas_backoff": lambda: _mutex("cas_backoff", 64),
+    "barrier_atomic": lambda: _barrier("atomic", 0),
+    "barrier_flag": lambda: _barrier("flag", 0),
+    "barrier_cluster2": lambda: _barrier("cluster", 2),
+    "sem_ticket_n4": lambda: _sem(4),
+}
+
+
+def main(argv):
+    if not argv or any(a not in CASES for a in argv):
+        print(f"usage: python -m paper_1110_4623_gb300.profile_cases {{{','.join(CASES)}}} ...")
+        return 2
+    torch.cuda.set_device(0)
+    launches = [CASES[a]() for a in argv]
+    for f in launches:
+        f()
+    torch.cuda.synchronize()
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main(sys.argv[1:]))
