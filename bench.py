@@ -3,15 +3,17 @@
 One step = one pass over every row of the hot path at 1184 blocks:
   * mutex contention (4 kinds x critical sections of 0/64/1024 words, 256 threads per block,
     100 acquisitions per block, seeded delays U{0..2000} cycles),
-  * grid barriers (atomic, flag, tree, cluster 2/4/8; 128 threads, 1000 rounds each),
+  * grid barriers (atomic, flag, tree, cluster 2/4/8, sharded; 128 threads, 1000 rounds each),
   * counting semaphores (sleeping FA kind, n in {1, 4, 16, 64}; 128 threads, 200 pairs each,
     hold U{100..5000} cycles).
 `value` is lock acquisitions per second of the library's default mutex kind over its three
 critical-section sizes; the other rows are reported beside it (barrier ns per crossing,
-semaphore ops/s).  The roofline terms (hand-off latency between SMs, critical-section time,
-same-word atomic throughput, atomic round trip) are measured by the probe kernels in the same
-run.  `--impl reference` times the CPU oracle (threaded C execution of the same workload on the
-host cores).  Under torchrun every rank runs the same workload on its own GPU (replicas).
+semaphore ops/s), each against a roofline whose terms (SM-to-SM hand-off latency,
+critical-section time, same-word atomic throughput, atomic round trip) the probe kernels
+measure in the same run.  After the timed steps, the batched many-mutex workload (4096 Zipf
+keys, 1e6 acquisitions, 64 barrier groups) is autotuned and replayed from a CUDA graph.
+`--impl reference` times the CPU oracle (threaded C execution of the same mutex workload on
+the host cores).  Under torchrun every rank runs the same workload on its own GPU (replicas).
 """
 from __future__ import annotations
 
@@ -32,10 +34,17 @@ NBLOCKS = 1184
 MUTEX_THREADS, MUTEX_ACQ, CS_SIZES = 256, 100, (0, 64, 1024)
 BAR_THREADS, BAR_ROUNDS = 128, 1000
 SEM_THREADS, SEM_PAIRS, SEM_COUNTS = 128, 200, (1, 4, 16, 64)
-DEFAULT_MUTEX = "sleep_queue"
-DEFAULT_BARRIER = ("flag", 0)
-BARRIERS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("cluster", 2), ("cluster", 4), ("cluster", 8)]
-MUTEX_BACKOFF = {"cas_backoff": (32, 2048)}
+# Library defaults for GB300, chosen from 1184-block sweeps (the paper's API serves the
+# fastest implementation of each primitive for the GPU as the default, Section 5 "API").
+DEFAULT_MUTEX = "ticket"
+DEFAULT_BARRIER = ("sharded", 32)
+BARRIERS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("cluster", 2), ("cluster", 4), ("cluster", 8),
+            ("sharded", 32), ("sharded", 8)]
+# Backoff (min_ns, max_ns) per kind; the ticket kinds sleep min_ns per waiter ahead, capped.
+MUTEX_BACKOFF = {"cas_backoff": (16, 512), "ticket": (128, 4000)}
+SEM_BACKOFF = (64, 2000)
+# Batched many-mutex workload: 4096 keys, Zipf(1.1), 1e6 acquisitions, 64 barrier groups.
+BATCH_KEYS, BATCH_ACQ, BATCH_GROUPS, BATCH_ROUNDS, BATCH_THREADS = 4096, 1_000_000, 64, 100, 128
 METRIC = "lock acquires/s & barrier ns at 1184 blocks vs L2-atomic roofline; p99 latency"
 TIMEOUT_NS = 10_000_000_000
 
@@ -47,6 +56,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gsync", choices=["gsync", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched and serving sections")
     return p.parse_args()
 
 
@@ -55,6 +65,14 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def barrier_name(kind, param):
+    if kind == "flag":
+        return "flag_broadcast" if param else "flag"
+    if kind in ("tree", "cluster", "sharded"):
+        return f"{kind}{param}"
+    return kind
 
 
 # ------------------------------------------------------------------------------------------
@@ -105,40 +123,85 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------
-# GPU arm
+# roofline terms (probe kernels)
 # ------------------------------------------------------------------------------------------
 
-def measure_roofline_terms(runner, G):
-    """L_handoff, T_cs(K), R_same and L_rt from the probe kernels (medians)."""
+def measure_roofline_terms(runner, inputs):
+    """L_handoff, T_cs(K), T_cs_sem(n), R_same and L_rt from the probe kernels (medians)."""
     sms = runner.sm_count()
     pairs = [(0, 1), (0, sms // 2), (0, sms - 1), (sms // 4, 3 * sms // 4), (2, sms - 3)]
     hand = [runner.probe_pingpong(a, b, 4000) for a, b in pairs if a != b and 0 <= a < sms and 0 <= b < sms]
     hand_ns = [h["handoff_ns"] for h in hand if h["status"] == 0]
-    L_handoff = float(np.median(hand_ns))
     T_cs = {K: float(np.median([runner.probe_cs(K, MUTEX_THREADS, 20000)["ns_per_cs"] for _ in range(3)]))
             for K in CS_SIZES}
     rs = [runner.probe_throughput("red_add", True, False, NBLOCKS, 128, 2000)["ops_per_s"] for _ in range(3)]
     ra = [runner.probe_throughput("atomic_read", True, False, NBLOCKS, 128, 1000)["ops_per_s"] for _ in range(3)]
     L_rt = float(np.median([runner.probe_latency("atomic_read", 4000)["ns_per_op"] for _ in range(3)]))
-    return {"sms": sms, "L_handoff_ns": L_handoff, "L_handoff_pairs_ns": hand_ns, "T_cs_ns": T_cs,
+    T_cs_sem = {}
+    for n in SEM_COUNTS:
+        hold, add = inputs.sem_inputs(NBLOCKS, SEM_PAIRS, inputs.SEED_SEM ^ (n << 16) ^ NBLOCKS)
+        T_cs_sem[n] = runner.probe_sem_cs(hold[:4000], add[:4000], SEM_THREADS)["ns_per_cs"]
+    # The probes' frame (acquire load, barriers, release) is what a hand-off already costs:
+    # subtract it so that hand-off + body does not count it twice.
+    T_frame = float(np.median([runner.probe_cs(-1, MUTEX_THREADS, 20000)["ns_per_cs"] for _ in range(3)]))
+    T_frame_sem = float(np.median([runner.probe_sem_cs(None, None, SEM_THREADS, iters=4000)["ns_per_cs"]
+                                   for _ in range(3)]))
+    return {"sms": sms, "L_handoff_ns": float(np.median(hand_ns)), "L_handoff_pairs_ns": hand_ns, "T_cs_ns": T_cs,
+            "T_frame_ns": T_frame, "T_cs_sem_ns": T_cs_sem, "T_frame_sem_ns": T_frame_sem,
             "R_same_red_ops_s": float(np.median(rs)), "R_same_atom_ops_s": float(np.median(ra)), "L_rt_ns": L_rt}
 
 
+def merge_terms(a, b):
+    """The stricter roof of two measurements: lower latencies, higher throughputs."""
+    out = dict(a)
+    for k in ("L_handoff_ns", "L_rt_ns"):
+        out[k] = min(a[k], b[k])
+    for k in ("R_same_red_ops_s", "R_same_atom_ops_s"):
+        out[k] = max(a[k], b[k])
+    out["T_cs_ns"] = {K: min(a["T_cs_ns"][K], b["T_cs_ns"][K]) for K in a["T_cs_ns"]}
+    out["T_cs_sem_ns"] = {n: min(a["T_cs_sem_ns"][n], b["T_cs_sem_ns"][n]) for n in a["T_cs_sem_ns"]}
+    # body = probe - frame, taken from the same measurement, then the smaller of the two
+    out["T_body_ns"] = {K: min(a["T_cs_ns"][K] - a["T_frame_ns"], b["T_cs_ns"][K] - b["T_frame_ns"])
+                        for K in a["T_cs_ns"]}
+    out["T_body_sem_ns"] = {n: min(a["T_cs_sem_ns"][n] - a["T_frame_sem_ns"], b["T_cs_sem_ns"][n] - b["T_frame_sem_ns"])
+                            for n in a["T_cs_sem_ns"]}
+    out["before_after"] = {"before": {k: a[k] for k in ("L_handoff_ns", "T_cs_ns", "T_cs_sem_ns")},
+                           "after": {k: b[k] for k in ("L_handoff_ns", "T_cs_ns", "T_cs_sem_ns")}}
+    return out
+
+
 def mutex_roof_acq_s(terms, K):
-    return min(terms["R_same_atom_ops_s"] / 2.0, 1e9 / (terms["L_handoff_ns"] + terms["T_cs_ns"][K]))
+    """A perfect lock still pays one SM-to-SM hand-off (release, transit, observation) plus the
+    critical-section body per acquisition, and two lock-word operations at the atomic unit."""
+    return min(terms["R_same_atom_ops_s"] / 2.0, 1e9 / (terms["L_handoff_ns"] + max(terms["T_body_ns"][K], 0.0)))
+
+
+def sem_roof_ops_s(terms, n):
+    """Under capacity a wait is one atomic; at capacity n holders each hand off per op."""
+    return min(terms["R_same_atom_ops_s"],
+               n * 1e9 / (terms["L_handoff_ns"] + max(terms["T_body_sem_ns"][n], 0.0)))
 
 
 def barrier_roof_ns(terms, kind, param, B):
-    b_eff = B / param if kind == "cluster" else B
+    """One atomic round trip, one hand-off, and the arrivals through the busiest atomic unit."""
+    if kind == "cluster":
+        b_eff = B / param
+    elif kind in ("sharded", "flag"):
+        b_eff = B / (param if kind == "sharded" else B)
+    else:
+        b_eff = B
     return terms["L_rt_ns"] + terms["L_handoff_ns"] + b_eff / terms["R_same_atom_ops_s"] * 1e9
 
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
 
 class GpuStep:
     """All buffers of one step, allocated once; launch() enqueues the whole step."""
 
     def __init__(self, runner, G, inputs):
         import torch
-        self.torch = torch
         self.mutex = {}
         for kind in G.MUTEX_KINDS:
             for K in CS_SIZES:
@@ -152,7 +215,8 @@ class GpuStep:
         self.sem = {}
         for n in SEM_COUNTS:
             hold, add = inputs.sem_inputs(NBLOCKS, SEM_PAIRS, inputs.SEED_SEM ^ (n << 16) ^ NBLOCKS)
-            self.sem[n] = (runner.SemRun("ticket", NBLOCKS, SEM_THREADS, SEM_PAIRS, n, hold, add,
+            bo = runner.backoff(min_ns=SEM_BACKOFF[0], max_ns=SEM_BACKOFF[1])
+            self.sem[n] = (runner.SemRun("ticket", NBLOCKS, SEM_THREADS, SEM_PAIRS, n, hold, add, bo=bo,
                                          timeout_ns=TIMEOUT_NS), add)
         ev = lambda: torch.cuda.Event(enable_timing=True)
         self.ev = {key: (ev(), ev()) for key in list(self.mutex) + list(self.barrier) + [("sem", n) for n in SEM_COUNTS]}
@@ -198,10 +262,11 @@ class GpuStep:
             want = calc.mutex_final(NBLOCKS, MUTEX_ACQ, K, add)
             if got["status"] or got["total"] != want["total"] or not np.array_equal(got["data"], want["data"]):
                 bad.append(f"mutex {kind} K={K}")
+        want_mix = calc.barrier_sampled(NBLOCKS, BAR_ROUNDS)["mix"]
         for key, br in self.barrier.items():
             st = int(br.status.cpu()[0])
             mix = br.mix.cpu().numpy().view(np.uint32)
-            if st or br.bad.cpu().numpy().any() or not np.array_equal(mix, calc.barrier_sampled(NBLOCKS, BAR_ROUNDS)["mix"]):
+            if st or br.bad.cpu().numpy().any() or not np.array_equal(mix, want_mix):
                 bad.append(f"barrier {key}")
         for n, (sr, add) in self.sem.items():
             got = sr.results()
@@ -211,17 +276,16 @@ class GpuStep:
         return bad
 
 
-def flush_l2(torch, buf):
-    buf.zero_()  # 512 MiB write: larger than the 129 MB L2
-
-
 def e2e_mutex(G, inputs, kind, reps=3):
-    """Default-kind mutex workload through gsync_bench_mutex_host with pinned host buffers."""
+    """Default-kind mutex workload through gsync_bench_mutex_host with pinned host buffers:
+    host->device copies of the inputs and device->host copies of every output are inside the
+    timed call."""
     import torch
     total_acq, total_s = 0, 0.0
     h2d = d2h = 0
+    n = NBLOCKS * MUTEX_ACQ
+    bo = G.gsync_backoff(0, *MUTEX_BACKOFF[kind], 0) if kind in MUTEX_BACKOFF else None
     for K in CS_SIZES:
-        n = NBLOCKS * MUTEX_ACQ
         delay, add = inputs.mutex_inputs(NBLOCKS, MUTEX_ACQ, inputs.mutex_seed(G.MUTEX_KINDS[kind], NBLOCKS, K))
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).pin_memory()
         hd, ha = pin(delay), pin(add)
@@ -234,7 +298,6 @@ def e2e_mutex(G, inputs, kind, reps=3):
                                outs["status"].data_ptr())
         nbytes = G.gsync_bench_mutex_workspace_bytes(w.kind, NBLOCKS, MUTEX_ACQ, K)
         ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-        bo = None
         G.check("gsync_bench_mutex_host", G.gsync_bench_mutex_host(w, bo, ws, nbytes))  # warm-up
         for _ in range(reps):
             t0 = time.perf_counter()
@@ -243,9 +306,92 @@ def e2e_mutex(G, inputs, kind, reps=3):
             total_acq += n
             assert int(outs["status"][0]) == 0 and int(outs["total"][0]) == n
         h2d += 8 * n
-        d2h += 4 * (max(K, 0) + 1 + 2 * n + NBLOCKS + 1)
-    return {"value": total_acq / total_s, "unit": "acq/s", "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "kind": kind}
+        d2h += 4 * (K + 1 + 2 * n + NBLOCKS + 1)
+    k = len(CS_SIZES)
+    return {"value": total_acq / total_s, "unit": "acq/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "kind": kind, "note": f"{k} host-buffer calls (one per CS size) per step; bytes summed over them"}
+
+
+def batched_section(G, calc, inputs, runner, autotune):
+    """Autotunes the batched many-mutex workload, then times its CUDA-graph replay."""
+    import torch
+    keys, adds, _ = inputs.batched_inputs(BATCH_ACQ, BATCH_KEYS, 1.1)
+    want = calc.batched_final(keys, adds, BATCH_KEYS)
+    t0 = time.perf_counter()
+    tuned = autotune.tune(keys, adds, BATCH_KEYS, NBLOCKS, BATCH_GROUPS, BATCH_ROUNDS, BATCH_THREADS)
+    tune_s = time.perf_counter() - t0
+    out = {"workload": f"{BATCH_ACQ} acquisitions over {BATCH_KEYS} mutexes, Zipf(1.1) keys, {NBLOCKS} blocks x "
+                       f"{BATCH_THREADS} threads, {BATCH_GROUPS} barrier groups x {BATCH_ROUNDS} rounds",
+           "class_sizes": tuned["class_sizes"], "tuned_policy": tuned["policy"], "tuned_cluster": tuned["cluster"],
+           "autotune_s": tune_s, "trials": len(tuned["trials"])}
+    results = {}
+    for label, policy, cluster in (("default", autotune.DEFAULT_POLICY, 1), ("tuned", tuned["policy"], tuned["cluster"])):
+        plain = cluster == 1
+        run = autotune.make_run(keys, adds, BATCH_KEYS, NBLOCKS, BATCH_GROUPS, BATCH_ROUNDS, cluster,
+                                tuned["key_class"], BATCH_THREADS, plain_launch=plain)
+        run.set_policy(policy)
+        graph = False
+        if plain:
+            try:
+                run.capture()
+                graph = True
+            except Exception:  # capture refused: time plain launches instead
+                graph = False
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(3):
+            if graph:
+                s.record()
+                run.replay()
+                e.record()
+            else:
+                run.reset()
+                s.record()
+                G.check("gsync_bench_batched", run.launch())
+                e.record()
+            torch.cuda.synchronize()
+            ts.append(s.elapsed_time(e))
+        got = run.results()
+        ok = (got["status"] == 0 and np.array_equal(got["sum"], want["sum"])
+              and np.array_equal(got["count"], want["count"]) and not got["bad"].any())
+        ms = float(np.median(ts))
+        results[label] = {"ms": ms, "acq_per_s": BATCH_ACQ / (ms * 1e-3), "cuda_graph": graph, "cluster": cluster,
+                          "parity": "ok" if ok else "FAILED"}
+    out.update(results)
+    return out
+
+
+SERVE_POOL = 128 << 20           # 512 MB of int32 values (4x the L2)
+SERVE_RATES = (1e3, 1e4, 1e5, 1e6)
+SERVE_SECONDS, SERVE_MAX_REQ = 0.5, 100_000
+
+
+def serve_section(calc, inputs, runner):
+    """Persistent serving loop vs one launch per request at swept Poisson arrival rates."""
+    import torch
+    off_all, len_all, pool = inputs.serve_inputs(SERVE_MAX_REQ, SERVE_POOL)
+    dpool = torch.from_numpy(pool).cuda()
+    rng = np.random.default_rng(0)
+    out = {"workload": f"int32 segmented sums, length log-uniform 256..1048576, pool {SERVE_POOL} values "
+                       f"({SERVE_POOL * 4 >> 20} MiB), Poisson arrivals, open loop (latency from the scheduled arrival "
+                       f"to the host seeing the completion flag)", "rates": {}}
+    for rate in SERVE_RATES:
+        nreq = int(min(SERVE_MAX_REQ, max(500, rate * SERVE_SECONDS)))
+        off, ln = off_all[:nreq], len_all[:nreq]
+        sched = inputs.poisson_arrivals(nreq, rate)
+        sample = rng.choice(nreq, size=min(nreq, 300), replace=False)
+        want = calc.serve_final(off[sample], ln[sample], pool)
+        row = {"nreq": nreq}
+        for arm in ("persistent", "per_request_launch"):
+            sr = runner.ServeRun(off, ln, sched, dpool, nslots=64, nblocks=304, admitters=8)
+            r = sr.run() if arm == "persistent" else sr.baseline(nstreams=8)
+            lat = r["latency_ns"] / 1e3
+            span = (sched[-1] + r["latency_ns"][-1]) / 1e9
+            row[arm] = {"rc": r["rc"], "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+                        "mean_us": float(lat.mean()), "achieved_req_s": nreq / max(span, 1e-9),
+                        "parity_sample": "ok" if np.array_equal(r["res"][sample], want) else "FAILED"}
+        out["rates"][f"{rate:g}"] = row
+    return out
 
 
 def cpu_baseline(inputs, kind):
@@ -267,7 +413,7 @@ def cpu_baseline(inputs, kind):
 def run_gpu(args):
     import torch
     from oracle import calc
-    from paper_1110_4623_gb300 import gsync as G, inputs, runner
+    from paper_1110_4623_gb300 import autotune, gsync as G, inputs, runner
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -275,7 +421,7 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     G.lib()
-    terms = measure_roofline_terms(runner, G)
+    terms_before = measure_roofline_terms(runner, inputs)
     step = GpuStep(runner, G, inputs)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
@@ -293,7 +439,7 @@ def run_gpu(args):
     clocks.start()
     wall0 = time.perf_counter()
     for _ in range(args.steps):
-        flush_l2(torch, flush)
+        flush.zero_()  # 512 MiB write: evicts the 129 MB L2 between steps (outside the step's events)
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record()
         step.launch()
@@ -306,6 +452,7 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.barrier()
     bad = step.verify(calc)
+    terms = merge_terms(terms_before, measure_roofline_terms(runner, inputs))
 
     step_ms = float(np.mean(per_step))
     if world > 1:
@@ -317,8 +464,9 @@ def run_gpu(args):
     mutex = {}
     for (kind, K) in step.mutex:
         ms = med[(kind, K)]
-        mutex.setdefault(kind, {})[K] = {"ms": ms, "acq_per_s": NBLOCKS * MUTEX_ACQ / (ms * 1e-3),
-                                         "roof_acq_per_s": mutex_roof_acq_s(terms, K)}
+        acq_s = NBLOCKS * MUTEX_ACQ / (ms * 1e-3)
+        roof = mutex_roof_acq_s(terms, K)
+        mutex.setdefault(kind, {})[str(K)] = {"ms": ms, "acq_per_s": acq_s, "roof_acq_per_s": roof, "frac": acq_s / roof}
     def_ms = sum(med[(DEFAULT_MUTEX, K)] for K in CS_SIZES)
     def_acq = NBLOCKS * MUTEX_ACQ * len(CS_SIZES)
     value = def_acq / (def_ms * 1e-3) * world
@@ -328,14 +476,14 @@ def run_gpu(args):
     for (k, p) in step.barrier:
         ns = med[(k, p)] * 1e6 / BAR_ROUNDS
         roof = barrier_roof_ns(terms, k, max(p, 1), NBLOCKS)
-        barrier[f"{k}{p if k in ('tree', 'cluster') else ('_broadcast' if p else '')}"] = {
-            "ns_per_crossing": ns, "roof_ns": roof, "frac": roof / ns}
-    dk, dp = DEFAULT_BARRIER
-    bkey = f"{dk}{'_broadcast' if dp else ''}"
+        barrier[barrier_name(k, p)] = {"ns_per_crossing": ns, "roof_ns": roof, "frac": roof / ns}
+    bkey = barrier_name(*DEFAULT_BARRIER)
     sem = {}
     for n in SEM_COUNTS:
         ms = med[("sem", n)]
-        sem[n] = {"ops_per_s": NBLOCKS * SEM_PAIRS / (ms * 1e-3)}
+        ops = NBLOCKS * SEM_PAIRS / (ms * 1e-3)
+        roof = sem_roof_ops_s(terms, n)
+        sem[str(n)] = {"ops_per_s": ops, "roof_ops_per_s": roof, "frac": ops / roof}
 
     out = {
         "metric": METRIC, "value": value, "unit": "acq/s", "n_gpus": world, "steps": args.steps,
@@ -344,15 +492,20 @@ def run_gpu(args):
         "config": {"workload": f"mutex contention, {NBLOCKS} blocks x {MUTEX_THREADS} threads, {MUTEX_ACQ} "
                                f"acquisitions/block, CS {list(CS_SIZES)} int32 words, delays U{{0..2000}} cycles; "
                                f"+ barriers ({BAR_ROUNDS} rounds) and semaphores ({SEM_PAIRS} pairs) at {NBLOCKS} blocks",
-                   "default_mutex": DEFAULT_MUTEX, "default_barrier": bkey, "nblocks": NBLOCKS,
+                   "default_mutex": f"{DEFAULT_MUTEX} (backoff {MUTEX_BACKOFF.get(DEFAULT_MUTEX)} ns)",
+                   "default_barrier": bkey, "nblocks": NBLOCKS,
                    "l2": "flushed (512 MiB write) before every timed step", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "l2_handoff_latency", "achieved": value / world, "peak": peak, "unit": "acq/s",
-                     "frac": (value / world) / peak, "traffic": None,
-                     "peak_source": "measured live: 1e9 / (L_handoff + T_cs(K)) per CS size, from the ping-pong and "
-                                    "critical-section probe kernels of this run (min with R_same/2)"},
-        "barrier": {"default": bkey, "ns_per_crossing": barrier[bkey]["ns_per_crossing"], "kinds": barrier},
-        "mutex": {k: {str(K): v for K, v in d.items()} for k, d in mutex.items()},
-        "semaphore": {"kind": "ticket", "ops_per_s": {str(n): v["ops_per_s"] for n, v in sem.items()}},
+                     "frac": (value / world) / peak, "traffic": 2.3e6,
+                     "traffic_note": "DRAM bytes per launch of the dominant kernel (queue/ticket mutex workload), "
+                                     "scaled from the ncu capture in profiles/ (input arrays only)",
+                     "peak_source": "measured live: sum over CS sizes of 1e9 / (L_handoff + T_cs(K)) from the "
+                                    "ping-pong and critical-section probe kernels of this run (min with R_same/2); "
+                                    "MEASURED_PEAKS.json's HBM and bf16 peaks do not bound this path"},
+        "barrier": {"default": bkey, "ns_per_crossing": barrier[bkey]["ns_per_crossing"],
+                    "frac": barrier[bkey]["frac"], "kinds": barrier},
+        "mutex": mutex,
+        "semaphore": {"kind": "ticket", "backoff_ns": list(SEM_BACKOFF), "n": sem},
         "roofline_terms": terms,
         "clocks": clk,
         "gpu_launches": step.launches * args.steps,
@@ -362,6 +515,13 @@ def run_gpu(args):
     if rank == 0:
         out["e2e"] = e2e_mutex(G, inputs, DEFAULT_MUTEX)
         out["e2e"]["value"] *= world
+        if not args.no_batched:
+            out["batched"] = batched_section(G, calc, inputs, runner, autotune)
+            out["serving"] = serve_section(calc, inputs, runner)
+            r5 = out["serving"]["rates"].get("100000")
+            if r5:
+                out["p99_latency_us"] = {"persistent_at_1e5_req_s": r5["persistent"]["p99_us"],
+                                         "per_request_launch_at_1e5_req_s": r5["per_request_launch"]["p99_us"]}
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(inputs, DEFAULT_MUTEX)
         print(json.dumps(out, default=float))
@@ -374,7 +534,7 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_1110_4623_gb300 import inputs
-    vals, secs_total = [], 0.0
+    vals = []
     base = None
     t_all = time.perf_counter()
     for _ in range(args.warmup):

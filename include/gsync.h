@@ -62,7 +62,8 @@ typedef enum gsync_barrier_kind {
   GSYNC_BAR_ATOMIC = 0,  /* two-stage atomic counter + release epoch */
   GSYNC_BAR_FLAG = 1,    /* decentralized flag barrier of Xiao and Feng (XF) */
   GSYNC_BAR_TREE = 2,    /* combining tree of atomic counters, fan-in = param */
-  GSYNC_BAR_CLUSTER = 3  /* hardware cluster barrier, then one leader per cluster on a counter */
+  GSYNC_BAR_CLUSTER = 3, /* hardware cluster barrier, then one leader per cluster on a counter */
+  GSYNC_BAR_SHARDED = 4  /* arrivals spread over param counters, gathered by one warp (XF-style release) */
 } gsync_barrier_kind;
 
 /* Semaphore kinds (Section 5, "Semaphore"; Appendix, spin-lock and sleeping semaphores). */
@@ -96,7 +97,9 @@ int gsync_mutex_init(void* state, size_t bytes, int kind, int max_waiters,
                      const gsync_backoff* backoff, uint64_t timeout_ns, void* stream);
 
 /* Bytes of a barrier for `nblocks` blocks.  param: fan-in (TREE, >= 2), cluster size
- * (CLUSTER, 1..8, divides nblocks), release mode (FLAG: 0 one flag per block, 1 one word). */
+ * (CLUSTER, 1..8, divides nblocks), release mode (FLAG: 0 one flag per block, 1 one word;
+ * FLAG takes at most 8192 blocks), number of arrival counters (SHARDED, 1..32).  FLAG and
+ * SHARDED need blockDim.x >= 32 (warp 0 of block 0 gathers the arrivals). */
 size_t gsync_barrier_bytes(int kind, int nblocks, int param);
 int gsync_barrier_init(void* state, size_t bytes, int kind, int nblocks, int param,
                        uint64_t timeout_ns, void* stream);
@@ -151,6 +154,14 @@ typedef struct gsync_barrier_work {
   uint32_t* status;
 } gsync_barrier_work;
 int gsync_bench_barrier(void* state, const gsync_barrier_work* w, void* stream);
+
+/* Phase trace of the sampled barrier workload (w->full must be 0): as gsync_bench_barrier,
+ * and block b also writes its %globaltimer just before and just after its round-r barrier
+ * into trace[2 * (b * rounds + r)] and trace[2 * (b * rounds + r) + 1] (device,
+ * 2 x nblocks x rounds u64).  A diagnostic: it shows how long the last arrival takes to
+ * release the first and the last waiter. */
+int gsync_probe_barrier_trace(void* state, const gsync_barrier_work* w, uint64_t* trace,
+                              void* stream);
 
 /* The barrier workload for callers that cannot allocate device memory.  The paper has no
  * counterpart; this is a library convenience.  Some callers cannot call cudaMalloc: code
@@ -221,6 +232,110 @@ typedef struct gsync_sem_work {
 } gsync_sem_work;
 int gsync_bench_sem(void* state, const gsync_sem_work* w, void* stream);
 
+/* Batched many-mutex workload (Section 5's mutex applied to many independent instances;
+ * the paper measures one instance per kernel, and names autotuning of the backoff constants
+ * as future work, Section 7).  One co-resident launch of nblocks blocks; acquisition i
+ * (i < nacq) belongs to block i mod nblocks and runs, in order, on that block's thread 0:
+ * lock mutex keys[i] with the policy of its contention class, sum[key] += adds[i] and
+ * count[key] += 1 with plain loads and stores, unlock.  Blocks of barrier group g (blocks
+ * group_start[g] .. + group_size[g] - 1; group_of_block[b] = g, or -1) also cross `rounds`
+ * group barriers spread evenly over their acquisitions, with the sampled slot check of the
+ * barrier workload (partner (j + r + 1) mod size inside the group); mix[b] and bad[b] as
+ * there.
+ *  - mutex_state (device, 128-byte aligned): nkeys x 384 bytes; zero it before the first
+ *    launch and whenever a key's policy kind changes (the objects are left consistent by
+ *    every completed launch otherwise).
+ *  - key_class (device, nkeys bytes): class of each key, < nclasses.
+ *  - policy (device, nclasses x 4 x u32): {kind (CAS_SPIN, CAS_BACKOFF or TICKET; others act
+ *    as TICKET), min_ns, max_ns, 0}: backoff of the CAS kind, or sleep per waiter ahead of
+ *    the ticket kind; min_ns = 0 spins without sleeping.
+ *  - keys (device, nacq x i32), adds (device, nacq x i64); sum (device, nkeys x i64) and
+ *    count (device, nkeys x u32) zeroed by the caller.
+ *  - group_state (device, 128-byte aligned): ngroups x 384 bytes, zeroed before the first
+ *    launch; slots (device, 2 x nblocks u32) scratch; mix, bad (device, nblocks u32);
+ *    status (device u32, zeroed).
+ *  - cluster > 1 launches clusters of that size and uses the cluster-hierarchical barrier
+ *    for the groups: every group must start at and span a multiple of `cluster` blocks
+ *    (checked on the device; a violation sets GSYNC_STATUS_CONFIG and skips the barriers).
+ *  - plain_launch = 1 uses an ordinary launch after the co-residency check instead of a
+ *    cooperative one (for stream capture into a CUDA graph); cluster must then be 1. */
+typedef struct gsync_batched_work {
+  int32_t nkeys, nacq, nblocks, block_threads, ngroups, rounds, cluster, nclasses;
+  int32_t plain_launch, reserved;
+  uint64_t timeout_ns;
+  void* mutex_state;
+  const uint8_t* key_class;
+  const uint32_t* policy;
+  const int32_t* keys;
+  const int64_t* adds;
+  int64_t* sum;
+  uint32_t* count;
+  const int32_t* group_start;
+  const int32_t* group_size;
+  const int32_t* group_of_block;
+  void* group_state;
+  uint32_t* slots;
+  uint32_t* mix;
+  uint32_t* bad;
+  uint32_t* status;
+} gsync_batched_work;
+int gsync_bench_batched(const gsync_batched_work* w, void* stream);
+
+/* Persistent serving loop with continuous batching (the paper motivates its primitives
+ * with task queues, Section 1, and wishes for hardware enqueue/dequeue, Section 7).  Each
+ * request q is an int32 segmented sum res[q] = sum of pool[offset[q] .. + length[q]) in
+ * int64.  gsync_serve_run launches one co-resident kernel of nblocks x 256 threads, then
+ * (host threads inside the call) publishes request q into the ring at time sched_ns[q]
+ * after the start and records latency_ns[q] = the host time its completion flag was first
+ * seen minus sched_ns[q] (open loop: latency counts from the scheduled arrival).
+ *  - On the device, `admitters` blocks take request indices under the ring's ticket lock,
+ *    wait on the admission semaphore (n = nslots in-flight requests), claim a free slot and
+ *    publish the request; every other block claims chunks of chunk_elems values of any
+ *    active request; the block that finishes a request's last chunk writes res[q] and
+ *    done[q] = 1 into pinned host memory, frees the slot and posts the semaphore.
+ *  - ring (ring_slots descriptors, a power of two), ctrl (64 words: ctrl[0] tail, ctrl[32]
+ *    shutdown), res (nreq x i64) and done (nreq x u32) are caller-owned pinned host memory
+ *    (cudaHostAlloc or registered); pool is device memory; offset, length, sched_ns and
+ *    latency_ns are ordinary host arrays.  workspace (device, 256-byte aligned) holds
+ *    gsync_serve_workspace_bytes(nslots) bytes.
+ *  - Requires 1 <= length[q] and at most 65535 chunks per request, nslots <= 64.
+ *  - Returns GSYNC_ETIMEDOUT if not every request completed within drain_timeout_s after the
+ *    last scheduled arrival, or if a device wait timed out (stats[3] = device status).
+ *    Synchronizes `stream` before returning.
+ * gsync_serve_baseline runs the same requests as one kernel launch each (block j sums chunk
+ * j; the last block writes res and done), issued at the scheduled times round-robin over
+ * `nstreams` caller streams, completions observed the same way.  workspace: device, 16-byte
+ * aligned, gsync_serve_baseline_workspace_bytes(nreq) bytes. */
+typedef struct gsync_serve_req {
+  int64_t off;
+  int64_t len;
+  uint32_t id;
+  uint32_t pad[3];
+} gsync_serve_req;
+typedef struct gsync_serve_cfg {
+  int32_t nreq, nslots, nblocks, admitters, chunk_elems, ring_slots;
+  int32_t start_delay_us, drain_timeout_s;
+  uint64_t timeout_ns;
+} gsync_serve_cfg;
+typedef struct gsync_serve_buffers {
+  const int32_t* pool;
+  const int64_t* offset;
+  const int64_t* length;
+  const int64_t* sched_ns;
+  gsync_serve_req* ring;
+  uint32_t* ctrl;
+  int64_t* res;
+  uint32_t* done;
+  int64_t* latency_ns;
+  uint32_t stats[4]; /* out: requests admitted, chunks processed, requests completed, device status */
+} gsync_serve_buffers;
+size_t gsync_serve_workspace_bytes(int nslots);
+int gsync_serve_run(const gsync_serve_cfg* cfg, gsync_serve_buffers* buf, void* workspace,
+                    size_t workspace_bytes, void* stream);
+size_t gsync_serve_baseline_workspace_bytes(int nreq);
+int gsync_serve_baseline(const gsync_serve_cfg* cfg, gsync_serve_buffers* buf, void* workspace,
+                         size_t workspace_bytes, void* const* streams, int nstreams);
+
 /* ------------------------------------------------------------------------------------ */
 /* Memory-system probes (Section 3, "Benchmarks"; Section 4 machine abstraction).        */
 /* ------------------------------------------------------------------------------------ */
@@ -268,12 +383,58 @@ int gsync_probe_nanosleep(const uint32_t* req_ns, int n, int iters, uint64_t* ou
                           void* stream);
 
 /* Critical-section probe (T_cs): one block runs the mutex workload's critical-section body
- * (with the release store that ends it) `iters` times with no lock and no delay, timed with
- * CUDA events; out[0] = elapsed ns.  Synchronizes `stream`.  scratch (device, 256-byte
- * aligned) needs gsync_probe_cs_scratch_bytes(cs_words, iters) bytes. */
+ * `iters` times with no lock and no delay, framed like a hand-off (an acquire load and a
+ * barrier before it, a barrier and a release store after it), timed with CUDA events;
+ * out[0] (host) = elapsed ns.  cs_words = -1 runs the frame alone (no body), so that
+ * T_cs(K) - T_frame is the body's own cost.  Synchronizes `stream`.  scratch (device,
+ * 256-byte aligned) needs gsync_probe_cs_scratch_bytes(cs_words, iters) bytes. */
 int gsync_probe_cs(int cs_words, int block_threads, int iters, void* scratch, uint64_t* out,
                    void* stream);
 size_t gsync_probe_cs_scratch_bytes(int cs_words, int iters);
+
+/* Semaphore critical-section probe (the semaphore roofline's T_cs): one block runs the
+ * semaphore workload's critical section -- occupancy bookkeeping, hold[p] SM cycles, the
+ * tally -- framed like a hand-off (an acquire load and a barrier before it, a barrier and a
+ * release fence and store after it) for p < iters, with no semaphore.  hold, addend
+ * (device) hold >= iters entries (hold may be NULL: no hold; both NULL: the frame alone,
+ * with an empty critical section).  scratch (device, 256-byte aligned, 1024 bytes).
+ * out[0] (host) = elapsed ns.  Synchronizes `stream`. */
+int gsync_probe_sem_cs(int block_threads, int iters, const uint32_t* hold, const uint32_t* addend,
+                       void* scratch, uint64_t* out, void* stream);
+
+/* Hand-off probe: the ping-pong of gsync_probe_pingpong with a choice of how a side
+ * releases (signal) and how the other side observes (wait); modes below.  Same buffers and
+ * outputs as gsync_probe_pingpong. */
+enum {
+  GSYNC_SIGNAL_ST_RELEASE = 0,       /* st.release.gpu */
+  GSYNC_SIGNAL_FENCE_ST_RELAXED = 1, /* fence.acq_rel.gpu; st.relaxed.gpu */
+  GSYNC_SIGNAL_ST_RELAXED = 2,       /* st.relaxed.gpu (no ordering: a latency floor only) */
+  GSYNC_SIGNAL_RED_RELEASE = 3,      /* red.release.gpu.add 1 */
+  GSYNC_SIGNAL_EXCH_RELEASE = 4      /* atom.release.gpu.exch */
+};
+enum {
+  GSYNC_WAIT_LD_ACQUIRE = 0,              /* poll with ld.acquire.gpu */
+  GSYNC_WAIT_LD_RELAXED_FENCE = 1,        /* poll with ld.relaxed.gpu, then fence.acq_rel.gpu */
+  GSYNC_WAIT_LD_RELAXED = 2,              /* poll with ld.relaxed.gpu (no ordering: floor only) */
+  GSYNC_WAIT_LD_RELAXED_THEN_ACQUIRE = 3, /* poll relaxed, then one ld.acquire.gpu */
+  GSYNC_WAIT_LD_VOLATILE_FENCE = 4,       /* poll with ld.volatile, then fence.acq_rel.gpu */
+  GSYNC_WAIT_LD_RELAXED_X2 = 5            /* two relaxed polls in flight ~40 ns apart, then fence */
+};
+int gsync_probe_handoff(int signal_mode, int wait_mode, int sm_a, int sm_b, int iters,
+                        void* scratch, uint64_t* out, void* stream);
+
+/* Cluster probe: one cluster of `cluster` blocks (2..8; 1..8 for op 0) x 128 threads.
+ * op 0: every thread runs `iters` hardware cluster barriers (out[0] / iters per barrier);
+ * op 1: ranks 0 and cluster-1 ping-pong a flag in each other's shared memory with
+ *       st.release.cluster / ld.acquire.cluster; op 2: the same with remote mbarrier arrives
+ *       and mbarrier.try_wait (hand-off = out[0] / (2 * iters)).  out (device, 4 x u64):
+ *       out[0] elapsed ns, out[3] status (0 ok, 1 timed out after 1 s). */
+int gsync_probe_cluster(int op, int cluster, int iters, uint64_t* out, void* stream);
+
+/* Fence probe: one thread runs `iters` gpu-scope fences; op 0 alone, op 1 after a relaxed
+ * store, op 2 after four plain stores, op 3 cluster-scope fences.  out (device, 2 x u64):
+ * elapsed ns and SM cycles.  scratch (device, 256-byte aligned) needs 1024 bytes. */
+int gsync_probe_fence(int op, int iters, void* scratch, uint64_t* out, void* stream);
 
 #ifdef __cplusplus
 }

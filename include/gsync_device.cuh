@@ -47,6 +47,25 @@ __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
   asm volatile("ld.volatile.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ uint4 ld_relaxed_v4(const uint32_t* p) {
+  uint4 v;
+  asm volatile("ld.relaxed.gpu.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ uint4 ld_acquire_v4(const uint32_t* p) {
+  uint4 v;
+  asm volatile("ld.acquire.gpu.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_v4(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.v4.u32 [%0], {%1, %1, %1, %1};" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -129,9 +148,10 @@ __device__ __forceinline__ uint32_t cluster_nctarank() {
   asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
   return r;
 }
-// Hardware barrier over every thread of every block of the cluster.
+// Hardware barrier over every thread of every block of the cluster.  The non-.aligned
+// forms let threads of a warp arrive from divergent paths.
 __device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 }  // namespace ptx
 
@@ -321,9 +341,15 @@ __device__ __forceinline__ int sem_wait_thread(const SemRef& s) {
     const uint32_t old = ptx::atom_add_acquire(s.word(1), 1u);
     if ((int32_t)old < (int32_t)s.n) return GSYNC_OK;
     const uint32_t wi = ptx::atom_add_relaxed(s.word(2), 1u);
-    while (!after(ptx::ld_acquire(s.word(3)), wi)) {
+    uint32_t turn;
+    while (!after(turn = ptx::ld_acquire(s.word(3)), wi)) {
       if (int rc = w.tick(s.timeout_ns, s.abort_word())) return rc;
-      if (s.bo.min_ns) __nanosleep(s.bo.min_ns);
+      // Sleep in proportion to the waiters ahead (wi - turn of them), capped at max_ns.
+      const uint32_t ahead = wi - turn;
+      if (s.bo.min_ns && ahead < 0x80000000u) {
+        const uint32_t ns = ahead * s.bo.min_ns;
+        __nanosleep(ns < s.bo.max_ns ? ns : s.bo.max_ns);
+      }
     }
     return GSYNC_OK;
   } else {
@@ -347,8 +373,10 @@ __device__ __forceinline__ int sem_wait_thread(const SemRef& s) {
 template <int KIND>
 __device__ __forceinline__ int sem_post_thread(const SemRef& s) {
   if (KIND == GSYNC_SEM_TICKET) {
-    const uint32_t old = ptx::atom_add_release(s.word(1), 0xFFFFFFFFu);
-    if ((int32_t)old > (int32_t)s.n) ptx::red_add_release(s.word(3), 1u);
+    // One release fence covers both writes: each strong write after it is a release.
+    ptx::fence_acq_rel();
+    const uint32_t old = ptx::atom_add_relaxed(s.word(1), 0xFFFFFFFFu);
+    if ((int32_t)old > (int32_t)s.n) ptx::red_add_relaxed(s.word(3), 1u);
     return GSYNC_OK;
   } else {
     Waiter w;
@@ -387,9 +415,17 @@ __device__ __forceinline__ int sem_post(const SemRef& s) {
 // ---------------------------------------------------------------------------------------
 // ATOMIC : line 1 arrival counter, line 2 release epoch.
 // FLAG   : lines 1.. arrival flags (one word per block, packed), then release flags (one
-//          word per block, packed; mode 1: a single release word on its own line).
+//          word per block, packed; mode 1: a single release word on its own line).  At most
+//          8192 blocks, and blockDim.x >= 32 (warp 0 of block 0 gathers the flags).
 // TREE   : line 1 release epoch, lines 2.. one counter line per tree node (fan-in = param).
-// CLUSTER: like ATOMIC over the cluster leaders; param = cluster size.
+// SHARDED: lines 1..S: S = param arrival counters (block b counts into counter b mod S with a
+//          fire-and-forget red.release; counters only grow, so after crossing e counter s
+//          holds e x (blocks of shard s)); then release flags (one word per block, packed).
+//          Warp 0 of block 0 watches the S counters and writes the release flags.
+// CLUSTER: like ATOMIC over the cluster leaders; param = cluster size.  Its first stage is
+//          the hardware cluster barrier, which cannot time out: every block of a cluster must
+//          make the same number of barrier_wait calls, also after one returned an error (the
+//          object's abort word makes those calls return quickly).
 // Epochs increase by one per crossing and are compared for equality, so no phase resets.
 struct BarrierRef {
   uint32_t* s;
@@ -400,7 +436,9 @@ struct BarrierRef {
   __device__ __forceinline__ uint32_t* abort_word() const { return s + kHdrAbort; }
   __device__ __forceinline__ uint32_t flag_lines() const { return (n + kLineWords - 1) / kLineWords; }
   __device__ __forceinline__ uint32_t* arrive_flags() const { return line(1); }
-  __device__ __forceinline__ uint32_t* release_flags() const { return line(1 + flag_lines()); }
+  __device__ __forceinline__ uint32_t* release_flags() const {
+    return kind == GSYNC_BAR_SHARDED ? line(1 + param) : line(1 + flag_lines());
+  }
 };
 
 // Reads the header and the current epoch.  All blocks must attach between the same two
@@ -413,7 +451,7 @@ __device__ __forceinline__ BarrierRef barrier_attach(void* state) {
   b.param = b.s[kHdrParam];
   b.mode = b.s[kHdrMode];
   b.timeout_ns = header_timeout(b.s);
-  if (b.kind == GSYNC_BAR_FLAG) {
+  if (b.kind == GSYNC_BAR_FLAG || b.kind == GSYNC_BAR_SHARDED) {
     // A block's own release flag always holds the epoch of the last crossing.
     b.epoch = b.mode ? ptx::ld_relaxed(b.release_flags()) : ptx::ld_relaxed(b.release_flags() + blockIdx.x);
   } else if (b.kind == GSYNC_BAR_TREE) {
@@ -491,29 +529,82 @@ __device__ __forceinline__ int barrier_wait(BarrierRef& b) {
       }
       s_rc = rc;
     }
-  } else {  // GSYNC_BAR_FLAG: decentralized XF barrier, block 0 is the master block
-    const uint32_t tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    const uint32_t nthr = blockDim.x * blockDim.y * blockDim.z;
+  } else if (KIND == GSYNC_BAR_SHARDED) {
+    const uint32_t S = b.param;
     if (blockIdx.x == 0) {
-      __shared__ int s_bad;
-      if (master) s_bad = GSYNC_OK;
-      __syncthreads();
+      if (threadIdx.x < 32 && threadIdx.y == 0 && threadIdx.z == 0) {
+        // Lane s < S watches counter s until it reaches e1 x (blocks of shard s, master
+        // excluded for shard 0), in wrapping uint32 arithmetic.
+        const uint32_t lane = threadIdx.x;
+        int rc = GSYNC_OK;
+        if (lane < S) {
+          const uint32_t members = (b.n - lane + S - 1u) / S - (lane == 0u ? 1u : 0u);
+          const uint32_t target = e1 * members;
+          Waiter w;
+          while (ptx::ld_relaxed(b.line(1 + lane)) != target)
+            if ((rc = w.tick(b.timeout_ns, b.abort_word())) != GSYNC_OK) break;
+        }
+        ptx::fence_acq_rel();  // acquire: the arrivals this lane counted
+        const int worst = __reduce_max_sync(0xFFFFFFFFu, rc);
+        __syncwarp();
+        if (worst == GSYNC_OK) {
+          ptx::fence_acq_rel();  // release: every lane's acquisitions precede the release flags
+          const uint32_t nvec = (b.n + 3u) >> 2;
+          for (uint32_t v = lane; v < nvec; v += 32u) ptx::st_relaxed_v4(b.release_flags() + 4u * v, e1);
+        }
+        if (lane == 0) s_rc = worst;
+      }
+    } else if (master) {
+      ptx::red_add_release(b.line(1 + blockIdx.x % S), 1u);
       Waiter w;
       int rc = GSYNC_OK;
-      for (uint32_t j = 1 + tid; j < b.n && rc == GSYNC_OK; j += nthr)
-        while (ptx::ld_acquire(b.arrive_flags() + j) != e1)
-          if ((rc = w.tick(b.timeout_ns, b.abort_word())) != GSYNC_OK) break;
-      if (rc != GSYNC_OK) s_bad = rc;
-      __syncthreads();
-      if (s_bad == GSYNC_OK) {
-        ptx::fence_acq_rel();
-        if (b.mode) {
-          if (master) ptx::st_relaxed(b.release_flags(), e1);
-        } else {
-          for (uint32_t j = tid; j < b.n; j += nthr) ptx::st_relaxed(b.release_flags() + j, e1);
+      while (ptx::ld_acquire(b.release_flags() + blockIdx.x) != e1)
+        if ((rc = w.tick(b.timeout_ns, b.abort_word())) != GSYNC_OK) break;
+      s_rc = rc;
+    }
+  } else {  // GSYNC_BAR_FLAG: decentralized XF barrier, block 0 is the master block
+    if (blockIdx.x == 0) {
+      // Warp 0 of the master block gathers every arrival flag with 16-byte relaxed loads, all
+      // of a lane's pending vectors in flight at once (lane l owns vectors l, l+32, ...; at most
+      // 64 per lane, so n <= 8192).  The flag arrays span whole lines, so a vector never leaves
+      // them; word 0 (the master's own flag) and words past n are ignored.  Relaxed loads
+      // pipeline (acquire loads would complete one at a time); each lane then fences to
+      // acquire what it saw, and after __syncwarp fences again so that its release-flag
+      // stores also release what the other lanes saw.
+      if (threadIdx.x < 32 && threadIdx.y == 0 && threadIdx.z == 0) {
+        const uint32_t lane = threadIdx.x;
+        const uint32_t nvec = (b.n + 3u) >> 2;
+        const uint32_t kmax = lane < nvec ? min(64u, (nvec - lane + 31u) / 32u) : 0u;
+        uint64_t pending = kmax == 64u ? ~0ull : ((1ull << kmax) - 1ull);
+        Waiter w;
+        int rc = GSYNC_OK;
+        while (pending) {
+          uint64_t still = 0;
+          for (uint32_t k = 0; k < kmax; ++k) {
+            if (!((pending >> k) & 1ull)) continue;
+            const uint32_t v = lane + 32u * k;
+            const uint4 x = ptx::ld_relaxed_v4(b.arrive_flags() + 4u * v);
+            const uint32_t base = 4u * v;
+            const bool ok = (base == 0u || base >= b.n || x.x == e1) && (base + 1u >= b.n || x.y == e1) &&
+                            (base + 2u >= b.n || x.z == e1) && (base + 3u >= b.n || x.w == e1);
+            if (!ok) still |= 1ull << k;
+          }
+          pending = still;
+          if (pending && (rc = w.tick(b.timeout_ns, b.abort_word())) != GSYNC_OK) break;
         }
+        ptx::fence_acq_rel();  // acquire: what this lane's relaxed loads observed
+        const int worst = __reduce_max_sync(0xFFFFFFFFu, rc);
+        __syncwarp();
+        if (worst == GSYNC_OK) {
+          ptx::fence_acq_rel();  // release: every lane's acquisitions precede the release flags
+          if (b.mode) {
+            if (lane == 0) ptx::st_relaxed(b.release_flags(), e1);
+          } else {
+            for (uint32_t v = lane; v < nvec; v += 32u) ptx::st_relaxed_v4(b.release_flags() + 4u * v, e1);
+          }
+        }
+        if (lane == 0) s_rc = worst;
       }
-      if (master) s_rc = s_bad;
     } else if (master) {
       ptx::st_release(b.arrive_flags() + blockIdx.x, e1);
       uint32_t* rel = b.mode ? b.release_flags() : b.release_flags() + blockIdx.x;

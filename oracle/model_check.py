@@ -24,6 +24,7 @@ The algorithms follow Section 5 ("Design") and the pseudocode of the Appendix:
   AtomicBarrier two-stage atomic-counter barrier (Section 5, "Barrier")
   FlagBarrier   decentralized XF flag barrier (Section 5, "Barrier")
   TreeBarrier   combining-tree barrier (Section 2, hierarchical barriers)
+  ShardedBarrier  arrivals counted on several counters, gathered by the master block
   ClusterBarrier  barrier inside groups of c blocks, then one leader per group globally
 Mutation variants with a planted mistake (`broken=...`) exist so that tests can show the
 checker catches each kind of error.
@@ -480,6 +481,61 @@ class TreeBarrier:
                 k += 1
                 return ((0 if k < ops else DONE), k, inc(e), p // self.fan), sh, ("pass",)
             return loc, sh, None
+        raise AssertionError(pc)
+
+
+class ShardedBarrier:
+    """Sharded-counter barrier: block p counts itself into counter p mod S (fetch-and-add,
+    counters never reset); the master block 0 checks that counter s holds
+    (epoch + 1) x (blocks of shard s, master excluded), one counter per step, then writes
+    each block's release flag.  broken="early": the master waits for one arrival fewer on
+    shard 0; broken="counts_master": it also expects its own (never made) arrival."""
+    kind = "barrier"
+
+    def __init__(self, shards=2, base=0, broken=None):
+        self.S, self.base, self.broken = shards, base & M32, broken
+
+    def init(self, nproc, ops):
+        # Consistent start at epoch `base`: counter s holds base x members (mod 2^32).
+        assert self.S <= nproc
+        true_members = [(nproc - s + self.S - 1) // self.S - (1 if s == 0 else 0) for s in range(self.S)]
+        counters = tuple((self.base * m) & M32 for m in true_members)
+        return counters + tuple([self.base] * nproc), tuple((0, 0, self.base, 0) for _ in range(nproc))
+
+    def members(self, s, nproc):
+        m = (nproc - s + self.S - 1) // self.S - (1 if s == 0 else 0)
+        if s == 0 and self.broken == "early":
+            m -= 1
+        if s == 0 and self.broken == "counts_master":
+            m += 1
+        return m
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, e, j = loc
+        ne = inc(e)
+        S = self.S
+        if p != 0:
+            if pc == 0:
+                return (1, k, e, j), _set(sh, p % S, inc(sh[p % S])), ("arrive",)
+            if pc == 1:
+                if sh[S + p] == ne:
+                    k += 1
+                    return ((0 if k < ops else DONE), k, ne, j), sh, ("pass",)
+                return loc, sh, None
+            raise AssertionError(pc)
+        if pc == 0:
+            return (1, k, e, 0), sh, ("arrive",)
+        if pc == 1:  # check counter j
+            if j >= S:
+                return (2, k, e, 0), sh, None
+            if sh[j] == (ne * self.members(j, nproc)) & M32:
+                return (1, k, e, j + 1), sh, None
+            return loc, sh, None
+        if pc == 2:  # write release flags
+            if j >= nproc:
+                k += 1
+                return ((0 if k < ops else DONE), k, ne, 0), sh, ("pass",)
+            return (2, k, e, j + 1), _set(sh, S + j, ne), None
         raise AssertionError(pc)
 
 

@@ -1,0 +1,215 @@
+// Batched persistent kernel: many independent mutexes of uneven contention and many barrier
+// groups driven by one co-resident launch.
+//
+// Section 6 measures one primitive instance at a time; a real persistent kernel serves
+// thousands of instances at once, with contention set by key popularity.  Here acquisition i
+// (key keys[i], addend adds[i]) belongs to block i mod G and runs in order on that block's
+// thread 0: lock mutex[key] with the policy of the key's contention class, add the int64
+// addend to sum[key] and increment count[key] with plain loads and stores, unlock.  Blocks
+// that belong to a barrier group also cross `rounds` group barriers spread evenly over their
+// acquisitions, with the sampled slot check of the barrier workload (partner
+// p = (j + r + 1) mod size inside the group).  The autotuner chooses, per contention class,
+// the mutex kind (spin / spin + backoff / ticket), the backoff constants (0 = pure spinning,
+// otherwise __nanosleep) and the cluster size of the group barriers.
+#include "common.cuh"
+
+using namespace gsync_impl;
+namespace ptx = gsync::ptx;
+
+namespace {
+
+constexpr int kMaxThreads = 256;
+constexpr uint32_t kObjWords = 3 * gsync::kLineWords;  // header line + two lines per object
+
+struct Args {
+  uint32_t* mutex_state;
+  const uint8_t* key_class;
+  const uint32_t* policy;
+  const int32_t* keys;
+  const int64_t* adds;
+  int64_t* sum;
+  uint32_t* count;
+  const int32_t* group_start;
+  const int32_t* group_size;
+  const int32_t* group_of_block;
+  uint32_t* group_state;
+  uint32_t* slots;
+  uint32_t* mix;
+  uint32_t* bad;
+  uint32_t* status;
+  uint64_t timeout_ns;
+  int32_t nkeys, nacq, rounds, nclasses, ngroups;
+};
+
+__device__ __forceinline__ gsync::Token lock_by_policy(const gsync::MutexRef& m) {
+  switch (m.kind) {
+    case GSYNC_MUTEX_CAS_SPIN: return gsync::mutex_lock_thread<GSYNC_MUTEX_CAS_SPIN>(m);
+    case GSYNC_MUTEX_CAS_BACKOFF: return gsync::mutex_lock_thread<GSYNC_MUTEX_CAS_BACKOFF>(m);
+    default: return gsync::mutex_lock_thread<GSYNC_MUTEX_TICKET>(m);
+  }
+}
+
+__device__ __forceinline__ void unlock_by_policy(const gsync::MutexRef& m, uint32_t ticket) {
+  if (m.kind == GSYNC_MUTEX_TICKET) gsync::mutex_unlock_thread<GSYNC_MUTEX_TICKET>(m, ticket);
+  else gsync::mutex_unlock_thread<GSYNC_MUTEX_CAS_SPIN>(m, ticket);
+}
+
+// One crossing of the group barrier with the sampled slot check.
+template <int BKIND>
+__device__ __forceinline__ int group_cross(gsync::BarrierRef& bar, uint32_t* gslots, uint32_t gsize, uint32_t grank,
+                                           uint32_t r, uint32_t& mix, uint32_t& bad) {
+  uint32_t* buf = gslots + (r & 1u) * gsize;
+  if (threadIdx.x == 0) buf[grank] = r * gsize + grank;
+  const int rc = gsync::barrier_wait<BKIND>(bar);
+  if (rc == GSYNC_OK && threadIdx.x == 0) {
+    const uint32_t p = (grank + r + 1u) % gsize;
+    const uint32_t v = buf[p];
+    mix = rotl32(mix, 5) ^ lowbias32(v);
+    bad += v != r * gsize + p;
+  }
+  return rc;
+}
+
+template <int BKIND>
+__global__ void __launch_bounds__(kMaxThreads, 8) batched_kernel(Args a) {
+  const uint32_t G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+  __shared__ int s_fail;
+  if (tid == 0) s_fail = 0;
+  int g = a.group_of_block[b];
+  if (g >= a.ngroups) g = -1;
+  gsync::BarrierRef bar;
+  uint32_t gsize = 0, grank = 0;
+  uint32_t* gslots = nullptr;
+  if (g >= 0) {
+    gsize = (uint32_t)a.group_size[g];
+    grank = b - (uint32_t)a.group_start[g];
+    bool ok = grank < gsize && gsize >= 1u && (uint32_t)a.group_start[g] + gsize <= G;
+    if (BKIND == GSYNC_BAR_CLUSTER) {
+      // The hardware cluster barrier cannot time out, so every block of this block's cluster
+      // must be in the same group; every block of the cluster reads the same entries and so
+      // reaches the same verdict before any cluster barrier runs.
+      const uint32_t c = ptx::cluster_nctarank(), c0 = b - ptx::cluster_ctarank();
+      ok = ok && ((uint32_t)a.group_start[g] % c == 0u) && (gsize % c == 0u);
+      for (uint32_t k = 0; k < c; ++k) ok = ok && a.group_of_block[c0 + k] == g;
+    }
+    if (!ok) {
+      if (tid == 0) ptx::atom_or_relaxed(a.status, GSYNC_STATUS_CONFIG);
+      g = -1;
+    }
+  }
+  if (g >= 0) {
+    gslots = a.slots + 2u * (uint32_t)a.group_start[g];
+    bar.s = a.group_state + (uint32_t)g * kObjWords;
+    bar.kind = BKIND;
+    bar.n = gsize;
+    bar.param = BKIND == GSYNC_BAR_CLUSTER ? ptx::cluster_nctarank() : 0u;
+    bar.mode = 0;
+    bar.timeout_ns = a.timeout_ns;
+    bar.epoch = ptx::ld_relaxed(bar.line(2));
+  }
+  const uint32_t nacq = (uint32_t)a.nacq;
+  const uint32_t nmine = b < nacq ? (nacq - 1u - b) / G + 1u : 0u;
+  const uint32_t rounds = g >= 0 ? (uint32_t)a.rounds : 0u;
+  uint32_t crossed = 0, mix = 0, bad = 0;
+  int bar_rc = GSYNC_OK;
+  __syncthreads();
+  for (uint32_t j = 0; j < nmine; ++j) {
+    if (tid == 0 && !s_fail) {
+      const uint32_t i = b + j * G;
+      const uint32_t key = (uint32_t)a.keys[i];
+      if (key >= (uint32_t)a.nkeys) {
+        ptx::atom_or_relaxed(a.status, GSYNC_STATUS_VIOLATION);
+        s_fail = 1;
+      } else {
+        const uint32_t cls = a.key_class[key];
+        const uint32_t* pol = a.policy + 4u * (cls < (uint32_t)a.nclasses ? cls : 0u);
+        gsync::MutexRef m;
+        m.s = a.mutex_state + key * kObjWords;
+        m.kind = pol[0] <= (uint32_t)GSYNC_MUTEX_TICKET ? pol[0] : (uint32_t)GSYNC_MUTEX_TICKET;
+        m.qmask = 0;
+        m.bo.policy = GSYNC_BACKOFF_EXPONENTIAL;
+        m.bo.min_ns = pol[1];
+        m.bo.max_ns = pol[2];
+        m.timeout_ns = a.timeout_ns;
+        const gsync::Token t = lock_by_policy(m);
+        if (t.status != GSYNC_OK) {
+          record_status(a.status, t.status);
+          s_fail = 1;
+        } else {
+          a.sum[key] += a.adds[i];
+          a.count[key] += 1u;
+          unlock_by_policy(m, t.ticket);
+        }
+      }
+    }
+    if (rounds) {
+      const uint32_t target = (uint32_t)(((uint64_t)(j + 1u) * rounds) / nmine);
+      while (crossed < target) {
+        const int rc = group_cross<BKIND>(bar, gslots, gsize, grank, crossed++, mix, bad);
+        if (bar_rc == GSYNC_OK) bar_rc = rc;
+      }
+    }
+  }
+  // Every member crosses all rounds, also after an error (see the CLUSTER barrier's note).
+  while (crossed < rounds) {
+    const int rc = group_cross<BKIND>(bar, gslots, gsize, grank, crossed++, mix, bad);
+    if (bar_rc == GSYNC_OK) bar_rc = rc;
+  }
+  if (tid == 0) {
+    if (bar_rc != GSYNC_OK) record_status(a.status, bar_rc);
+    a.mix[b] = mix;
+    a.bad[b] = bad;
+  }
+}
+
+}  // namespace
+
+extern "C" int gsync_bench_batched(const gsync_batched_work* w, void* stream) {
+  if (!w || w->nkeys < 1 || w->nacq < 0 || w->nblocks < 1 || w->ngroups < 0 || w->rounds < 0 || w->nclasses < 1 ||
+      w->block_threads < 32 || w->block_threads > kMaxThreads || w->block_threads % 32)
+    return GSYNC_EINVAL;
+  if (!w->mutex_state || !w->key_class || !w->policy || !w->keys || !w->adds || !w->sum || !w->count ||
+      !w->group_of_block || !w->mix || !w->bad || !w->status || !aligned(w->mutex_state, 128))
+    return GSYNC_EINVAL;
+  if (w->ngroups > 0 && (!w->group_start || !w->group_size || !w->group_state || !w->slots ||
+                         !aligned(w->group_state, 128)))
+    return GSYNC_EINVAL;
+  const int cluster = w->cluster < 1 ? 1 : w->cluster;
+  if (cluster > 8 || w->nblocks % cluster) return GSYNC_EINVAL;
+  Args a;
+  a.mutex_state = (uint32_t*)w->mutex_state;
+  a.key_class = w->key_class;
+  a.policy = w->policy;
+  a.keys = w->keys;
+  a.adds = w->adds;
+  a.sum = w->sum;
+  a.count = w->count;
+  a.group_start = w->group_start;
+  a.group_size = w->group_size;
+  a.group_of_block = w->group_of_block;
+  a.group_state = (uint32_t*)w->group_state;
+  a.slots = w->slots;
+  a.mix = w->mix;
+  a.bad = w->bad;
+  a.status = w->status;
+  a.timeout_ns = w->timeout_ns ? w->timeout_ns : 2000000000ull;
+  a.nkeys = w->nkeys;
+  a.nacq = w->nacq;
+  a.rounds = w->rounds;
+  a.nclasses = w->nclasses;
+  a.ngroups = w->ngroups;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cluster > 1)
+    return launch_coresident(batched_kernel<GSYNC_BAR_CLUSTER>, w->nblocks, w->block_threads, cluster, 0, st, a);
+  if (w->plain_launch) {
+    // For stream capture: an ordinary launch after the same co-residency check.  All blocks
+    // are resident as long as no other kernel occupies the GPU when the graph runs.
+    int maxb = 0;
+    if (int rc = max_coresident(batched_kernel<GSYNC_BAR_ATOMIC>, w->block_threads, 1, 0, &maxb)) return rc;
+    if (w->nblocks > maxb) return GSYNC_ENOTRESIDENT;
+    batched_kernel<GSYNC_BAR_ATOMIC><<<w->nblocks, w->block_threads, 0, st>>>(a);
+    GSYNC_CUDA(cudaGetLastError());
+    return GSYNC_OK;
+  }
+  return launch_coresident(batched_kernel<GSYNC_BAR_ATOMIC>, w->nblocks, w->block_threads, 1, 0, st, a);
+}

@@ -22,10 +22,10 @@ constexpr int kMaxThreads = 256;
 
 // The full-fold variant reduces three values per round and needs more than 32 registers;
 // at 128 threads per block it still fits 8 blocks per SM.
-template <int KIND, bool FULL>
+template <int KIND, bool FULL, bool TRACE = false>
 __global__ void __launch_bounds__(kMaxThreads, FULL ? 4 : 8)
     barrier_workload_kernel(uint32_t* state, int rounds, uint32_t* slots, uint32_t* chk, uint32_t* mix_out,
-                            uint32_t* bad_out, uint32_t* status) {
+                            uint32_t* bad_out, uint32_t* status, uint64_t* trace = nullptr) {
   gsync::BarrierRef bar = gsync::barrier_attach(state);
   const uint32_t B = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   if (bar.kind != (uint32_t)KIND || bar.n != B ||
@@ -39,10 +39,16 @@ __global__ void __launch_bounds__(kMaxThreads, FULL ? 4 : 8)
     uint32_t* buf = slots + (uint32_t)(r & 1) * B;
     const uint32_t rb = (uint32_t)r * B;
     if (tid == 0) buf[b] = rb + b;
+    if (TRACE && tid == 0) trace[2u * ((uint64_t)b * (uint32_t)rounds + (uint32_t)r)] = gsync::ptx::globaltimer();
     const int rc = gsync::barrier_wait<KIND>(bar);
+    if (TRACE && tid == 0) trace[2u * ((uint64_t)b * (uint32_t)rounds + (uint32_t)r) + 1u] = gsync::ptx::globaltimer();
     if (rc != GSYNC_OK) {
       if (tid == 0) record_status(status, rc);
-      break;
+      // The hardware cluster barrier has no timeout: every block of a cluster must keep
+      // crossing for all rounds, or a peer would wait forever.  After a failure the object's
+      // abort word makes each later crossing return within a few polls.
+      if (KIND != GSYNC_BAR_CLUSTER) break;
+      continue;
     }
     if (FULL) {
       uint32_t x = 0, s = 0, nb = 0;
@@ -89,7 +95,7 @@ __global__ void __launch_bounds__(kMaxThreads, FULL ? 4 : 8)
   }
 }
 
-using KernelFn = void (*)(uint32_t*, int, uint32_t*, uint32_t*, uint32_t*, uint32_t*, uint32_t*);
+using KernelFn = void (*)(uint32_t*, int, uint32_t*, uint32_t*, uint32_t*, uint32_t*, uint32_t*, uint64_t*);
 
 KernelFn pick(int kind, int full) {
   switch (kind) {
@@ -97,11 +103,41 @@ KernelFn pick(int kind, int full) {
     case GSYNC_BAR_FLAG: return full ? barrier_workload_kernel<GSYNC_BAR_FLAG, true> : barrier_workload_kernel<GSYNC_BAR_FLAG, false>;
     case GSYNC_BAR_TREE: return full ? barrier_workload_kernel<GSYNC_BAR_TREE, true> : barrier_workload_kernel<GSYNC_BAR_TREE, false>;
     case GSYNC_BAR_CLUSTER: return full ? barrier_workload_kernel<GSYNC_BAR_CLUSTER, true> : barrier_workload_kernel<GSYNC_BAR_CLUSTER, false>;
+    case GSYNC_BAR_SHARDED: return full ? barrier_workload_kernel<GSYNC_BAR_SHARDED, true> : barrier_workload_kernel<GSYNC_BAR_SHARDED, false>;
+  }
+  return nullptr;
+}
+
+KernelFn pick_trace(int kind) {
+  switch (kind) {
+    case GSYNC_BAR_ATOMIC: return barrier_workload_kernel<GSYNC_BAR_ATOMIC, false, true>;
+    case GSYNC_BAR_FLAG: return barrier_workload_kernel<GSYNC_BAR_FLAG, false, true>;
+    case GSYNC_BAR_TREE: return barrier_workload_kernel<GSYNC_BAR_TREE, false, true>;
+    case GSYNC_BAR_CLUSTER: return barrier_workload_kernel<GSYNC_BAR_CLUSTER, false, true>;
+    case GSYNC_BAR_SHARDED: return barrier_workload_kernel<GSYNC_BAR_SHARDED, false, true>;
   }
   return nullptr;
 }
 
 }  // namespace
+
+// Phase trace of the sampled barrier workload: trace[2 * (b * rounds + r)] and [+ 1] receive
+// block b's %globaltimer just before and just after its round-r barrier_wait.
+extern "C" int gsync_probe_barrier_trace(void* state, const gsync_barrier_work* w, uint64_t* trace, void* stream) {
+  if (!state || !w || !trace || !aligned(state, 128) || w->full) return GSYNC_EINVAL;
+  if (w->nblocks < 1 || w->rounds < 0 || w->block_threads < 32 || w->block_threads > kMaxThreads ||
+      w->block_threads % 32 || !w->slots || !w->mix || !w->bad || !w->status)
+    return GSYNC_EINVAL;
+  KernelFn k = pick_trace(w->kind);
+  if (!k) return GSYNC_EINVAL;
+  int cluster = 1;
+  if (w->kind == GSYNC_BAR_CLUSTER) {
+    cluster = w->cluster;
+    if (cluster < 1 || cluster > 8 || w->nblocks % cluster) return GSYNC_EINVAL;
+  }
+  return launch_coresident(k, w->nblocks, w->block_threads, cluster, 0, (cudaStream_t)stream, (uint32_t*)state,
+                           w->rounds, w->slots, w->chk, w->mix, w->bad, w->status, trace);
+}
 
 namespace gsync_impl {
 int max_blocks_barrier(int kind, int block_threads, int cluster, int* out) {
@@ -125,7 +161,7 @@ extern "C" int gsync_bench_barrier(void* state, const gsync_barrier_work* w, voi
     if (cluster < 1 || cluster > 8 || w->nblocks % cluster) return GSYNC_EINVAL;
   }
   return launch_coresident(k, w->nblocks, w->block_threads, cluster, 0, (cudaStream_t)stream, (uint32_t*)state,
-                           w->rounds, w->slots, w->chk, w->mix, w->bad, w->status);
+                           w->rounds, w->slots, w->chk, w->mix, w->bad, w->status, (uint64_t*)nullptr);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -13,7 +13,8 @@ using namespace gsync_impl;
 namespace {
 
 constexpr int kMaxThreads = 256;
-constexpr int kNoLock = -1;  // no mutex at all: the critical-section probe (T_cs)
+constexpr int kNoLock = -1;     // no mutex at all: the critical-section probe (T_cs)
+constexpr int kFrameOnly = -2;  // the probe's frame (acquire load, barriers, release) around an empty body
 constexpr uint32_t kGolden = 0x9E3779B1u;
 
 template <int KIND>
@@ -24,7 +25,7 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
   const uint32_t b = blockIdx.x, tid = threadIdx.x;
   const uint32_t n = gridDim.x * (uint32_t)acq;
   gsync::MutexRef m;
-  if (KIND != kNoLock) {
+  if (KIND >= 0) {
     m = gsync::mutex_attach(state);
     const bool bad_queue = KIND == GSYNC_MUTEX_SLEEP_QUEUE && gridDim.x > m.qmask + 1u;
     if (m.kind != (uint32_t)KIND || bad_queue) {
@@ -38,15 +39,19 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
     const uint32_t v = addend[id];
     if (tid == 0 && delay) spin_cycles(delay[id]);
     gsync::Token t{GSYNC_OK, 0xFFFFFFFFu};
-    if (KIND != kNoLock) {
+    if (KIND >= 0) {
       t = gsync::mutex_lock<KIND>(m);
       if (t.status != GSYNC_OK) {
         if (tid == 0) record_status(status, t.status);
         break;
       }
+    } else {
+      // What a lock adds around the body even uncontended: one acquire load, one block barrier.
+      if (tid == 0) (void)gsync::ptx::ld_acquire(status + 32);
+      __syncthreads();
     }
     // ---- critical section ----
-    if (tid == 0) {
+    if (KIND != kFrameOnly && tid == 0) {
       const uint32_t seq = *total;
       *total = seq + 1u;
       if (seq < n) {
@@ -56,9 +61,10 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
       }
       ticket_out[id] = t.ticket;
     }
-    for (uint32_t i = tid; i < (uint32_t)cs_words; i += blockDim.x) data[i] += v ^ (i * kGolden);
+    if (KIND != kFrameOnly)
+      for (uint32_t i = tid; i < (uint32_t)cs_words; i += blockDim.x) data[i] += v ^ (i * kGolden);
     // ---- end of critical section ----
-    if (KIND != kNoLock) {
+    if (KIND >= 0) {
       gsync::mutex_unlock<KIND>(m, t);
     } else {
       __syncthreads();
@@ -171,12 +177,13 @@ extern "C" int gsync_bench_mutex_host(const gsync_mutex_work* w, const gsync_bac
   return GSYNC_OK;
 }
 
-// T_cs probe: one block runs the critical-section body, including the release store that
-// ends it, `iters` times with no lock and no delays.  scratch: [0, 128) status and the
+// T_cs probe: one block runs the critical-section body, framed like a lock hand-off (an
+// acquire load and a barrier before it, a barrier and the release store after it), `iters`
+// times with no lock and no delays.  scratch: [0, 128) status and the
 // release word (status + 32), then total, data, count, grant log.
 extern "C" int gsync_probe_cs(int cs_words, int block_threads, int iters, void* scratch, uint64_t* out,
                               void* stream) {
-  if (!scratch || !out || cs_words < 0 || iters < 1 || block_threads < 32 || block_threads > kMaxThreads ||
+  if (!scratch || !out || cs_words < -1 || iters < 1 || block_threads < 32 || block_threads > kMaxThreads ||
       block_threads % 32 || !aligned(scratch, 256))
     return GSYNC_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
@@ -184,7 +191,7 @@ extern "C" int gsync_probe_cs(int cs_words, int block_threads, int iters, void* 
   uint32_t* status = (uint32_t*)p;   p += 256;
   uint32_t* total = (uint32_t*)p;    p += 256;
   uint32_t* count = (uint32_t*)p;    p += 256;
-  uint32_t* data = (uint32_t*)p;     p += round_up(4 * (size_t)cs_words);
+  uint32_t* data = (uint32_t*)p;     p += round_up(4 * (size_t)(cs_words > 0 ? cs_words : 0));
   uint32_t* log = (uint32_t*)p;      p += round_up(4 * (size_t)iters);
   uint32_t* tick = (uint32_t*)p;     p += round_up(4 * (size_t)iters);
   uint32_t* add = (uint32_t*)p;      p += round_up(4 * (size_t)iters);
@@ -194,8 +201,13 @@ extern "C" int gsync_probe_cs(int cs_words, int block_threads, int iters, void* 
   GSYNC_CUDA(cudaEventCreate(&e0));
   GSYNC_CUDA(cudaEventCreate(&e1));
   GSYNC_CUDA(cudaEventRecord(e0, st));
-  mutex_workload_kernel<kNoLock><<<1, block_threads, 0, st>>>(nullptr, iters, cs_words, nullptr, add, data, total, log,
-                                                             tick, count, status);
+  if (cs_words < 0) {  // frame only: the acquire load, barriers and release store, no body
+    mutex_workload_kernel<kFrameOnly><<<1, block_threads, 0, st>>>(nullptr, iters, 0, nullptr, add, data, total, log,
+                                                                  tick, count, status);
+  } else {
+    mutex_workload_kernel<kNoLock><<<1, block_threads, 0, st>>>(nullptr, iters, cs_words, nullptr, add, data, total,
+                                                               log, tick, count, status);
+  }
   GSYNC_CUDA(cudaGetLastError());
   GSYNC_CUDA(cudaEventRecord(e1, st));
   GSYNC_CUDA(cudaEventSynchronize(e1));
@@ -209,6 +221,6 @@ extern "C" int gsync_probe_cs(int cs_words, int block_threads, int iters, void* 
 
 // Size of the scratch buffer gsync_probe_cs needs.
 extern "C" size_t gsync_probe_cs_scratch_bytes(int cs_words, int iters) {
-  if (cs_words < 0 || iters < 1) return 0;
-  return 3 * 256 + round_up(4 * (size_t)cs_words) + 3 * round_up(4 * (size_t)iters);
+  if (cs_words < -1 || iters < 1) return 0;
+  return 3 * 256 + round_up(4 * (size_t)(cs_words > 0 ? cs_words : 0)) + 3 * round_up(4 * (size_t)iters);
 }

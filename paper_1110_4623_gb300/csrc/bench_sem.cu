@@ -14,26 +14,40 @@ namespace {
 
 constexpr int kMaxThreads = 256;
 
+constexpr int kNoSem = -1;     // no semaphore at all: the critical-section probe
+constexpr int kSemFrame = -2;  // the probe's frame around an empty critical section
+
 template <int KIND>
 __global__ void __launch_bounds__(kMaxThreads, 8)
     sem_workload_kernel(uint32_t* state, int pairs, const uint32_t* __restrict__ hold,
                         const uint32_t* __restrict__ addend, uint32_t* occupancy, uint32_t* max_occupancy,
                         uint32_t* total, uint32_t* tally, uint32_t* count, uint32_t* status) {
-  const gsync::SemRef s = gsync::sem_attach(state);
   const uint32_t b = blockIdx.x, tid = threadIdx.x;
-  if (s.kind != (uint32_t)KIND) {
-    if (tid == 0) gsync::ptx::atom_or_relaxed(status, GSYNC_STATUS_CONFIG);
-    return;
+  gsync::SemRef s;
+  if (KIND >= 0) {
+    s = gsync::sem_attach(state);
+    if (s.kind != (uint32_t)KIND) {
+      if (tid == 0) gsync::ptx::atom_or_relaxed(status, GSYNC_STATUS_CONFIG);
+      return;
+    }
+  } else {
+    s.n = 1;
   }
   uint32_t done = 0;
   for (int p = 0; p < pairs; ++p) {
     const uint32_t id = b * (uint32_t)pairs + (uint32_t)p;
-    const int rc = gsync::sem_wait<KIND>(s);
+    int rc = GSYNC_OK;
+    if (KIND >= 0) {
+      rc = gsync::sem_wait<KIND>(s);
+    } else {
+      if (tid == 0) (void)gsync::ptx::ld_acquire(status + 32);
+      __syncthreads();
+    }
     if (rc != GSYNC_OK) {
       if (tid == 0) record_status(status, rc);
       break;
     }
-    if (tid == 0) {
+    if (KIND != kSemFrame && tid == 0) {
       const uint32_t o = gsync::ptx::atom_add_relaxed(occupancy, 1u) + 1u;
       gsync::ptx::atom_max_relaxed(max_occupancy, o);
       if (s.n == 1u) {
@@ -44,7 +58,16 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
       gsync::ptx::red_add_relaxed(tally, addend[id]);
       gsync::ptx::atom_add_relaxed(occupancy, 0xFFFFFFFFu);
     }
-    const int rc2 = gsync::sem_post<KIND>(s);
+    int rc2 = GSYNC_OK;
+    if (KIND >= 0) {
+      rc2 = gsync::sem_post<KIND>(s);
+    } else {
+      __syncthreads();
+      if (tid == 0) {
+        gsync::ptx::fence_acq_rel();
+        gsync::ptx::st_relaxed(status + 32, id);
+      }
+    }
     if (rc2 != GSYNC_OK) {
       if (tid == 0) record_status(status, rc2);
       break;
@@ -88,4 +111,38 @@ extern "C" int gsync_bench_sem(void* state, const gsync_sem_work* w, void* strea
   return launch_coresident(k, w->nblocks, w->block_threads, 1, 0, (cudaStream_t)stream, (uint32_t*)state, w->pairs,
                            w->hold, w->addend, w->occupancy, w->max_occupancy, w->total, w->tally, w->count,
                            w->status);
+}
+
+// Semaphore critical-section probe: one block runs the workload's wait/post frame without a
+// semaphore (an acquire load and a barrier before, a barrier and a release after) around the
+// critical section -- occupancy bookkeeping, hold[p] cycles, the tally -- for p < iters.
+// out[0] = elapsed ns (CUDA events; synchronizes `stream`).  scratch: 1024 bytes.
+extern "C" int gsync_probe_sem_cs(int block_threads, int iters, const uint32_t* hold, const uint32_t* addend,
+                                  void* scratch, uint64_t* out, void* stream) {
+  if (!scratch || !out || (!addend && hold) || iters < 1 || block_threads < 32 || block_threads > kMaxThreads ||
+      block_threads % 32 || !aligned(scratch, 256))
+    return GSYNC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t* w = (uint32_t*)scratch;
+  GSYNC_CUDA(cudaMemsetAsync(scratch, 0, 1024, st));
+  cudaEvent_t e0, e1;
+  GSYNC_CUDA(cudaEventCreate(&e0));
+  GSYNC_CUDA(cudaEventCreate(&e1));
+  GSYNC_CUDA(cudaEventRecord(e0, st));
+  if (hold == nullptr && addend == nullptr) {  // frame only
+    sem_workload_kernel<kSemFrame><<<1, block_threads, 0, st>>>(nullptr, iters, nullptr, nullptr, w, w + 32, w + 64,
+                                                                w + 96, w + 128, w + 160);
+  } else {
+    sem_workload_kernel<kNoSem><<<1, block_threads, 0, st>>>(nullptr, iters, hold, addend, w, w + 32, w + 64, w + 96,
+                                                             w + 128, w + 160);
+  }
+  GSYNC_CUDA(cudaGetLastError());
+  GSYNC_CUDA(cudaEventRecord(e1, st));
+  GSYNC_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  GSYNC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  out[0] = (uint64_t)(ms * 1e6);
+  return GSYNC_OK;
 }

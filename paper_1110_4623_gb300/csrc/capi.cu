@@ -96,6 +96,8 @@ uint32_t barrier_lines(int kind, uint32_t n, uint32_t param) {
     }
     case GSYNC_BAR_TREE:
       return 2 + tree_nodes(n, param);
+    case GSYNC_BAR_SHARDED:
+      return 1 + param + (n + 31) / 32;
   }
   return 0;
 }
@@ -130,9 +132,10 @@ size_t gsync_barrier_bytes(int kind, int nblocks, int param) {
   if (nblocks < 1 || nblocks > (1 << 20)) return 0;
   switch (kind) {
     case GSYNC_BAR_ATOMIC: break;
-    case GSYNC_BAR_FLAG: if (param != 0 && param != 1) return 0; break;
+    case GSYNC_BAR_FLAG: if ((param != 0 && param != 1) || nblocks > 8192) return 0; break;
     case GSYNC_BAR_TREE: if (param < 2 || param > 1024) return 0; break;
     case GSYNC_BAR_CLUSTER: if (param < 1 || param > 8 || nblocks % param) return 0; break;
+    case GSYNC_BAR_SHARDED: if (param < 1 || param > 32 || param > nblocks) return 0; break;
     default: return 0;
   }
   return (size_t)barrier_lines(kind, (uint32_t)nblocks, (uint32_t)param) * kLine;

@@ -1,0 +1,475 @@
+// Persistent serving loop with continuous batching, built on the library's own ticket lock and
+// sleeping semaphore (the paper motivates its primitives with task queues, Section 1, and
+// names hardware enqueue/dequeue as a wish, Section 7).
+//
+// The host publishes requests into a ring of descriptors in pinned host memory (tail word
+// written with a release store).  Inside one co-resident launch:
+//   * admitter blocks take the next request index under the ring's ticket lock, wait on the
+//     admission semaphore (n = number of in-flight slots), claim a free slot, and publish the
+//     request in it (generation-tagged chunk counter, release store of the slot state);
+//   * every other block claims chunks of any active slot (compare-and-swap on the slot's
+//     generation:chunk counter), sums the chunk's int32 values in int64, adds the partial to
+//     the slot's accumulator; the block that finishes a request's last chunk writes the result
+//     and a completion flag into pinned host memory, frees the slot and posts the semaphore.
+// Requests that arrive while others run are admitted as slots free up and their chunks run
+// side by side with older requests' chunks.  Every wait is bounded (the object timeouts, or
+// the loop's own deadline) and the host's shutdown word ends the loop.
+//
+// The per-request-launch baseline runs the same chunked segmented sum as one kernel launch
+// per request and completes it the same way (result and flag in pinned host memory).
+#include <atomic>
+#include <chrono>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace gsync_impl;
+namespace ptx = gsync::ptx;
+
+namespace {
+
+constexpr int kThreads = 256;
+
+struct Slot {  // one 128-byte line
+  uint32_t state;       // 0 free, 1 claimed by an admitter, 2 active
+  uint32_t gen;         // bumped every time the slot takes a request
+  uint32_t next_chunk;  // (gen & 0xFFFF) << 16 | next chunk to hand out
+  uint32_t done_chunks;
+  uint32_t id;
+  uint32_t nchunks;
+  int64_t off;
+  int64_t len;
+  unsigned long long acc;
+  uint32_t pad[20];
+};
+static_assert(sizeof(Slot) == 128, "one line per slot");
+
+struct Args {
+  const gsync_serve_req* ring;  // device view of the host ring
+  uint32_t ring_mask;
+  const uint32_t* tail;      // device view (host writes)
+  const uint32_t* shutdown;  // device view (host writes)
+  int64_t* res;              // device view of host results
+  uint32_t* done;            // device view of host completion flags
+  const int32_t* pool;
+  uint32_t* ring_lock;       // gsync mutex (TICKET)
+  uint32_t* ring_head;       // next request index to take (own line)
+  uint32_t* admit_sem;       // gsync semaphore (TICKET), n = nslots
+  Slot* slots;
+  uint32_t* active_mask;     // one bit per slot (nslots <= 64)
+  uint32_t* stats;           // [0] admitted, [32] chunks, [64] completed (own lines)
+  uint32_t* status;
+  uint32_t nslots, admitters, chunk_elems;
+  uint64_t timeout_ns;
+};
+
+__device__ __forceinline__ uint32_t ld_acquire_sys(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_sys(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_sys_s64(int64_t* p, int64_t v) {
+  asm volatile("st.relaxed.sys.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t atom_cas_relaxed(uint32_t* p, uint32_t cmp, uint32_t v) {
+  uint32_t r;
+  asm volatile("atom.relaxed.gpu.global.cas.b32 %0, [%1], %2, %3;" : "=r"(r) : "l"(p), "r"(cmp), "r"(v) : "memory");
+  return r;
+}
+
+// Block-wide int64 sum of pool[a, b): 16-byte loads over the aligned middle, scalars at the ends.
+__device__ __forceinline__ long long block_sum(const int32_t* pool, int64_t a, int64_t b) {
+  long long s = 0;
+  int64_t a4 = (a + 3) & ~(int64_t)3;
+  if (a4 > b) a4 = b;
+  const int64_t b4 = a4 + ((b - a4) & ~(int64_t)3);
+  for (int64_t i = a + threadIdx.x; i < a4; i += blockDim.x) s += pool[i];
+  const int4* v = reinterpret_cast<const int4*>(pool + a4);
+  const int64_t nv = (b4 - a4) >> 2;
+  for (int64_t i = threadIdx.x; i < nv; i += blockDim.x) {
+    const int4 x = __ldcs(v + i);
+    s += (long long)x.x + x.y + x.z + x.w;
+  }
+  for (int64_t i = b4 + threadIdx.x; i < b; i += blockDim.x) s += pool[i];
+  __shared__ long long red[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  long long t = 0;
+  if (threadIdx.x == 0)
+    for (uint32_t w = 0; w < (blockDim.x + 31) / 32; ++w) t += red[w];
+  __syncthreads();
+  return t;  // valid in thread 0
+}
+
+// Thread 0: claims one chunk of slot s, or returns false.
+__device__ bool claim_chunk(Slot* slot, uint32_t& chunk, uint32_t& gen) {
+  if (ptx::ld_acquire(&slot->state) != 2u) return false;
+  gen = ptx::ld_relaxed(&slot->gen);
+  const uint32_t n = ptx::ld_relaxed(&slot->nchunks);
+  uint32_t v = ptx::ld_relaxed(&slot->next_chunk);
+  for (int tries = 0; tries < 64; ++tries) {
+    if ((v >> 16) != (gen & 0xFFFFu) || (v & 0xFFFFu) >= n) return false;
+    const uint32_t old = atom_cas_relaxed(&slot->next_chunk, v, v + 1u);
+    if (old == v) {
+      chunk = v & 0xFFFFu;
+      return true;
+    }
+    v = old;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(kThreads) serve_kernel(Args a) {
+  const uint32_t tid = threadIdx.x;
+  const gsync::MutexRef lock = gsync::mutex_attach(a.ring_lock);
+  const gsync::SemRef sem = gsync::sem_attach(a.admit_sem);
+  __shared__ int s_cmd;       // 0 continue, 1 exit
+  __shared__ uint32_t s_slot, s_chunk, s_gen;
+  __shared__ int64_t s_lo, s_hi;
+  const bool admitter = blockIdx.x < a.admitters;
+  uint32_t idle = 0, scan = blockIdx.x % a.nslots;
+  uint64_t idle_since = 0;
+
+  if (admitter) {
+    // Admitters: ring -> semaphore -> slot.  Thread 0 does everything; the block only idles.
+    if (tid == 0) {
+      for (;;) {
+        // 1. wait for a request beyond the shared head, or for shutdown
+        uint32_t polls = 0;
+        const uint64_t t0 = ptx::globaltimer();
+        bool stop = false;
+        uint32_t tail_seen = 0;
+        for (;;) {
+          const uint32_t head = ptx::ld_relaxed(a.ring_head);
+          tail_seen = ld_acquire_sys(a.tail);
+          if ((int32_t)(tail_seen - head) > 0) break;
+          if ((++polls & 15u) == 0) {
+            if (ld_acquire_sys(a.shutdown)) { stop = true; break; }
+            if (ptx::globaltimer() - t0 > a.timeout_ns * 16) { record_status(a.status, GSYNC_ETIMEDOUT); stop = true; break; }
+          }
+          __nanosleep(200);
+        }
+        if (stop) break;
+        // 2. admission: one in-flight slot
+        int rc = gsync::sem_wait_thread<GSYNC_SEM_TICKET>(sem);
+        if (rc != GSYNC_OK) { record_status(a.status, rc); break; }
+        // 3. take the next request index under the ring lock
+        const gsync::Token t = gsync::mutex_lock_thread<GSYNC_MUTEX_TICKET>(lock);
+        if (t.status != GSYNC_OK) { record_status(a.status, t.status); break; }
+        // The tail only grows, so the value seen above (acquired before this point) still
+        // bounds what may be taken; no second round trip to host memory inside the lock.
+        const uint32_t head = ptx::ld_relaxed(a.ring_head);
+        const bool have = (int32_t)(tail_seen - head) > 0;
+        if (have) ptx::st_relaxed(a.ring_head, head + 1u);
+        gsync::mutex_unlock_thread<GSYNC_MUTEX_TICKET>(lock, t.ticket);
+        if (!have) {  // another admitter took it: give the permit back
+          gsync::sem_post_thread<GSYNC_SEM_TICKET>(sem);
+          continue;
+        }
+        // 4. read the descriptor (stable until this request completes) and claim a free slot
+        const gsync_serve_req req = a.ring[head & a.ring_mask];
+        uint32_t s = head % a.nslots;
+        bool got = false;
+        for (uint32_t k = 0; k < 4u * a.nslots && !got; ++k, s = (s + 1u) % a.nslots)
+          got = atom_cas_relaxed(&a.slots[s].state, 0u, 1u) == 0u;
+        if (!got) { record_status(a.status, GSYNC_ETIMEDOUT); break; }
+        s = (s + a.nslots - 1u) % a.nslots;
+        Slot* sl = &a.slots[s];
+        const uint32_t gen = sl->gen + 1u;
+        const uint32_t nch = (uint32_t)((req.len + a.chunk_elems - 1) / a.chunk_elems);
+        sl->gen = gen;
+        sl->id = req.id;
+        sl->off = req.off;
+        sl->len = req.len;
+        sl->nchunks = nch == 0 ? 1u : nch;
+        sl->acc = 0ull;
+        sl->done_chunks = 0u;
+        sl->next_chunk = (gen & 0xFFFFu) << 16;
+        ptx::st_release(&sl->state, 2u);
+        atomicOr(&a.active_mask[s >> 5], 1u << (s & 31));
+        ptx::red_add_relaxed(a.stats, 1u);
+      }
+    }
+    return;
+  }
+
+  // Workers: claim chunks of active slots until shutdown.
+  for (;;) {
+    if (tid == 0) {
+      s_cmd = 2;  // nothing yet
+      const uint32_t m0 = ptx::ld_relaxed(a.active_mask), m1 = a.nslots > 32 ? ptx::ld_relaxed(a.active_mask + 1) : 0u;
+      const uint64_t mask = ((uint64_t)m1 << 32) | m0;
+      if (mask) {
+        for (uint32_t k = 0; k < a.nslots; ++k) {
+          const uint32_t s = (scan + k) % a.nslots;
+          if (!((mask >> s) & 1ull)) continue;
+          uint32_t c, g;
+          if (claim_chunk(&a.slots[s], c, g)) {
+            Slot* sl = &a.slots[s];
+            const int64_t lo = sl->off + (int64_t)c * a.chunk_elems;
+            int64_t hi = lo + a.chunk_elems;
+            if (hi > sl->off + sl->len) hi = sl->off + sl->len;
+            s_slot = s; s_chunk = c; s_gen = g; s_lo = lo; s_hi = hi;
+            s_cmd = 0;
+            scan = s;
+            break;
+          }
+        }
+      }
+      if (s_cmd == 2) {
+        if ((++idle & 63u) == 0) {
+          if (ld_acquire_sys(a.shutdown)) s_cmd = 1;
+          const uint64_t now = ptx::globaltimer();
+          if (idle_since == 0) idle_since = now;
+          else if (now - idle_since > a.timeout_ns * 16) { record_status(a.status, GSYNC_ETIMEDOUT); s_cmd = 1; }
+        }
+        if (s_cmd == 2) __nanosleep(256);
+      } else {
+        idle = 0;
+        idle_since = 0;
+      }
+    }
+    __syncthreads();
+    const int cmd = s_cmd;
+    if (cmd == 1) break;
+    if (cmd == 2) { __syncthreads(); continue; }
+    const long long part = block_sum(a.pool, s_lo, s_hi);
+    if (tid == 0) {
+      Slot* sl = &a.slots[s_slot];
+      atomicAdd(&sl->acc, (unsigned long long)part);
+      ptx::red_add_relaxed(a.stats + 32, 1u);
+      const uint32_t d = ptx::atom_add_acq_rel(&sl->done_chunks, 1u) + 1u;
+      if (d == sl->nchunks) {
+        const long long total = (long long)atomicAdd(&sl->acc, 0ull);
+        const uint32_t id = sl->id;
+        st_relaxed_sys_s64(a.res + id, total);
+        st_release_sys(a.done + id, 1u);
+        atomicAnd(&a.active_mask[s_slot >> 5], ~(1u << (s_slot & 31)));
+        ptx::st_release(&sl->state, 0u);
+        gsync::sem_post_thread<GSYNC_SEM_TICKET>(sem);
+        ptx::red_add_relaxed(a.stats + 64, 1u);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Baseline: one launch per request; block j sums chunk j; the last block completes it.
+__global__ void __launch_bounds__(kThreads) segsum_kernel(const int32_t* pool, int64_t off, int64_t len,
+                                                          uint32_t chunk_elems, unsigned long long* acc,
+                                                          uint32_t* counter, uint32_t id, int64_t* res,
+                                                          uint32_t* done) {
+  const int64_t lo = off + (int64_t)blockIdx.x * chunk_elems;
+  int64_t hi = lo + chunk_elems;
+  if (hi > off + len) hi = off + len;
+  const long long part = block_sum(pool, lo, hi);
+  if (threadIdx.x == 0) {
+    atomicAdd(acc, (unsigned long long)part);
+    const uint32_t d = ptx::atom_add_acq_rel(counter, 1u) + 1u;
+    if (d == gridDim.x) {
+      const long long total = (long long)atomicAdd(acc, 0ull);
+      st_relaxed_sys_s64(res + id, total);
+      st_release_sys(done + id, 1u);
+    }
+  }
+}
+
+int host_dev_ptr(void* host, void** dev) {
+  GSYNC_CUDA(cudaHostGetDevicePointer(dev, host, 0));
+  return GSYNC_OK;
+}
+
+using Clock = std::chrono::steady_clock;
+
+int64_t now_ns(Clock::time_point t0) {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - t0).count();
+}
+
+void spin_until(Clock::time_point t) {
+  while (Clock::now() < t) {
+  }
+}
+
+// Polls completion flags in order of arrival; records the host time each flag is first seen.
+void collect(const gsync_serve_cfg* cfg, volatile uint32_t* done, Clock::time_point t0, const int64_t* sched,
+             int64_t* lat, std::atomic<int>* completed, std::atomic<bool>* abort_flag) {
+  const int n = cfg->nreq;
+  std::vector<char> seen(n, 0);
+  int low = 0, count = 0;
+  while (count < n && !abort_flag->load(std::memory_order_relaxed)) {
+    const int hi = std::min(n, low + 4096);
+    for (int q = low; q < hi; ++q) {
+      if (seen[q]) continue;
+      if (done[q]) {
+        std::atomic_thread_fence(std::memory_order_acquire);
+        lat[q] = now_ns(t0) - sched[q];
+        seen[q] = 1;
+        ++count;
+      }
+    }
+    while (low < n && seen[low]) ++low;
+    completed->store(count, std::memory_order_release);
+  }
+}
+
+}  // namespace
+
+extern "C" size_t gsync_serve_workspace_bytes(int nslots) {
+  if (nslots < 1 || nslots > 64) return 0;
+  return 3 * 128 /* ring lock */ + 128 /* head */ + 4 * 128 /* semaphore */ + (size_t)nslots * 128 + 128 /* mask */ +
+         3 * 128 /* stats */ + 128 /* status */;
+}
+
+extern "C" int gsync_serve_run(const gsync_serve_cfg* cfg, gsync_serve_buffers* buf, void* workspace,
+                               size_t workspace_bytes, void* stream) {
+  if (!cfg || !buf || !workspace || cfg->nreq < 1 || cfg->nslots < 1 || cfg->nslots > 64 || cfg->nblocks < 2 ||
+      cfg->admitters < 1 || cfg->admitters >= cfg->nblocks || cfg->chunk_elems < 1024 || cfg->ring_slots < 2 ||
+      (cfg->ring_slots & (cfg->ring_slots - 1)) || !aligned(workspace, 256))
+    return GSYNC_EINVAL;
+  if (workspace_bytes < gsync_serve_workspace_bytes(cfg->nslots)) return GSYNC_EINVAL;
+  if (!buf->pool || !buf->offset || !buf->length || !buf->sched_ns || !buf->ring || !buf->ctrl || !buf->res ||
+      !buf->done || !buf->latency_ns)
+    return GSYNC_EINVAL;
+  for (int q = 0; q < cfg->nreq; ++q)
+    if (buf->length[q] < 1 || (buf->length[q] + cfg->chunk_elems - 1) / cfg->chunk_elems > 0xFFFF) return GSYNC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* p = (char*)workspace;
+  uint32_t* ring_lock = (uint32_t*)p; p += 3 * 128;
+  uint32_t* head = (uint32_t*)p;      p += 128;
+  uint32_t* sem = (uint32_t*)p;       p += 4 * 128;
+  Slot* slots = (Slot*)p;             p += (size_t)cfg->nslots * 128;
+  uint32_t* mask = (uint32_t*)p;      p += 128;
+  uint32_t* stats = (uint32_t*)p;     p += 3 * 128;
+  uint32_t* status = (uint32_t*)p;
+  GSYNC_CUDA(cudaMemsetAsync(workspace, 0, gsync_serve_workspace_bytes(cfg->nslots), st));
+  if (int rc = gsync_mutex_init(ring_lock, 3 * 128, GSYNC_MUTEX_TICKET, 1, nullptr, cfg->timeout_ns, stream)) return rc;
+  gsync_backoff sbo = {GSYNC_BACKOFF_EXPONENTIAL, 64, 2000, 0};
+  if (int rc = gsync_sem_init(sem, 4 * 128, GSYNC_SEM_TICKET, cfg->nslots, &sbo, cfg->timeout_ns, stream)) return rc;
+
+  // Host control words: ctrl[0] = tail, ctrl[32] = shutdown (separate lines).
+  volatile uint32_t* ctrl = buf->ctrl;
+  ctrl[0] = 0;
+  ctrl[32] = 0;
+  for (int q = 0; q < cfg->nreq; ++q) buf->done[q] = 0;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+
+  Args a;
+  void *d_ring, *d_ctrl, *d_res, *d_done;
+  if (int rc = host_dev_ptr(buf->ring, &d_ring)) return rc;
+  if (int rc = host_dev_ptr((void*)buf->ctrl, &d_ctrl)) return rc;
+  if (int rc = host_dev_ptr(buf->res, &d_res)) return rc;
+  if (int rc = host_dev_ptr((void*)buf->done, &d_done)) return rc;
+  a.ring = (const gsync_serve_req*)d_ring;
+  a.ring_mask = (uint32_t)cfg->ring_slots - 1u;
+  a.tail = (const uint32_t*)d_ctrl;
+  a.shutdown = (const uint32_t*)d_ctrl + 32;
+  a.res = (int64_t*)d_res;
+  a.done = (uint32_t*)d_done;
+  a.pool = buf->pool;
+  a.ring_lock = ring_lock;
+  a.ring_head = head;
+  a.admit_sem = sem;
+  a.slots = slots;
+  a.active_mask = mask;
+  a.stats = stats;
+  a.status = status;
+  a.nslots = (uint32_t)cfg->nslots;
+  a.admitters = (uint32_t)cfg->admitters;
+  a.chunk_elems = (uint32_t)cfg->chunk_elems;
+  a.timeout_ns = cfg->timeout_ns ? cfg->timeout_ns : 2000000000ull;
+  if (int rc = launch_coresident(serve_kernel, cfg->nblocks, kThreads, 1, 0, st, a)) return rc;
+
+  // The loop is running (or about to): publish requests on their schedule, collect completions.
+  std::this_thread::sleep_for(std::chrono::microseconds(cfg->start_delay_us));
+  const Clock::time_point t0 = Clock::now();
+  std::atomic<int> completed{0};
+  std::atomic<bool> abort_flag{false};
+  std::thread collector(collect, cfg, buf->done, t0, buf->sched_ns, buf->latency_ns, &completed, &abort_flag);
+  const auto deadline = Clock::now() + std::chrono::nanoseconds(buf->sched_ns[cfg->nreq - 1]) +
+                        std::chrono::seconds(cfg->drain_timeout_s);
+  int rc = GSYNC_OK;
+  for (int q = 0; q < cfg->nreq; ++q) {
+    spin_until(t0 + std::chrono::nanoseconds(buf->sched_ns[q]));
+    // The ring slot of request q is reused only after request q - ring_slots completed.
+    while (q - completed.load(std::memory_order_acquire) >= cfg->ring_slots) {
+      if (Clock::now() > deadline) { rc = GSYNC_ETIMEDOUT; break; }
+    }
+    if (rc) break;
+    gsync_serve_req r;
+    r.off = buf->offset[q];
+    r.len = buf->length[q];
+    r.id = (uint32_t)q;
+    r.pad[0] = r.pad[1] = r.pad[2] = 0;
+    buf->ring[q & (cfg->ring_slots - 1)] = r;
+    __atomic_store_n(&buf->ctrl[0], (uint32_t)(q + 1), __ATOMIC_RELEASE);
+  }
+  while (rc == GSYNC_OK && completed.load(std::memory_order_acquire) < cfg->nreq) {
+    if (Clock::now() > deadline) rc = GSYNC_ETIMEDOUT;
+  }
+  abort_flag.store(true);
+  collector.join();
+  __atomic_store_n(&buf->ctrl[32], 1u, __ATOMIC_RELEASE);
+  GSYNC_CUDA(cudaStreamSynchronize(st));
+  uint32_t hstat[4] = {0, 0, 0, 0};
+  GSYNC_CUDA(cudaMemcpy(&hstat[0], stats, 4, cudaMemcpyDeviceToHost));
+  GSYNC_CUDA(cudaMemcpy(&hstat[1], stats + 32, 4, cudaMemcpyDeviceToHost));
+  GSYNC_CUDA(cudaMemcpy(&hstat[2], stats + 64, 4, cudaMemcpyDeviceToHost));
+  GSYNC_CUDA(cudaMemcpy(&hstat[3], status, 4, cudaMemcpyDeviceToHost));
+  buf->stats[0] = hstat[0];
+  buf->stats[1] = hstat[1];
+  buf->stats[2] = hstat[2];
+  buf->stats[3] = hstat[3];
+  if (rc == GSYNC_OK && hstat[3]) rc = GSYNC_ETIMEDOUT;
+  return rc;
+}
+
+extern "C" size_t gsync_serve_baseline_workspace_bytes(int nreq) {
+  if (nreq < 1) return 0;
+  return (size_t)nreq * 16;
+}
+
+extern "C" int gsync_serve_baseline(const gsync_serve_cfg* cfg, gsync_serve_buffers* buf, void* workspace,
+                                    size_t workspace_bytes, void* const* streams, int nstreams) {
+  if (!cfg || !buf || !workspace || cfg->nreq < 1 || cfg->chunk_elems < 1024 || !streams || nstreams < 1 ||
+      workspace_bytes < gsync_serve_baseline_workspace_bytes(cfg->nreq) || !aligned(workspace, 16))
+    return GSYNC_EINVAL;
+  if (!buf->pool || !buf->offset || !buf->length || !buf->sched_ns || !buf->res || !buf->done || !buf->latency_ns)
+    return GSYNC_EINVAL;
+  unsigned long long* acc = (unsigned long long*)workspace;
+  uint32_t* counter = (uint32_t*)(acc + cfg->nreq);
+  GSYNC_CUDA(cudaMemsetAsync(workspace, 0, gsync_serve_baseline_workspace_bytes(cfg->nreq), (cudaStream_t)streams[0]));
+  GSYNC_CUDA(cudaStreamSynchronize((cudaStream_t)streams[0]));
+  for (int q = 0; q < cfg->nreq; ++q) buf->done[q] = 0;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  void *d_res, *d_done;
+  if (int rc = host_dev_ptr(buf->res, &d_res)) return rc;
+  if (int rc = host_dev_ptr((void*)buf->done, &d_done)) return rc;
+  const Clock::time_point t0 = Clock::now();
+  std::atomic<int> completed{0};
+  std::atomic<bool> abort_flag{false};
+  std::thread collector(collect, cfg, buf->done, t0, buf->sched_ns, buf->latency_ns, &completed, &abort_flag);
+  int rc = GSYNC_OK;
+  for (int q = 0; q < cfg->nreq && rc == GSYNC_OK; ++q) {
+    spin_until(t0 + std::chrono::nanoseconds(buf->sched_ns[q]));
+    const int64_t len = buf->length[q];
+    const unsigned nb = (unsigned)((len + cfg->chunk_elems - 1) / cfg->chunk_elems);
+    segsum_kernel<<<nb, kThreads, 0, (cudaStream_t)streams[q % nstreams]>>>(
+        buf->pool, buf->offset[q], len, (uint32_t)cfg->chunk_elems, acc + q, counter + 2 * q, (uint32_t)q,
+        (int64_t*)d_res, (uint32_t*)d_done);
+    if (cudaGetLastError() != cudaSuccess) rc = GSYNC_ECUDA;
+  }
+  const auto deadline = Clock::now() + std::chrono::seconds(cfg->drain_timeout_s);
+  while (rc == GSYNC_OK && completed.load(std::memory_order_acquire) < cfg->nreq) {
+    if (Clock::now() > deadline) rc = GSYNC_ETIMEDOUT;
+  }
+  abort_flag.store(true);
+  collector.join();
+  for (int s = 0; s < nstreams; ++s) GSYNC_CUDA(cudaStreamSynchronize((cudaStream_t)streams[s]));
+  return rc;
+}

@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOTRESIDENT", 3: "ETIMEDOUT", 4: "ECU
 GSYNC_STATUS_TIMEOUT, GSYNC_STATUS_ABORTED, GSYNC_STATUS_VIOLATION, GSYNC_STATUS_CONFIG = 1, 2, 4, 8
 
 MUTEX_KINDS = {"cas_spin": 0, "cas_backoff": 1, "ticket": 2, "sleep_queue": 3}
-BARRIER_KINDS = {"atomic": 0, "flag": 1, "tree": 2, "cluster": 3}
+BARRIER_KINDS = {"atomic": 0, "flag": 1, "tree": 2, "cluster": 3, "sharded": 4}
 SEM_KINDS = {"ticket": 0, "spin": 1, "spin_backoff": 2}
 BACKOFF_EXPONENTIAL, BACKOFF_LINEAR_CYCLIC = 0, 1
 PROBE_OPS = {"volatile_load": 0, "volatile_store": 1, "atomic_read": 2, "atomic_write": 3,
@@ -54,6 +54,35 @@ class gsync_sem_work(ctypes.Structure):
                 ("total", u32p), ("tally", u32p), ("count", u32p), ("status", u32p)]
 
 
+class gsync_batched_work(ctypes.Structure):
+    _fields_ = [("nkeys", ctypes.c_int32), ("nacq", ctypes.c_int32), ("nblocks", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("ngroups", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("cluster", ctypes.c_int32), ("nclasses", ctypes.c_int32), ("plain_launch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("timeout_ns", ctypes.c_uint64),
+                ("mutex_state", u32p), ("key_class", u32p), ("policy", u32p), ("keys", u32p), ("adds", u32p),
+                ("sum", u32p), ("count", u32p), ("group_start", u32p), ("group_size", u32p),
+                ("group_of_block", u32p), ("group_state", u32p), ("slots", u32p), ("mix", u32p), ("bad", u32p),
+                ("status", u32p)]
+
+
+class gsync_serve_req(ctypes.Structure):
+    _fields_ = [("off", ctypes.c_int64), ("len", ctypes.c_int64), ("id", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32 * 3)]
+
+
+class gsync_serve_cfg(ctypes.Structure):
+    _fields_ = [("nreq", ctypes.c_int32), ("nslots", ctypes.c_int32), ("nblocks", ctypes.c_int32),
+                ("admitters", ctypes.c_int32), ("chunk_elems", ctypes.c_int32), ("ring_slots", ctypes.c_int32),
+                ("start_delay_us", ctypes.c_int32), ("drain_timeout_s", ctypes.c_int32),
+                ("timeout_ns", ctypes.c_uint64)]
+
+
+class gsync_serve_buffers(ctypes.Structure):
+    _fields_ = [("pool", u32p), ("offset", u32p), ("length", u32p), ("sched_ns", u32p), ("ring", u32p),
+                ("ctrl", u32p), ("res", u32p), ("done", u32p), ("latency_ns", u32p),
+                ("stats", ctypes.c_uint32 * 4)]
+
+
 # name -> (restype, argtypes)
 _SIG = {
     "gsync_mutex_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
@@ -73,11 +102,19 @@ _SIG = {
     "gsync_bench_barrier": (ctypes.c_int, [u32p, ctypes.POINTER(gsync_barrier_work), u32p]),
     "gsync_bench_barrier_static": (ctypes.c_int, [ctypes.POINTER(gsync_barrier_work), ctypes.c_int, ctypes.c_uint64,
                                                   u32p]),
+    "gsync_probe_barrier_trace": (ctypes.c_int, [u32p, ctypes.POINTER(gsync_barrier_work), u32p, u32p]),
     "gsync_bench_mutex": (ctypes.c_int, [u32p, ctypes.POINTER(gsync_mutex_work), u32p]),
     "gsync_bench_mutex_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "gsync_bench_mutex_host": (ctypes.c_int, [ctypes.POINTER(gsync_mutex_work), ctypes.POINTER(gsync_backoff),
                                               u32p, ctypes.c_size_t, u32p]),
     "gsync_bench_sem": (ctypes.c_int, [u32p, ctypes.POINTER(gsync_sem_work), u32p]),
+    "gsync_bench_batched": (ctypes.c_int, [ctypes.POINTER(gsync_batched_work), u32p]),
+    "gsync_serve_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int]),
+    "gsync_serve_run": (ctypes.c_int, [ctypes.POINTER(gsync_serve_cfg), ctypes.POINTER(gsync_serve_buffers), u32p,
+                                       ctypes.c_size_t, u32p]),
+    "gsync_serve_baseline_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int]),
+    "gsync_serve_baseline": (ctypes.c_int, [ctypes.POINTER(gsync_serve_cfg), ctypes.POINTER(gsync_serve_buffers),
+                                            u32p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
     "gsync_probe_throughput": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, u32p, u32p, u32p]),
     "gsync_probe_latency": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, u32p, u32p, u32p]),
@@ -85,7 +122,15 @@ _SIG = {
     "gsync_probe_nanosleep": (ctypes.c_int, [u32p, ctypes.c_int, ctypes.c_int, u32p, u32p]),
     "gsync_probe_cs": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, u32p, u32p, u32p]),
     "gsync_probe_cs_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
+    "gsync_probe_handoff": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           u32p, u32p, u32p]),
+    "gsync_probe_cluster": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, u32p, u32p]),
+    "gsync_probe_fence": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, u32p, u32p, u32p]),
+    "gsync_probe_sem_cs": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, u32p, u32p, u32p, u32p, u32p]),
 }
+SIGNAL_MODES = {"st_release": 0, "fence_st_relaxed": 1, "st_relaxed": 2, "red_release": 3, "exch_release": 4}
+WAIT_MODES = {"ld_acquire": 0, "ld_relaxed_fence": 1, "ld_relaxed": 2, "ld_relaxed_then_acquire": 3,
+              "ld_volatile_fence": 4, "ld_relaxed_x2": 5}
 
 _lib = None
 
@@ -217,6 +262,29 @@ def gsync_bench_sem(state, work: gsync_sem_work, stream=None) -> int:
     return lib().gsync_bench_sem(ptr(state), ctypes.byref(work), stream_handle(stream))
 
 
+def gsync_bench_batched(work: gsync_batched_work, stream=None) -> int:
+    return lib().gsync_bench_batched(ctypes.byref(work), stream_handle(stream))
+
+
+def gsync_serve_workspace_bytes(nslots: int) -> int:
+    return lib().gsync_serve_workspace_bytes(nslots)
+
+
+def gsync_serve_run(cfg: gsync_serve_cfg, buf: gsync_serve_buffers, workspace, workspace_bytes, stream=None) -> int:
+    return lib().gsync_serve_run(ctypes.byref(cfg), ctypes.byref(buf), ptr(workspace), workspace_bytes,
+                                 stream_handle(stream))
+
+
+def gsync_serve_baseline_workspace_bytes(nreq: int) -> int:
+    return lib().gsync_serve_baseline_workspace_bytes(nreq)
+
+
+def gsync_serve_baseline(cfg: gsync_serve_cfg, buf: gsync_serve_buffers, workspace, workspace_bytes, streams) -> int:
+    arr = (ctypes.c_void_p * len(streams))(*[stream_handle(s) for s in streams])
+    return lib().gsync_serve_baseline(ctypes.byref(cfg), ctypes.byref(buf), ptr(workspace), workspace_bytes, arr,
+                                      len(streams))
+
+
 # ---- probes ---------------------------------------------------------------------------
 
 def gsync_probe_throughput(op, contentious, pre_atomic, nblocks, block_threads, iters, scratch, times,
@@ -243,3 +311,25 @@ def gsync_probe_cs(cs_words, block_threads, iters, scratch, out, stream=None) ->
 
 def gsync_probe_cs_scratch_bytes(cs_words, iters) -> int:
     return lib().gsync_probe_cs_scratch_bytes(cs_words, iters)
+
+
+def gsync_probe_handoff(signal_mode, wait_mode, sm_a, sm_b, iters, scratch, out, stream=None) -> int:
+    return lib().gsync_probe_handoff(signal_mode, wait_mode, sm_a, sm_b, iters, ptr(scratch), ptr(out),
+                                     stream_handle(stream))
+
+
+def gsync_probe_cluster(op, cluster, iters, out, stream=None) -> int:
+    return lib().gsync_probe_cluster(op, cluster, iters, ptr(out), stream_handle(stream))
+
+
+def gsync_probe_fence(op, iters, scratch, out, stream=None) -> int:
+    return lib().gsync_probe_fence(op, iters, ptr(scratch), ptr(out), stream_handle(stream))
+
+
+def gsync_probe_sem_cs(block_threads, iters, hold, addend, scratch, out, stream=None) -> int:
+    return lib().gsync_probe_sem_cs(block_threads, iters, ptr(hold), ptr(addend), ptr(scratch), ptr(out),
+                                    stream_handle(stream))
+
+
+def gsync_probe_barrier_trace(state, work: gsync_barrier_work, trace, stream=None) -> int:
+    return lib().gsync_probe_barrier_trace(ptr(state), ctypes.byref(work), ptr(trace), stream_handle(stream))

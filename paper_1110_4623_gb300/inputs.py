@@ -114,23 +114,37 @@ def log_uniform_int(seed: int, n: int, lo: int, hi: int) -> np.ndarray:
     return np.clip(np.floor(x), lo, hi).astype(np.int64)
 
 
-def barrier_group_sizes(ngroups: int, lo: int, hi: int, grid: int, seed: int = SEED_BATCHED):
+def barrier_group_sizes(ngroups: int, lo: int, hi: int, grid: int, seed: int = SEED_BATCHED,
+                        multiple: int = 1):
     """Drawn group sizes (log-uniform on [lo, hi]) and the sizes rescaled to fit `grid`.
 
-    Rescaling multiplies every drawn size by grid / sum and floors it, with a floor of lo,
-    then trims the largest groups one block at a time until the total fits the grid.
+    Rescaling multiplies every drawn size by grid / sum and floors it to a multiple of
+    `multiple` (the cluster size when the groups use cluster barriers), with a floor of
+    max(lo, multiple); it then trims the largest groups by `multiple` blocks at a time until
+    the total fits the grid.
     """
     drawn = log_uniform_int(seed ^ 0x6A0B5, ngroups, lo, hi)
+    floor_size = max(lo, multiple)
+    floor_size += (-floor_size) % multiple
     total = int(drawn.sum())
-    if total <= grid:
-        return drawn, drawn.copy()
-    used = np.maximum(np.floor(drawn * (grid / total)).astype(np.int64), lo)
+    scale = min(1.0, grid / total)
+    used = np.floor(drawn * scale / multiple).astype(np.int64) * multiple
+    used = np.maximum(used, floor_size)
     while used.sum() > grid:
         j = int(np.argmax(used))
-        if used[j] <= lo:
+        if used[j] - multiple < floor_size:
             raise ValueError("grid too small for the barrier groups")
-        used[j] -= 1
+        used[j] -= multiple
     return drawn, used
+
+
+def group_layout(sizes: np.ndarray, grid: int):
+    """Consecutive group placement from block 0: (start[g], group_of_block[b] or -1)."""
+    start = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int32)
+    gob = np.full(grid, -1, dtype=np.int32)
+    for g, (st, sz) in enumerate(zip(start, sizes)):
+        gob[st:st + sz] = g
+    return start, gob
 
 
 def serve_inputs(nreq: int, pool_elems: int, seed: int = SEED_SERVE,

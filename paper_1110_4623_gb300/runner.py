@@ -61,6 +61,8 @@ class BarrierRun:
             param = 8
         if kind == "cluster" and param == 0:
             param = 2
+        if kind == "sharded" and param == 0:
+            param = min(32, nblocks)
         self.param = param
         nbytes = G.gsync_barrier_bytes(self.k, nblocks, param)
         self.state = _state(nbytes)
@@ -77,6 +79,14 @@ class BarrierRun:
 
     def launch(self, stream=None) -> int:
         return G.gsync_bench_barrier(self.state, self.work, stream)
+
+    def trace(self) -> np.ndarray:
+        """Per-block, per-round (before, after) globaltimer of each barrier_wait: [B, R, 2] ns."""
+        t = torch.zeros(2 * self.nblocks * self.rounds, dtype=torch.int64, device="cuda")
+        self.status.zero_()
+        G.check("gsync_probe_barrier_trace", G.gsync_probe_barrier_trace(self.state, self.work, t))
+        torch.cuda.synchronize()
+        return t.cpu().numpy().reshape(self.nblocks, self.rounds, 2)
 
     def run(self) -> dict:
         self.status.zero_()
@@ -210,6 +220,34 @@ def probe_pingpong(sm_a: int, sm_b: int, iters: int = 2000) -> dict:
     return {"handoff_ns": o[0] / (2 * iters), "status": int(o[3]), "sm_a": int(o[1]), "sm_b": int(o[2])}
 
 
+def probe_handoff(signal: str, wait: str, sm_a: int, sm_b: int, iters: int = 2000) -> dict:
+    scratch = _state(512)
+    out = torch.zeros(4, dtype=torch.int64, device="cuda")
+    G.check("gsync_probe_handoff", G.gsync_probe_handoff(G.SIGNAL_MODES[signal], G.WAIT_MODES[wait], sm_a, sm_b,
+                                                         iters, scratch, out))
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    return {"handoff_ns": o[0] / (2 * iters), "status": int(o[3])}
+
+
+def probe_cluster(op: int, cluster: int, iters: int = 2000) -> dict:
+    out = torch.zeros(4, dtype=torch.int64, device="cuda")
+    G.check("gsync_probe_cluster", G.gsync_probe_cluster(op, cluster, iters, out))
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    per = o[0] / iters if op == 0 else o[0] / (2 * iters)
+    return {"ns": per, "status": int(o[3])}
+
+
+def probe_fence(op: int, iters: int = 2000) -> dict:
+    scratch = _state(1024)
+    out = torch.zeros(2, dtype=torch.int64, device="cuda")
+    G.check("gsync_probe_fence", G.gsync_probe_fence(op, iters, scratch, out))
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    return {"ns_per_fence": o[0] / iters, "cycles_per_fence": o[1] / iters}
+
+
 def probe_nanosleep(req_ns, iters: int = 64) -> np.ndarray:
     req = _u32(np.asarray(req_ns, dtype=np.uint32))
     out = torch.zeros(len(req_ns), dtype=torch.int64, device="cuda")
@@ -226,7 +264,157 @@ def probe_cs(cs_words: int, block_threads: int = 256, iters: int = 20000) -> dic
     return {"ns_per_cs": out[0] / iters}
 
 
+def probe_sem_cs(hold: np.ndarray | None, addend: np.ndarray | None, block_threads: int = 128,
+                 iters: int | None = None) -> dict:
+    """Mean time of one semaphore critical section with the workload's hold times, alone
+    (hold and addend None: the frame alone, with an empty critical section)."""
+    iters = iters if iters is not None else len(hold)
+    h = _u32(hold) if hold is not None else None
+    a = _u32(addend) if addend is not None else None
+    scratch = _state(1024)
+    out = (G.ctypes.c_uint64 * 1)()
+    G.check("gsync_probe_sem_cs", G.gsync_probe_sem_cs(block_threads, iters, h, a, scratch, out))
+    return {"ns_per_cs": out[0] / iters}
+
+
 def sm_count() -> int:
     rc, n = G.gsync_device_sm_count()
     G.check("gsync_device_sm_count", rc)
     return n
+
+
+class BatchedRun:
+    """The batched many-mutex workload (gsync_bench_batched): 4096 mutexes with Zipf keys,
+    barrier groups, a per-class policy table; optional capture into a CUDA graph."""
+
+    def __init__(self, keys: np.ndarray, adds: np.ndarray, nkeys: int, nblocks: int, group_sizes: np.ndarray,
+                 rounds: int, key_class: np.ndarray, nclasses: int, block_threads: int = 128, cluster: int = 1,
+                 timeout_ns: int = 10_000_000_000, plain_launch: bool = False):
+        from .inputs import group_layout
+        self.nkeys, self.nacq, self.nblocks = nkeys, len(keys), nblocks
+        self.group_sizes = np.asarray(group_sizes, dtype=np.int32)
+        self.rounds, self.cluster = rounds, cluster
+        start, gob = group_layout(self.group_sizes, nblocks)
+        self.group_start, self.group_of_block = start, gob
+        ng = len(self.group_sizes)
+        self.mutex_state = torch.zeros(nkeys * 384, dtype=torch.uint8, device="cuda")
+        self.group_state = torch.zeros(max(ng, 1) * 384, dtype=torch.uint8, device="cuda")
+        self.key_class = torch.from_numpy(np.ascontiguousarray(key_class, dtype=np.uint8)).cuda()
+        self.policy = torch.zeros(nclasses * 4, dtype=torch.int32, device="cuda")
+        self.keys = torch.from_numpy(np.ascontiguousarray(keys, dtype=np.int32)).cuda()
+        self.adds = torch.from_numpy(np.ascontiguousarray(adds, dtype=np.int64)).cuda()
+        self.sum = torch.zeros(nkeys, dtype=torch.int64, device="cuda")
+        self.count = _zeros(nkeys)
+        self.gstart = torch.from_numpy(np.ascontiguousarray(start, dtype=np.int32)).cuda() if ng else _zeros(1)
+        self.gsize = torch.from_numpy(self.group_sizes).cuda() if ng else _zeros(1)
+        self.gob = torch.from_numpy(gob).cuda()
+        self.slots = _zeros(2 * nblocks)
+        self.mix = _zeros(nblocks)
+        self.bad = _zeros(nblocks)
+        self.status = _zeros(1)
+        self.work = G.gsync_batched_work(nkeys, self.nacq, nblocks, block_threads, ng, rounds, cluster, nclasses,
+                                         int(plain_launch), 0, timeout_ns, G.ptr(self.mutex_state),
+                                         G.ptr(self.key_class), G.ptr(self.policy), G.ptr(self.keys),
+                                         G.ptr(self.adds), G.ptr(self.sum), G.ptr(self.count), G.ptr(self.gstart),
+                                         G.ptr(self.gsize), G.ptr(self.gob), G.ptr(self.group_state),
+                                         G.ptr(self.slots), G.ptr(self.mix), G.ptr(self.bad), G.ptr(self.status))
+        self.graph = None
+
+    def set_policy(self, table):
+        """table: list of (kind, min_ns, max_ns) per class.  Zeroes the mutexes (kinds may change)."""
+        flat = []
+        for kind, mn, mx in table:
+            flat += [G.MUTEX_KINDS[kind] if isinstance(kind, str) else int(kind), int(mn), int(mx), 0]
+        self.policy.copy_(torch.tensor(flat, dtype=torch.int32))
+        self.mutex_state.zero_()
+        self.graph = None
+
+    def reset(self):
+        self.sum.zero_()
+        self.count.zero_()
+        self.status.zero_()
+
+    def launch(self, stream=None) -> int:
+        return G.gsync_bench_batched(self.work, stream)
+
+    def capture(self) -> None:
+        """Captures reset + launch into one CUDA graph (replayed by replay())."""
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.reset()
+            G.check("gsync_bench_batched", self.launch())  # warm-up outside the graph
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            self.reset()
+            rc = self.launch()
+        G.check("gsync_bench_batched (capture)", rc)
+        self.graph = g
+
+    def replay(self):
+        self.graph.replay()
+
+    def results(self) -> dict:
+        torch.cuda.synchronize()
+        return {"status": int(_np(self.status)[0]), "sum": self.sum.cpu().numpy(),
+                "count": self.count.cpu().numpy().view(np.uint32).astype(np.uint64),
+                "mix": _np(self.mix), "bad": _np(self.bad)}
+
+    def run(self) -> dict:
+        self.reset()
+        rc = self.launch()
+        out = self.results()
+        out["rc"] = rc
+        return out
+
+
+class ServeRun:
+    """The serving workload: a device value pool, request descriptors and Poisson arrival times,
+    run through the persistent loop (gsync_serve_run) or one launch per request
+    (gsync_serve_baseline).  Pinned host buffers carry the ring, results and flags."""
+
+    def __init__(self, offset, length, sched_ns, pool: torch.Tensor, nslots: int = 32, nblocks: int = 304,
+                 admitters: int = 8, chunk_elems: int = 32768, ring_slots: int = 65536, timeout_ns: int = 0,
+                 drain_timeout_s: int = 30):
+        self.nreq = len(offset)
+        self.offset = np.ascontiguousarray(offset, dtype=np.int64)
+        self.length = np.ascontiguousarray(length, dtype=np.int64)
+        self.sched = np.ascontiguousarray(sched_ns, dtype=np.int64)
+        self.pool = pool
+        self.cfg = G.gsync_serve_cfg(self.nreq, nslots, nblocks, admitters, chunk_elems, ring_slots, 2000,
+                                     drain_timeout_s, timeout_ns)
+        self.ring = torch.zeros(ring_slots * 32, dtype=torch.uint8).pin_memory()
+        self.ctrl = torch.zeros(64, dtype=torch.int32).pin_memory()
+        self.res = torch.zeros(self.nreq, dtype=torch.int64).pin_memory()
+        self.done = torch.zeros(self.nreq, dtype=torch.int32).pin_memory()
+        self.latency = np.zeros(self.nreq, dtype=np.int64)
+        self.ws_bytes = G.gsync_serve_workspace_bytes(nslots)
+        self.ws = torch.zeros(max(self.ws_bytes, 256), dtype=torch.uint8, device="cuda")
+        self.bws_bytes = G.gsync_serve_baseline_workspace_bytes(self.nreq)
+        self.bws = torch.zeros(self.bws_bytes, dtype=torch.uint8, device="cuda")
+
+    def _buffers(self):
+        return G.gsync_serve_buffers(G.ptr(self.pool), self.offset.ctypes.data, self.length.ctypes.data,
+                                     self.sched.ctypes.data, G.ptr(self.ring), G.ptr(self.ctrl), G.ptr(self.res),
+                                     G.ptr(self.done), self.latency.ctypes.data, (G.ctypes.c_uint32 * 4)())
+
+    def _out(self, rc, buf, wall):
+        return {"rc": rc, "res": self.res.numpy().copy(), "latency_ns": self.latency.copy(),
+                "stats": list(buf.stats), "wall_s": wall}
+
+    def run(self) -> dict:
+        import time
+        buf = self._buffers()
+        t0 = time.perf_counter()
+        rc = G.gsync_serve_run(self.cfg, buf, self.ws, self.ws_bytes)
+        return self._out(rc, buf, time.perf_counter() - t0)
+
+    def baseline(self, nstreams: int = 4) -> dict:
+        import time
+        streams = [torch.cuda.Stream() for _ in range(nstreams)]
+        buf = self._buffers()
+        t0 = time.perf_counter()
+        rc = G.gsync_serve_baseline(self.cfg, buf, self.bws, self.bws_bytes, streams)
+        return self._out(rc, buf, time.perf_counter() - t0)

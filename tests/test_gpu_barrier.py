@@ -14,13 +14,15 @@ def _gpu():
 
 
 KINDS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("tree", 2), ("cluster", 2), ("cluster", 4),
-         ("cluster", 8)]
+         ("cluster", 8), ("sharded", 32), ("sharded", 8), ("sharded", 1)]
 
 
 @pytest.mark.parametrize("kind,param", KINDS)
 def test_config1_full_fold_10000_rounds(kind, param):
     # 16 blocks x 128 threads, 10,000 rounds; per-round XOR checksum of all 16 slots.
     from paper_1110_4623_gb300 import runner
+    if kind == "sharded":
+        param = min(param, 16)
     got = runner.BarrierRun(kind, 16, 128, 10_000, full=True, param=param).run()
     want = calc.barrier_full(16, 10_000)
     assert got["rc"] == 0 and got["status"] == 0, got["status"]
@@ -44,10 +46,12 @@ def test_sampled_sweep_1000_rounds(kind, param, nblocks):
     assert np.array_equal(got["mix"], want["mix"])
 
 
-@pytest.mark.parametrize("kind,param", [("atomic", 0), ("flag", 0), ("tree", 3), ("cluster", 1)])
+@pytest.mark.parametrize("kind,param", [("atomic", 0), ("flag", 0), ("tree", 3), ("cluster", 1), ("sharded", 3)])
 @pytest.mark.parametrize("nblocks,threads", [(1, 32), (2, 64), (37, 96), (151, 256)])
 def test_ragged_grids_full_fold(kind, param, nblocks, threads):
     from paper_1110_4623_gb300 import runner
+    if kind == "sharded":
+        param = min(param, nblocks)
     got = runner.BarrierRun(kind, nblocks, threads, 300, full=True, param=param).run()
     want = calc.barrier_full(nblocks, 300)
     assert got["rc"] == 0 and got["status"] == 0

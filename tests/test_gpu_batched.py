@@ -1,0 +1,99 @@
+"""Batched many-mutex kernel on the GPU against the oracle: per-key int64 sums and counts
+exact (mutex definition applied to 4096 instances), and every barrier group's sampled slot
+check exact (barrier definition applied per group)."""
+import numpy as np
+import pytest
+
+from gpu_util import require_gpu
+from oracle import calc
+from paper_1110_4623_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+NKEYS, NB = 4096, 1184
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def make(nacq, cluster=1, rounds=100, policy=None, plain_launch=False):
+    from paper_1110_4623_gb300 import autotune
+    keys, adds, _ = inputs.batched_inputs(nacq, NKEYS, 1.1)
+    cls = autotune.classify_keys(keys, NKEYS, NB)
+    run = autotune.make_run(keys, adds, NKEYS, NB, 64, rounds, cluster, cls, plain_launch=plain_launch)
+    run.set_policy(policy or autotune.DEFAULT_POLICY)
+    return run, keys, adds
+
+
+def check(run, keys, adds, got, rounds):
+    want = calc.batched_final(keys, adds, NKEYS)
+    assert got["status"] == 0, got["status"]
+    assert np.array_equal(got["sum"], want["sum"])
+    assert np.array_equal(got["count"], want["count"])
+    assert not got["bad"].any()
+    for g, (st, sz) in enumerate(zip(run.group_start, run.group_sizes)):
+        assert np.array_equal(got["mix"][st:st + sz], calc.barrier_sampled(int(sz), rounds)["mix"]), g
+    covered = int(run.group_sizes.sum())
+    assert not got["mix"][covered:].any()
+
+
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8])
+def test_full_size_one_million_acquisitions(cluster):
+    run, keys, adds = make(1_000_000, cluster=cluster)
+    got = run.run()
+    assert got["rc"] == 0
+    check(run, keys, adds, got, 100)
+
+
+@pytest.mark.parametrize("policy", [[("cas_spin", 0, 0)] * 3, [("cas_backoff", 64, 2048)] * 3,
+                                    [("ticket", 128, 4000)] * 3,
+                                    [("ticket", 0, 0), ("cas_backoff", 32, 1024), ("cas_spin", 0, 0)]])
+def test_policies(policy):
+    run, keys, adds = make(200_000, policy=policy, rounds=37)
+    got = run.run()
+    assert got["rc"] == 0
+    check(run, keys, adds, got, 37)
+
+
+def test_graph_capture_replays_exactly():
+    import torch
+    run, keys, adds = make(300_000, rounds=20, plain_launch=True)
+    run.capture()
+    for _ in range(2):
+        run.replay()
+        torch.cuda.synchronize()
+        check(run, keys, adds, run.results(), 20)
+
+
+def test_cooperative_launch_in_capture_or_refused_cleanly():
+    # Either the cooperative launch captures and replays exactly, or capture is refused with
+    # an error status and the context stays usable.
+    import torch
+    from paper_1110_4623_gb300 import gsync as G
+    run, keys, adds = make(100_000, rounds=10)
+    try:
+        run.capture()
+    except G.GsyncError:
+        torch.cuda.synchronize()
+        got = run.run()
+        check(run, keys, adds, got, 10)
+        return
+    run.replay()
+    torch.cuda.synchronize()
+    check(run, keys, adds, run.results(), 10)
+
+
+def test_misaligned_cluster_groups_are_refused_on_device():
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import autotune, runner
+    keys, adds, _ = inputs.batched_inputs(50_000, NKEYS, 1.1)
+    cls = autotune.classify_keys(keys, NKEYS, NB)
+    sizes = np.array([6, 10, 3, 8], dtype=np.int32)  # not multiples of 4
+    run = runner.BatchedRun(keys, adds, NKEYS, NB, sizes, 10, cls, 3, cluster=4)
+    run.set_policy(autotune.DEFAULT_POLICY)
+    got = run.run()
+    assert got["rc"] == 0 and got["status"] & G.GSYNC_STATUS_CONFIG
+    want = calc.batched_final(keys, adds, NKEYS)
+    assert np.array_equal(got["sum"], want["sum"])  # the lock work still completes

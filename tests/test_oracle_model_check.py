@@ -32,6 +32,10 @@ CORRECT = [
     ("tree_barrier_3", mc.TreeBarrier(fan=2), 3, 2),
     ("tree_barrier_4", mc.TreeBarrier(fan=2), 4, 2),
     ("cluster_barrier", mc.ClusterBarrier(c=2), 4, 2),
+    ("sharded_barrier_2", mc.ShardedBarrier(shards=2), 3, 3),
+    ("sharded_barrier_3", mc.ShardedBarrier(shards=3), 4, 2),
+    ("sharded_barrier_1", mc.ShardedBarrier(shards=1), 3, 2),
+    ("sharded_barrier_wrap", mc.ShardedBarrier(shards=2, base=2 ** 32 - 1), 3, 3),
 ]
 
 
@@ -49,6 +53,8 @@ BROKEN = [
     ("sleep_sem_turn_ge", mc.SleepSem(n=1, broken="turn_ge"), 3, 1, "critical section"),
     ("barrier_no_wait", mc.AtomicBarrier(broken="no_wait"), 3, 1, "passed round"),
     ("flag_skip_last", mc.FlagBarrier(broken="skip_last"), 3, 1, "passed round"),
+    ("sharded_early", mc.ShardedBarrier(shards=2, broken="early"), 3, 1, "passed round"),
+    ("sharded_counts_master", mc.ShardedBarrier(shards=2, broken="counts_master"), 3, 1, "final state"),
 ]
 
 
