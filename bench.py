@@ -37,7 +37,7 @@ SEM_THREADS, SEM_PAIRS, SEM_COUNTS = 128, 200, (1, 4, 16, 64)
 # Library defaults for GB300, chosen from 1184-block sweeps (the paper's API serves the
 # fastest implementation of each primitive for the GPU as the default, Section 5 "API").
 DEFAULT_MUTEX = "ticket"
-DEFAULT_BARRIER = ("sharded", 32)
+DEFAULT_BARRIER = ("atomic", 0)
 BARRIERS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("cluster", 2), ("cluster", 4), ("cluster", 8),
             ("sharded", 32), ("sharded", 8)]
 # Backoff (min_ns, max_ns) per kind; the ticket kinds sleep min_ns per waiter ahead, capped.

@@ -288,17 +288,21 @@ int gsync_bench_batched(const gsync_batched_work* w, void* stream);
  * (host threads inside the call) publishes request q into the ring at time sched_ns[q]
  * after the start and records latency_ns[q] = the host time its completion flag was first
  * seen minus sched_ns[q] (open loop: latency counts from the scheduled arrival).
- *  - On the device, `admitters` blocks take request indices under the ring's ticket lock,
- *    wait on the admission semaphore (n = nslots in-flight requests), claim a free slot and
- *    publish the request; every other block claims chunks of chunk_elems values of any
- *    active request; the block that finishes a request's last chunk writes res[q] and
- *    done[q] = 1 into pinned host memory, frees the slot and posts the semaphore.
- *  - ring (ring_slots descriptors, a power of two), ctrl (64 words: ctrl[0] tail, ctrl[32]
- *    shutdown), res (nreq x i64) and done (nreq x u32) are caller-owned pinned host memory
+ *  - On the device, each of the `admitters` blocks first waits on the admission semaphore
+ *    (n = nslots in-flight requests), then takes the next request index under the ring's
+ *    ticket lock, then waits for that ring entry to be published, claims a free slot and
+ *    publishes the request in it; every other block claims chunks of chunk_elems values of
+ *    any active request; the block that finishes a request's last chunk writes res[q] and
+ *    done[q] = 1 into pinned host memory, frees the slot and posts the semaphore.  The
+ *    semaphore and the lock are taken before the request arrives, off its latency path.
+ *  - ring (ring_slots entries of 128 bytes, ring_slots a power of two), ctrl (64 words:
+ *    ctrl[32] = shutdown), res
+ *    (nreq x i64) and done (nreq x u32) are caller-owned pinned host memory
  *    (cudaHostAlloc or registered); pool is device memory; offset, length, sched_ns and
  *    latency_ns are ordinary host arrays.  workspace (device, 256-byte aligned) holds
  *    gsync_serve_workspace_bytes(nslots) bytes.
- *  - Requires 1 <= length[q] and at most 65535 chunks per request, nslots <= 64.
+ *  - Requires 0 <= offset[q], 1 <= length[q], offset[q] + length[q] <= pool_elems <= 2^32,
+ *    at most 65535 chunks per request, nslots <= 64, non-decreasing sched_ns.
  *  - Returns GSYNC_ETIMEDOUT if not every request completed within drain_timeout_s after the
  *    last scheduled arrival, or if a device wait timed out (stats[3] = device status).
  *    Synchronizes `stream` before returning.
@@ -306,11 +310,15 @@ int gsync_bench_batched(const gsync_batched_work* w, void* stream);
  * j; the last block writes res and done), issued at the scheduled times round-robin over
  * `nstreams` caller streams, completions observed the same way.  workspace: device, 16-byte
  * aligned, gsync_serve_baseline_workspace_bytes(nreq) bytes. */
+/* One ring entry (16 bytes), at the start of its own 128-byte line of the ring (entry i at
+ * byte 128 * i).  Request q is in the ring when seq == seq_check == q + 1; the host writes
+ * len, off and seq_check first and seq last with a release store, and the device reads the
+ * entry with one 16-byte acquire load. */
 typedef struct gsync_serve_req {
-  int64_t off;
-  int64_t len;
-  uint32_t id;
-  uint32_t pad[3];
+  uint32_t seq;
+  uint32_t len;
+  uint32_t off;
+  uint32_t seq_check;
 } gsync_serve_req;
 typedef struct gsync_serve_cfg {
   int32_t nreq, nslots, nblocks, admitters, chunk_elems, ring_slots;
@@ -319,6 +327,7 @@ typedef struct gsync_serve_cfg {
 } gsync_serve_cfg;
 typedef struct gsync_serve_buffers {
   const int32_t* pool;
+  int64_t pool_elems; /* every request must satisfy 0 <= offset, offset + length <= pool_elems */
   const int64_t* offset;
   const int64_t* length;
   const int64_t* sched_ns;
@@ -327,6 +336,9 @@ typedef struct gsync_serve_buffers {
   int64_t* res;
   uint32_t* done;
   int64_t* latency_ns;
+  uint64_t* trace;   /* optional (device, 4 x nreq u64, or NULL): %globaltimer when request q's
+                        entry was seen, its slot published, its first chunk claimed, its last
+                        chunk finished (persistent loop only) */
   uint32_t stats[4]; /* out: requests admitted, chunks processed, requests completed, device status */
 } gsync_serve_buffers;
 size_t gsync_serve_workspace_bytes(int nslots);
@@ -335,6 +347,13 @@ int gsync_serve_run(const gsync_serve_cfg* cfg, gsync_serve_buffers* buf, void* 
 size_t gsync_serve_baseline_workspace_bytes(int nreq);
 int gsync_serve_baseline(const gsync_serve_cfg* cfg, gsync_serve_buffers* buf, void* workspace,
                          size_t workspace_bytes, void* const* streams, int nstreams);
+
+/* Host <-> device hand-off probe: one GPU thread and one host thread ping-pong a counter
+ * through two words of pinned host memory (`words`, 64 u32, caller-owned, from cudaHostAlloc)
+ * with system-scope release stores and acquire loads, `iters` times.  out_ns[0] (host) =
+ * elapsed host ns for the whole exchange (one hand-off = out_ns[0] / (2 * iters)).
+ * Synchronizes `stream`. */
+int gsync_probe_host_pingpong(uint32_t* words, int iters, uint64_t* out_ns, void* stream);
 
 /* ------------------------------------------------------------------------------------ */
 /* Memory-system probes (Section 3, "Benchmarks"; Section 4 machine abstraction).        */

@@ -416,7 +416,7 @@ __device__ __forceinline__ int sem_post(const SemRef& s) {
 // ATOMIC : line 1 arrival counter, line 2 release epoch.
 // FLAG   : lines 1.. arrival flags (one word per block, packed), then release flags (one
 //          word per block, packed; mode 1: a single release word on its own line).  At most
-//          8192 blocks, and blockDim.x >= 32 (warp 0 of block 0 gathers the flags).
+//          8192 blocks; the master block's threads gather the flags.
 // TREE   : line 1 release epoch, lines 2.. one counter line per tree node (fan-in = param).
 // SHARDED: lines 1..S: S = param arrival counters (block b counts into counter b mod S with a
 //          fire-and-forget red.release; counters only grow, so after crossing e counter s
@@ -564,47 +564,51 @@ __device__ __forceinline__ int barrier_wait(BarrierRef& b) {
     }
   } else {  // GSYNC_BAR_FLAG: decentralized XF barrier, block 0 is the master block
     if (blockIdx.x == 0) {
-      // Warp 0 of the master block gathers every arrival flag with 16-byte relaxed loads, all
-      // of a lane's pending vectors in flight at once (lane l owns vectors l, l+32, ...; at most
-      // 64 per lane, so n <= 8192).  The flag arrays span whole lines, so a vector never leaves
-      // them; word 0 (the master's own flag) and words past n are ignored.  Relaxed loads
-      // pipeline (acquire loads would complete one at a time); each lane then fences to
-      // acquire what it saw, and after __syncwarp fences again so that its release-flag
-      // stores also release what the other lanes saw.
-      if (threadIdx.x < 32 && threadIdx.y == 0 && threadIdx.z == 0) {
-        const uint32_t lane = threadIdx.x;
-        const uint32_t nvec = (b.n + 3u) >> 2;
-        const uint32_t kmax = lane < nvec ? min(64u, (nvec - lane + 31u) / 32u) : 0u;
-        uint64_t pending = kmax == 64u ? ~0ull : ((1ull << kmax) - 1ull);
-        Waiter w;
-        int rc = GSYNC_OK;
+      // Every thread of the master block watches its share of the arrival flags as 16-byte
+      // vectors (thread t: vectors t, t + nthr, ...).  Each pass issues a thread's pending
+      // loads back to back (2 in flight, neither waiting on the other) before it checks them,
+      // so a pass costs about one L2 round trip.  The flag arrays span whole lines, so a
+      // vector never leaves them; word 0 (the master's own flag) and words past n are
+      // ignored.  Each thread then fences to acquire what it saw, the block agrees that all
+      // arrived, and each thread fences again before writing its share of the release flags.
+      const uint32_t tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+      const uint32_t nthr = blockDim.x * blockDim.y * blockDim.z;
+      const uint32_t nvec = (b.n + 3u) >> 2;
+      Waiter w;
+      int rc = GSYNC_OK;
+      for (uint32_t v0 = tid; v0 < nvec && rc == GSYNC_OK; v0 += 2u * nthr) {
+        uint32_t pending = 0;
+        for (uint32_t k = 0; k < 2u; ++k)
+          if (v0 + k * nthr < nvec) pending |= 1u << k;
         while (pending) {
-          uint64_t still = 0;
-          for (uint32_t k = 0; k < kmax; ++k) {
-            if (!((pending >> k) & 1ull)) continue;
-            const uint32_t v = lane + 32u * k;
-            const uint4 x = ptx::ld_relaxed_v4(b.arrive_flags() + 4u * v);
-            const uint32_t base = 4u * v;
-            const bool ok = (base == 0u || base >= b.n || x.x == e1) && (base + 1u >= b.n || x.y == e1) &&
-                            (base + 2u >= b.n || x.z == e1) && (base + 3u >= b.n || x.w == e1);
-            if (!ok) still |= 1ull << k;
+          uint4 x[2];
+#pragma unroll
+          for (uint32_t k = 0; k < 2u; ++k)
+            if ((pending >> k) & 1u) x[k] = ptx::ld_relaxed_v4(b.arrive_flags() + 4u * (v0 + k * nthr));
+          uint32_t still = 0;
+#pragma unroll
+          for (uint32_t k = 0; k < 2u; ++k) {
+            if (!((pending >> k) & 1u)) continue;
+            const uint32_t base = 4u * (v0 + k * nthr);
+            const bool ok = (base == 0u || base >= b.n || x[k].x == e1) && (base + 1u >= b.n || x[k].y == e1) &&
+                            (base + 2u >= b.n || x[k].z == e1) && (base + 3u >= b.n || x[k].w == e1);
+            if (!ok) still |= 1u << k;
           }
           pending = still;
           if (pending && (rc = w.tick(b.timeout_ns, b.abort_word())) != GSYNC_OK) break;
         }
-        ptx::fence_acq_rel();  // acquire: what this lane's relaxed loads observed
-        const int worst = __reduce_max_sync(0xFFFFFFFFu, rc);
-        __syncwarp();
-        if (worst == GSYNC_OK) {
-          ptx::fence_acq_rel();  // release: every lane's acquisitions precede the release flags
-          if (b.mode) {
-            if (lane == 0) ptx::st_relaxed(b.release_flags(), e1);
-          } else {
-            for (uint32_t v = lane; v < nvec; v += 32u) ptx::st_relaxed_v4(b.release_flags() + 4u * v, e1);
-          }
-        }
-        if (lane == 0) s_rc = worst;
       }
+      ptx::fence_acq_rel();  // acquire: what this thread's relaxed loads observed
+      const int any_bad = __syncthreads_or(rc != GSYNC_OK);
+      if (!any_bad) {
+        ptx::fence_acq_rel();  // release: every thread's acquisitions precede the release flags
+        if (b.mode) {
+          if (master) ptx::st_relaxed(b.release_flags(), e1);
+        } else {
+          for (uint32_t v = tid; v < nvec; v += nthr) ptx::st_relaxed_v4(b.release_flags() + 4u * v, e1);
+        }
+      }
+      if (master) s_rc = !any_bad ? GSYNC_OK : (rc != GSYNC_OK ? rc : GSYNC_EABORTED);
     } else if (master) {
       ptx::st_release(b.arrive_flags() + blockIdx.x, e1);
       uint32_t* rel = b.mode ? b.release_flags() : b.release_flags() + blockIdx.x;

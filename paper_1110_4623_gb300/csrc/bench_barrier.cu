@@ -20,10 +20,11 @@ namespace {
 
 constexpr int kMaxThreads = 256;
 
-// The full-fold variant reduces three values per round and needs more than 32 registers;
-// at 128 threads per block it still fits 8 blocks per SM.
+// Register budget: the full-fold variant reduces three values per round (64 registers); the
+// sampled variant's flag gather keeps two 16-byte vectors in flight (42 registers).  Both
+// still fit 8 blocks of 128 threads per SM, the shape of the 1184-block workloads.
 template <int KIND, bool FULL, bool TRACE = false>
-__global__ void __launch_bounds__(kMaxThreads, FULL ? 4 : 8)
+__global__ void __launch_bounds__(kMaxThreads, FULL ? 4 : 6)
     barrier_workload_kernel(uint32_t* state, int rounds, uint32_t* slots, uint32_t* chk, uint32_t* mix_out,
                             uint32_t* bad_out, uint32_t* status, uint64_t* trace = nullptr) {
   gsync::BarrierRef bar = gsync::barrier_attach(state);

@@ -2,11 +2,13 @@
 // sleeping semaphore (the paper motivates its primitives with task queues, Section 1, and
 // names hardware enqueue/dequeue as a wish, Section 7).
 //
-// The host publishes requests into a ring of descriptors in pinned host memory (tail word
-// written with a release store).  Inside one co-resident launch:
-//   * admitter blocks take the next request index under the ring's ticket lock, wait on the
-//     admission semaphore (n = number of in-flight slots), claim a free slot, and publish the
-//     request in it (generation-tagged chunk counter, release store of the slot state);
+// The host publishes requests into a ring of 16-byte entries in pinned host memory (each
+// entry carries its sequence number, written last with a release store).  Inside one
+// co-resident launch:
+//   * admitter blocks wait on the admission semaphore (n = number of in-flight slots), take
+//     the next request index under the ring's ticket lock, wait for that entry to appear,
+//     claim a free slot and publish the request in it (generation-tagged chunk counter,
+//     release store of the slot state);
 //   * every other block claims chunks of any active slot (compare-and-swap on the slot's
 //     generation:chunk counter), sums the chunk's int32 values in int64, adds the partial to
 //     the slot's accumulator; the block that finishes a request's last chunk writes the result
@@ -17,6 +19,11 @@
 //
 // The per-request-launch baseline runs the same chunked segmented sum as one kernel launch
 // per request and completes it the same way (result and flag in pinned host memory).
+#include <pthread.h>
+#include <sched.h>
+#include <string.h>
+#include <unistd.h>
+
 #include <atomic>
 #include <chrono>
 #include <thread>
@@ -30,14 +37,20 @@ namespace ptx = gsync::ptx;
 namespace {
 
 constexpr int kThreads = 256;
+// Ring entries sit one per 128-byte line, so the host writing entry q never touches a line
+// that an admitter polls for another entry.
+constexpr size_t kRingStride = 128;
+// The active mask is kept in kMaskCopies copies on separate lines (set and cleared in all,
+// read from one per worker) to spread the workers' polling.
+constexpr uint32_t kMaskCopies = 4;
 
-struct Slot {  // one 128-byte line
+struct Slot {  // one 128-byte line; the first 16 bytes are everything a chunk claim reads
   uint32_t state;       // 0 free, 1 claimed by an admitter, 2 active
   uint32_t gen;         // bumped every time the slot takes a request
   uint32_t next_chunk;  // (gen & 0xFFFF) << 16 | next chunk to hand out
+  uint32_t nchunks;
   uint32_t done_chunks;
   uint32_t id;
-  uint32_t nchunks;
   int64_t off;
   int64_t len;
   unsigned long long acc;
@@ -48,8 +61,8 @@ static_assert(sizeof(Slot) == 128, "one line per slot");
 struct Args {
   const gsync_serve_req* ring;  // device view of the host ring
   uint32_t ring_mask;
-  const uint32_t* tail;      // device view (host writes)
   const uint32_t* shutdown;  // device view (host writes)
+  uint32_t* dev_shutdown;    // device copy of the shutdown word, set by an admitter (own line)
   int64_t* res;              // device view of host results
   uint32_t* done;            // device view of host completion flags
   const int32_t* pool;
@@ -60,6 +73,7 @@ struct Args {
   uint32_t* active_mask;     // one bit per slot (nslots <= 64)
   uint32_t* stats;           // [0] admitted, [32] chunks, [64] completed (own lines)
   uint32_t* status;
+  unsigned long long* trace;  // optional per-request timestamps (4 per request)
   uint32_t nslots, admitters, chunk_elems;
   uint64_t timeout_ns;
 };
@@ -67,6 +81,14 @@ struct Args {
 __device__ __forceinline__ uint32_t ld_acquire_sys(const uint32_t* p) {
   uint32_t v;
   asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint4 ld_acquire_sys_v4(const void* p) {
+  uint4 v;
+  asm volatile("ld.acquire.sys.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p)
+               : "memory");
   return v;
 }
 __device__ __forceinline__ void st_release_sys(uint32_t* p, uint32_t v) {
@@ -81,8 +103,10 @@ __device__ __forceinline__ uint32_t atom_cas_relaxed(uint32_t* p, uint32_t cmp, 
   return r;
 }
 
-// Block-wide int64 sum of pool[a, b): 16-byte loads over the aligned middle, scalars at the ends.
+// Block-wide int64 sum of pool[a, b): 16-byte streaming loads over the aligned middle, eight
+// of them in flight per thread (issued before any is added), scalars at the ends.
 __device__ __forceinline__ long long block_sum(const int32_t* pool, int64_t a, int64_t b) {
+  constexpr int kInFlight = 8;
   long long s = 0;
   int64_t a4 = (a + 3) & ~(int64_t)3;
   if (a4 > b) a4 = b;
@@ -90,7 +114,16 @@ __device__ __forceinline__ long long block_sum(const int32_t* pool, int64_t a, i
   for (int64_t i = a + threadIdx.x; i < a4; i += blockDim.x) s += pool[i];
   const int4* v = reinterpret_cast<const int4*>(pool + a4);
   const int64_t nv = (b4 - a4) >> 2;
-  for (int64_t i = threadIdx.x; i < nv; i += blockDim.x) {
+  const int64_t step = (int64_t)blockDim.x * kInFlight;
+  int64_t i = threadIdx.x;
+  for (; i + (kInFlight - 1) * (int64_t)blockDim.x < nv; i += step) {
+    int4 x[kInFlight];
+#pragma unroll
+    for (int k = 0; k < kInFlight; ++k) x[k] = __ldcs(v + i + k * (int64_t)blockDim.x);
+#pragma unroll
+    for (int k = 0; k < kInFlight; ++k) s += (long long)x[k].x + x[k].y + x[k].z + x[k].w;
+  }
+  for (; i < nv; i += blockDim.x) {
     const int4 x = __ldcs(v + i);
     s += (long long)x.x + x.y + x.z + x.w;
   }
@@ -107,17 +140,20 @@ __device__ __forceinline__ long long block_sum(const int32_t* pool, int64_t a, i
   return t;  // valid in thread 0
 }
 
-// Thread 0: claims one chunk of slot s, or returns false.
-__device__ bool claim_chunk(Slot* slot, uint32_t& chunk, uint32_t& gen) {
-  if (ptx::ld_acquire(&slot->state) != 2u) return false;
-  gen = ptx::ld_relaxed(&slot->gen);
-  const uint32_t n = ptx::ld_relaxed(&slot->nchunks);
-  uint32_t v = ptx::ld_relaxed(&slot->next_chunk);
+// Thread 0: claims one chunk of slot s, or returns false.  One 16-byte acquire load reads
+// the state, generation, chunk counter and chunk count together.
+__device__ bool claim_chunk(Slot* slot, uint32_t& chunk, uint32_t& gen, bool& last) {
+  const uint4 h = gsync::ptx::ld_acquire_v4(&slot->state);
+  if (h.x != 2u) return false;
+  gen = h.y;
+  const uint32_t n = h.w;
+  uint32_t v = h.z;
   for (int tries = 0; tries < 64; ++tries) {
     if ((v >> 16) != (gen & 0xFFFFu) || (v & 0xFFFFu) >= n) return false;
     const uint32_t old = atom_cas_relaxed(&slot->next_chunk, v, v + 1u);
     if (old == v) {
       chunk = v & 0xFFFFu;
+      last = chunk + 1u == n;
       return true;
     }
     v = old;
@@ -137,63 +173,71 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(Args a) {
   uint64_t idle_since = 0;
 
   if (admitter) {
-    // Admitters: ring -> semaphore -> slot.  Thread 0 does everything; the block only idles.
+    // Admitters: semaphore -> ring index (ticket lock) -> wait for that entry -> slot.  The
+    // permit and the index are taken before the request exists, so its arrival only waits
+    // for one read of host memory.  Thread 0 does everything; the block only idles.
     if (tid == 0) {
       for (;;) {
-        // 1. wait for a request beyond the shared head, or for shutdown
-        uint32_t polls = 0;
-        const uint64_t t0 = ptx::globaltimer();
-        bool stop = false;
-        uint32_t tail_seen = 0;
-        for (;;) {
-          const uint32_t head = ptx::ld_relaxed(a.ring_head);
-          tail_seen = ld_acquire_sys(a.tail);
-          if ((int32_t)(tail_seen - head) > 0) break;
-          if ((++polls & 15u) == 0) {
-            if (ld_acquire_sys(a.shutdown)) { stop = true; break; }
-            if (ptx::globaltimer() - t0 > a.timeout_ns * 16) { record_status(a.status, GSYNC_ETIMEDOUT); stop = true; break; }
-          }
-          __nanosleep(200);
-        }
-        if (stop) break;
-        // 2. admission: one in-flight slot
+        if (ptx::ld_relaxed(a.dev_shutdown)) break;
         int rc = gsync::sem_wait_thread<GSYNC_SEM_TICKET>(sem);
         if (rc != GSYNC_OK) { record_status(a.status, rc); break; }
-        // 3. take the next request index under the ring lock
+        if (ptx::ld_relaxed(a.dev_shutdown)) {  // pass the permit on so blocked admitters exit too
+          gsync::sem_post_thread<GSYNC_SEM_TICKET>(sem);
+          break;
+        }
         const gsync::Token t = gsync::mutex_lock_thread<GSYNC_MUTEX_TICKET>(lock);
         if (t.status != GSYNC_OK) { record_status(a.status, t.status); break; }
-        // The tail only grows, so the value seen above (acquired before this point) still
-        // bounds what may be taken; no second round trip to host memory inside the lock.
-        const uint32_t head = ptx::ld_relaxed(a.ring_head);
-        const bool have = (int32_t)(tail_seen - head) > 0;
-        if (have) ptx::st_relaxed(a.ring_head, head + 1u);
+        const uint32_t h = ptx::ld_relaxed(a.ring_head);
+        ptx::st_relaxed(a.ring_head, h + 1u);
         gsync::mutex_unlock_thread<GSYNC_MUTEX_TICKET>(lock, t.ticket);
-        if (!have) {  // another admitter took it: give the permit back
-          gsync::sem_post_thread<GSYNC_SEM_TICKET>(sem);
-          continue;
+        // wait for entry h (seq == seq_check == h + 1) or shutdown
+        const gsync_serve_req* e =
+            (const gsync_serve_req*)((const char*)a.ring + (size_t)(h & a.ring_mask) * kRingStride);
+        uint4 v;
+        uint32_t polls = 0;
+        bool stop = false;
+        const uint64_t t0 = ptx::globaltimer();
+        for (;;) {
+          v = ld_acquire_sys_v4(e);
+          if (v.x == h + 1u && v.w == h + 1u) break;
+          if ((++polls & 15u) == 0) {
+            if (ld_acquire_sys(a.shutdown)) {
+              ptx::st_release(a.dev_shutdown, 1u);
+              stop = true;
+              break;
+            }
+            if (ptx::globaltimer() - t0 > a.timeout_ns * 16) { record_status(a.status, GSYNC_ETIMEDOUT); stop = true; break; }
+          }
         }
-        // 4. read the descriptor (stable until this request completes) and claim a free slot
-        const gsync_serve_req req = a.ring[head & a.ring_mask];
-        uint32_t s = head % a.nslots;
+        if (stop) {  // the permit goes back so that admitters blocked on it can see shutdown
+          gsync::sem_post_thread<GSYNC_SEM_TICKET>(sem);
+          break;
+        }
+        const uint32_t req_len = v.y, req_off = v.z, req_id = h;
+        if (a.trace) a.trace[4ull * req_id] = ptx::globaltimer();
+        // claim a free slot (the permit guarantees one)
+        uint32_t s = h % a.nslots;
         bool got = false;
-        for (uint32_t k = 0; k < 4u * a.nslots && !got; ++k, s = (s + 1u) % a.nslots)
-          got = atom_cas_relaxed(&a.slots[s].state, 0u, 1u) == 0u;
+        for (uint32_t k = 0; k < 4u * a.nslots; ++k) {
+          if (ptx::atom_cas_acquire(&a.slots[s].state, 0u, 1u) == 0u) { got = true; break; }
+          s = (s + 1u) % a.nslots;
+        }
         if (!got) { record_status(a.status, GSYNC_ETIMEDOUT); break; }
-        s = (s + a.nslots - 1u) % a.nslots;
         Slot* sl = &a.slots[s];
         const uint32_t gen = sl->gen + 1u;
-        const uint32_t nch = (uint32_t)((req.len + a.chunk_elems - 1) / a.chunk_elems);
+        const uint32_t nch = (req_len + a.chunk_elems - 1u) / a.chunk_elems;
         sl->gen = gen;
-        sl->id = req.id;
-        sl->off = req.off;
-        sl->len = req.len;
+        sl->id = req_id;
+        sl->off = (int64_t)req_off;
+        sl->len = (int64_t)req_len;
         sl->nchunks = nch == 0 ? 1u : nch;
         sl->acc = 0ull;
         sl->done_chunks = 0u;
         sl->next_chunk = (gen & 0xFFFFu) << 16;
         ptx::st_release(&sl->state, 2u);
-        atomicOr(&a.active_mask[s >> 5], 1u << (s & 31));
+        for (uint32_t m = 0; m < kMaskCopies; ++m) atomicOr(&a.active_mask[32u * m + (s >> 5)], 1u << (s & 31));
         ptx::red_add_relaxed(a.stats, 1u);
+        if (a.trace) a.trace[4ull * req_id + 1] = ptx::globaltimer();
       }
     }
     return;
@@ -203,19 +247,26 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(Args a) {
   for (;;) {
     if (tid == 0) {
       s_cmd = 2;  // nothing yet
-      const uint32_t m0 = ptx::ld_relaxed(a.active_mask), m1 = a.nslots > 32 ? ptx::ld_relaxed(a.active_mask + 1) : 0u;
+      const uint32_t* my_mask = a.active_mask + 32u * (blockIdx.x % kMaskCopies);
+      const uint32_t m0 = ptx::ld_relaxed(my_mask), m1 = a.nslots > 32 ? ptx::ld_relaxed(my_mask + 1) : 0u;
       const uint64_t mask = ((uint64_t)m1 << 32) | m0;
       if (mask) {
         for (uint32_t k = 0; k < a.nslots; ++k) {
           const uint32_t s = (scan + k) % a.nslots;
           if (!((mask >> s) & 1ull)) continue;
           uint32_t c, g;
-          if (claim_chunk(&a.slots[s], c, g)) {
+          bool last;
+          if (claim_chunk(&a.slots[s], c, g, last)) {
+            // The last chunk is handed out: the slot has no more work to find, so it leaves the
+            // active mask now (it cannot be reused before this chunk completes).
+            if (last)
+              for (uint32_t m = 0; m < kMaskCopies; ++m) atomicAnd(&a.active_mask[32u * m + (s >> 5)], ~(1u << (s & 31)));
             Slot* sl = &a.slots[s];
             const int64_t lo = sl->off + (int64_t)c * a.chunk_elems;
             int64_t hi = lo + a.chunk_elems;
             if (hi > sl->off + sl->len) hi = sl->off + sl->len;
             s_slot = s; s_chunk = c; s_gen = g; s_lo = lo; s_hi = hi;
+            if (a.trace && c == 0) a.trace[4ull * sl->id + 2] = ptx::globaltimer();
             s_cmd = 0;
             scan = s;
             break;
@@ -223,13 +274,14 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(Args a) {
         }
       }
       if (s_cmd == 2) {
-        if ((++idle & 63u) == 0) {
+        if ((idle & 15u) == 15u && ptx::ld_relaxed(a.dev_shutdown)) s_cmd = 1;
+        if ((++idle & 255u) == 0) {
           if (ld_acquire_sys(a.shutdown)) s_cmd = 1;
           const uint64_t now = ptx::globaltimer();
           if (idle_since == 0) idle_since = now;
           else if (now - idle_since > a.timeout_ns * 16) { record_status(a.status, GSYNC_ETIMEDOUT); s_cmd = 1; }
         }
-        if (s_cmd == 2) __nanosleep(256);
+        if (s_cmd == 2) __nanosleep(32);
       } else {
         idle = 0;
         idle_since = 0;
@@ -248,9 +300,9 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(Args a) {
       if (d == sl->nchunks) {
         const long long total = (long long)atomicAdd(&sl->acc, 0ull);
         const uint32_t id = sl->id;
+        if (a.trace) a.trace[4ull * id + 3] = ptx::globaltimer();
         st_relaxed_sys_s64(a.res + id, total);
         st_release_sys(a.done + id, 1u);
-        atomicAnd(&a.active_mask[s_slot >> 5], ~(1u << (s_slot & 31)));
         ptx::st_release(&sl->state, 0u);
         gsync::sem_post_thread<GSYNC_SEM_TICKET>(sem);
         ptx::red_add_relaxed(a.stats + 64, 1u);
@@ -287,6 +339,17 @@ int host_dev_ptr(void* host, void** dev) {
 
 using Clock = std::chrono::steady_clock;
 
+// Pins a host thread to one core (counted from the last core down) so that the producer and
+// the collector are not descheduled behind each other.  Best effort: ignored on failure.
+void pin_to_core_from_end(std::thread& t, int k) {
+  const long n = sysconf(_SC_NPROCESSORS_ONLN);
+  if (n < 4) return;
+  cpu_set_t set;
+  CPU_ZERO(&set);
+  CPU_SET((int)(n - 1 - k), &set);
+  (void)pthread_setaffinity_np(t.native_handle(), sizeof(set), &set);
+}
+
 int64_t now_ns(Clock::time_point t0) {
   return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - t0).count();
 }
@@ -318,12 +381,23 @@ void collect(const gsync_serve_cfg* cfg, volatile uint32_t* done, Clock::time_po
   }
 }
 
+// Every request must lie inside the pool and fit the chunk counter.
+int check_requests(const gsync_serve_cfg* cfg, const gsync_serve_buffers* buf) {
+  for (int q = 0; q < cfg->nreq; ++q) {
+    const int64_t o = buf->offset[q], n = buf->length[q];
+    if (o < 0 || n < 1 || o > buf->pool_elems - n) return GSYNC_EINVAL;
+    if ((n + cfg->chunk_elems - 1) / cfg->chunk_elems > 0xFFFF) return GSYNC_EINVAL;
+    if (q > 0 && buf->sched_ns[q] < buf->sched_ns[q - 1]) return GSYNC_EINVAL;
+  }
+  return GSYNC_OK;
+}
+
 }  // namespace
 
 extern "C" size_t gsync_serve_workspace_bytes(int nslots) {
   if (nslots < 1 || nslots > 64) return 0;
-  return 3 * 128 /* ring lock */ + 128 /* head */ + 4 * 128 /* semaphore */ + (size_t)nslots * 128 + 128 /* mask */ +
-         3 * 128 /* stats */ + 128 /* status */;
+  return 3 * 128 /* ring lock */ + 128 /* head */ + 4 * 128 /* semaphore */ + (size_t)nslots * 128 +
+         128 * kMaskCopies /* active mask */ + 3 * 128 /* stats */ + 128 /* status */ + 128 /* device shutdown */;
 }
 
 extern "C" int gsync_serve_run(const gsync_serve_cfg* cfg, gsync_serve_buffers* buf, void* workspace,
@@ -336,26 +410,30 @@ extern "C" int gsync_serve_run(const gsync_serve_cfg* cfg, gsync_serve_buffers* 
   if (!buf->pool || !buf->offset || !buf->length || !buf->sched_ns || !buf->ring || !buf->ctrl || !buf->res ||
       !buf->done || !buf->latency_ns)
     return GSYNC_EINVAL;
-  for (int q = 0; q < cfg->nreq; ++q)
-    if (buf->length[q] < 1 || (buf->length[q] + cfg->chunk_elems - 1) / cfg->chunk_elems > 0xFFFF) return GSYNC_EINVAL;
+  if (int rc = check_requests(cfg, buf)) return rc;
+  if (buf->pool_elems > (int64_t)0xFFFFFFFFll) return GSYNC_EINVAL;  // 32-bit offsets in the ring
   cudaStream_t st = (cudaStream_t)stream;
   char* p = (char*)workspace;
   uint32_t* ring_lock = (uint32_t*)p; p += 3 * 128;
   uint32_t* head = (uint32_t*)p;      p += 128;
   uint32_t* sem = (uint32_t*)p;       p += 4 * 128;
   Slot* slots = (Slot*)p;             p += (size_t)cfg->nslots * 128;
-  uint32_t* mask = (uint32_t*)p;      p += 128;
+  uint32_t* mask = (uint32_t*)p;      p += 128 * kMaskCopies;
   uint32_t* stats = (uint32_t*)p;     p += 3 * 128;
-  uint32_t* status = (uint32_t*)p;
+  uint32_t* status = (uint32_t*)p;    p += 128;
+  uint32_t* dev_shutdown = (uint32_t*)p;
   GSYNC_CUDA(cudaMemsetAsync(workspace, 0, gsync_serve_workspace_bytes(cfg->nslots), st));
-  if (int rc = gsync_mutex_init(ring_lock, 3 * 128, GSYNC_MUTEX_TICKET, 1, nullptr, cfg->timeout_ns, stream)) return rc;
+  // Admitters may legitimately wait for a permit or an index while arrivals are sparse: the
+  // lock and the semaphore get 16x the per-wait bound.
+  const uint64_t wait_ns = (cfg->timeout_ns ? cfg->timeout_ns : 2000000000ull) * 16;
+  if (int rc = gsync_mutex_init(ring_lock, 3 * 128, GSYNC_MUTEX_TICKET, 1, nullptr, wait_ns, stream)) return rc;
   gsync_backoff sbo = {GSYNC_BACKOFF_EXPONENTIAL, 64, 2000, 0};
-  if (int rc = gsync_sem_init(sem, 4 * 128, GSYNC_SEM_TICKET, cfg->nslots, &sbo, cfg->timeout_ns, stream)) return rc;
+  if (int rc = gsync_sem_init(sem, 4 * 128, GSYNC_SEM_TICKET, cfg->nslots, &sbo, wait_ns, stream)) return rc;
 
-  // Host control words: ctrl[0] = tail, ctrl[32] = shutdown (separate lines).
+  // Host control word ctrl[32] = shutdown; the ring starts empty (no entry has a valid seq).
   volatile uint32_t* ctrl = buf->ctrl;
-  ctrl[0] = 0;
   ctrl[32] = 0;
+  memset(buf->ring, 0, kRingStride * (size_t)cfg->ring_slots);
   for (int q = 0; q < cfg->nreq; ++q) buf->done[q] = 0;
   std::atomic_thread_fence(std::memory_order_seq_cst);
 
@@ -367,8 +445,8 @@ extern "C" int gsync_serve_run(const gsync_serve_cfg* cfg, gsync_serve_buffers* 
   if (int rc = host_dev_ptr((void*)buf->done, &d_done)) return rc;
   a.ring = (const gsync_serve_req*)d_ring;
   a.ring_mask = (uint32_t)cfg->ring_slots - 1u;
-  a.tail = (const uint32_t*)d_ctrl;
   a.shutdown = (const uint32_t*)d_ctrl + 32;
+  a.dev_shutdown = dev_shutdown;
   a.res = (int64_t*)d_res;
   a.done = (uint32_t*)d_done;
   a.pool = buf->pool;
@@ -379,6 +457,7 @@ extern "C" int gsync_serve_run(const gsync_serve_cfg* cfg, gsync_serve_buffers* 
   a.active_mask = mask;
   a.stats = stats;
   a.status = status;
+  a.trace = (unsigned long long*)buf->trace;
   a.nslots = (uint32_t)cfg->nslots;
   a.admitters = (uint32_t)cfg->admitters;
   a.chunk_elems = (uint32_t)cfg->chunk_elems;
@@ -391,28 +470,40 @@ extern "C" int gsync_serve_run(const gsync_serve_cfg* cfg, gsync_serve_buffers* 
   std::atomic<int> completed{0};
   std::atomic<bool> abort_flag{false};
   std::thread collector(collect, cfg, buf->done, t0, buf->sched_ns, buf->latency_ns, &completed, &abort_flag);
+  pin_to_core_from_end(collector, 1);
   const auto deadline = Clock::now() + std::chrono::nanoseconds(buf->sched_ns[cfg->nreq - 1]) +
                         std::chrono::seconds(cfg->drain_timeout_s);
-  int rc = GSYNC_OK;
-  for (int q = 0; q < cfg->nreq; ++q) {
-    spin_until(t0 + std::chrono::nanoseconds(buf->sched_ns[q]));
-    // The ring slot of request q is reused only after request q - ring_slots completed.
-    while (q - completed.load(std::memory_order_acquire) >= cfg->ring_slots) {
-      if (Clock::now() > deadline) { rc = GSYNC_ETIMEDOUT; break; }
+  // The producer runs on its own pinned core too; this thread only waits.
+  std::atomic<int> prod_rc{GSYNC_OK};
+  std::thread producer([&]() {
+    for (int q = 0; q < cfg->nreq; ++q) {
+      spin_until(t0 + std::chrono::nanoseconds(buf->sched_ns[q]));
+      // The ring entry of request q is reused only after request q - ring_slots completed.
+      while (q - completed.load(std::memory_order_acquire) >= cfg->ring_slots) {
+        if (Clock::now() > deadline || abort_flag.load(std::memory_order_relaxed)) {
+          prod_rc.store(GSYNC_ETIMEDOUT);
+          return;
+        }
+      }
+      gsync_serve_req* e = (gsync_serve_req*)((char*)buf->ring + (size_t)(q & (cfg->ring_slots - 1)) * kRingStride);
+      e->len = (uint32_t)buf->length[q];
+      e->off = (uint32_t)buf->offset[q];
+      e->seq_check = (uint32_t)(q + 1);
+      __atomic_store_n(&e->seq, (uint32_t)(q + 1), __ATOMIC_RELEASE);
     }
-    if (rc) break;
-    gsync_serve_req r;
-    r.off = buf->offset[q];
-    r.len = buf->length[q];
-    r.id = (uint32_t)q;
-    r.pad[0] = r.pad[1] = r.pad[2] = 0;
-    buf->ring[q & (cfg->ring_slots - 1)] = r;
-    __atomic_store_n(&buf->ctrl[0], (uint32_t)(q + 1), __ATOMIC_RELEASE);
-  }
-  while (rc == GSYNC_OK && completed.load(std::memory_order_acquire) < cfg->nreq) {
-    if (Clock::now() > deadline) rc = GSYNC_ETIMEDOUT;
+  });
+  pin_to_core_from_end(producer, 0);
+  int rc = GSYNC_OK;
+  while (completed.load(std::memory_order_acquire) < cfg->nreq) {
+    if (Clock::now() > deadline || prod_rc.load() != GSYNC_OK) {
+      rc = GSYNC_ETIMEDOUT;
+      break;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
   abort_flag.store(true);
+  producer.join();
+  if (rc == GSYNC_OK) rc = prod_rc.load();
   collector.join();
   __atomic_store_n(&buf->ctrl[32], 1u, __ATOMIC_RELEASE);
   GSYNC_CUDA(cudaStreamSynchronize(st));
@@ -441,6 +532,7 @@ extern "C" int gsync_serve_baseline(const gsync_serve_cfg* cfg, gsync_serve_buff
     return GSYNC_EINVAL;
   if (!buf->pool || !buf->offset || !buf->length || !buf->sched_ns || !buf->res || !buf->done || !buf->latency_ns)
     return GSYNC_EINVAL;
+  if (int rc = check_requests(cfg, buf)) return rc;
   unsigned long long* acc = (unsigned long long*)workspace;
   uint32_t* counter = (uint32_t*)(acc + cfg->nreq);
   GSYNC_CUDA(cudaMemsetAsync(workspace, 0, gsync_serve_baseline_workspace_bytes(cfg->nreq), (cudaStream_t)streams[0]));
@@ -454,22 +546,89 @@ extern "C" int gsync_serve_baseline(const gsync_serve_cfg* cfg, gsync_serve_buff
   std::atomic<int> completed{0};
   std::atomic<bool> abort_flag{false};
   std::thread collector(collect, cfg, buf->done, t0, buf->sched_ns, buf->latency_ns, &completed, &abort_flag);
-  int rc = GSYNC_OK;
-  for (int q = 0; q < cfg->nreq && rc == GSYNC_OK; ++q) {
-    spin_until(t0 + std::chrono::nanoseconds(buf->sched_ns[q]));
-    const int64_t len = buf->length[q];
-    const unsigned nb = (unsigned)((len + cfg->chunk_elems - 1) / cfg->chunk_elems);
-    segsum_kernel<<<nb, kThreads, 0, (cudaStream_t)streams[q % nstreams]>>>(
-        buf->pool, buf->offset[q], len, (uint32_t)cfg->chunk_elems, acc + q, counter + 2 * q, (uint32_t)q,
-        (int64_t*)d_res, (uint32_t*)d_done);
-    if (cudaGetLastError() != cudaSuccess) rc = GSYNC_ECUDA;
-  }
+  pin_to_core_from_end(collector, 1);
+  int dev = 0;
+  GSYNC_CUDA(cudaGetDevice(&dev));
+  std::atomic<int> launch_rc{GSYNC_OK};
+  // The launching loop runs on its own pinned core, like the persistent loop's producer.
+  std::thread launcher([&]() {
+    if (cudaSetDevice(dev) != cudaSuccess) {
+      launch_rc.store(GSYNC_ECUDA);
+      return;
+    }
+    for (int q = 0; q < cfg->nreq; ++q) {
+      spin_until(t0 + std::chrono::nanoseconds(buf->sched_ns[q]));
+      const int64_t len = buf->length[q];
+      const unsigned nb = (unsigned)((len + cfg->chunk_elems - 1) / cfg->chunk_elems);
+      segsum_kernel<<<nb, kThreads, 0, (cudaStream_t)streams[q % nstreams]>>>(
+          buf->pool, buf->offset[q], len, (uint32_t)cfg->chunk_elems, acc + q, counter + 2 * q, (uint32_t)q,
+          (int64_t*)d_res, (uint32_t*)d_done);
+      if (cudaGetLastError() != cudaSuccess) {
+        launch_rc.store(GSYNC_ECUDA);
+        return;
+      }
+    }
+  });
+  pin_to_core_from_end(launcher, 0);
+  launcher.join();
+  int rc = launch_rc.load();
   const auto deadline = Clock::now() + std::chrono::seconds(cfg->drain_timeout_s);
   while (rc == GSYNC_OK && completed.load(std::memory_order_acquire) < cfg->nreq) {
     if (Clock::now() > deadline) rc = GSYNC_ETIMEDOUT;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
   abort_flag.store(true);
   collector.join();
   for (int s = 0; s < nstreams; ++s) GSYNC_CUDA(cudaStreamSynchronize((cudaStream_t)streams[s]));
   return rc;
+}
+
+namespace {
+
+__global__ void host_pingpong_kernel(uint32_t* words, int iters, uint32_t* status) {
+  // words[0]: device -> host, words[32]: host -> device (separate lines).
+  const uint64_t deadline = ptx::globaltimer() + 2000000000ull;
+  for (int i = 1; i <= iters; ++i) {
+    st_release_sys(words, (uint32_t)i);
+    uint32_t polls = 0;
+    while (ld_acquire_sys(words + 32) != (uint32_t)i) {
+      if ((++polls & 63u) == 0 && ptx::globaltimer() > deadline) {
+        *status = 1;
+        st_release_sys(words, 0xFFFFFFFFu);  // tells the host thread to stop
+        return;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" int gsync_probe_host_pingpong(uint32_t* words, int iters, uint64_t* out_ns, void* stream) {
+  if (!words || !out_ns || iters < 1) return GSYNC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  void* dwords = nullptr;
+  if (int rc = host_dev_ptr(words, &dwords)) return rc;
+  volatile uint32_t* w = words;
+  w[0] = 0;
+  w[32] = 0;
+  w[48] = 0;  // device-side status word
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  host_pingpong_kernel<<<1, 1, 0, st>>>((uint32_t*)dwords, iters, (uint32_t*)dwords + 48);
+  GSYNC_CUDA(cudaGetLastError());
+  const auto deadline = Clock::now() + std::chrono::seconds(5);
+  Clock::time_point t0 = Clock::now();
+  bool ok = true;
+  for (int i = 1; i <= iters && ok; ++i) {
+    uint32_t v;
+    while ((v = __atomic_load_n(&words[0], __ATOMIC_ACQUIRE)) != (uint32_t)i) {
+      if (v == 0xFFFFFFFFu || Clock::now() > deadline) { ok = false; break; }
+    }
+    if (i == 1) t0 = Clock::now();
+    __atomic_store_n(&words[32], (uint32_t)i, __ATOMIC_RELEASE);
+  }
+  const auto t1 = Clock::now();
+  GSYNC_CUDA(cudaStreamSynchronize(st));
+  if (!ok || w[48]) return GSYNC_ETIMEDOUT;
+  out_ns[0] = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(t1 - t0).count();
+  return GSYNC_OK;
 }

@@ -66,8 +66,8 @@ class gsync_batched_work(ctypes.Structure):
 
 
 class gsync_serve_req(ctypes.Structure):
-    _fields_ = [("off", ctypes.c_int64), ("len", ctypes.c_int64), ("id", ctypes.c_uint32),
-                ("pad", ctypes.c_uint32 * 3)]
+    _fields_ = [("seq", ctypes.c_uint32), ("len", ctypes.c_uint32), ("off", ctypes.c_uint32),
+                ("seq_check", ctypes.c_uint32)]
 
 
 class gsync_serve_cfg(ctypes.Structure):
@@ -78,8 +78,9 @@ class gsync_serve_cfg(ctypes.Structure):
 
 
 class gsync_serve_buffers(ctypes.Structure):
-    _fields_ = [("pool", u32p), ("offset", u32p), ("length", u32p), ("sched_ns", u32p), ("ring", u32p),
-                ("ctrl", u32p), ("res", u32p), ("done", u32p), ("latency_ns", u32p),
+    _fields_ = [("pool", u32p), ("pool_elems", ctypes.c_int64), ("offset", u32p), ("length", u32p),
+                ("sched_ns", u32p), ("ring", u32p),
+                ("ctrl", u32p), ("res", u32p), ("done", u32p), ("latency_ns", u32p), ("trace", u32p),
                 ("stats", ctypes.c_uint32 * 4)]
 
 
@@ -113,6 +114,7 @@ _SIG = {
     "gsync_serve_run": (ctypes.c_int, [ctypes.POINTER(gsync_serve_cfg), ctypes.POINTER(gsync_serve_buffers), u32p,
                                        ctypes.c_size_t, u32p]),
     "gsync_serve_baseline_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int]),
+    "gsync_probe_host_pingpong": (ctypes.c_int, [u32p, ctypes.c_int, u32p, u32p]),
     "gsync_serve_baseline": (ctypes.c_int, [ctypes.POINTER(gsync_serve_cfg), ctypes.POINTER(gsync_serve_buffers),
                                             u32p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
     "gsync_probe_throughput": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -333,3 +335,7 @@ def gsync_probe_sem_cs(block_threads, iters, hold, addend, scratch, out, stream=
 
 def gsync_probe_barrier_trace(state, work: gsync_barrier_work, trace, stream=None) -> int:
     return lib().gsync_probe_barrier_trace(ptr(state), ctypes.byref(work), ptr(trace), stream_handle(stream))
+
+
+def gsync_probe_host_pingpong(words, iters, out_ns, stream=None) -> int:
+    return lib().gsync_probe_host_pingpong(ptr(words), iters, ptr(out_ns), stream_handle(stream))

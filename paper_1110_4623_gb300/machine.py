@@ -1,0 +1,77 @@
+"""Machine abstraction of the GPU this runs on (Section 3 "Benchmarks", Section 4 "Machine
+Abstraction"), measured with the library's probe kernels.
+
+measure_table() times the paper's probe matrix: one master thread per block issues `iters`
+accesses -- volatile or atomic, read or write, to one shared word (contentious) or to its own
+word 256 bytes from the next block's (noncontentious), and the volatile ones also after one
+preceding atomic -- on a saturated grid.  ratios() turns those times into the paper's two
+ratio tables, abstraction() into its three parameters, and design() into the choice of
+primitive each parameter set favours.
+"""
+from __future__ import annotations
+
+from . import runner
+
+ROWS = ("cont_volatile", "noncont_volatile", "cont_atomic", "noncont_atomic",
+        "cont_vol_after_atomic", "noncont_vol_after_atomic")
+# (probe op for reads, probe op for writes, contentious, preceded by one atomic)
+_PROBES = {
+    "cont_volatile": ("volatile_load", "volatile_store", True, False),
+    "noncont_volatile": ("volatile_load", "volatile_store", False, False),
+    "cont_atomic": ("atomic_read", "atomic_write", True, False),
+    "noncont_atomic": ("atomic_read", "atomic_write", False, False),
+    "cont_vol_after_atomic": ("volatile_load", "volatile_store", True, True),
+    "noncont_vol_after_atomic": ("volatile_load", "volatile_store", False, True),
+}
+
+
+def measure_table(nblocks: int, block_threads: int = 128, iters: int = 1000, reps: int = 3) -> dict:
+    """{(row, 'read'|'write'): milliseconds} for the paper's twelve + four probes."""
+    out = {}
+    for row, (rd, wr, cont, pre) in _PROBES.items():
+        for d, op in (("read", rd), ("write", wr)):
+            ns = sorted(runner.probe_throughput(op, cont, pre, nblocks, block_threads, iters)["ns"] for _ in range(reps))
+            out[(row, d)] = ns[len(ns) // 2] / 1e6
+    return out
+
+
+def ratios(t: dict) -> tuple[dict, dict]:
+    """Table 2 (contentious / noncontentious) and Table 3 (against the volatile access of the
+    same contention), per access direction."""
+    t2, t3 = {}, {}
+    for d in ("read", "write"):
+        t2[("volatile", d)] = t[("cont_volatile", d)] / t[("noncont_volatile", d)]
+        t2[("atomic", d)] = t[("cont_atomic", d)] / t[("noncont_atomic", d)]
+        t2[("vol_after_atomic", d)] = t[("cont_vol_after_atomic", d)] / t[("noncont_vol_after_atomic", d)]
+        t3[("cont_atomic", d)] = t[("cont_atomic", d)] / t[("cont_volatile", d)]
+        t3[("noncont_atomic", d)] = t[("noncont_atomic", d)] / t[("noncont_volatile", d)]
+        t3[("cont_vol_after_atomic", d)] = t[("cont_vol_after_atomic", d)] / t[("cont_volatile", d)]
+        t3[("noncont_vol_after_atomic", d)] = t[("noncont_vol_after_atomic", d)] / t[("noncont_volatile", d)]
+    return t2, t3
+
+
+# Thresholds of the reading of Section 4: a preceding atomic that slows contentious volatile
+# accesses by more than 1.5x holds the line hostage; contentious atomics more than 20x slower
+# than volatile accesses make every spinning design prohibitive.
+HOSTAGE_THRESHOLD = 1.5
+PROHIBITIVE_ATOMIC_RATIO = 20.0
+
+
+def abstraction(t: dict) -> dict:
+    t2, t3 = ratios(t)
+    return {
+        "atomic_volatile": max(t3[("cont_atomic", "read")], t3[("cont_atomic", "write")]),
+        "atomic_volatile_read": t3[("cont_atomic", "read")],
+        "cont_noncont_volatile": max(t2[("volatile", "read")], t2[("volatile", "write")]),
+        "line_hostage": max(t3[("cont_vol_after_atomic", "read")], t3[("cont_vol_after_atomic", "write")])
+        > HOSTAGE_THRESHOLD,
+    }
+
+
+def design(params: dict) -> dict:
+    """The Section 4 strategy for a parameter set (Section 6's best-per-GPU table)."""
+    if params["atomic_volatile"] > PROHIBITIVE_ATOMIC_RATIO:
+        return {"barrier": "flag", "mutex": "ticket", "sem_low": "ticket", "sem_high": "ticket"}
+    if params["line_hostage"]:
+        return {"barrier": "flag", "mutex": "cas_backoff", "sem_low": "spin_backoff", "sem_high": "ticket"}
+    return {"barrier": "flag", "mutex": "cas_backoff", "sem_low": "ticket", "sem_high": "ticket"}

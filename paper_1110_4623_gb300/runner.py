@@ -385,7 +385,7 @@ class ServeRun:
         self.pool = pool
         self.cfg = G.gsync_serve_cfg(self.nreq, nslots, nblocks, admitters, chunk_elems, ring_slots, 2000,
                                      drain_timeout_s, timeout_ns)
-        self.ring = torch.zeros(ring_slots * 32, dtype=torch.uint8).pin_memory()
+        self.ring = torch.zeros(ring_slots * 128, dtype=torch.uint8).pin_memory()
         self.ctrl = torch.zeros(64, dtype=torch.int32).pin_memory()
         self.res = torch.zeros(self.nreq, dtype=torch.int64).pin_memory()
         self.done = torch.zeros(self.nreq, dtype=torch.int32).pin_memory()
@@ -394,15 +394,26 @@ class ServeRun:
         self.ws = torch.zeros(max(self.ws_bytes, 256), dtype=torch.uint8, device="cuda")
         self.bws_bytes = G.gsync_serve_baseline_workspace_bytes(self.nreq)
         self.bws = torch.zeros(self.bws_bytes, dtype=torch.uint8, device="cuda")
+        self.trace = None
 
     def _buffers(self):
-        return G.gsync_serve_buffers(G.ptr(self.pool), self.offset.ctypes.data, self.length.ctypes.data,
+        return G.gsync_serve_buffers(G.ptr(self.pool), self.pool.numel(), self.offset.ctypes.data,
+                                     self.length.ctypes.data,
                                      self.sched.ctypes.data, G.ptr(self.ring), G.ptr(self.ctrl), G.ptr(self.res),
-                                     G.ptr(self.done), self.latency.ctypes.data, (G.ctypes.c_uint32 * 4)())
+                                     G.ptr(self.done), self.latency.ctypes.data, G.ptr(self.trace),
+                                     (G.ctypes.c_uint32 * 4)())
 
     def _out(self, rc, buf, wall):
         return {"rc": rc, "res": self.res.numpy().copy(), "latency_ns": self.latency.copy(),
                 "stats": list(buf.stats), "wall_s": wall}
+
+    def enable_trace(self):
+        self.trace = torch.zeros(4 * self.nreq, dtype=torch.int64, device="cuda")
+
+    def trace_ns(self) -> np.ndarray:
+        """[nreq, 4] globaltimer: entry seen, slot published, first chunk claimed, last chunk done."""
+        torch.cuda.synchronize()
+        return self.trace.cpu().numpy().reshape(self.nreq, 4)
 
     def run(self) -> dict:
         import time
@@ -418,3 +429,11 @@ class ServeRun:
         t0 = time.perf_counter()
         rc = G.gsync_serve_baseline(self.cfg, buf, self.bws, self.bws_bytes, streams)
         return self._out(rc, buf, time.perf_counter() - t0)
+
+
+def probe_host_pingpong(iters: int = 2000) -> dict:
+    """One host <-> device hand-off through pinned host memory (release/acquire, system scope)."""
+    words = torch.zeros(64, dtype=torch.int32).pin_memory()
+    out = (G.ctypes.c_uint64 * 1)()
+    G.check("gsync_probe_host_pingpong", G.gsync_probe_host_pingpong(words, iters, out))
+    return {"handoff_ns": out[0] / (2 * iters)}

@@ -1,0 +1,39 @@
+"""Machine abstraction on the GPU: the library's ratio arithmetic over its own measured
+Table-1 times agrees with the oracle's arithmetic over the same times (the measured times
+themselves are hardware facts: parity unpinned, only sanity-checked)."""
+import math
+
+import pytest
+
+from gpu_util import require_gpu
+from oracle import classify
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def table():
+    require_gpu()
+    from paper_1110_4623_gb300 import machine
+    return machine.measure_table(1184, 128, 1000, reps=1)
+
+
+def test_all_sixteen_probes_measured(table):
+    assert len(table) == 12
+    assert all(v > 0 and math.isfinite(v) for v in table.values())
+
+
+def test_ratio_arithmetic_matches_oracle(table):
+    from paper_1110_4623_gb300 import machine
+    t2, t3 = machine.ratios(table)
+    o2, o3 = classify.table2(table), classify.table3(table)
+    assert t2.keys() == o2.keys() and t3.keys() == o3.keys()
+    for k in o2:
+        assert math.isclose(t2[k], o2[k], rel_tol=1e-12)
+    for k in o3:
+        assert math.isclose(t3[k], o3[k], rel_tol=1e-12)
+    assert machine.design(machine.abstraction(table)) == classify.design_choice(classify.abstraction(table))
+
+
+def test_contentious_atomics_slower_than_noncontentious(table):
+    assert table[("cont_atomic", "read")] > table[("noncont_atomic", "read")]
