@@ -364,6 +364,7 @@ def batched_section(G, calc, inputs, runner, autotune):
 SERVE_POOL = 128 << 20           # 512 MB of int32 values (4x the L2)
 SERVE_RATES = (1e3, 1e4, 1e5, 1e6)
 SERVE_SECONDS, SERVE_MAX_REQ = 0.5, 100_000
+SERVE_CHUNK = 8192                # values per chunk (one block's share), both arms
 
 
 def serve_section(calc, inputs, runner):
@@ -381,14 +382,15 @@ def serve_section(calc, inputs, runner):
         sched = inputs.poisson_arrivals(nreq, rate)
         sample = rng.choice(nreq, size=min(nreq, 300), replace=False)
         want = calc.serve_final(off[sample], ln[sample], pool)
-        row = {"nreq": nreq}
+        row = {"nreq": nreq, "chunk_values": SERVE_CHUNK}
         for arm in ("persistent", "per_request_launch"):
-            sr = runner.ServeRun(off, ln, sched, dpool, nslots=64, nblocks=304, admitters=8)
+            sr = runner.ServeRun(off, ln, sched, dpool, nslots=64, nblocks=304, admitters=8, chunk_elems=SERVE_CHUNK)
             r = sr.run() if arm == "persistent" else sr.baseline(nstreams=8)
             lat = r["latency_ns"] / 1e3
             span = (sched[-1] + r["latency_ns"][-1]) / 1e9
             row[arm] = {"rc": r["rc"], "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
                         "mean_us": float(lat.mean()), "achieved_req_s": nreq / max(span, 1e-9),
+                        "host_publish_delay_max_us": float(r["publish_delay_ns"].max() / 1e3),
                         "parity_sample": "ok" if np.array_equal(r["res"][sample], want) else "FAILED"}
         out["rates"][f"{rate:g}"] = row
     return out

@@ -302,7 +302,7 @@ int gsync_bench_batched(const gsync_batched_work* w, void* stream);
  *    latency_ns are ordinary host arrays.  workspace (device, 256-byte aligned) holds
  *    gsync_serve_workspace_bytes(nslots) bytes.
  *  - Requires 0 <= offset[q], 1 <= length[q], offset[q] + length[q] <= pool_elems <= 2^32,
- *    at most 65535 chunks per request, nslots <= 64, non-decreasing sched_ns.
+ *    at most 32767 chunks per request, nslots <= 64, non-decreasing sched_ns.
  *  - Returns GSYNC_ETIMEDOUT if not every request completed within drain_timeout_s after the
  *    last scheduled arrival, or if a device wait timed out (stats[3] = device status).
  *    Synchronizes `stream` before returning.
@@ -336,6 +336,8 @@ typedef struct gsync_serve_buffers {
   int64_t* res;
   uint32_t* done;
   int64_t* latency_ns;
+  int64_t* publish_ns; /* optional (host, nreq, or NULL): host time request q was published
+                          (persistent loop) or launched (baseline), ns from the start */
   uint64_t* trace;   /* optional (device, 4 x nreq u64, or NULL): %globaltimer when request q's
                         entry was seen, its slot published, its first chunk claimed, its last
                         chunk finished (persistent loop only) */

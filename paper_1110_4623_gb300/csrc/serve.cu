@@ -140,25 +140,35 @@ __device__ __forceinline__ long long block_sum(const int32_t* pool, int64_t a, i
   return t;  // valid in thread 0
 }
 
-// Thread 0: claims one chunk of slot s, or returns false.  One 16-byte acquire load reads
-// the state, generation, chunk counter and chunk count together.
-__device__ bool claim_chunk(Slot* slot, uint32_t& chunk, uint32_t& gen, bool& last) {
-  const uint4 h = gsync::ptx::ld_acquire_v4(&slot->state);
-  if (h.x != 2u) return false;
-  gen = h.y;
-  const uint32_t n = h.w;
-  uint32_t v = h.z;
-  for (int tries = 0; tries < 64; ++tries) {
-    if ((v >> 16) != (gen & 0xFFFFu) || (v & 0xFFFFu) >= n) return false;
-    const uint32_t old = atom_cas_relaxed(&slot->next_chunk, v, v + 1u);
-    if (old == v) {
-      chunk = v & 0xFFFFu;
-      last = chunk + 1u == n;
+__device__ __forceinline__ bool gen_after(uint32_t a, uint32_t b) { return (int16_t)(uint16_t)(a - b) > 0; }
+
+// Thread 0: claims one chunk of slot s, or returns false.  The claim is one fetch-and-add on
+// the slot's (generation:16 | chunk:16) counter, so racing workers each get a distinct chunk
+// in one round trip.  A result past the generation's chunk count is an over-claim and is
+// dropped (a request has at most 32767 chunks, so over-claims never reach the generation
+// bits).  A claim that lands after the slot moved to a newer request is a real chunk of that
+// request: the worker waits (bounded) for the newer generation to be published and serves
+// it.  A claim of an older generation than the one now published is dropped.
+__device__ bool claim_chunk(Slot* slot, uint32_t& chunk, uint32_t& gen, bool& last, uint64_t timeout_ns) {
+  const uint32_t v = gsync::ptx::atom_add_relaxed(&slot->next_chunk, 1u);
+  const uint32_t g = v >> 16, c = v & 0xFFFFu;
+  uint64_t deadline = 0;
+  for (;;) {
+    const uint4 h = gsync::ptx::ld_acquire_v4(&slot->state);
+    const uint32_t hg = h.y & 0xFFFFu;
+    if (h.x == 2u && hg == g) {
+      if (c >= h.w) return false;
+      chunk = c;
+      gen = h.y;
+      last = c + 1u == h.w;
       return true;
     }
-    v = old;
+    if (gen_after(hg, g) || (hg == g && h.x != 2u && h.x != 1u)) return false;  // stale claim
+    // generation g is being set up (or not yet published): wait for it, bounded
+    const uint64_t now = ptx::globaltimer();
+    if (deadline == 0) deadline = now + timeout_ns;
+    if (now > deadline) return false;
   }
-  return false;
 }
 
 __global__ void __launch_bounds__(kThreads) serve_kernel(Args a) {
@@ -224,16 +234,19 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(Args a) {
         }
         if (!got) { record_status(a.status, GSYNC_ETIMEDOUT); break; }
         Slot* sl = &a.slots[s];
-        const uint32_t gen = sl->gen + 1u;
+        // gen, nchunks and the chunk counter are read (and the counter added to) by workers
+        // at any time, so they are written with strong (relaxed) stores; the rest is read
+        // only after the release of state = 2.
+        const uint32_t gen = ptx::ld_relaxed(&sl->gen) + 1u;
         const uint32_t nch = (req_len + a.chunk_elems - 1u) / a.chunk_elems;
-        sl->gen = gen;
+        ptx::st_relaxed(&sl->gen, gen);
         sl->id = req_id;
         sl->off = (int64_t)req_off;
         sl->len = (int64_t)req_len;
-        sl->nchunks = nch == 0 ? 1u : nch;
+        ptx::st_relaxed(&sl->nchunks, nch == 0 ? 1u : nch);
         sl->acc = 0ull;
         sl->done_chunks = 0u;
-        sl->next_chunk = (gen & 0xFFFFu) << 16;
+        ptx::st_relaxed(&sl->next_chunk, (gen & 0xFFFFu) << 16);
         ptx::st_release(&sl->state, 2u);
         for (uint32_t m = 0; m < kMaskCopies; ++m) atomicOr(&a.active_mask[32u * m + (s >> 5)], 1u << (s & 31));
         ptx::red_add_relaxed(a.stats, 1u);
@@ -256,7 +269,7 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(Args a) {
           if (!((mask >> s) & 1ull)) continue;
           uint32_t c, g;
           bool last;
-          if (claim_chunk(&a.slots[s], c, g, last)) {
+          if (claim_chunk(&a.slots[s], c, g, last, a.timeout_ns)) {
             // The last chunk is handed out: the slot has no more work to find, so it leaves the
             // active mask now (it cannot be reused before this chunk completes).
             if (last)
@@ -386,7 +399,7 @@ int check_requests(const gsync_serve_cfg* cfg, const gsync_serve_buffers* buf) {
   for (int q = 0; q < cfg->nreq; ++q) {
     const int64_t o = buf->offset[q], n = buf->length[q];
     if (o < 0 || n < 1 || o > buf->pool_elems - n) return GSYNC_EINVAL;
-    if ((n + cfg->chunk_elems - 1) / cfg->chunk_elems > 0xFFFF) return GSYNC_EINVAL;
+    if ((n + cfg->chunk_elems - 1) / cfg->chunk_elems > 32767) return GSYNC_EINVAL;
     if (q > 0 && buf->sched_ns[q] < buf->sched_ns[q - 1]) return GSYNC_EINVAL;
   }
   return GSYNC_OK;
@@ -430,6 +443,10 @@ extern "C" int gsync_serve_run(const gsync_serve_cfg* cfg, gsync_serve_buffers* 
   gsync_backoff sbo = {GSYNC_BACKOFF_EXPONENTIAL, 64, 2000, 0};
   if (int rc = gsync_sem_init(sem, 4 * 128, GSYNC_SEM_TICKET, cfg->nslots, &sbo, wait_ns, stream)) return rc;
 
+  // The host threads write these arrays on the latency path: touch every page first.
+  for (int q = 0; q < cfg->nreq; ++q) buf->latency_ns[q] = 0;
+  if (buf->publish_ns)
+    for (int q = 0; q < cfg->nreq; ++q) buf->publish_ns[q] = 0;
   // Host control word ctrl[32] = shutdown; the ring starts empty (no entry has a valid seq).
   volatile uint32_t* ctrl = buf->ctrl;
   ctrl[32] = 0;
@@ -476,20 +493,39 @@ extern "C" int gsync_serve_run(const gsync_serve_cfg* cfg, gsync_serve_buffers* 
   // The producer runs on its own pinned core too; this thread only waits.
   std::atomic<int> prod_rc{GSYNC_OK};
   std::thread producer([&]() {
-    for (int q = 0; q < cfg->nreq; ++q) {
+    // Publishes every request whose time has come in one batch: the entries' bodies, one
+    // release fence, then their sequence numbers.  A store to a line the device is polling
+    // waits for that line's copy to be invalidated (~1 us over the C2C link), so one fence
+    // per batch instead of one per entry keeps the producer on schedule at high rates.
+    int q = 0;
+    while (q < cfg->nreq) {
       spin_until(t0 + std::chrono::nanoseconds(buf->sched_ns[q]));
-      // The ring entry of request q is reused only after request q - ring_slots completed.
-      while (q - completed.load(std::memory_order_acquire) >= cfg->ring_slots) {
+      const int64_t now = now_ns(t0);
+      int qe = q + 1;
+      while (qe < cfg->nreq && buf->sched_ns[qe] <= now && qe - q < 64) ++qe;
+      // The ring entry of request i is reused only after request i - ring_slots completed.
+      while (qe - 1 - completed.load(std::memory_order_acquire) >= cfg->ring_slots) {
         if (Clock::now() > deadline || abort_flag.load(std::memory_order_relaxed)) {
           prod_rc.store(GSYNC_ETIMEDOUT);
           return;
         }
       }
-      gsync_serve_req* e = (gsync_serve_req*)((char*)buf->ring + (size_t)(q & (cfg->ring_slots - 1)) * kRingStride);
-      e->len = (uint32_t)buf->length[q];
-      e->off = (uint32_t)buf->offset[q];
-      e->seq_check = (uint32_t)(q + 1);
-      __atomic_store_n(&e->seq, (uint32_t)(q + 1), __ATOMIC_RELEASE);
+      for (int i = q; i < qe; ++i) {
+        gsync_serve_req* e = (gsync_serve_req*)((char*)buf->ring + (size_t)(i & (cfg->ring_slots - 1)) * kRingStride);
+        e->len = (uint32_t)buf->length[i];
+        e->off = (uint32_t)buf->offset[i];
+        e->seq_check = (uint32_t)(i + 1);
+      }
+      std::atomic_thread_fence(std::memory_order_release);
+      for (int i = q; i < qe; ++i) {
+        gsync_serve_req* e = (gsync_serve_req*)((char*)buf->ring + (size_t)(i & (cfg->ring_slots - 1)) * kRingStride);
+        __atomic_store_n(&e->seq, (uint32_t)(i + 1), __ATOMIC_RELAXED);
+      }
+      if (buf->publish_ns) {
+        const int64_t t = now_ns(t0);
+        for (int i = q; i < qe; ++i) buf->publish_ns[i] = t;
+      }
+      q = qe;
     }
   });
   pin_to_core_from_end(producer, 0);
@@ -538,6 +574,9 @@ extern "C" int gsync_serve_baseline(const gsync_serve_cfg* cfg, gsync_serve_buff
   GSYNC_CUDA(cudaMemsetAsync(workspace, 0, gsync_serve_baseline_workspace_bytes(cfg->nreq), (cudaStream_t)streams[0]));
   GSYNC_CUDA(cudaStreamSynchronize((cudaStream_t)streams[0]));
   for (int q = 0; q < cfg->nreq; ++q) buf->done[q] = 0;
+  for (int q = 0; q < cfg->nreq; ++q) buf->latency_ns[q] = 0;
+  if (buf->publish_ns)
+    for (int q = 0; q < cfg->nreq; ++q) buf->publish_ns[q] = 0;
   std::atomic_thread_fence(std::memory_order_seq_cst);
   void *d_res, *d_done;
   if (int rc = host_dev_ptr(buf->res, &d_res)) return rc;
@@ -563,6 +602,7 @@ extern "C" int gsync_serve_baseline(const gsync_serve_cfg* cfg, gsync_serve_buff
       segsum_kernel<<<nb, kThreads, 0, (cudaStream_t)streams[q % nstreams]>>>(
           buf->pool, buf->offset[q], len, (uint32_t)cfg->chunk_elems, acc + q, counter + 2 * q, (uint32_t)q,
           (int64_t*)d_res, (uint32_t*)d_done);
+      if (buf->publish_ns) buf->publish_ns[q] = now_ns(t0);
       if (cudaGetLastError() != cudaSuccess) {
         launch_rc.store(GSYNC_ECUDA);
         return;

@@ -80,7 +80,8 @@ class gsync_serve_cfg(ctypes.Structure):
 class gsync_serve_buffers(ctypes.Structure):
     _fields_ = [("pool", u32p), ("pool_elems", ctypes.c_int64), ("offset", u32p), ("length", u32p),
                 ("sched_ns", u32p), ("ring", u32p),
-                ("ctrl", u32p), ("res", u32p), ("done", u32p), ("latency_ns", u32p), ("trace", u32p),
+                ("ctrl", u32p), ("res", u32p), ("done", u32p), ("latency_ns", u32p), ("publish_ns", u32p),
+                ("trace", u32p),
                 ("stats", ctypes.c_uint32 * 4)]
 
 

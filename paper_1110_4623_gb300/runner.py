@@ -390,6 +390,7 @@ class ServeRun:
         self.res = torch.zeros(self.nreq, dtype=torch.int64).pin_memory()
         self.done = torch.zeros(self.nreq, dtype=torch.int32).pin_memory()
         self.latency = np.zeros(self.nreq, dtype=np.int64)
+        self.publish = np.zeros(self.nreq, dtype=np.int64)
         self.ws_bytes = G.gsync_serve_workspace_bytes(nslots)
         self.ws = torch.zeros(max(self.ws_bytes, 256), dtype=torch.uint8, device="cuda")
         self.bws_bytes = G.gsync_serve_baseline_workspace_bytes(self.nreq)
@@ -400,12 +401,13 @@ class ServeRun:
         return G.gsync_serve_buffers(G.ptr(self.pool), self.pool.numel(), self.offset.ctypes.data,
                                      self.length.ctypes.data,
                                      self.sched.ctypes.data, G.ptr(self.ring), G.ptr(self.ctrl), G.ptr(self.res),
-                                     G.ptr(self.done), self.latency.ctypes.data, G.ptr(self.trace),
+                                     G.ptr(self.done), self.latency.ctypes.data, self.publish.ctypes.data,
+                                     G.ptr(self.trace),
                                      (G.ctypes.c_uint32 * 4)())
 
     def _out(self, rc, buf, wall):
         return {"rc": rc, "res": self.res.numpy().copy(), "latency_ns": self.latency.copy(),
-                "stats": list(buf.stats), "wall_s": wall}
+                "publish_delay_ns": self.publish - self.sched, "stats": list(buf.stats), "wall_s": wall}
 
     def enable_trace(self):
         self.trace = torch.zeros(4 * self.nreq, dtype=torch.int64, device="cuda")

@@ -19,7 +19,7 @@ def buffers(G, off, ln, sched, pool_elems):
             np.zeros(len(off), np.uint32), np.zeros(len(off), np.int64)]
     b = G.gsync_serve_buffers(0x1000, pool_elems, off.ctypes.data, ln.ctypes.data, sched.ctypes.data,
                               keep[3].ctypes.data, keep[4].ctypes.data, keep[5].ctypes.data, keep[6].ctypes.data,
-                              keep[7].ctypes.data, None, (ctypes.c_uint32 * 4)())
+                              keep[7].ctypes.data, None, None, (ctypes.c_uint32 * 4)())
     return b, keep
 
 
@@ -27,7 +27,7 @@ def buffers(G, off, ln, sched, pool_elems):
                                            ([-1], [5], [0]),                     # negative offset
                                            ([90], [20], [0]),                    # past the pool end
                                            ([0, 0], [4, 4], [5, 1]),             # arrivals out of order
-                                           ([0], [(1 << 16) * 1024 + 1], [0])])  # too many chunks
+                                           ([0], [(1 << 15) * 1024 + 1], [0])])  # too many chunks
 def test_bad_requests_rejected(G, off, ln, sched):
     pool = 100 if max(ln) < 1 << 20 else 1 << 40
     b, keep = buffers(G, off, ln, sched, pool)
