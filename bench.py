@@ -1,7 +1,8 @@
 """Benchmark of the inter-block synchronization hot path on GB300.
 
 One step = one pass over every row of the hot path at 1184 blocks:
-  * mutex contention (4 kinds x critical sections of 0/64/1024 words, 256 threads per block,
+  * mutex contention (the paper's 4 kinds and the two-die cohort lock x critical sections of
+    0/64/1024 words, 256 threads per block,
     100 acquisitions per block, seeded delays U{0..2000} cycles),
   * grid barriers (atomic, flag, tree, cluster 2/4/8, sharded; 128 threads, 1000 rounds each),
   * counting semaphores (sleeping FA kind, n in {1, 4, 16, 64}; 128 threads, 200 pairs each,
@@ -36,16 +37,20 @@ BAR_THREADS, BAR_ROUNDS = 128, 1000
 SEM_THREADS, SEM_PAIRS, SEM_COUNTS = 128, 200, (1, 4, 16, 64)
 # Library defaults for GB300, chosen from 1184-block sweeps (the paper's API serves the
 # fastest implementation of each primitive for the GPU as the default, Section 5 "API").
-DEFAULT_MUTEX = "ticket"
+DEFAULT_MUTEX = "cohort"
 DEFAULT_BARRIER = ("atomic", 0)
 BARRIERS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("cluster", 2), ("cluster", 4), ("cluster", 8),
             ("sharded", 32), ("sharded", 8)]
 # Backoff (min_ns, max_ns) per kind; the ticket kinds sleep min_ns per waiter ahead, capped.
-MUTEX_BACKOFF = {"cas_backoff": (16, 512), "ticket": (128, 4000)}
+MUTEX_BACKOFF = {"cas_backoff": (16, 512), "ticket": (128, 4000), "cohort": (128, 4000)}
 SEM_BACKOFF = (64, 2000)
 # Batched many-mutex workload: 4096 keys, Zipf(1.1), 1e6 acquisitions, 64 barrier groups.
 BATCH_KEYS, BATCH_ACQ, BATCH_GROUPS, BATCH_ROUNDS, BATCH_THREADS = 4096, 1_000_000, 64, 100, 128
 METRIC = "lock acquires/s & barrier ns at 1184 blocks vs L2-atomic roofline; p99 latency"
+# DRAM bytes per launch of the default mutex kind's workload kernel from an ncu capture, or
+# None while the kernel has changed since the last capture.
+ROOF_TRAFFIC = None
+ROOF_TRAFFIC_NOTE = "not yet captured for the cohort kernel"
 TIMEOUT_NS = 10_000_000_000
 
 
@@ -65,6 +70,25 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(vals, world, device="cuda"):
+    """Elementwise maximum of a list of floats over all ranks of the default process group
+    (the identity for a single process)."""
+    vals = [float(v) for v in vals]
+    if world == 1:
+        return vals
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def replica_value(units_per_rank, ms_max, world):
+    """Whole-job throughput of `world` independent replicas: every rank processes
+    `units_per_rank`, and the job takes as long as its slowest rank."""
+    return units_per_rank * world / (ms_max * 1e-3)
 
 
 def barrier_name(kind, param):
@@ -401,15 +425,19 @@ def cpu_baseline(inputs, kind):
     from oracle import cpu
     from paper_1110_4623_gb300 import gsync as G
     acq, secs, threads = 0, 0.0, 0
+    # The host has no dies to keep hand-offs on: the oracle runs the cohort workload (same
+    # inputs, same result) with its ticket lock.
+    cpu_kind = kind if kind in cpu.MUTEX_KINDS else "ticket"
     for K in CS_SIZES:
         delay, add = inputs.mutex_inputs(NBLOCKS, MUTEX_ACQ, inputs.mutex_seed(G.MUTEX_KINDS[kind], NBLOCKS, K))
-        r = cpu.mutex_run(kind, NBLOCKS, MUTEX_ACQ, K, add, delay)
+        r = cpu.mutex_run(cpu_kind, NBLOCKS, MUTEX_ACQ, K, add, delay)
         acq += NBLOCKS * MUTEX_ACQ
         secs += r["seconds"]
         threads = r["threads"]
     return {"value": acq / secs, "unit": "acq/s", "cores": threads, "kind": "oracle",
-            "sample": f"{kind} mutex, {NBLOCKS} blocks x {MUTEX_ACQ} acquisitions x CS {list(CS_SIZES)} words "
-                      f"(the full step's mutex workload of the default kind), blocks round-robin on {threads} threads"}
+            "sample": f"{kind} mutex workload, {NBLOCKS} blocks x {MUTEX_ACQ} acquisitions x CS {list(CS_SIZES)} "
+                      f"words (the full step's mutex workload of the default kind; the oracle's {cpu_kind} lock), "
+                      f"blocks round-robin on {threads} threads"}
 
 
 def run_gpu(args):
@@ -456,22 +484,17 @@ def run_gpu(args):
     bad = step.verify(calc)
     terms = merge_terms(terms_before, measure_roofline_terms(runner, inputs))
 
-    step_ms = float(np.mean(per_step))
-    if world > 1:
-        t = torch.tensor([step_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(t.item())
-
     med = {k: float(np.median([pk[k] for pk in per_kernel])) for k in per_kernel[0]}
+    def_ms = sum(med[(DEFAULT_MUTEX, K)] for K in CS_SIZES)
+    step_ms, def_ms = max_over_ranks([float(np.mean(per_step)), def_ms], world)
     mutex = {}
     for (kind, K) in step.mutex:
         ms = med[(kind, K)]
         acq_s = NBLOCKS * MUTEX_ACQ / (ms * 1e-3)
         roof = mutex_roof_acq_s(terms, K)
         mutex.setdefault(kind, {})[str(K)] = {"ms": ms, "acq_per_s": acq_s, "roof_acq_per_s": roof, "frac": acq_s / roof}
-    def_ms = sum(med[(DEFAULT_MUTEX, K)] for K in CS_SIZES)
     def_acq = NBLOCKS * MUTEX_ACQ * len(CS_SIZES)
-    value = def_acq / (def_ms * 1e-3) * world
+    value = replica_value(def_acq, def_ms, world)
     roof_ms = sum(NBLOCKS * MUTEX_ACQ / mutex_roof_acq_s(terms, K) * 1e3 for K in CS_SIZES)
     peak = def_acq / (roof_ms * 1e-3)
     barrier = {}
@@ -498,9 +521,8 @@ def run_gpu(args):
                    "default_barrier": bkey, "nblocks": NBLOCKS,
                    "l2": "flushed (512 MiB write) before every timed step", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "l2_handoff_latency", "achieved": value / world, "peak": peak, "unit": "acq/s",
-                     "frac": (value / world) / peak, "traffic": 2.3e6,
-                     "traffic_note": "DRAM bytes per launch of the dominant kernel (queue/ticket mutex workload), "
-                                     "scaled from the ncu capture in profiles/ (input arrays only)",
+                     "frac": (value / world) / peak, "traffic": ROOF_TRAFFIC,
+                     "traffic_note": ROOF_TRAFFIC_NOTE,
                      "peak_source": "measured live: sum over CS sizes of 1e9 / (L_handoff + T_cs(K)) from the "
                                     "ping-pong and critical-section probe kernels of this run (min with R_same/2); "
                                     "MEASURED_PEAKS.json's HBM and bf16 peaks do not bound this path"},
@@ -514,9 +536,12 @@ def run_gpu(args):
         "wall_s_timed_loop": wall,
         "parity_after_timing": "ok" if not bad else bad,
     }
+    e2e = e2e_mutex(G, inputs, DEFAULT_MUTEX)
+    # Every rank ran the same number of acquisitions; the job's time is the slowest rank's.
+    (ms_per_acq,) = max_over_ranks([1e3 / e2e["value"]], world)
+    e2e["value"] = replica_value(1, ms_per_acq, world)
     if rank == 0:
-        out["e2e"] = e2e_mutex(G, inputs, DEFAULT_MUTEX)
-        out["e2e"]["value"] *= world
+        out["e2e"] = e2e
         if not args.no_batched:
             out["batched"] = batched_section(G, calc, inputs, runner, autotune)
             out["serving"] = serve_section(calc, inputs, runner)

@@ -54,7 +54,10 @@ typedef enum gsync_mutex_kind {
   GSYNC_MUTEX_CAS_SPIN = 0,    /* spin on atomicCAS(0 -> 1); unlock = release store 0 */
   GSYNC_MUTEX_CAS_BACKOFF = 1, /* the same with __nanosleep backoff after each failure */
   GSYNC_MUTEX_TICKET = 2,      /* fetch-and-add ticket; poll turn; unlock stores turn + 1 */
-  GSYNC_MUTEX_SLEEP_QUEUE = 3  /* queue lock: each waiter polls its own padded flag slot */
+  GSYNC_MUTEX_SLEEP_QUEUE = 3, /* queue lock: each waiter polls its own padded flag slot */
+  GSYNC_MUTEX_COHORT = 4       /* two-die cohort lock: a ticket lock per die (homed on that
+                                  die) under a global ticket lock; hand-offs stay on a die
+                                  for up to `budget` acquisitions in a row */
 } gsync_mutex_kind;
 
 /* Barrier kinds (Section 5, "Barrier"). */
@@ -89,12 +92,33 @@ typedef struct gsync_backoff {
 /* and zeroes it; here the caller allocates and the library writes the initial state).   */
 /* ------------------------------------------------------------------------------------ */
 
-/* Bytes of a mutex for at most `max_waiters` blocks waiting at once; 0 if invalid. */
+/* Bytes of a mutex for at most `max_waiters` blocks waiting at once; 0 if invalid.
+ * COHORT takes 32 KB whatever the waiters. */
 size_t gsync_mutex_bytes(int kind, int max_waiters);
 /* Writes the initial state of a mutex into `state` (device) on `stream`.  `backoff` (host,
- * may be NULL for no sleeping) is copied; timeout_ns = 0 selects 2 s. */
+ * may be NULL for no sleeping) is copied; timeout_ns = 0 selects 2 s.  COHORT: as
+ * gsync_mutex_init_cohort with GSYNC_COHORT_DEFAULT_BUDGET. */
 int gsync_mutex_init(void* state, size_t bytes, int kind, int max_waiters,
                      const gsync_backoff* backoff, uint64_t timeout_ns, void* stream);
+
+/* Cohort mutex (GSYNC_MUTEX_COHORT) with a chosen budget (1..32767): the lock passes from a
+ * holder to the next waiter on the same die at most budget - 1 times in a row before the
+ * global lock goes to the other die, so a block waits behind at most its own die's queue
+ * plus `budget` acquisitions per other-die turn.  Measures the device's SM-to-die map (once
+ * per device and process: the gsync_probe_rtt_by_sm probe, ~3 ms) and the home die of the
+ * state's 4 KB pages, then places each die's local lock on a page homed on that die;
+ * synchronizes `stream`.  On a one-die GPU both local locks serve every SM.  state: device,
+ * 128-byte aligned, bytes >= gsync_mutex_bytes(GSYNC_MUTEX_COHORT, 1). */
+enum { GSYNC_COHORT_DEFAULT_BUDGET = 64 };
+int gsync_mutex_init_cohort(void* state, size_t bytes, int budget, const gsync_backoff* backoff,
+                            uint64_t timeout_ns, void* stream);
+
+/* The device's SM-to-die map: die_of_sm (host, >= sm_count bytes) receives 0 or 1 per SM id
+ * (die 0 = the SMs near a fixed line of the library's static memory), *ndies_out 1 or 2.
+ * Measured once per device and process with gsync_probe_rtt_by_sm (the atomic round trip to
+ * a line homed on the other die is ~2x longer), then cached; synchronizes `stream` on first
+ * use. */
+int gsync_device_topology(uint8_t* die_of_sm, int* ndies_out, void* stream);
 
 /* Bytes of a barrier for `nblocks` blocks.  param: fan-in (TREE, >= 2), cluster size
  * (CLUSTER, 1..8, divides nblocks), release mode (FLAG: 0 one flag per block, 1 one word;
@@ -456,6 +480,22 @@ int gsync_probe_cluster(int op, int cluster, int iters, uint64_t* out, void* str
  * store, op 2 after four plain stores, op 3 cluster-scope fences.  out (device, 2 x u64):
  * elapsed ns and SM cycles.  scratch (device, 256-byte aligned) needs 1024 bytes. */
 int gsync_probe_fence(int op, int iters, void* scratch, uint64_t* out, void* stream);
+
+/* Topology probes (extends Section 4's machine abstraction to a two-die GPU: the distance
+ * from an SM to a line's home die).  Both time chains of `iters` dependent atomic exchanges
+ * (plus 4 untimed warm-up exchanges) from one thread and clobber the lines they touch.
+ *
+ * gsync_probe_rtt_by_sm: one block per SM, taking turns (the line is never contended);
+ *   out_ns[s] (device, sm_count x u64) = ns for the chain from SM s to `line` (device,
+ *   4-byte aligned).  scratch: device, 128-byte aligned, >= 128 bytes (the turn word).
+ *   *status (device u32) = 0, or bit 0 if a turn wait ran past 1 s (entries left 0).
+ * gsync_probe_rtt_by_line: from SM `sm`, out_ns[i] (device, nlines x u64) = ns for the chain
+ *   to base + i * stride_bytes, for i < nlines (<= 65536); the caller owns that range.
+ * Both are asynchronous on `stream`; GSYNC_EINVAL on bad arguments. */
+int gsync_probe_rtt_by_sm(void* line, int iters, void* scratch, uint64_t* out_ns, uint32_t* status,
+                          void* stream);
+int gsync_probe_rtt_by_line(int sm, void* base, int nlines, int stride_bytes, int iters,
+                            uint64_t* out_ns, void* stream);
 
 #ifdef __cplusplus
 }

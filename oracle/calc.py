@@ -108,14 +108,17 @@ def mutex_final(nblocks: int, acq: int, cs_words: int, addend: np.ndarray) -> di
 
 
 def check_grant_log(log: np.ndarray, ticket: np.ndarray | None, nblocks: int, acq: int,
-                    fifo: bool, ticket_base: int = 0) -> list[str]:
+                    fifo: bool, ticket_base: int = 0, per_die: bool = False,
+                    die_bases: tuple = (0, 0)) -> list[str]:
     """Validity of a grant log (the parts of the result that are not unique).
 
     log[s] is the acquisition id granted s-th.  It must be a permutation of 0..B*A-1 in
     which each block's acquisitions appear in increasing order (a block acquires
     sequentially).  For the fair kinds (ticket and queue locks, Section 5: "gives access to
     the critical section to blocks in the order in which they request access") the ticket
-    drawn by the acquisition granted s-th must be ticket_base + s.
+    drawn by the acquisition granted s-th must be ticket_base + s.  per_die (the two-die
+    cohort lock): ticket bit 31 is the die and bits 30..0 that die's ticket; each die's
+    grants, in grant order, must carry die_bases[d] + 0, 1, 2, ...
     """
     n = nblocks * acq
     log = np.asarray(log, dtype=np.int64)
@@ -135,7 +138,21 @@ def check_grant_log(log: np.ndarray, ticket: np.ndarray | None, nblocks: int, ac
         want = (np.arange(n, dtype=np.uint64) + np.uint64(ticket_base)) & np.uint64(M32)
         if not np.array_equal(t, want):
             problems.append("grants are not in ticket order")
+    if per_die:
+        t = np.asarray(ticket, dtype=np.uint64)[log]
+        die, local = t >> np.uint64(31), t & np.uint64(0x7FFFFFFF)
+        for d in (0, 1):
+            got = local[die == d]
+            want = (np.arange(len(got), dtype=np.uint64) + np.uint64(die_bases[d])) & np.uint64(0x7FFFFFFF)
+            if not np.array_equal(got, want):
+                problems.append(f"die {d}'s grants are not in its ticket order")
     return problems
+
+
+def die_grant_counts(ticket: np.ndarray) -> tuple:
+    """Grants per die in a cohort lock's ticket record (bit 31 = die)."""
+    d = np.asarray(ticket, dtype=np.uint64) >> np.uint64(31)
+    return int((d == 0).sum()), int((d == 1).sum())
 
 
 # --------------------------------------------------------------------------------------------

@@ -19,6 +19,7 @@ The algorithms follow Section 5 ("Design") and the pseudocode of the Appendix:
   TicketMutex   fetch-and-add mutex ("FA Mutex"; Section 5, "Fetch-and-Add Mutex")
   QueueMutex    sleep-waiting queue lock: each waiter polls its own slot of a ring of flags
   RingMutex     the paper's ring-buffer sleeping mutex (Section 5, "design alternative")
+  CohortMutex   two-die cohort lock: a ticket lock per die under a global ticket lock
   SpinSem       spin-lock semaphore with optional backoff ("Spin-Lock Semaphore")
   SleepSem      sleeping (FA) semaphore ("Sleeping Semaphore")
   AtomicBarrier two-stage atomic-counter barrier (Section 5, "Barrier")
@@ -245,6 +246,89 @@ class RingMutex:
 # --------------------------------------------------------------------------------------------
 # Semaphores
 # --------------------------------------------------------------------------------------------
+
+
+class CohortMutex:
+    """Two-level cohort lock over two dies (lock cohorting: Dice, Marathe and Shavit, PPoPP
+    2012), the library's GB300 design that keeps hand-offs inside a die.
+
+    Block p sits on die p mod 2.  Each die d has a local ticket counter next_d and a local turn
+    word (served_d, word_d) read and written as one 64-bit access; word_d's OWNED bit says the
+    die's cohort already holds the global ticket lock (gnext, gturn; 16-bit ticket compare).
+    lock: t <- FA(next_d); wait until served_d = t; if OWNED, inherit the global lock (passes
+      and global ticket from word_d); else g <- FA(gnext) mod 2^16, wait until gturn = g.
+    unlock: if next_d != t + 1 (a local waiter) and passes + 1 < budget: (served_d, word_d) <-
+      (t + 1, OWNED | passes + 1 | g); else gturn <- g + 1 mod 2^16, then (served_d, word_d)
+      <- (t + 1, 0).
+    Grants are FIFO within a die (the event carries the die and the local ticket).
+    broken="no_global": the first of a cohort enters without the global lock.
+    broken="owned_on_release": the release path also marks the local turn OWNED.
+    broken="skip_ticket": a pass within the die serves ticket t + 2 instead of t + 1.
+    broken="pass_always": passes within the die whether or not a local waiter exists, and
+    past the budget (the global lock is never released: the other die starves).
+    """
+    kind, capacity, fifo = "mutex", 1, False
+    OWNED = 0x80000000
+
+    def __init__(self, budget=2, base=0, gbase=0, broken=None):
+        self.budget, self.base, self.gbase, self.broken = budget, base & M32, gbase & M32, broken
+        self.dies = 2
+
+    def init(self, nproc, ops):
+        b, g = self.base, self.gbase
+        # (next0, served0, word0, next1, served1, word1, gnext, gturn)
+        return (b, b, 0, b, b, 0, g, g & 0xFFFF), tuple((0, 0, 0, 0) for _ in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, t, c = loc
+        d = p % 2
+        nx, sv, wd = sh[3 * d], sh[3 * d + 1], sh[3 * d + 2]
+        gnext, gturn = sh[6], sh[7]
+
+        def put_local(nx2, sv2, wd2):
+            return sh[:3 * d] + (nx2, sv2, wd2) + sh[3 * d + 3:]
+
+        def finish():
+            k2 = k + 1
+            return (0 if k2 < ops else DONE), k2
+
+        if pc == 0:
+            return (1, k, nx, c), put_local(inc(nx), sv, wd), None
+        if pc == 1:
+            if sv != t:
+                return loc, sh, None
+            if wd & self.OWNED:
+                return (PC_ENTER, k, t, wd & ~self.OWNED & M32), sh, None
+            if self.broken == "no_global":
+                return (PC_ENTER, k, t, 0), sh, None
+            return (2, k, t, c), sh, None
+        if pc == 2:
+            return (3, k, t, gnext & 0xFFFF), sh[:6] + (inc(gnext), gturn), None
+        if pc == 3:
+            return ((PC_ENTER if (gturn & 0xFFFF) == c else 3), k, t, c), sh, None
+        if pc == PC_ENTER:
+            return (PC_EXIT, k, t, c), sh, ("enter", (d, t))
+        if pc == PC_EXIT:
+            return (4, k, t, c), sh, ("exit",)
+        if pc == 4:
+            passes = (c >> 16) & 0x7FFF
+            if self.broken == "pass_always":
+                return (5, k, t, c), sh, None
+            waiter = nx != inc(t)
+            return ((5 if waiter and passes + 1 < self.budget else 6), k, t, c), sh, None
+        if pc == 5:
+            passes, g = (c >> 16) & 0x7FFF, c & 0xFFFF
+            pc2, k2 = finish()
+            word = self.OWNED | ((passes + 1) << 16) | g
+            return (pc2, k2, t, c), put_local(nx, inc(t, 2 if self.broken == "skip_ticket" else 1), word), None
+        if pc == 6:
+            g = c & 0xFFFF
+            return (7, k, t, c), sh[:7] + ((g + 1) & 0xFFFF,), None
+        if pc == 7:
+            pc2, k2 = finish()
+            word = self.OWNED if self.broken == "owned_on_release" else 0
+            return (pc2, k2, t, c), put_local(nx, inc(t), word), None
+        raise AssertionError(pc)
 
 
 class SpinSem:
@@ -598,6 +682,8 @@ class ClusterBarrier:
 def _ghost0(model, nproc):
     if model.kind == "barrier":
         return (tuple([0] * nproc), tuple([0] * nproc))
+    if getattr(model, "dies", 0):
+        return (0, 0, (0,) * model.dies)  # (blocks inside, grants, grants per die)
     return (0, 0)  # (blocks inside, grants so far)
 
 
@@ -613,7 +699,8 @@ def _apply(model, ghost, p, ev, nproc):
         if min(arrived) < r + 1:
             return ghost, f"block {p} passed round {r} before every block arrived"
         return (arrived, _set(passed, p, r + 1)), None
-    inside, grants = ghost
+    inside, grants = ghost[0], ghost[1]
+    rest = ghost[2:]
     if ev[0] == "enter":
         inside += 1
         if inside > model.capacity:
@@ -622,8 +709,15 @@ def _apply(model, ghost, p, ev, nproc):
             want = (getattr(model, "base", 0) + grants) & M32
             if ev[1] != want:
                 return ghost, f"grant {grants} went to ticket {ev[1]:#x}, expected {want:#x}"
-        return (inside, grants + 1), None
-    return (inside - 1, grants), None
+        if rest:  # FIFO within each die: the die's grants follow its local tickets
+            d, t = ev[1]
+            per = rest[0]
+            want = (model.base + per[d]) & M32
+            if t != want:
+                return ghost, f"die {d} grant {per[d]} went to local ticket {t:#x}, expected {want:#x}"
+            rest = (_set(per, d, per[d] + 1),)
+        return (inside, grants + 1) + rest, None
+    return (inside - 1, grants) + rest, None
 
 
 def check(model, nproc: int, ops: int, max_states: int = 2_000_000) -> Result:

@@ -5,7 +5,8 @@
 // log at position `total` and increments `total` with a plain load and store, and the
 // block's threads add addend[id] ^ (i * 0x9E3779B1) to data[i] for i < cs_words with plain
 // loads and stores.  Broken exclusion loses updates to total/data or corrupts the log; the
-// fair kinds also record their ticket so the host can check grants follow ticket order.
+// fair kinds also record their ticket so the host can check grants follow ticket order
+// (the cohort lock: each die's grants follow that die's tickets).
 #include "common.cuh"
 
 using namespace gsync_impl;
@@ -59,7 +60,9 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
       } else {
         gsync::ptx::atom_or_relaxed(status, GSYNC_STATUS_VIOLATION);
       }
-      ticket_out[id] = t.ticket;
+      // COHORT: tickets are per die; bit 31 records the die so the host can check each
+      // die's grants in ticket order.
+      ticket_out[id] = KIND == GSYNC_MUTEX_COHORT ? (m.die << 31) | (t.ticket & 0x7FFFFFFFu) : t.ticket;
     }
     if (KIND != kFrameOnly)
       for (uint32_t i = tid; i < (uint32_t)cs_words; i += blockDim.x) data[i] += v ^ (i * kGolden);
@@ -84,6 +87,7 @@ KernelFn pick(int kind) {
     case GSYNC_MUTEX_CAS_BACKOFF: return mutex_workload_kernel<GSYNC_MUTEX_CAS_BACKOFF>;
     case GSYNC_MUTEX_TICKET: return mutex_workload_kernel<GSYNC_MUTEX_TICKET>;
     case GSYNC_MUTEX_SLEEP_QUEUE: return mutex_workload_kernel<GSYNC_MUTEX_SLEEP_QUEUE>;
+    case GSYNC_MUTEX_COHORT: return mutex_workload_kernel<GSYNC_MUTEX_COHORT>;
   }
   return nullptr;
 }

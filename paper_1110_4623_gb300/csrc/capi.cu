@@ -18,17 +18,24 @@ constexpr uint32_t kLine = 128;
 constexpr uint32_t kMagic = 0x6B5C0000u;
 enum : uint32_t { kPrimMutex = 1, kPrimBarrier = 2, kPrimSem = 3 };
 
+constexpr size_t kCohortBytes = 32 * 1024;  // room for a 4 KB page homed on each die
+constexpr size_t kPage = 4096;              // granularity of the dies' address interleave
+
 struct InitSpec {
   uint32_t header[16];
   uint32_t nwords;
   uint32_t queue_slots;  // SLEEP_QUEUE: flag lines start at line 3
   uint32_t spin_sem_s;   // spin semaphores: initial S (line 1), else 0
+  uint32_t die_table;    // COHORT: write die[] at kDieTableWord
+  uint32_t die[gsync::kMaxSmIds / 4];  // packed bytes
 };
 
 __global__ void init_state_kernel(uint32_t* s, InitSpec spec) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < spec.nwords; i += gridDim.x * blockDim.x) {
     uint32_t v = 0;
     if (i < 16) v = spec.header[i];
+    if (spec.die_table && i >= gsync::kDieTableWord && i < gsync::kDieTableWord + gsync::kMaxSmIds / 4)
+      v = spec.die[i - gsync::kDieTableWord];
     const uint32_t line = i / 32, word = i % 32;
     if (spec.queue_slots && word == 0 && line >= 3 && line < 3 + spec.queue_slots) {
       // Slot k first serves ticket k; before that it holds k - Q, the ticket of the previous
@@ -109,10 +116,48 @@ extern "C" {
 int gsync_last_cuda_error(void) { return g_last_cuda_error; }
 
 size_t gsync_mutex_bytes(int kind, int max_waiters) {
-  if (kind < GSYNC_MUTEX_CAS_SPIN || kind > GSYNC_MUTEX_SLEEP_QUEUE || max_waiters < 1) return 0;
+  if (kind < GSYNC_MUTEX_CAS_SPIN || kind > GSYNC_MUTEX_COHORT || max_waiters < 1) return 0;
   if (max_waiters > (1 << 24)) return 0;
+  if (kind == GSYNC_MUTEX_COHORT) return kCohortBytes;
   const uint32_t q = kind == GSYNC_MUTEX_SLEEP_QUEUE ? pow2_at_least((uint32_t)max_waiters) : 0;
   return (size_t)(3 + q) * kLine;
+}
+
+int gsync_mutex_init_cohort(void* state, size_t bytes, int budget, const gsync_backoff* backoff, uint64_t timeout_ns,
+                            void* stream) {
+  if (!state || !aligned(state, kLine) || bytes < kCohortBytes || budget < 1 || budget > 32767) return GSYNC_EINVAL;
+  if (backoff && backoff->policy > GSYNC_BACKOFF_LINEAR_CYCLIC) return GSYNC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  InitSpec spec;
+  fill_header(spec, kPrimMutex, GSYNC_MUTEX_COHORT, 0, (uint32_t)budget, backoff, timeout_ns, 0);
+  uint8_t die[gsync::kMaxSmIds];
+  int ndies = 1, sms = 0;
+  if (int rc = device_topology(st, die, &ndies, &sms)) return rc;
+  // Candidate pages for the local locks: every 4 KB boundary past the header, global lock and
+  // die table (lines 0-4) with two lines of room before the end of the state.
+  const uintptr_t lo = (uintptr_t)state, hi = lo + kCohortBytes;
+  const uintptr_t first = (lo + 5 * kLine + kPage - 1) & ~(uintptr_t)(kPage - 1);
+  const int npages = first + 2 * kLine <= hi ? (int)((hi - 2 * kLine - first) / kPage) + 1 : 0;
+  if (npages < 2) return GSYNC_EINVAL;
+  uint8_t home[gsync::kMaxSmIds] = {};
+  if (ndies == 2)
+    if (int rc = line_homes((const void*)first, npages, kPage, die, sms, st, home)) return rc;
+  // Die d's local lock goes on the first page homed on d; a die with no such page (or a
+  // one-die GPU) takes the next unused page, which only costs locality.
+  int page[2] = {-1, -1};
+  for (int d = 0; d < 2; ++d)
+    for (int i = 0; i < npages && page[d] < 0; ++i)
+      if (home[i] == d && i != page[0]) page[d] = i;
+  for (int d = 0; d < 2; ++d)
+    for (int i = 0; i < npages && page[d] < 0; ++i)
+      if (i != page[0] && i != page[1]) page[d] = i;
+  for (int d = 0; d < 2; ++d)
+    spec.header[d ? gsync::kHdrDieOff1 : gsync::kHdrDieOff0] = (uint32_t)((first + (size_t)page[d] * kPage - lo) / 4);
+  spec.nwords = (uint32_t)(kCohortBytes / 4);
+  spec.die_table = 1;
+  memset(spec.die, 0, sizeof spec.die);
+  for (int i = 0; i < sms; ++i) ((uint8_t*)spec.die)[i] = ndies == 2 ? die[i] : 0;
+  return launch_init(state, bytes, spec, st);
 }
 
 int gsync_mutex_init(void* state, size_t bytes, int kind, int max_waiters, const gsync_backoff* backoff,
@@ -120,6 +165,8 @@ int gsync_mutex_init(void* state, size_t bytes, int kind, int max_waiters, const
   const size_t need = gsync_mutex_bytes(kind, max_waiters);
   if (need == 0 || bytes < need) return GSYNC_EINVAL;
   if (backoff && backoff->policy > GSYNC_BACKOFF_LINEAR_CYCLIC) return GSYNC_EINVAL;
+  if (kind == GSYNC_MUTEX_COHORT)
+    return gsync_mutex_init_cohort(state, bytes, GSYNC_COHORT_DEFAULT_BUDGET, backoff, timeout_ns, stream);
   const uint32_t q = kind == GSYNC_MUTEX_SLEEP_QUEUE ? pow2_at_least((uint32_t)max_waiters) : 0;
   InitSpec spec;
   fill_header(spec, kPrimMutex, (uint32_t)kind, (uint32_t)max_waiters, q, backoff, timeout_ns, 0);

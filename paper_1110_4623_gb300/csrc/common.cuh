@@ -93,6 +93,12 @@ int launch_coresident(void (*kernel)(Params...), int grid, int block, int cluste
   return GSYNC_OK;
 }
 
+// SM-to-die map of the current device (0/1 per SM id; measured on first use, then cached),
+// and the home die of `nlines` lines base + i * stride (<= 256 lines; synchronizes `st`).
+int device_topology(cudaStream_t st, uint8_t* die_of_sm, int* ndies, int* sms);
+int line_homes(const void* base, int nlines, size_t stride, const uint8_t* die_of_sm, int sms, cudaStream_t st,
+               uint8_t* die_out);
+
 // Maps a device-side wait result onto the caller's status bits.
 __device__ __forceinline__ void record_status(uint32_t* status, int rc) {
   if (rc == GSYNC_OK || status == nullptr) return;

@@ -18,7 +18,8 @@ GSYNC_OK, GSYNC_EINVAL, GSYNC_ENOTRESIDENT, GSYNC_ETIMEDOUT, GSYNC_ECUDA, GSYNC_
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOTRESIDENT", 3: "ETIMEDOUT", 4: "ECUDA", 5: "EABORTED"}
 GSYNC_STATUS_TIMEOUT, GSYNC_STATUS_ABORTED, GSYNC_STATUS_VIOLATION, GSYNC_STATUS_CONFIG = 1, 2, 4, 8
 
-MUTEX_KINDS = {"cas_spin": 0, "cas_backoff": 1, "ticket": 2, "sleep_queue": 3}
+MUTEX_KINDS = {"cas_spin": 0, "cas_backoff": 1, "ticket": 2, "sleep_queue": 3, "cohort": 4}
+COHORT_DEFAULT_BUDGET = 64
 BARRIER_KINDS = {"atomic": 0, "flag": 1, "tree": 2, "cluster": 3, "sharded": 4}
 SEM_KINDS = {"ticket": 0, "spin": 1, "spin_backoff": 2}
 BACKOFF_EXPONENTIAL, BACKOFF_LINEAR_CYCLIC = 0, 1
@@ -90,6 +91,9 @@ _SIG = {
     "gsync_mutex_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
     "gsync_mutex_init": (ctypes.c_int, [u32p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(gsync_backoff), ctypes.c_uint64, u32p]),
+    "gsync_mutex_init_cohort": (ctypes.c_int, [u32p, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(gsync_backoff),
+                                               ctypes.c_uint64, u32p]),
+    "gsync_device_topology": (ctypes.c_int, [u32p, ctypes.POINTER(ctypes.c_int), u32p]),
     "gsync_barrier_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "gsync_barrier_init": (ctypes.c_int, [u32p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_uint64, u32p]),
@@ -130,6 +134,9 @@ _SIG = {
     "gsync_probe_cluster": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, u32p, u32p]),
     "gsync_probe_fence": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, u32p, u32p, u32p]),
     "gsync_probe_sem_cs": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, u32p, u32p, u32p, u32p, u32p]),
+    "gsync_probe_rtt_by_sm": (ctypes.c_int, [u32p, ctypes.c_int, u32p, u32p, u32p, u32p]),
+    "gsync_probe_rtt_by_line": (ctypes.c_int, [ctypes.c_int, u32p, ctypes.c_int, ctypes.c_int, ctypes.c_int, u32p,
+                                               u32p]),
 }
 SIGNAL_MODES = {"st_release": 0, "fence_st_relaxed": 1, "st_relaxed": 2, "red_release": 3, "exch_release": 4}
 WAIT_MODES = {"ld_acquire": 0, "ld_relaxed_fence": 1, "ld_relaxed": 2, "ld_relaxed_then_acquire": 3,
@@ -224,6 +231,18 @@ def gsync_max_coresident_blocks(workload: int, kind: int, block_threads: int, cl
     v = ctypes.c_int(0)
     rc = lib().gsync_max_coresident_blocks(workload, kind, block_threads, cluster, ctypes.byref(v))
     return rc, v.value
+
+
+def gsync_mutex_init_cohort(state, nbytes, budget, backoff=None, timeout_ns=0, stream=None) -> int:
+    bo = ctypes.byref(backoff) if backoff is not None else None
+    return lib().gsync_mutex_init_cohort(ptr(state), nbytes, budget, bo, timeout_ns, stream_handle(stream))
+
+
+def gsync_device_topology(die_of_sm, stream=None) -> tuple[int, int]:
+    """die_of_sm: a writable host buffer (numpy uint8) of at least sm_count bytes."""
+    nd = ctypes.c_int(0)
+    rc = lib().gsync_device_topology(die_of_sm.ctypes.data, ctypes.byref(nd), stream_handle(stream))
+    return rc, nd.value
 
 
 def gsync_device_sm_count() -> tuple[int, int]:
@@ -327,6 +346,14 @@ def gsync_probe_cluster(op, cluster, iters, out, stream=None) -> int:
 
 def gsync_probe_fence(op, iters, scratch, out, stream=None) -> int:
     return lib().gsync_probe_fence(op, iters, ptr(scratch), ptr(out), stream_handle(stream))
+
+
+def gsync_probe_rtt_by_sm(line, iters, scratch, out_ns, status, stream=None) -> int:
+    return lib().gsync_probe_rtt_by_sm(ptr(line), iters, ptr(scratch), ptr(out_ns), ptr(status), stream_handle(stream))
+
+
+def gsync_probe_rtt_by_line(sm, base, nlines, stride_bytes, iters, out_ns, stream=None) -> int:
+    return lib().gsync_probe_rtt_by_line(sm, ptr(base), nlines, stride_bytes, iters, ptr(out_ns), stream_handle(stream))
 
 
 def gsync_probe_sem_cs(block_threads, iters, hold, addend, scratch, out, stream=None) -> int:

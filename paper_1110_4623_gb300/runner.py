@@ -103,14 +103,17 @@ class MutexRun:
 
     def __init__(self, kind: str, nblocks: int, block_threads: int, acq: int, cs_words: int,
                  delay: np.ndarray | None, addend: np.ndarray, bo: G.gsync_backoff | None = None,
-                 timeout_ns: int = 0):
+                 timeout_ns: int = 0, budget: int | None = None):
         self.kind, self.k = kind, G.MUTEX_KINDS[kind]
         self.nblocks, self.acq, self.cs_words = nblocks, acq, cs_words
         self.bo = bo
         n = nblocks * acq
         self.nbytes = G.gsync_mutex_bytes(self.k, nblocks)
         self.state = _state(self.nbytes)
-        G.check("gsync_mutex_init", G.gsync_mutex_init(self.state, self.nbytes, self.k, nblocks, bo, timeout_ns))
+        if budget is not None:
+            G.check("gsync_mutex_init_cohort", G.gsync_mutex_init_cohort(self.state, self.nbytes, budget, bo, timeout_ns))
+        else:
+            G.check("gsync_mutex_init", G.gsync_mutex_init(self.state, self.nbytes, self.k, nblocks, bo, timeout_ns))
         self.delay = _u32(delay) if delay is not None else None
         self.addend = _u32(addend)
         self.data = _zeros(cs_words)
@@ -237,6 +240,34 @@ def probe_cluster(op: int, cluster: int, iters: int = 2000) -> dict:
     o = out.cpu().numpy()
     per = o[0] / iters if op == 0 else o[0] / (2 * iters)
     return {"ns": per, "status": int(o[3])}
+
+
+def device_topology() -> tuple[np.ndarray, int]:
+    """(die of every SM id, number of dies) as the library measured and cached it."""
+    die = np.zeros(256, dtype=np.uint8)
+    rc, nd = G.gsync_device_topology(die)
+    G.check("gsync_device_topology", rc)
+    return die[:sm_count()].copy(), nd
+
+
+def probe_rtt_by_sm(line: torch.Tensor, iters: int = 64) -> dict:
+    """ns per dependent atomic round trip from every SM to the line at line.data_ptr()."""
+    scratch = _state(128)
+    out = torch.zeros(sm_count(), dtype=torch.int64, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    G.check("gsync_probe_rtt_by_sm", G.gsync_probe_rtt_by_sm(line, iters, scratch, out, status))
+    torch.cuda.synchronize()
+    return {"rtt_ns": out.cpu().numpy() / iters, "status": int(status.item())}
+
+
+def probe_rtt_by_line(sm: int, buf: torch.Tensor, nlines: int, stride_bytes: int = 128, iters: int = 16) -> np.ndarray:
+    """ns per dependent atomic round trip from SM `sm` to each line buf + i * stride_bytes."""
+    if (nlines - 1) * stride_bytes + 4 > buf.numel() * buf.element_size():
+        raise ValueError("line range exceeds the buffer")
+    out = torch.zeros(nlines, dtype=torch.int64, device="cuda")
+    G.check("gsync_probe_rtt_by_line", G.gsync_probe_rtt_by_line(sm, buf, nlines, stride_bytes, iters, out))
+    torch.cuda.synchronize()
+    return out.cpu().numpy() / iters
 
 
 def probe_fence(op: int, iters: int = 2000) -> dict:

@@ -9,8 +9,14 @@ from paper_1110_4623_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-KINDS = ["cas_spin", "cas_backoff", "ticket", "sleep_queue"]
+KINDS = ["cas_spin", "cas_backoff", "ticket", "sleep_queue", "cohort"]
 FAIR = {"ticket", "sleep_queue"}
+
+
+def grant_problems(kind, got, nblocks, acq, base=0, die_bases=(0, 0)):
+    fifo = kind in FAIR
+    return calc.check_grant_log(got["log"], got["ticket"] if fifo or kind == "cohort" else None, nblocks, acq,
+                                fifo, ticket_base=base, per_die=kind == "cohort", die_bases=die_bases)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -35,8 +41,7 @@ def check(kind, nblocks, threads, acq, cs_words, max_delay=2000):
     assert got["total"] == want["total"]
     assert np.array_equal(got["count"], want["count"])
     assert np.array_equal(got["data"], want["data"])
-    fifo = kind in FAIR
-    assert calc.check_grant_log(got["log"], got["ticket"] if fifo else None, nblocks, acq, fifo) == []
+    assert grant_problems(kind, got, nblocks, acq) == []
 
 
 @pytest.mark.parametrize("kind", KINDS)
@@ -69,12 +74,15 @@ def test_state_reused_across_launches(kind):
     delay, add = inputs.mutex_inputs(296, 20, 77, max_delay=100)
     mr = runner.MutexRun(kind, 296, 256, 20, 64, delay, add, bo=backoff_for(kind))
     want = calc.mutex_final(296, 20, 64, add)
+    die_bases = (0, 0)
     for rep in range(3):
         got = mr.run()
         assert got["status"] == 0 and np.array_equal(got["data"], want["data"])
         base = rep * 296 * 20 if kind in FAIR else 0
-        fifo = kind in FAIR
-        assert calc.check_grant_log(got["log"], got["ticket"] if fifo else None, 296, 20, fifo, ticket_base=base) == []
+        assert grant_problems(kind, got, 296, 20, base, die_bases) == []
+        if kind == "cohort":
+            c = calc.die_grant_counts(got["ticket"])
+            die_bases = (die_bases[0] + c[0], die_bases[1] + c[1])
 
 
 def test_host_buffer_entry_point():
@@ -96,3 +104,55 @@ def test_host_buffer_entry_point():
     want = calc.mutex_final(B, A, K, add)
     assert total[0] == want["total"] and np.array_equal(data, want["data"])
     assert calc.check_grant_log(log, tick, B, A, fifo=True) == []
+
+
+def test_cohort_host_buffer_entry_point():
+    import torch
+    from paper_1110_4623_gb300 import gsync as G
+    B, A, K = 1184, 20, 64
+    delay, add = inputs.mutex_inputs(B, A, 4242)
+    n = B * A
+    data = np.zeros(K, np.uint32); total = np.zeros(1, np.uint32); log = np.zeros(n, np.uint32)
+    tick = np.zeros(n, np.uint32); count = np.zeros(B, np.uint32); status = np.zeros(1, np.uint32)
+    p = lambda a: a.ctypes.data
+    w = G.gsync_mutex_work(G.MUTEX_KINDS["cohort"], B, 256, A, K, 0, p(delay), p(add), p(data), p(total), p(log),
+                           p(tick), p(count), p(status))
+    nbytes = G.gsync_bench_mutex_workspace_bytes(w.kind, B, A, K)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    assert G.gsync_bench_mutex_host(w, None, ws, nbytes) == 0 and status[0] == 0
+    want = calc.mutex_final(B, A, K, add)
+    assert total[0] == want["total"] and np.array_equal(data, want["data"])
+    assert calc.check_grant_log(log, tick, B, A, fifo=False, per_die=True) == []
+
+
+@pytest.mark.parametrize("budget", [1, 2, 64, 32767])
+def test_cohort_budgets(budget):
+    # budget 1: every acquisition goes through the global lock; 32767: passes stay on a die
+    # for as long as it has waiters.
+    from paper_1110_4623_gb300 import runner
+    B, A, K = 592, 30, 64
+    delay, add = inputs.mutex_inputs(B, A, 900 + budget, max_delay=500)
+    mr = runner.MutexRun("cohort", B, 256, A, K, delay, add, budget=budget, timeout_ns=10_000_000_000)
+    got = mr.run()
+    want = calc.mutex_final(B, A, K, add)
+    assert got["status"] == 0 and got["total"] == want["total"] and np.array_equal(got["data"], want["data"])
+    assert grant_problems("cohort", got, B, A) == []
+
+
+def test_cohort_local_locks_are_homed_on_their_dies():
+    # Each die's local lock sits on a page that is near (short atomic round trip) to the SMs
+    # of that die and far from the other die's SMs.
+    import torch
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    die, ndies = runner.device_topology()
+    if ndies < 2:
+        pytest.skip("one-die GPU")
+    mr = runner.MutexRun("cohort", 8, 128, 1, 1, None, np.zeros(8, np.uint32))
+    hdr = mr.state[:64].view(torch.int32).cpu().numpy()
+    sm = {d: int(np.flatnonzero(die == d)[0]) for d in (0, 1)}
+    for d, word in ((0, hdr[10]), (1, hdr[11])):
+        line = mr.state[4 * int(word):]
+        near = runner.probe_rtt_by_line(sm[d], line, 1)[0]
+        far = runner.probe_rtt_by_line(sm[1 - d], line, 1)[0]
+        assert near + 60 < far, (d, near, far)

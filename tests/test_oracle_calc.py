@@ -125,6 +125,24 @@ def test_grant_log_checks():
     assert calc.check_grant_log(good, tick3, B, A, fifo=True, ticket_base=base) == []
 
 
+def test_grant_log_per_die():
+    # Grants s = 0..5 of acquisitions good[s]; dies alternate 0,1,1,0,0,1; each die's tickets
+    # count from its own base in grant order, with bit 31 marking die 1.
+    B, A = 3, 2
+    good = np.array([0, 2, 4, 1, 3, 5])
+    die = np.array([0, 1, 1, 0, 0, 1])
+    local = np.array([5, 9, 10, 6, 7, 11])  # die 0 from 5, die 1 from 9
+    tick = np.empty(6, np.uint32)
+    tick[good] = ((die.astype(np.uint64) << np.uint64(31)) | local.astype(np.uint64)).astype(np.uint32)
+    assert calc.check_grant_log(good, tick, B, A, fifo=False, per_die=True, die_bases=(5, 9)) == []
+    assert calc.die_grant_counts(tick) == (3, 3)
+    assert calc.check_grant_log(good, tick, B, A, fifo=False, per_die=True, die_bases=(5, 8))
+    bad = tick.copy(); bad[[good[0], good[3]]] = bad[[good[3], good[0]]]  # die 0 out of order
+    assert "die 0" in calc.check_grant_log(good, bad, B, A, fifo=False, per_die=True, die_bases=(5, 9))[0]
+    # a single global ticket order is not a per-die order once dies interleave
+    assert calc.check_grant_log(good, tick, B, A, fifo=True)
+
+
 # ---- semaphore, batched, serving --------------------------------------------------------
 
 def test_sem_closed_forms():

@@ -18,6 +18,11 @@ CORRECT = [
     ("queue_wrap", mc.QueueMutex(q=4, base=W), 3, 2),
     ("queue_exact_fit", mc.QueueMutex(q=2, base=W), 2, 3),
     ("ring", mc.RingMutex(q=4), 3, 2),
+    ("cohort_budget_1", mc.CohortMutex(budget=1), 4, 1),
+    ("cohort_budget_2", mc.CohortMutex(budget=2), 3, 2),
+    ("cohort_budget_2_4x2", mc.CohortMutex(budget=2), 4, 2),
+    ("cohort_budget_3", mc.CohortMutex(budget=3), 3, 2),
+    ("cohort_wrap", mc.CohortMutex(budget=2, base=W, gbase=0xFFFE), 3, 2),
     ("spin_sem_1", mc.SpinSem(n=1), 3, 2),
     ("spin_sem_2", mc.SpinSem(n=2), 3, 2),
     ("spin_sem_2_backoff", mc.SpinSem(n=2, backoff=True), 3, 2),
@@ -50,6 +55,10 @@ BROKEN = [
     ("test_then_set", mc.SpinMutex(broken="test_then_set"), 2, 1, "critical section"),
     ("ticket_no_advance", mc.TicketMutex(broken="no_advance"), 2, 2, "final state"),
     ("ring_no_clear", mc.RingMutex(q=2, broken="no_clear"), 2, 3, "grant"),
+    ("cohort_no_global", mc.CohortMutex(broken="no_global"), 2, 1, "critical section"),
+    ("cohort_owned_on_release", mc.CohortMutex(broken="owned_on_release"), 2, 2, "critical section"),
+    ("cohort_pass_always", mc.CohortMutex(broken="pass_always"), 2, 2, "final state"),
+    ("cohort_skip_ticket", mc.CohortMutex(broken="skip_ticket"), 3, 2, "local ticket"),
     ("sleep_sem_turn_ge", mc.SleepSem(n=1, broken="turn_ge"), 3, 1, "critical section"),
     ("barrier_no_wait", mc.AtomicBarrier(broken="no_wait"), 3, 1, "passed round"),
     ("flag_skip_last", mc.FlagBarrier(broken="skip_last"), 3, 1, "passed round"),
