@@ -4,7 +4,8 @@ One step = one pass over every row of the hot path at 1184 blocks:
   * mutex contention (the paper's 4 kinds and the two-die cohort lock x critical sections of
     0/64/1024 words, 256 threads per block,
     100 acquisitions per block, seeded delays U{0..2000} cycles),
-  * grid barriers (atomic, flag, tree, cluster 2/4/8, sharded; 128 threads, 1000 rounds each),
+  * grid barriers (atomic, flag, tree, cluster 2/4/8, sharded, two-die, split; 128 threads,
+    1000 rounds each),
   * counting semaphores (sleeping FA kind, n in {1, 4, 16, 64}; 128 threads, 200 pairs each,
     hold U{100..5000} cycles).
 `value` is lock acquisitions per second of the library's default mutex kind over its three
@@ -40,7 +41,7 @@ SEM_THREADS, SEM_PAIRS, SEM_COUNTS = 128, 200, (1, 4, 16, 64)
 DEFAULT_MUTEX = "cohort"
 DEFAULT_BARRIER = ("atomic", 0)
 BARRIERS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("cluster", 2), ("cluster", 4), ("cluster", 8),
-            ("sharded", 32), ("sharded", 8)]
+            ("sharded", 32), ("sharded", 8), ("die", 0), ("split", 16 | 16 << 8)]
 # Backoff (min_ns, max_ns) per kind; the ticket kinds sleep min_ns per waiter ahead, capped.
 MUTEX_BACKOFF = {"cas_backoff": (16, 512), "ticket": (128, 4000), "cohort": (128, 4000)}
 SEM_BACKOFF = (64, 2000)
@@ -96,6 +97,8 @@ def barrier_name(kind, param):
         return "flag_broadcast" if param else "flag"
     if kind in ("tree", "cluster", "sharded"):
         return f"{kind}{param}"
+    if kind == "split":
+        return f"split{param & 0xFF}x{param >> 8}"
     return kind
 
 
@@ -207,14 +210,21 @@ def sem_roof_ops_s(terms, n):
 
 
 def barrier_roof_ns(terms, kind, param, B):
-    """One atomic round trip, one hand-off, and the arrivals through the busiest atomic unit."""
+    """One atomic round trip, one hand-off, and the arrivals through the busiest atomic unit
+    (DIE: the larger die's share of the blocks, and one more round trip for the top counter)."""
+    rts = 1
     if kind == "cluster":
         b_eff = B / param
     elif kind in ("sharded", "flag"):
         b_eff = B / (param if kind == "sharded" else B)
+    elif kind == "die":
+        b_eff, rts = B / 2, 2
+    elif kind == "split":
+        S = param & 0xFF
+        b_eff, rts = (-(-B // S) + S, 2) if S > 1 else (B, 1)
     else:
         b_eff = B
-    return terms["L_rt_ns"] + terms["L_handoff_ns"] + b_eff / terms["R_same_atom_ops_s"] * 1e9
+    return rts * terms["L_rt_ns"] + terms["L_handoff_ns"] + b_eff / terms["R_same_atom_ops_s"] * 1e9
 
 
 # ------------------------------------------------------------------------------------------

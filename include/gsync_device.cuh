@@ -503,7 +503,7 @@ __device__ __forceinline__ int sem_post(const SemRef& s) {
 // ---------------------------------------------------------------------------------------
 // Grid barrier (Section 5 "Barrier"): every block of the grid participates.
 // ---------------------------------------------------------------------------------------
-// ATOMIC : line 1 arrival counter, line 2 release epoch.
+// ATOMIC : lines 1 and 3 arrival counters (odd and even epochs), line 2 release epoch.
 // FLAG   : lines 1.. arrival flags (one word per block, packed), then release flags (one
 //          word per block, packed; mode 1: a single release word on its own line).  At most
 //          8192 blocks; the master block's threads gather the flags.
@@ -516,12 +516,30 @@ __device__ __forceinline__ int sem_post(const SemRef& s) {
 //          the hardware cluster barrier, which cannot time out: every block of a cluster must
 //          make the same number of barrier_wait calls, also after one returned an error (the
 //          object's abort word makes those calls return quickly).
+// DIE    : line 1 a flat arrival counter (registration crossings), line 2 {members of die
+//          0, members of die 1, blocks of die 0, blocks of die 1, dies with blocks}, lines
+//          3-4 the SM-to-die table; for each die d, at word offset kHdrDieOff<d> (on a 4 KB
+//          page homed on die d): line 0 the arrival counter of odd epochs, line 1 the
+//          release epoch, line 3 the arrival counter of even epochs; die 0's lines 2 and 4
+//          are the top counters of odd and even epochs.  A block's first crossing of a launch
+//          registers it (flat count, membership per die); later crossings count in per die,
+//          and the second die to finish releases both.
+// SPLIT  : param = S | R << 8 (1..64 each).  Lines 1..R the release copies, then 2S arrival
+//          counters (S of odd epochs, then S of even epochs), then the top counters of odd and
+//          even epochs.  Block b counts in on counter b mod S and polls copy b mod R; the last
+//          arriver at a counter counts in at the top (when S > 1), and the last there writes
+//          every copy.  The blocks that used a counter reset it (the releaser after the
+//          release), as in counter_arrive_wait.
 // Epochs increase by one per crossing and are compared for equality, so no phase resets.
 struct BarrierRef {
   uint32_t* s;
   uint32_t kind, n, param, mode;
   uint32_t epoch;  // epoch of the last crossing, kept by each block
   uint64_t timeout_ns;
+  uint32_t die, n_mine, active;  // DIE: this block's die, its die's blocks (0 = unregistered), dies
+  __device__ __forceinline__ uint32_t* die_line(uint32_t d, uint32_t i) const {
+    return s + s[d ? kHdrDieOff1 : kHdrDieOff0] + i * kLineWords;
+  }
   __device__ __forceinline__ uint32_t* line(uint32_t i) const { return s + i * kLineWords; }
   __device__ __forceinline__ uint32_t* abort_word() const { return s + kHdrAbort; }
   __device__ __forceinline__ uint32_t flag_lines() const { return (n + kLineWords - 1) / kLineWords; }
@@ -541,23 +559,116 @@ __device__ __forceinline__ BarrierRef barrier_attach(void* state) {
   b.param = b.s[kHdrParam];
   b.mode = b.s[kHdrMode];
   b.timeout_ns = header_timeout(b.s);
+  b.die = 0;
   if (b.kind == GSYNC_BAR_FLAG || b.kind == GSYNC_BAR_SHARDED) {
     // A block's own release flag always holds the epoch of the last crossing.
     b.epoch = b.mode ? ptx::ld_relaxed(b.release_flags()) : ptx::ld_relaxed(b.release_flags() + blockIdx.x);
   } else if (b.kind == GSYNC_BAR_TREE) {
     b.epoch = ptx::ld_relaxed(b.line(1));
+  } else if (b.kind == GSYNC_BAR_SPLIT) {
+    b.epoch = ptx::ld_relaxed(b.line(1u + blockIdx.x % (b.param >> 8)));
+  } else if (b.kind == GSYNC_BAR_DIE) {
+    const uint32_t sm = ptx::smid();
+    const uint8_t* table = (const uint8_t*)(b.s + kDieTableWord);
+    b.die = (sm < kMaxSmIds && table[sm]) ? 1u : 0u;
+    b.epoch = ptx::ld_relaxed(b.die_line(b.die, 1));  // both dies' release words move together
   } else {
     b.epoch = ptx::ld_relaxed(b.line(2));
   }
+  b.n_mine = 0;
+  b.active = 0;
   return b;
 }
 
-// Master-thread arrival on a two-stage atomic counter of `parties` participants.
+// Bounded poll of a release word until it holds e1 (acquire).
+__device__ __forceinline__ int wait_epoch(const BarrierRef& b, const uint32_t* rel, uint32_t e1) {
+  Waiter w;
+  while (ptx::ld_acquire(rel) != e1)
+    if (int rc = w.tick(b.timeout_ns, b.abort_word())) return rc;
+  return GSYNC_OK;
+}
+
+// Master thread of a SPLIT barrier (see the layout above).
+__device__ __forceinline__ int split_arrive_wait(const BarrierRef& b, uint32_t e1) {
+  const uint32_t S = b.param & 0xFFu, R = b.param >> 8;
+  const uint32_t groups = min(S, b.n), c = blockIdx.x % S;
+  const uint32_t members = (b.n - c + S - 1u) / S;
+  const bool odd = (e1 & 1u) != 0u;
+  uint32_t* cnt = b.line(1u + R + (odd ? 0u : S) + c);
+  uint32_t* top = b.line(1u + R + 2u * S + (odd ? 0u : 1u));
+  uint32_t* rel = b.line(1u + blockIdx.x % R);
+  if (ptx::atom_add_acq_rel(cnt, 1u) != members - 1u) return wait_epoch(b, rel, e1);
+  if (groups > 1u && ptx::atom_add_acq_rel(top, 1u) != groups - 1u) {
+    ptx::st_relaxed(cnt, 0u);
+    return wait_epoch(b, rel, e1);
+  }
+  ptx::fence_acq_rel();  // release: everything acquired above precedes every copy
+  for (uint32_t r = 0; r < R; ++r) ptx::st_relaxed(b.line(1u + r), e1);
+  ptx::st_relaxed(cnt, 0u);
+  if (groups > 1u) ptx::st_relaxed(top, 0u);
+  return GSYNC_OK;
+}
+
+// Master thread of a DIE barrier (see the layout above).
+__device__ __forceinline__ int die_arrive_wait(BarrierRef& b, uint32_t e1) {
+  uint32_t* rel = b.die_line(b.die, 1);
+  uint32_t* info = b.line(2);
+  if (b.n_mine == 0) {
+    // Registration crossing: count in on the flat counter, and into this die's membership.
+    ptx::red_add_relaxed(info + b.die, 1u);
+    const uint32_t old = ptx::atom_add_acq_rel(b.line(1), 1u);  // release: orders the red above
+    int rc = GSYNC_OK;
+    if (old == b.n - 1u) {
+      ptx::st_relaxed(b.line(1), 0u);
+      const uint32_t m0 = ptx::ld_relaxed(info), m1 = ptx::ld_relaxed(info + 1);
+      ptx::st_relaxed(info, 0u);
+      ptx::st_relaxed(info + 1, 0u);
+      ptx::st_relaxed(info + 2, m0);
+      ptx::st_relaxed(info + 3, m1);
+      ptx::st_relaxed(info + 4, (m0 ? 1u : 0u) + (m1 ? 1u : 0u));
+      ptx::fence_acq_rel();  // release: everything above precedes both release words
+      ptx::st_relaxed(b.die_line(0, 1), e1);
+      ptx::st_relaxed(b.die_line(1, 1), e1);
+    } else {
+      rc = wait_epoch(b, rel, e1);
+    }
+    if (rc == GSYNC_OK) {
+      b.n_mine = ptx::ld_relaxed(info + 2 + b.die);
+      b.active = ptx::ld_relaxed(info + 4);
+    }
+    return rc;
+  }
+  // Counters alternate by epoch parity (as in counter_arrive_wait): the releasing block
+  // resets the ones it used after the release.
+  const bool odd = (e1 & 1u) != 0u;
+  uint32_t* cnt = b.die_line(b.die, odd ? 0u : 3u);
+  const uint32_t old = ptx::atom_add_acq_rel(cnt, 1u);
+  if (old != b.n_mine - 1u) return wait_epoch(b, rel, e1);
+  // Last of this die; the second die to get here releases both dies.
+  uint32_t* top = b.die_line(0, odd ? 2u : 4u);
+  if (b.active == 2u && ptx::atom_add_acq_rel(top, 1u) != 1u) {
+    ptx::st_relaxed(cnt, 0u);
+    return wait_epoch(b, rel, e1);
+  }
+  ptx::fence_acq_rel();
+  ptx::st_relaxed(b.die_line(0, 1), e1);
+  ptx::st_relaxed(b.die_line(1, 1), e1);
+  ptx::st_relaxed(cnt, 0u);
+  if (b.active == 2u) ptx::st_relaxed(top, 0u);
+  return GSYNC_OK;
+}
+
+// Master-thread arrival on a two-stage atomic counter of `parties` participants.  Crossings
+// alternate between two counters (lines 1 and 3, by epoch parity), so the last arriver
+// releases first and resets its counter after, off the release path: the counter is next
+// used two crossings later, which no block can reach before the last arriver has arrived at
+// the crossing in between.
 __device__ __forceinline__ int counter_arrive_wait(const BarrierRef& b, uint32_t parties, uint32_t e1) {
-  const uint32_t old = ptx::atom_add_acq_rel(b.line(1), 1u);
+  uint32_t* cnt = b.line((e1 & 1u) ? 1u : 3u);
+  const uint32_t old = ptx::atom_add_acq_rel(cnt, 1u);
   if (old == parties - 1u) {
-    ptx::st_relaxed(b.line(1), 0u);
     ptx::st_release(b.line(2), e1);
+    ptx::st_relaxed(cnt, 0u);
     return GSYNC_OK;
   }
   Waiter w;
@@ -578,6 +689,10 @@ __device__ __forceinline__ int barrier_wait(BarrierRef& b) {
   }
   if (KIND == GSYNC_BAR_ATOMIC) {
     if (master) s_rc = counter_arrive_wait(b, b.n, e1);
+  } else if (KIND == GSYNC_BAR_DIE) {
+    if (master) s_rc = die_arrive_wait(b, e1);
+  } else if (KIND == GSYNC_BAR_SPLIT) {
+    if (master) s_rc = split_arrive_wait(b, e1);
   } else if (KIND == GSYNC_BAR_CLUSTER) {
     if (master) {
       int rc = GSYNC_OK;

@@ -27,6 +27,8 @@ The algorithms follow Section 5 ("Design") and the pseudocode of the Appendix:
   TreeBarrier   combining-tree barrier (Section 2, hierarchical barriers)
   ShardedBarrier  arrivals counted on several counters, gathered by the master block
   ClusterBarrier  barrier inside groups of c blocks, then one leader per group globally
+  DieBarrier    per-die counters and release words, a top counter between the dies
+  SplitBarrier  S arrival counters under a top counter, R copies of the release word
 Mutation variants with a planted mistake (`broken=...`) exist so that tests can show the
 checker catches each kind of error.
 """
@@ -430,31 +432,202 @@ class SleepSem:
 class AtomicBarrier:
     """Two-stage atomic barrier: stage 1 counts arrivals with fetch-and-add; the last arriver
     resets the counter and advances the release epoch; stage 2 polls the epoch.  Each block
-    keeps its expected epoch locally.  broken="no_wait": non-last arrivers leave at once."""
+    keeps its expected epoch locally.  broken="no_wait": non-last arrivers leave at once.
+
+    parity=True (the library's form): crossing e counts on counter e mod 2, and the last
+    arriver advances the epoch first and resets that counter after, off the release path; the
+    counter is next used two crossings later, which cannot start before the last arriver has
+    arrived at the crossing in between.  broken="reset_one_counter": parity counting with the
+    reset after the release but a single counter (a fast block can count into the next
+    crossing before the reset)."""
     kind = "barrier"
 
-    def __init__(self, base=0, broken=None):
+    def __init__(self, base=0, broken=None, parity=False):
         self.base, self.broken = base & M32, broken
+        self.parity = parity or broken == "reset_one_counter"
 
     def init(self, nproc, ops):
-        return (0, self.base), tuple((0, 0, self.base, 0) for _ in range(nproc))
+        return (0, 0, self.base), tuple((0, 0, self.base, 0) for _ in range(nproc))
 
     def step(self, p, loc, sh, nproc, ops):
         pc, k, e, r = loc
-        count, release = sh
+        counts, release = sh[:2], sh[2]
+        c = (inc(e) & 1) if self.parity and self.broken != "reset_one_counter" else 0
         if pc == 0:
-            last = count + 1 == nproc
-            return ((1 if last else 3), k, e, r), (count + 1, release), ("arrive",)
-        if pc == 1:
-            return (2, k, e, r), (0, release), None
-        if pc == 2:
-            k += 1
-            return ((0 if k < ops else DONE), k, inc(e), r), (count, inc(e)), ("pass",)
+            last = counts[c] + 1 == nproc
+            return ((1 if last else 3), k, e, r), _set(counts, c, counts[c] + 1) + (release,), ("arrive",)
+        if not self.parity:
+            if pc == 1:
+                return (2, k, e, r), _set(counts, c, 0) + (release,), None
+            if pc == 2:
+                k += 1
+                return ((0 if k < ops else DONE), k, inc(e), r), counts + (inc(e),), ("pass",)
+        else:
+            if pc == 1:  # release first ...
+                return (2, k, e, r), counts + (inc(e),), ("pass",)
+            if pc == 2:  # ... then reset the counter this crossing used
+                k += 1
+                return ((0 if k < ops else DONE), k, inc(e), r), _set(counts, c, 0) + (release,), None
         if pc == 3:
             if release == inc(e) or self.broken == "no_wait":
                 k += 1
                 return ((0 if k < ops else DONE), k, inc(e), r), sh, ("pass",)
             return loc, sh, None
+        raise AssertionError(pc)
+
+
+class SplitBarrier:
+    """Split barrier: block p counts in on counter p mod S; the last arriver at a counter
+    counts in on a top counter (skipped when S = 1), and the last arriver there writes the
+    new epoch to R release copies; block p polls copy p mod R.  Counters alternate by epoch
+    parity and the block that used one resets it (after the release when it released, before
+    waiting otherwise).  broken="one_copy_early": the releaser passes after writing only the
+    first copy and the rest never get written.  broken="no_top": the last arriver at any
+    counter releases."""
+    kind = "barrier"
+
+    def __init__(self, S=2, R=2, base=0, broken=None):
+        self.S, self.R, self.base, self.broken = S, R, base & M32, broken
+
+    def init(self, nproc, ops):
+        e = self.base
+        # (counters[par][S] flattened: 2S, top[2], release[R])
+        return (0,) * (2 * self.S + 2) + (e,) * self.R, tuple((0, 0, e, 0) for _ in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, e, j = loc  # j: copy index being written by the releaser
+        S, R = self.S, self.R
+        e1 = inc(e)
+        par = e1 & 1
+        c = p % S
+        ci, ti, rel0 = par * S + c, 2 * S + par, 2 * S + 2
+        members = len(range(c, nproc, S))
+        groups = min(S, nproc)
+
+        def passed():
+            k2 = k + 1
+            return ((0 if k2 < ops else DONE), k2, e1, 0)
+
+        if pc == 0:
+            last = sh[ci] + 1 == members
+            nxt = (1 if groups > 1 and self.broken != "no_top" else 3) if last else 6
+            return (nxt, k, e, 0), _set(sh, ci, sh[ci] + 1), ("arrive",)
+        if pc == 1:  # last at its counter: count in at the top
+            last = sh[ti] + 1 == groups
+            return ((3 if last else 2), k, e, 0), _set(sh, ti, sh[ti] + 1), None
+        if pc == 2:  # not the releaser: reset the counter, then wait
+            return (6, k, e, 0), _set(sh, ci, 0), None
+        if pc == 3:  # releaser: write the copies one by one
+            sh2 = _set(sh, rel0 + j, e1)
+            if j + 1 < R and self.broken != "one_copy_early":
+                return (3, k, e, j + 1), sh2, None
+            return (4, k, e, 0), sh2, ("pass",)
+        if pc == 4:
+            sh2 = _set(sh, ci, 0)
+            if groups > 1:
+                sh2 = _set(sh2, ti, 0)
+            return passed(), sh2, None
+        if pc == 6:
+            if sh[rel0 + p % R] != e1:
+                return loc, sh, None
+            return passed(), sh, ("pass",)
+        raise AssertionError(pc)
+
+
+class DieBarrier:
+    """Two-die barrier: blocks count in on their own die's counter and poll their own die's
+    release word (both homed on that die); the last arriver of each die counts in on a top
+    counter, and the second die to finish releases both dies.
+
+    The blocks per die are not known in advance: a block's first crossing of a launch is a
+    registration crossing that counts all blocks on one flat counter while each block also
+    counts itself into its die's membership word; the last arriver turns the membership into
+    the dies' block counts and the number of dies with blocks, resets it, and releases both
+    dies.  Later crossings use the per-die counters, two of each (and two top counters) by
+    epoch parity: the releasing block resets the counters it used after the release, and a
+    die leader that does not release resets its die counter before it waits.
+    layout[p] is block p's die.
+    broken="no_top": a die's last arriver releases without waiting for the other die.
+    broken="no_reset": a die's last arriver does not reset its die's counter.
+    """
+    kind = "barrier"
+
+    def __init__(self, layout=None, base=0, broken=None):
+        self.layout, self.base, self.broken = layout, base & M32, broken
+
+    def die(self, p):
+        return self.layout[p] if self.layout is not None else p % 2
+
+    def init(self, nproc, ops):
+        if self.layout is not None:
+            assert len(self.layout) == nproc
+        e = self.base
+        # (cnt_all, mem0, mem1, n0, n1, active, cnt[d=0,par=0], cnt[0,1], cnt[1,0], cnt[1,1],
+        #  top[0], top[1], rel0, rel1)
+        sh = (0,) * 12 + (e, e)
+        return sh, tuple((0, 0, e, 0, 0) for _ in range(nproc))  # (pc, k, epoch, n_mine, active)
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, e, nm, act = loc
+        d = self.die(p)
+        e1 = inc(e)
+        par = e1 & 1
+        CNT_ALL, MEM, N, ACT, CNT, TOP, REL = 0, 1, 3, 5, 6, 10, 12
+        ci, ti = CNT + 2 * d + par, TOP + par
+
+        def passed(n_mine=nm, active=act):
+            k2 = k + 1
+            return ((0 if k2 < ops else DONE), k2, e1, n_mine, active)
+
+        if pc == 0:
+            return ((10 if nm == 0 else 20), k, e, nm, act), sh, None
+        # registration crossing
+        if pc == 10:
+            return (11, k, e, nm, act), _set(sh, MEM + d, sh[MEM + d] + 1), None
+        if pc == 11:
+            last = sh[CNT_ALL] + 1 == nproc
+            return ((12 if last else 16), k, e, nm, act), _set(sh, CNT_ALL, sh[CNT_ALL] + 1), ("arrive",)
+        if pc == 12:
+            return (13, k, e, nm, act), _set(sh, CNT_ALL, 0), None
+        if pc == 13:
+            m0, m1 = sh[MEM], sh[MEM + 1]
+            sh2 = sh[:MEM] + (0, 0, m0, m1, int(m0 > 0) + int(m1 > 0)) + sh[ACT + 1:]
+            return (14, k, e, nm, act), sh2, None
+        if pc == 14:
+            return (15, k, e, nm, act), _set(sh, REL, e1), None
+        if pc == 15:
+            return passed(sh[N + d], sh[ACT]), _set(sh, REL + 1, e1), ("pass",)
+        if pc == 16:
+            if sh[REL + d] != e1:
+                return loc, sh, None
+            return passed(sh[N + d], sh[ACT]), sh, ("pass",)
+        # per-die crossing
+        if pc == 20:
+            last = sh[ci] + 1 == nm
+            return ((21 if last else 26), k, e, nm, act), _set(sh, ci, sh[ci] + 1), ("arrive",)
+        if pc == 21:
+            return ((24 if act == 1 or self.broken == "no_top" else 22), k, e, nm, act), sh, None
+        if pc == 22:
+            last = sh[ti] == 1
+            return ((24 if last else 27), k, e, nm, act), _set(sh, ti, sh[ti] + 1), None
+        if pc == 27:  # leader of the first die to finish: reset, then wait
+            sh2 = sh if self.broken == "no_reset" else _set(sh, ci, 0)
+            return (26, k, e, nm, act), sh2, None
+        if pc == 24:
+            return (25, k, e, nm, act), _set(sh, REL, e1), None
+        if pc == 25:
+            return (28, k, e, nm, act), _set(sh, REL + 1, e1), ("pass",)
+        if pc == 28:  # after the release: reset the counters this crossing used
+            sh2 = sh if self.broken == "no_reset" else _set(sh, ci, 0)
+            return ((29 if act == 2 and self.broken != "no_top" else 30), k, e, nm, act), sh2, None
+        if pc == 29:
+            return (30, k, e, nm, act), _set(sh, ti, 0), None
+        if pc == 30:
+            return passed(), sh, None
+        if pc == 26:
+            if sh[REL + d] != e1:
+                return loc, sh, None
+            return passed(), sh, ("pass",)
         raise AssertionError(pc)
 
 

@@ -105,6 +105,8 @@ KernelFn pick(int kind, int full) {
     case GSYNC_BAR_TREE: return full ? barrier_workload_kernel<GSYNC_BAR_TREE, true> : barrier_workload_kernel<GSYNC_BAR_TREE, false>;
     case GSYNC_BAR_CLUSTER: return full ? barrier_workload_kernel<GSYNC_BAR_CLUSTER, true> : barrier_workload_kernel<GSYNC_BAR_CLUSTER, false>;
     case GSYNC_BAR_SHARDED: return full ? barrier_workload_kernel<GSYNC_BAR_SHARDED, true> : barrier_workload_kernel<GSYNC_BAR_SHARDED, false>;
+    case GSYNC_BAR_DIE: return full ? barrier_workload_kernel<GSYNC_BAR_DIE, true> : barrier_workload_kernel<GSYNC_BAR_DIE, false>;
+    case GSYNC_BAR_SPLIT: return full ? barrier_workload_kernel<GSYNC_BAR_SPLIT, true> : barrier_workload_kernel<GSYNC_BAR_SPLIT, false>;
   }
   return nullptr;
 }
@@ -116,6 +118,8 @@ KernelFn pick_trace(int kind) {
     case GSYNC_BAR_TREE: return barrier_workload_kernel<GSYNC_BAR_TREE, false, true>;
     case GSYNC_BAR_CLUSTER: return barrier_workload_kernel<GSYNC_BAR_CLUSTER, false, true>;
     case GSYNC_BAR_SHARDED: return barrier_workload_kernel<GSYNC_BAR_SHARDED, false, true>;
+    case GSYNC_BAR_DIE: return barrier_workload_kernel<GSYNC_BAR_DIE, false, true>;
+    case GSYNC_BAR_SPLIT: return barrier_workload_kernel<GSYNC_BAR_SPLIT, false, true>;
   }
   return nullptr;
 }

@@ -96,7 +96,7 @@ uint32_t barrier_lines(int kind, uint32_t n, uint32_t param) {
   switch (kind) {
     case GSYNC_BAR_ATOMIC:
     case GSYNC_BAR_CLUSTER:
-      return 3;
+      return 4;
     case GSYNC_BAR_FLAG: {
       const uint32_t fl = (n + 31) / 32;
       return 1 + fl + (param ? 1 : fl);
@@ -105,6 +105,10 @@ uint32_t barrier_lines(int kind, uint32_t n, uint32_t param) {
       return 2 + tree_nodes(n, param);
     case GSYNC_BAR_SHARDED:
       return 1 + param + (n + 31) / 32;
+    case GSYNC_BAR_DIE:
+      return (uint32_t)(kCohortBytes / kLine);
+    case GSYNC_BAR_SPLIT:
+      return 1 + (param >> 8) + 2 * (param & 0xFFu) + 2;
   }
   return 0;
 }
@@ -123,27 +127,30 @@ size_t gsync_mutex_bytes(int kind, int max_waiters) {
   return (size_t)(3 + q) * kLine;
 }
 
-int gsync_mutex_init_cohort(void* state, size_t bytes, int budget, const gsync_backoff* backoff, uint64_t timeout_ns,
-                            void* stream) {
-  if (!state || !aligned(state, kLine) || bytes < kCohortBytes || budget < 1 || budget > 32767) return GSYNC_EINVAL;
-  if (backoff && backoff->policy > GSYNC_BACKOFF_LINEAR_CYCLIC) return GSYNC_EINVAL;
-  cudaStream_t st = (cudaStream_t)stream;
-  InitSpec spec;
-  fill_header(spec, kPrimMutex, GSYNC_MUTEX_COHORT, 0, (uint32_t)budget, backoff, timeout_ns, 0);
+}  // extern "C"
+
+namespace {
+
+// Two-die objects (COHORT mutex, DIE barrier): measures the SM-to-die map and the home die
+// of the state's 4 KB pages, puts each die's per-die lines on a page homed on that die, and
+// fills the header offsets and the die table of `spec`.
+int place_on_dies(void* state, InitSpec& spec, cudaStream_t st) {
   uint8_t die[gsync::kMaxSmIds];
   int ndies = 1, sms = 0;
   if (int rc = device_topology(st, die, &ndies, &sms)) return rc;
-  // Candidate pages for the local locks: every 4 KB boundary past the header, global lock and
-  // die table (lines 0-4) with two lines of room before the end of the state.
+  // Candidate pages for the per-die lines (at most five per die): every 4 KB boundary past
+  // the shared lines and the die table (lines 0-4) with five lines of room before the end.
+  constexpr uintptr_t kDieLines = 5;
   const uintptr_t lo = (uintptr_t)state, hi = lo + kCohortBytes;
   const uintptr_t first = (lo + 5 * kLine + kPage - 1) & ~(uintptr_t)(kPage - 1);
-  const int npages = first + 2 * kLine <= hi ? (int)((hi - 2 * kLine - first) / kPage) + 1 : 0;
+  const int npages =
+      first + kDieLines * kLine <= hi ? (int)((hi - kDieLines * kLine - first) / kPage) + 1 : 0;
   if (npages < 2) return GSYNC_EINVAL;
   uint8_t home[gsync::kMaxSmIds] = {};
   if (ndies == 2)
     if (int rc = line_homes((const void*)first, npages, kPage, die, sms, st, home)) return rc;
-  // Die d's local lock goes on the first page homed on d; a die with no such page (or a
-  // one-die GPU) takes the next unused page, which only costs locality.
+  // Die d's lines go on the first page homed on d; a die with no such page (or a one-die
+  // GPU) takes the next unused page, which only costs locality.
   int page[2] = {-1, -1};
   for (int d = 0; d < 2; ++d)
     for (int i = 0; i < npages && page[d] < 0; ++i)
@@ -157,6 +164,21 @@ int gsync_mutex_init_cohort(void* state, size_t bytes, int budget, const gsync_b
   spec.die_table = 1;
   memset(spec.die, 0, sizeof spec.die);
   for (int i = 0; i < sms; ++i) ((uint8_t*)spec.die)[i] = ndies == 2 ? die[i] : 0;
+  return GSYNC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gsync_mutex_init_cohort(void* state, size_t bytes, int budget, const gsync_backoff* backoff, uint64_t timeout_ns,
+                            void* stream) {
+  if (!state || !aligned(state, kLine) || bytes < kCohortBytes || budget < 1 || budget > 32767) return GSYNC_EINVAL;
+  if (backoff && backoff->policy > GSYNC_BACKOFF_LINEAR_CYCLIC) return GSYNC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  InitSpec spec;
+  fill_header(spec, kPrimMutex, GSYNC_MUTEX_COHORT, 0, (uint32_t)budget, backoff, timeout_ns, 0);
+  if (int rc = place_on_dies(state, spec, st)) return rc;
   return launch_init(state, bytes, spec, st);
 }
 
@@ -183,6 +205,12 @@ size_t gsync_barrier_bytes(int kind, int nblocks, int param) {
     case GSYNC_BAR_TREE: if (param < 2 || param > 1024) return 0; break;
     case GSYNC_BAR_CLUSTER: if (param < 1 || param > 8 || nblocks % param) return 0; break;
     case GSYNC_BAR_SHARDED: if (param < 1 || param > 32 || param > nblocks) return 0; break;
+    case GSYNC_BAR_DIE: if (param != 0) return 0; break;
+    case GSYNC_BAR_SPLIT: {
+      const int S = param & 0xFF, R = param >> 8;
+      if (param < 0 || S < 1 || S > 64 || R < 1 || R > 64) return 0;
+      break;
+    }
     default: return 0;
   }
   return (size_t)barrier_lines(kind, (uint32_t)nblocks, (uint32_t)param) * kLine;
@@ -195,6 +223,8 @@ int gsync_barrier_init(void* state, size_t bytes, int kind, int nblocks, int par
   InitSpec spec;
   const uint32_t mode = kind == GSYNC_BAR_FLAG ? (uint32_t)param : 0u;
   fill_header(spec, kPrimBarrier, (uint32_t)kind, (uint32_t)nblocks, (uint32_t)param, nullptr, timeout_ns, mode);
+  if (kind == GSYNC_BAR_DIE)
+    if (int rc = place_on_dies(state, spec, (cudaStream_t)stream)) return rc;
   spec.nwords = (uint32_t)(need / 4);
   return launch_init(state, bytes, spec, (cudaStream_t)stream);
 }

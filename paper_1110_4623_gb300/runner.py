@@ -63,6 +63,8 @@ class BarrierRun:
             param = 2
         if kind == "sharded" and param == 0:
             param = min(32, nblocks)
+        if kind == "split" and param == 0:
+            param = 8 | 8 << 8
         self.param = param
         nbytes = G.gsync_barrier_bytes(self.k, nblocks, param)
         self.state = _state(nbytes)

@@ -56,13 +56,22 @@ def test_size_queries_without_gpu(lib_path):
     assert G.gsync_mutex_bytes(G.MUTEX_KINDS["cas_spin"], 1184) == 3 * 128
     assert G.gsync_mutex_bytes(G.MUTEX_KINDS["sleep_queue"], 1184) == (3 + 2048) * 128
     assert G.gsync_mutex_bytes(9, 4) == 0 and G.gsync_mutex_bytes(0, 0) == 0
-    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["atomic"], 1184, 0) == 3 * 128
+    # two arrival counters (by epoch parity) and the release epoch
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["atomic"], 1184, 0) == 4 * 128
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["flag"], 1184, 0) == (1 + 37 + 37) * 128
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["flag"], 1184, 1) == (1 + 37 + 1) * 128
     # fan-in 8 over 1184 blocks: 148 + 19 + 3 + 1 nodes
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["tree"], 1184, 8) == (2 + 148 + 19 + 3 + 1) * 128
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["tree"], 16, 1) == 0
-    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["cluster"], 1184, 8) == 3 * 128
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["cluster"], 1184, 8) == 4 * 128
+    # two-die objects: 32 KB, room for a 4 KB page homed on each die
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["die"], 1184, 0) == 32768
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["die"], 1184, 1) == 0
+    # split: header, R release copies, 2S counters, 2 top counters
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["split"], 1184, 16 | 8 << 8) == (1 + 8 + 32 + 2) * 128
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["split"], 1184, 65 | 8 << 8) == 0
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["split"], 1184, 16) == 0  # R = 0
+    assert G.gsync_mutex_bytes(G.MUTEX_KINDS["cohort"], 1) == 32768
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["cluster"], 1183, 8) == 0
     assert G.gsync_sem_bytes(0) == 4 * 128 and G.gsync_sem_bytes(3) == 0
     assert G.gsync_bench_mutex_workspace_bytes(2, 1184, 100, 1024) > 4 * 1184 * 100 * 4
@@ -73,6 +82,12 @@ def test_invalid_arguments_rejected_without_gpu(lib_path):
     from paper_1110_4623_gb300 import gsync as G
     # Null / misaligned state is rejected before any CUDA call.
     assert G.lib().gsync_mutex_init(None, 384, 0, 4, None, 0, None) == G.GSYNC_EINVAL
+    # cohort: null state, budget outside 1..32767, too small a state
+    assert G.lib().gsync_mutex_init_cohort(None, 32768, 64, None, 0, None) == G.GSYNC_EINVAL
+    assert G.lib().gsync_mutex_init_cohort(256, 32768, 0, None, 0, None) == G.GSYNC_EINVAL
+    assert G.lib().gsync_mutex_init_cohort(256, 32768, 32768, None, 0, None) == G.GSYNC_EINVAL
+    assert G.lib().gsync_mutex_init_cohort(256, 4096, 64, None, 0, None) == G.GSYNC_EINVAL
+    assert G.lib().gsync_device_topology(None, None, None) == G.GSYNC_EINVAL
     assert G.lib().gsync_mutex_init(0x1001, 384, 0, 4, None, 0, None) == G.GSYNC_EINVAL
     assert G.lib().gsync_barrier_init(0x1000, 10, 0, 4, 0, 0, None) == G.GSYNC_EINVAL  # too small
     w = G.gsync_mutex_work(0, 0, 256, 1, 1, 0, None, None, None, None, None, None, None, None)

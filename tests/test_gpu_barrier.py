@@ -14,7 +14,8 @@ def _gpu():
 
 
 KINDS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("tree", 2), ("cluster", 2), ("cluster", 4),
-         ("cluster", 8), ("sharded", 32), ("sharded", 8), ("sharded", 1)]
+         ("cluster", 8), ("sharded", 32), ("sharded", 8), ("sharded", 1), ("die", 0), ("split", 1 | 1 << 8),
+         ("split", 1 | 16 << 8), ("split", 16 | 16 << 8), ("split", 64 | 64 << 8), ("split", 7 | 3 << 8)]
 
 
 @pytest.mark.parametrize("kind,param", KINDS)
@@ -46,7 +47,8 @@ def test_sampled_sweep_1000_rounds(kind, param, nblocks):
     assert np.array_equal(got["mix"], want["mix"])
 
 
-@pytest.mark.parametrize("kind,param", [("atomic", 0), ("flag", 0), ("tree", 3), ("cluster", 1), ("sharded", 3)])
+@pytest.mark.parametrize("kind,param", [("atomic", 0), ("flag", 0), ("tree", 3), ("cluster", 1), ("sharded", 3),
+                                        ("die", 0), ("split", 5 | 3 << 8)])
 @pytest.mark.parametrize("nblocks,threads", [(1, 32), (2, 64), (37, 96), (151, 256)])
 def test_ragged_grids_full_fold(kind, param, nblocks, threads):
     from paper_1110_4623_gb300 import runner
@@ -65,14 +67,17 @@ def test_zero_rounds():
     assert got["rc"] == 0 and got["status"] == 0 and not got["mix"].any()
 
 
-def test_repeated_launches_continue_epochs():
-    # The object keeps its epoch across launches: a second launch attaches at the new epoch.
+@pytest.mark.parametrize("kind,nblocks", [("flag", 64), ("die", 64), ("die", 1184), ("die", 7), ("split", 1184)])
+def test_repeated_launches_continue_epochs(kind, nblocks):
+    # The object keeps its epoch across launches: a second launch attaches at the new epoch
+    # (DIE: and counts its blocks per die again in its first crossing).
     from paper_1110_4623_gb300 import runner
-    br = runner.BarrierRun("flag", 64, 128, 501, full=False)
+    br = runner.BarrierRun(kind, nblocks, 128, 501, full=False)
     for _ in range(3):
         got = br.run()
         assert got["status"] == 0 and not got["bad"].any()
-        assert np.array_equal(got["mix"], calc.barrier_sampled(64, 501)["mix"])
+        assert np.array_equal(got["mix"], calc.barrier_sampled(nblocks, 501)["mix"])
+
 
 
 def test_max_coresident_grid_runs():

@@ -31,6 +31,8 @@ CORRECT = [
     ("sleep_sem_wrap", mc.SleepSem(n=1, base=W), 3, 2),
     ("atomic_barrier", mc.AtomicBarrier(), 3, 2),
     ("atomic_barrier_wrap", mc.AtomicBarrier(base=2 ** 32 - 1), 3, 3),
+    ("atomic_barrier_parity", mc.AtomicBarrier(parity=True), 4, 3),
+    ("atomic_barrier_parity_wrap", mc.AtomicBarrier(parity=True, base=2 ** 32 - 2), 3, 4),
     ("flag_barrier", mc.FlagBarrier(), 3, 2),
     ("flag_barrier_broadcast", mc.FlagBarrier(broadcast=True), 3, 2),
     ("flag_barrier_wrap", mc.FlagBarrier(base=2 ** 32 - 1), 3, 3),
@@ -41,6 +43,15 @@ CORRECT = [
     ("sharded_barrier_3", mc.ShardedBarrier(shards=3), 4, 2),
     ("sharded_barrier_1", mc.ShardedBarrier(shards=1), 3, 2),
     ("sharded_barrier_wrap", mc.ShardedBarrier(shards=2, base=2 ** 32 - 1), 3, 3),
+    ("split_barrier_1x1", mc.SplitBarrier(S=1, R=1), 4, 3),
+    ("split_barrier_1x2", mc.SplitBarrier(S=1, R=2), 4, 3),
+    ("split_barrier_2x2", mc.SplitBarrier(S=2, R=2), 4, 3),
+    ("split_barrier_3x2", mc.SplitBarrier(S=3, R=2), 4, 3),
+    ("split_barrier_wrap", mc.SplitBarrier(S=2, R=3, base=2 ** 32 - 2), 3, 4),
+    ("die_barrier_alternating", mc.DieBarrier(), 4, 3),
+    ("die_barrier_uneven", mc.DieBarrier(layout=(0, 0, 1)), 3, 4),
+    ("die_barrier_one_die", mc.DieBarrier(layout=(1, 1, 1)), 3, 3),
+    ("die_barrier_wrap", mc.DieBarrier(base=2 ** 32 - 2), 3, 4),
 ]
 
 
@@ -61,8 +72,13 @@ BROKEN = [
     ("cohort_skip_ticket", mc.CohortMutex(broken="skip_ticket"), 3, 2, "local ticket"),
     ("sleep_sem_turn_ge", mc.SleepSem(n=1, broken="turn_ge"), 3, 1, "critical section"),
     ("barrier_no_wait", mc.AtomicBarrier(broken="no_wait"), 3, 1, "passed round"),
+    ("barrier_late_reset_one_counter", mc.AtomicBarrier(broken="reset_one_counter"), 2, 3, "deadlock"),
     ("flag_skip_last", mc.FlagBarrier(broken="skip_last"), 3, 1, "passed round"),
     ("sharded_early", mc.ShardedBarrier(shards=2, broken="early"), 3, 1, "passed round"),
+    ("die_no_top", mc.DieBarrier(broken="no_top"), 2, 2, "passed round"),
+    ("split_no_top", mc.SplitBarrier(S=2, R=2, broken="no_top"), 3, 1, "passed round"),
+    ("split_one_copy_early", mc.SplitBarrier(S=2, R=2, broken="one_copy_early"), 3, 3, "completion"),
+    ("die_no_reset", mc.DieBarrier(broken="no_reset"), 2, 4, "final state"),
     ("sharded_counts_master", mc.ShardedBarrier(shards=2, broken="counts_master"), 3, 1, "final state"),
 ]
 
