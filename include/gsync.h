@@ -283,7 +283,7 @@ int gsync_bench_sem(void* state, const gsync_sem_work* w, void* stream);
  *    the ticket kind; min_ns = 0 spins without sleeping.
  *  - keys (device, nacq x i32), adds (device, nacq x i64); sum (device, nkeys x i64) and
  *    count (device, nkeys x u32) zeroed by the caller.
- *  - group_state (device, 128-byte aligned): ngroups x 384 bytes, zeroed before the first
+ *  - group_state (device, 128-byte aligned): ngroups x 512 bytes, zeroed before the first
  *    launch; slots (device, 2 x nblocks u32) scratch; mix, bad (device, nblocks u32);
  *    status (device u32, zeroed).
  *  - cluster > 1 launches clusters of that size and uses the cluster-hierarchical barrier

@@ -19,7 +19,10 @@ namespace ptx = gsync::ptx;
 namespace {
 
 constexpr int kMaxThreads = 256;
-constexpr uint32_t kObjWords = 3 * gsync::kLineWords;  // header line + two lines per object
+// Per-object memory: a mutex is a header line and two lines (lock word, turn); a group
+// barrier a header line, two arrival counters (by epoch parity) and the release epoch.
+constexpr uint32_t kMutexObjWords = 3 * gsync::kLineWords;
+constexpr uint32_t kBarObjWords = 4 * gsync::kLineWords;
 
 struct Args {
   uint32_t* mutex_state;
@@ -99,7 +102,7 @@ __global__ void __launch_bounds__(kMaxThreads, 8) batched_kernel(Args a) {
   }
   if (g >= 0) {
     gslots = a.slots + 2u * (uint32_t)a.group_start[g];
-    bar.s = a.group_state + (uint32_t)g * kObjWords;
+    bar.s = a.group_state + (uint32_t)g * kBarObjWords;
     bar.kind = BKIND;
     bar.n = gsize;
     bar.param = BKIND == GSYNC_BAR_CLUSTER ? ptx::cluster_nctarank() : 0u;
@@ -124,7 +127,7 @@ __global__ void __launch_bounds__(kMaxThreads, 8) batched_kernel(Args a) {
         const uint32_t cls = a.key_class[key];
         const uint32_t* pol = a.policy + 4u * (cls < (uint32_t)a.nclasses ? cls : 0u);
         gsync::MutexRef m;
-        m.s = a.mutex_state + key * kObjWords;
+        m.s = a.mutex_state + key * kMutexObjWords;
         m.kind = pol[0] <= (uint32_t)GSYNC_MUTEX_TICKET ? pol[0] : (uint32_t)GSYNC_MUTEX_TICKET;
         m.qmask = 0;
         m.bo.policy = GSYNC_BACKOFF_EXPONENTIAL;

@@ -331,7 +331,7 @@ class BatchedRun:
         self.group_start, self.group_of_block = start, gob
         ng = len(self.group_sizes)
         self.mutex_state = torch.zeros(nkeys * 384, dtype=torch.uint8, device="cuda")
-        self.group_state = torch.zeros(max(ng, 1) * 384, dtype=torch.uint8, device="cuda")
+        self.group_state = torch.zeros(max(ng, 1) * 512, dtype=torch.uint8, device="cuda")
         self.key_class = torch.from_numpy(np.ascontiguousarray(key_class, dtype=np.uint8)).cuda()
         self.policy = torch.zeros(nclasses * 4, dtype=torch.int32, device="cuda")
         self.keys = torch.from_numpy(np.ascontiguousarray(keys, dtype=np.int32)).cuda()
