@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(Args a) {
         bool got = false;
         for (uint32_t k = 0; k < 4u * a.nslots; ++k) {
           if (ptx::atom_cas_acquire(&a.slots[s].state, 0u, 1u) == 0u) { got = true; break; }
-          s = (s + 1u) % a.nslots;
+          if (++s == a.nslots) s = 0;
         }
         if (!got) { record_status(a.status, GSYNC_ETIMEDOUT); break; }
         Slot* sl = &a.slots[s];
@@ -263,27 +263,30 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(Args a) {
       const uint32_t* my_mask = a.active_mask + 32u * (blockIdx.x % kMaskCopies);
       const uint32_t m0 = ptx::ld_relaxed(my_mask), m1 = a.nslots > 32 ? ptx::ld_relaxed(my_mask + 1) : 0u;
       const uint64_t mask = ((uint64_t)m1 << 32) | m0;
-      if (mask) {
-        for (uint32_t k = 0; k < a.nslots; ++k) {
-          const uint32_t s = (scan + k) % a.nslots;
-          if (!((mask >> s) & 1ull)) continue;
+      // Visit only the set bits, in the order scan, scan + 1, ..., nslots - 1, 0, ..., scan - 1
+      // (bits at or above `scan` first): a walk over all slots with a division per step costs a
+      // single thread ~10 us, which every idle worker would pay whenever any slot is active.
+      const uint64_t upper = mask & (~0ull << scan), lower = mask & ~(~0ull << scan);
+      bool got = false;
+      for (int pass = 0; pass < 2 && !got; ++pass) {
+        for (uint64_t m = pass ? lower : upper; m && !got; m &= m - 1u) {
+          const uint32_t s = (uint32_t)__ffsll((long long)m) - 1u;
           uint32_t c, g;
           bool last;
-          if (claim_chunk(&a.slots[s], c, g, last, a.timeout_ns)) {
-            // The last chunk is handed out: the slot has no more work to find, so it leaves the
-            // active mask now (it cannot be reused before this chunk completes).
-            if (last)
-              for (uint32_t m = 0; m < kMaskCopies; ++m) atomicAnd(&a.active_mask[32u * m + (s >> 5)], ~(1u << (s & 31)));
-            Slot* sl = &a.slots[s];
-            const int64_t lo = sl->off + (int64_t)c * a.chunk_elems;
-            int64_t hi = lo + a.chunk_elems;
-            if (hi > sl->off + sl->len) hi = sl->off + sl->len;
-            s_slot = s; s_chunk = c; s_gen = g; s_lo = lo; s_hi = hi;
-            if (a.trace && c == 0) a.trace[4ull * sl->id + 2] = ptx::globaltimer();
-            s_cmd = 0;
-            scan = s;
-            break;
-          }
+          if (!claim_chunk(&a.slots[s], c, g, last, a.timeout_ns)) continue;
+          // The last chunk is handed out: the slot has no more work to find, so it leaves the
+          // active mask now (it cannot be reused before this chunk completes).
+          if (last)
+            for (uint32_t k = 0; k < kMaskCopies; ++k) atomicAnd(&a.active_mask[32u * k + (s >> 5)], ~(1u << (s & 31)));
+          Slot* sl = &a.slots[s];
+          const int64_t lo = sl->off + (int64_t)c * a.chunk_elems;
+          int64_t hi = lo + a.chunk_elems;
+          if (hi > sl->off + sl->len) hi = sl->off + sl->len;
+          s_slot = s; s_chunk = c; s_gen = g; s_lo = lo; s_hi = hi;
+          if (a.trace && c == 0) a.trace[4ull * sl->id + 2] = ptx::globaltimer();
+          s_cmd = 0;
+          scan = s;
+          got = true;
         }
       }
       if (s_cmd == 2) {
