@@ -400,6 +400,7 @@ SERVE_POOL = 128 << 20           # 512 MB of int32 values (4x the L2)
 SERVE_RATES = (1e3, 1e4, 1e5, 1e6)
 SERVE_SECONDS, SERVE_MAX_REQ = 0.5, 100_000
 SERVE_CHUNK = 8192                # values per chunk (one block's share), both arms
+SERVE_ADMITTERS = 16             # admitter blocks of the persistent loop (the other 288 blocks work)
 
 
 def serve_section(calc, inputs, runner):
@@ -410,7 +411,8 @@ def serve_section(calc, inputs, runner):
     rng = np.random.default_rng(0)
     out = {"workload": f"int32 segmented sums, length log-uniform 256..1048576, pool {SERVE_POOL} values "
                        f"({SERVE_POOL * 4 >> 20} MiB), Poisson arrivals, open loop (latency from the scheduled arrival "
-                       f"to the host seeing the completion flag)", "rates": {}}
+                       f"to the host seeing the completion flag); persistent loop: 304 blocks of which "
+                       f"{SERVE_ADMITTERS} admit, 64 slots; both arms: chunks of {SERVE_CHUNK} values", "rates": {}}
     for rate in SERVE_RATES:
         nreq = int(min(SERVE_MAX_REQ, max(500, rate * SERVE_SECONDS)))
         off, ln = off_all[:nreq], len_all[:nreq]
@@ -419,7 +421,8 @@ def serve_section(calc, inputs, runner):
         want = calc.serve_final(off[sample], ln[sample], pool)
         row = {"nreq": nreq, "chunk_values": SERVE_CHUNK}
         for arm in ("persistent", "per_request_launch"):
-            sr = runner.ServeRun(off, ln, sched, dpool, nslots=64, nblocks=304, admitters=8, chunk_elems=SERVE_CHUNK)
+            sr = runner.ServeRun(off, ln, sched, dpool, nslots=64, nblocks=304, admitters=SERVE_ADMITTERS,
+                                 chunk_elems=SERVE_CHUNK)
             r = sr.run() if arm == "persistent" else sr.baseline(nstreams=8)
             lat = r["latency_ns"] / 1e3
             span = (sched[-1] + r["latency_ns"][-1]) / 1e9

@@ -261,8 +261,8 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(Args a) {
     if (tid == 0) {
       s_cmd = 2;  // nothing yet
       const uint32_t* my_mask = a.active_mask + 32u * (blockIdx.x % kMaskCopies);
-      const uint32_t m0 = ptx::ld_relaxed(my_mask), m1 = a.nslots > 32 ? ptx::ld_relaxed(my_mask + 1) : 0u;
-      const uint64_t mask = ((uint64_t)m1 << 32) | m0;
+      uint64_t mask;  // both mask words in one load (the copy starts a line)
+      asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(mask) : "l"(my_mask) : "memory");
       // Visit only the set bits, in the order scan, scan + 1, ..., nslots - 1, 0, ..., scan - 1
       // (bits at or above `scan` first): a walk over all slots with a division per step costs a
       // single thread ~10 us, which every idle worker would pay whenever any slot is active.
