@@ -41,7 +41,7 @@ SEM_THREADS, SEM_PAIRS, SEM_COUNTS = 128, 200, (1, 4, 16, 64)
 DEFAULT_MUTEX = "cohort"
 DEFAULT_BARRIER = ("atomic", 0)
 BARRIERS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("cluster", 2), ("cluster", 4), ("cluster", 8),
-            ("sharded", 32), ("sharded", 8), ("die", 0), ("split", 16 | 16 << 8)]
+            ("sharded", 32), ("sharded", 8), ("die", 0), ("die", 1), ("split", 16 | 16 << 8)]
 # Backoff (min_ns, max_ns) per kind; the ticket kinds sleep min_ns per waiter ahead, capped.
 MUTEX_BACKOFF = {"cas_backoff": (16, 512), "ticket": (128, 4000), "cohort": (128, 4000)}
 SEM_BACKOFF = (64, 2000)
@@ -100,6 +100,8 @@ def barrier_name(kind, param):
         return f"{kind}{param}"
     if kind == "split":
         return f"split{param & 0xFF}x{param >> 8}"
+    if kind == "die":
+        return "die_flat" if param else "die"
     return kind
 
 
@@ -157,6 +159,10 @@ class ClockSampler:
 def measure_roofline_terms(runner, inputs):
     """L_handoff, T_cs(K), T_cs_sem(n), R_same and L_rt from the probe kernels (medians)."""
     sms = runner.sm_count()
+    # The bound is the shortest hand-off the machine offers: two SMs of one die, on lines homed
+    # on that die.  Five fixed pairs on lines homed wherever are reported beside it.
+    near = [runner.near_handoff(4000) for _ in range(3)]
+    near_ns = [h["handoff_ns"] for h in near if h["status"] == 0]
     pairs = [(0, 1), (0, sms // 2), (0, sms - 1), (sms // 4, 3 * sms // 4), (2, sms - 3)]
     hand = [runner.probe_pingpong(a, b, 4000) for a, b in pairs if a != b and 0 <= a < sms and 0 <= b < sms]
     hand_ns = [h["handoff_ns"] for h in hand if h["status"] == 0]
@@ -174,7 +180,7 @@ def measure_roofline_terms(runner, inputs):
     T_frame = float(np.median([runner.probe_cs(-1, MUTEX_THREADS, 20000)["ns_per_cs"] for _ in range(3)]))
     T_frame_sem = float(np.median([runner.probe_sem_cs(None, None, SEM_THREADS, iters=4000)["ns_per_cs"]
                                    for _ in range(3)]))
-    return {"sms": sms, "L_handoff_ns": float(np.median(hand_ns)), "L_handoff_pairs_ns": hand_ns, "T_cs_ns": T_cs,
+    return {"sms": sms, "L_handoff_ns": float(np.median(near_ns)), "L_handoff_pairs_ns": hand_ns, "T_cs_ns": T_cs,
             "T_frame_ns": T_frame, "T_cs_sem_ns": T_cs_sem, "T_frame_sem_ns": T_frame_sem,
             "R_same_red_ops_s": float(np.median(rs)), "R_same_atom_ops_s": float(np.median(ra)), "L_rt_ns": L_rt}
 
@@ -219,7 +225,7 @@ def barrier_roof_ns(terms, kind, param, B):
     elif kind in ("sharded", "flag"):
         b_eff = B / (param if kind == "sharded" else B)
     elif kind == "die":
-        b_eff, rts = B / 2, 2
+        b_eff, rts = (B, 1) if param == 1 else (B / 2, 2)
     elif kind == "split":
         S = param & 0xFF
         b_eff, rts = (-(-B // S) + S, 2) if S > 1 else (B, 1)
@@ -514,7 +520,7 @@ def run_gpu(args):
     barrier = {}
     for (k, p) in step.barrier:
         ns = med[(k, p)] * 1e6 / BAR_ROUNDS
-        roof = barrier_roof_ns(terms, k, max(p, 1), NBLOCKS)
+        roof = barrier_roof_ns(terms, k, p if k in ("die", "split") else max(p, 1), NBLOCKS)
         barrier[barrier_name(k, p)] = {"ns_per_crossing": ns, "roof_ns": roof, "frac": roof / ns}
     bkey = barrier_name(*DEFAULT_BARRIER)
     sem = {}
@@ -537,8 +543,9 @@ def run_gpu(args):
         "roofline": {"bound": "l2_handoff_latency", "achieved": value / world, "peak": peak, "unit": "acq/s",
                      "frac": (value / world) / peak, "traffic": ROOF_TRAFFIC,
                      "traffic_note": ROOF_TRAFFIC_NOTE,
-                     "peak_source": "measured live: sum over CS sizes of 1e9 / (L_handoff + T_cs(K)) from the "
-                                    "ping-pong and critical-section probe kernels of this run (min with R_same/2); "
+                     "peak_source": "measured live: sum over CS sizes of 1e9 / (L_handoff + T_body(K)); L_handoff "
+                                    "= ping-pong of two SMs of one die on lines homed on that die (the shortest "
+                                    "hand-off), T_body = critical-section probe minus its frame; min with R_same/2; "
                                     "MEASURED_PEAKS.json's HBM and bf16 peaks do not bound this path"},
         "barrier": {"default": bkey, "ns_per_crossing": barrier[bkey]["ns_per_crossing"],
                     "frac": barrier[bkey]["frac"], "kinds": barrier},

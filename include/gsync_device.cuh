@@ -523,7 +523,8 @@ __device__ __forceinline__ int sem_post(const SemRef& s) {
 //          release epoch, line 3 the arrival counter of even epochs; die 0's lines 2 and 4
 //          are the top counters of odd and even epochs.  A block's first crossing of a launch
 //          registers it (flat count, membership per die); later crossings count in per die,
-//          and the second die to finish releases both.
+//          and the second die to finish releases both.  param 1: every crossing counts all
+//          blocks on die 0's arrival counters, and the last arriver writes both release words.
 // SPLIT  : param = S | R << 8 (1..64 each).  Lines 1..R the release copies, then 2S arrival
 //          counters (S of odd epochs, then S of even epochs), then the top counters of odd and
 //          even epochs.  Block b counts in on counter b mod S and polls copy b mod R; the last
@@ -612,6 +613,18 @@ __device__ __forceinline__ int split_arrive_wait(const BarrierRef& b, uint32_t e
 // Master thread of a DIE barrier (see the layout above).
 __device__ __forceinline__ int die_arrive_wait(BarrierRef& b, uint32_t e1) {
   uint32_t* rel = b.die_line(b.die, 1);
+  if (b.param == 1u) {
+    // Flat arrivals on one counter pair (die 0's page), release words on both dies: the
+    // split protocol with one counter and one release copy per die, each block polling the
+    // copy homed on its own die.
+    uint32_t* cnt = b.die_line(0, (e1 & 1u) ? 0u : 3u);
+    if (ptx::atom_add_acq_rel(cnt, 1u) != b.n - 1u) return wait_epoch(b, rel, e1);
+    ptx::fence_acq_rel();
+    ptx::st_relaxed(b.die_line(0, 1), e1);
+    ptx::st_relaxed(b.die_line(1, 1), e1);
+    ptx::st_relaxed(cnt, 0u);
+    return GSYNC_OK;
+  }
   uint32_t* info = b.line(2);
   if (b.n_mine == 0) {
     // Registration crossing: count in on the flat counter, and into this die's membership.

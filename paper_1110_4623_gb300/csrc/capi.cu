@@ -205,7 +205,7 @@ size_t gsync_barrier_bytes(int kind, int nblocks, int param) {
     case GSYNC_BAR_TREE: if (param < 2 || param > 1024) return 0; break;
     case GSYNC_BAR_CLUSTER: if (param < 1 || param > 8 || nblocks % param) return 0; break;
     case GSYNC_BAR_SHARDED: if (param < 1 || param > 32 || param > nblocks) return 0; break;
-    case GSYNC_BAR_DIE: if (param != 0) return 0; break;
+    case GSYNC_BAR_DIE: if (param != 0 && param != 1) return 0; break;
     case GSYNC_BAR_SPLIT: {
       const int S = param & 0xFF, R = param >> 8;
       if (param < 0 || S < 1 || S > 64 || R < 1 || R > 64) return 0;

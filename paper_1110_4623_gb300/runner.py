@@ -216,8 +216,10 @@ def probe_latency(op: str, iters: int = 4096) -> dict:
     return {"ns_per_op": o[0] / iters, "cycles_per_op": o[1] / iters}
 
 
-def probe_pingpong(sm_a: int, sm_b: int, iters: int = 2000) -> dict:
-    scratch = _state(512)
+def probe_pingpong(sm_a: int, sm_b: int, iters: int = 2000, scratch: torch.Tensor | None = None) -> dict:
+    """Half a release/acquire ping-pong between SMs sm_a and sm_b on the flag lines at the start
+    of `scratch` (512 bytes, 128-byte aligned; a fresh buffer when None)."""
+    scratch = _state(512) if scratch is None else scratch
     out = torch.zeros(4, dtype=torch.int64, device="cuda")
     G.check("gsync_probe_pingpong", G.gsync_probe_pingpong(sm_a, sm_b, iters, scratch, out))
     torch.cuda.synchronize()
@@ -242,6 +244,24 @@ def probe_cluster(op: int, cluster: int, iters: int = 2000) -> dict:
     o = out.cpu().numpy()
     per = o[0] / iters if op == 0 else o[0] / (2 * iters)
     return {"ns": per, "status": int(o[3])}
+
+
+def near_handoff(iters: int = 4000) -> dict:
+    """The shortest SM-to-SM hand-off on this GPU: a ping-pong between two SMs of one die on
+    flag lines homed on that die (found with the topology probes).  On a one-die GPU, any pair."""
+    die, nd = device_topology()
+    buf = _state(64 << 10)
+    d0 = np.flatnonzero(die == 0)
+    sm_a, sm_b = int(d0[0]), int(d0[len(d0) // 2])
+    page = 0
+    if nd == 2:
+        # first 4 KB page homed on die 0: nearer to an SM of die 0 than to one of die 1
+        near = probe_rtt_by_line(sm_a, buf, 16, 4096, 8)
+        far = probe_rtt_by_line(int(np.flatnonzero(die == 1)[0]), buf, 16, 4096, 8)
+        page = int(np.flatnonzero(near < far)[0])
+    r = probe_pingpong(sm_a, sm_b, iters, scratch=buf[page * 4096:])
+    r["page"] = page
+    return r
 
 
 def device_topology() -> tuple[np.ndarray, int]:

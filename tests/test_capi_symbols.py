@@ -66,7 +66,8 @@ def test_size_queries_without_gpu(lib_path):
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["cluster"], 1184, 8) == 4 * 128
     # two-die objects: 32 KB, room for a 4 KB page homed on each die
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["die"], 1184, 0) == 32768
-    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["die"], 1184, 1) == 0
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["die"], 1184, 1) == 32768
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["die"], 1184, 2) == 0
     # split: header, R release copies, 2S counters, 2 top counters
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["split"], 1184, 16 | 8 << 8) == (1 + 8 + 32 + 2) * 128
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["split"], 1184, 65 | 8 << 8) == 0

@@ -14,7 +14,7 @@ def _gpu():
 
 
 KINDS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("tree", 2), ("cluster", 2), ("cluster", 4),
-         ("cluster", 8), ("sharded", 32), ("sharded", 8), ("sharded", 1), ("die", 0), ("split", 1 | 1 << 8),
+         ("cluster", 8), ("sharded", 32), ("sharded", 8), ("sharded", 1), ("die", 0), ("die", 1), ("split", 1 | 1 << 8),
          ("split", 1 | 16 << 8), ("split", 16 | 16 << 8), ("split", 64 | 64 << 8), ("split", 7 | 3 << 8)]
 
 
@@ -48,7 +48,7 @@ def test_sampled_sweep_1000_rounds(kind, param, nblocks):
 
 
 @pytest.mark.parametrize("kind,param", [("atomic", 0), ("flag", 0), ("tree", 3), ("cluster", 1), ("sharded", 3),
-                                        ("die", 0), ("split", 5 | 3 << 8)])
+                                        ("die", 0), ("die", 1), ("split", 5 | 3 << 8)])
 @pytest.mark.parametrize("nblocks,threads", [(1, 32), (2, 64), (37, 96), (151, 256)])
 def test_ragged_grids_full_fold(kind, param, nblocks, threads):
     from paper_1110_4623_gb300 import runner
