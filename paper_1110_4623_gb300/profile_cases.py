@@ -40,6 +40,15 @@ def _sem(n, pairs=20):
     return lambda: G.check("gsync_bench_sem", r.launch())
 
 
+def _batched(nacq=200_000, rounds=20):
+    from . import autotune
+    keys, adds, _ = inputs.batched_inputs(nacq, 4096, 1.1)
+    cls = autotune.classify_keys(keys, 4096, NB)
+    r = autotune.make_run(keys, adds, 4096, NB, 64, rounds, 1, cls)
+    r.set_policy(autotune.DEFAULT_POLICY)
+    return lambda: G.check("gsync_bench_batched", r.launch())
+
+
 CASES = {
     "mutex_sleep_queue": lambda: _mutex("sleep_queue", 64),
     "mutex_ticket": lambda: _mutex("ticket", 64),
@@ -50,6 +59,7 @@ CASES = {
     "barrier_flag": lambda: _barrier("flag", 0),
     "barrier_cluster2": lambda: _barrier("cluster", 2),
     "sem_ticket_n4": lambda: _sem(4),
+    "batched_200k": lambda: _batched(),
 }
 
 
