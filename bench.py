@@ -1,8 +1,8 @@
 """Benchmark of the inter-block synchronization hot path on GB300.
 
 One step = one pass over every row of the hot path at 1184 blocks:
-  * mutex contention (the paper's 4 kinds and the two-die cohort lock x critical sections of
-    0/64/1024 words, 256 threads per block,
+  * mutex contention (the paper's 4 kinds, its ring-buffer mutex and spin-then-sleep policy,
+    and the two-die cohort lock x critical sections of 0/64/1024 words, 256 threads per block,
     100 acquisitions per block, seeded delays U{0..2000} cycles),
   * grid barriers (atomic, flag, tree, cluster 2/4/8, sharded, two-die, split; 128 threads,
     1000 rounds each),
@@ -44,6 +44,12 @@ BARRIERS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("cluster", 2)
             ("sharded", 32), ("sharded", 8), ("die", 0), ("die", 1), ("split", 16 | 16 << 8)]
 # Backoff (min_ns, max_ns) per kind; the ticket kinds sleep min_ns per waiter ahead, capped.
 MUTEX_BACKOFF = {"cas_backoff": (16, 512), "ticket": (128, 4000), "cohort": (128, 4000)}
+# The measured mutex configurations: (name, kind, backoff policy, (min_ns, max_ns), spin).
+# cas_spin_then_sleep is Section 5's futex stand-in: the CAS lock spins, then backs off.
+MUTEX_CONFIGS = [("cas_spin", "cas_spin", 0, None, 0), ("cas_backoff", "cas_backoff", 0, (16, 512), 0),
+                 ("cas_spin_then_sleep", "cas_backoff", 2, (16, 512), 32), ("ticket", "ticket", 0, (128, 4000), 0),
+                 ("sleep_queue", "sleep_queue", 0, None, 0), ("ring", "ring", 0, None, 0),
+                 ("cohort", "cohort", 0, (128, 4000), 0)]
 SEM_BACKOFF = (64, 2000)
 # Batched many-mutex workload: 4096 keys, Zipf(1.1), 1e6 acquisitions, 64 barrier groups.
 BATCH_KEYS, BATCH_ACQ, BATCH_GROUPS, BATCH_ROUNDS, BATCH_THREADS = 4096, 1_000_000, 64, 100, 128
@@ -244,12 +250,11 @@ class GpuStep:
     def __init__(self, runner, G, inputs):
         import torch
         self.mutex = {}
-        for kind in G.MUTEX_KINDS:
+        for name, kind, policy, bo_ns, spin in MUTEX_CONFIGS:
             for K in CS_SIZES:
                 delay, add = inputs.mutex_inputs(NBLOCKS, MUTEX_ACQ, inputs.mutex_seed(G.MUTEX_KINDS[kind], NBLOCKS, K))
-                bo = runner.backoff(min_ns=MUTEX_BACKOFF[kind][0], max_ns=MUTEX_BACKOFF[kind][1]) \
-                    if kind in MUTEX_BACKOFF else None
-                self.mutex[(kind, K)] = (runner.MutexRun(kind, NBLOCKS, MUTEX_THREADS, MUTEX_ACQ, K, delay, add, bo=bo,
+                bo = runner.backoff(policy=policy, min_ns=bo_ns[0], max_ns=bo_ns[1], spin=spin) if bo_ns else None
+                self.mutex[(name, K)] = (runner.MutexRun(kind, NBLOCKS, MUTEX_THREADS, MUTEX_ACQ, K, delay, add, bo=bo,
                                                          timeout_ns=TIMEOUT_NS), add)
         self.barrier = {(k, p): runner.BarrierRun(k, NBLOCKS, BAR_THREADS, BAR_ROUNDS, full=False, param=p,
                                                   timeout_ns=TIMEOUT_NS) for k, p in BARRIERS}

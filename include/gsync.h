@@ -55,9 +55,12 @@ typedef enum gsync_mutex_kind {
   GSYNC_MUTEX_CAS_BACKOFF = 1, /* the same with __nanosleep backoff after each failure */
   GSYNC_MUTEX_TICKET = 2,      /* fetch-and-add ticket; poll turn; unlock stores turn + 1 */
   GSYNC_MUTEX_SLEEP_QUEUE = 3, /* queue lock: each waiter polls its own padded flag slot */
-  GSYNC_MUTEX_COHORT = 4       /* two-die cohort lock: a ticket lock per die (homed on that
+  GSYNC_MUTEX_COHORT = 4,      /* two-die cohort lock: a ticket lock per die (homed on that
                                   die) under a global ticket lock; hand-offs stay on a die
                                   for up to `budget` acquisitions in a row */
+  GSYNC_MUTEX_RING = 5         /* the paper's ring-buffer sleeping mutex (Section 5, design
+                                  alternative): a waiter writes its block id at the ring's
+                                  end and polls the head pointer and the entry it names */
 } gsync_mutex_kind;
 
 /* Barrier kinds (Section 5, "Barrier"). */
@@ -83,13 +86,19 @@ typedef enum gsync_sem_kind {
 
 /* Backoff policy (Section 5: "Backoff"; the paper's counter I runs from Imin to Imax by +1
  * and wraps; exponential doubling is the other common policy). */
-enum { GSYNC_BACKOFF_EXPONENTIAL = 0, GSYNC_BACKOFF_LINEAR_CYCLIC = 1 };
+enum {
+  GSYNC_BACKOFF_EXPONENTIAL = 0,
+  GSYNC_BACKOFF_LINEAR_CYCLIC = 1,
+  /* Section 5's GPU stand-in for a futex: spin aggressively (no sleep) for `spin` failed
+   * attempts, then fall back to exponential backoff from min_ns (CAS kinds). */
+  GSYNC_BACKOFF_SPIN_THEN_SLEEP = 2
+};
 
 typedef struct gsync_backoff {
   uint32_t policy; /* GSYNC_BACKOFF_* */
   uint32_t min_ns; /* first sleep (and, for ticket locks, sleep per waiter ahead); 0 = no sleeping */
   uint32_t max_ns; /* cap */
-  uint32_t reserved;
+  uint32_t spin;   /* SPIN_THEN_SLEEP: failed attempts before the first sleep (0 selects 32) */
 } gsync_backoff;
 
 /* ------------------------------------------------------------------------------------ */

@@ -174,6 +174,7 @@ enum HeaderWord : uint32_t {
   kHdrMagic = 0, kHdrN = 1, kHdrParam = 2, kHdrPolicy = 3, kHdrMinNs = 4, kHdrMaxNs = 5,
   kHdrTimeoutLo = 6, kHdrTimeoutHi = 7, kHdrAbort = 8, kHdrMode = 9,
   kHdrDieOff0 = 10, kHdrDieOff1 = 11,  // COHORT: word offset of each die's local lock
+  kHdrSpin = 12,                       // SPIN_THEN_SLEEP backoff: failed attempts before sleeping
 };
 // COHORT: lines 3-4 hold the die of every SM (one byte per SM id, 256 entries).
 enum : uint32_t { kDieTableWord = 3 * kLineWords, kMaxSmIds = 256 };
@@ -197,7 +198,7 @@ struct Waiter {
 };
 
 struct Backoff {
-  uint32_t policy, min_ns, max_ns;
+  uint32_t policy, min_ns, max_ns, spin;
   // Next sleep after `cur`: doubling up to max_ns (exponential), or the paper's cyclic
   // policy that adds min_ns after each failure and wraps back to min_ns past max_ns.
   __device__ __forceinline__ uint32_t next(uint32_t cur) const {
@@ -218,9 +219,11 @@ __device__ __forceinline__ uint64_t header_timeout(const uint32_t* s) {
 // ---------------------------------------------------------------------------------------
 // Mutex (Section 5 "Mutex"; Appendix: spin-lock mutex, FA mutex)
 // ---------------------------------------------------------------------------------------
-// line 1: lock word (CAS kinds) or ticket counter (TICKET, SLEEP_QUEUE, COHORT global lock)
-// line 2: turn (TICKET, COHORT global lock)
-// lines 3 .. 3+Q-1: one flag per queue slot (SLEEP_QUEUE), Q = power of two >= waiters
+// line 1: lock word (CAS kinds) or ticket counter (TICKET, SLEEP_QUEUE, COHORT global lock,
+//         RING tail)
+// line 2: turn (TICKET, COHORT global lock) or head pointer (RING)
+// lines 3 .. 3+Q-1: one flag per queue slot (SLEEP_QUEUE) or ring entry (RING), Q = power of
+//         two >= waiters
 // COHORT: lines 3-4 the SM-to-die table; for each die d, at word offset kHdrDieOff<d> (on a
 //   4 KB page homed on die d), a local ticket counter line and a local turn line whose first
 //   8 bytes hold {served ticket (low 32), cohort word (high 32)}.
@@ -248,6 +251,7 @@ __device__ __forceinline__ MutexRef mutex_attach(void* state) {
   m.bo.policy = m.s[kHdrPolicy];
   m.bo.min_ns = m.s[kHdrMinNs];
   m.bo.max_ns = m.s[kHdrMaxNs];
+  m.bo.spin = m.s[kHdrSpin];
   m.timeout_ns = header_timeout(m.s);
   m.local = nullptr;
   m.die = 0;
@@ -270,6 +274,9 @@ struct Token {
   uint32_t next_seen;
 };
 
+// RING: the value of an empty ring entry (block ids are below it).
+enum : uint32_t { kRingEmpty = 0xFFFFFFFFu };
+
 // COHORT local turn word: bit 31 of the high half says the cohort already holds the global
 // lock (the next local holder inherits it instead of queueing for it).
 enum : uint32_t { kCohortOwned = 0x80000000u };
@@ -280,10 +287,16 @@ __device__ __forceinline__ Token mutex_lock_thread(const MutexRef& m) {
   Waiter w;
   if (KIND == GSYNC_MUTEX_CAS_SPIN || KIND == GSYNC_MUTEX_CAS_BACKOFF) {
     // Algorithm 1 / spin-lock mutex: swap 1 in until the old value was 0 (atomicCAS form).
+    // SPIN_THEN_SLEEP (Section 5's stand-in for a futex) spins `spin` failed attempts first.
     uint32_t sleep_ns = m.bo.min_ns;
+    uint32_t spins = m.bo.policy == GSYNC_BACKOFF_SPIN_THEN_SLEEP ? m.bo.spin : 0u;
     while (ptx::atom_cas_acquire(m.lockw(), 0u, 1u) != 0u) {
       if (int rc = w.tick(m.timeout_ns, m.abort_word())) return {rc, 0u};
       if (KIND == GSYNC_MUTEX_CAS_BACKOFF) {
+        if (spins) {
+          --spins;
+          continue;
+        }
         __nanosleep(sleep_ns);
         sleep_ns = m.bo.next(sleep_ns);
       }
@@ -328,6 +341,21 @@ __device__ __forceinline__ Token mutex_lock_thread(const MutexRef& m) {
       if (m.bo.min_ns) __nanosleep(m.bo.min_ns);
     }
     return {GSYNC_OK, t, g, ptx::ld_relaxed(m.local_next())};
+  } else if (KIND == GSYNC_MUTEX_RING) {
+    // Ring-buffer sleeping mutex (Section 5, design alternative): claim the ring's end with a
+    // fetch-and-add on the tail, write this block's id there, then poll the head pointer and
+    // the entry it names until that entry is this block.  Two reads per poll, as Section 5
+    // counts against it.
+    const uint32_t t = ptx::atom_add_relaxed(m.lockw(), 1u);
+    const uint32_t me = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    ptx::st_relaxed(m.flag(t), me);
+    for (;;) {
+      const uint32_t h = ptx::ld_acquire(m.turn());
+      if (ptx::ld_acquire(m.flag(h)) == me) break;
+      if (int rc = w.tick(m.timeout_ns, m.abort_word())) return {rc, t};
+      if (m.bo.min_ns) __nanosleep(m.bo.min_ns);
+    }
+    return {GSYNC_OK, t};
   } else {
     // Queue lock: take a slot, poll the slot's own flag until it holds this ticket.
     const uint32_t t = ptx::atom_add_relaxed(m.lockw(), 1u);
@@ -362,6 +390,11 @@ __device__ __forceinline__ void mutex_unlock_thread(const MutexRef& m, const Tok
       ptx::st_release(m.turn(), (g + 1u) & 0xFFFFu);
       ptx::st_release_u64(m.local_turn(), (uint64_t)(ticket + 1u));
     }
+  } else if (KIND == GSYNC_MUTEX_RING) {
+    // Clear this block's entry before moving the head past it, so that no block can match
+    // its own id left over from an earlier lap of the ring.
+    ptx::st_relaxed(m.flag(ticket), kRingEmpty);
+    ptx::st_release(m.turn(), ticket + 1u);
   } else {
     ptx::st_release(m.flag(ticket + 1u), ticket + 1u);
   }
@@ -419,6 +452,7 @@ __device__ __forceinline__ SemRef sem_attach(void* state) {
   r.bo.policy = r.s[kHdrPolicy];
   r.bo.min_ns = r.s[kHdrMinNs];
   r.bo.max_ns = r.s[kHdrMaxNs];
+  r.bo.spin = r.s[kHdrSpin];
   r.timeout_ns = header_timeout(r.s);
   return r;
 }

@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(kMaxThreads, 8) batched_kernel(Args a) {
         m.bo.policy = GSYNC_BACKOFF_EXPONENTIAL;
         m.bo.min_ns = pol[1];
         m.bo.max_ns = pol[2];
+        m.bo.spin = 0;
         m.timeout_ns = a.timeout_ns;
         const gsync::Token t = lock_by_policy(m);
         if (t.status != GSYNC_OK) {

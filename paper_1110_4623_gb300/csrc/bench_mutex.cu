@@ -28,7 +28,8 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
   gsync::MutexRef m;
   if (KIND >= 0) {
     m = gsync::mutex_attach(state);
-    const bool bad_queue = KIND == GSYNC_MUTEX_SLEEP_QUEUE && gridDim.x > m.qmask + 1u;
+    const bool bad_queue =
+        (KIND == GSYNC_MUTEX_SLEEP_QUEUE || KIND == GSYNC_MUTEX_RING) && gridDim.x > m.qmask + 1u;
     if (m.kind != (uint32_t)KIND || bad_queue) {
       if (tid == 0) gsync::ptx::atom_or_relaxed(status, GSYNC_STATUS_CONFIG);
       return;
@@ -88,6 +89,7 @@ KernelFn pick(int kind) {
     case GSYNC_MUTEX_TICKET: return mutex_workload_kernel<GSYNC_MUTEX_TICKET>;
     case GSYNC_MUTEX_SLEEP_QUEUE: return mutex_workload_kernel<GSYNC_MUTEX_SLEEP_QUEUE>;
     case GSYNC_MUTEX_COHORT: return mutex_workload_kernel<GSYNC_MUTEX_COHORT>;
+    case GSYNC_MUTEX_RING: return mutex_workload_kernel<GSYNC_MUTEX_RING>;
   }
   return nullptr;
 }

@@ -25,6 +25,7 @@ struct InitSpec {
   uint32_t header[16];
   uint32_t nwords;
   uint32_t queue_slots;  // SLEEP_QUEUE: flag lines start at line 3
+  uint32_t ring_slots;   // RING: entry lines start at line 3, all empty
   uint32_t spin_sem_s;   // spin semaphores: initial S (line 1), else 0
   uint32_t die_table;    // COHORT: write die[] at kDieTableWord
   uint32_t die[gsync::kMaxSmIds / 4];  // packed bytes
@@ -43,6 +44,7 @@ __global__ void init_state_kernel(uint32_t* s, InitSpec spec) {
       const uint32_t k = line - 3;
       v = k == 0 ? 0u : k - spec.queue_slots;
     }
+    if (spec.ring_slots && word == 0 && line >= 3 && line < 3 + spec.ring_slots) v = gsync::kRingEmpty;
     if (spec.spin_sem_s && line == 1 && word == 0) v = spec.spin_sem_s;
     s[i] = v;
   }
@@ -69,6 +71,7 @@ void fill_header(InitSpec& spec, uint32_t prim, uint32_t kind, uint32_t n, uint3
     spec.header[gsync::kHdrPolicy] = bo->policy;
     spec.header[gsync::kHdrMinNs] = bo->min_ns;
     spec.header[gsync::kHdrMaxNs] = bo->max_ns;
+    if (bo->policy == GSYNC_BACKOFF_SPIN_THEN_SLEEP) spec.header[gsync::kHdrSpin] = bo->spin ? bo->spin : 32u;
   }
   spec.header[gsync::kHdrTimeoutLo] = (uint32_t)timeout_ns;
   spec.header[gsync::kHdrTimeoutHi] = (uint32_t)(timeout_ns >> 32);
@@ -120,10 +123,11 @@ extern "C" {
 int gsync_last_cuda_error(void) { return g_last_cuda_error; }
 
 size_t gsync_mutex_bytes(int kind, int max_waiters) {
-  if (kind < GSYNC_MUTEX_CAS_SPIN || kind > GSYNC_MUTEX_COHORT || max_waiters < 1) return 0;
+  if (kind < GSYNC_MUTEX_CAS_SPIN || kind > GSYNC_MUTEX_RING || max_waiters < 1) return 0;
   if (max_waiters > (1 << 24)) return 0;
   if (kind == GSYNC_MUTEX_COHORT) return kCohortBytes;
-  const uint32_t q = kind == GSYNC_MUTEX_SLEEP_QUEUE ? pow2_at_least((uint32_t)max_waiters) : 0;
+  const bool queued = kind == GSYNC_MUTEX_SLEEP_QUEUE || kind == GSYNC_MUTEX_RING;
+  const uint32_t q = queued ? pow2_at_least((uint32_t)max_waiters) : 0;
   return (size_t)(3 + q) * kLine;
 }
 
@@ -174,7 +178,7 @@ extern "C" {
 int gsync_mutex_init_cohort(void* state, size_t bytes, int budget, const gsync_backoff* backoff, uint64_t timeout_ns,
                             void* stream) {
   if (!state || !aligned(state, kLine) || bytes < kCohortBytes || budget < 1 || budget > 32767) return GSYNC_EINVAL;
-  if (backoff && backoff->policy > GSYNC_BACKOFF_LINEAR_CYCLIC) return GSYNC_EINVAL;
+  if (backoff && backoff->policy > GSYNC_BACKOFF_SPIN_THEN_SLEEP) return GSYNC_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   InitSpec spec;
   fill_header(spec, kPrimMutex, GSYNC_MUTEX_COHORT, 0, (uint32_t)budget, backoff, timeout_ns, 0);
@@ -186,14 +190,16 @@ int gsync_mutex_init(void* state, size_t bytes, int kind, int max_waiters, const
                      uint64_t timeout_ns, void* stream) {
   const size_t need = gsync_mutex_bytes(kind, max_waiters);
   if (need == 0 || bytes < need) return GSYNC_EINVAL;
-  if (backoff && backoff->policy > GSYNC_BACKOFF_LINEAR_CYCLIC) return GSYNC_EINVAL;
+  if (backoff && backoff->policy > GSYNC_BACKOFF_SPIN_THEN_SLEEP) return GSYNC_EINVAL;
   if (kind == GSYNC_MUTEX_COHORT)
     return gsync_mutex_init_cohort(state, bytes, GSYNC_COHORT_DEFAULT_BUDGET, backoff, timeout_ns, stream);
-  const uint32_t q = kind == GSYNC_MUTEX_SLEEP_QUEUE ? pow2_at_least((uint32_t)max_waiters) : 0;
+  const bool queued = kind == GSYNC_MUTEX_SLEEP_QUEUE || kind == GSYNC_MUTEX_RING;
+  const uint32_t q = queued ? pow2_at_least((uint32_t)max_waiters) : 0;
   InitSpec spec;
   fill_header(spec, kPrimMutex, (uint32_t)kind, (uint32_t)max_waiters, q, backoff, timeout_ns, 0);
   spec.nwords = (uint32_t)(need / 4);
-  spec.queue_slots = q;
+  spec.queue_slots = kind == GSYNC_MUTEX_SLEEP_QUEUE ? q : 0u;
+  spec.ring_slots = kind == GSYNC_MUTEX_RING ? q : 0u;
   return launch_init(state, bytes, spec, (cudaStream_t)stream);
 }
 
@@ -238,7 +244,7 @@ int gsync_sem_init(void* state, size_t bytes, int kind, int initial_count, const
                    uint64_t timeout_ns, void* stream) {
   const size_t need = gsync_sem_bytes(kind);
   if (need == 0 || bytes < need || initial_count < 1 || initial_count > (1 << 30)) return GSYNC_EINVAL;
-  if (backoff && backoff->policy > GSYNC_BACKOFF_LINEAR_CYCLIC) return GSYNC_EINVAL;
+  if (backoff && backoff->policy > GSYNC_BACKOFF_SPIN_THEN_SLEEP) return GSYNC_EINVAL;
   InitSpec spec;
   fill_header(spec, kPrimSem, (uint32_t)kind, (uint32_t)initial_count, 0, backoff, timeout_ns, 0);
   spec.nwords = (uint32_t)(need / 4);

@@ -18,11 +18,11 @@ GSYNC_OK, GSYNC_EINVAL, GSYNC_ENOTRESIDENT, GSYNC_ETIMEDOUT, GSYNC_ECUDA, GSYNC_
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOTRESIDENT", 3: "ETIMEDOUT", 4: "ECUDA", 5: "EABORTED"}
 GSYNC_STATUS_TIMEOUT, GSYNC_STATUS_ABORTED, GSYNC_STATUS_VIOLATION, GSYNC_STATUS_CONFIG = 1, 2, 4, 8
 
-MUTEX_KINDS = {"cas_spin": 0, "cas_backoff": 1, "ticket": 2, "sleep_queue": 3, "cohort": 4}
+MUTEX_KINDS = {"cas_spin": 0, "cas_backoff": 1, "ticket": 2, "sleep_queue": 3, "cohort": 4, "ring": 5}
 COHORT_DEFAULT_BUDGET = 64
 BARRIER_KINDS = {"atomic": 0, "flag": 1, "tree": 2, "cluster": 3, "sharded": 4, "die": 5, "split": 6}
 SEM_KINDS = {"ticket": 0, "spin": 1, "spin_backoff": 2}
-BACKOFF_EXPONENTIAL, BACKOFF_LINEAR_CYCLIC = 0, 1
+BACKOFF_EXPONENTIAL, BACKOFF_LINEAR_CYCLIC, BACKOFF_SPIN_THEN_SLEEP = 0, 1, 2
 PROBE_OPS = {"volatile_load": 0, "volatile_store": 1, "atomic_read": 2, "atomic_write": 3,
              "load_acquire": 4, "load_relaxed": 5, "store_release": 6, "red_add": 7,
              "atomic_add64": 8, "atomic_acqrel": 9}
@@ -32,7 +32,7 @@ u32p = ctypes.c_void_p
 
 class gsync_backoff(ctypes.Structure):
     _fields_ = [("policy", ctypes.c_uint32), ("min_ns", ctypes.c_uint32),
-                ("max_ns", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("max_ns", ctypes.c_uint32), ("spin", ctypes.c_uint32)]
 
 
 class gsync_barrier_work(ctypes.Structure):

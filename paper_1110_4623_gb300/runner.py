@@ -34,8 +34,8 @@ def _state(nbytes: int) -> torch.Tensor:
     return t
 
 
-def backoff(policy: int = G.BACKOFF_EXPONENTIAL, min_ns: int = 0, max_ns: int = 0) -> G.gsync_backoff:
-    return G.gsync_backoff(policy, min_ns, max_ns, 0)
+def backoff(policy: int = G.BACKOFF_EXPONENTIAL, min_ns: int = 0, max_ns: int = 0, spin: int = 0) -> G.gsync_backoff:
+    return G.gsync_backoff(policy, min_ns, max_ns, spin)
 
 
 @dataclass

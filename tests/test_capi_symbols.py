@@ -73,6 +73,9 @@ def test_size_queries_without_gpu(lib_path):
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["split"], 1184, 65 | 8 << 8) == 0
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["split"], 1184, 16) == 0  # R = 0
     assert G.gsync_mutex_bytes(G.MUTEX_KINDS["cohort"], 1) == 32768
+    # ring: header, tail, head, one line per entry (a power of two >= the waiters)
+    assert G.gsync_mutex_bytes(G.MUTEX_KINDS["ring"], 1184) == (3 + 2048) * 128
+    assert G.gsync_mutex_bytes(6, 4) == 0
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["cluster"], 1183, 8) == 0
     assert G.gsync_sem_bytes(0) == 4 * 128 and G.gsync_sem_bytes(3) == 0
     assert G.gsync_bench_mutex_workspace_bytes(2, 1184, 100, 1024) > 4 * 1184 * 100 * 4
@@ -89,6 +92,11 @@ def test_invalid_arguments_rejected_without_gpu(lib_path):
     assert G.lib().gsync_mutex_init_cohort(256, 32768, 32768, None, 0, None) == G.GSYNC_EINVAL
     assert G.lib().gsync_mutex_init_cohort(256, 4096, 64, None, 0, None) == G.GSYNC_EINVAL
     assert G.lib().gsync_device_topology(None, None, None) == G.GSYNC_EINVAL
+    # backoff policies 0..2 only (checked before any CUDA call)
+    import ctypes
+    bad = G.gsync_backoff(3, 16, 512, 0)
+    assert G.lib().gsync_mutex_init(256, 384, G.MUTEX_KINDS["cas_backoff"], 4, ctypes.byref(bad), 0,
+                                    None) == G.GSYNC_EINVAL
     assert G.lib().gsync_mutex_init(0x1001, 384, 0, 4, None, 0, None) == G.GSYNC_EINVAL
     assert G.lib().gsync_barrier_init(0x1000, 10, 0, 4, 0, 0, None) == G.GSYNC_EINVAL  # too small
     w = G.gsync_mutex_work(0, 0, 256, 1, 1, 0, None, None, None, None, None, None, None, None)

@@ -9,8 +9,8 @@ from paper_1110_4623_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-KINDS = ["cas_spin", "cas_backoff", "ticket", "sleep_queue", "cohort"]
-FAIR = {"ticket", "sleep_queue"}
+KINDS = ["cas_spin", "cas_backoff", "ticket", "sleep_queue", "cohort", "ring"]
+FAIR = {"ticket", "sleep_queue", "ring"}
 
 
 def grant_problems(kind, got, nblocks, acq, base=0, die_bases=(0, 0)):
@@ -156,3 +156,32 @@ def test_cohort_local_locks_are_homed_on_their_dies():
         near = runner.probe_rtt_by_line(sm[d], line, 1)[0]
         far = runner.probe_rtt_by_line(sm[1 - d], line, 1)[0]
         assert near + 60 < far, (d, near, far)
+
+
+@pytest.mark.parametrize("spin", [1, 32, 4096])
+def test_spin_then_sleep_policy(spin):
+    # Section 5's futex stand-in: the CAS lock spins `spin` failed attempts, then backs off.
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    B, A, K = 1184, 30, 64
+    delay, add = inputs.mutex_inputs(B, A, 700 + spin, max_delay=800)
+    bo = runner.backoff(policy=G.BACKOFF_SPIN_THEN_SLEEP, min_ns=16, max_ns=512, spin=spin)
+    got = runner.MutexRun("cas_backoff", B, 256, A, K, delay, add, bo=bo, timeout_ns=10_000_000_000).run()
+    want = calc.mutex_final(B, A, K, add)
+    assert got["status"] == 0 and got["total"] == want["total"] and np.array_equal(got["data"], want["data"])
+    assert grant_problems("cas_backoff", got, B, A) == []
+
+
+def test_ring_refuses_more_blocks_than_entries():
+    # The ring holds one entry per waiting block: a grid larger than the ring is a config error.
+    import torch
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    delay, add = inputs.mutex_inputs(64, 2, 5)
+    mr = runner.MutexRun("ring", 64, 128, 2, 8, delay, add)
+    small = torch.zeros(G.gsync_mutex_bytes(G.MUTEX_KINDS["ring"], 16), dtype=torch.uint8, device="cuda")
+    G.check("init", G.gsync_mutex_init(small, small.numel(), G.MUTEX_KINDS["ring"], 16, None, 0))
+    mr.state = small
+    mr.reset()
+    assert mr.launch() == 0
+    assert mr.results()["status"] & G.GSYNC_STATUS_CONFIG
