@@ -414,6 +414,41 @@ SERVE_CHUNK = 8192                # values per chunk (one block's share), both a
 SERVE_ADMITTERS = 16             # admitter blocks of the persistent loop (the other 288 blocks work)
 
 
+CV_PRODUCERS, CV_CONSUMERS, CV_ITEMS, CV_CAPACITY = 592, 592, 100, 16
+
+
+def condvar_section(calc, inputs, runner, terms):
+    """Condition variables (future work in Section 7): bounded producer/consumer queue at 1184
+    blocks.  Every item takes two lock acquisitions (the put and the take), so the mutex
+    roofline at an empty critical section bounds it at half that rate."""
+    import torch
+    n = CV_PRODUCERS * CV_ITEMS
+    value = inputs.condvar_inputs(n)
+    run = runner.CondVarRun(CV_PRODUCERS, CV_CONSUMERS, CV_ITEMS, CV_CAPACITY, value,
+                            bo=runner.backoff(min_ns=64, max_ns=2000))
+    want = calc.condvar_final(value, CV_PRODUCERS, CV_ITEMS, CV_CONSUMERS)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms, ok = [], True
+    for _ in range(4):
+        run.reset()
+        s.record()
+        rc = run.launch()
+        e.record()
+        torch.cuda.synchronize()
+        st = int(run.status.cpu()[0])
+        seen = run.seen.cpu().numpy().view(np.uint32)
+        ok = ok and rc == 0 and st == 0 and np.array_equal(seen, want["seen"]) and \
+            int(run.sum.sum().item()) == want["total"]
+        ms.append(s.elapsed_time(e))
+    t = float(np.median(ms[1:]))
+    items_s = n / (t * 1e-3)
+    roof = mutex_roof_acq_s(terms, 0) / 2
+    return {"workload": f"{CV_PRODUCERS} producer + {CV_CONSUMERS} consumer blocks x 128 threads, {CV_ITEMS} items "
+                        f"per producer, queue capacity {CV_CAPACITY}, one ticket mutex + two condition variables",
+            "ms": t, "items_per_s": items_s, "roof_items_per_s": roof, "frac": items_s / roof,
+            "parity": "ok" if ok else "FAILED"}
+
+
 def serve_section(calc, inputs, runner):
     """Persistent serving loop vs one launch per request at swept Poisson arrival rates."""
     import torch
@@ -568,6 +603,7 @@ def run_gpu(args):
     e2e["value"] = replica_value(1, ms_per_acq, world)
     if rank == 0:
         out["e2e"] = e2e
+        out["condvar"] = condvar_section(calc, inputs, runner, terms)
         if not args.no_batched:
             out["batched"] = batched_section(G, calc, inputs, runner, autotune)
             out["serving"] = serve_section(calc, inputs, runner)

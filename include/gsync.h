@@ -147,6 +147,17 @@ size_t gsync_barrier_bytes(int kind, int nblocks, int param);
 int gsync_barrier_init(void* state, size_t bytes, int kind, int nblocks, int param,
                        uint64_t timeout_ns, void* stream);
 
+/* Condition variable (named as future work in Section 7; the paper gives no algorithm):
+ * two counters, waiters so far and waiters released so far.  Device side (gsync_device.cuh):
+ * cond_wait(cv, mutex, token) called by the whole block while it holds the mutex takes a
+ * ticket, releases the mutex, waits until the releases pass its ticket and takes the mutex
+ * again; cond_signal_thread / cond_broadcast_thread, called by thread 0 while it holds the
+ * mutex, release the oldest waiter / every waiter.  `backoff` (may be NULL) sets the sleep
+ * between polls of a waiting block; timeout_ns = 0 selects 2 s. */
+size_t gsync_cond_bytes(void);
+int gsync_cond_init(void* state, size_t bytes, const gsync_backoff* backoff, uint64_t timeout_ns,
+                    void* stream);
+
 /* Bytes of a counting semaphore. */
 size_t gsync_sem_bytes(int kind);
 /* Initial count n >= 1 (Section 5: at most n blocks inside at once). */
@@ -274,6 +285,31 @@ typedef struct gsync_sem_work {
   uint32_t* status;
 } gsync_sem_work;
 int gsync_bench_sem(void* state, const gsync_sem_work* w, void* stream);
+
+/* Condition-variable workload: a bounded buffer (producer/consumer queue) of `capacity` item
+ * ids guarded by one TICKET mutex and two condition variables (not_full, not_empty).  Blocks
+ * 0 .. producers-1 each put items_per_producer items (item id = block * items_per_producer +
+ * i); the next `consumers` blocks each take producers * items_per_producer / consumers items
+ * (which must divide exactly).  A producer waits on not_full while the buffer is full and
+ * signals not_empty after each put; a consumer the other way round.  A consumer adds value[id]
+ * to sum[c] (int64) and seen[id] += 1 outside the mutex; count[c] = items it took.
+ * Results: seen[i] = 1 for every item, sum over consumers = sum of value[] (int64).
+ * Host entry: copies nothing; value, seen, sum, count, status are device buffers; the mutex,
+ * the two condition variables and the buffer live in `workspace` (device, 256-byte aligned,
+ * >= gsync_bench_condvar_workspace_bytes(capacity)), initialised by the call.  backoff (host,
+ * may be NULL) sets the waiters' sleep; one co-resident launch of producers + consumers
+ * blocks; GSYNC_ENOTRESIDENT if it does not fit.  status bits as for the other workloads. */
+typedef struct gsync_condvar_work {
+  int32_t producers, consumers, items_per_producer, capacity, block_threads, reserved;
+  const uint32_t* value;
+  uint32_t* seen;
+  int64_t* sum;
+  uint32_t* count;
+  uint32_t* status;
+} gsync_condvar_work;
+size_t gsync_bench_condvar_workspace_bytes(int capacity);
+int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_backoff* backoff, void* workspace,
+                        size_t workspace_bytes, void* stream);
 
 /* Batched many-mutex workload (Section 5's mutex applied to many independent instances;
  * the paper measures one instance per kernel, and names autotuning of the backoff constants

@@ -431,6 +431,77 @@ __device__ __forceinline__ void mutex_unlock(const MutexRef& m, Token t) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Condition variable (named as future work in Section 7; the paper gives no algorithm)
+// ---------------------------------------------------------------------------------------
+// line 1: tickets (waiters so far), line 2: signals (waiters released so far).  A waiter
+// takes its ticket while it still holds the mutex, so a signal made under the mutex after
+// the waiter's release cannot be lost; signal and broadcast must be called with the mutex
+// held, which also makes them plain (non-atomic) updates.  Waiters are released in ticket
+// order; a signal with no waiter does nothing.
+struct CondRef {
+  uint32_t* s;
+  Backoff bo;
+  uint64_t timeout_ns;
+  __device__ __forceinline__ uint32_t* tickets() const { return s + 1 * kLineWords; }
+  __device__ __forceinline__ uint32_t* signals() const { return s + 2 * kLineWords; }
+  __device__ __forceinline__ uint32_t* abort_word() const { return s + kHdrAbort; }
+};
+
+__device__ __forceinline__ CondRef cond_attach(void* state) {
+  CondRef c;
+  c.s = (uint32_t*)state;
+  c.bo.policy = c.s[kHdrPolicy];
+  c.bo.min_ns = c.s[kHdrMinNs];
+  c.bo.max_ns = c.s[kHdrMaxNs];
+  c.bo.spin = 0;
+  c.timeout_ns = header_timeout(c.s);
+  return c;
+}
+
+// Thread 0, holding mutex m with token tok: waits on cv and returns holding m again (tok is
+// the new token).  Releases m, polls the signals counter past its ticket, takes m again.
+template <int MKIND>
+__device__ __forceinline__ int cond_wait_thread(const CondRef& cv, const MutexRef& m, Token& tok) {
+  const uint32_t t = ptx::ld_relaxed(cv.tickets());
+  ptx::st_relaxed(cv.tickets(), t + 1u);  // under the mutex: no other writer
+  mutex_unlock_thread<MKIND>(m, tok);
+  Waiter w;
+  uint32_t sleep_ns = cv.bo.min_ns;
+  while (!after(ptx::ld_acquire(cv.signals()), t)) {
+    if (int rc = w.tick(cv.timeout_ns, cv.abort_word())) return rc;
+    if (sleep_ns) {
+      __nanosleep(sleep_ns);
+      sleep_ns = cv.bo.next(sleep_ns);
+    }
+  }
+  tok = mutex_lock_thread<MKIND>(m);
+  return tok.status;
+}
+
+// Thread 0, holding the mutex: release the oldest waiter, if any.
+__device__ __forceinline__ void cond_signal_thread(const CondRef& cv) {
+  const uint32_t sg = ptx::ld_relaxed(cv.signals()), tk = ptx::ld_relaxed(cv.tickets());
+  if (sg != tk) ptx::st_relaxed(cv.signals(), sg + 1u);
+}
+
+// Thread 0, holding the mutex: release every waiter.
+__device__ __forceinline__ void cond_broadcast_thread(const CondRef& cv) {
+  ptx::st_relaxed(cv.signals(), ptx::ld_relaxed(cv.tickets()));
+}
+
+// Block-level wait: all threads call it while the block holds m (the block's accesses before
+// the call are released with the mutex); returns holding m, with t the new token in thread 0.
+template <int MKIND>
+__device__ __forceinline__ int cond_wait(const CondRef& cv, const MutexRef& m, Token& t) {
+  __shared__ int s_rc;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) s_rc = cond_wait_thread<MKIND>(cv, m, t);
+  __syncthreads();
+  const int rc = s_rc;
+  return rc;
+}
+
+// ---------------------------------------------------------------------------------------
 // Counting semaphore (Section 5 "Semaphore"; Appendix: spin-lock and sleeping semaphores)
 // ---------------------------------------------------------------------------------------
 // TICKET (sleeping): line 1 count, line 2 ticket, line 3 turn; header N = max count.

@@ -178,6 +178,22 @@ def sem_final(nblocks: int, pairs: int, n_init: int, addend: np.ndarray) -> dict
 
 
 # --------------------------------------------------------------------------------------------
+# Condition-variable workload (a bounded producer/consumer queue; condition variables are
+# future work in Section 7): every item is put once and taken exactly once.
+# --------------------------------------------------------------------------------------------
+
+
+def condvar_final(value: np.ndarray, producers: int, items_per_producer: int, consumers: int) -> dict:
+    """seen[i] = 1 for every item; the consumers' int64 sums add up to the sum of the values
+    (read as int32); each consumer takes producers * items_per_producer / consumers items."""
+    n = producers * items_per_producer
+    v = np.asarray(value, dtype=np.uint32).view(np.int32).astype(np.int64)
+    assert v.shape == (n,) and n % consumers == 0
+    return {"seen": np.ones(n, dtype=np.uint32), "total": int(v.sum()),
+            "count": np.full(consumers, n // consumers, dtype=np.uint32)}
+
+
+# --------------------------------------------------------------------------------------------
 # Batched many-mutex workload (mutex definition, applied per key)
 # --------------------------------------------------------------------------------------------
 

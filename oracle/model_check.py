@@ -20,6 +20,7 @@ The algorithms follow Section 5 ("Design") and the pseudocode of the Appendix:
   QueueMutex    sleep-waiting queue lock: each waiter polls its own slot of a ring of flags
   RingMutex     the paper's ring-buffer sleeping mutex (Section 5, "design alternative")
   CohortMutex   two-die cohort lock: a ticket lock per die under a global ticket lock
+  CondVarQueue  condition variables (ticket and signal counters) on a bounded buffer
   SpinSem       spin-lock semaphore with optional backoff ("Spin-Lock Semaphore")
   SleepSem      sleeping (FA) semaphore ("Sleeping Semaphore")
   AtomicBarrier two-stage atomic-counter barrier (Section 5, "Barrier")
@@ -242,6 +243,85 @@ class RingMutex:
         if pc == 5:      # advance the head
             k += 1
             return ((0 if k < ops else DONE), k, t, h), _set(sh, 0, inc(t)), None
+        raise AssertionError(pc)
+
+
+class CondVarQueue:
+    """Condition variables (the paper names them as future work, without an algorithm): a
+    bounded buffer of capacity C guarded by one mutex and two condition variables, not_empty
+    and not_full.  Blocks p < P produce, the rest consume; every block makes `ops` operations,
+    so the producers' and consumers' operation totals must match.
+
+    A condition variable is two counters: tickets (waiters so far) and signals (waiters
+    released so far).  wait(cv): with the mutex held, t <- tickets; tickets <- t + 1; release
+    the mutex; poll until signals > t (wrap-safe); take the mutex again.  signal(cv), with the
+    mutex held: if signals != tickets then signals <- signals + 1 (release the oldest waiter;
+    a signal with no waiter is lost, as usual).  broadcast: signals <- tickets.  The mutex is
+    modelled as an atomic test-and-set word (its own correctness is checked elsewhere).
+
+    Safety: one block at a time updates the buffer (the mutex), and the buffer never under-
+    or overflows (a "violation" event); progress: every schedule can finish, which needs
+    P x ops produced = (nproc - P) x ops consumed.  broken="signal_before_ticket": a waiter releases the mutex before
+    taking its ticket (a signal in between is lost: deadlock).  broken="no_recheck": a woken
+    waiter does not re-test the condition (another block can take the item first: underflow).
+    """
+    kind, capacity, fifo = "mutex", 1, False
+
+    def __init__(self, P=1, C=1, broadcast=False, broken=None):
+        self.P, self.C, self.broadcast, self.broken = P, C, broadcast, broken
+
+    def init(self, nproc, ops):
+        # (lock, count, ne_tickets, ne_signals, nf_tickets, nf_signals)
+        return (0, 0, 0, 0, 0, 0), tuple((0, 0, 0, 0) for _ in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, t, r = loc
+        lock, count, net, nes, nft, nfs = sh
+        producer = p < self.P
+        # cv indices: the condition this block waits on, and the one it signals
+        W = (4, 5) if producer else (2, 3)   # producers wait for not_full, consumers for not_empty
+        S = (2, 3) if producer else (4, 5)
+
+        if pc == 0:      # lock
+            if lock:
+                return loc, sh, None
+            return (1, k, t, r), _set(sh, 0, 1), None
+        if pc == 1:      # test the condition (under the mutex)
+            ready = count < self.C if producer else count > 0
+            return ((10 if ready else (2 if self.broken != "signal_before_ticket" else 20)), k, t, r), sh, None
+        if pc == 2:      # wait: take a ticket (mutex held) ...
+            tk = sh[W[0]]
+            return (3, k, tk, r), _set(sh, W[0], inc(tk)), None
+        if pc == 3:      # ... release the mutex ...
+            return (4, k, t, r), _set(sh, 0, 0), None
+        if pc == 4:      # ... wait for a signal past the ticket ...
+            if not s_gt(sh[W[1]], t):
+                return loc, sh, None
+            return (5, k, t, r), sh, None
+        if pc == 5:      # ... and take the mutex again
+            if lock:
+                return loc, sh, None
+            return ((1 if self.broken != "no_recheck" else 10), k, t, r), _set(sh, 0, 1), None
+        if pc == 20:     # broken: release first, then take the ticket
+            return (21, k, t, r), _set(sh, 0, 0), None
+        if pc == 21:
+            tk = sh[W[0]]
+            return (4, k, tk, r), _set(sh, W[0], inc(tk)), None
+        if pc == 10:     # the buffer update (the critical section)
+            return (11, k, t, r), sh, ("enter", None)
+        if pc == 11:
+            c2 = count + 1 if producer else count - 1
+            if c2 < 0 or c2 > self.C:
+                return loc, sh, ("violation", f"buffer count {c2} outside 0..{self.C}")
+            return (12, k, t, r), _set(sh, 1, c2), ("exit",)
+        if pc == 12:     # signal (or broadcast) the other side, mutex held
+            tk, sg = sh[S[0]], sh[S[1]]
+            if sg != tk:
+                sg = tk if self.broadcast else inc(sg)
+            return (13, k, t, r), _set(sh, S[1], sg), None
+        if pc == 13:     # unlock
+            k += 1
+            return ((0 if k < ops else DONE), k, t, r), _set(sh, 0, 0), None
         raise AssertionError(pc)
 
 
@@ -864,6 +944,8 @@ def _apply(model, ghost, p, ev, nproc):
     """Updates the ghost bookkeeping for an event; returns (ghost, violation or None)."""
     if ev is None:
         return ghost, None
+    if ev[0] == "violation":
+        return ghost, ev[1]
     if model.kind == "barrier":
         arrived, passed = ghost
         if ev[0] == "arrive":

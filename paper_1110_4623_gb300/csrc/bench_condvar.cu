@@ -1,0 +1,129 @@
+// Condition-variable workload: a bounded producer/consumer queue of item ids under one
+// TICKET mutex and two condition variables (condition variables are named as future work in
+// Section 7; the design is in gsync_device.cuh).  Each item id is put once and must be taken
+// exactly once: seen[] counts takes, and the consumers' int64 sums must add up to the sum of
+// the items' values.
+#include "common.cuh"
+
+using namespace gsync_impl;
+namespace ptx = gsync::ptx;
+
+namespace {
+
+constexpr int kMaxThreads = 256;
+
+// The queue's bookkeeping, guarded by the mutex (plain accesses by the holder's thread 0).
+struct Queue {
+  uint32_t count, head, tail, capacity;
+};
+
+__global__ void __launch_bounds__(kMaxThreads)
+    condvar_workload_kernel(uint32_t* mutex_state, uint32_t* nf_state, uint32_t* ne_state, Queue* q, uint32_t* buf,
+                            int producers, int items_per_producer, int items_per_consumer,
+                            const uint32_t* __restrict__ value, uint32_t* seen, int64_t* sum, uint32_t* count,
+                            uint32_t* status) {
+  const gsync::MutexRef m = gsync::mutex_attach(mutex_state);
+  const gsync::CondRef not_full = gsync::cond_attach(nf_state), not_empty = gsync::cond_attach(ne_state);
+  const bool producer = (int)blockIdx.x < producers;
+  const int ops = producer ? items_per_producer : items_per_consumer;
+  const bool t0 = threadIdx.x == 0;
+  __shared__ int s_ok;
+  __shared__ uint32_t s_id;
+  int64_t my_sum = 0;
+  uint32_t taken = 0;
+  for (int i = 0; i < ops; ++i) {
+    gsync::Token tok = gsync::mutex_lock<GSYNC_MUTEX_TICKET>(m);
+    if (tok.status != GSYNC_OK) {
+      if (t0) record_status(status, tok.status);
+      break;
+    }
+    // wait while the buffer is full (producer) or empty (consumer); re-test after each wake
+    int rc = GSYNC_OK;
+    for (;;) {
+      if (t0) {
+        const uint32_t c = q->count;
+        s_ok = producer ? c < q->capacity : c > 0u;
+      }
+      __syncthreads();
+      if (s_ok) break;
+      rc = gsync::cond_wait<GSYNC_MUTEX_TICKET>(producer ? not_full : not_empty, m, tok);
+      if (rc != GSYNC_OK) break;
+    }
+    if (rc != GSYNC_OK) {
+      if (t0) record_status(status, rc);
+      break;  // the mutex is not held after a failed wait
+    }
+    if (t0) {
+      if (producer) {
+        const uint32_t id = blockIdx.x * (uint32_t)items_per_producer + (uint32_t)i;
+        buf[q->tail % q->capacity] = id;
+        q->tail = q->tail + 1u;
+        q->count = q->count + 1u;
+        gsync::cond_signal_thread(not_empty);
+      } else {
+        s_id = buf[q->head % q->capacity];
+        q->head = q->head + 1u;
+        q->count = q->count - 1u;
+        gsync::cond_signal_thread(not_full);
+      }
+    }
+    gsync::mutex_unlock<GSYNC_MUTEX_TICKET>(m, tok);
+    if (!producer && t0) {
+      const uint32_t id = s_id;
+      if (id < (uint32_t)(producers * items_per_producer)) {
+        atomicAdd(seen + id, 1u);
+        my_sum += (int64_t)(int32_t)value[id];
+        ++taken;
+      } else {
+        ptx::atom_or_relaxed(status, GSYNC_STATUS_VIOLATION);
+      }
+    }
+  }
+  if (!producer && t0) {
+    const uint32_t c = blockIdx.x - (uint32_t)producers;
+    sum[c] = my_sum;
+    count[c] = taken;
+  }
+}
+
+size_t round_up(size_t n) { return (n + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" size_t gsync_bench_condvar_workspace_bytes(int capacity) {
+  if (capacity < 1 || capacity > (1 << 24)) return 0;
+  return round_up(gsync_mutex_bytes(GSYNC_MUTEX_TICKET, 1)) + 2 * round_up(gsync_cond_bytes()) +
+         round_up(sizeof(Queue)) + round_up(4 * (size_t)capacity);
+}
+
+extern "C" int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_backoff* backoff, void* workspace,
+                                   size_t workspace_bytes, void* stream) {
+  if (!w || w->producers < 1 || w->consumers < 1 || w->items_per_producer < 0 || w->capacity < 1 ||
+      w->block_threads < 32 || w->block_threads > kMaxThreads || w->block_threads % 32)
+    return GSYNC_EINVAL;
+  const int64_t items = (int64_t)w->producers * w->items_per_producer;
+  if (items > (1ll << 30) || items % w->consumers) return GSYNC_EINVAL;
+  if (!w->value || !w->seen || !w->sum || !w->count || !w->status) return GSYNC_EINVAL;
+  const size_t need = gsync_bench_condvar_workspace_bytes(w->capacity);
+  if (need == 0 || !workspace || workspace_bytes < need || !aligned(workspace, 256)) return GSYNC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* p = (char*)workspace;
+  uint32_t* mstate = (uint32_t*)p;  p += round_up(gsync_mutex_bytes(GSYNC_MUTEX_TICKET, 1));
+  uint32_t* nf = (uint32_t*)p;      p += round_up(gsync_cond_bytes());
+  uint32_t* ne = (uint32_t*)p;      p += round_up(gsync_cond_bytes());
+  Queue* q = (Queue*)p;             p += round_up(sizeof(Queue));
+  uint32_t* buf = (uint32_t*)p;
+  const uint64_t timeout_ns = 10000000000ull;
+  if (int rc = gsync_mutex_init(mstate, gsync_mutex_bytes(GSYNC_MUTEX_TICKET, 1), GSYNC_MUTEX_TICKET, 1, backoff,
+                                timeout_ns, stream))
+    return rc;
+  if (int rc = gsync_cond_init(nf, gsync_cond_bytes(), backoff, timeout_ns, stream)) return rc;
+  if (int rc = gsync_cond_init(ne, gsync_cond_bytes(), backoff, timeout_ns, stream)) return rc;
+  const Queue q0 = {0u, 0u, 0u, (uint32_t)w->capacity};
+  GSYNC_CUDA(cudaMemcpyAsync(q, &q0, sizeof q0, cudaMemcpyHostToDevice, st));
+  GSYNC_CUDA(cudaStreamSynchronize(st));  // q0 lives on this stack frame
+  const int items_per_consumer = (int)(items / w->consumers);
+  return launch_coresident(condvar_workload_kernel, w->producers + w->consumers, w->block_threads, 1, 0, st, mstate, nf,
+                           ne, q, buf, w->producers, w->items_per_producer, items_per_consumer, w->value, w->seen,
+                           w->sum, w->count, w->status);
+}

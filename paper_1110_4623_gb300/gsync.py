@@ -35,6 +35,12 @@ class gsync_backoff(ctypes.Structure):
                 ("max_ns", ctypes.c_uint32), ("spin", ctypes.c_uint32)]
 
 
+class gsync_condvar_work(ctypes.Structure):
+    _fields_ = [("producers", ctypes.c_int32), ("consumers", ctypes.c_int32), ("items_per_producer", ctypes.c_int32),
+                ("capacity", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("value", u32p), ("seen", u32p), ("sum", u32p), ("count", u32p), ("status", u32p)]
+
+
 class gsync_barrier_work(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("nblocks", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("rounds", ctypes.c_int32), ("full", ctypes.c_int32), ("cluster", ctypes.c_int32),
@@ -94,6 +100,11 @@ _SIG = {
     "gsync_mutex_init_cohort": (ctypes.c_int, [u32p, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(gsync_backoff),
                                                ctypes.c_uint64, u32p]),
     "gsync_device_topology": (ctypes.c_int, [u32p, ctypes.POINTER(ctypes.c_int), u32p]),
+    "gsync_cond_bytes": (ctypes.c_size_t, []),
+    "gsync_cond_init": (ctypes.c_int, [u32p, ctypes.c_size_t, ctypes.POINTER(gsync_backoff), ctypes.c_uint64, u32p]),
+    "gsync_bench_condvar_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int]),
+    "gsync_bench_condvar": (ctypes.c_int, [ctypes.POINTER(gsync_condvar_work), ctypes.POINTER(gsync_backoff), u32p,
+                                           ctypes.c_size_t, u32p]),
     "gsync_barrier_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "gsync_barrier_init": (ctypes.c_int, [u32p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_uint64, u32p]),
@@ -243,6 +254,24 @@ def gsync_device_topology(die_of_sm, stream=None) -> tuple[int, int]:
     nd = ctypes.c_int(0)
     rc = lib().gsync_device_topology(die_of_sm.ctypes.data, ctypes.byref(nd), stream_handle(stream))
     return rc, nd.value
+
+
+def gsync_cond_bytes() -> int:
+    return lib().gsync_cond_bytes()
+
+
+def gsync_cond_init(state, nbytes, backoff=None, timeout_ns=0, stream=None) -> int:
+    bo = ctypes.byref(backoff) if backoff is not None else None
+    return lib().gsync_cond_init(ptr(state), nbytes, bo, timeout_ns, stream_handle(stream))
+
+
+def gsync_bench_condvar_workspace_bytes(capacity) -> int:
+    return lib().gsync_bench_condvar_workspace_bytes(capacity)
+
+
+def gsync_bench_condvar(work, backoff, workspace, nbytes, stream=None) -> int:
+    bo = ctypes.byref(backoff) if backoff is not None else None
+    return lib().gsync_bench_condvar(ctypes.byref(work), bo, ptr(workspace), nbytes, stream_handle(stream))
 
 
 def gsync_device_sm_count() -> tuple[int, int]:

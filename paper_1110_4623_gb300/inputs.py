@@ -28,6 +28,7 @@ SEED_MUTEX = 0x5EED0002
 SEED_SEM = 0x5EED0003
 SEED_BATCHED = 0x5EED0004
 SEED_SERVE = 0x5EED0005
+SEED_CONDVAR = 0x5EED0006
 
 
 def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
@@ -84,6 +85,12 @@ def sem_inputs(nblocks: int, pairs: int, seed: int, hold_lo: int = 100, hold_hi:
     hold = uniform_u32(seed, n, hold_lo, hold_hi)
     addend = bits_u32(seed ^ 0x5E3A5E3A, n)
     return hold, addend
+
+
+def condvar_inputs(nitems: int, seed: int = SEED_CONDVAR) -> np.ndarray:
+    """Per-item values of the condition-variable (producer/consumer) workload: uint32 bits,
+    read as int32 on both sides."""
+    return bits_u32(seed, nitems)
 
 
 def zipf_keys(seed: int, n: int, nkeys: int, s: float) -> np.ndarray:

@@ -151,6 +151,42 @@ class MutexRun:
         return out
 
 
+class CondVarRun:
+    """The condition-variable workload (gsync_bench_condvar): a bounded producer/consumer
+    queue under one mutex and two condition variables."""
+
+    def __init__(self, producers: int, consumers: int, items_per_producer: int, capacity: int,
+                 value: np.ndarray, block_threads: int = 128, bo: G.gsync_backoff | None = None):
+        n = producers * items_per_producer
+        self.producers, self.consumers, self.n, self.bo = producers, consumers, n, bo
+        self.value = _u32(value) if n else _zeros(1)
+        self.seen = _zeros(n)
+        self.sum = torch.zeros(consumers, dtype=torch.int64, device="cuda")
+        self.count = _zeros(consumers)
+        self.status = _zeros(1)
+        self.nbytes = G.gsync_bench_condvar_workspace_bytes(capacity)
+        self.ws = _state(self.nbytes)
+        self.work = G.gsync_condvar_work(producers, consumers, items_per_producer, capacity, block_threads, 0,
+                                         G.ptr(self.value), G.ptr(self.seen), G.ptr(self.sum), G.ptr(self.count),
+                                         G.ptr(self.status))
+
+    def reset(self):
+        self.seen.zero_()
+        self.sum.zero_()
+        self.count.zero_()
+        self.status.zero_()
+
+    def launch(self, stream=None) -> int:
+        return G.gsync_bench_condvar(self.work, self.bo, self.ws, self.nbytes, stream)
+
+    def run(self) -> dict:
+        self.reset()
+        rc = self.launch()
+        torch.cuda.synchronize()
+        return {"rc": rc, "status": int(_np(self.status)[0]), "seen": _np(self.seen, self.n),
+                "sum": self.sum.cpu().numpy(), "count": _np(self.count, self.consumers)}
+
+
 class SemRun:
     """A counting semaphore plus the buffers of the semaphore workload (gsync_bench_sem)."""
 

@@ -1,0 +1,53 @@
+"""Condition variables on the GPU (future work in Section 7): a bounded producer/consumer
+queue under one mutex and two condition variables.  Every item must be taken exactly once,
+and the consumers' int64 sums must add up to the oracle's total."""
+import numpy as np
+import pytest
+
+from gpu_util import require_gpu
+from oracle import calc
+from paper_1110_4623_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def check(producers, consumers, items, capacity, threads=128, bo=None):
+    from paper_1110_4623_gb300 import runner
+    n = producers * items
+    value = inputs.condvar_inputs(n, inputs.SEED_CONDVAR ^ producers ^ (consumers << 12) ^ (capacity << 24))
+    got = runner.CondVarRun(producers, consumers, items, capacity, value, block_threads=threads, bo=bo).run()
+    want = calc.condvar_final(value, producers, items, consumers)
+    assert got["rc"] == 0 and got["status"] == 0, got["status"]
+    assert np.array_equal(got["seen"], want["seen"]), int((got["seen"] != 1).sum())
+    assert int(got["sum"].sum()) == want["total"]
+    assert np.array_equal(got["count"], want["count"])
+
+
+@pytest.mark.parametrize("producers,consumers,items,capacity", [
+    (1, 1, 200, 1), (1, 1, 200, 7), (4, 4, 50, 2), (16, 4, 20, 3), (4, 16, 40, 1), (100, 10, 20, 8),
+    (592, 592, 100, 16), (592, 592, 100, 1), (1000, 184, 92, 64)])
+def test_producer_consumer_exactly_once(producers, consumers, items, capacity):
+    check(producers, consumers, items, capacity)
+
+
+def test_sleeping_waiters_and_ragged_threads():
+    from paper_1110_4623_gb300 import runner
+    check(37, 11, 33, 5, threads=96, bo=runner.backoff(min_ns=64, max_ns=2000))
+
+
+def test_no_items():
+    from paper_1110_4623_gb300 import runner
+    got = runner.CondVarRun(8, 8, 0, 4, np.zeros(0, np.uint32)).run()
+    assert got["rc"] == 0 and got["status"] == 0 and not got["count"].any()
+
+
+def test_uneven_split_is_refused():
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    r = runner.CondVarRun(3, 2, 5, 4, np.zeros(15, np.uint32))  # 15 items over 2 consumers
+    assert r.launch() == G.GSYNC_EINVAL

@@ -181,3 +181,14 @@ def test_serve_constant_pool():
     pool = np.full(1 << 20, -(2 ** 20), np.int32)
     res = calc.serve_final(np.array([0, 5]), np.array([1 << 20, 256]), pool)
     assert list(res) == [-(2 ** 40), -(2 ** 28)]  # exceeds int32: accumulated in int64
+
+
+def test_condvar_closed_form():
+    # Values read as int32: 0xFFFFFFFF is -1, so [1, 2, 0xFFFFFFFF, 5] sums to 7.
+    v = np.array([1, 2, 0xFFFFFFFF, 5], np.uint32)
+    out = calc.condvar_final(v, 2, 2, 4)
+    assert out["total"] == 7 and np.array_equal(out["count"], [1, 1, 1, 1])
+    assert np.array_equal(out["seen"], [1, 1, 1, 1])
+    # all-ones values over many items: n * (-1), beyond int32 range only in magnitude here
+    out = calc.condvar_final(np.full(1 << 16, 0x80000000, np.uint32), 4, 1 << 14, 8)
+    assert out["total"] == -(1 << 31) * (1 << 16)

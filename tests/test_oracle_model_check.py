@@ -18,6 +18,10 @@ CORRECT = [
     ("queue_wrap", mc.QueueMutex(q=4, base=W), 3, 2),
     ("queue_exact_fit", mc.QueueMutex(q=2, base=W), 2, 3),
     ("ring", mc.RingMutex(q=4), 3, 2),
+    ("condvar_1p1c", mc.CondVarQueue(P=1, C=1), 2, 3),
+    ("condvar_1p1c_cap2", mc.CondVarQueue(P=1, C=2), 2, 3),
+    ("condvar_2p2c", mc.CondVarQueue(P=2, C=1), 4, 2),
+    ("condvar_2p2c_broadcast", mc.CondVarQueue(P=2, C=1, broadcast=True), 4, 2),
     ("cohort_budget_1", mc.CohortMutex(budget=1), 4, 1),
     ("cohort_budget_2", mc.CohortMutex(budget=2), 3, 2),
     ("cohort_budget_2_4x2", mc.CohortMutex(budget=2), 4, 2),
@@ -66,6 +70,8 @@ BROKEN = [
     ("test_then_set", mc.SpinMutex(broken="test_then_set"), 2, 1, "critical section"),
     ("ticket_no_advance", mc.TicketMutex(broken="no_advance"), 2, 2, "final state"),
     ("ring_no_clear", mc.RingMutex(q=2, broken="no_clear"), 2, 3, "grant"),
+    ("condvar_release_before_ticket", mc.CondVarQueue(P=1, C=1, broken="signal_before_ticket"), 2, 3, "deadlock"),
+    ("condvar_no_recheck", mc.CondVarQueue(P=2, C=1, broken="no_recheck"), 4, 2, "buffer count"),
     ("cohort_no_global", mc.CohortMutex(broken="no_global"), 2, 1, "critical section"),
     ("cohort_owned_on_release", mc.CohortMutex(broken="owned_on_release"), 2, 2, "critical section"),
     ("cohort_pass_always", mc.CohortMutex(broken="pass_always"), 2, 2, "final state"),
