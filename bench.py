@@ -65,7 +65,7 @@ TIMEOUT_NS = 10_000_000_000
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gsync", choices=["gsync", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
