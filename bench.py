@@ -4,8 +4,8 @@ One step = one pass over every row of the hot path at 1184 blocks:
   * mutex contention (the paper's 4 kinds, its ring-buffer mutex and spin-then-sleep policy,
     and the two-die cohort lock x critical sections of 0/64/1024 words, 256 threads per block,
     100 acquisitions per block, seeded delays U{0..2000} cycles),
-  * grid barriers (atomic, flag, tree, cluster 2/4/8, sharded, two-die, split; 128 threads,
-    1000 rounds each),
+  * grid barriers (atomic, flag, tree, cluster 2/4/8, sharded, two-die, split, counting;
+    128 threads, 1000 rounds each),
   * counting semaphores (sleeping FA kind, n in {1, 4, 16, 64}; 128 threads, 200 pairs each,
     hold U{100..5000} cycles).
 `value` is lock acquisitions per second of the library's default mutex kind over its three
@@ -39,9 +39,9 @@ SEM_THREADS, SEM_PAIRS, SEM_COUNTS = 128, 200, (1, 4, 16, 64)
 # Library defaults for GB300, chosen from 1184-block sweeps (the paper's API serves the
 # fastest implementation of each primitive for the GPU as the default, Section 5 "API").
 DEFAULT_MUTEX = "cohort"
-DEFAULT_BARRIER = ("atomic", 0)
+DEFAULT_BARRIER = ("count", 8)
 BARRIERS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("cluster", 2), ("cluster", 4), ("cluster", 8),
-            ("sharded", 32), ("sharded", 8), ("die", 0), ("die", 1), ("split", 16 | 16 << 8)]
+            ("sharded", 32), ("sharded", 8), ("die", 0), ("die", 1), ("split", 16 | 16 << 8), ("count", 0), ("count", 8)]
 # Backoff (min_ns, max_ns) per kind; the ticket kinds sleep min_ns per waiter ahead, capped.
 MUTEX_BACKOFF = {"cas_backoff": (16, 512), "ticket": (128, 4000), "cohort": (128, 4000)}
 # The measured mutex configurations: (name, kind, backoff policy, (min_ns, max_ns), spin).
@@ -102,7 +102,7 @@ def replica_value(units_per_rank, ms_max, world):
 def barrier_name(kind, param):
     if kind == "flag":
         return "flag_broadcast" if param else "flag"
-    if kind in ("tree", "cluster", "sharded"):
+    if kind in ("tree", "cluster", "sharded") or (kind == "count" and param):
         return f"{kind}{param}"
     if kind == "split":
         return f"split{param & 0xFF}x{param >> 8}"
@@ -235,6 +235,8 @@ def barrier_roof_ns(terms, kind, param, B):
     elif kind == "split":
         S = param & 0xFF
         b_eff, rts = (-(-B // S) + S, 2) if S > 1 else (B, 1)
+    elif kind == "count":
+        b_eff, rts = B, 0  # the last arrival is the release: no round trip back to it
     else:
         b_eff = B
     return rts * terms["L_rt_ns"] + terms["L_handoff_ns"] + b_eff / terms["R_same_atom_ops_s"] * 1e9
@@ -560,7 +562,7 @@ def run_gpu(args):
     barrier = {}
     for (k, p) in step.barrier:
         ns = med[(k, p)] * 1e6 / BAR_ROUNDS
-        roof = barrier_roof_ns(terms, k, p if k in ("die", "split") else max(p, 1), NBLOCKS)
+        roof = barrier_roof_ns(terms, k, p if k in ("die", "split", "count") else max(p, 1), NBLOCKS)
         barrier[barrier_name(k, p)] = {"ns_per_crossing": ns, "roof_ns": roof, "frac": roof / ns}
     bkey = barrier_name(*DEFAULT_BARRIER)
     sem = {}

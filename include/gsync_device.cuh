@@ -74,6 +74,16 @@ __device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t atom_add_acq_rel_u64(uint64_t* p, uint64_t v) {
+  uint64_t r;
+  asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(v) : "memory");
+  return r;
+}
 __device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -636,6 +646,10 @@ __device__ __forceinline__ int sem_post(const SemRef& s) {
 //          arriver at a counter counts in at the top (when S > 1), and the last there writes
 //          every copy.  The blocks that used a counter reset it (the releaser after the
 //          release), as in counter_arrive_wait.
+// COUNT  : line 1 a 64-bit arrival counter that only grows.  Each block adds 1 per crossing
+//          and polls it until it reaches base + e x n for its e-th crossing since attach: the
+//          last arrival's increment is the release itself (no epoch word, no release store).
+//          param: ns of sleep before the first poll per 16 arrivals still missing (0: none).
 // Epochs increase by one per crossing and are compared for equality, so no phase resets.
 struct BarrierRef {
   uint32_t* s;
@@ -643,6 +657,7 @@ struct BarrierRef {
   uint32_t epoch;  // epoch of the last crossing, kept by each block
   uint64_t timeout_ns;
   uint32_t die, n_mine, active;  // DIE: this block's die, its die's blocks (0 = unregistered), dies
+  uint64_t base;                 // COUNT: the counter's value at attach (a multiple of n)
   __device__ __forceinline__ uint32_t* die_line(uint32_t d, uint32_t i) const {
     return s + s[d ? kHdrDieOff1 : kHdrDieOff0] + i * kLineWords;
   }
@@ -673,6 +688,12 @@ __device__ __forceinline__ BarrierRef barrier_attach(void* state) {
     b.epoch = ptx::ld_relaxed(b.line(1));
   } else if (b.kind == GSYNC_BAR_SPLIT) {
     b.epoch = ptx::ld_relaxed(b.line(1u + blockIdx.x % (b.param >> 8)));
+  } else if (b.kind == GSYNC_BAR_COUNT) {
+    // No crossing can complete before every block has attached and arrived, so the counter
+    // read here lies in [k n, k n + n - 1]: rounding down gives every block the same base.
+    const uint64_t c = ptx::ld_relaxed_u64((const uint64_t*)b.line(1));
+    b.base = c - c % b.n;
+    b.epoch = 0;
   } else if (b.kind == GSYNC_BAR_DIE) {
     const uint32_t sm = ptx::smid();
     const uint8_t* table = (const uint8_t*)(b.s + kDieTableWord);
@@ -811,6 +832,26 @@ __device__ __forceinline__ int barrier_wait(BarrierRef& b) {
     if (master) s_rc = die_arrive_wait(b, e1);
   } else if (KIND == GSYNC_BAR_SPLIT) {
     if (master) s_rc = split_arrive_wait(b, e1);
+  } else if (KIND == GSYNC_BAR_COUNT) {
+    if (master) {
+      uint64_t* cnt = (uint64_t*)b.line(1);
+      const uint64_t target = b.base + (uint64_t)e1 * b.n;
+      int rc = GSYNC_OK;
+      const uint64_t now = ptx::atom_add_acq_rel_u64(cnt, 1ull) + 1ull;
+      if (now != target) {
+        // param = ns of sleep per 16 arrivals still missing: keep the early arrivers' polls off
+        // the counter while the atomic unit works through the rest of the arrivals.
+        const uint64_t missing = target - now;
+        if (b.param && missing < (1ull << 24)) {
+          const uint64_t ns = missing * b.param / 16u;
+          __nanosleep((uint32_t)(ns < 4000u ? ns : 4000u));
+        }
+        Waiter w;
+        while (ptx::ld_acquire_u64(cnt) < target)
+          if ((rc = w.tick(b.timeout_ns, b.abort_word())) != GSYNC_OK) break;
+      }
+      s_rc = rc;
+    }
   } else if (KIND == GSYNC_BAR_CLUSTER) {
     if (master) {
       int rc = GSYNC_OK;

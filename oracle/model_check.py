@@ -30,6 +30,7 @@ The algorithms follow Section 5 ("Design") and the pseudocode of the Appendix:
   ClusterBarrier  barrier inside groups of c blocks, then one leader per group globally
   DieBarrier    per-die counters and release words, a top counter between the dies
   SplitBarrier  S arrival counters under a top counter, R copies of the release word
+  CountBarrier  one growing arrival counter that every block polls
 Mutation variants with a planted mistake (`broken=...`) exist so that tests can show the
 checker catches each kind of error.
 """
@@ -553,6 +554,35 @@ class AtomicBarrier:
                 k += 1
                 return ((0 if k < ops else DONE), k, inc(e), r), sh, ("pass",)
             return loc, sh, None
+        raise AssertionError(pc)
+
+
+class CountBarrier:
+    """Counting barrier: one arrival counter that only grows (64-bit on the device, so it never
+    wraps in practice).  Every block adds 1 per crossing and then polls the counter until it
+    reaches base + e x B for its e-th crossing: the last arrival's increment is itself the
+    release, with no epoch word.  It cannot reach e x B before every block has made its e-th
+    arrival, because no block arrives at crossing e + 1 before passing crossing e.
+    broken="off_by_one": a block waits only for base + e x B - 1."""
+    kind = "barrier"
+
+    def __init__(self, base=0, broken=None):
+        self.base, self.broken = base, broken
+
+    def init(self, nproc, ops):
+        return (self.base * nproc,), tuple((0, 0, 0, 0) for _ in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, e, r = loc
+        (count,) = sh
+        if pc == 0:
+            return (1, k, e + 1, r), (count + 1,), ("arrive",)
+        if pc == 1:
+            target = (self.base + e) * nproc - (1 if self.broken == "off_by_one" else 0)
+            if count < target:
+                return loc, sh, None
+            k += 1
+            return ((0 if k < ops else DONE), k, e, r), sh, ("pass",)
         raise AssertionError(pc)
 
 

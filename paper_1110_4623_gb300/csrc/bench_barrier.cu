@@ -107,6 +107,7 @@ KernelFn pick(int kind, int full) {
     case GSYNC_BAR_SHARDED: return full ? barrier_workload_kernel<GSYNC_BAR_SHARDED, true> : barrier_workload_kernel<GSYNC_BAR_SHARDED, false>;
     case GSYNC_BAR_DIE: return full ? barrier_workload_kernel<GSYNC_BAR_DIE, true> : barrier_workload_kernel<GSYNC_BAR_DIE, false>;
     case GSYNC_BAR_SPLIT: return full ? barrier_workload_kernel<GSYNC_BAR_SPLIT, true> : barrier_workload_kernel<GSYNC_BAR_SPLIT, false>;
+    case GSYNC_BAR_COUNT: return full ? barrier_workload_kernel<GSYNC_BAR_COUNT, true> : barrier_workload_kernel<GSYNC_BAR_COUNT, false>;
   }
   return nullptr;
 }
@@ -120,6 +121,7 @@ KernelFn pick_trace(int kind) {
     case GSYNC_BAR_SHARDED: return barrier_workload_kernel<GSYNC_BAR_SHARDED, false, true>;
     case GSYNC_BAR_DIE: return barrier_workload_kernel<GSYNC_BAR_DIE, false, true>;
     case GSYNC_BAR_SPLIT: return barrier_workload_kernel<GSYNC_BAR_SPLIT, false, true>;
+    case GSYNC_BAR_COUNT: return barrier_workload_kernel<GSYNC_BAR_COUNT, false, true>;
   }
   return nullptr;
 }

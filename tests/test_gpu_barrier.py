@@ -15,7 +15,8 @@ def _gpu():
 
 KINDS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("tree", 2), ("cluster", 2), ("cluster", 4),
          ("cluster", 8), ("sharded", 32), ("sharded", 8), ("sharded", 1), ("die", 0), ("die", 1), ("split", 1 | 1 << 8),
-         ("split", 1 | 16 << 8), ("split", 16 | 16 << 8), ("split", 64 | 64 << 8), ("split", 7 | 3 << 8)]
+         ("split", 1 | 16 << 8), ("split", 16 | 16 << 8), ("split", 64 | 64 << 8), ("split", 7 | 3 << 8),
+         ("count", 0), ("count", 8), ("count", 1024)]
 
 
 @pytest.mark.parametrize("kind,param", KINDS)
@@ -48,7 +49,7 @@ def test_sampled_sweep_1000_rounds(kind, param, nblocks):
 
 
 @pytest.mark.parametrize("kind,param", [("atomic", 0), ("flag", 0), ("tree", 3), ("cluster", 1), ("sharded", 3),
-                                        ("die", 0), ("die", 1), ("split", 5 | 3 << 8)])
+                                        ("die", 0), ("die", 1), ("split", 5 | 3 << 8), ("count", 0)])
 @pytest.mark.parametrize("nblocks,threads", [(1, 32), (2, 64), (37, 96), (151, 256)])
 def test_ragged_grids_full_fold(kind, param, nblocks, threads):
     from paper_1110_4623_gb300 import runner
@@ -67,7 +68,8 @@ def test_zero_rounds():
     assert got["rc"] == 0 and got["status"] == 0 and not got["mix"].any()
 
 
-@pytest.mark.parametrize("kind,nblocks", [("flag", 64), ("die", 64), ("die", 1184), ("die", 7), ("split", 1184)])
+@pytest.mark.parametrize("kind,nblocks", [("flag", 64), ("die", 64), ("die", 1184), ("die", 7), ("split", 1184),
+                                          ("count", 1184), ("count", 7)])
 def test_repeated_launches_continue_epochs(kind, nblocks):
     # The object keeps its epoch across launches: a second launch attaches at the new epoch
     # (DIE: and counts its blocks per die again in its first crossing).

@@ -47,6 +47,8 @@ CORRECT = [
     ("sharded_barrier_3", mc.ShardedBarrier(shards=3), 4, 2),
     ("sharded_barrier_1", mc.ShardedBarrier(shards=1), 3, 2),
     ("sharded_barrier_wrap", mc.ShardedBarrier(shards=2, base=2 ** 32 - 1), 3, 3),
+    ("count_barrier", mc.CountBarrier(), 4, 3),
+    ("count_barrier_base", mc.CountBarrier(base=5), 3, 4),
     ("split_barrier_1x1", mc.SplitBarrier(S=1, R=1), 4, 3),
     ("split_barrier_1x2", mc.SplitBarrier(S=1, R=2), 4, 3),
     ("split_barrier_2x2", mc.SplitBarrier(S=2, R=2), 4, 3),
@@ -83,6 +85,7 @@ BROKEN = [
     ("sharded_early", mc.ShardedBarrier(shards=2, broken="early"), 3, 1, "passed round"),
     ("die_no_top", mc.DieBarrier(broken="no_top"), 2, 2, "passed round"),
     ("split_no_top", mc.SplitBarrier(S=2, R=2, broken="no_top"), 3, 1, "passed round"),
+    ("count_off_by_one", mc.CountBarrier(broken="off_by_one"), 3, 1, "passed round"),
     ("split_one_copy_early", mc.SplitBarrier(S=2, R=2, broken="one_copy_early"), 3, 3, "completion"),
     ("die_no_reset", mc.DieBarrier(broken="no_reset"), 2, 4, "final state"),
     ("sharded_counts_master", mc.ShardedBarrier(shards=2, broken="counts_master"), 3, 1, "final state"),
