@@ -371,8 +371,8 @@ int gsync_bench_batched(const gsync_batched_work* w, void* stream);
  * after the start and records latency_ns[q] = the host time its completion flag was first
  * seen minus sched_ns[q] (open loop: latency counts from the scheduled arrival).
  *  - On the device, each of the `admitters` blocks first waits on the admission semaphore
- *    (n = nslots in-flight requests), then takes the next request index under the ring's
- *    ticket lock, then waits for that ring entry to be published, claims a free slot and
+ *    (n = nslots in-flight requests), then takes the next request index (its ticket of the
+ *    ring's ticket lock), then waits for that ring entry to be published, claims a free slot and
  *    publishes the request in it; every other block claims chunks of chunk_elems values of
  *    any active request; the block that finishes a request's last chunk writes res[q] and
  *    done[q] = 1 into pinned host memory, frees the slot and posts the semaphore.  The

@@ -67,7 +67,6 @@ struct Args {
   uint32_t* done;            // device view of host completion flags
   const int32_t* pool;
   uint32_t* ring_lock;       // gsync mutex (TICKET)
-  uint32_t* ring_head;       // next request index to take (own line)
   uint32_t* admit_sem;       // gsync semaphore (TICKET), n = nslots
   Slot* slots;
   uint32_t* active_mask;     // one bit per slot (nslots <= 64)
@@ -195,10 +194,12 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(Args a) {
           gsync::sem_post_thread<GSYNC_SEM_TICKET>(sem);
           break;
         }
+        // The ring's head index is the ticket of the ring lock: tickets are handed out in
+        // order from 0, one per acquisition, so the holder needs no head word and releases
+        // the lock at once.
         const gsync::Token t = gsync::mutex_lock_thread<GSYNC_MUTEX_TICKET>(lock);
         if (t.status != GSYNC_OK) { record_status(a.status, t.status); break; }
-        const uint32_t h = ptx::ld_relaxed(a.ring_head);
-        ptx::st_relaxed(a.ring_head, h + 1u);
+        const uint32_t h = t.ticket;
         gsync::mutex_unlock_thread<GSYNC_MUTEX_TICKET>(lock, t.ticket);
         // wait for entry h (seq == seq_check == h + 1) or shutdown
         const gsync_serve_req* e =
@@ -412,7 +413,7 @@ int check_requests(const gsync_serve_cfg* cfg, const gsync_serve_buffers* buf) {
 
 extern "C" size_t gsync_serve_workspace_bytes(int nslots) {
   if (nslots < 1 || nslots > 64) return 0;
-  return 3 * 128 /* ring lock */ + 128 /* head */ + 4 * 128 /* semaphore */ + (size_t)nslots * 128 +
+  return 3 * 128 /* ring lock */ + 4 * 128 /* semaphore */ + (size_t)nslots * 128 +
          128 * kMaskCopies /* active mask */ + 3 * 128 /* stats */ + 128 /* status */ + 128 /* device shutdown */;
 }
 
@@ -431,7 +432,6 @@ extern "C" int gsync_serve_run(const gsync_serve_cfg* cfg, gsync_serve_buffers* 
   cudaStream_t st = (cudaStream_t)stream;
   char* p = (char*)workspace;
   uint32_t* ring_lock = (uint32_t*)p; p += 3 * 128;
-  uint32_t* head = (uint32_t*)p;      p += 128;
   uint32_t* sem = (uint32_t*)p;       p += 4 * 128;
   Slot* slots = (Slot*)p;             p += (size_t)cfg->nslots * 128;
   uint32_t* mask = (uint32_t*)p;      p += 128 * kMaskCopies;
@@ -471,7 +471,6 @@ extern "C" int gsync_serve_run(const gsync_serve_cfg* cfg, gsync_serve_buffers* 
   a.done = (uint32_t*)d_done;
   a.pool = buf->pool;
   a.ring_lock = ring_lock;
-  a.ring_head = head;
   a.admit_sem = sem;
   a.slots = slots;
   a.active_mask = mask;
