@@ -58,6 +58,7 @@ CASES = {
     "barrier_atomic": lambda: _barrier("atomic", 0),
     "barrier_flag": lambda: _barrier("flag", 0),
     "barrier_cluster2": lambda: _barrier("cluster", 2),
+    "barrier_count8": lambda: _barrier("count", 8),
     "sem_ticket_n4": lambda: _sem(4),
     "batched_200k": lambda: _batched(),
 }
