@@ -75,8 +75,8 @@ typedef enum gsync_barrier_kind {
                             param 1: one flat counter */
   GSYNC_BAR_SPLIT = 6,   /* S arrival counters under a top counter, R copies of the release
                             word (param = S | R << 8) */
-  GSYNC_BAR_COUNT = 7    /* one growing 64-bit arrival counter that every block polls: the
-                            last arrival is the release (no epoch word) */
+  GSYNC_BAR_COUNT = 7    /* a growing 64-bit arrival counter that every block polls: the last
+                            arrival is the release (no epoch word); optionally two levels */
 } gsync_barrier_kind;
 
 /* Semaphore kinds (Section 5, "Semaphore"; Appendix, spin-lock and sleeping semaphores). */
@@ -140,8 +140,9 @@ int gsync_device_topology(uint8_t* die_of_sm, int* ndies_out, void* stream);
  * (CLUSTER, 1..8, divides nblocks), release mode (FLAG: 0 one flag per block, 1 one word;
  * FLAG takes at most 8192 blocks), number of arrival counters (SHARDED, 1..32), S | R << 8
  * (SPLIT: S arrival counters and R release copies, 1..64 each), 0 or 1 (DIE: per-die counters,
- * or one flat counter with a release word on each die), 0..1024 (COUNT: ns of sleep before the
- * first poll per 16 arrivals still missing; 0 polls at once), 0 (ATOMIC).  FLAG and SHARDED need blockDim.x >= 32 (warp 0 of block 0 gathers the arrivals).
+ * or one flat counter with a release word on each die), sleep | S << 16 (COUNT: sleep 0..1023 =
+ * ns of sleep before the first poll per 16 arrivals still missing, 0 polls at once; S 0..64,
+ * S > 1 counts in through S sub-counters), 0 (ATOMIC).  FLAG and SHARDED need blockDim.x >= 32 (warp 0 of block 0 gathers the arrivals).
  * DIE takes 32 KB; its init measures the SM-to-die map and the home die of the state's
  * 4 KB pages as gsync_mutex_init_cohort does (and synchronizes `stream`); the first
  * crossing of each launch counts the blocks per die (a flat crossing), later ones run per

@@ -84,6 +84,9 @@ __device__ __forceinline__ uint64_t atom_add_acq_rel_u64(uint64_t* p, uint64_t v
   asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(v) : "memory");
   return r;
 }
+__device__ __forceinline__ void red_add_release_u64(uint64_t* p, uint64_t v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 __device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -649,7 +652,11 @@ __device__ __forceinline__ int sem_post(const SemRef& s) {
 // COUNT  : line 1 a 64-bit arrival counter that only grows.  Each block adds 1 per crossing
 //          and polls it until it reaches base + e x n for its e-th crossing since attach: the
 //          last arrival's increment is the release itself (no epoch word, no release store).
-//          param: ns of sleep before the first poll per 16 arrivals still missing (0: none).
+//          param bits 0-9: ns of sleep before the first poll per 16 arrivals still missing
+//          (0: none); bits 16-22: S.  S > 1 counts in two levels: block b adds to sub-counter
+//          b mod S (lines 2 .. S+1), the arrival that completes a sub-counter's crossing adds 1
+//          to the line-1 counter with a fire-and-forget release, and every block polls line 1
+//          until it reaches base + e x G (G = min(S, n) sub-counters in use).
 // Epochs increase by one per crossing and are compared for equality, so no phase resets.
 struct BarrierRef {
   uint32_t* s;
@@ -657,7 +664,7 @@ struct BarrierRef {
   uint32_t epoch;  // epoch of the last crossing, kept by each block
   uint64_t timeout_ns;
   uint32_t die, n_mine, active;  // DIE: this block's die, its die's blocks (0 = unregistered), dies
-  uint64_t base;                 // COUNT: the counter's value at attach (a multiple of n)
+  uint64_t base, sub_base;       // COUNT: counters' values at attach (multiples of their parties)
   __device__ __forceinline__ uint32_t* die_line(uint32_t d, uint32_t i) const {
     return s + s[d ? kHdrDieOff1 : kHdrDieOff0] + i * kLineWords;
   }
@@ -690,9 +697,19 @@ __device__ __forceinline__ BarrierRef barrier_attach(void* state) {
     b.epoch = ptx::ld_relaxed(b.line(1u + blockIdx.x % (b.param >> 8)));
   } else if (b.kind == GSYNC_BAR_COUNT) {
     // No crossing can complete before every block has attached and arrived, so the counter
-    // read here lies in [k n, k n + n - 1]: rounding down gives every block the same base.
+    // read here lies in [k P, k P + P - 1] for its P parties per crossing: rounding down
+    // gives every block the same base (and every block of a sub-counter the same sub-base).
+    const uint32_t S = (b.param >> 16) & 0x7Fu;
+    const uint64_t P = S > 1u ? (uint64_t)min(S, b.n) : (uint64_t)b.n;
     const uint64_t c = ptx::ld_relaxed_u64((const uint64_t*)b.line(1));
-    b.base = c - c % b.n;
+    b.base = c - c % P;
+    b.sub_base = 0;
+    if (S > 1u) {
+      const uint32_t g = blockIdx.x % S;
+      const uint64_t members = (b.n - g + S - 1u) / S;
+      const uint64_t v = ptx::ld_relaxed_u64((const uint64_t*)b.line(2u + g));
+      b.sub_base = v - v % members;
+    }
     b.epoch = 0;
   } else if (b.kind == GSYNC_BAR_DIE) {
     const uint32_t sm = ptx::smid();
@@ -834,20 +851,34 @@ __device__ __forceinline__ int barrier_wait(BarrierRef& b) {
     if (master) s_rc = split_arrive_wait(b, e1);
   } else if (KIND == GSYNC_BAR_COUNT) {
     if (master) {
-      uint64_t* cnt = (uint64_t*)b.line(1);
-      const uint64_t target = b.base + (uint64_t)e1 * b.n;
+      const uint32_t S = (b.param >> 16) & 0x7Fu, sleep16 = b.param & 0x3FFu;
+      uint64_t* top = (uint64_t*)b.line(1);
       int rc = GSYNC_OK;
-      const uint64_t now = ptx::atom_add_acq_rel_u64(cnt, 1ull) + 1ull;
-      if (now != target) {
-        // param = ns of sleep per 16 arrivals still missing: keep the early arrivers' polls off
-        // the counter while the atomic unit works through the rest of the arrivals.
-        const uint64_t missing = target - now;
-        if (b.param && missing < (1ull << 24)) {
-          const uint64_t ns = missing * b.param / 16u;
+      uint64_t target, missing;
+      if (S > 1u) {
+        const uint32_t g = blockIdx.x % S;
+        const uint64_t members = (b.n - g + S - 1u) / S;
+        const uint64_t sub_target = b.sub_base + (uint64_t)e1 * members;
+        const uint64_t now = ptx::atom_add_acq_rel_u64((uint64_t*)b.line(2u + g), 1ull) + 1ull;
+        if (now == sub_target) ptx::red_add_release_u64(top, 1ull);  // this sub-counter is complete
+        target = b.base + (uint64_t)e1 * min(S, b.n);
+        missing = sub_target - now;
+      } else {
+        target = b.base + (uint64_t)e1 * b.n;
+        const uint64_t now = ptx::atom_add_acq_rel_u64(top, 1ull) + 1ull;
+        missing = target - now;
+      }
+      if (missing) {
+        // Sleep in proportion to the arrivals still missing, to keep the early arrivers' polls
+        // off the counter while the atomic unit works through the rest of the arrivals.
+        if (sleep16 && missing < (1ull << 24)) {
+          const uint64_t ns = missing * sleep16 / 16u;
           __nanosleep((uint32_t)(ns < 4000u ? ns : 4000u));
         }
+      }
+      if (S > 1u || missing) {
         Waiter w;
-        while (ptx::ld_acquire_u64(cnt) < target)
+        while (ptx::ld_acquire_u64(top) < target)
           if ((rc = w.tick(b.timeout_ns, b.abort_word())) != GSYNC_OK) break;
       }
       s_rc = rc;

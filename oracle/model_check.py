@@ -563,23 +563,53 @@ class CountBarrier:
     reaches base + e x B for its e-th crossing: the last arrival's increment is itself the
     release, with no epoch word.  It cannot reach e x B before every block has made its e-th
     arrival, because no block arrives at crossing e + 1 before passing crossing e.
-    broken="off_by_one": a block waits only for base + e x B - 1."""
+    broken="off_by_one": a block waits only for base + e x B - 1.
+
+    S > 1 (two levels): block p counts in on sub-counter p mod S; the arrival that completes
+    its sub-counter's e-th crossing (known from the value its fetch-and-add returns) adds 1 to
+    the top counter without waiting for a return, and every block polls the top counter until
+    it reaches base + e x G (G = min(S, B) sub-counters in use).  broken="top_early": the top
+    counter gets its increment from the first arrival of a sub-counter, not the last."""
     kind = "barrier"
 
-    def __init__(self, base=0, broken=None):
-        self.base, self.broken = base, broken
+    def __init__(self, base=0, S=1, broken=None):
+        self.base, self.S, self.broken = base, S, broken
 
     def init(self, nproc, ops):
-        return (self.base * nproc,), tuple((0, 0, 0, 0) for _ in range(nproc))
+        if self.S == 1:
+            return (self.base * nproc,), tuple((0, 0, 0, 0) for _ in range(nproc))
+        G = min(self.S, nproc)
+        subs = tuple(self.base * len(range(c, nproc, self.S)) for c in range(self.S))
+        return (self.base * G,) + subs, tuple((0, 0, 0, 0) for _ in range(nproc))
 
     def step(self, p, loc, sh, nproc, ops):
         pc, k, e, r = loc
-        (count,) = sh
-        if pc == 0:
-            return (1, k, e + 1, r), (count + 1,), ("arrive",)
+        if self.S == 1:
+            (count,) = sh
+            if pc == 0:
+                return (1, k, e + 1, r), (count + 1,), ("arrive",)
+            if pc == 1:
+                target = (self.base + e) * nproc - (1 if self.broken == "off_by_one" else 0)
+                if count < target:
+                    return loc, sh, None
+                k += 1
+                return ((0 if k < ops else DONE), k, e, r), sh, ("pass",)
+            raise AssertionError(pc)
+        G = min(self.S, nproc)
+        c = p % self.S
+        members = len(range(c, nproc, self.S))
+        top = sh[0]
+        if pc == 0:      # sub-counter fetch-and-add
+            old = sh[1 + c]
+            e1 = e + 1
+            last = old + 1 == (self.base + e1) * members
+            first = old == (self.base + e1 - 1) * members
+            bump = first if self.broken == "top_early" else last
+            return ((2 if bump else 1), k, e1, r), _set(sh, 1 + c, old + 1), ("arrive",)
+        if pc == 2:      # completes the sub-counter: count in at the top (no return awaited)
+            return (1, k, e, r), _set(sh, 0, top + 1), None
         if pc == 1:
-            target = (self.base + e) * nproc - (1 if self.broken == "off_by_one" else 0)
-            if count < target:
+            if top < (self.base + e) * G:
                 return loc, sh, None
             k += 1
             return ((0 if k < ops else DONE), k, e, r), sh, ("pass",)

@@ -112,8 +112,10 @@ uint32_t barrier_lines(int kind, uint32_t n, uint32_t param) {
       return (uint32_t)(kCohortBytes / kLine);
     case GSYNC_BAR_SPLIT:
       return 1 + (param >> 8) + 2 * (param & 0xFFu) + 2;
-    case GSYNC_BAR_COUNT:
-      return 2;
+    case GSYNC_BAR_COUNT: {
+      const uint32_t S = (param >> 16) & 0x7Fu;
+      return 2 + (S > 1 ? S : 0);
+    }
   }
   return 0;
 }
@@ -214,7 +216,11 @@ size_t gsync_barrier_bytes(int kind, int nblocks, int param) {
     case GSYNC_BAR_CLUSTER: if (param < 1 || param > 8 || nblocks % param) return 0; break;
     case GSYNC_BAR_SHARDED: if (param < 1 || param > 32 || param > nblocks) return 0; break;
     case GSYNC_BAR_DIE: if (param != 0 && param != 1) return 0; break;
-    case GSYNC_BAR_COUNT: if (param < 0 || param > 1024) return 0; break;
+    case GSYNC_BAR_COUNT: {
+      const int sleep16 = param & 0xFFFF, S = param >> 16;
+      if (param < 0 || sleep16 > 1023 || S > 64) return 0;
+      break;
+    }
     case GSYNC_BAR_SPLIT: {
       const int S = param & 0xFF, R = param >> 8;
       if (param < 0 || S < 1 || S > 64 || R < 1 || R > 64) return 0;

@@ -73,7 +73,9 @@ def test_size_queries_without_gpu(lib_path):
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["split"], 1184, 65 | 8 << 8) == 0
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["split"], 1184, 16) == 0  # R = 0
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["count"], 1184, 0) == 2 * 128
-    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["count"], 1184, 1025) == 0
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["count"], 1184, 1024) == 0
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["count"], 1184, 8 | 16 << 16) == (2 + 16) * 128
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["count"], 1184, 8 | 65 << 16) == 0
     assert G.gsync_mutex_bytes(G.MUTEX_KINDS["cohort"], 1) == 32768
     # ring: header, tail, head, one line per entry (a power of two >= the waiters)
     assert G.gsync_mutex_bytes(G.MUTEX_KINDS["ring"], 1184) == (3 + 2048) * 128

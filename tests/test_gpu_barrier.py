@@ -16,7 +16,8 @@ def _gpu():
 KINDS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("tree", 2), ("cluster", 2), ("cluster", 4),
          ("cluster", 8), ("sharded", 32), ("sharded", 8), ("sharded", 1), ("die", 0), ("die", 1), ("split", 1 | 1 << 8),
          ("split", 1 | 16 << 8), ("split", 16 | 16 << 8), ("split", 64 | 64 << 8), ("split", 7 | 3 << 8),
-         ("count", 0), ("count", 8), ("count", 1024)]
+         ("count", 0), ("count", 8), ("count", 1023), ("count", 8 | 16 << 16), ("count", 2 << 16),
+         ("count", 8 | 64 << 16), ("count", 7 << 16)]
 
 
 @pytest.mark.parametrize("kind,param", KINDS)
@@ -49,7 +50,8 @@ def test_sampled_sweep_1000_rounds(kind, param, nblocks):
 
 
 @pytest.mark.parametrize("kind,param", [("atomic", 0), ("flag", 0), ("tree", 3), ("cluster", 1), ("sharded", 3),
-                                        ("die", 0), ("die", 1), ("split", 5 | 3 << 8), ("count", 0)])
+                                        ("die", 0), ("die", 1), ("split", 5 | 3 << 8), ("count", 0),
+                                        ("count", 8 | 5 << 16)])
 @pytest.mark.parametrize("nblocks,threads", [(1, 32), (2, 64), (37, 96), (151, 256)])
 def test_ragged_grids_full_fold(kind, param, nblocks, threads):
     from paper_1110_4623_gb300 import runner

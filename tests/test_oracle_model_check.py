@@ -49,6 +49,9 @@ CORRECT = [
     ("sharded_barrier_wrap", mc.ShardedBarrier(shards=2, base=2 ** 32 - 1), 3, 3),
     ("count_barrier", mc.CountBarrier(), 4, 3),
     ("count_barrier_base", mc.CountBarrier(base=5), 3, 4),
+    ("count_barrier_two_level", mc.CountBarrier(S=2), 4, 3),
+    ("count_barrier_two_level_3", mc.CountBarrier(S=3, base=2), 4, 3),
+    ("count_barrier_more_subs_than_blocks", mc.CountBarrier(S=4), 3, 3),
     ("split_barrier_1x1", mc.SplitBarrier(S=1, R=1), 4, 3),
     ("split_barrier_1x2", mc.SplitBarrier(S=1, R=2), 4, 3),
     ("split_barrier_2x2", mc.SplitBarrier(S=2, R=2), 4, 3),
@@ -86,6 +89,7 @@ BROKEN = [
     ("die_no_top", mc.DieBarrier(broken="no_top"), 2, 2, "passed round"),
     ("split_no_top", mc.SplitBarrier(S=2, R=2, broken="no_top"), 3, 1, "passed round"),
     ("count_off_by_one", mc.CountBarrier(broken="off_by_one"), 3, 1, "passed round"),
+    ("count_top_early", mc.CountBarrier(S=2, broken="top_early"), 4, 2, "passed round"),
     ("split_one_copy_early", mc.SplitBarrier(S=2, R=2, broken="one_copy_early"), 3, 3, "completion"),
     ("die_no_reset", mc.DieBarrier(broken="no_reset"), 2, 4, "final state"),
     ("sharded_counts_master", mc.ShardedBarrier(shards=2, broken="counts_master"), 3, 1, "final state"),
