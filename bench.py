@@ -572,6 +572,13 @@ def run_gpu(args):
         roof = sem_roof_ops_s(terms, n)
         sem[str(n)] = {"ops_per_s": ops, "roof_ops_per_s": roof, "frac": ops / roof}
 
+    # Section 4's rule plus its GB300 extensions (dies, hand-off gap, same-word atomic cost),
+    # applied to this GPU's measurements, beside the defaults the sweeps chose.
+    from paper_1110_4623_gb300 import machine
+    ext = machine.measure_extended(NBLOCKS)
+    params = machine.abstraction(machine.measure_table(NBLOCKS, 128, 1000, reps=1))
+    design_rule = {"section4": machine.design(params), "extended": machine.design_extended(params, ext, NBLOCKS),
+                   "measured": ext, "defaults": {"mutex": DEFAULT_MUTEX, "barrier": barrier_name(*DEFAULT_BARRIER)}}
     out = {
         "metric": METRIC, "value": value, "unit": "acq/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -594,6 +601,7 @@ def run_gpu(args):
         "mutex": mutex,
         "semaphore": {"kind": "ticket", "backoff_ns": list(SEM_BACKOFF), "n": sem},
         "roofline_terms": terms,
+        "design_rule": design_rule,
         "clocks": clk,
         "gpu_launches": step.launches * args.steps,
         "wall_s_timed_loop": wall,

@@ -75,3 +75,41 @@ def design(params: dict) -> dict:
     if params["line_hostage"]:
         return {"barrier": "flag", "mutex": "cas_backoff", "sem_low": "spin_backoff", "sem_high": "ticket"}
     return {"barrier": "flag", "mutex": "cas_backoff", "sem_low": "ticket", "sem_high": "ticket"}
+
+
+# ---- GB300 extensions of the abstraction ------------------------------------------------
+# Section 4 rates a GPU by how its atomics compare with its volatile accesses.  On GB300 two
+# more things decide the design: a hand-off's cost depends on the dies of the two SMs and of
+# the line (a two-die part), and a same-word atomic at the L2 slice (~0.6 ns) is cheap next to
+# a release fence or an SM-to-SM hand-off (~160-480 ns), so serialized arrivals can cost less
+# than an extra hand-off stage.
+
+# A cross-die hand-off this much slower than an on-die one makes keeping hand-offs on a die pay.
+DIE_GAP_NS = 100.0
+
+
+def measure_extended(nblocks: int = 1184) -> dict:
+    """Dies, near and far hand-off, release-fence cost and same-word atomic time, measured."""
+    import numpy as np
+    die, nd = runner.device_topology()
+    near = runner.near_handoff(2000)["handoff_ns"]
+    far = near
+    if nd == 2:
+        a, b = int(np.flatnonzero(die == 0)[0]), int(np.flatnonzero(die == 1)[0])
+        far = runner.probe_pingpong(a, b, 2000)["handoff_ns"]
+    fence = runner.probe_fence(0)["ns_per_fence"]
+    r_same = runner.probe_throughput("red_add", True, False, nblocks, 128, 2000)["ops_per_s"]
+    return {"dies": nd, "handoff_near_ns": near, "handoff_far_ns": far, "fence_ns": fence,
+            "atomic_same_ns": 1e9 / r_same}
+
+
+def design_extended(params: dict, ext: dict, nblocks: int = 1184) -> dict:
+    """The Section 4 choice, then the GB300 extensions: a cohort lock on a two-die part whose
+    cross-die hand-off is DIE_GAP_NS slower, and the counting barrier when `nblocks` serialized
+    same-word atomics cost less than the two hand-offs of the flag barrier's extra stage."""
+    choice = dict(design(params))
+    if ext["dies"] == 2 and ext["handoff_far_ns"] - ext["handoff_near_ns"] > DIE_GAP_NS:
+        choice["mutex"] = "cohort"
+    if nblocks * ext["atomic_same_ns"] < 2.0 * ext["handoff_near_ns"]:
+        choice["barrier"] = "count"
+    return choice

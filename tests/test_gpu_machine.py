@@ -37,3 +37,15 @@ def test_ratio_arithmetic_matches_oracle(table):
 
 def test_contentious_atomics_slower_than_noncontentious(table):
     assert table[("cont_atomic", "read")] > table[("noncont_atomic", "read")]
+
+
+def test_extended_abstraction_measured_on_this_gpu():
+    from paper_1110_4623_gb300 import machine
+    ext = machine.measure_extended(1184)
+    assert ext["dies"] in (1, 2)
+    assert 0 < ext["atomic_same_ns"] < 100 and 50 < ext["handoff_near_ns"] < 5000 and ext["fence_ns"] > 0
+    if ext["dies"] == 2:
+        # the cross-die hand-off is the slower one, and the rule then keeps hand-offs on a die
+        assert ext["handoff_far_ns"] > ext["handoff_near_ns"]
+        params = machine.abstraction(machine.measure_table(1184, 128, 1000, reps=1))
+        assert machine.design_extended(params, ext)["mutex"] == "cohort"
