@@ -1,0 +1,66 @@
+"""Seeded repetitions of the GB300 designs across shapes and parameters (cohort mutex,
+counting barrier, condition variables, serving loop), each checked exactly against the
+oracle: a net for races that one shape per test could miss."""
+import numpy as np
+import pytest
+
+from gpu_util import require_gpu
+from oracle import calc
+from paper_1110_4623_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+@pytest.mark.parametrize("i", range(30))
+def test_cohort_mutex_repeated(i):
+    from paper_1110_4623_gb300 import runner
+    B = [148, 296, 592, 1184, 1216][i % 5]
+    K = [0, 64, 1024][i % 3]
+    budget = [1, 2, 16, 64, 4096][i % 5]
+    delay, add = inputs.mutex_inputs(B, 20, 10_000 + i, max_delay=[0, 300, 2000][i % 3])
+    got = runner.MutexRun("cohort", B, 256, 20, K, delay, add, budget=budget, timeout_ns=10**10,
+                          bo=runner.backoff(min_ns=[0, 128][i % 2], max_ns=4000)).run()
+    want = calc.mutex_final(B, 20, K, add)
+    assert got["status"] == 0 and got["total"] == want["total"] and np.array_equal(got["data"], want["data"])
+    assert calc.check_grant_log(got["log"], got["ticket"], B, 20, False, per_die=True) == []
+
+
+@pytest.mark.parametrize("i", range(30))
+def test_counting_barrier_repeated(i):
+    from paper_1110_4623_gb300 import runner
+    B = [2, 7, 64, 148, 600, 1184, 1216][i % 7]
+    param = [0, 8, 16, 8 | 4 << 16, 1023][i % 5]
+    got = runner.BarrierRun("count", B, 128, 300, full=True, param=param, timeout_ns=10**10).run()
+    want = calc.barrier_full(B, 300)
+    assert got["status"] == 0 and not got["bad"].any()
+    assert np.array_equal(got["chk"], want["chk"]) and np.array_equal(got["mix"], want["mix"])
+
+
+@pytest.mark.parametrize("i", range(20))
+def test_condvar_repeated(i):
+    from paper_1110_4623_gb300 import runner
+    P, C, items = [(1, 1, 50), (8, 8, 20), (100, 50, 10), (592, 592, 40), (1100, 100, 10)][i % 5]
+    v = inputs.condvar_inputs(P * items, 777 + i)
+    got = runner.CondVarRun(P, C, items, [1, 2, 16, 64][i % 4], v,
+                            bo=runner.backoff(min_ns=[0, 64][i % 2], max_ns=2000)).run()
+    want = calc.condvar_final(v, P, items, C)
+    assert got["rc"] == 0 and got["status"] == 0
+    assert np.array_equal(got["seen"], want["seen"]) and int(got["sum"].sum()) == want["total"]
+
+
+@pytest.mark.parametrize("i,rate,nslots,admitters,chunk", [
+    (0, 1e4, 64, 16, 8192), (1, 1e5, 8, 4, 1024), (2, 5e5, 1, 1, 32768), (3, 1e6, 64, 16, 4096),
+    (4, 2e6, 32, 8, 8192), (5, 1e5, 3, 2, 2048)])
+def test_serving_repeated(i, rate, nslots, admitters, chunk):
+    import torch
+    from paper_1110_4623_gb300 import runner
+    off, ln, pool = inputs.serve_inputs(3000, 16 << 20, seed=99)
+    sched = inputs.poisson_arrivals(3000, rate, seed=500 + i)
+    r = runner.ServeRun(off, ln, sched, torch.from_numpy(pool).cuda(), nslots=nslots, nblocks=304,
+                        admitters=admitters, chunk_elems=chunk).run()
+    assert r["rc"] == 0 and np.array_equal(r["res"], calc.serve_final(off, ln, pool))
