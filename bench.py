@@ -426,29 +426,32 @@ def condvar_section(calc, inputs, runner, terms):
     import torch
     n = CV_PRODUCERS * CV_ITEMS
     value = inputs.condvar_inputs(n)
-    run = runner.CondVarRun(CV_PRODUCERS, CV_CONSUMERS, CV_ITEMS, CV_CAPACITY, value,
-                            bo=runner.backoff(min_ns=64, max_ns=2000))
     want = calc.condvar_final(value, CV_PRODUCERS, CV_ITEMS, CV_CONSUMERS)
-    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ms, ok = [], True
-    for _ in range(4):
-        run.reset()
-        s.record()
-        rc = run.launch()
-        e.record()
-        torch.cuda.synchronize()
-        st = int(run.status.cpu()[0])
-        seen = run.seen.cpu().numpy().view(np.uint32)
-        ok = ok and rc == 0 and st == 0 and np.array_equal(seen, want["seen"]) and \
-            int(run.sum.sum().item()) == want["total"]
-        ms.append(s.elapsed_time(e))
-    t = float(np.median(ms[1:]))
-    items_s = n / (t * 1e-3)
     roof = mutex_roof_acq_s(terms, 0) / 2
-    return {"workload": f"{CV_PRODUCERS} producer + {CV_CONSUMERS} consumer blocks x 128 threads, {CV_ITEMS} items "
-                        f"per producer, queue capacity {CV_CAPACITY}, one ticket mutex + two condition variables",
-            "ms": t, "items_per_s": items_s, "roof_items_per_s": roof, "frac": items_s / roof,
-            "parity": "ok" if ok else "FAILED"}
+    out = {"workload": f"{CV_PRODUCERS} producer + {CV_CONSUMERS} consumer blocks x 128 threads, {CV_ITEMS} items "
+                       f"per producer, queue capacity {CV_CAPACITY}, one mutex + two condition variables",
+           "roof_items_per_s": roof, "mutex": {}}
+    for mutex, bo in (("ticket", (64, 2000)), ("cohort", (128, 4000))):
+        run = runner.CondVarRun(CV_PRODUCERS, CV_CONSUMERS, CV_ITEMS, CV_CAPACITY, value,
+                                bo=runner.backoff(min_ns=bo[0], max_ns=bo[1]), mutex=mutex)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms, ok = [], True
+        for _ in range(4):
+            run.reset()
+            s.record()
+            rc = run.launch()
+            e.record()
+            torch.cuda.synchronize()
+            st = int(run.status.cpu()[0])
+            seen = run.seen.cpu().numpy().view(np.uint32)
+            ok = ok and rc == 0 and st == 0 and np.array_equal(seen, want["seen"]) and \
+                int(run.sum.sum().item()) == want["total"]
+            ms.append(s.elapsed_time(e))
+        t = float(np.median(ms[1:]))
+        items_s = n / (t * 1e-3)
+        out["mutex"][mutex] = {"ms": t, "items_per_s": items_s, "frac": items_s / roof,
+                               "parity": "ok" if ok else "FAILED"}
+    return out
 
 
 def serve_section(calc, inputs, runner):

@@ -291,7 +291,8 @@ typedef struct gsync_sem_work {
 int gsync_bench_sem(void* state, const gsync_sem_work* w, void* stream);
 
 /* Condition-variable workload: a bounded buffer (producer/consumer queue) of `capacity` item
- * ids guarded by one TICKET mutex and two condition variables (not_full, not_empty).  Blocks
+ * ids guarded by one mutex (TICKET or COHORT) and two condition variables (not_full,
+ * not_empty).  Blocks
  * 0 .. producers-1 each put items_per_producer items (item id = block * items_per_producer +
  * i); the next `consumers` blocks each take producers * items_per_producer / consumers items
  * (which must divide exactly).  A producer waits on not_full while the buffer is full and
@@ -304,7 +305,8 @@ int gsync_bench_sem(void* state, const gsync_sem_work* w, void* stream);
  * may be NULL) sets the waiters' sleep; one co-resident launch of producers + consumers
  * blocks; GSYNC_ENOTRESIDENT if it does not fit.  status bits as for the other workloads. */
 typedef struct gsync_condvar_work {
-  int32_t producers, consumers, items_per_producer, capacity, block_threads, reserved;
+  int32_t producers, consumers, items_per_producer, capacity, block_threads;
+  int32_t mutex_kind; /* the queue's mutex: GSYNC_MUTEX_TICKET or GSYNC_MUTEX_COHORT */
   const uint32_t* value;
   uint32_t* seen;
   int64_t* sum;

@@ -1,5 +1,5 @@
 // Condition-variable workload: a bounded producer/consumer queue of item ids under one
-// TICKET mutex and two condition variables (condition variables are named as future work in
+// mutex (TICKET or COHORT) and two condition variables (condition variables are named as future work in
 // Section 7; the design is in gsync_device.cuh).  Each item id is put once and must be taken
 // exactly once: seen[] counts takes, and the consumers' int64 sums must add up to the sum of
 // the items' values.
@@ -17,6 +17,7 @@ struct Queue {
   uint32_t count, head, tail, capacity;
 };
 
+template <int MKIND>
 __global__ void __launch_bounds__(kMaxThreads)
     condvar_workload_kernel(uint32_t* mutex_state, uint32_t* nf_state, uint32_t* ne_state, Queue* q, uint32_t* buf,
                             int producers, int items_per_producer, int items_per_consumer,
@@ -32,7 +33,7 @@ __global__ void __launch_bounds__(kMaxThreads)
   int64_t my_sum = 0;
   uint32_t taken = 0;
   for (int i = 0; i < ops; ++i) {
-    gsync::Token tok = gsync::mutex_lock<GSYNC_MUTEX_TICKET>(m);
+    gsync::Token tok = gsync::mutex_lock<MKIND>(m);
     if (tok.status != GSYNC_OK) {
       if (t0) record_status(status, tok.status);
       break;
@@ -46,7 +47,7 @@ __global__ void __launch_bounds__(kMaxThreads)
       }
       __syncthreads();
       if (s_ok) break;
-      rc = gsync::cond_wait<GSYNC_MUTEX_TICKET>(producer ? not_full : not_empty, m, tok);
+      rc = gsync::cond_wait<MKIND>(producer ? not_full : not_empty, m, tok);
       if (rc != GSYNC_OK) break;
     }
     if (rc != GSYNC_OK) {
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(kMaxThreads)
         gsync::cond_signal_thread(not_full);
       }
     }
-    gsync::mutex_unlock<GSYNC_MUTEX_TICKET>(m, tok);
+    gsync::mutex_unlock<MKIND>(m, tok);
     if (!producer && t0) {
       const uint32_t id = s_id;
       if (id < (uint32_t)(producers * items_per_producer)) {
@@ -90,10 +91,16 @@ size_t round_up(size_t n) { return (n + 255) & ~(size_t)255; }
 
 }  // namespace
 
+// The mutex sits first in the workspace and takes the larger of the two kinds' sizes.
+size_t mutex_region() {
+  const size_t a = gsync_mutex_bytes(GSYNC_MUTEX_TICKET, 1), b = gsync_mutex_bytes(GSYNC_MUTEX_COHORT, 1);
+  return round_up(a > b ? a : b);
+}
+
 extern "C" size_t gsync_bench_condvar_workspace_bytes(int capacity) {
   if (capacity < 1 || capacity > (1 << 24)) return 0;
-  return round_up(gsync_mutex_bytes(GSYNC_MUTEX_TICKET, 1)) + 2 * round_up(gsync_cond_bytes()) +
-         round_up(sizeof(Queue)) + round_up(4 * (size_t)capacity);
+  return mutex_region() + 2 * round_up(gsync_cond_bytes()) + round_up(sizeof(Queue)) +
+         round_up(4 * (size_t)capacity);
 }
 
 extern "C" int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_backoff* backoff, void* workspace,
@@ -104,18 +111,19 @@ extern "C" int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_back
   const int64_t items = (int64_t)w->producers * w->items_per_producer;
   if (items > (1ll << 30) || items % w->consumers) return GSYNC_EINVAL;
   if (!w->value || !w->seen || !w->sum || !w->count || !w->status) return GSYNC_EINVAL;
+  if (w->mutex_kind != GSYNC_MUTEX_TICKET && w->mutex_kind != GSYNC_MUTEX_COHORT) return GSYNC_EINVAL;
   const size_t need = gsync_bench_condvar_workspace_bytes(w->capacity);
   if (need == 0 || !workspace || workspace_bytes < need || !aligned(workspace, 256)) return GSYNC_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   char* p = (char*)workspace;
-  uint32_t* mstate = (uint32_t*)p;  p += round_up(gsync_mutex_bytes(GSYNC_MUTEX_TICKET, 1));
+  uint32_t* mstate = (uint32_t*)p;  p += mutex_region();
   uint32_t* nf = (uint32_t*)p;      p += round_up(gsync_cond_bytes());
   uint32_t* ne = (uint32_t*)p;      p += round_up(gsync_cond_bytes());
   Queue* q = (Queue*)p;             p += round_up(sizeof(Queue));
   uint32_t* buf = (uint32_t*)p;
   const uint64_t timeout_ns = 10000000000ull;
-  if (int rc = gsync_mutex_init(mstate, gsync_mutex_bytes(GSYNC_MUTEX_TICKET, 1), GSYNC_MUTEX_TICKET, 1, backoff,
-                                timeout_ns, stream))
+  if (int rc = gsync_mutex_init(mstate, gsync_mutex_bytes(w->mutex_kind, 1), w->mutex_kind, 1, backoff, timeout_ns,
+                                stream))
     return rc;
   if (int rc = gsync_cond_init(nf, gsync_cond_bytes(), backoff, timeout_ns, stream)) return rc;
   if (int rc = gsync_cond_init(ne, gsync_cond_bytes(), backoff, timeout_ns, stream)) return rc;
@@ -123,7 +131,9 @@ extern "C" int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_back
   GSYNC_CUDA(cudaMemcpyAsync(q, &q0, sizeof q0, cudaMemcpyHostToDevice, st));
   GSYNC_CUDA(cudaStreamSynchronize(st));  // q0 lives on this stack frame
   const int items_per_consumer = (int)(items / w->consumers);
-  return launch_coresident(condvar_workload_kernel, w->producers + w->consumers, w->block_threads, 1, 0, st, mstate, nf,
-                           ne, q, buf, w->producers, w->items_per_producer, items_per_consumer, w->value, w->seen,
-                           w->sum, w->count, w->status);
+  auto kernel = w->mutex_kind == GSYNC_MUTEX_COHORT ? condvar_workload_kernel<GSYNC_MUTEX_COHORT>
+                                                    : condvar_workload_kernel<GSYNC_MUTEX_TICKET>;
+  return launch_coresident(kernel, w->producers + w->consumers, w->block_threads, 1, 0, st, mstate, nf, ne, q, buf,
+                           w->producers, w->items_per_producer, items_per_consumer, w->value, w->seen, w->sum,
+                           w->count, w->status);
 }

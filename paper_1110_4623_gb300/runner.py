@@ -156,7 +156,8 @@ class CondVarRun:
     queue under one mutex and two condition variables."""
 
     def __init__(self, producers: int, consumers: int, items_per_producer: int, capacity: int,
-                 value: np.ndarray, block_threads: int = 128, bo: G.gsync_backoff | None = None):
+                 value: np.ndarray, block_threads: int = 128, bo: G.gsync_backoff | None = None,
+                 mutex: str = "ticket"):
         n = producers * items_per_producer
         self.producers, self.consumers, self.n, self.bo = producers, consumers, n, bo
         self.value = _u32(value) if n else _zeros(1)
@@ -166,7 +167,8 @@ class CondVarRun:
         self.status = _zeros(1)
         self.nbytes = G.gsync_bench_condvar_workspace_bytes(capacity)
         self.ws = _state(self.nbytes)
-        self.work = G.gsync_condvar_work(producers, consumers, items_per_producer, capacity, block_threads, 0,
+        self.work = G.gsync_condvar_work(producers, consumers, items_per_producer, capacity, block_threads,
+                                         G.MUTEX_KINDS[mutex],
                                          G.ptr(self.value), G.ptr(self.seen), G.ptr(self.sum), G.ptr(self.count),
                                          G.ptr(self.status))
 

@@ -16,11 +16,12 @@ def _gpu():
     require_gpu()
 
 
-def check(producers, consumers, items, capacity, threads=128, bo=None):
+def check(producers, consumers, items, capacity, threads=128, bo=None, mutex="ticket"):
     from paper_1110_4623_gb300 import runner
     n = producers * items
     value = inputs.condvar_inputs(n, inputs.SEED_CONDVAR ^ producers ^ (consumers << 12) ^ (capacity << 24))
-    got = runner.CondVarRun(producers, consumers, items, capacity, value, block_threads=threads, bo=bo).run()
+    got = runner.CondVarRun(producers, consumers, items, capacity, value, block_threads=threads, bo=bo,
+                            mutex=mutex).run()
     want = calc.condvar_final(value, producers, items, consumers)
     assert got["rc"] == 0 and got["status"] == 0, got["status"]
     assert np.array_equal(got["seen"], want["seen"]), int((got["seen"] != 1).sum())
@@ -33,6 +34,19 @@ def check(producers, consumers, items, capacity, threads=128, bo=None):
     (592, 592, 100, 16), (592, 592, 100, 1), (1000, 184, 92, 64)])
 def test_producer_consumer_exactly_once(producers, consumers, items, capacity):
     check(producers, consumers, items, capacity)
+
+
+@pytest.mark.parametrize("producers,consumers,items,capacity", [(1, 1, 100, 1), (592, 592, 100, 16), (16, 4, 20, 3)])
+def test_producer_consumer_on_the_cohort_lock(producers, consumers, items, capacity):
+    from paper_1110_4623_gb300 import runner
+    check(producers, consumers, items, capacity, mutex="cohort", bo=runner.backoff(min_ns=128, max_ns=4000))
+
+
+def test_other_mutex_kinds_are_refused():
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    r = runner.CondVarRun(2, 2, 4, 4, np.zeros(8, np.uint32), mutex="cas_spin")
+    assert r.launch() == G.GSYNC_EINVAL
 
 
 def test_sleeping_waiters_and_ragged_threads():
