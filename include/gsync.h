@@ -182,6 +182,25 @@ int gsync_object_abort_flag(const void* state, uint32_t* flag_out, void* stream)
 int gsync_max_coresident_blocks(int workload, int kind, int block_threads, int cluster,
                                 int* max_blocks_out);
 
+/* The same gate for the caller's own kernels (the ones that call barrier_wait and the other
+ * device primitives of gsync_device.cuh).  `kernel` is the kernel's cudaFunction_t handle,
+ * from cudaGetFuncBySymbol(&f, (const void*)my_kernel) in the caller's program (a host-stub
+ * pointer would be unknown to the library's own CUDA runtime); smem_bytes its dynamic shared
+ * memory (over 48 KB the caller sets the kernel's attribute first); cluster its blocks per
+ * cluster (1 = no clusters).  Driver calls are made through cudaGetDriverEntryPointByVersion;
+ * GSYNC_ECUDA if the driver lacks them, GSYNC_EINVAL if the handle is not a kernel.
+ * gsync_check_coresident: *max_blocks_out = the largest co-resident grid; returns GSYNC_OK,
+ *   or GSYNC_ENOTRESIDENT when grid exceeds it.
+ * gsync_launch_coresident: launches the kernel on grid x block_threads (1-D), smem_bytes and
+ *   `stream`, with args (an array of pointers to the arguments, as for cudaLaunchKernel), so
+ *   that every block
+ *   is resident at once (a cooperative launch; an occupancy-checked cluster launch when
+ *   cluster > 1), or refuses with GSYNC_ENOTRESIDENT before anything runs.  Asynchronous. */
+int gsync_check_coresident(const void* kernel, int grid, int block_threads, size_t smem_bytes,
+                           int cluster, int* max_blocks_out);
+int gsync_launch_coresident(const void* kernel, int grid, int block_threads, size_t smem_bytes,
+                            int cluster, void** args, void* stream);
+
 /* Number of SMs of the current device. */
 int gsync_device_sm_count(int* sms_out);
 

@@ -2,8 +2,11 @@
 // Algorithm 1 ("CreateSpinLock") allocates one word on the GPU and zeroes it from the CPU;
 // here the caller owns the memory and gsync_*_init writes each object's initial state with
 // one small kernel on the caller's stream.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <string.h>
+
+#include <mutex>
 
 #include "common.cuh"
 
@@ -13,6 +16,43 @@ thread_local int g_last_cuda_error = 0;
 using namespace gsync_impl;
 
 namespace {
+
+// Driver calls for kernels owned by the caller: a kernel handle (CUfunction, which the
+// caller gets from cudaGetFuncBySymbol) is valid in any runtime instance of the process,
+// while a host-stub pointer is only known to the runtime that registered it.
+struct DriverCalls {
+  CUresult (*occ_blocks)(int*, CUfunction, int, size_t);
+  CUresult (*occ_clusters)(int*, CUfunction, const CUlaunchConfig*);
+  CUresult (*launch)(const CUlaunchConfig*, CUfunction, void**, void**);
+};
+
+int driver_calls(const DriverCalls** out) {
+  static DriverCalls calls;
+  static int status = -1;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> g(mu);
+  if (status < 0) {
+    void *a = nullptr, *b = nullptr, *c = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb, qc;
+    const bool ok =
+        cudaGetDriverEntryPointByVersion("cuOccupancyMaxActiveBlocksPerMultiprocessor", &a, 12000, cudaEnableDefault,
+                                         &qa) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuOccupancyMaxActiveClusters", &b, 12000, cudaEnableDefault, &qb) ==
+            cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuLaunchKernelEx", &c, 12000, cudaEnableDefault, &qc) == cudaSuccess &&
+        qa == cudaDriverEntryPointSuccess && qb == cudaDriverEntryPointSuccess && qc == cudaDriverEntryPointSuccess;
+    if (ok) {
+      calls.occ_blocks = (CUresult(*)(int*, CUfunction, int, size_t))a;
+      calls.occ_clusters = (CUresult(*)(int*, CUfunction, const CUlaunchConfig*))b;
+      calls.launch = (CUresult(*)(const CUlaunchConfig*, CUfunction, void**, void**))c;
+    }
+    (void)cudaGetLastError();
+    status = ok ? 1 : 0;
+  }
+  if (!status) return GSYNC_ECUDA;
+  *out = &calls;
+  return GSYNC_OK;
+}
 
 constexpr uint32_t kLine = 128;
 constexpr uint32_t kMagic = 0x6B5C0000u;
@@ -277,6 +317,77 @@ int gsync_object_abort_flag(const void* state, uint32_t* flag_out, void* stream)
   cudaStream_t st = (cudaStream_t)stream;
   GSYNC_CUDA(cudaMemcpyAsync(flag_out, (const uint32_t*)state + gsync::kHdrAbort, 4, cudaMemcpyDeviceToHost, st));
   GSYNC_CUDA(cudaStreamSynchronize(st));
+  return GSYNC_OK;
+}
+
+int gsync_check_coresident(const void* kernel, int grid, int block_threads, size_t smem_bytes, int cluster,
+                           int* max_blocks_out) {
+  if (!kernel || !max_blocks_out || grid < 1 || block_threads < 1 || block_threads > 1024 || cluster < 1 ||
+      cluster > 16)
+    return GSYNC_EINVAL;
+  const DriverCalls* d = nullptr;
+  if (int rc = driver_calls(&d)) return rc;
+  CUfunction f = (CUfunction)kernel;
+  int maxb = 0;
+  if (cluster > 1) {
+    CUlaunchAttribute attr[1];
+    attr[0].id = CU_LAUNCH_ATTRIBUTE_CLUSTER_DIMENSION;
+    attr[0].value.clusterDim.x = (unsigned)cluster;
+    attr[0].value.clusterDim.y = 1;
+    attr[0].value.clusterDim.z = 1;
+    CUlaunchConfig cfg = {};
+    cfg.gridDimX = (unsigned)cluster;
+    cfg.gridDimY = cfg.gridDimZ = 1;
+    cfg.blockDimX = (unsigned)block_threads;
+    cfg.blockDimY = cfg.blockDimZ = 1;
+    cfg.sharedMemBytes = (unsigned)smem_bytes;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (d->occ_clusters(&clusters, f, &cfg) != CUDA_SUCCESS) return GSYNC_EINVAL;
+    maxb = clusters * cluster;
+  } else {
+    int per_sm = 0, sms = 0;
+    if (d->occ_blocks(&per_sm, f, block_threads, smem_bytes) != CUDA_SUCCESS) return GSYNC_EINVAL;
+    if (int rc = device_sms(&sms)) return rc;
+    maxb = per_sm * sms;
+  }
+  *max_blocks_out = maxb;
+  return grid <= maxb ? GSYNC_OK : GSYNC_ENOTRESIDENT;
+}
+
+int gsync_launch_coresident(const void* kernel, int grid, int block_threads, size_t smem_bytes, int cluster,
+                            void** args, void* stream) {
+  int maxb = 0;
+  if (int rc = gsync_check_coresident(kernel, grid, block_threads, smem_bytes, cluster, &maxb)) return rc;
+  if (cluster > 1 && grid % cluster) return GSYNC_EINVAL;
+  const DriverCalls* d = nullptr;
+  if (int rc = driver_calls(&d)) return rc;
+  CUlaunchAttribute attr[1];
+  if (cluster > 1) {
+    attr[0].id = CU_LAUNCH_ATTRIBUTE_CLUSTER_DIMENSION;
+    attr[0].value.clusterDim.x = (unsigned)cluster;
+    attr[0].value.clusterDim.y = 1;
+    attr[0].value.clusterDim.z = 1;
+  } else {
+    attr[0].id = CU_LAUNCH_ATTRIBUTE_COOPERATIVE;
+    attr[0].value.cooperative = 1;
+  }
+  CUlaunchConfig cfg = {};
+  cfg.gridDimX = (unsigned)grid;
+  cfg.gridDimY = cfg.gridDimZ = 1;
+  cfg.blockDimX = (unsigned)block_threads;
+  cfg.blockDimY = cfg.blockDimZ = 1;
+  cfg.sharedMemBytes = (unsigned)smem_bytes;
+  cfg.hStream = (CUstream)stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const CUresult r = d->launch(&cfg, (CUfunction)kernel, args, nullptr);
+  if (r == CUDA_ERROR_COOPERATIVE_LAUNCH_TOO_LARGE) return GSYNC_ENOTRESIDENT;
+  if (r != CUDA_SUCCESS) {
+    g_last_cuda_error = (int)r;
+    return GSYNC_ECUDA;
+  }
   return GSYNC_OK;
 }
 

@@ -100,6 +100,10 @@ _SIG = {
     "gsync_mutex_init_cohort": (ctypes.c_int, [u32p, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(gsync_backoff),
                                                ctypes.c_uint64, u32p]),
     "gsync_device_topology": (ctypes.c_int, [u32p, ctypes.POINTER(ctypes.c_int), u32p]),
+    "gsync_check_coresident": (ctypes.c_int, [u32p, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_int)]),
+    "gsync_launch_coresident": (ctypes.c_int, [u32p, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_int, u32p,
+                                               u32p]),
     "gsync_cond_bytes": (ctypes.c_size_t, []),
     "gsync_cond_init": (ctypes.c_int, [u32p, ctypes.c_size_t, ctypes.POINTER(gsync_backoff), ctypes.c_uint64, u32p]),
     "gsync_bench_condvar_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int]),

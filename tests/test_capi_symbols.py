@@ -87,6 +87,7 @@ def test_size_queries_without_gpu(lib_path):
 
 
 def test_invalid_arguments_rejected_without_gpu(lib_path):
+    import ctypes
     from paper_1110_4623_gb300 import gsync as G
     # Null / misaligned state is rejected before any CUDA call.
     assert G.lib().gsync_mutex_init(None, 384, 0, 4, None, 0, None) == G.GSYNC_EINVAL
@@ -96,6 +97,12 @@ def test_invalid_arguments_rejected_without_gpu(lib_path):
     assert G.lib().gsync_mutex_init_cohort(256, 32768, 32768, None, 0, None) == G.GSYNC_EINVAL
     assert G.lib().gsync_mutex_init_cohort(256, 4096, 64, None, 0, None) == G.GSYNC_EINVAL
     assert G.lib().gsync_device_topology(None, None, None) == G.GSYNC_EINVAL
+    # the caller-kernel gate rejects a null kernel or a bad shape before any CUDA call
+    lib = G.lib()
+    n = ctypes.c_int(0)
+    assert lib.gsync_check_coresident(None, 1, 128, 0, 1, ctypes.byref(n)) == G.GSYNC_EINVAL
+    assert lib.gsync_check_coresident(8, 0, 128, 0, 1, ctypes.byref(n)) == G.GSYNC_EINVAL
+    assert lib.gsync_check_coresident(8, 1, 128, 0, 17, ctypes.byref(n)) == G.GSYNC_EINVAL
     # backoff policies 0..2 only (checked before any CUDA call)
     import ctypes
     bad = G.gsync_backoff(3, 16, 512, 0)
