@@ -49,6 +49,12 @@ def _batched(nacq=200_000, rounds=20):
     return lambda: G.check("gsync_bench_batched", r.launch())
 
 
+def _condvar(mutex="cohort", items=20):
+    v = inputs.condvar_inputs(592 * items)
+    r = runner.CondVarRun(592, 592, items, 16, v, bo=runner.backoff(min_ns=128, max_ns=4000), mutex=mutex)
+    return lambda: G.check("gsync_bench_condvar", r.launch())
+
+
 CASES = {
     "mutex_sleep_queue": lambda: _mutex("sleep_queue", 64),
     "mutex_ticket": lambda: _mutex("ticket", 64),
@@ -61,6 +67,7 @@ CASES = {
     "barrier_count8": lambda: _barrier("count", 8),
     "sem_ticket_n4": lambda: _sem(4),
     "batched_200k": lambda: _batched(),
+    "condvar_cohort": lambda: _condvar(),
 }
 
 
