@@ -36,7 +36,8 @@ def _barrier(kind, param, rounds=200):
 
 def _sem(n, pairs=20):
     hold, add = inputs.sem_inputs(NB, pairs, inputs.SEED_SEM ^ (n << 16) ^ NB)
-    r = runner.SemRun("ticket", NB, 128, pairs, n, hold, add, timeout_ns=10_000_000_000)
+    r = runner.SemRun("ticket", NB, 128, pairs, n, hold, add, bo=runner.backoff(min_ns=16, max_ns=2000),
+                      timeout_ns=10_000_000_000)
     return lambda: G.check("gsync_bench_sem", r.launch())
 
 
