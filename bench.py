@@ -505,6 +505,28 @@ def cpu_baseline(inputs, kind):
                       f"blocks round-robin on {threads} threads"}
 
 
+# The paper's own figures (context only, other hardware): same-word atomic throughput from
+# Table 1 (1000 contentious atomics per block on a saturated GPU: Tesla GTX295, 240 blocks,
+# 78.4 ms; Fermi GTX580, 128 blocks, 1.47 ms) and the relative results of Section 6.
+PAPER_CONTEXT = {
+    "same_word_atomics_per_s": {"tesla_gtx295": 240_000 / 78.407e-3, "fermi_gtx580": 128_000 / 1.479e-3},
+    "atomic_barrier_vs_xf": {"tesla_gtx295": "< 0.05 at 60 blocks", "fermi_gtx580": "~0.30 at 128 blocks"},
+    "fa_mutex_vs_spin_backoff": {"tesla_gtx295": "> 20 (spin+backoff < 5 % of FA)", "fermi_gtx580": "~0.5"},
+}
+
+
+def paper_context(terms, barrier, mutex):
+    """The paper's figures beside the same quantities measured on this GPU in this run."""
+    return {"paper": PAPER_CONTEXT,
+            "gb300": {"same_word_atomics_per_s": terms["R_same_atom_ops_s"],
+                      "atomic_barrier_vs_xf": barrier["flag"]["ns_per_crossing"] / barrier["atomic"]["ns_per_crossing"],
+                      "fa_mutex_vs_spin_backoff": float(np.mean([mutex["ticket"][k]["acq_per_s"] /
+                                                                 mutex["cas_backoff"][k]["acq_per_s"]
+                                                                 for k in mutex["ticket"]]))},
+            "note": "speed ratios (higher = the first design is faster); the paper's figures are for its "
+                    "hardware, quoted as context, not targets"}
+
+
 def run_gpu(args):
     import torch
     from oracle import calc
@@ -605,6 +627,7 @@ def run_gpu(args):
         "semaphore": {"kind": "ticket", "backoff_ns": list(SEM_BACKOFF), "n": sem},
         "roofline_terms": terms,
         "design_rule": design_rule,
+        "paper_context": paper_context(terms, barrier, mutex),
         "clocks": clk,
         "gpu_launches": step.launches * args.steps,
         "wall_s_timed_loop": wall,
