@@ -38,18 +38,19 @@ BAR_THREADS, BAR_ROUNDS = 128, 1000
 SEM_THREADS, SEM_PAIRS, SEM_COUNTS = 128, 200, (1, 4, 16, 64)
 # Library defaults for GB300, chosen from 1184-block sweeps (the paper's API serves the
 # fastest implementation of each primitive for the GPU as the default, Section 5 "API").
-DEFAULT_MUTEX = "cohort"
+DEFAULT_MUTEX = "cluster"
 DEFAULT_BARRIER = ("count", 8)
 BARRIERS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("cluster", 2), ("cluster", 4), ("cluster", 8),
             ("sharded", 32), ("sharded", 8), ("die", 0), ("die", 1), ("split", 16 | 16 << 8), ("count", 0), ("count", 8)]
 # Backoff (min_ns, max_ns) per kind; the ticket kinds sleep min_ns per waiter ahead, capped.
-MUTEX_BACKOFF = {"cas_backoff": (16, 512), "ticket": (128, 4000), "cohort": (128, 4000)}
+MUTEX_BACKOFF = {"cas_backoff": (16, 512), "ticket": (128, 4000), "cohort": (128, 4000), "cluster": (128, 4000)}
+MUTEX_CLUSTER = 4  # blocks per cluster of the cluster cohort lock (a sweep of 2 / 4 / 8 picked 4)
 # The measured mutex configurations: (name, kind, backoff policy, (min_ns, max_ns), spin).
 # cas_spin_then_sleep is Section 5's futex stand-in: the CAS lock spins, then backs off.
 MUTEX_CONFIGS = [("cas_spin", "cas_spin", 0, None, 0), ("cas_backoff", "cas_backoff", 0, (16, 512), 0),
                  ("cas_spin_then_sleep", "cas_backoff", 2, (16, 512), 32), ("ticket", "ticket", 0, (128, 4000), 0),
                  ("sleep_queue", "sleep_queue", 0, None, 0), ("ring", "ring", 0, None, 0),
-                 ("cohort", "cohort", 0, (128, 4000), 0)]
+                 ("cohort", "cohort", 0, (128, 4000), 0), ("cluster", "cluster", 0, (128, 4000), 0)]
 SEM_BACKOFF = (16, 2000)
 # Batched many-mutex workload: 4096 keys, Zipf(1.1), 1e6 acquisitions, 64 barrier groups.
 BATCH_KEYS, BATCH_ACQ, BATCH_GROUPS, BATCH_ROUNDS, BATCH_THREADS = 4096, 1_000_000, 64, 100, 128
@@ -169,6 +170,9 @@ def measure_roofline_terms(runner, inputs):
     # on that die.  Five fixed pairs on lines homed wherever are reported beside it.
     near = [runner.near_handoff(4000) for _ in range(3)]
     near_ns = [h["handoff_ns"] for h in near if h["status"] == 0]
+    # ... or inside a thread-block cluster, through distributed shared memory
+    dsm = [runner.probe_cluster(1, 2, 4000) for _ in range(3)]
+    dsm_ns = [h["ns"] for h in dsm if h["status"] == 0]
     pairs = [(0, 1), (0, sms // 2), (0, sms - 1), (sms // 4, 3 * sms // 4), (2, sms - 3)]
     hand = [runner.probe_pingpong(a, b, 4000) for a, b in pairs if a != b and 0 <= a < sms and 0 <= b < sms]
     hand_ns = [h["handoff_ns"] for h in hand if h["status"] == 0]
@@ -186,7 +190,9 @@ def measure_roofline_terms(runner, inputs):
     T_frame = float(np.median([runner.probe_cs(-1, MUTEX_THREADS, 20000)["ns_per_cs"] for _ in range(3)]))
     T_frame_sem = float(np.median([runner.probe_sem_cs(None, None, SEM_THREADS, iters=4000)["ns_per_cs"]
                                    for _ in range(3)]))
-    return {"sms": sms, "L_handoff_ns": float(np.median(near_ns)), "L_handoff_pairs_ns": hand_ns, "T_cs_ns": T_cs,
+    return {"sms": sms, "L_handoff_ns": float(min(np.median(near_ns), np.median(dsm_ns))),
+            "L_handoff_l2_near_ns": float(np.median(near_ns)), "L_handoff_dsmem_ns": float(np.median(dsm_ns)),
+            "L_handoff_pairs_ns": hand_ns, "T_cs_ns": T_cs,
             "T_frame_ns": T_frame, "T_cs_sem_ns": T_cs_sem, "T_frame_sem_ns": T_frame_sem,
             "R_same_red_ops_s": float(np.median(rs)), "R_same_atom_ops_s": float(np.median(ra)), "L_rt_ns": L_rt}
 
@@ -194,7 +200,7 @@ def measure_roofline_terms(runner, inputs):
 def merge_terms(a, b):
     """The stricter roof of two measurements: lower latencies, higher throughputs."""
     out = dict(a)
-    for k in ("L_handoff_ns", "L_rt_ns"):
+    for k in ("L_handoff_ns", "L_handoff_l2_near_ns", "L_handoff_dsmem_ns", "L_rt_ns"):
         out[k] = min(a[k], b[k])
     for k in ("R_same_red_ops_s", "R_same_atom_ops_s"):
         out[k] = max(a[k], b[k])
@@ -219,7 +225,7 @@ def mutex_roof_acq_s(terms, K):
 def sem_roof_ops_s(terms, n):
     """Under capacity a wait is one atomic; at capacity n holders each hand off per op."""
     return min(terms["R_same_atom_ops_s"],
-               n * 1e9 / (terms["L_handoff_ns"] + max(terms["T_body_sem_ns"][n], 0.0)))
+               n * 1e9 / (terms["L_handoff_l2_near_ns"] + max(terms["T_body_sem_ns"][n], 0.0)))
 
 
 def barrier_roof_ns(terms, kind, param, B):
@@ -239,7 +245,8 @@ def barrier_roof_ns(terms, kind, param, B):
         b_eff, rts = B, 0  # the last arrival is the release: no round trip back to it
     else:
         b_eff = B
-    return rts * terms["L_rt_ns"] + terms["L_handoff_ns"] + b_eff / terms["R_same_atom_ops_s"] * 1e9
+    # a grid-wide release reaches every block through L2: the on-die L2 hand-off bounds it
+    return rts * terms["L_rt_ns"] + terms["L_handoff_l2_near_ns"] + b_eff / terms["R_same_atom_ops_s"] * 1e9
 
 
 # ------------------------------------------------------------------------------------------
@@ -257,7 +264,7 @@ class GpuStep:
                 delay, add = inputs.mutex_inputs(NBLOCKS, MUTEX_ACQ, inputs.mutex_seed(G.MUTEX_KINDS[kind], NBLOCKS, K))
                 bo = runner.backoff(policy=policy, min_ns=bo_ns[0], max_ns=bo_ns[1], spin=spin) if bo_ns else None
                 self.mutex[(name, K)] = (runner.MutexRun(kind, NBLOCKS, MUTEX_THREADS, MUTEX_ACQ, K, delay, add, bo=bo,
-                                                         timeout_ns=TIMEOUT_NS), add)
+                                                         timeout_ns=TIMEOUT_NS, cluster=MUTEX_CLUSTER), add)
         self.barrier = {(k, p): runner.BarrierRun(k, NBLOCKS, BAR_THREADS, BAR_ROUNDS, full=False, param=p,
                                                   timeout_ns=TIMEOUT_NS) for k, p in BARRIERS}
         self.sem = {}
@@ -340,7 +347,8 @@ def e2e_mutex(G, inputs, kind, reps=3):
         outs = {nm: torch.zeros(sz, dtype=torch.int32).pin_memory()
                 for nm, sz in (("data", max(K, 1)), ("total", 1), ("log", n), ("ticket", n), ("count", NBLOCKS),
                                ("status", 1))}
-        w = G.gsync_mutex_work(G.MUTEX_KINDS[kind], NBLOCKS, MUTEX_THREADS, MUTEX_ACQ, K, 0, hd.data_ptr(),
+        w = G.gsync_mutex_work(G.MUTEX_KINDS[kind], NBLOCKS, MUTEX_THREADS, MUTEX_ACQ, K,
+                               MUTEX_CLUSTER if kind == "cluster" else 0, hd.data_ptr(),
                                ha.data_ptr(), outs["data"].data_ptr(), outs["total"].data_ptr(),
                                outs["log"].data_ptr(), outs["ticket"].data_ptr(), outs["count"].data_ptr(),
                                outs["status"].data_ptr())
@@ -608,7 +616,8 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "acq/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded SplitMix64 delays/addends/hold times)",
-        "config": {"workload": f"mutex contention, {NBLOCKS} blocks x {MUTEX_THREADS} threads, {MUTEX_ACQ} "
+        "config": {"workload": f"mutex contention, {NBLOCKS} blocks x {MUTEX_THREADS} threads"
+                               f"{f' in clusters of {MUTEX_CLUSTER}' if DEFAULT_MUTEX == 'cluster' else ''}, {MUTEX_ACQ} "
                                f"acquisitions/block, CS {list(CS_SIZES)} int32 words, delays U{{0..2000}} cycles; "
                                f"+ barriers ({BAR_ROUNDS} rounds) and semaphores ({SEM_PAIRS} pairs) at {NBLOCKS} blocks",
                    "default_mutex": f"{DEFAULT_MUTEX} (backoff {MUTEX_BACKOFF.get(DEFAULT_MUTEX)} ns)",
@@ -618,9 +627,11 @@ def run_gpu(args):
                      "frac": (value / world) / peak, "traffic": ROOF_TRAFFIC,
                      "traffic_note": ROOF_TRAFFIC_NOTE,
                      "peak_source": "measured live: sum over CS sizes of 1e9 / (L_handoff + T_body(K)); L_handoff "
-                                    "= ping-pong of two SMs of one die on lines homed on that die (the shortest "
-                                    "hand-off), T_body = critical-section probe minus its frame; min with R_same/2; "
-                                    "MEASURED_PEAKS.json's HBM and bf16 peaks do not bound this path"},
+                                    "= the shortest hand-off the GPU offers: min of a ping-pong of two SMs of one "
+                                    "die on lines homed on that die and a ping-pong inside a thread-block cluster "
+                                    "through distributed shared memory; T_body = critical-section probe minus its "
+                                    "frame; min with R_same/2; MEASURED_PEAKS.json's HBM and bf16 peaks do not "
+                                    "bound this path"},
         "barrier": {"default": bkey, "ns_per_crossing": barrier[bkey]["ns_per_crossing"],
                     "frac": barrier[bkey]["frac"], "kinds": barrier},
         "mutex": mutex,

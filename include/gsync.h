@@ -58,9 +58,12 @@ typedef enum gsync_mutex_kind {
   GSYNC_MUTEX_COHORT = 4,      /* two-die cohort lock: a ticket lock per die (homed on that
                                   die) under a global ticket lock; hand-offs stay on a die
                                   for up to `budget` acquisitions in a row */
-  GSYNC_MUTEX_RING = 5         /* the paper's ring-buffer sleeping mutex (Section 5, design
+  GSYNC_MUTEX_RING = 5,        /* the paper's ring-buffer sleeping mutex (Section 5, design
                                   alternative): a waiter writes its block id at the ring's
                                   end and polls the head pointer and the entry it names */
+  GSYNC_MUTEX_CLUSTER = 6      /* cohort lock over thread-block clusters: a ticket lock per
+                                  cluster in distributed shared memory under a global ticket
+                                  lock; needs a cluster launch (see gsync_mutex_init_cluster) */
 } gsync_mutex_kind;
 
 /* Barrier kinds (Section 5, "Barrier"). */
@@ -124,10 +127,21 @@ int gsync_mutex_init(void* state, size_t bytes, int kind, int max_waiters,
  * per device and process: the gsync_probe_rtt_by_sm probe, ~3 ms) and the home die of the
  * state's 4 KB pages, then places each die's local lock on a page homed on that die;
  * synchronizes `stream`.  On a one-die GPU both local locks serve every SM.  state: device,
- * 128-byte aligned, bytes >= gsync_mutex_bytes(GSYNC_MUTEX_COHORT, 1). */
+ * 128-byte aligned, bytes >= gsync_mutex_bytes(GSYNC_MUTEX_COHORT, 1).  gsync_mutex_init with
+ * COHORT or CLUSTER uses GSYNC_COHORT_DEFAULT_BUDGET. */
 enum { GSYNC_COHORT_DEFAULT_BUDGET = 64 };
 int gsync_mutex_init_cohort(void* state, size_t bytes, int budget, const gsync_backoff* backoff,
                             uint64_t timeout_ns, void* stream);
+
+/* Cluster mutex (GSYNC_MUTEX_CLUSTER): the cohort protocol with the thread-block cluster as the
+ * group (a holder passes to a waiter of its own cluster through distributed shared memory, at
+ * most budget - 1 times in a row).  state holds only the global ticket lock (3 lines); each
+ * cluster's local lock is a gsync::ClusterLocal the kernel declares __shared__ and hands to
+ * gsync::mutex_attach_cluster at its start (all threads), and the kernel calls
+ * gsync::mutex_cluster_end() before exiting.  The kernel must be launched with clusters
+ * (gsync_launch_coresident with cluster > 1).  budget 1..32767; asynchronous on `stream`. */
+int gsync_mutex_init_cluster(void* state, size_t bytes, int budget, const gsync_backoff* backoff,
+                             uint64_t timeout_ns, void* stream);
 
 /* The device's SM-to-die map: die_of_sm (host, >= sm_count bytes) receives 0 or 1 per SM id
  * (die 0 = the SMs near a fixed line of the library's static memory), *ndies_out 1 or 2.
@@ -266,11 +280,14 @@ int gsync_bench_barrier_static(const gsync_barrier_work* w, int param, uint64_t 
  * grant_log[total] and increments total (plain load/store), records the lock ticket in
  * ticket[id] (0xFFFFFFFF for the CAS kinds), and its threads add addend[id] XOR
  * (i * 0x9E3779B1) to data[i] for every i < cs_words (plain loads/stores); then it unlocks.
- * count[b] receives the number of completed acquisitions.
+ * count[b] receives the number of completed acquisitions.  The per-group kinds record a
+ * ticket of their group's lock: COHORT as (die << 31) | ticket, CLUSTER as (cluster << 20) |
+ * ticket (ticket below 2^20).
  * Buffers (device): delay, addend, grant_log, ticket [nblocks*acq]; data [cs_words];
  * total [1]; count [nblocks]; status [1].  data, total and status must start at zero. */
 typedef struct gsync_mutex_work {
-  int32_t kind, nblocks, block_threads, acq, cs_words, reserved;
+  int32_t kind, nblocks, block_threads, acq, cs_words;
+  int32_t cluster; /* GSYNC_MUTEX_CLUSTER: blocks per cluster (2..8, divides nblocks); else 0 or 1 */
   const uint32_t* delay;
   const uint32_t* addend;
   uint32_t* data;

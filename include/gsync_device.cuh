@@ -169,6 +169,33 @@ __device__ __forceinline__ uint32_t cluster_nctarank() {
   asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
   return r;
 }
+// Generic address of the same shared-memory variable in cluster block `rank` (mapa).
+template <typename T>
+__device__ __forceinline__ T* map_cluster_rank(T* p, uint32_t rank) {
+  uint64_t r;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(r) : "l"((uint64_t)p), "r"(rank));
+  return (T*)r;
+}
+// Cluster-scope accesses through generic addresses (shared memory of any block of the
+// cluster, reached with mapa).
+__device__ __forceinline__ uint32_t atom_add_relaxed_cluster(uint32_t* p, uint32_t v) {
+  uint32_t r;
+  asm volatile("atom.relaxed.cluster.add.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
+  return r;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_cluster(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.cluster.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t ld_acquire_cluster_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.cluster.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_cluster_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.release.cluster.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 // Hardware barrier over every thread of every block of the cluster.  The non-.aligned
 // forms let threads of a warp arrive from divergent paths.
 __device__ __forceinline__ void cluster_sync() {
@@ -240,6 +267,16 @@ __device__ __forceinline__ uint64_t header_timeout(const uint32_t* s) {
 // COHORT: lines 3-4 the SM-to-die table; for each die d, at word offset kHdrDieOff<d> (on a
 //   4 KB page homed on die d), a local ticket counter line and a local turn line whose first
 //   8 bytes hold {served ticket (low 32), cohort word (high 32)}.
+// CLUSTER: the same protocol with the thread-block cluster as the group: lines 1-2 hold the
+//   global ticket lock and each cluster's local lock is a ClusterLocal in the shared memory
+//   of the cluster's block 0 (see mutex_attach_cluster).
+// The local lock of a CLUSTER mutex, declared __shared__ by the kernel.
+struct ClusterLocal {
+  uint32_t next;
+  uint32_t pad;
+  uint64_t turn;  // {served ticket (low 32), cohort word (high 32)}
+};
+
 struct MutexRef {
   uint32_t* s;
   uint32_t kind, qmask;
@@ -247,6 +284,7 @@ struct MutexRef {
   uint64_t timeout_ns;
   uint32_t* local;  // COHORT: this block's die's local lock (counter line, then turn line)
   uint32_t die;     // COHORT: the die of this block's SM (0 or 1)
+  ClusterLocal* cl; // CLUSTER: the cluster's local lock (in block 0's shared memory)
   __device__ __forceinline__ uint32_t* lockw() const { return s + 1 * kLineWords; }
   __device__ __forceinline__ uint32_t* turn() const { return s + 2 * kLineWords; }
   __device__ __forceinline__ uint32_t* flag(uint32_t t) const { return s + (3 + (t & qmask)) * kLineWords; }
@@ -267,6 +305,7 @@ __device__ __forceinline__ MutexRef mutex_attach(void* state) {
   m.bo.spin = m.s[kHdrSpin];
   m.timeout_ns = header_timeout(m.s);
   m.local = nullptr;
+  m.cl = nullptr;
   m.die = 0;
   if (m.kind == GSYNC_MUTEX_COHORT) {
     const uint32_t sm = ptx::smid();
@@ -276,6 +315,23 @@ __device__ __forceinline__ MutexRef mutex_attach(void* state) {
   }
   return m;
 }
+
+// CLUSTER mutex: every thread of every block of the (cluster-launched) grid calls this at the
+// kernel's start with the same __shared__ ClusterLocal; it initialises block 0's copy and
+// crosses the hardware cluster barrier, so the local lock is ready before anyone uses it.
+// The kernel must call mutex_cluster_end() before any of its blocks exits: block 0's shared
+// memory has to outlive the other blocks' last access to it.
+__device__ __forceinline__ MutexRef mutex_attach_cluster(void* state, ClusterLocal* local) {
+  MutexRef m = mutex_attach(state);
+  if (ptx::cluster_ctarank() == 0 && threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
+    local->next = 0;
+    local->turn = 0;
+  }
+  m.cl = ptx::map_cluster_rank(local, 0u);
+  ptx::cluster_sync();
+  return m;
+}
+__device__ __forceinline__ void mutex_cluster_end() { ptx::cluster_sync(); }
 
 // Result of a lock: the status, the ticket the holder needs to unlock, and (COHORT) the
 // cohort word -- passes within the die so far (bits 30..16) and the global ticket (15..0) --
@@ -354,6 +410,28 @@ __device__ __forceinline__ Token mutex_lock_thread(const MutexRef& m) {
       if (m.bo.min_ns) __nanosleep(m.bo.min_ns);
     }
     return {GSYNC_OK, t, g, ptx::ld_relaxed(m.local_next())};
+  } else if (KIND == GSYNC_MUTEX_CLUSTER) {
+    // The cohort protocol with the cluster as the group: the local ticket lock lives in the
+    // shared memory of the cluster's block 0 and is passed with cluster-scope release and
+    // acquire (distributed shared memory); the global ticket lock is passed between clusters.
+    const uint32_t t = ptx::atom_add_relaxed_cluster(&m.cl->next, 1u);
+    uint64_t v;
+    while ((uint32_t)(v = ptx::ld_acquire_cluster_u64(&m.cl->turn)) != t) {
+      if (int rc = w.tick(m.timeout_ns, m.abort_word())) return {rc, t, 0u};
+      const uint32_t ahead = t - (uint32_t)v;
+      if (m.bo.min_ns && ahead > 1u && ahead < 0x80000000u) {
+        const uint32_t ns = (ahead - 1u) * m.bo.min_ns;
+        __nanosleep(ns < m.bo.max_ns ? ns : m.bo.max_ns);
+      }
+    }
+    const uint32_t word = (uint32_t)(v >> 32);
+    if (word & kCohortOwned) return {GSYNC_OK, t, word & ~kCohortOwned, ptx::ld_relaxed_cluster(&m.cl->next)};
+    const uint32_t g = ptx::atom_add_relaxed(m.lockw(), 1u) & 0xFFFFu;
+    while ((ptx::ld_acquire(m.turn()) & 0xFFFFu) != g) {
+      if (int rc = w.tick(m.timeout_ns, m.abort_word())) return {rc, t, 0u};
+      if (m.bo.min_ns) __nanosleep(m.bo.min_ns);
+    }
+    return {GSYNC_OK, t, g, ptx::ld_relaxed_cluster(&m.cl->next)};
   } else if (KIND == GSYNC_MUTEX_RING) {
     // Ring-buffer sleeping mutex (Section 5, design alternative): claim the ring's end with a
     // fetch-and-add on the tail, write this block's id there, then poll the head pointer and
@@ -403,6 +481,18 @@ __device__ __forceinline__ void mutex_unlock_thread(const MutexRef& m, const Tok
       ptx::st_release(m.turn(), (g + 1u) & 0xFFFFu);
       ptx::st_release_u64(m.local_turn(), (uint64_t)(ticket + 1u));
     }
+  } else if (KIND == GSYNC_MUTEX_CLUSTER) {
+    const uint32_t passes = (tok.cohort >> 16) & 0x7FFFu, g = tok.cohort & 0xFFFFu;
+    const bool may_pass = passes + 1u < m.budget();
+    const bool local_waiter =
+        may_pass && (tok.next_seen != ticket + 1u || ptx::ld_relaxed_cluster(&m.cl->next) != ticket + 1u);
+    if (local_waiter) {
+      const uint32_t word = kCohortOwned | ((passes + 1u) << 16) | g;
+      ptx::st_release_cluster_u64(&m.cl->turn, ((uint64_t)word << 32) | (ticket + 1u));
+    } else {
+      ptx::st_release(m.turn(), (g + 1u) & 0xFFFFu);
+      ptx::st_release_cluster_u64(&m.cl->turn, (uint64_t)(ticket + 1u));
+    }
   } else if (KIND == GSYNC_MUTEX_RING) {
     // Clear this block's entry before moving the head past it, so that no block can match
     // its own id left over from an earlier lap of the ring.
@@ -416,7 +506,7 @@ __device__ __forceinline__ void mutex_unlock_thread(const MutexRef& m, const Tok
 // Ticket-only form for the kinds whose unlock needs nothing but the ticket.
 template <int KIND>
 __device__ __forceinline__ void mutex_unlock_thread(const MutexRef& m, uint32_t ticket) {
-  static_assert(KIND != GSYNC_MUTEX_COHORT, "a cohort unlock needs the whole Token");
+  static_assert(KIND != GSYNC_MUTEX_COHORT && KIND != GSYNC_MUTEX_CLUSTER, "a cohort unlock needs the whole Token");
   mutex_unlock_thread<KIND>(m, Token{GSYNC_OK, ticket, 0u, 0u});
 }
 

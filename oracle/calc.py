@@ -109,7 +109,7 @@ def mutex_final(nblocks: int, acq: int, cs_words: int, addend: np.ndarray) -> di
 
 def check_grant_log(log: np.ndarray, ticket: np.ndarray | None, nblocks: int, acq: int,
                     fifo: bool, ticket_base: int = 0, per_die: bool = False,
-                    die_bases: tuple = (0, 0)) -> list[str]:
+                    die_bases: tuple = (0, 0), group_bits: int = 0) -> list[str]:
     """Validity of a grant log (the parts of the result that are not unique).
 
     log[s] is the acquisition id granted s-th.  It must be a permutation of 0..B*A-1 in
@@ -118,7 +118,9 @@ def check_grant_log(log: np.ndarray, ticket: np.ndarray | None, nblocks: int, ac
     the critical section to blocks in the order in which they request access") the ticket
     drawn by the acquisition granted s-th must be ticket_base + s.  per_die (the two-die
     cohort lock): ticket bit 31 is the die and bits 30..0 that die's ticket; each die's
-    grants, in grant order, must carry die_bases[d] + 0, 1, 2, ...
+    grants, in grant order, must carry die_bases[d] + 0, 1, 2, ...  group_bits = g (the
+    cluster cohort lock): the top g bits are the group and the rest its ticket, and each
+    group's grants, in grant order, must carry 0, 1, 2, ...
     """
     n = nblocks * acq
     log = np.asarray(log, dtype=np.int64)
@@ -138,6 +140,15 @@ def check_grant_log(log: np.ndarray, ticket: np.ndarray | None, nblocks: int, ac
         want = (np.arange(n, dtype=np.uint64) + np.uint64(ticket_base)) & np.uint64(M32)
         if not np.array_equal(t, want):
             problems.append("grants are not in ticket order")
+    if group_bits:
+        t = np.asarray(ticket, dtype=np.uint64)[log]
+        shift = np.uint64(32 - group_bits)
+        grp, local = t >> shift, t & ((np.uint64(1) << shift) - np.uint64(1))
+        for g in np.unique(grp):
+            got = local[grp == g]
+            if not np.array_equal(got, np.arange(len(got), dtype=np.uint64)):
+                problems.append(f"group {int(g)}'s grants are not in its ticket order")
+                break
     if per_die:
         t = np.asarray(ticket, dtype=np.uint64)[log]
         die, local = t >> np.uint64(31), t & np.uint64(0x7FFFFFFF)

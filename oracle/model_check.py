@@ -335,7 +335,8 @@ class CohortMutex:
     """Two-level cohort lock over two dies (lock cohorting: Dice, Marathe and Shavit, PPoPP
     2012), the library's GB300 design that keeps hand-offs inside a die.
 
-    Block p sits on die p mod 2.  Each die d has a local ticket counter next_d and a local turn
+    Block p sits on die p mod 2 (group p mod `groups`: the library also runs the protocol
+    over thread-block clusters, with the local lock in distributed shared memory).  Each die d has a local ticket counter next_d and a local turn
     word (served_d, word_d) read and written as one 64-bit access; word_d's OWNED bit says the
     die's cohort already holds the global ticket lock (gnext, gturn; 16-bit ticket compare).
     lock: t <- FA(next_d); wait until served_d = t; if OWNED, inherit the global lock (passes
@@ -353,20 +354,21 @@ class CohortMutex:
     kind, capacity, fifo = "mutex", 1, False
     OWNED = 0x80000000
 
-    def __init__(self, budget=2, base=0, gbase=0, broken=None):
+    def __init__(self, budget=2, base=0, gbase=0, broken=None, groups=2):
         self.budget, self.base, self.gbase, self.broken = budget, base & M32, gbase & M32, broken
-        self.dies = 2
+        self.dies = groups  # dies, or thread-block clusters: the protocol is the same
 
     def init(self, nproc, ops):
         b, g = self.base, self.gbase
-        # (next0, served0, word0, next1, served1, word1, gnext, gturn)
-        return (b, b, 0, b, b, 0, g, g & 0xFFFF), tuple((0, 0, 0, 0) for _ in range(nproc))
+        # (next_d, served_d, word_d) per group, then (gnext, gturn)
+        return (b, b, 0) * self.dies + (g, g & 0xFFFF), tuple((0, 0, 0, 0) for _ in range(nproc))
 
     def step(self, p, loc, sh, nproc, ops):
         pc, k, t, c = loc
-        d = p % 2
+        d = p % self.dies
         nx, sv, wd = sh[3 * d], sh[3 * d + 1], sh[3 * d + 2]
-        gnext, gturn = sh[6], sh[7]
+        G = 3 * self.dies
+        gnext, gturn = sh[G], sh[G + 1]
 
         def put_local(nx2, sv2, wd2):
             return sh[:3 * d] + (nx2, sv2, wd2) + sh[3 * d + 3:]
@@ -386,7 +388,7 @@ class CohortMutex:
                 return (PC_ENTER, k, t, 0), sh, None
             return (2, k, t, c), sh, None
         if pc == 2:
-            return (3, k, t, gnext & 0xFFFF), sh[:6] + (inc(gnext), gturn), None
+            return (3, k, t, gnext & 0xFFFF), sh[:G] + (inc(gnext), gturn), None
         if pc == 3:
             return ((PC_ENTER if (gturn & 0xFFFF) == c else 3), k, t, c), sh, None
         if pc == PC_ENTER:
@@ -406,7 +408,7 @@ class CohortMutex:
             return (pc2, k2, t, c), put_local(nx, inc(t, 2 if self.broken == "skip_ticket" else 1), word), None
         if pc == 6:
             g = c & 0xFFFF
-            return (7, k, t, c), sh[:7] + ((g + 1) & 0xFFFF,), None
+            return (7, k, t, c), sh[:G + 1] + ((g + 1) & 0xFFFF,), None
         if pc == 7:
             pc2, k2 = finish()
             word = self.OWNED if self.broken == "owned_on_release" else 0

@@ -26,8 +26,13 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
   const uint32_t b = blockIdx.x, tid = threadIdx.x;
   const uint32_t n = gridDim.x * (uint32_t)acq;
   gsync::MutexRef m;
-  if (KIND >= 0) {
+  if (KIND == GSYNC_MUTEX_CLUSTER) {
+    __shared__ gsync::ClusterLocal cluster_lock;
+    m = gsync::mutex_attach_cluster(state, &cluster_lock);
+  } else if (KIND >= 0) {
     m = gsync::mutex_attach(state);
+  }
+  if (KIND >= 0) {
     const bool bad_queue =
         (KIND == GSYNC_MUTEX_SLEEP_QUEUE || KIND == GSYNC_MUTEX_RING) && gridDim.x > m.qmask + 1u;
     if (m.kind != (uint32_t)KIND || bad_queue) {
@@ -63,7 +68,9 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
       }
       // COHORT: tickets are per die; bit 31 records the die so the host can check each
       // die's grants in ticket order.
-      ticket_out[id] = KIND == GSYNC_MUTEX_COHORT ? (m.die << 31) | (t.ticket & 0x7FFFFFFFu) : t.ticket;
+      ticket_out[id] = KIND == GSYNC_MUTEX_COHORT    ? (m.die << 31) | (t.ticket & 0x7FFFFFFFu)
+                       : KIND == GSYNC_MUTEX_CLUSTER ? ((b / gsync::ptx::cluster_nctarank()) << 20) | (t.ticket & 0xFFFFFu)
+                                                     : t.ticket;
     }
     if (KIND != kFrameOnly)
       for (uint32_t i = tid; i < (uint32_t)cs_words; i += blockDim.x) data[i] += v ^ (i * kGolden);
@@ -77,6 +84,7 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
     ++done;
   }
   if (tid == 0) count[b] = done;
+  if (KIND == GSYNC_MUTEX_CLUSTER) gsync::mutex_cluster_end();  // block 0's shared lock outlives every user
 }
 
 using KernelFn = void (*)(uint32_t*, int, int, const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*,
@@ -90,6 +98,7 @@ KernelFn pick(int kind) {
     case GSYNC_MUTEX_SLEEP_QUEUE: return mutex_workload_kernel<GSYNC_MUTEX_SLEEP_QUEUE>;
     case GSYNC_MUTEX_COHORT: return mutex_workload_kernel<GSYNC_MUTEX_COHORT>;
     case GSYNC_MUTEX_RING: return mutex_workload_kernel<GSYNC_MUTEX_RING>;
+    case GSYNC_MUTEX_CLUSTER: return mutex_workload_kernel<GSYNC_MUTEX_CLUSTER>;
   }
   return nullptr;
 }
@@ -99,8 +108,18 @@ int check_work(const gsync_mutex_work* w) {
       w->block_threads > kMaxThreads || w->block_threads % 32)
     return GSYNC_EINVAL;
   if ((uint64_t)w->nblocks * (uint64_t)w->acq >= (1ull << 31)) return GSYNC_EINVAL;
+  if (w->kind == GSYNC_MUTEX_CLUSTER) {
+    // cluster ids and tickets must fit the recorded (cluster << 20) | ticket
+    if (w->cluster < 2 || w->cluster > 8 || w->nblocks % w->cluster || w->nblocks / w->cluster > 4096 ||
+        (uint64_t)w->cluster * (uint64_t)w->acq >= (1ull << 20))
+      return GSYNC_EINVAL;
+  } else if (w->cluster > 1) {
+    return GSYNC_EINVAL;
+  }
   return GSYNC_OK;
 }
+
+int launch_cluster(const gsync_mutex_work* w) { return w->kind == GSYNC_MUTEX_CLUSTER ? w->cluster : 1; }
 
 size_t round_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -122,7 +141,8 @@ extern "C" int gsync_bench_mutex(void* state, const gsync_mutex_work* w, void* s
     return GSYNC_EINVAL;
   KernelFn k = pick(w->kind);
   if (!k) return GSYNC_EINVAL;
-  return launch_coresident(k, w->nblocks, w->block_threads, 1, 0, (cudaStream_t)stream, (uint32_t*)state, w->acq,
+  return launch_coresident(k, w->nblocks, w->block_threads, launch_cluster(w), 0, (cudaStream_t)stream,
+                           (uint32_t*)state, w->acq,
                            w->cs_words, w->delay, w->addend, w->data, w->total, w->grant_log, w->ticket, w->count,
                            w->status);
 }

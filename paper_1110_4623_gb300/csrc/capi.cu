@@ -167,7 +167,7 @@ extern "C" {
 int gsync_last_cuda_error(void) { return g_last_cuda_error; }
 
 size_t gsync_mutex_bytes(int kind, int max_waiters) {
-  if (kind < GSYNC_MUTEX_CAS_SPIN || kind > GSYNC_MUTEX_RING || max_waiters < 1) return 0;
+  if (kind < GSYNC_MUTEX_CAS_SPIN || kind > GSYNC_MUTEX_CLUSTER || max_waiters < 1) return 0;
   if (max_waiters > (1 << 24)) return 0;
   if (kind == GSYNC_MUTEX_COHORT) return kCohortBytes;
   const bool queued = kind == GSYNC_MUTEX_SLEEP_QUEUE || kind == GSYNC_MUTEX_RING;
@@ -230,6 +230,16 @@ int gsync_mutex_init_cohort(void* state, size_t bytes, int budget, const gsync_b
   return launch_init(state, bytes, spec, st);
 }
 
+int gsync_mutex_init_cluster(void* state, size_t bytes, int budget, const gsync_backoff* backoff, uint64_t timeout_ns,
+                             void* stream) {
+  if (!state || !aligned(state, kLine) || bytes < 3 * kLine || budget < 1 || budget > 32767) return GSYNC_EINVAL;
+  if (backoff && backoff->policy > GSYNC_BACKOFF_SPIN_THEN_SLEEP) return GSYNC_EINVAL;
+  InitSpec spec;
+  fill_header(spec, kPrimMutex, GSYNC_MUTEX_CLUSTER, 0, (uint32_t)budget, backoff, timeout_ns, 0);
+  spec.nwords = 3 * kLine / 4;
+  return launch_init(state, bytes, spec, (cudaStream_t)stream);
+}
+
 int gsync_mutex_init(void* state, size_t bytes, int kind, int max_waiters, const gsync_backoff* backoff,
                      uint64_t timeout_ns, void* stream) {
   const size_t need = gsync_mutex_bytes(kind, max_waiters);
@@ -237,6 +247,8 @@ int gsync_mutex_init(void* state, size_t bytes, int kind, int max_waiters, const
   if (backoff && backoff->policy > GSYNC_BACKOFF_SPIN_THEN_SLEEP) return GSYNC_EINVAL;
   if (kind == GSYNC_MUTEX_COHORT)
     return gsync_mutex_init_cohort(state, bytes, GSYNC_COHORT_DEFAULT_BUDGET, backoff, timeout_ns, stream);
+  if (kind == GSYNC_MUTEX_CLUSTER)
+    return gsync_mutex_init_cluster(state, bytes, GSYNC_COHORT_DEFAULT_BUDGET, backoff, timeout_ns, stream);
   const bool queued = kind == GSYNC_MUTEX_SLEEP_QUEUE || kind == GSYNC_MUTEX_RING;
   const uint32_t q = queued ? pow2_at_least((uint32_t)max_waiters) : 0;
   InitSpec spec;

@@ -18,7 +18,7 @@ GSYNC_OK, GSYNC_EINVAL, GSYNC_ENOTRESIDENT, GSYNC_ETIMEDOUT, GSYNC_ECUDA, GSYNC_
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOTRESIDENT", 3: "ETIMEDOUT", 4: "ECUDA", 5: "EABORTED"}
 GSYNC_STATUS_TIMEOUT, GSYNC_STATUS_ABORTED, GSYNC_STATUS_VIOLATION, GSYNC_STATUS_CONFIG = 1, 2, 4, 8
 
-MUTEX_KINDS = {"cas_spin": 0, "cas_backoff": 1, "ticket": 2, "sleep_queue": 3, "cohort": 4, "ring": 5}
+MUTEX_KINDS = {"cas_spin": 0, "cas_backoff": 1, "ticket": 2, "sleep_queue": 3, "cohort": 4, "ring": 5, "cluster": 6}
 COHORT_DEFAULT_BUDGET = 64
 BARRIER_KINDS = {"atomic": 0, "flag": 1, "tree": 2, "cluster": 3, "sharded": 4, "die": 5, "split": 6, "count": 7}
 SEM_KINDS = {"ticket": 0, "spin": 1, "spin_backoff": 2}
@@ -49,7 +49,7 @@ class gsync_barrier_work(ctypes.Structure):
 
 class gsync_mutex_work(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("nblocks", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("acq", ctypes.c_int32), ("cs_words", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("acq", ctypes.c_int32), ("cs_words", ctypes.c_int32), ("cluster", ctypes.c_int32),
                 ("delay", u32p), ("addend", u32p), ("data", u32p), ("total", u32p), ("grant_log", u32p),
                 ("ticket", u32p), ("count", u32p), ("status", u32p)]
 
@@ -100,6 +100,8 @@ _SIG = {
     "gsync_mutex_init_cohort": (ctypes.c_int, [u32p, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(gsync_backoff),
                                                ctypes.c_uint64, u32p]),
     "gsync_device_topology": (ctypes.c_int, [u32p, ctypes.POINTER(ctypes.c_int), u32p]),
+    "gsync_mutex_init_cluster": (ctypes.c_int, [u32p, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(gsync_backoff),
+                                                ctypes.c_uint64, u32p]),
     "gsync_check_coresident": (ctypes.c_int, [u32p, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_int,
                                               ctypes.POINTER(ctypes.c_int)]),
     "gsync_launch_coresident": (ctypes.c_int, [u32p, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_int, u32p,
@@ -251,6 +253,11 @@ def gsync_max_coresident_blocks(workload: int, kind: int, block_threads: int, cl
 def gsync_mutex_init_cohort(state, nbytes, budget, backoff=None, timeout_ns=0, stream=None) -> int:
     bo = ctypes.byref(backoff) if backoff is not None else None
     return lib().gsync_mutex_init_cohort(ptr(state), nbytes, budget, bo, timeout_ns, stream_handle(stream))
+
+
+def gsync_mutex_init_cluster(state, nbytes, budget, backoff=None, timeout_ns=0, stream=None) -> int:
+    bo = ctypes.byref(backoff) if backoff is not None else None
+    return lib().gsync_mutex_init_cluster(ptr(state), nbytes, budget, bo, timeout_ns, stream_handle(stream))
 
 
 def gsync_device_topology(die_of_sm, stream=None) -> tuple[int, int]:

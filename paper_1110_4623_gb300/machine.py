@@ -99,17 +99,23 @@ def measure_extended(nblocks: int = 1184) -> dict:
         far = runner.probe_pingpong(a, b, 2000)["handoff_ns"]
     fence = runner.probe_fence(0)["ns_per_fence"]
     r_same = runner.probe_throughput("red_add", True, False, nblocks, 128, 2000)["ops_per_s"]
-    return {"dies": nd, "handoff_near_ns": near, "handoff_far_ns": far, "fence_ns": fence,
-            "atomic_same_ns": 1e9 / r_same}
+    dsmem = runner.probe_cluster(1, 2, 2000)["ns"]
+    return {"dies": nd, "handoff_near_ns": near, "handoff_far_ns": far, "handoff_dsmem_ns": dsmem,
+            "fence_ns": fence, "atomic_same_ns": 1e9 / r_same}
 
 
 def design_extended(params: dict, ext: dict, nblocks: int = 1184) -> dict:
     """The Section 4 choice, then the GB300 extensions: a cohort lock on a two-die part whose
-    cross-die hand-off is DIE_GAP_NS slower, and the counting barrier when `nblocks` serialized
+    cross-die hand-off is DIE_GAP_NS slower (mutex_without_clusters), and over thread-block
+    clusters when a hand-off through distributed shared memory beats the on-die L2 one and the
+    kernel can launch in clusters (mutex); the counting barrier when `nblocks` serialized
     same-word atomics cost less than the two hand-offs of the flag barrier's extra stage."""
     choice = dict(design(params))
     if ext["dies"] == 2 and ext["handoff_far_ns"] - ext["handoff_near_ns"] > DIE_GAP_NS:
         choice["mutex"] = "cohort"
+    choice["mutex_without_clusters"] = choice["mutex"]
+    if ext.get("handoff_dsmem_ns", float("inf")) < ext["handoff_near_ns"]:
+        choice["mutex"] = "cluster"
     if nblocks * ext["atomic_same_ns"] < 2.0 * ext["handoff_near_ns"]:
         choice["barrier"] = "count"
     return choice

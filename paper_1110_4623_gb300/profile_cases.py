@@ -19,13 +19,13 @@ NB = 1184
 
 
 # Backoff as the bench runs each kind (ticket kinds: ns per waiter ahead, capped).
-_BACKOFF = {"cas_backoff": (32, 2048), "cohort": (128, 4000)}
+_BACKOFF = {"cas_backoff": (32, 2048), "cohort": (128, 4000), "cluster": (128, 4000)}
 
 
 def _mutex(kind, K, acq=20):
     delay, add = inputs.mutex_inputs(NB, acq, inputs.mutex_seed(G.MUTEX_KINDS[kind], NB, K))
     bo = runner.backoff(min_ns=_BACKOFF[kind][0], max_ns=_BACKOFF[kind][1]) if kind in _BACKOFF else None
-    r = runner.MutexRun(kind, NB, 256, acq, K, delay, add, bo=bo, timeout_ns=10_000_000_000)
+    r = runner.MutexRun(kind, NB, 256, acq, K, delay, add, bo=bo, timeout_ns=10_000_000_000, cluster=4)
     return lambda: G.check("gsync_bench_mutex", r.launch())
 
 
@@ -62,6 +62,7 @@ CASES = {
     "mutex_cas_spin": lambda: _mutex("cas_spin", 64),
     "mutex_cas_backoff": lambda: _mutex("cas_backoff", 64),
     "mutex_cohort": lambda: _mutex("cohort", 64),
+    "mutex_cluster": lambda: _mutex("cluster", 64),
     "barrier_atomic": lambda: _barrier("atomic", 0),
     "barrier_flag": lambda: _barrier("flag", 0),
     "barrier_cluster2": lambda: _barrier("cluster", 2),

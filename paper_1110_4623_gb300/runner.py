@@ -105,14 +105,18 @@ class MutexRun:
 
     def __init__(self, kind: str, nblocks: int, block_threads: int, acq: int, cs_words: int,
                  delay: np.ndarray | None, addend: np.ndarray, bo: G.gsync_backoff | None = None,
-                 timeout_ns: int = 0, budget: int | None = None):
+                 timeout_ns: int = 0, budget: int | None = None, cluster: int = 8):
         self.kind, self.k = kind, G.MUTEX_KINDS[kind]
+        self.cluster = cluster if kind == "cluster" else 0
         self.nblocks, self.acq, self.cs_words = nblocks, acq, cs_words
         self.bo = bo
         n = nblocks * acq
         self.nbytes = G.gsync_mutex_bytes(self.k, nblocks)
         self.state = _state(self.nbytes)
-        if budget is not None:
+        if budget is not None and kind == "cluster":
+            G.check("gsync_mutex_init_cluster", G.gsync_mutex_init_cluster(self.state, self.nbytes, budget, bo,
+                                                                          timeout_ns))
+        elif budget is not None:
             G.check("gsync_mutex_init_cohort", G.gsync_mutex_init_cohort(self.state, self.nbytes, budget, bo, timeout_ns))
         else:
             G.check("gsync_mutex_init", G.gsync_mutex_init(self.state, self.nbytes, self.k, nblocks, bo, timeout_ns))
@@ -124,7 +128,7 @@ class MutexRun:
         self.ticket = _zeros(n)
         self.count = _zeros(nblocks)
         self.status = _zeros(1)
-        self.work = G.gsync_mutex_work(self.k, nblocks, block_threads, acq, cs_words, 0,
+        self.work = G.gsync_mutex_work(self.k, nblocks, block_threads, acq, cs_words, self.cluster,
                                        G.ptr(self.delay), G.ptr(self.addend), G.ptr(self.data), G.ptr(self.total),
                                        G.ptr(self.log), G.ptr(self.ticket), G.ptr(self.count), G.ptr(self.status))
 

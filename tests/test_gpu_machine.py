@@ -48,4 +48,6 @@ def test_extended_abstraction_measured_on_this_gpu():
         # the cross-die hand-off is the slower one, and the rule then keeps hand-offs on a die
         assert ext["handoff_far_ns"] > ext["handoff_near_ns"]
         params = machine.abstraction(machine.measure_table(1184, 128, 1000, reps=1))
-        assert machine.design_extended(params, ext)["mutex"] == "cohort"
+        got = machine.design_extended(params, ext)
+        assert got["mutex_without_clusters"] == "cohort"
+        assert got["mutex"] == ("cluster" if ext["handoff_dsmem_ns"] < ext["handoff_near_ns"] else "cohort")

@@ -106,6 +106,43 @@ def test_host_buffer_entry_point():
     assert calc.check_grant_log(log, tick, B, A, fifo=True) == []
 
 
+@pytest.mark.parametrize("cluster", [2, 4, 8])
+@pytest.mark.parametrize("nblocks,cs_words", [(1184, 0), (1184, 64), (1184, 1024), (592, 64), (16, 7)])
+def test_cluster_cohort_mutex(cluster, nblocks, cs_words):
+    # The cohort protocol over thread-block clusters: the local lock lives in distributed
+    # shared memory; each cluster's grants follow its own tickets.
+    from paper_1110_4623_gb300 import runner
+    nb = nblocks - nblocks % cluster
+    delay, add = inputs.mutex_inputs(nb, 50, 31_000 + cluster + nb + cs_words)
+    got = runner.MutexRun("cluster", nb, 256, 50, cs_words, delay, add, cluster=cluster, timeout_ns=10_000_000_000,
+                          bo=runner.backoff(min_ns=128, max_ns=4000)).run()
+    want = calc.mutex_final(nb, 50, cs_words, add)
+    assert got["rc"] == 0 and got["status"] == 0, got["status"]
+    assert got["total"] == want["total"] and np.array_equal(got["data"], want["data"])
+    assert calc.check_grant_log(got["log"], got["ticket"], nb, 50, False, group_bits=12) == []
+
+
+@pytest.mark.parametrize("budget", [1, 3, 32767])
+def test_cluster_cohort_budgets(budget):
+    from paper_1110_4623_gb300 import runner
+    delay, add = inputs.mutex_inputs(1184, 20, 41_000 + budget, max_delay=300)
+    got = runner.MutexRun("cluster", 1184, 256, 20, 64, delay, add, cluster=8, budget=budget,
+                          timeout_ns=10_000_000_000).run()
+    want = calc.mutex_final(1184, 20, 64, add)
+    assert got["status"] == 0 and np.array_equal(got["data"], want["data"])
+    assert calc.check_grant_log(got["log"], got["ticket"], 1184, 20, False, group_bits=12) == []
+
+
+def test_cluster_mutex_needs_a_cluster_size():
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    delay, add = inputs.mutex_inputs(64, 2, 5)
+    mr = runner.MutexRun("cluster", 64, 128, 2, 8, delay, add, cluster=8)
+    for bad in (1, 3, 16):  # not a cluster, does not divide 64, above 8
+        mr.work.cluster = bad
+        assert mr.launch() == G.GSYNC_EINVAL
+
+
 def test_cohort_host_buffer_entry_point():
     import torch
     from paper_1110_4623_gb300 import gsync as G

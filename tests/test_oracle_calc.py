@@ -192,3 +192,16 @@ def test_condvar_closed_form():
     # all-ones values over many items: n * (-1), beyond int32 range only in magnitude here
     out = calc.condvar_final(np.full(1 << 16, 0x80000000, np.uint32), 4, 1 << 14, 8)
     assert out["total"] == -(1 << 31) * (1 << 16)
+
+
+def test_grant_log_per_group():
+    # Two groups in the top 12 bits; each group's tickets count from 0 in grant order.
+    B, A = 2, 3
+    good = np.array([0, 3, 1, 4, 2, 5])        # grant order of acquisition ids
+    grp = np.array([0, 1, 0, 1, 0, 1])
+    local = np.array([0, 0, 1, 1, 2, 2])
+    tick = np.empty(6, np.uint32)
+    tick[good] = ((grp.astype(np.uint64) << np.uint64(20)) | local.astype(np.uint64)).astype(np.uint32)
+    assert calc.check_grant_log(good, tick, B, A, fifo=False, group_bits=12) == []
+    bad = tick.copy(); bad[[good[0], good[2]]] = bad[[good[2], good[0]]]
+    assert "group 0" in calc.check_grant_log(good, bad, B, A, fifo=False, group_bits=12)[0]

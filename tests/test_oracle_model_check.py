@@ -27,6 +27,7 @@ CORRECT = [
     ("cohort_budget_2_4x2", mc.CohortMutex(budget=2), 4, 2),
     ("cohort_budget_3", mc.CohortMutex(budget=3), 3, 2),
     ("cohort_wrap", mc.CohortMutex(budget=2, base=W, gbase=0xFFFE), 3, 2),
+    ("cohort_three_groups", mc.CohortMutex(budget=2, groups=3), 4, 2),
     ("spin_sem_1", mc.SpinSem(n=1), 3, 2),
     ("spin_sem_2", mc.SpinSem(n=2), 3, 2),
     ("spin_sem_2_backoff", mc.SpinSem(n=2, backoff=True), 3, 2),
