@@ -184,7 +184,8 @@ def measure_roofline_terms(runner, inputs):
     T_cs_sem = {}
     for n in SEM_COUNTS:
         hold, add = inputs.sem_inputs(NBLOCKS, SEM_PAIRS, inputs.SEED_SEM ^ (n << 16) ^ NBLOCKS)
-        T_cs_sem[n] = runner.probe_sem_cs(hold[:4000], add[:4000], SEM_THREADS)["ns_per_cs"]
+        T_cs_sem[n] = float(np.median([runner.probe_sem_cs(hold[:4000], add[:4000], SEM_THREADS)["ns_per_cs"]
+                                       for _ in range(3)]))
     # The probes' frame (acquire load, barriers, release) is what a hand-off already costs:
     # subtract it so that hand-off + body does not count it twice.
     T_frame = float(np.median([runner.probe_cs(-1, MUTEX_THREADS, 20000)["ns_per_cs"] for _ in range(3)]))
