@@ -57,8 +57,8 @@ BATCH_KEYS, BATCH_ACQ, BATCH_GROUPS, BATCH_ROUNDS, BATCH_THREADS = 4096, 1_000_0
 METRIC = "lock acquires/s & barrier ns at 1184 blocks vs L2-atomic roofline; p99 latency"
 # DRAM bytes per launch of the default mutex kind's workload kernel from an ncu capture, or
 # None while the kernel has changed since the last capture.
-ROOF_TRAFFIC = 997_120
-ROOF_TRAFFIC_NOTE = ("DRAM bytes per launch of the dominant kernel (cohort mutex workload), scaled x5 from the "
+ROOF_TRAFFIC = 995_840
+ROOF_TRAFFIC_NOTE = ("DRAM bytes per launch of the dominant kernel (cluster cohort mutex workload), scaled x5 from the "
                      "20-acquisition ncu capture in profiles/ (input arrays only)")
 TIMEOUT_NS = 10_000_000_000
 

@@ -82,6 +82,11 @@ BROKEN = [
     ("cohort_owned_on_release", mc.CohortMutex(broken="owned_on_release"), 2, 2, "critical section"),
     ("cohort_pass_always", mc.CohortMutex(broken="pass_always"), 2, 2, "final state"),
     ("cohort_skip_ticket", mc.CohortMutex(broken="skip_ticket"), 3, 2, "local ticket"),
+    # The same mistakes with three groups, the shape of the cluster cohort lock.
+    ("cohort3_no_global", mc.CohortMutex(broken="no_global", groups=3), 3, 1, "critical section"),
+    ("cohort3_owned_on_release", mc.CohortMutex(broken="owned_on_release", groups=3), 3, 2, "critical section"),
+    ("cohort3_pass_always", mc.CohortMutex(broken="pass_always", groups=3), 3, 2, "final state"),
+    ("cohort3_skip_ticket", mc.CohortMutex(broken="skip_ticket", groups=3), 4, 2, "local ticket"),
     ("sleep_sem_turn_ge", mc.SleepSem(n=1, broken="turn_ge"), 3, 1, "critical section"),
     ("barrier_no_wait", mc.AtomicBarrier(broken="no_wait"), 3, 1, "passed round"),
     ("barrier_late_reset_one_counter", mc.AtomicBarrier(broken="reset_one_counter"), 2, 3, "deadlock"),
