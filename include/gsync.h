@@ -327,8 +327,8 @@ typedef struct gsync_sem_work {
 int gsync_bench_sem(void* state, const gsync_sem_work* w, void* stream);
 
 /* Condition-variable workload: a bounded buffer (producer/consumer queue) of `capacity` item
- * ids guarded by one mutex (TICKET or COHORT) and two condition variables (not_full,
- * not_empty).  Blocks
+ * ids guarded by one mutex (TICKET, COHORT or CLUSTER) and two condition variables
+ * (not_full, not_empty).  Blocks
  * 0 .. producers-1 each put items_per_producer items (item id = block * items_per_producer +
  * i); the next `consumers` blocks each take producers * items_per_producer / consumers items
  * (which must divide exactly).  A producer waits on not_full while the buffer is full and
@@ -339,10 +339,14 @@ int gsync_bench_sem(void* state, const gsync_sem_work* w, void* stream);
  * the two condition variables and the buffer live in `workspace` (device, 256-byte aligned,
  * >= gsync_bench_condvar_workspace_bytes(capacity)), initialised by the call.  backoff (host,
  * may be NULL) sets the waiters' sleep; one co-resident launch of producers + consumers
- * blocks; GSYNC_ENOTRESIDENT if it does not fit.  status bits as for the other workloads. */
+ * blocks (in clusters of `cluster` for CLUSTER); GSYNC_ENOTRESIDENT if it does not fit.
+ * status bits as for the other workloads. */
 typedef struct gsync_condvar_work {
   int32_t producers, consumers, items_per_producer, capacity, block_threads;
-  int32_t mutex_kind; /* the queue's mutex: GSYNC_MUTEX_TICKET or GSYNC_MUTEX_COHORT */
+  int32_t mutex_kind; /* the queue's mutex: GSYNC_MUTEX_TICKET, GSYNC_MUTEX_COHORT or
+                         GSYNC_MUTEX_CLUSTER */
+  int32_t cluster;    /* GSYNC_MUTEX_CLUSTER: blocks per cluster, 2..8, dividing producers +
+                         consumers (0 = 4); ignored by the other kinds */
   const uint32_t* value;
   uint32_t* seen;
   int64_t* sum;

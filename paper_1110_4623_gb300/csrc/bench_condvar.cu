@@ -1,5 +1,5 @@
 // Condition-variable workload: a bounded producer/consumer queue of item ids under one
-// mutex (TICKET or COHORT) and two condition variables (condition variables are named as future work in
+// mutex (TICKET, COHORT or CLUSTER) and two condition variables (condition variables are named as future work in
 // Section 7; the design is in gsync_device.cuh).  Each item id is put once and must be taken
 // exactly once: seen[] counts takes, and the consumers' int64 sums must add up to the sum of
 // the items' values.
@@ -23,7 +23,13 @@ __global__ void __launch_bounds__(kMaxThreads)
                             int producers, int items_per_producer, int items_per_consumer,
                             const uint32_t* __restrict__ value, uint32_t* seen, int64_t* sum, uint32_t* count,
                             uint32_t* status) {
-  const gsync::MutexRef m = gsync::mutex_attach(mutex_state);
+  gsync::MutexRef m;
+  if (MKIND == GSYNC_MUTEX_CLUSTER) {
+    __shared__ gsync::ClusterLocal cluster_lock;
+    m = gsync::mutex_attach_cluster(mutex_state, &cluster_lock);
+  } else {
+    m = gsync::mutex_attach(mutex_state);
+  }
   const gsync::CondRef not_full = gsync::cond_attach(nf_state), not_empty = gsync::cond_attach(ne_state);
   const bool producer = (int)blockIdx.x < producers;
   const int ops = producer ? items_per_producer : items_per_consumer;
@@ -85,16 +91,21 @@ __global__ void __launch_bounds__(kMaxThreads)
     sum[c] = my_sum;
     count[c] = taken;
   }
+  if (MKIND == GSYNC_MUTEX_CLUSTER) gsync::mutex_cluster_end();  // block 0's shared lock outlives every user
 }
 
 size_t round_up(size_t n) { return (n + 255) & ~(size_t)255; }
 
 }  // namespace
 
-// The mutex sits first in the workspace and takes the larger of the two kinds' sizes.
+// The mutex sits first in the workspace and takes the largest of the kinds' sizes.
 size_t mutex_region() {
-  const size_t a = gsync_mutex_bytes(GSYNC_MUTEX_TICKET, 1), b = gsync_mutex_bytes(GSYNC_MUTEX_COHORT, 1);
-  return round_up(a > b ? a : b);
+  size_t n = 0;
+  for (int kind : {GSYNC_MUTEX_TICKET, GSYNC_MUTEX_COHORT, GSYNC_MUTEX_CLUSTER}) {
+    const size_t k = gsync_mutex_bytes(kind, 1);
+    n = k > n ? k : n;
+  }
+  return round_up(n);
 }
 
 extern "C" size_t gsync_bench_condvar_workspace_bytes(int capacity) {
@@ -111,7 +122,12 @@ extern "C" int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_back
   const int64_t items = (int64_t)w->producers * w->items_per_producer;
   if (items > (1ll << 30) || items % w->consumers) return GSYNC_EINVAL;
   if (!w->value || !w->seen || !w->sum || !w->count || !w->status) return GSYNC_EINVAL;
-  if (w->mutex_kind != GSYNC_MUTEX_TICKET && w->mutex_kind != GSYNC_MUTEX_COHORT) return GSYNC_EINVAL;
+  if (w->mutex_kind != GSYNC_MUTEX_TICKET && w->mutex_kind != GSYNC_MUTEX_COHORT &&
+      w->mutex_kind != GSYNC_MUTEX_CLUSTER)
+    return GSYNC_EINVAL;
+  const int cluster = w->mutex_kind != GSYNC_MUTEX_CLUSTER ? 1 : w->cluster ? w->cluster : 4;
+  if ((w->mutex_kind == GSYNC_MUTEX_CLUSTER && (cluster < 2 || cluster > 8)) || (w->producers + w->consumers) % cluster)
+    return GSYNC_EINVAL;
   const size_t need = gsync_bench_condvar_workspace_bytes(w->capacity);
   if (need == 0 || !workspace || workspace_bytes < need || !aligned(workspace, 256)) return GSYNC_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
@@ -131,9 +147,10 @@ extern "C" int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_back
   GSYNC_CUDA(cudaMemcpyAsync(q, &q0, sizeof q0, cudaMemcpyHostToDevice, st));
   GSYNC_CUDA(cudaStreamSynchronize(st));  // q0 lives on this stack frame
   const int items_per_consumer = (int)(items / w->consumers);
-  auto kernel = w->mutex_kind == GSYNC_MUTEX_COHORT ? condvar_workload_kernel<GSYNC_MUTEX_COHORT>
-                                                    : condvar_workload_kernel<GSYNC_MUTEX_TICKET>;
-  return launch_coresident(kernel, w->producers + w->consumers, w->block_threads, 1, 0, st, mstate, nf, ne, q, buf,
+  auto kernel = w->mutex_kind == GSYNC_MUTEX_COHORT    ? condvar_workload_kernel<GSYNC_MUTEX_COHORT>
+                : w->mutex_kind == GSYNC_MUTEX_CLUSTER ? condvar_workload_kernel<GSYNC_MUTEX_CLUSTER>
+                                                       : condvar_workload_kernel<GSYNC_MUTEX_TICKET>;
+  return launch_coresident(kernel, w->producers + w->consumers, w->block_threads, cluster, 0, st, mstate, nf, ne, q, buf,
                            w->producers, w->items_per_producer, items_per_consumer, w->value, w->seen, w->sum,
                            w->count, w->status);
 }

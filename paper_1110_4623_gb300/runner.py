@@ -161,7 +161,7 @@ class CondVarRun:
 
     def __init__(self, producers: int, consumers: int, items_per_producer: int, capacity: int,
                  value: np.ndarray, block_threads: int = 128, bo: G.gsync_backoff | None = None,
-                 mutex: str = "ticket"):
+                 mutex: str = "ticket", cluster: int = 0):
         n = producers * items_per_producer
         self.producers, self.consumers, self.n, self.bo = producers, consumers, n, bo
         self.value = _u32(value) if n else _zeros(1)
@@ -172,7 +172,7 @@ class CondVarRun:
         self.nbytes = G.gsync_bench_condvar_workspace_bytes(capacity)
         self.ws = _state(self.nbytes)
         self.work = G.gsync_condvar_work(producers, consumers, items_per_producer, capacity, block_threads,
-                                         G.MUTEX_KINDS[mutex],
+                                         G.MUTEX_KINDS[mutex], cluster,
                                          G.ptr(self.value), G.ptr(self.seen), G.ptr(self.sum), G.ptr(self.count),
                                          G.ptr(self.status))
 
@@ -351,22 +351,26 @@ def probe_nanosleep(req_ns, iters: int = 64) -> np.ndarray:
     return out.cpu().numpy()
 
 
-def probe_cs(cs_words: int, block_threads: int = 256, iters: int = 20000) -> dict:
-    nbytes = G.gsync_probe_cs_scratch_bytes(cs_words, iters)
-    scratch = _state(nbytes)
+def probe_cs(cs_words: int, block_threads: int = 256, iters: int = 20000, scratch=None) -> dict:
+    """scratch: None (a fresh buffer) or the device address of gsync_probe_cs_scratch_bytes
+    bytes, 256-byte aligned (lets the caller choose where the probe's hot lines live)."""
+    if scratch is None:
+        scratch = _state(G.gsync_probe_cs_scratch_bytes(cs_words, iters))
     out = (G.ctypes.c_uint64 * 1)()
     G.check("gsync_probe_cs", G.gsync_probe_cs(cs_words, block_threads, iters, scratch, out))
     return {"ns_per_cs": out[0] / iters}
 
 
 def probe_sem_cs(hold: np.ndarray | None, addend: np.ndarray | None, block_threads: int = 128,
-                 iters: int | None = None) -> dict:
+                 iters: int | None = None, scratch=None) -> dict:
     """Mean time of one semaphore critical section with the workload's hold times, alone
-    (hold and addend None: the frame alone, with an empty critical section)."""
+    (hold and addend None: the frame alone, with an empty critical section).  scratch: None
+    or the device address of 1024 bytes, 256-byte aligned."""
     iters = iters if iters is not None else len(hold)
     h = _u32(hold) if hold is not None else None
     a = _u32(addend) if addend is not None else None
-    scratch = _state(1024)
+    if scratch is None:
+        scratch = _state(1024)
     out = (G.ctypes.c_uint64 * 1)()
     G.check("gsync_probe_sem_cs", G.gsync_probe_sem_cs(block_threads, iters, h, a, scratch, out))
     return {"ns_per_cs": out[0] / iters}

@@ -16,12 +16,12 @@ def _gpu():
     require_gpu()
 
 
-def check(producers, consumers, items, capacity, threads=128, bo=None, mutex="ticket"):
+def check(producers, consumers, items, capacity, threads=128, bo=None, mutex="ticket", cluster=0):
     from paper_1110_4623_gb300 import runner
     n = producers * items
     value = inputs.condvar_inputs(n, inputs.SEED_CONDVAR ^ producers ^ (consumers << 12) ^ (capacity << 24))
     got = runner.CondVarRun(producers, consumers, items, capacity, value, block_threads=threads, bo=bo,
-                            mutex=mutex).run()
+                            mutex=mutex, cluster=cluster).run()
     want = calc.condvar_final(value, producers, items, consumers)
     assert got["rc"] == 0 and got["status"] == 0, got["status"]
     assert np.array_equal(got["seen"], want["seen"]), int((got["seen"] != 1).sum())
@@ -40,6 +40,24 @@ def test_producer_consumer_exactly_once(producers, consumers, items, capacity):
 def test_producer_consumer_on_the_cohort_lock(producers, consumers, items, capacity):
     from paper_1110_4623_gb300 import runner
     check(producers, consumers, items, capacity, mutex="cohort", bo=runner.backoff(min_ns=128, max_ns=4000))
+
+
+@pytest.mark.parametrize("producers,consumers,items,capacity,cluster", [
+    (1, 1, 100, 1, 2), (592, 592, 100, 16, 4), (592, 592, 100, 1, 8), (16, 4, 20, 3, 4), (37, 11, 33, 5, 2)])
+def test_producer_consumer_on_the_cluster_lock(producers, consumers, items, capacity, cluster):
+    # Clusters mix producer and consumer blocks wherever producers is not a multiple of the
+    # cluster size; the cohort passes the mutex between them inside the cluster.
+    from paper_1110_4623_gb300 import runner
+    check(producers, consumers, items, capacity, mutex="cluster", cluster=cluster,
+          bo=runner.backoff(min_ns=128, max_ns=4000))
+
+
+def test_cluster_lock_needs_a_cluster_size_that_divides_the_grid():
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    for bad in (1, 3, 16):  # not a cluster, does not divide 8 blocks, above 8
+        r = runner.CondVarRun(4, 4, 4, 4, np.zeros(16, np.uint32), mutex="cluster", cluster=bad)
+        assert r.launch() == G.GSYNC_EINVAL
 
 
 def test_other_mutex_kinds_are_refused():
