@@ -511,8 +511,11 @@ int gsync_probe_throughput(int op, int contentious, int pre_atomic, int nblocks,
                            void* stream);
 
 /* Latency probe: one thread performs `iters` dependent accesses (each address depends on
- * the previous result): op = ATOMIC_READ (atom.add round trip, L_rt) or LOAD_RELAXED (L2
- * load round trip).  out[0] = elapsed ns, out[1] = elapsed SM cycles. */
+ * the previous result) of one kind that returns a value: VOLATILE_LOAD, LOAD_RELAXED,
+ * LOAD_ACQUIRE (L2 load round trips), ATOMIC_READ (atom.add of 0: L_rt), ATOMIC_WRITE,
+ * ATOMIC_ADD64 or ATOMIC_ACQREL (each adds 0 or swaps in 0); the stores and red are refused
+ * (GSYNC_EINVAL).  scratch (device, 128-byte aligned, 128 bytes) is overwritten.
+ * out (device) [0] = elapsed ns, [1] = elapsed SM cycles. */
 int gsync_probe_latency(int op, int iters, void* scratch, uint64_t* out, void* stream);
 
 /* Ping-pong probe: the blocks on SMs sm_a and sm_b pass a token back and forth `iters`

@@ -69,9 +69,14 @@ __global__ void probe_latency_kernel(uint32_t* scratch, int iters, uint64_t* out
   const uint64_t t0 = ptx::globaltimer();
   const long long c0 = clock64();
   for (int i = 0; i < iters; ++i) {
-    uint32_t* q = scratch + (v >> 31);
+    uint32_t* q = scratch + ((v >> 31) << 1);  // stays 8-byte aligned for the 64-bit atomic
     if (OP == GSYNC_PROBE_ATOMIC_READ) v = ptx::atom_add_relaxed(q, 0u);
-    else v = ptx::ld_relaxed(q);
+    if (OP == GSYNC_PROBE_LOAD_RELAXED) v = ptx::ld_relaxed(q);
+    if (OP == GSYNC_PROBE_VOLATILE_LOAD) v = ptx::ld_volatile(q);
+    if (OP == GSYNC_PROBE_LOAD_ACQUIRE) v = ptx::ld_acquire(q);
+    if (OP == GSYNC_PROBE_ATOMIC_WRITE) v = atomicExch(q, 0u);
+    if (OP == GSYNC_PROBE_ATOMIC_ADD64) v = (uint32_t)atomicAdd((unsigned long long*)q, 0ull);
+    if (OP == GSYNC_PROBE_ATOMIC_ACQREL) v = ptx::atom_add_acq_rel(q, 0u);
   }
   const long long c1 = clock64();
   const uint64_t t1 = ptx::globaltimer();
@@ -150,13 +155,18 @@ extern "C" int gsync_probe_throughput(int op, int contentious, int pre_atomic, i
 extern "C" int gsync_probe_latency(int op, int iters, void* scratch, uint64_t* out, void* stream) {
   if (iters < 1 || !scratch || !out || !aligned(scratch, 128)) return GSYNC_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  if (op == GSYNC_PROBE_ATOMIC_READ) {
-    probe_latency_kernel<GSYNC_PROBE_ATOMIC_READ><<<1, 32, 0, st>>>((uint32_t*)scratch, iters, out);
-  } else if (op == GSYNC_PROBE_LOAD_RELAXED) {
-    probe_latency_kernel<GSYNC_PROBE_LOAD_RELAXED><<<1, 32, 0, st>>>((uint32_t*)scratch, iters, out);
-  } else {
-    return GSYNC_EINVAL;
+  void (*k)(uint32_t*, int, uint64_t*) = nullptr;
+  switch (op) {
+    case GSYNC_PROBE_VOLATILE_LOAD: k = probe_latency_kernel<GSYNC_PROBE_VOLATILE_LOAD>; break;
+    case GSYNC_PROBE_ATOMIC_READ: k = probe_latency_kernel<GSYNC_PROBE_ATOMIC_READ>; break;
+    case GSYNC_PROBE_ATOMIC_WRITE: k = probe_latency_kernel<GSYNC_PROBE_ATOMIC_WRITE>; break;
+    case GSYNC_PROBE_LOAD_ACQUIRE: k = probe_latency_kernel<GSYNC_PROBE_LOAD_ACQUIRE>; break;
+    case GSYNC_PROBE_LOAD_RELAXED: k = probe_latency_kernel<GSYNC_PROBE_LOAD_RELAXED>; break;
+    case GSYNC_PROBE_ATOMIC_ADD64: k = probe_latency_kernel<GSYNC_PROBE_ATOMIC_ADD64>; break;
+    case GSYNC_PROBE_ATOMIC_ACQREL: k = probe_latency_kernel<GSYNC_PROBE_ATOMIC_ACQREL>; break;
+    default: return GSYNC_EINVAL;  // stores and red return nothing to chain on
   }
+  k<<<1, 32, 0, st>>>((uint32_t*)scratch, iters, out);
   GSYNC_CUDA(cudaGetLastError());
   return GSYNC_OK;
 }

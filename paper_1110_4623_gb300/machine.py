@@ -63,8 +63,8 @@ def abstraction(t: dict) -> dict:
         "atomic_volatile": max(t3[("cont_atomic", "read")], t3[("cont_atomic", "write")]),
         "atomic_volatile_read": t3[("cont_atomic", "read")],
         "cont_noncont_volatile": max(t2[("volatile", "read")], t2[("volatile", "write")]),
-        "line_hostage": max(t3[("cont_vol_after_atomic", "read")], t3[("cont_vol_after_atomic", "write")])
-        > HOSTAGE_THRESHOLD,
+        "line_hostage": bool(max(t3[("cont_vol_after_atomic", "read")], t3[("cont_vol_after_atomic", "write")])
+                             > HOSTAGE_THRESHOLD),
     }
 
 
@@ -119,3 +119,100 @@ def design_extended(params: dict, ext: dict, nblocks: int = 1184) -> dict:
     if nblocks * ext["atomic_same_ns"] < 2.0 * ext["handoff_near_ns"]:
         choice["barrier"] = "count"
     return choice
+
+
+# ---- the whole description -----------------------------------------------------------------
+
+LATENCY_OPS = ("volatile_load", "load_relaxed", "load_acquire", "atomic_read", "atomic_add64", "atomic_acqrel")
+SWEEP_BLOCKS = (1, 8, 38, 76, 152, 304, 608, 1184)
+SLEEP_NS = (0, 20, 40, 100, 200, 500, 1000, 2000, 4000, 8000)
+CLUSTER_SIZES = (2, 4, 8)
+FENCE_OPS = {"alone": 0, "after_relaxed_store": 1, "after_four_stores": 2, "cluster_scope": 3}
+
+
+def measure_all(nblocks: int = 1184, quick: bool = False) -> dict:
+    """Everything the probes measure, as one JSON-ready description of this GPU:
+    - the paper's probe matrix (Table 1 shape), its two ratio tables, the three Section 4
+      parameters and the primitives they favour;
+    - dependent-chain latency of one thread per access kind (32- and 64-bit atomics, relaxed
+      and acquire loads);
+    - same-word and distinct-word throughput of `red` and `atom` against the number of blocks;
+    - the two dies: SMs per die and the atomic round trip to a line homed on the SM's own die
+      and on the other;
+    - SM-to-SM hand-offs (near, far, inside a cluster through distributed shared memory or an
+      mbarrier), the hardware cluster barrier, release fences, __nanosleep accuracy and the
+      host-to-GPU hand-off through pinned memory;
+    - the GB300 extension of the design rule.
+    quick: fewer accesses per probe (a check that everything runs, not a measurement)."""
+    import numpy as np
+    iters = 100 if quick else 1000
+    reps = 1 if quick else 3
+    table = measure_table(nblocks, 128, iters, reps)
+    t2, t3 = ratios(table)
+    params = abstraction(table)
+    out = {
+        "sm_count": runner.sm_count(),
+        "table1_ms": {row: {d: table[(row, d)] for d in ("read", "write")} for row in ROWS},
+        "table2": {f"{a}_{d}": v for (a, d), v in t2.items()},
+        "table3": {f"{a}_{d}": v for (a, d), v in t3.items()},
+        "parameters": params,
+        "design_section4": design(params),
+    }
+    # The chained word at eight successive 4 KB pages: line homes alternate between the dies by
+    # page, so the fastest is the round trip to the probe SM's own die and the slowest to the
+    # other die (equal on a one-die part).
+    n_lat = 256 if quick else 4096
+    pages = runner._state(8 * 4096)
+    out["latency_ns"] = {}
+    for op in LATENCY_OPS:
+        t = [runner.probe_latency(op, n_lat, scratch=pages.data_ptr() + i * 4096)["ns_per_op"] for i in range(8)]
+        out["latency_ns"][op] = {"near": min(t), "far": max(t)}
+    sweep = {}
+    for op in ("red_add", "atomic_read"):
+        for cont in (True, False):
+            key = f"{op}_{'same' if cont else 'distinct'}_word_ops_per_s"
+            sweep[key] = {str(b): runner.probe_throughput(op, cont, False, b, 128, iters)["ops_per_s"]
+                          for b in SWEEP_BLOCKS if b <= nblocks}
+    out["throughput_vs_blocks"] = sweep
+    die, nd = runner.device_topology()
+    sms = out["sm_count"]
+    line = runner._state(128)
+    rtt = runner.probe_rtt_by_sm(line, 16 if quick else 64)["rtt_ns"]
+    by_die = [rtt[:sms][die[:sms] == d] for d in range(nd)]
+    # one line, homed on one of the dies: the SMs of that die see the near round trip
+    out["dies"] = {"count": nd, "sms_per_die": [int(len(x)) for x in by_die],
+                   "atomic_rtt_ns_to_one_line_by_die_of_sm": [float(np.median(x)) for x in by_die]}
+    ext = measure_extended(nblocks)
+    n_hand = 500 if quick else 2000
+    out["handoff_ns"] = {
+        "near": ext["handoff_near_ns"], "far": ext["handoff_far_ns"],
+        "dsmem": {str(c): runner.probe_cluster(1, c, n_hand)["ns"] for c in CLUSTER_SIZES},
+        "mbarrier": {str(c): runner.probe_cluster(2, c, n_hand)["ns"] for c in CLUSTER_SIZES},
+        "host": runner.probe_host_pingpong(200 if quick else 2000)["handoff_ns"],
+    }
+    out["cluster_barrier_ns"] = {str(c): runner.probe_cluster(0, c, n_hand)["ns"] for c in (1,) + CLUSTER_SIZES}
+    out["fence_ns"] = {k: runner.probe_fence(op, n_hand)["ns_per_fence"] for k, op in FENCE_OPS.items()}
+    slept = runner.probe_nanosleep(list(SLEEP_NS), 8 if quick else 64)
+    out["nanosleep_ns"] = {str(r): float(s) for r, s in zip(SLEEP_NS, slept)}
+    out["extended"] = ext
+    out["design_extended"] = design_extended(params, ext, nblocks)
+    return out
+
+
+def main(argv=None) -> int:
+    import argparse
+    import json
+    p = argparse.ArgumentParser(description="Measure this GPU's machine description (Sections 3-4, extended).")
+    p.add_argument("--out", default="machine.json", help="where to write the JSON description")
+    p.add_argument("--blocks", type=int, default=1184, help="grid of the saturated probes")
+    p.add_argument("--quick", action="store_true", help="short probes: checks that everything runs")
+    a = p.parse_args(argv)
+    desc = measure_all(a.blocks, a.quick)
+    with open(a.out, "w") as f:
+        json.dump(desc, f, indent=1, default=float)
+    print(json.dumps({"design_section4": desc["design_section4"], "design_extended": desc["design_extended"]}))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

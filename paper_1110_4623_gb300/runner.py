@@ -249,8 +249,11 @@ def probe_throughput(op: str, contentious: bool, pre_atomic: bool, nblocks: int,
             "mean_block_ns": float((t[:, 1] - t[:, 0]).mean())}
 
 
-def probe_latency(op: str, iters: int = 4096) -> dict:
-    scratch = _state(256)
+def probe_latency(op: str, iters: int = 4096, scratch=None) -> dict:
+    """Dependent-chain latency of one access kind; scratch: None (a fresh buffer) or the
+    device address of 128 bytes, 128-byte aligned (where the chained word lives)."""
+    if scratch is None:
+        scratch = _state(256)
     out = torch.zeros(2, dtype=torch.int64, device="cuda")
     G.check("gsync_probe_latency", G.gsync_probe_latency(G.PROBE_OPS[op], iters, scratch, out))
     torch.cuda.synchronize()

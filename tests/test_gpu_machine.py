@@ -51,3 +51,35 @@ def test_extended_abstraction_measured_on_this_gpu():
         got = machine.design_extended(params, ext)
         assert got["mutex_without_clusters"] == "cohort"
         assert got["mutex"] == ("cluster" if ext["handoff_dsmem_ns"] < ext["handoff_near_ns"] else "cohort")
+
+
+def test_machine_description_cli(tmp_path):
+    # The whole description (python -m paper_1110_4623_gb300.machine) in its short form: every
+    # section present, every time finite and positive, and its Section 4 choice the oracle's
+    # choice for the Table 1 times it wrote.
+    import json
+    from paper_1110_4623_gb300 import machine
+    out = tmp_path / "machine.json"
+    assert machine.main(["--quick", "--out", str(out)]) == 0
+    d = json.loads(out.read_text())
+    sms = d["sm_count"]
+    assert set(d["table1_ms"]) == set(machine.ROWS)
+    table = {(row, k): v for row, rw in d["table1_ms"].items() for k, v in rw.items()}
+    assert all(v > 0 and math.isfinite(v) for v in table.values())
+    assert d["design_section4"] == classify.design_choice(classify.abstraction(table))
+    assert set(d["latency_ns"]) == set(machine.LATENCY_OPS)
+    assert all(0 < v["near"] <= v["far"] for v in d["latency_ns"].values())
+    for key, per_blocks in d["throughput_vs_blocks"].items():
+        assert list(per_blocks) == [str(b) for b in machine.SWEEP_BLOCKS], key
+        assert all(v > 0 for v in per_blocks.values()), key
+    assert sum(d["dies"]["sms_per_die"]) == sms and d["dies"]["count"] in (1, 2)
+    if d["dies"]["count"] == 2:
+        near, far = sorted(d["dies"]["atomic_rtt_ns_to_one_line_by_die_of_sm"])
+        assert far > near
+    hand = d["handoff_ns"]
+    assert hand["near"] > 0 and hand["far"] > 0 and hand["host"] > 0
+    assert all(v > 0 for v in list(hand["dsmem"].values()) + list(hand["mbarrier"].values()))
+    assert all(v > 0 for v in d["cluster_barrier_ns"].values()) and all(v > 0 for v in d["fence_ns"].values())
+    assert list(d["nanosleep_ns"]) == [str(n) for n in machine.SLEEP_NS]
+    assert d["nanosleep_ns"]["8000"] > d["nanosleep_ns"]["100"]
+    assert d["design_extended"]["mutex"] in ("cluster", "cohort", "ticket", "cas_backoff")

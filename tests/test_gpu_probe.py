@@ -41,6 +41,21 @@ def test_latency_and_handoff_probes():
     assert pp["status"] == 0 and 50 < pp["handoff_ns"] < 20_000
 
 
+@pytest.mark.parametrize("op", ["volatile_load", "load_acquire", "atomic_write", "atomic_add64", "atomic_acqrel"])
+def test_latency_probe_every_value_returning_access(op):
+    # a dependent chain costs at least an L1 hit and less than a far-die round trip plus slack
+    from paper_1110_4623_gb300 import runner
+    assert 5 < runner.probe_latency(op, 1000)["ns_per_op"] < 10_000
+
+
+@pytest.mark.parametrize("op", ["volatile_store", "store_release", "red_add"])
+def test_latency_probe_refuses_accesses_without_a_result(op):
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    with pytest.raises(G.GsyncError):
+        runner.probe_latency(op, 10)
+
+
 def test_nanosleep_probe_monotone_on_average():
     from paper_1110_4623_gb300 import runner
     out = runner.probe_nanosleep([0, 1000, 10000], 32)
