@@ -38,7 +38,8 @@ typedef enum gsync_status {
   GSYNC_ENOTRESIDENT = 2,  /* the grid cannot be co-resident, so a barrier could deadlock */
   GSYNC_ETIMEDOUT = 3,     /* a device wait exceeded the object's timeout */
   GSYNC_ECUDA = 4,         /* a CUDA runtime call failed (see gsync_last_cuda_error) */
-  GSYNC_EABORTED = 5       /* a device wait gave up because another wait timed out */
+  GSYNC_EABORTED = 5       /* a device wait gave up because another wait on the object timed
+                              out, or the host aborted the object (gsync_object_abort) */
 } gsync_status;
 
 /* Bits of the device `status` word that the workload kernels OR in. */
@@ -183,8 +184,20 @@ int gsync_sem_init(void* state, size_t bytes, int kind, int initial_count,
                    const gsync_backoff* backoff, uint64_t timeout_ns, void* stream);
 
 /* Reads an object's abort word (device -> host, synchronous on `stream`): 0 when no wait
- * on the object has timed out. */
+ * on the object has timed out and the host has not aborted it; bit 0 set by a device wait
+ * that timed out, bit 1 by gsync_object_abort. */
 int gsync_object_abort_flag(const void* state, uint32_t* flag_out, void* stream);
+
+/* Host-side abort (the watchdog's lever): sets the object's abort word, so that every wait on
+ * it -- running now or later -- returns GSYNC_EABORTED within a few polls instead of running
+ * to the object's timeout.  A 32-bit stream write (cuStreamWriteValue32) enqueued on
+ * `stream`, asynchronous: the GPU's front end performs it, so it needs no SM (it lands while
+ * a co-resident grid holds every SM) and no host staging.  `stream` must not be ordered after
+ * the kernel that waits: a stream created with cudaStreamNonBlocking, other than the
+ * kernel's.  (Where the driver lacks stream memory operations, a host-to-device copy is used
+ * instead, which lands only if the waiting kernel is not on the legacy default stream.)
+ * gsync_*_init clears the word.  GSYNC_EINVAL for a NULL or misaligned state. */
+int gsync_object_abort(void* state, void* stream);
 
 /* ------------------------------------------------------------------------------------ */
 /* Co-residency (Section 5: the barrier needs every block resident, "persistent threads") */

@@ -54,6 +54,26 @@ int driver_calls(const DriverCalls** out) {
   return GSYNC_OK;
 }
 
+// cuStreamWriteValue32 (32-bit stream memory operations; a driver that lacks them returns
+// CUDA_ERROR_NOT_SUPPORTED from the call, and the caller falls back).
+using StreamWrite32 = CUresult (*)(CUstream, CUdeviceptr, cuuint32_t, unsigned int);
+StreamWrite32 stream_write32() {
+  static StreamWrite32 fn = nullptr;
+  static bool looked = false;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> g(mu);
+  if (!looked) {
+    looked = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuStreamWriteValue32", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (StreamWrite32)p;
+    (void)cudaGetLastError();
+  }
+  return fn;
+}
+
 constexpr uint32_t kLine = 128;
 constexpr uint32_t kMagic = 0x6B5C0000u;
 enum : uint32_t { kPrimMutex = 1, kPrimBarrier = 2, kPrimSem = 3, kPrimCond = 4 };
@@ -329,6 +349,23 @@ int gsync_object_abort_flag(const void* state, uint32_t* flag_out, void* stream)
   cudaStream_t st = (cudaStream_t)stream;
   GSYNC_CUDA(cudaMemcpyAsync(flag_out, (const uint32_t*)state + gsync::kHdrAbort, 4, cudaMemcpyDeviceToHost, st));
   GSYNC_CUDA(cudaStreamSynchronize(st));
+  return GSYNC_OK;
+}
+
+int gsync_object_abort(void* state, void* stream) {
+  if (!state || !aligned(state, kLine)) return GSYNC_EINVAL;
+  constexpr uint32_t kHostAbort = 2u;  // bit 0 is set by a device wait that timed out
+  uint32_t* word = (uint32_t*)state + gsync::kHdrAbort;
+  // A stream write is carried out by the GPU's front end: no SM (a memset kernel could wait
+  // behind the very grid it is meant to stop, which may hold every SM) and no staging of
+  // host memory (a copy from pageable memory waits for the legacy default stream, where the
+  // stuck kernel may be running).
+  if (const StreamWrite32 write = stream_write32())
+    if (write((CUstream)stream, (CUdeviceptr)word, kHostAbort, 0u) == CUDA_SUCCESS) return GSYNC_OK;
+  // Without stream memory operations: a copy from host memory (lands only if the stuck kernel
+  // is not on the legacy default stream).
+  static const uint32_t kValue = kHostAbort;
+  GSYNC_CUDA(cudaMemcpyAsync(word, &kValue, 4, cudaMemcpyHostToDevice, (cudaStream_t)stream));
   return GSYNC_OK;
 }
 

@@ -118,6 +118,7 @@ _SIG = {
     "gsync_sem_init": (ctypes.c_int, [u32p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
                                       ctypes.POINTER(gsync_backoff), ctypes.c_uint64, u32p]),
     "gsync_object_abort_flag": (ctypes.c_int, [u32p, ctypes.POINTER(ctypes.c_uint32), u32p]),
+    "gsync_object_abort": (ctypes.c_int, [u32p, u32p]),
     "gsync_max_coresident_blocks": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                    ctypes.POINTER(ctypes.c_int)]),
     "gsync_device_sm_count": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
@@ -242,6 +243,10 @@ def gsync_object_abort_flag(state, stream=None) -> tuple[int, int]:
     v = ctypes.c_uint32(0)
     rc = lib().gsync_object_abort_flag(ptr(state), ctypes.byref(v), stream_handle(stream))
     return rc, v.value
+
+
+def gsync_object_abort(state, stream=None) -> int:
+    return lib().gsync_object_abort(ptr(state), stream_handle(stream))
 
 
 def gsync_max_coresident_blocks(workload: int, kind: int, block_threads: int, cluster: int = 1) -> tuple[int, int]:

@@ -50,6 +50,42 @@ class StatusView:
 
 # ---------------------------------------------------------------------------------------
 
+class Watchdog:
+    """Host-side watchdog on a stream (the host half of failure detection; the device half is
+    every wait's own deadline).  wait() records an event on `stream` and polls it; if the work
+    queued before it has not finished within `deadline_s`, it sets the abort word of every
+    object in `objects` (gsync_object_abort, on a stream of its own that is not ordered after
+    the watched one), so their waits return GSYNC_EABORTED within a few polls, and then waits
+    for the stream to drain.  Returns True if it had to abort.
+
+    Construct it before launching the work it watches: it creates its own stream and event
+    here, because creating a stream while a kernel runs on the legacy default stream can wait
+    for that kernel -- the very wait the watchdog exists to cut short."""
+
+    def __init__(self, objects, deadline_s: float, stream=None):
+        self.objects = list(objects)
+        self.deadline_s = deadline_s
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.side = torch.cuda.Stream()  # torch creates its pool streams non-blocking
+        self.done = torch.cuda.Event()
+        self.fired = False
+
+    def wait(self, poll_s: float = 0.001) -> bool:
+        import time
+        self.done.record(self.stream)
+        t_end = time.monotonic() + self.deadline_s
+        while not self.done.query():
+            if time.monotonic() > t_end:
+                for obj in self.objects:
+                    G.check("gsync_object_abort", G.gsync_object_abort(obj, self.side))
+                self.fired = True
+                self.side.synchronize()
+                break
+            time.sleep(poll_s)
+        self.done.synchronize()
+        return self.fired
+
+
 class BarrierRun:
     """A barrier object plus the buffers of the barrier workload (gsync_bench_barrier)."""
 

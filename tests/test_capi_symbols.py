@@ -98,6 +98,9 @@ def test_invalid_arguments_rejected_without_gpu(lib_path):
     assert G.lib().gsync_mutex_init_cohort(256, 32768, 32768, None, 0, None) == G.GSYNC_EINVAL
     assert G.lib().gsync_mutex_init_cohort(256, 4096, 64, None, 0, None) == G.GSYNC_EINVAL
     assert G.lib().gsync_device_topology(None, None, None) == G.GSYNC_EINVAL
+    # the host-side abort: null or misaligned state
+    assert G.lib().gsync_object_abort(None, None) == G.GSYNC_EINVAL
+    assert G.lib().gsync_object_abort(0x1004, None) == G.GSYNC_EINVAL
     # the caller-kernel gate rejects a null kernel or a bad shape before any CUDA call
     lib = G.lib()
     n = ctypes.c_int(0)

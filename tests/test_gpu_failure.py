@@ -1,6 +1,7 @@
 """Failure detection without a GPU fault: waits that can never succeed (a lock word that
 nothing releases, a barrier counter that can never reach its target) end at the object's
-timeout, report it in the status word, and leave the context usable."""
+timeout, or sooner when the host-side watchdog aborts the object, report it in the status
+word, and leave the context usable."""
 import numpy as np
 import pytest
 import torch
@@ -62,3 +63,57 @@ def test_semaphore_with_no_free_slot_times_out():
     sr.state.view(torch.int32)[32] = 1000  # count says 1000 holders: every wait must queue
     got = sr.run()
     assert got["status"] & G.GSYNC_STATUS_TIMEOUT
+
+
+def _timed_watch(wd):
+    import time
+    t0 = time.monotonic()
+    fired = wd.wait()
+    return fired, time.monotonic() - t0
+
+
+def test_watchdog_aborts_a_lock_that_is_never_released():
+    # The object's own timeout is 3 s; the watchdog gives up after 0.1 s and the kernel must
+    # return well before the timeout could end it.
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    delay, add = inputs.mutex_inputs(64, 4, 2, max_delay=0)
+    mr = runner.MutexRun("ticket", 64, 128, 4, 8, delay, add, bo=runner.backoff(min_ns=100, max_ns=1000),
+                         timeout_ns=3_000_000_000)
+    mr.reset()
+    mr.state.view(torch.int32)[2 * 32] = 0x40000000  # a turn no ticket reaches
+    wd = runner.Watchdog([mr.state], 0.1)
+    assert mr.launch() == 0
+    fired, elapsed = _timed_watch(wd)
+    got = mr.results()
+    assert fired and elapsed < 1.5, elapsed
+    assert got["status"] & G.GSYNC_STATUS_ABORTED and got["total"] == 0
+    assert G.gsync_object_abort_flag(mr.state)[1] & 2  # set by the host
+    ok = runner.MutexRun("ticket", 64, 128, 4, 8, delay, add).run()
+    assert ok["status"] == 0 and ok["total"] == 256
+
+
+def test_watchdog_aborts_a_barrier_that_cannot_complete():
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    br = runner.BarrierRun("atomic", 64, 128, 10, full=False, timeout_ns=3_000_000_000)
+    br.status.zero_()
+    br.state.view(torch.int32)[32] = 1_000_000  # arrival counter already past every target: nobody is last
+    wd = runner.Watchdog([br.state], 0.1)
+    assert br.launch() == 0
+    fired, elapsed = _timed_watch(wd)
+    torch.cuda.synchronize()
+    assert fired and elapsed < 1.5, elapsed
+    assert int(br.status.cpu()[0]) & G.GSYNC_STATUS_ABORTED
+
+
+def test_watchdog_stays_quiet_on_work_that_finishes():
+    from paper_1110_4623_gb300 import runner
+    delay, add = inputs.mutex_inputs(296, 20, 3)
+    mr = runner.MutexRun("cluster", 296, 256, 20, 64, delay, add, cluster=4)
+    mr.reset()
+    wd = runner.Watchdog([mr.state], 10.0)
+    assert mr.launch() == 0
+    fired, _ = _timed_watch(wd)
+    got = mr.results()
+    assert not fired and got["status"] == 0 and got["total"] == 296 * 20
