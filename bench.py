@@ -52,6 +52,8 @@ MUTEX_CONFIGS = [("cas_spin", "cas_spin", 0, None, 0), ("cas_backoff", "cas_back
                  ("sleep_queue", "sleep_queue", 0, None, 0), ("ring", "ring", 0, None, 0),
                  ("cohort", "cohort", 0, (128, 4000), 0), ("cluster", "cluster", 0, (128, 4000), 0)]
 SEM_BACKOFF = (16, 2000)
+SEM_STEP_KINDS = ("window", "ticket")  # the library's default (the ticket window), then the paper's FA semaphore
+DEFAULT_SEM = "window"
 # Batched many-mutex workload: 4096 keys, Zipf(1.1), 1e6 acquisitions, 64 barrier groups.
 BATCH_KEYS, BATCH_ACQ, BATCH_GROUPS, BATCH_ROUNDS, BATCH_THREADS = 4096, 1_000_000, 64, 100, 128
 METRIC = "lock acquires/s & barrier ns at 1184 blocks vs L2-atomic roofline; p99 latency"
@@ -285,13 +287,14 @@ class GpuStep:
         self.barrier = {(k, p): runner.BarrierRun(k, NBLOCKS, BAR_THREADS, BAR_ROUNDS, full=False, param=p,
                                                   timeout_ns=TIMEOUT_NS) for k, p in BARRIERS}
         self.sem = {}
-        for n in SEM_COUNTS:
-            hold, add = inputs.sem_inputs(NBLOCKS, SEM_PAIRS, inputs.SEED_SEM ^ (n << 16) ^ NBLOCKS)
-            bo = runner.backoff(min_ns=SEM_BACKOFF[0], max_ns=SEM_BACKOFF[1])
-            self.sem[n] = (runner.SemRun("ticket", NBLOCKS, SEM_THREADS, SEM_PAIRS, n, hold, add, bo=bo,
-                                         timeout_ns=TIMEOUT_NS), add)
+        for kind in SEM_STEP_KINDS:
+            for n in SEM_COUNTS:
+                hold, add = inputs.sem_inputs(NBLOCKS, SEM_PAIRS, inputs.SEED_SEM ^ (n << 16) ^ NBLOCKS)
+                bo = runner.backoff(min_ns=SEM_BACKOFF[0], max_ns=SEM_BACKOFF[1])
+                self.sem[(kind, n)] = (runner.SemRun(kind, NBLOCKS, SEM_THREADS, SEM_PAIRS, n, hold, add, bo=bo,
+                                                     timeout_ns=TIMEOUT_NS), add)
         ev = lambda: torch.cuda.Event(enable_timing=True)
-        self.ev = {key: (ev(), ev()) for key in list(self.mutex) + list(self.barrier) + [("sem", n) for n in SEM_COUNTS]}
+        self.ev = {key: (ev(), ev()) for key in list(self.mutex) + list(self.barrier) + [("sem",) + k for k in self.sem]}
         self.launches = 0
 
     def launch(self):
@@ -313,13 +316,13 @@ class GpuStep:
             b.record()
             assert rc == 0, (key, rc)
             launches += 1
-        for n, (sr, _) in self.sem.items():
+        for key, (sr, _) in self.sem.items():
             sr.reset()
-            a, b = self.ev[("sem", n)]
+            a, b = self.ev[("sem",) + key]
             a.record()
             rc = sr.launch()
             b.record()
-            assert rc == 0, (n, rc)
+            assert rc == 0, (key, rc)
             launches += 1
         self.launches = launches
 
@@ -340,11 +343,11 @@ class GpuStep:
             mix = br.mix.cpu().numpy().view(np.uint32)
             if st or br.bad.cpu().numpy().any() or not np.array_equal(mix, want_mix):
                 bad.append(f"barrier {key}")
-        for n, (sr, add) in self.sem.items():
+        for (kind, n), (sr, add) in self.sem.items():
             got = sr.results()
             want = calc.sem_final(NBLOCKS, SEM_PAIRS, n, add)
             if got["status"] or got["tally"] != want["tally"] or got["max_occ"] > n:
-                bad.append(f"sem n={n}")
+                bad.append(f"sem {kind} n={n}")
         return bad
 
 
@@ -616,12 +619,15 @@ def run_gpu(args):
         roof = barrier_roof_ns(terms, k, p if k in ("die", "split", "count") else max(p, 1), NBLOCKS)
         barrier[barrier_name(k, p)] = {"ns_per_crossing": ns, "roof_ns": roof, "frac": roof / ns}
     bkey = barrier_name(*DEFAULT_BARRIER)
-    sem = {}
-    for n in SEM_COUNTS:
-        ms = med[("sem", n)]
-        ops = NBLOCKS * SEM_PAIRS / (ms * 1e-3)
-        roof = sem_roof_ops_s(terms, n)
-        sem[str(n)] = {"ops_per_s": ops, "roof_ops_per_s": roof, "frac": ops / roof}
+    sem_kinds = {}
+    for kind in SEM_STEP_KINDS:
+        sem_kinds[kind] = {}
+        for n in SEM_COUNTS:
+            ms = med[("sem", kind, n)]
+            ops = NBLOCKS * SEM_PAIRS / (ms * 1e-3)
+            roof = sem_roof_ops_s(terms, n)
+            sem_kinds[kind][str(n)] = {"ops_per_s": ops, "roof_ops_per_s": roof, "frac": ops / roof}
+    sem = sem_kinds[DEFAULT_SEM]
 
     # Section 4's rule plus its GB300 extensions (dies, hand-off gap, same-word atomic cost),
     # applied to this GPU's measurements, beside the defaults the sweeps chose.
@@ -629,7 +635,8 @@ def run_gpu(args):
     ext = machine.measure_extended(NBLOCKS)
     params = machine.abstraction(machine.measure_table(NBLOCKS, 128, 1000, reps=1))
     design_rule = {"section4": machine.design(params), "extended": machine.design_extended(params, ext, NBLOCKS),
-                   "measured": ext, "defaults": {"mutex": DEFAULT_MUTEX, "barrier": barrier_name(*DEFAULT_BARRIER)}}
+                   "measured": ext, "defaults": {"mutex": DEFAULT_MUTEX, "barrier": barrier_name(*DEFAULT_BARRIER),
+                                                  "sem": DEFAULT_SEM}}
     out = {
         "metric": METRIC, "value": value, "unit": "acq/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -654,7 +661,7 @@ def run_gpu(args):
         "barrier": {"default": bkey, "ns_per_crossing": barrier[bkey]["ns_per_crossing"],
                     "frac": barrier[bkey]["frac"], "kinds": barrier},
         "mutex": mutex,
-        "semaphore": {"kind": "ticket", "backoff_ns": list(SEM_BACKOFF), "n": sem},
+        "semaphore": {"kind": DEFAULT_SEM, "backoff_ns": list(SEM_BACKOFF), "n": sem, "kinds": sem_kinds},
         "roofline_terms": terms,
         "design_rule": design_rule,
         "paper_context": paper_context(terms, barrier, mutex),

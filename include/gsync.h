@@ -87,7 +87,10 @@ typedef enum gsync_barrier_kind {
 typedef enum gsync_sem_kind {
   GSYNC_SEM_TICKET = 0,       /* sleeping FA semaphore: <= 2 atomics per wait and per post */
   GSYNC_SEM_SPIN = 1,         /* spin-lock semaphore: S = X + 1, swap with 0 to update */
-  GSYNC_SEM_SPIN_BACKOFF = 2  /* the same with backoff in wait (not in post) */
+  GSYNC_SEM_SPIN_BACKOFF = 2, /* the same with backoff in wait (not in post) */
+  GSYNC_SEM_WINDOW = 3        /* ticket window (GB300 alternative): wait takes a ticket t and
+                                 enters once turn + n > t; post is one fire-and-forget add to
+                                 turn, with no round trip */
 } gsync_sem_kind;
 
 /* Backoff policy (Section 5: "Backoff"; the paper's counter I runs from Imin to Imax by +1

@@ -617,6 +617,11 @@ __device__ __forceinline__ int cond_wait(const CondRef& cv, const MutexRef& m, T
 // ---------------------------------------------------------------------------------------
 // TICKET (sleeping): line 1 count, line 2 ticket, line 3 turn; header N = max count.
 // SPIN / SPIN_BACKOFF: line 1 S (initially N + 1; 0 while a block updates it).
+// WINDOW: line 1 ticket, line 2 turn (the number of posts); the holders are the tickets in
+//   [turn, turn + N).  Not in the paper: its FA semaphore's post must learn from the count
+//   whether anyone waits (a round trip to L2) before it may advance the turn; here the post
+//   only advances the turn, and the wait pays for it with a load of the turn issued beside
+//   its ticket fetch-and-add.
 struct SemRef {
   uint32_t* s;
   uint32_t kind, n;
@@ -658,6 +663,23 @@ __device__ __forceinline__ int sem_wait_thread(const SemRef& s) {
       }
     }
     return GSYNC_OK;
+  } else if (KIND == GSYNC_SEM_WINDOW) {
+    // The load of the turn does not wait for the ticket's return (the fetch-and-add is
+    // relaxed; the acquire is the load's).  A turn read early is smaller, so it can only
+    // delay the entry, never allow one too many.
+    const uint32_t t = ptx::atom_add_relaxed(s.word(1), 1u);
+    uint32_t turn = ptx::ld_acquire(s.word(2));
+    while (!after(turn + s.n, t)) {
+      if (int rc = w.tick(s.timeout_ns, s.abort_word())) return rc;
+      // Sleep in proportion to the holders that must leave before this ticket's turn.
+      const uint32_t ahead = t - (turn + s.n) + 1u;
+      if (s.bo.min_ns && ahead < 0x80000000u) {
+        const uint32_t ns = ahead * s.bo.min_ns;
+        __nanosleep(ns < s.bo.max_ns ? ns : s.bo.max_ns);
+      }
+      turn = ptx::ld_acquire(s.word(2));
+    }
+    return GSYNC_OK;
   } else {
     uint32_t sleep_ns = s.bo.min_ns;
     for (;;) {
@@ -683,6 +705,9 @@ __device__ __forceinline__ int sem_post_thread(const SemRef& s) {
     ptx::fence_acq_rel();
     const uint32_t old = ptx::atom_add_relaxed(s.word(1), 0xFFFFFFFFu);
     if ((int32_t)old > (int32_t)s.n) ptx::red_add_relaxed(s.word(3), 1u);
+    return GSYNC_OK;
+  } else if (KIND == GSYNC_SEM_WINDOW) {
+    ptx::red_add_release(s.word(2), 1u);  // no return trip: the poster goes on at once
     return GSYNC_OK;
   } else {
     Waiter w;

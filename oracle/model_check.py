@@ -507,6 +507,42 @@ class SleepSem:
         raise AssertionError(pc)
 
 
+class WindowSem:
+    """Ticket-window semaphore (the library's GB300 alternative to the FA semaphore of Section 5):
+    wait takes t <- fetch-and-add(ticket, 1) and enters once turn + N > t (signed difference),
+    polling turn; post adds 1 to turn and nothing else.  Holders are tickets in
+    [turn, turn + N), so at most N are inside, in ticket order of admission windows.  A stale
+    read of turn is smaller, so it only delays an entry: the model reads turn after taking
+    the ticket, the latest value it could see.
+    broken="window_ge" enters once turn + N >= t (one holder too many)."""
+    kind, fifo = "sem", False
+
+    def __init__(self, n=1, base=0, broken=None):
+        self.capacity, self.base, self.broken = n, base & M32, broken
+
+    def init(self, nproc, ops):
+        return (self.base, self.base), tuple((0, 0, 0) for _ in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, t = loc
+        ticket, turn = sh
+        N = self.capacity
+        if pc == 0:
+            return (1, k, ticket), (inc(ticket), turn), None
+        if pc == 1:
+            edge = (turn + N) & M32
+            ok = s_ge(edge, t) if self.broken == "window_ge" else s_gt(edge, t)
+            return ((PC_ENTER if ok else 1), k, t), sh, None
+        if pc == PC_ENTER:
+            return (PC_EXIT, k, t), sh, ("enter", None)
+        if pc == PC_EXIT:
+            return (3, k, t), sh, ("exit",)
+        if pc == 3:
+            k += 1
+            return ((0 if k < ops else DONE), k, t), (ticket, inc(turn)), None
+        raise AssertionError(pc)
+
+
 # --------------------------------------------------------------------------------------------
 # Barriers.  Events: ("arrive",) when a block arrives, ("pass",) when it leaves the barrier.
 # --------------------------------------------------------------------------------------------

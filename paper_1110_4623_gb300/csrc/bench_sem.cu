@@ -85,6 +85,7 @@ KernelFn pick(int kind) {
     case GSYNC_SEM_TICKET: return sem_workload_kernel<GSYNC_SEM_TICKET>;
     case GSYNC_SEM_SPIN: return sem_workload_kernel<GSYNC_SEM_SPIN>;
     case GSYNC_SEM_SPIN_BACKOFF: return sem_workload_kernel<GSYNC_SEM_SPIN_BACKOFF>;
+    case GSYNC_SEM_WINDOW: return sem_workload_kernel<GSYNC_SEM_WINDOW>;
   }
   return nullptr;
 }

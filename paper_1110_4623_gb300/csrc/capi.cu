@@ -317,7 +317,7 @@ int gsync_barrier_init(void* state, size_t bytes, int kind, int nblocks, int par
 }
 
 size_t gsync_sem_bytes(int kind) {
-  if (kind < GSYNC_SEM_TICKET || kind > GSYNC_SEM_SPIN_BACKOFF) return 0;
+  if (kind < GSYNC_SEM_TICKET || kind > GSYNC_SEM_WINDOW) return 0;
   return 4 * kLine;
 }
 
@@ -329,7 +329,8 @@ int gsync_sem_init(void* state, size_t bytes, int kind, int initial_count, const
   InitSpec spec;
   fill_header(spec, kPrimSem, (uint32_t)kind, (uint32_t)initial_count, 0, backoff, timeout_ns, 0);
   spec.nwords = (uint32_t)(need / 4);
-  spec.spin_sem_s = kind == GSYNC_SEM_TICKET ? 0u : (uint32_t)initial_count + 1u;
+  const bool spin = kind == GSYNC_SEM_SPIN || kind == GSYNC_SEM_SPIN_BACKOFF;
+  spec.spin_sem_s = spin ? (uint32_t)initial_count + 1u : 0u;
   return launch_init(state, bytes, spec, (cudaStream_t)stream);
 }
 

@@ -21,7 +21,7 @@ GSYNC_STATUS_TIMEOUT, GSYNC_STATUS_ABORTED, GSYNC_STATUS_VIOLATION, GSYNC_STATUS
 MUTEX_KINDS = {"cas_spin": 0, "cas_backoff": 1, "ticket": 2, "sleep_queue": 3, "cohort": 4, "ring": 5, "cluster": 6}
 COHORT_DEFAULT_BUDGET = 64
 BARRIER_KINDS = {"atomic": 0, "flag": 1, "tree": 2, "cluster": 3, "sharded": 4, "die": 5, "split": 6, "count": 7}
-SEM_KINDS = {"ticket": 0, "spin": 1, "spin_backoff": 2}
+SEM_KINDS = {"ticket": 0, "spin": 1, "spin_backoff": 2, "window": 3}
 BACKOFF_EXPONENTIAL, BACKOFF_LINEAR_CYCLIC, BACKOFF_SPIN_THEN_SLEEP = 0, 1, 2
 PROBE_OPS = {"volatile_load": 0, "volatile_store": 1, "atomic_read": 2, "atomic_write": 3,
              "load_acquire": 4, "load_relaxed": 5, "store_release": 6, "red_add": 7,

@@ -100,8 +100,17 @@ def measure_extended(nblocks: int = 1184) -> dict:
     fence = runner.probe_fence(0)["ns_per_fence"]
     r_same = runner.probe_throughput("red_add", True, False, nblocks, 128, 2000)["ops_per_s"]
     dsmem = runner.probe_cluster(1, 2, 2000)["ns"]
+    # the atomic round trip to a line homed on the probe's own die (fastest of eight pages)
+    pages = runner._state(8 * 4096)
+    rtt = min(runner.probe_latency("atomic_read", 1000, scratch=pages.data_ptr() + i * 4096)["ns_per_op"]
+              for i in range(8))
     return {"dies": nd, "handoff_near_ns": near, "handoff_far_ns": far, "handoff_dsmem_ns": dsmem,
-            "fence_ns": fence, "atomic_same_ns": 1e9 / r_same}
+            "fence_ns": fence, "atomic_same_ns": 1e9 / r_same, "atomic_rtt_ns": rtt}
+
+
+# An atomic round trip this large a part of a hand-off makes the ticket-window semaphore pay:
+# its post advances the turn without the FA semaphore's round trip to the count.
+WINDOW_RTT_FRACTION = 0.25
 
 
 def design_extended(params: dict, ext: dict, nblocks: int = 1184) -> dict:
@@ -109,7 +118,9 @@ def design_extended(params: dict, ext: dict, nblocks: int = 1184) -> dict:
     cross-die hand-off is DIE_GAP_NS slower (mutex_without_clusters), and over thread-block
     clusters when a hand-off through distributed shared memory beats the on-die L2 one and the
     kernel can launch in clusters (mutex); the counting barrier when `nblocks` serialized
-    same-word atomics cost less than the two hand-offs of the flag barrier's extra stage."""
+    same-word atomics cost less than the two hand-offs of the flag barrier's extra stage; the
+    ticket-window semaphore when an atomic round trip exceeds WINDOW_RTT_FRACTION of the
+    on-die hand-off."""
     choice = dict(design(params))
     if ext["dies"] == 2 and ext["handoff_far_ns"] - ext["handoff_near_ns"] > DIE_GAP_NS:
         choice["mutex"] = "cohort"
@@ -118,6 +129,8 @@ def design_extended(params: dict, ext: dict, nblocks: int = 1184) -> dict:
         choice["mutex"] = "cluster"
     if nblocks * ext["atomic_same_ns"] < 2.0 * ext["handoff_near_ns"]:
         choice["barrier"] = "count"
+    if ext.get("atomic_rtt_ns", 0.0) > WINDOW_RTT_FRACTION * ext["handoff_near_ns"]:
+        choice["sem_low"] = choice["sem_high"] = "window"
     return choice
 
 

@@ -34,9 +34,9 @@ def _barrier(kind, param, rounds=200):
     return lambda: G.check("gsync_bench_barrier", r.launch())
 
 
-def _sem(n, pairs=20):
+def _sem(n, pairs=20, kind="ticket"):
     hold, add = inputs.sem_inputs(NB, pairs, inputs.SEED_SEM ^ (n << 16) ^ NB)
-    r = runner.SemRun("ticket", NB, 128, pairs, n, hold, add, bo=runner.backoff(min_ns=16, max_ns=2000),
+    r = runner.SemRun(kind, NB, 128, pairs, n, hold, add, bo=runner.backoff(min_ns=16, max_ns=2000),
                       timeout_ns=10_000_000_000)
     return lambda: G.check("gsync_bench_sem", r.launch())
 
@@ -68,6 +68,7 @@ CASES = {
     "barrier_cluster2": lambda: _barrier("cluster", 2),
     "barrier_count8": lambda: _barrier("count", 8),
     "sem_ticket_n4": lambda: _sem(4),
+    "sem_window_n4": lambda: _sem(4, kind="window"),
     "batched_200k": lambda: _batched(),
     "condvar_cohort": lambda: _condvar(),
 }

@@ -82,7 +82,7 @@ def test_size_queries_without_gpu(lib_path):
     assert G.gsync_mutex_bytes(G.MUTEX_KINDS["cluster"], 4) == 3 * 128  # the global lock; local locks live in smem
     assert G.gsync_mutex_bytes(7, 4) == 0
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["cluster"], 1183, 8) == 0
-    assert G.gsync_sem_bytes(0) == 4 * 128 and G.gsync_sem_bytes(3) == 0
+    assert G.gsync_sem_bytes(0) == 4 * 128 and G.gsync_sem_bytes(3) == 4 * 128 and G.gsync_sem_bytes(4) == 0
     assert G.gsync_bench_mutex_workspace_bytes(2, 1184, 100, 1024) > 4 * 1184 * 100 * 4
     assert G.gsync_probe_cs_scratch_bytes(64, 1000) > 0
 

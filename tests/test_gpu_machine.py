@@ -51,6 +51,8 @@ def test_extended_abstraction_measured_on_this_gpu():
         got = machine.design_extended(params, ext)
         assert got["mutex_without_clusters"] == "cohort"
         assert got["mutex"] == ("cluster" if ext["handoff_dsmem_ns"] < ext["handoff_near_ns"] else "cohort")
+        window = ext["atomic_rtt_ns"] > machine.WINDOW_RTT_FRACTION * ext["handoff_near_ns"]
+        assert got["sem_high"] == ("window" if window else machine.design(params)["sem_high"])
 
 
 def test_machine_description_cli(tmp_path):

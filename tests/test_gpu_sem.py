@@ -9,7 +9,7 @@ from paper_1110_4623_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-KINDS = ["ticket", "spin", "spin_backoff"]
+KINDS = ["ticket", "spin", "spin_backoff", "window"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -44,8 +44,8 @@ def test_semaphore_full_size(kind, n_init, nblocks):
     # so that kind runs a bounded sample of 10 pairs per block at 1184 blocks.
     pairs = 10 if (kind == "spin" and nblocks > 296) else 200
     got = run(kind, nblocks, pairs, n_init, timeout_ns=30_000_000_000)
-    if kind == "ticket" and nblocks >= 296:
-        # Under load the sleeping semaphore fills every slot.
+    if kind in ("ticket", "window") and nblocks >= 296:
+        # Under load the sleeping semaphores fill every slot.
         assert got["max_occ"] == n_init
 
 
@@ -53,3 +53,24 @@ def test_semaphore_full_size(kind, n_init, nblocks):
 @pytest.mark.parametrize("nblocks,pairs,n_init", [(1, 10, 1), (5, 7, 8), (37, 13, 3), (300, 3, 299)])
 def test_ragged(kind, nblocks, pairs, n_init):
     run(kind, nblocks, pairs, n_init, hold_lo=0, hold_hi=500, threads=96)
+
+
+@pytest.mark.parametrize("n_init", [1, 16])
+def test_window_semaphore_with_sleep_and_wrapping_counters(n_init):
+    # The ticket and turn words start 100 below 2^32, so both wrap during the run; waiters
+    # sleep in proportion to the holders ahead of them.
+    import torch
+    from paper_1110_4623_gb300 import runner
+    nblocks, pairs = 296, 50
+    hold, add = inputs.sem_inputs(nblocks, pairs, 77 + n_init, 100, 2000)
+    sr = runner.SemRun("window", nblocks, 128, pairs, n_init, hold, add, bo=runner.backoff(min_ns=16, max_ns=2000),
+                       timeout_ns=10_000_000_000)
+    words = sr.state.view(torch.int32)
+    words[32] = -100  # ticket
+    words[64] = -100  # turn
+    got = sr.run()
+    want = calc.sem_final(nblocks, pairs, n_init, add)
+    assert got["status"] == 0 and np.array_equal(got["count"], want["count"]) and got["tally"] == want["tally"]
+    assert 1 <= got["max_occ"] <= n_init and got["occupancy"] == 0
+    if n_init == 1:
+        assert got["total"] == want["total"]

@@ -22,7 +22,7 @@ ONE_DIE_SLOW_ATOMICS = {"dies": 1, "handoff_near_ns": 1500.0, "handoff_far_ns": 
 # GB300 as measured: 477 ns on-die hand-off, ~770 ns across dies, 385 ns inside a cluster
 # through distributed shared memory, 0.64 ns same-word atomics.
 GB300 = {"dies": 2, "handoff_near_ns": 477.0, "handoff_far_ns": 770.0, "handoff_dsmem_ns": 385.0, "fence_ns": 160.0,
-         "atomic_same_ns": 0.64}
+         "atomic_same_ns": 0.64, "atomic_rtt_ns": 197.0}
 
 
 def test_paper_machines_keep_the_paper_choice():
@@ -37,7 +37,7 @@ def test_gb300_measurements_pick_cohort_and_count():
     params = machine.abstraction(times("tesla"))  # the atomic:volatile class GB300 falls in
     got = machine.design_extended(params, GB300, nblocks=1184)
     assert got["mutex"] == "cluster" and got["mutex_without_clusters"] == "cohort" and got["barrier"] == "count"
-    assert got["sem_high"] == machine.design(params)["sem_high"]
+    assert got["sem_low"] == got["sem_high"] == "window"
 
 
 def test_each_extension_needs_its_own_condition():
@@ -51,3 +51,6 @@ def test_each_extension_needs_its_own_condition():
     # a cluster hand-off no faster than the on-die one: the die cohort stays the choice
     got = machine.design_extended(params, dict(GB300, handoff_dsmem_ns=500.0))
     assert got["mutex"] == "cohort"
+    # an atomic round trip small next to a hand-off: the paper's semaphore stays
+    got = machine.design_extended(params, dict(GB300, atomic_rtt_ns=100.0))
+    assert got["sem_high"] == machine.design(params)["sem_high"] and got["sem_low"] == machine.design(params)["sem_low"]

@@ -34,6 +34,10 @@ CORRECT = [
     ("sleep_sem_1", mc.SleepSem(n=1), 3, 2),
     ("sleep_sem_2", mc.SleepSem(n=2), 3, 2),
     ("sleep_sem_wrap", mc.SleepSem(n=1, base=W), 3, 2),
+    ("window_sem_1", mc.WindowSem(n=1), 3, 2),
+    ("window_sem_2", mc.WindowSem(n=2), 3, 2),
+    ("window_sem_2_of_4", mc.WindowSem(n=2), 4, 2),
+    ("window_sem_wrap", mc.WindowSem(n=2, base=W), 3, 3),
     ("atomic_barrier", mc.AtomicBarrier(), 3, 2),
     ("atomic_barrier_wrap", mc.AtomicBarrier(base=2 ** 32 - 1), 3, 3),
     ("atomic_barrier_parity", mc.AtomicBarrier(parity=True), 4, 3),
@@ -88,6 +92,7 @@ BROKEN = [
     ("cohort3_pass_always", mc.CohortMutex(broken="pass_always", groups=3), 3, 2, "final state"),
     ("cohort3_skip_ticket", mc.CohortMutex(broken="skip_ticket", groups=3), 4, 2, "local ticket"),
     ("sleep_sem_turn_ge", mc.SleepSem(n=1, broken="turn_ge"), 3, 1, "critical section"),
+    ("window_sem_ge", mc.WindowSem(n=2, broken="window_ge"), 3, 1, "critical section"),
     ("barrier_no_wait", mc.AtomicBarrier(broken="no_wait"), 3, 1, "passed round"),
     ("barrier_late_reset_one_counter", mc.AtomicBarrier(broken="reset_one_counter"), 2, 3, "deadlock"),
     ("flag_skip_last", mc.FlagBarrier(broken="skip_last"), 3, 1, "passed round"),
