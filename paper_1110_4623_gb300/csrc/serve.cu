@@ -1,5 +1,5 @@
 // Persistent serving loop with continuous batching, built on the library's own ticket lock and
-// sleeping semaphore (the paper motivates its primitives with task queues, Section 1, and
+// ticket-window semaphore (the paper motivates its primitives with task queues, Section 1, and
 // names hardware enqueue/dequeue as a wish, Section 7).
 //
 // The host publishes requests into a ring of 16-byte entries in pinned host memory (each
@@ -67,7 +67,7 @@ struct Args {
   uint32_t* done;            // device view of host completion flags
   const int32_t* pool;
   uint32_t* ring_lock;       // gsync mutex (TICKET)
-  uint32_t* admit_sem;       // gsync semaphore (TICKET), n = nslots
+  uint32_t* admit_sem;       // gsync semaphore (WINDOW), n = nslots
   Slot* slots;
   uint32_t* active_mask;     // one bit per slot (nslots <= 64)
   uint32_t* stats;           // [0] admitted, [32] chunks, [64] completed (own lines)
@@ -188,10 +188,10 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(Args a) {
     if (tid == 0) {
       for (;;) {
         if (ptx::ld_relaxed(a.dev_shutdown)) break;
-        int rc = gsync::sem_wait_thread<GSYNC_SEM_TICKET>(sem);
+        int rc = gsync::sem_wait_thread<GSYNC_SEM_WINDOW>(sem);
         if (rc != GSYNC_OK) { record_status(a.status, rc); break; }
         if (ptx::ld_relaxed(a.dev_shutdown)) {  // pass the permit on so blocked admitters exit too
-          gsync::sem_post_thread<GSYNC_SEM_TICKET>(sem);
+          gsync::sem_post_thread<GSYNC_SEM_WINDOW>(sem);
           break;
         }
         // The ring's head index is the ticket of the ring lock: tickets are handed out in
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(Args a) {
           }
         }
         if (stop) {  // the permit goes back so that admitters blocked on it can see shutdown
-          gsync::sem_post_thread<GSYNC_SEM_TICKET>(sem);
+          gsync::sem_post_thread<GSYNC_SEM_WINDOW>(sem);
           break;
         }
         const uint32_t req_len = v.y, req_off = v.z, req_id = h;
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(Args a) {
         st_relaxed_sys_s64(a.res + id, total);
         st_release_sys(a.done + id, 1u);
         ptx::st_release(&sl->state, 0u);
-        gsync::sem_post_thread<GSYNC_SEM_TICKET>(sem);
+        gsync::sem_post_thread<GSYNC_SEM_WINDOW>(sem);
         ptx::red_add_relaxed(a.stats + 64, 1u);
       }
     }
@@ -444,7 +444,7 @@ extern "C" int gsync_serve_run(const gsync_serve_cfg* cfg, gsync_serve_buffers* 
   const uint64_t wait_ns = (cfg->timeout_ns ? cfg->timeout_ns : 2000000000ull) * 16;
   if (int rc = gsync_mutex_init(ring_lock, 3 * 128, GSYNC_MUTEX_TICKET, 1, nullptr, wait_ns, stream)) return rc;
   gsync_backoff sbo = {GSYNC_BACKOFF_EXPONENTIAL, 64, 2000, 0};
-  if (int rc = gsync_sem_init(sem, 4 * 128, GSYNC_SEM_TICKET, cfg->nslots, &sbo, wait_ns, stream)) return rc;
+  if (int rc = gsync_sem_init(sem, 4 * 128, GSYNC_SEM_WINDOW, cfg->nslots, &sbo, wait_ns, stream)) return rc;
 
   // The host threads write these arrays on the latency path: touch every page first.
   for (int q = 0; q < cfg->nreq; ++q) buf->latency_ns[q] = 0;
