@@ -73,7 +73,39 @@ def parse():
     p.add_argument("--impl", default="gsync", choices=["gsync", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the batched and serving sections")
+    p.add_argument("--jsonl", default=None, help="also append one JSON row per measured configuration to this file")
     return p.parse_args()
+
+
+def result_rows(out):
+    """The bench line flattened into one row per measured configuration (section, kind, grid,
+    parameter): rate or time, roofline and its fraction, latency percentiles."""
+    grid = out["config"].get("nblocks")
+    rows = []
+    for kind, per_cs in out.get("mutex", {}).items():
+        for cs, r in per_cs.items():
+            rows.append({"section": "mutex", "kind": kind, "nblocks": grid, "cs_words": int(cs),
+                         "acq_per_s": r["acq_per_s"], "roof_acq_per_s": r["roof_acq_per_s"], "frac": r["frac"]})
+    for kind, r in out.get("barrier", {}).get("kinds", {}).items():
+        rows.append({"section": "barrier", "kind": kind, "nblocks": grid, "ns_per_crossing": r["ns_per_crossing"],
+                     "roof_ns": r["roof_ns"], "frac": r["frac"]})
+    for kind, per_n in out.get("semaphore", {}).get("kinds", {}).items():
+        for n, r in per_n.items():
+            rows.append({"section": "semaphore", "kind": kind, "nblocks": grid, "n": int(n),
+                         "ops_per_s": r["ops_per_s"], "roof_ops_per_s": r["roof_ops_per_s"], "frac": r["frac"]})
+    for kind, r in out.get("condvar", {}).get("mutex", {}).items():
+        rows.append({"section": "condvar", "kind": kind, "items_per_s": r["items_per_s"], "frac": r["frac"]})
+    for arm in ("default", "tuned"):
+        r = out.get("batched", {}).get(arm)
+        if r:
+            rows.append({"section": "batched", "kind": arm, "acq_per_s": r["acq_per_s"], "cluster": r["cluster"]})
+    for rate, r in out.get("serving", {}).get("rates", {}).items():
+        for arm in ("persistent", "per_request_launch"):
+            a = r[arm]
+            rows.append({"section": "serving", "kind": arm, "offered_req_s": float(rate),
+                         "achieved_req_s": a["achieved_req_s"], "p50_us": a["p50_us"], "p99_us": a["p99_us"]})
+    stamp = {"clocks_sm_mhz": out.get("clocks", {}).get("sm_mhz"), "n_gpus": out.get("n_gpus")}
+    return [dict(row, **stamp) for row in rows]
 
 
 def dist_env():
@@ -686,6 +718,10 @@ def run_gpu(args):
                                          "per_request_launch_at_1e5_req_s": r5["per_request_launch"]["p99_us"]}
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(inputs, DEFAULT_MUTEX)
+        if args.jsonl:
+            with open(args.jsonl, "a") as f:
+                for row in result_rows(out):
+                    f.write(json.dumps(row, default=float) + "\n")
         print(json.dumps(out, default=float))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -1,0 +1,36 @@
+"""The bench line's results log (--jsonl): one row per measured configuration, with the
+rate or time, its roofline and fraction (host logic on a synthetic line, no GPU)."""
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def test_rows_cover_every_measured_configuration():
+    import bench
+    out = {
+        "config": {"nblocks": 1184}, "n_gpus": 1, "clocks": {"sm_mhz": 2070.0},
+        "mutex": {"ticket": {"0": {"acq_per_s": 8e5, "roof_acq_per_s": 1e6, "frac": 0.8},
+                             "64": {"acq_per_s": 7e5, "roof_acq_per_s": 1e6, "frac": 0.7}}},
+        "barrier": {"kinds": {"count8": {"ns_per_crossing": 2200.0, "roof_ns": 1200.0, "frac": 0.545}}},
+        "semaphore": {"kinds": {"window": {"1": {"ops_per_s": 3e5, "roof_ops_per_s": 4e5, "frac": 0.75}}}},
+        "condvar": {"mutex": {"cohort": {"items_per_s": 3e5, "frac": 0.48}}},
+        "batched": {"default": {"acq_per_s": 4.8e6, "cluster": 1}, "tuned": {"acq_per_s": 5.2e6, "cluster": 4}},
+        "serving": {"rates": {"1000": {"persistent": {"achieved_req_s": 1000.0, "p50_us": 8.0, "p99_us": 11.0},
+                                       "per_request_launch": {"achieved_req_s": 1000.0, "p50_us": 12.0,
+                                                              "p99_us": 18.0}}}},
+    }
+    rows = bench.result_rows(out)
+    sections = [r["section"] for r in rows]
+    assert sections.count("mutex") == 2 and sections.count("barrier") == 1 and sections.count("semaphore") == 1
+    assert sections.count("condvar") == 1 and sections.count("batched") == 2 and sections.count("serving") == 2
+    m = [r for r in rows if r["section"] == "mutex" and r["cs_words"] == 64][0]
+    assert m["kind"] == "ticket" and m["frac"] == 0.7 and m["nblocks"] == 1184
+    s = [r for r in rows if r["section"] == "serving" and r["kind"] == "persistent"][0]
+    assert s["offered_req_s"] == 1000.0 and s["p99_us"] == 11.0
+    assert all(r["clocks_sm_mhz"] == 2070.0 and r["n_gpus"] == 1 for r in rows)
+
+
+def test_rows_of_a_line_without_optional_sections():
+    import bench
+    assert bench.result_rows({"config": {}, "n_gpus": 1}) == []
