@@ -229,7 +229,10 @@ def measure_roofline_terms(runner, inputs):
             for K in CS_SIZES}
     rs = [runner.probe_throughput("red_add", True, False, NBLOCKS, 128, 2000)["ops_per_s"] for _ in range(3)]
     ra = [runner.probe_throughput("atomic_read", True, False, NBLOCKS, 128, 1000)["ops_per_s"] for _ in range(3)]
-    L_rt = float(np.median([runner.probe_latency("atomic_read", 4000)["ns_per_op"] for _ in range(3)]))
+    # dependent chains of one thread: atomic round trip and L2 load, on a line homed on the
+    # probe's own die (a fresh buffer lands on either die: ~190 or ~390 ns for the atomic)
+    L_rt = best_placement(lambda a: runner.probe_latency("atomic_read", 4000, scratch=a)["ns_per_op"], 256, runner)
+    L_ld = best_placement(lambda a: runner.probe_latency("load_relaxed", 4000, scratch=a)["ns_per_op"], 256, runner)
     T_cs_sem = {}
     for n in SEM_COUNTS:
         hold, add = inputs.sem_inputs(NBLOCKS, SEM_PAIRS, inputs.SEED_SEM ^ (n << 16) ^ NBLOCKS)
@@ -245,13 +248,14 @@ def measure_roofline_terms(runner, inputs):
             "L_handoff_l2_near_ns": float(np.median(near_ns)), "L_handoff_dsmem_ns": float(np.median(dsm_ns)),
             "L_handoff_pairs_ns": hand_ns, "T_cs_ns": T_cs,
             "T_frame_ns": T_frame, "T_cs_sem_ns": T_cs_sem, "T_frame_sem_ns": T_frame_sem,
-            "R_same_red_ops_s": float(np.median(rs)), "R_same_atom_ops_s": float(np.median(ra)), "L_rt_ns": L_rt}
+            "R_same_red_ops_s": float(np.median(rs)), "R_same_atom_ops_s": float(np.median(ra)), "L_rt_ns": L_rt,
+            "L_ld_ns": L_ld}
 
 
 def merge_terms(a, b):
     """The stricter roof of two measurements: lower latencies, higher throughputs."""
     out = dict(a)
-    for k in ("L_handoff_ns", "L_handoff_l2_near_ns", "L_handoff_dsmem_ns", "L_rt_ns"):
+    for k in ("L_handoff_ns", "L_handoff_l2_near_ns", "L_handoff_dsmem_ns", "L_rt_ns", "L_ld_ns"):
         out[k] = min(a[k], b[k])
     for k in ("R_same_red_ops_s", "R_same_atom_ops_s"):
         out[k] = max(a[k], b[k])
@@ -281,7 +285,9 @@ def sem_roof_ops_s(terms, n):
 
 def barrier_roof_ns(terms, kind, param, B):
     """One atomic round trip, one hand-off, and the arrivals through the busiest atomic unit
-    (DIE: the larger die's share of the blocks, and one more round trip for the top counter)."""
+    (DIE: the larger die's share of the blocks, and one more round trip for the top counter),
+    plus the workload's own share of a round: the partner slot each block reads after a
+    crossing is a dependent L2 load on the critical path to its next arrival."""
     rts = 1
     if kind == "cluster":
         b_eff = B / param
@@ -297,7 +303,8 @@ def barrier_roof_ns(terms, kind, param, B):
     else:
         b_eff = B
     # a grid-wide release reaches every block through L2: the on-die L2 hand-off bounds it
-    return rts * terms["L_rt_ns"] + terms["L_handoff_l2_near_ns"] + b_eff / terms["R_same_atom_ops_s"] * 1e9
+    return (rts * terms["L_rt_ns"] + terms["L_handoff_l2_near_ns"] + b_eff / terms["R_same_atom_ops_s"] * 1e9
+            + terms.get("L_ld_ns", 0.0))
 
 
 # ------------------------------------------------------------------------------------------
