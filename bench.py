@@ -517,7 +517,10 @@ def condvar_section(calc, inputs, runner, terms):
             ms.append(s.elapsed_time(e))
         t = float(np.median(ms[1:]))
         items_s = n / (t * 1e-3)
+        acq = int(run.acq.cpu()[0])  # acquisitions of the last launch, re-locks after waits included
         out["mutex"][mutex] = {"ms": t, "items_per_s": items_s, "frac": items_s / roof,
+                               "acquisitions_per_item": acq / n if n else 0.0,
+                               "lock_acq_per_s": acq / (t * 1e-3), "lock_frac": acq / (t * 1e-3) / (2 * roof),
                                "parity": "ok" if ok else "FAILED"}
     return out
 

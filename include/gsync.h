@@ -368,6 +368,8 @@ typedef struct gsync_condvar_work {
   int64_t* sum;
   uint32_t* count;
   uint32_t* status;
+  uint32_t* acquisitions; /* optional (device, 1 word, zeroed by the caller, or NULL): mutex
+                             acquisitions made, the re-locks after condition waits included */
 } gsync_condvar_work;
 size_t gsync_bench_condvar_workspace_bytes(int capacity);
 int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_backoff* backoff, void* workspace,

@@ -12,8 +12,9 @@ namespace {
 
 constexpr int kMaxThreads = 256;
 
-// The queue's bookkeeping, guarded by the mutex (plain accesses by the holder's thread 0).
-struct Queue {
+// The queue's bookkeeping, guarded by the mutex (plain accesses by the holder's thread 0, the
+// whole struct in one 16-byte load and one 16-byte store: one L2 round trip per look).
+struct __align__(16) Queue {
   uint32_t count, head, tail, capacity;
 };
 
@@ -22,7 +23,7 @@ __global__ void __launch_bounds__(kMaxThreads)
     condvar_workload_kernel(uint32_t* mutex_state, uint32_t* nf_state, uint32_t* ne_state, Queue* q, uint32_t* buf,
                             int producers, int items_per_producer, int items_per_consumer,
                             const uint32_t* __restrict__ value, uint32_t* seen, int64_t* sum, uint32_t* count,
-                            uint32_t* status) {
+                            uint32_t* status, uint32_t* acquisitions) {
   gsync::MutexRef m;
   if (MKIND == GSYNC_MUTEX_CLUSTER) {
     __shared__ gsync::ClusterLocal cluster_lock;
@@ -36,6 +37,7 @@ __global__ void __launch_bounds__(kMaxThreads)
   const bool t0 = threadIdx.x == 0;
   __shared__ int s_ok;
   __shared__ uint32_t s_id;
+  Queue qv = {0u, 0u, 0u, 1u};  // thread 0's copy of *q while it holds the mutex
   int64_t my_sum = 0;
   uint32_t taken = 0;
   for (int i = 0; i < ops; ++i) {
@@ -44,17 +46,19 @@ __global__ void __launch_bounds__(kMaxThreads)
       if (t0) record_status(status, tok.status);
       break;
     }
+    if (t0 && acquisitions) ptx::red_add_relaxed(acquisitions, 1u);  // fire-and-forget: no round trip
     // wait while the buffer is full (producer) or empty (consumer); re-test after each wake
     int rc = GSYNC_OK;
     for (;;) {
       if (t0) {
-        const uint32_t c = q->count;
-        s_ok = producer ? c < q->capacity : c > 0u;
+        qv = *q;
+        s_ok = producer ? qv.count < qv.capacity : qv.count > 0u;
       }
       __syncthreads();
       if (s_ok) break;
       rc = gsync::cond_wait<MKIND>(producer ? not_full : not_empty, m, tok);
       if (rc != GSYNC_OK) break;
+      if (t0 && acquisitions) ptx::red_add_relaxed(acquisitions, 1u);  // the wait took the mutex again
     }
     if (rc != GSYNC_OK) {
       if (t0) record_status(status, rc);
@@ -63,14 +67,12 @@ __global__ void __launch_bounds__(kMaxThreads)
     if (t0) {
       if (producer) {
         const uint32_t id = blockIdx.x * (uint32_t)items_per_producer + (uint32_t)i;
-        buf[q->tail % q->capacity] = id;
-        q->tail = q->tail + 1u;
-        q->count = q->count + 1u;
+        buf[qv.tail % qv.capacity] = id;
+        *q = Queue{qv.count + 1u, qv.head, qv.tail + 1u, qv.capacity};
         gsync::cond_signal_thread(not_empty);
       } else {
-        s_id = buf[q->head % q->capacity];
-        q->head = q->head + 1u;
-        q->count = q->count - 1u;
+        s_id = buf[qv.head % qv.capacity];
+        *q = Queue{qv.count - 1u, qv.head + 1u, qv.tail, qv.capacity};
         gsync::cond_signal_thread(not_full);
       }
     }
@@ -152,5 +154,5 @@ extern "C" int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_back
                                                        : condvar_workload_kernel<GSYNC_MUTEX_TICKET>;
   return launch_coresident(kernel, w->producers + w->consumers, w->block_threads, cluster, 0, st, mstate, nf, ne, q, buf,
                            w->producers, w->items_per_producer, items_per_consumer, w->value, w->seen, w->sum,
-                           w->count, w->status);
+                           w->count, w->status, w->acquisitions);
 }

@@ -38,7 +38,8 @@ class gsync_backoff(ctypes.Structure):
 class gsync_condvar_work(ctypes.Structure):
     _fields_ = [("producers", ctypes.c_int32), ("consumers", ctypes.c_int32), ("items_per_producer", ctypes.c_int32),
                 ("capacity", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("mutex_kind", ctypes.c_int32),
-                ("cluster", ctypes.c_int32), ("value", u32p), ("seen", u32p), ("sum", u32p), ("count", u32p), ("status", u32p)]
+                ("cluster", ctypes.c_int32), ("value", u32p), ("seen", u32p), ("sum", u32p), ("count", u32p), ("status", u32p),
+                ("acquisitions", u32p)]
 
 
 class gsync_barrier_work(ctypes.Structure):

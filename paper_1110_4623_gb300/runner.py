@@ -205,18 +205,20 @@ class CondVarRun:
         self.sum = torch.zeros(consumers, dtype=torch.int64, device="cuda")
         self.count = _zeros(consumers)
         self.status = _zeros(1)
+        self.acq = _zeros(1)
         self.nbytes = G.gsync_bench_condvar_workspace_bytes(capacity)
         self.ws = _state(self.nbytes)
         self.work = G.gsync_condvar_work(producers, consumers, items_per_producer, capacity, block_threads,
                                          G.MUTEX_KINDS[mutex], cluster,
                                          G.ptr(self.value), G.ptr(self.seen), G.ptr(self.sum), G.ptr(self.count),
-                                         G.ptr(self.status))
+                                         G.ptr(self.status), G.ptr(self.acq))
 
     def reset(self):
         self.seen.zero_()
         self.sum.zero_()
         self.count.zero_()
         self.status.zero_()
+        self.acq.zero_()
 
     def launch(self, stream=None) -> int:
         return G.gsync_bench_condvar(self.work, self.bo, self.ws, self.nbytes, stream)
@@ -226,7 +228,8 @@ class CondVarRun:
         rc = self.launch()
         torch.cuda.synchronize()
         return {"rc": rc, "status": int(_np(self.status)[0]), "seen": _np(self.seen, self.n),
-                "sum": self.sum.cpu().numpy(), "count": _np(self.count, self.consumers)}
+                "sum": self.sum.cpu().numpy(), "count": _np(self.count, self.consumers),
+                "acquisitions": int(_np(self.acq)[0])}
 
 
 class SemRun:

@@ -27,6 +27,8 @@ def check(producers, consumers, items, capacity, threads=128, bo=None, mutex="ti
     assert np.array_equal(got["seen"], want["seen"]), int((got["seen"] != 1).sum())
     assert int(got["sum"].sum()) == want["total"]
     assert np.array_equal(got["count"], want["count"])
+    # every item is put under one acquisition and taken under another; waits add re-locks
+    assert got["acquisitions"] >= 2 * n
 
 
 @pytest.mark.parametrize("producers,consumers,items,capacity", [
