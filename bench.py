@@ -488,16 +488,23 @@ CV_PRODUCERS, CV_CONSUMERS, CV_ITEMS, CV_CAPACITY = 592, 592, 100, 16
 
 def condvar_section(calc, inputs, runner, terms):
     """Condition variables (future work in Section 7): bounded producer/consumer queue at 1184
-    blocks.  Every item takes two lock acquisitions (the put and the take), so the mutex
-    roofline at an empty critical section bounds it at half that rate."""
+    blocks.  Every item takes at least two lock acquisitions (the put and the take), each a
+    hand-off plus the queue's own critical section, so the roof is half of
+    1e9 / (L_handoff + T_body_cv), with T_body_cv from the single-block probe of that critical
+    section minus its frame (the fastest of PROBE_PAGES placements)."""
     import torch
     n = CV_PRODUCERS * CV_ITEMS
     value = inputs.condvar_inputs(n)
     want = calc.condvar_final(value, CV_PRODUCERS, CV_ITEMS, CV_CONSUMERS)
-    roof = mutex_roof_acq_s(terms, 0) / 2
+    nbytes = runner.G.gsync_bench_condvar_workspace_bytes(16)
+    t_cs = best_placement(lambda a: runner.probe_condvar_cs(128, 4000, False, scratch=a)["ns_per_cs"], nbytes, runner)
+    t_frame = best_placement(lambda a: runner.probe_condvar_cs(128, 4000, True, scratch=a)["ns_per_cs"], nbytes, runner)
+    t_body = max(t_cs - t_frame, 0.0)
+    acq_roof = min(terms["R_same_atom_ops_s"] / 2.0, 1e9 / (terms["L_handoff_ns"] + t_body))
+    roof = acq_roof / 2
     out = {"workload": f"{CV_PRODUCERS} producer + {CV_CONSUMERS} consumer blocks x 128 threads, {CV_ITEMS} items "
                        f"per producer, queue capacity {CV_CAPACITY}, one mutex + two condition variables",
-           "roof_items_per_s": roof, "mutex": {}}
+           "roof_items_per_s": roof, "T_cs_cv_ns": t_cs, "T_frame_cv_ns": t_frame, "mutex": {}}
     for mutex, bo in (("ticket", (64, 2000)), ("cohort", (128, 4000)), ("cluster", (128, 4000))):
         run = runner.CondVarRun(CV_PRODUCERS, CV_CONSUMERS, CV_ITEMS, CV_CAPACITY, value,
                                 bo=runner.backoff(min_ns=bo[0], max_ns=bo[1]), mutex=mutex,
@@ -520,7 +527,7 @@ def condvar_section(calc, inputs, runner, terms):
         acq = int(run.acq.cpu()[0])  # acquisitions of the last launch, re-locks after waits included
         out["mutex"][mutex] = {"ms": t, "items_per_s": items_s, "frac": items_s / roof,
                                "acquisitions_per_item": acq / n if n else 0.0,
-                               "lock_acq_per_s": acq / (t * 1e-3), "lock_frac": acq / (t * 1e-3) / (2 * roof),
+                               "lock_acq_per_s": acq / (t * 1e-3), "lock_frac": acq / (t * 1e-3) / acq_roof,
                                "parity": "ok" if ok else "FAILED"}
     return out
 

@@ -372,6 +372,15 @@ typedef struct gsync_condvar_work {
                              acquisitions made, the re-locks after condition waits included */
 } gsync_condvar_work;
 size_t gsync_bench_condvar_workspace_bytes(int capacity);
+/* Critical-section probe of the condition-variable queue (its roofline's T_cs): one block of
+ * block_threads alternates a put and a take -- the workload's test of the queue under block
+ * barriers, the slot and the queue's state, the signal -- framed like a hand-off (an acquire
+ * load and a barrier before it, a barrier and a release store after it), `iters` times, with
+ * no mutex and no waits; frame_only != 0 runs the frame around an empty body.  workspace
+ * (device, 256-byte aligned) >= gsync_bench_condvar_workspace_bytes(16), initialised by the
+ * call; out[0] (host) = elapsed ns.  Synchronizes `stream`. */
+int gsync_probe_condvar_cs(int block_threads, int iters, int frame_only, void* workspace,
+                           size_t workspace_bytes, uint64_t* out, void* stream);
 int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_backoff* backoff, void* workspace,
                         size_t workspace_bytes, void* stream);
 

@@ -98,6 +98,52 @@ __global__ void __launch_bounds__(kMaxThreads)
 
 size_t round_up(size_t n) { return (n + 255) & ~(size_t)255; }
 
+// Critical-section probe of the queue (the roofline's T_cs for the condition-variable
+// workload): one block alternates a put and a take, each the workload's critical section --
+// the test of the queue under block barriers, the slot and the queue's state, the signal --
+// framed like a hand-off (an acquire load and a barrier before, a barrier and a release store
+// after), with no mutex and no waits.  frame_only runs the frame around an empty body.
+__global__ void __launch_bounds__(kMaxThreads)
+    condvar_cs_probe_kernel(uint32_t* nf_state, uint32_t* ne_state, Queue* q, uint32_t* buf, int iters, int frame_only,
+                            uint32_t* word) {
+  const gsync::CondRef not_full = gsync::cond_attach(nf_state), not_empty = gsync::cond_attach(ne_state);
+  const bool t0 = threadIdx.x == 0;
+  __shared__ int s_ok;
+  __shared__ uint32_t s_id;
+  Queue qv = {0u, 0u, 0u, 1u};
+  uint32_t acc = 0;
+  if (t0) s_id = 0;
+  for (int i = 0; i < iters; ++i) {
+    if (t0) (void)ptx::ld_acquire(word);
+    __syncthreads();
+    const bool put = (i & 1) == 0;
+    if (!frame_only) {
+      if (t0) {
+        qv = *q;
+        s_ok = put ? qv.count < qv.capacity : qv.count > 0u;
+      }
+      __syncthreads();
+      if (t0 && s_ok) {
+        if (put) {
+          buf[qv.tail % qv.capacity] = (uint32_t)i;
+          *q = Queue{qv.count + 1u, qv.head, qv.tail + 1u, qv.capacity};
+          gsync::cond_signal_thread(not_empty);
+        } else {
+          s_id = buf[qv.head % qv.capacity];
+          *q = Queue{qv.count - 1u, qv.head + 1u, qv.tail, qv.capacity};
+          gsync::cond_signal_thread(not_full);
+        }
+      }
+    }
+    __syncthreads();
+    if (t0) {
+      acc += s_id;
+      ptx::st_release(word, (uint32_t)i);
+    }
+  }
+  if (t0 && acc == 0xFFFFFFFFu) word[1] = acc;  // keeps the taken ids live
+}
+
 }  // namespace
 
 // The mutex sits first in the workspace and takes the largest of the kinds' sizes.
@@ -155,4 +201,40 @@ extern "C" int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_back
   return launch_coresident(kernel, w->producers + w->consumers, w->block_threads, cluster, 0, st, mstate, nf, ne, q, buf,
                            w->producers, w->items_per_producer, items_per_consumer, w->value, w->seen, w->sum,
                            w->count, w->status, w->acquisitions);
+}
+
+// T_cs probe of the condition-variable queue: see condvar_cs_probe_kernel.  workspace as for
+// gsync_bench_condvar (capacity 16 is enough); out[0] (host) = elapsed ns for `iters` critical
+// sections.  Synchronizes `stream`.
+extern "C" int gsync_probe_condvar_cs(int block_threads, int iters, int frame_only, void* workspace,
+                                      size_t workspace_bytes, uint64_t* out, void* stream) {
+  if (!out || iters < 1 || block_threads < 32 || block_threads > kMaxThreads || block_threads % 32) return GSYNC_EINVAL;
+  const size_t need = gsync_bench_condvar_workspace_bytes(16);
+  if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return GSYNC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* p = (char*)workspace;
+  uint32_t* word = (uint32_t*)p;    p += mutex_region();  // the frame's acquire/release word
+  uint32_t* nf = (uint32_t*)p;      p += round_up(gsync_cond_bytes());
+  uint32_t* ne = (uint32_t*)p;      p += round_up(gsync_cond_bytes());
+  Queue* q = (Queue*)p;             p += round_up(sizeof(Queue));
+  uint32_t* buf = (uint32_t*)p;
+  if (int rc = gsync_cond_init(nf, gsync_cond_bytes(), nullptr, 1000000000ull, stream)) return rc;
+  if (int rc = gsync_cond_init(ne, gsync_cond_bytes(), nullptr, 1000000000ull, stream)) return rc;
+  const Queue q0 = {0u, 0u, 0u, 16u};
+  GSYNC_CUDA(cudaMemcpyAsync(q, &q0, sizeof q0, cudaMemcpyHostToDevice, st));
+  GSYNC_CUDA(cudaMemsetAsync(word, 0, 256, st));
+  cudaEvent_t e0, e1;
+  GSYNC_CUDA(cudaEventCreate(&e0));
+  GSYNC_CUDA(cudaEventCreate(&e1));
+  GSYNC_CUDA(cudaEventRecord(e0, st));
+  condvar_cs_probe_kernel<<<1, block_threads, 0, st>>>(nf, ne, q, buf, iters, frame_only, word);
+  GSYNC_CUDA(cudaGetLastError());
+  GSYNC_CUDA(cudaEventRecord(e1, st));
+  GSYNC_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  GSYNC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  out[0] = (uint64_t)(ms * 1e6);
+  return GSYNC_OK;
 }

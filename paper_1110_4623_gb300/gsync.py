@@ -110,6 +110,8 @@ _SIG = {
     "gsync_cond_bytes": (ctypes.c_size_t, []),
     "gsync_cond_init": (ctypes.c_int, [u32p, ctypes.c_size_t, ctypes.POINTER(gsync_backoff), ctypes.c_uint64, u32p]),
     "gsync_bench_condvar_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int]),
+    "gsync_probe_condvar_cs": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, u32p, ctypes.c_size_t,
+                                              ctypes.POINTER(ctypes.c_uint64), u32p]),
     "gsync_bench_condvar": (ctypes.c_int, [ctypes.POINTER(gsync_condvar_work), ctypes.POINTER(gsync_backoff), u32p,
                                            ctypes.c_size_t, u32p]),
     "gsync_barrier_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -284,6 +286,13 @@ def gsync_cond_init(state, nbytes, backoff=None, timeout_ns=0, stream=None) -> i
 
 def gsync_bench_condvar_workspace_bytes(capacity) -> int:
     return lib().gsync_bench_condvar_workspace_bytes(capacity)
+
+
+def gsync_probe_condvar_cs(block_threads, iters, frame_only, workspace, nbytes, stream=None) -> tuple[int, int]:
+    out = (ctypes.c_uint64 * 1)()
+    rc = lib().gsync_probe_condvar_cs(block_threads, iters, int(frame_only), ptr(workspace), nbytes, out,
+                                      stream_handle(stream))
+    return rc, out[0]
 
 
 def gsync_bench_condvar(work, backoff, workspace, nbytes, stream=None) -> int:

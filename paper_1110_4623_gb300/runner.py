@@ -418,6 +418,18 @@ def probe_sem_cs(hold: np.ndarray | None, addend: np.ndarray | None, block_threa
     return {"ns_per_cs": out[0] / iters}
 
 
+def probe_condvar_cs(block_threads: int = 128, iters: int = 4000, frame_only: bool = False, scratch=None) -> dict:
+    """Mean time of one critical section of the condition-variable queue, alone (frame_only:
+    the frame around an empty body).  scratch: None or the device address of
+    gsync_bench_condvar_workspace_bytes(16) bytes, 256-byte aligned."""
+    nbytes = G.gsync_bench_condvar_workspace_bytes(16)
+    if scratch is None:
+        scratch = _state(nbytes)
+    rc, ns = G.gsync_probe_condvar_cs(block_threads, iters, frame_only, scratch, nbytes)
+    G.check("gsync_probe_condvar_cs", rc)
+    return {"ns_per_cs": ns / iters}
+
+
 def sm_count() -> int:
     rc, n = G.gsync_device_sm_count()
     G.check("gsync_device_sm_count", rc)

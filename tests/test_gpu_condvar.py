@@ -85,3 +85,15 @@ def test_uneven_split_is_refused():
     from paper_1110_4623_gb300 import runner
     r = runner.CondVarRun(3, 2, 5, 4, np.zeros(15, np.uint32))  # 15 items over 2 consumers
     assert r.launch() == G.GSYNC_EINVAL
+
+
+def test_critical_section_probe():
+    # The probe of the queue's critical section: positive, longer than its frame, and refused
+    # for a workspace that is too small.
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    body = runner.probe_condvar_cs(128, 1000)["ns_per_cs"]
+    frame = runner.probe_condvar_cs(128, 1000, frame_only=True)["ns_per_cs"]
+    assert 0 < frame < body < 100_000
+    small = runner._state(256)
+    assert G.gsync_probe_condvar_cs(128, 10, 0, small, 256)[0] == G.GSYNC_EINVAL
