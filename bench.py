@@ -98,7 +98,8 @@ def result_rows(out):
     for arm in ("default", "tuned"):
         r = out.get("batched", {}).get(arm)
         if r:
-            rows.append({"section": "batched", "kind": arm, "acq_per_s": r["acq_per_s"], "cluster": r["cluster"]})
+            rows.append({"section": "batched", "kind": arm, "acq_per_s": r["acq_per_s"], "frac": r.get("frac"),
+                         "cluster": r["cluster"]})
     for rate, r in out.get("serving", {}).get("rates", {}).items():
         for arm in ("persistent", "per_request_launch"):
             a = r[arm]
@@ -427,8 +428,11 @@ def e2e_mutex(G, inputs, kind, reps=3):
             "kind": kind, "note": f"{k} host-buffer calls (one per CS size) per step; bytes summed over them"}
 
 
-def batched_section(G, calc, inputs, runner, autotune):
-    """Autotunes the batched many-mutex workload, then times its CUDA-graph replay."""
+def batched_section(G, calc, inputs, runner, autotune, terms):
+    """Autotunes the batched many-mutex workload, then times its CUDA-graph replay.  Roofline:
+    the hottest key's acquisitions are serial, each an L2 hand-off (the per-key locks are L2
+    locks: the on-die hand-off bounds them) plus one dependent L2 round trip (the key's sum and
+    count, read and written together), so acq/s <= nacq / (n_hot * (L_handoff_l2_near + L_ld))."""
     import torch
     keys, adds, _ = inputs.batched_inputs(BATCH_ACQ, BATCH_KEYS, 1.1)
     want = calc.batched_final(keys, adds, BATCH_KEYS)
@@ -439,6 +443,9 @@ def batched_section(G, calc, inputs, runner, autotune):
                        f"{BATCH_THREADS} threads, {BATCH_GROUPS} barrier groups x {BATCH_ROUNDS} rounds",
            "class_sizes": tuned["class_sizes"], "tuned_policy": tuned["policy"], "tuned_cluster": tuned["cluster"],
            "autotune_s": tune_s, "trials": len(tuned["trials"])}
+    n_hot = int(np.bincount(np.asarray(keys, dtype=np.int64), minlength=BATCH_KEYS).max())
+    roof = BATCH_ACQ / (n_hot * (terms["L_handoff_l2_near_ns"] + terms["L_ld_ns"]) * 1e-9)
+    out.update({"hottest_key_acquisitions": n_hot, "roof_acq_per_s": roof})
     results = {}
     for label, policy, cluster in (("default", autotune.DEFAULT_POLICY, 1), ("tuned", tuned["policy"], tuned["cluster"])):
         plain = cluster == 1
@@ -470,8 +477,8 @@ def batched_section(G, calc, inputs, runner, autotune):
         ok = (got["status"] == 0 and np.array_equal(got["sum"], want["sum"])
               and np.array_equal(got["count"], want["count"]) and not got["bad"].any())
         ms = float(np.median(ts))
-        results[label] = {"ms": ms, "acq_per_s": BATCH_ACQ / (ms * 1e-3), "cuda_graph": graph, "cluster": cluster,
-                          "parity": "ok" if ok else "FAILED"}
+        results[label] = {"ms": ms, "acq_per_s": BATCH_ACQ / (ms * 1e-3), "frac": BATCH_ACQ / (ms * 1e-3) / roof,
+                          "cuda_graph": graph, "cluster": cluster, "parity": "ok" if ok else "FAILED"}
     out.update(results)
     return out
 
@@ -727,7 +734,7 @@ def run_gpu(args):
         out["e2e"] = e2e
         out["condvar"] = condvar_section(calc, inputs, runner, terms)
         if not args.no_batched:
-            out["batched"] = batched_section(G, calc, inputs, runner, autotune)
+            out["batched"] = batched_section(G, calc, inputs, runner, autotune, terms)
             out["serving"] = serve_section(calc, inputs, runner)
             r5 = out["serving"]["rates"].get("100000")
             if r5:
