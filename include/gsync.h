@@ -398,9 +398,12 @@ int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_backoff* backof
  *    launch and whenever a key's policy kind changes (the objects are left consistent by
  *    every completed launch otherwise).
  *  - key_class (device, nkeys bytes): class of each key, < nclasses.
- *  - policy (device, nclasses x 4 x u32): {kind (CAS_SPIN, CAS_BACKOFF or TICKET; others act
- *    as TICKET), min_ns, max_ns, 0}: backoff of the CAS kind, or sleep per waiter ahead of
- *    the ticket kind; min_ns = 0 spins without sleeping.
+ *  - policy (device, nclasses x 4 x u32): {kind (CAS_SPIN, CAS_BACKOFF, TICKET or CLUSTER;
+ *    others act as TICKET), min_ns, max_ns, budget}: backoff of the CAS kind, or sleep per
+ *    waiter ahead of the ticket kinds; min_ns = 0 spins without sleeping.  CLUSTER (the
+ *    cluster cohort lock) applies in a cluster launch (cluster > 1) to keys below 256, whose
+ *    local locks live in the blocks' shared memory, with `budget` passes per cohort (0 = the
+ *    default, 64); elsewhere it acts as TICKET.  budget is ignored by the other kinds.
  *  - keys (device, nacq x i32), adds (device, nacq x i64); sum (device, nkeys x i64) and
  *    count (device, nkeys x u32) zeroed by the caller.
  *  - group_state (device, 128-byte aligned): ngroups x 512 bytes, zeroed before the first

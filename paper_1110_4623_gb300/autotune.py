@@ -6,7 +6,8 @@ when it expects at least one waiter per hand-off (count >= acquisitions / blocks
 when it expects one sixteenth of that, *cold* otherwise.  For each class in turn (hot first,
 since it bounds the makespan), the tuner times every candidate policy -- mutex kind, backoff
 constants, spinning (min_ns = 0) or __nanosleep -- with the other classes fixed, keeps the
-fastest, and then picks the cluster size of the barrier groups.  Every trial is one real
+fastest, and then picks the cluster size of the barrier groups; with clusters, it last tries
+the cluster cohort lock for the hot and warm classes.  Every trial is one real
 launch of the batched kernel through the C ABI, timed with CUDA events on the launching
 stream; results are verified against nothing here (the parity tests do that).
 """
@@ -31,6 +32,9 @@ CANDIDATES = [
     ("ticket", 256, 4000),
 ]
 CLUSTERS = [1, 2, 4, 8]
+# Tried last, for the hot and warm classes, once a cluster size above 1 is chosen: the cluster
+# cohort lock (keys below 256) needs a cluster launch.
+CLUSTER_CANDIDATES = [("cluster", 128, 4000)]
 DEFAULT_POLICY = [("ticket", 0, 0)] * NCLASSES
 
 
@@ -91,6 +95,18 @@ def tune(keys, adds, nkeys: int, nblocks: int, ngroups: int, rounds: int, block_
         trials.append({"class": None, "policy": None, "cluster": c, "ms": ms})
         if best_cluster[0] is None or ms < best_cluster[0]:
             best_cluster = (ms, c)
+    if best_cluster[1] > 1:
+        r = make_run(keys, adds, nkeys, nblocks, ngroups, rounds, best_cluster[1], key_class, block_threads)
+        for cls in (HOT, WARM):
+            for cand in CLUSTER_CANDIDATES:
+                trial = list(policy)
+                trial[cls] = cand
+                r.set_policy(trial)
+                ms = _time(r, reps)
+                trials.append({"class": cls, "policy": cand, "cluster": best_cluster[1], "ms": ms})
+                if ms < best_cluster[0]:
+                    best_cluster = (ms, best_cluster[1])
+                    policy[cls] = cand
     return {"policy": policy, "cluster": best_cluster[1], "best_ms": best_cluster[0],
             "class_sizes": [int((key_class == c).sum()) for c in range(NCLASSES)], "trials": trials,
             "key_class": key_class}

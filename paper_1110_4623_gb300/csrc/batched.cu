@@ -9,7 +9,8 @@
 // that belong to a barrier group also cross `rounds` group barriers spread evenly over their
 // acquisitions, with the sampled slot check of the barrier workload (partner
 // p = (j + r + 1) mod size inside the group).  The autotuner chooses, per contention class,
-// the mutex kind (spin / spin + backoff / ticket), the backoff constants (0 = pure spinning,
+// the mutex kind (spin / spin + backoff / ticket, or -- in a cluster launch -- the cluster
+// cohort lock for keys below kLocalKeys), the backoff constants (0 = pure spinning,
 // otherwise __nanosleep) and the cluster size of the group barriers.
 #include "common.cuh"
 
@@ -23,6 +24,9 @@ constexpr int kMaxThreads = 256;
 // barrier a header line, two arrival counters (by epoch parity) and the release epoch.
 constexpr uint32_t kMutexObjWords = 3 * gsync::kLineWords;
 constexpr uint32_t kBarObjWords = 4 * gsync::kLineWords;
+// Keys below this may use the cluster cohort lock: their local locks live in a table in each
+// block's shared memory (16 bytes a key); the per-key object's lines 1-2 are the global lock.
+constexpr uint32_t kLocalKeys = 256;
 
 struct Args {
   uint32_t* mutex_state;
@@ -48,13 +52,15 @@ __device__ __forceinline__ gsync::Token lock_by_policy(const gsync::MutexRef& m)
   switch (m.kind) {
     case GSYNC_MUTEX_CAS_SPIN: return gsync::mutex_lock_thread<GSYNC_MUTEX_CAS_SPIN>(m);
     case GSYNC_MUTEX_CAS_BACKOFF: return gsync::mutex_lock_thread<GSYNC_MUTEX_CAS_BACKOFF>(m);
+    case GSYNC_MUTEX_CLUSTER: return gsync::mutex_lock_thread<GSYNC_MUTEX_CLUSTER>(m);
     default: return gsync::mutex_lock_thread<GSYNC_MUTEX_TICKET>(m);
   }
 }
 
-__device__ __forceinline__ void unlock_by_policy(const gsync::MutexRef& m, uint32_t ticket) {
-  if (m.kind == GSYNC_MUTEX_TICKET) gsync::mutex_unlock_thread<GSYNC_MUTEX_TICKET>(m, ticket);
-  else gsync::mutex_unlock_thread<GSYNC_MUTEX_CAS_SPIN>(m, ticket);
+__device__ __forceinline__ void unlock_by_policy(const gsync::MutexRef& m, const gsync::Token& t) {
+  if (m.kind == GSYNC_MUTEX_TICKET) gsync::mutex_unlock_thread<GSYNC_MUTEX_TICKET>(m, t.ticket);
+  else if (m.kind == GSYNC_MUTEX_CLUSTER) gsync::mutex_unlock_thread<GSYNC_MUTEX_CLUSTER>(m, t);
+  else gsync::mutex_unlock_thread<GSYNC_MUTEX_CAS_SPIN>(m, t.ticket);
 }
 
 // One crossing of the group barrier with the sampled slot check.
@@ -78,6 +84,18 @@ __global__ void __launch_bounds__(kMaxThreads, 8) batched_kernel(Args a) {
   const uint32_t G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   __shared__ int s_fail;
   if (tid == 0) s_fail = 0;
+  // The cluster cohort lock's local locks (one per key below kLocalKeys; block 0 of each
+  // cluster holds the ones in use).  Initialised before any block of the cluster can use them,
+  // and kept alive by the cluster barrier at the end of the kernel.
+  __shared__ gsync::ClusterLocal local_locks[BKIND == GSYNC_BAR_CLUSTER ? kLocalKeys : 1];
+  if (BKIND == GSYNC_BAR_CLUSTER) {
+    if (ptx::cluster_ctarank() == 0)
+      for (uint32_t i = tid; i < kLocalKeys; i += blockDim.x) {
+        local_locks[i].next = 0u;
+        local_locks[i].turn = 0ull;
+      }
+    ptx::cluster_sync();
+  }
   int g = a.group_of_block[b];
   if (g >= a.ngroups) g = -1;
   gsync::BarrierRef bar;
@@ -128,8 +146,14 @@ __global__ void __launch_bounds__(kMaxThreads, 8) batched_kernel(Args a) {
         const uint32_t* pol = a.policy + 4u * (cls < (uint32_t)a.nclasses ? cls : 0u);
         gsync::MutexRef m;
         m.s = a.mutex_state + key * kMutexObjWords;
-        m.kind = pol[0] <= (uint32_t)GSYNC_MUTEX_TICKET ? pol[0] : (uint32_t)GSYNC_MUTEX_TICKET;
-        m.qmask = 0;
+        const bool cohort = BKIND == GSYNC_BAR_CLUSTER && pol[0] == (uint32_t)GSYNC_MUTEX_CLUSTER && key < kLocalKeys;
+        m.kind = cohort ? (uint32_t)GSYNC_MUTEX_CLUSTER
+                        : pol[0] <= (uint32_t)GSYNC_MUTEX_TICKET ? pol[0] : (uint32_t)GSYNC_MUTEX_TICKET;
+        // cohort budget (fourth policy word, 0 = the default), kept as budget - 1
+        m.qmask = cohort ? (pol[3] ? min(pol[3], 32767u) : (uint32_t)GSYNC_COHORT_DEFAULT_BUDGET) - 1u : 0u;
+        m.cl = cohort ? ptx::map_cluster_rank(&local_locks[key], 0u) : nullptr;
+        m.local = nullptr;
+        m.die = 0;
         m.bo.policy = GSYNC_BACKOFF_EXPONENTIAL;
         m.bo.min_ns = pol[1];
         m.bo.max_ns = pol[2];
@@ -142,7 +166,7 @@ __global__ void __launch_bounds__(kMaxThreads, 8) batched_kernel(Args a) {
         } else {
           a.sum[key] += a.adds[i];
           a.count[key] += 1u;
-          unlock_by_policy(m, t.ticket);
+          unlock_by_policy(m, t);
         }
       }
     }
@@ -164,6 +188,7 @@ __global__ void __launch_bounds__(kMaxThreads, 8) batched_kernel(Args a) {
     a.mix[b] = mix;
     a.bad[b] = bad;
   }
+  if (BKIND == GSYNC_BAR_CLUSTER) ptx::cluster_sync();  // block 0's local locks outlive every user
 }
 
 }  // namespace

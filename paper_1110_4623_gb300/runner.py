@@ -474,10 +474,13 @@ class BatchedRun:
         self.graph = None
 
     def set_policy(self, table):
-        """table: list of (kind, min_ns, max_ns) per class.  Zeroes the mutexes (kinds may change)."""
+        """table: list of (kind, min_ns, max_ns[, budget]) per class (budget: the cluster cohort
+        lock's passes per cohort, 0 = default).  Zeroes the mutexes (kinds may change)."""
         flat = []
-        for kind, mn, mx in table:
-            flat += [G.MUTEX_KINDS[kind] if isinstance(kind, str) else int(kind), int(mn), int(mx), 0]
+        for entry in table:
+            kind, mn, mx = entry[:3]
+            budget = entry[3] if len(entry) > 3 else 0
+            flat += [G.MUTEX_KINDS[kind] if isinstance(kind, str) else int(kind), int(mn), int(mx), int(budget)]
         self.policy.copy_(torch.tensor(flat, dtype=torch.int32))
         self.mutex_state.zero_()
         self.graph = None

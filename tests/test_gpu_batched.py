@@ -57,6 +57,21 @@ def test_policies(policy):
     check(run, keys, adds, got, 37)
 
 
+@pytest.mark.parametrize("cluster,policy", [
+    (4, [("cluster", 128, 4000), ("ticket", 256, 4000), ("ticket", 64, 2000)]),
+    (2, [("cluster", 0, 0, 3), ("cluster", 128, 4000), ("cas_spin", 0, 0)]),
+    (8, [("cluster", 128, 4000, 32767)] * 3),
+    (1, [("cluster", 128, 4000)] * 3)])  # no clusters: the policy acts as the ticket lock
+def test_cluster_cohort_policy(cluster, policy):
+    # The cluster cohort lock for keys below 256 (the hot and warm keys of the Zipf stream),
+    # with budgets 3, the default and the maximum; keys at or above 256 fall back to the
+    # ticket lock.
+    run, keys, adds = make(1_000_000 if cluster == 4 else 200_000, cluster=cluster, policy=policy, rounds=23)
+    got = run.run()
+    assert got["rc"] == 0
+    check(run, keys, adds, got, 23)
+
+
 def test_graph_capture_replays_exactly():
     import torch
     run, keys, adds = make(300_000, rounds=20, plain_launch=True)
