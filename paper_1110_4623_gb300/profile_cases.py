@@ -3,7 +3,9 @@
     python -m paper_1110_4623_gb300.profile_cases <case> [<case> ...]
 
 Each case launches a single workload kernel at the bench's grid (1184 blocks) with fewer
-operations per block than the bench, so that a multi-pass profiler capture stays short.
+operations per block than the bench, so that a multi-pass profiler capture stays short
+(mutex_cluster_bench runs the bench's own three launches of the default kind, for one-pass
+counters).
 The result is checked against nothing; the parity tests do that.
 """
 from __future__ import annotations
@@ -27,6 +29,13 @@ def _mutex(kind, K, acq=20):
     bo = runner.backoff(min_ns=_BACKOFF[kind][0], max_ns=_BACKOFF[kind][1]) if kind in _BACKOFF else None
     r = runner.MutexRun(kind, NB, 256, acq, K, delay, add, bo=bo, timeout_ns=10_000_000_000, cluster=4)
     return lambda: G.check("gsync_bench_mutex", r.launch())
+
+
+def _chain(launches):
+    def run():
+        for f in launches:
+            f()
+    return run
 
 
 def _barrier(kind, param, rounds=200):
@@ -63,6 +72,9 @@ CASES = {
     "mutex_cas_backoff": lambda: _mutex("cas_backoff", 64),
     "mutex_cohort": lambda: _mutex("cohort", 64),
     "mutex_cluster": lambda: _mutex("cluster", 64),
+    # the bench step's launches of the default kind, at full size: CS 0, 64 and 1024 words,
+    # 100 acquisitions per block (for per-launch DRAM traffic without scaling)
+    "mutex_cluster_bench": lambda: _chain([_mutex("cluster", K, acq=100) for K in (0, 64, 1024)]),
     "barrier_atomic": lambda: _barrier("atomic", 0),
     "barrier_flag": lambda: _barrier("flag", 0),
     "barrier_cluster2": lambda: _barrier("cluster", 2),
