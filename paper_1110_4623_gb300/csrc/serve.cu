@@ -96,11 +96,6 @@ __device__ __forceinline__ void st_release_sys(uint32_t* p, uint32_t v) {
 __device__ __forceinline__ void st_relaxed_sys_s64(int64_t* p, int64_t v) {
   asm volatile("st.relaxed.sys.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-__device__ __forceinline__ uint32_t atom_cas_relaxed(uint32_t* p, uint32_t cmp, uint32_t v) {
-  uint32_t r;
-  asm volatile("atom.relaxed.gpu.global.cas.b32 %0, [%1], %2, %3;" : "=r"(r) : "l"(p), "r"(cmp), "r"(v) : "memory");
-  return r;
-}
 
 // Block-wide int64 sum of pool[a, b): 16-byte streaming loads over the aligned middle, eight
 // of them in flight per thread (issued before any is added), scalars at the ends.
@@ -175,7 +170,7 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(Args a) {
   const gsync::MutexRef lock = gsync::mutex_attach(a.ring_lock);
   const gsync::SemRef sem = gsync::sem_attach(a.admit_sem);
   __shared__ int s_cmd;       // 0 continue, 1 exit
-  __shared__ uint32_t s_slot, s_chunk, s_gen;
+  __shared__ uint32_t s_slot;
   __shared__ int64_t s_lo, s_hi;
   const bool admitter = blockIdx.x < a.admitters;
   uint32_t idle = 0, scan = blockIdx.x % a.nslots;
@@ -283,7 +278,7 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(Args a) {
           const int64_t lo = sl->off + (int64_t)c * a.chunk_elems;
           int64_t hi = lo + a.chunk_elems;
           if (hi > sl->off + sl->len) hi = sl->off + sl->len;
-          s_slot = s; s_chunk = c; s_gen = g; s_lo = lo; s_hi = hi;
+          s_slot = s; s_lo = lo; s_hi = hi;
           if (a.trace && c == 0) a.trace[4ull * sl->id + 2] = ptx::globaltimer();
           s_cmd = 0;
           scan = s;

@@ -1,5 +1,4 @@
 """Memory-system probes run, stay bounded and report sane values (Section 3, "Benchmarks")."""
-import numpy as np
 import pytest
 
 from gpu_util import require_gpu
