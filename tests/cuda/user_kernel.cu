@@ -1,9 +1,13 @@
-// A program written the way a user of the library writes one: its own kernel calls the
-// device primitives of gsync_device.cuh (the counting barrier and the cohort mutex), the
-// objects are created through the C ABI, and the grid is launched through the library's
-// co-residency gate.  Checked exactly: every round of the barrier sees every block's value of
-// that round, and a counter updated with plain loads and stores under the mutex ends at
-// blocks x rounds.  Prints "OK" and exits 0 on success.
+// A program written the way a user of the library writes one: its own kernels call the
+// device primitives of gsync_device.cuh, the objects are created through the C ABI, and the
+// grids are launched through the library's co-residency gate.
+//   user_kernel: the counting barrier and the two-die cohort mutex, a plain launch.
+//   user_kernel_cluster: the GB300 defaults -- the counting barrier, the cluster cohort mutex
+//     (its local lock in the kernel's shared memory) and the ticket-window semaphore -- in a
+//     launch with clusters of 4.
+// Checked exactly: every round of the barrier sees every block's value of that round, a
+// counter updated with plain loads and stores under the mutex ends at blocks x rounds, and
+// the semaphore never admits more than its count.  Prints "OK" and exits 0 on success.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -35,6 +39,47 @@ __global__ void user_kernel(void* bar_state, void* mutex_state, uint32_t* slots,
     if (threadIdx.x == 0) *counter = *counter + 1u;  // plain read-modify-write under the mutex
     gsync::mutex_unlock<GSYNC_MUTEX_COHORT>(m, t);
   }
+}
+
+__global__ void user_kernel_cluster(void* bar_state, void* mutex_state, void* sem_state, uint32_t* slots,
+                                    uint32_t* counter, uint32_t* bad, uint32_t* occ, int rounds) {
+  __shared__ gsync::ClusterLocal cluster_lock;
+  gsync::BarrierRef bar = gsync::barrier_attach(bar_state);
+  const gsync::MutexRef m = gsync::mutex_attach_cluster(mutex_state, &cluster_lock);
+  const gsync::SemRef s = gsync::sem_attach(sem_state);
+  const uint32_t b = blockIdx.x, B = gridDim.x;
+  bool ok = true;
+  for (int r = 0; r < rounds && ok; ++r) {
+    uint32_t* buf = slots + (r & 1) * B;
+    if (threadIdx.x == 0) buf[b] = (uint32_t)r * B + b;
+    if (gsync::barrier_wait<GSYNC_BAR_COUNT>(bar) != GSYNC_OK) {
+      ok = false;
+      break;
+    }
+    if (threadIdx.x == 0) {
+      const uint32_t p = (b + (uint32_t)r + 1u) % B;
+      if (buf[p] != (uint32_t)r * B + p) atomicAdd(bad, 1u);
+    }
+    gsync::Token t = gsync::mutex_lock<GSYNC_MUTEX_CLUSTER>(m);
+    if (t.status != GSYNC_OK) {
+      ok = false;
+      break;
+    }
+    if (threadIdx.x == 0) *counter = *counter + 1u;  // plain read-modify-write under the mutex
+    gsync::mutex_unlock<GSYNC_MUTEX_CLUSTER>(m, t);
+    if (gsync::sem_wait<GSYNC_SEM_WINDOW>(s) != GSYNC_OK) {
+      ok = false;
+      break;
+    }
+    if (threadIdx.x == 0) {
+      const uint32_t o = atomicAdd(occ, 1u) + 1u;  // holders inside, and the most seen
+      atomicMax(occ + 1, o);
+      atomicSub(occ, 1u);
+    }
+    gsync::sem_post<GSYNC_SEM_WINDOW>(s);
+  }
+  if (!ok && threadIdx.x == 0) atomicAdd(bad, 1u);
+  gsync::mutex_cluster_end();  // block 0's local lock outlives every user in the cluster
 }
 
 #define CHECK(x)                                                              \
@@ -81,6 +126,42 @@ int main() {
     printf("FAIL counter %u (want %u), bad %u\n", h[0], (uint32_t)B * rounds, h[1]);
     return 1;
   }
-  printf("OK %d blocks x %d rounds\n", B, rounds);
+
+  // The GB300 defaults in a cluster launch.
+  cudaFunction_t fc;
+  CHECK(cudaGetFuncBySymbol(&fc, (const void*)user_kernel_cluster));
+  const int C = 4, n = 4;
+  int maxc = 0;
+  CHECK(gsync_check_coresident((const void*)fc, C, threads, 0, C, &maxc));
+  const int BC = (maxc < 1184 ? maxc : 1184) / C * C;
+  void *bar2 = nullptr, *mtx2 = nullptr, *sem = nullptr;
+  uint32_t* w = nullptr;  // counter, bad, occupancy, max occupancy
+  uint32_t* slots2 = nullptr;
+  const size_t bar2_bytes = gsync_barrier_bytes(GSYNC_BAR_COUNT, BC, 8);
+  const size_t mtx2_bytes = gsync_mutex_bytes(GSYNC_MUTEX_CLUSTER, BC);
+  const size_t sem_bytes = gsync_sem_bytes(GSYNC_SEM_WINDOW);
+  CHECK(cudaMalloc(&bar2, bar2_bytes));
+  CHECK(cudaMalloc(&mtx2, mtx2_bytes));
+  CHECK(cudaMalloc(&sem, sem_bytes));
+  CHECK(cudaMalloc(&w, 4 * sizeof(uint32_t)));
+  CHECK(cudaMalloc(&slots2, 2 * BC * sizeof(uint32_t)));
+  CHECK(cudaMemset(w, 0, 4 * sizeof(uint32_t)));
+  CHECK(gsync_barrier_init(bar2, bar2_bytes, GSYNC_BAR_COUNT, BC, 8, 0, nullptr));
+  CHECK(gsync_mutex_init(mtx2, mtx2_bytes, GSYNC_MUTEX_CLUSTER, BC, &bo, 0, nullptr));
+  gsync_backoff sbo = {GSYNC_BACKOFF_EXPONENTIAL, 16, 2000, 0};
+  CHECK(gsync_sem_init(sem, sem_bytes, GSYNC_SEM_WINDOW, n, &sbo, 0, nullptr));
+  uint32_t *cnt2 = w, *bad2 = w + 1, *occ = w + 2;
+  void* args2[] = {&bar2, &mtx2, &sem, &slots2, &cnt2, &bad2, &occ, &r};
+  CHECK(gsync_launch_coresident((const void*)fc, BC, threads, 0, C, args2, nullptr));
+  CHECK(cudaDeviceSynchronize());
+  uint32_t h2[4];
+  CHECK(cudaMemcpy(h2, w, sizeof h2, cudaMemcpyDeviceToHost));
+  if (h2[1] != 0 || h2[0] != (uint32_t)BC * rounds || h2[2] != 0 || h2[3] < 1 || h2[3] > (uint32_t)n) {
+    printf("FAIL cluster kernel: counter %u (want %u), bad %u, occupancy %u, max %u (n %d)\n", h2[0],
+           (uint32_t)BC * rounds, h2[1], h2[2], h2[3], n);
+    return 1;
+  }
+  printf("OK %d blocks x %d rounds; %d blocks in clusters of %d x %d rounds, at most %u of %d inside\n", B, rounds,
+         BC, C, rounds, h2[3], n);
   return 0;
 }
