@@ -1,6 +1,6 @@
-"""Seeded repetitions of the GB300 designs across shapes and parameters (cohort mutex,
-counting barrier, condition variables, serving loop), each checked exactly against the
-oracle: a net for races that one shape per test could miss."""
+"""Seeded repetitions of the GB300 designs across shapes and parameters (cohort and cluster
+cohort mutexes, counting barrier, ticket-window semaphore, condition variables, serving loop),
+each checked exactly against the oracle: a net for races that one shape per test could miss."""
 import numpy as np
 import pytest
 
@@ -31,6 +31,36 @@ def test_cohort_mutex_repeated(i):
 
 
 @pytest.mark.parametrize("i", range(30))
+def test_cluster_mutex_repeated(i):
+    from paper_1110_4623_gb300 import runner
+    c = [2, 4, 8][i % 3]
+    B = [16, 296, 592, 1184, 1184][i % 5] // c * c
+    K = [0, 64, 1024, 7][i % 4]
+    budget = [1, 2, 64, 4096, 32767][i % 5]
+    delay, add = inputs.mutex_inputs(B, 20, 20_000 + i, max_delay=[0, 300, 2000][i % 3])
+    got = runner.MutexRun("cluster", B, 256, 20, K, delay, add, budget=budget, cluster=c, timeout_ns=10**10,
+                          bo=runner.backoff(min_ns=[0, 128][i % 2], max_ns=4000)).run()
+    want = calc.mutex_final(B, 20, K, add)
+    assert got["status"] == 0 and got["total"] == want["total"] and np.array_equal(got["data"], want["data"])
+    assert calc.check_grant_log(got["log"], got["ticket"], B, 20, False, group_bits=12) == []
+
+
+@pytest.mark.parametrize("i", range(30))
+def test_window_semaphore_repeated(i):
+    from paper_1110_4623_gb300 import runner
+    B = [1, 37, 296, 592, 1184][i % 5]
+    n = [1, 2, 4, 16, 64, 1000][i % 6]
+    hold, add = inputs.sem_inputs(B, 30, 30_000 + i, [0, 100][i % 2], [500, 5000][i % 2])
+    bo = runner.backoff(min_ns=[0, 16, 128][i % 3], max_ns=2000) if i % 3 else None
+    got = runner.SemRun("window", B, 128, 30, n, hold, add, bo=bo, timeout_ns=10**10).run()
+    want = calc.sem_final(B, 30, n, add)
+    assert got["status"] == 0 and np.array_equal(got["count"], want["count"]) and got["tally"] == want["tally"]
+    assert 1 <= got["max_occ"] <= min(n, B) and got["occupancy"] == 0
+    if n == 1:
+        assert got["total"] == want["total"]
+
+
+@pytest.mark.parametrize("i", range(30))
 def test_counting_barrier_repeated(i):
     from paper_1110_4623_gb300 import runner
     B = [2, 7, 64, 148, 600, 1184, 1216][i % 7]
@@ -46,7 +76,8 @@ def test_condvar_repeated(i):
     from paper_1110_4623_gb300 import runner
     P, C, items = [(1, 1, 50), (8, 8, 20), (100, 50, 10), (592, 592, 40), (1100, 100, 10)][i % 5]
     v = inputs.condvar_inputs(P * items, 777 + i)
-    got = runner.CondVarRun(P, C, items, [1, 2, 16, 64][i % 4], v,
+    mutex = ["ticket", "cohort", "cluster"][i % 3]  # every grid here is even: clusters of 2 fit
+    got = runner.CondVarRun(P, C, items, [1, 2, 16, 64][i % 4], v, mutex=mutex, cluster=2 if mutex == "cluster" else 0,
                             bo=runner.backoff(min_ns=[0, 64][i % 2], max_ns=2000)).run()
     want = calc.condvar_final(v, P, items, C)
     assert got["rc"] == 0 and got["status"] == 0
