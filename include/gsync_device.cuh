@@ -528,6 +528,16 @@ __device__ __forceinline__ Token mutex_lock(const MutexRef& m) {
   return t;
 }
 
+// Block-level lock with a wait bound for this call (ns), instead of the object's own: on
+// expiry the call returns GSYNC_ETIMEDOUT and, as any timed-out wait does, marks the object
+// aborted (an abandoned ticket leaves the lock unusable).
+template <int KIND>
+__device__ __forceinline__ Token mutex_lock(const MutexRef& m, uint64_t timeout_ns) {
+  MutexRef bounded = m;
+  bounded.timeout_ns = timeout_ns;
+  return mutex_lock<KIND>(bounded);
+}
+
 // Block-level unlock: the block's critical-section accesses complete before the release.
 template <int KIND>
 __device__ __forceinline__ void mutex_unlock(const MutexRef& m, Token t) {
@@ -729,6 +739,15 @@ __device__ __forceinline__ int sem_wait(const SemRef& s) {
   __syncthreads();
   const int rc = s_rc;
   return rc;
+}
+
+// Block-level wait with a wait bound for this call (ns): GSYNC_ETIMEDOUT on expiry, and the
+// object is marked aborted (a ticket taken and abandoned holds a permit forever).
+template <int KIND>
+__device__ __forceinline__ int sem_wait(const SemRef& s, uint64_t timeout_ns) {
+  SemRef bounded = s;
+  bounded.timeout_ns = timeout_ns;
+  return sem_wait<KIND>(bounded);
 }
 
 template <int KIND>
@@ -1140,6 +1159,18 @@ __device__ __forceinline__ int barrier_wait(BarrierRef& b) {
   __syncthreads();
   const int rc = s_rc;
   b.epoch = e1;
+  return rc;
+}
+
+// barrier_wait with a wait bound for this call (ns) instead of the object's own; on expiry
+// GSYNC_ETIMEDOUT, and the object is marked aborted (the crossing cannot complete for the
+// others either).
+template <int KIND>
+__device__ __forceinline__ int barrier_wait(BarrierRef& b, uint64_t timeout_ns) {
+  const uint64_t own = b.timeout_ns;
+  b.timeout_ns = timeout_ns;
+  const int rc = barrier_wait<KIND>(b);
+  b.timeout_ns = own;
   return rc;
 }
 

@@ -5,6 +5,7 @@
 //   user_kernel_cluster: the GB300 defaults -- the counting barrier, the cluster cohort mutex
 //     (its local lock in the kernel's shared memory) and the ticket-window semaphore -- in a
 //     launch with clusters of 4.
+//   bounded_waits_kernel: the per-call wait bounds of sem_wait, mutex_lock and barrier_wait.
 // Checked exactly: every round of the barrier sees every block's value of that round, a
 // counter updated with plain loads and stores under the mutex ends at blocks x rounds, and
 // the semaphore never admits more than its count.  Prints "OK" and exits 0 on success.
@@ -80,6 +81,30 @@ __global__ void user_kernel_cluster(void* bar_state, void* mutex_state, void* se
   }
   if (!ok && threadIdx.x == 0) atomicAdd(bad, 1u);
   gsync::mutex_cluster_end();  // block 0's local lock outlives every user in the cluster
+}
+
+// The per-call wait bounds: block 0 takes the semaphore's only permit and then waits for a
+// second one, takes the mutex and then asks for it again, and waits at a barrier that block 1
+// never reaches -- each second wait bounded at 1 ms, so each must return GSYNC_ETIMEDOUT after
+// about that long (rc[i], elapsed ns in ns_out[i]).
+__global__ void bounded_waits_kernel(void* sem_state, void* mutex_state, void* bar_state, int* rc, uint64_t* ns_out) {
+  if (blockIdx.x != 0) return;  // block 1 never arrives at the barrier
+  const gsync::SemRef s = gsync::sem_attach(sem_state);
+  const gsync::MutexRef m = gsync::mutex_attach(mutex_state);
+  gsync::BarrierRef bar = gsync::barrier_attach(bar_state);
+  const uint64_t bound = 1000000ull;
+  uint64_t t0;
+  int r = gsync::sem_wait<GSYNC_SEM_WINDOW>(s);
+  t0 = gsync::ptx::globaltimer();
+  if (r == GSYNC_OK) r = gsync::sem_wait<GSYNC_SEM_WINDOW>(s, bound);
+  if (threadIdx.x == 0) { rc[0] = r; ns_out[0] = gsync::ptx::globaltimer() - t0; }
+  gsync::Token t = gsync::mutex_lock<GSYNC_MUTEX_TICKET>(m);
+  t0 = gsync::ptx::globaltimer();
+  r = t.status == GSYNC_OK ? gsync::mutex_lock<GSYNC_MUTEX_TICKET>(m, bound).status : t.status;
+  if (threadIdx.x == 0) { rc[1] = r; ns_out[1] = gsync::ptx::globaltimer() - t0; }
+  t0 = gsync::ptx::globaltimer();
+  r = gsync::barrier_wait<GSYNC_BAR_COUNT>(bar, bound);
+  if (threadIdx.x == 0) { rc[2] = r; ns_out[2] = gsync::ptx::globaltimer() - t0; }
 }
 
 #define CHECK(x)                                                              \
@@ -161,7 +186,38 @@ int main() {
            (uint32_t)BC * rounds, h2[1], h2[2], h2[3], n);
     return 1;
   }
-  printf("OK %d blocks x %d rounds; %d blocks in clusters of %d x %d rounds, at most %u of %d inside\n", B, rounds,
-         BC, C, rounds, h2[3], n);
+
+  // Per-call wait bounds: each second wait must end with GSYNC_ETIMEDOUT after ~1 ms (the
+  // objects' own timeouts are 10 s).
+  cudaFunction_t fb;
+  CHECK(cudaGetFuncBySymbol(&fb, (const void*)bounded_waits_kernel));
+  void *sem3 = nullptr, *mtx3 = nullptr, *bar3 = nullptr;
+  int* rc3 = nullptr;
+  uint64_t* ns3 = nullptr;
+  const size_t bar3_bytes = gsync_barrier_bytes(GSYNC_BAR_COUNT, 2, 0);
+  CHECK(cudaMalloc(&sem3, gsync_sem_bytes(GSYNC_SEM_WINDOW)));
+  CHECK(cudaMalloc(&mtx3, gsync_mutex_bytes(GSYNC_MUTEX_TICKET, 2)));
+  CHECK(cudaMalloc(&bar3, bar3_bytes));
+  CHECK(cudaMalloc(&rc3, 3 * sizeof(int)));
+  CHECK(cudaMalloc(&ns3, 3 * sizeof(uint64_t)));
+  const uint64_t own = 10000000000ull;
+  CHECK(gsync_sem_init(sem3, gsync_sem_bytes(GSYNC_SEM_WINDOW), GSYNC_SEM_WINDOW, 1, nullptr, own, nullptr));
+  CHECK(gsync_mutex_init(mtx3, gsync_mutex_bytes(GSYNC_MUTEX_TICKET, 2), GSYNC_MUTEX_TICKET, 2, nullptr, own, nullptr));
+  CHECK(gsync_barrier_init(bar3, bar3_bytes, GSYNC_BAR_COUNT, 2, 0, own, nullptr));
+  void* args3[] = {&sem3, &mtx3, &bar3, &rc3, &ns3};
+  CHECK(gsync_launch_coresident((const void*)fb, 2, threads, 0, 1, args3, nullptr));
+  CHECK(cudaDeviceSynchronize());
+  int hrc[3];
+  uint64_t hns[3];
+  CHECK(cudaMemcpy(hrc, rc3, sizeof hrc, cudaMemcpyDeviceToHost));
+  CHECK(cudaMemcpy(hns, ns3, sizeof hns, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < 3; ++i)
+    if (hrc[i] != GSYNC_ETIMEDOUT || hns[i] < 1000000ull || hns[i] > 200000000ull) {
+      printf("FAIL bounded wait %d: rc %d after %llu ns\n", i, hrc[i], (unsigned long long)hns[i]);
+      return 1;
+    }
+  printf("OK %d blocks x %d rounds; %d blocks in clusters of %d x %d rounds, at most %u of %d inside; "
+         "bounded waits ended after %.2f / %.2f / %.2f ms\n", B, rounds, BC, C, rounds, h2[3], n, hns[0] / 1e6,
+         hns[1] / 1e6, hns[2] / 1e6);
   return 0;
 }
