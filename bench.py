@@ -596,15 +596,44 @@ def cpu_baseline(inputs, kind):
 # 78.4 ms; Fermi GTX580, 128 blocks, 1.47 ms) and the relative results of Section 6.
 PAPER_CONTEXT = {
     "same_word_atomics_per_s": {"tesla_gtx295": 240_000 / 78.407e-3, "fermi_gtx580": 128_000 / 1.479e-3},
+    "kernel_relaunch_as_barrier_us": {"gt200_quoted": "10-14 synchronous, 3-7 asynchronous (Volkov and Demmel)"},
     "atomic_barrier_vs_xf": {"tesla_gtx295": "< 0.05 at 60 blocks", "fermi_gtx580": "~0.30 at 128 blocks"},
     "fa_mutex_vs_spin_backoff": {"tesla_gtx295": "> 20 (spin+backoff < 5 % of FA)", "fermi_gtx580": "~0.5"},
 }
 
 
-def paper_context(terms, barrier, mutex):
+def relaunch_barrier_us(runner, reps=200):
+    """The alternative the paper sets its grid barrier against (Section 2): ending the kernel and
+    launching the next one.  An empty launch of the barrier workload's 1184-block grid (zero
+    rounds; a cooperative launch, as the workload's), back to back on one stream (asynchronous:
+    one launch's cost as a barrier) and with the host waiting for each (synchronous), in
+    microseconds per relaunch."""
+    import torch
+    br = runner.BarrierRun("count", NBLOCKS, BAR_THREADS, 0, full=False, param=8)
+    for _ in range(10):
+        assert br.launch() == 0
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        br.launch()
+    e.record()
+    torch.cuda.synchronize()
+    asyn = s.elapsed_time(e) * 1e3 / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        br.launch()
+        torch.cuda.synchronize()
+    syn = (time.perf_counter() - t0) * 1e6 / reps
+    return {"asynchronous": asyn, "synchronous": syn}
+
+
+def paper_context(terms, barrier, mutex, relaunch=None):
     """The paper's figures beside the same quantities measured on this GPU in this run."""
     return {"paper": PAPER_CONTEXT,
-            "gb300": {"same_word_atomics_per_s": terms["R_same_atom_ops_s"],
+            "gb300": {"kernel_relaunch_as_barrier_us": relaunch,
+                      "grid_barrier_us": barrier[barrier_name(*DEFAULT_BARRIER)]["ns_per_crossing"] / 1e3,
+                      "same_word_atomics_per_s": terms["R_same_atom_ops_s"],
                       "atomic_barrier_vs_xf": barrier["flag"]["ns_per_crossing"] / barrier["atomic"]["ns_per_crossing"],
                       "fa_mutex_vs_spin_backoff": float(np.mean([mutex["ticket"][k]["acq_per_s"] /
                                                                  mutex["cas_backoff"][k]["acq_per_s"]
@@ -721,7 +750,7 @@ def run_gpu(args):
         "semaphore": {"kind": DEFAULT_SEM, "backoff_ns": list(SEM_BACKOFF), "n": sem, "kinds": sem_kinds},
         "roofline_terms": terms,
         "design_rule": design_rule,
-        "paper_context": paper_context(terms, barrier, mutex),
+        "paper_context": paper_context(terms, barrier, mutex, relaunch_barrier_us(runner)),
         "clocks": clk,
         "gpu_launches": step.launches * args.steps,
         "wall_s_timed_loop": wall,
