@@ -98,7 +98,9 @@ __device__ __forceinline__ void st_relaxed_sys_s64(int64_t* p, int64_t v) {
 }
 
 // Block-wide int64 sum of pool[a, b): 16-byte streaming loads over the aligned middle, eight
-// of them in flight per thread (issued before any is added), scalars at the ends.
+// of them in flight per thread (issued before any is added; the last, partial pass -- every
+// request's last chunk -- too, with the loads past the end predicated off), scalars at the
+// ends.
 __device__ __forceinline__ long long block_sum(const int32_t* pool, int64_t a, int64_t b) {
   constexpr int kInFlight = 8;
   long long s = 0;
@@ -117,9 +119,15 @@ __device__ __forceinline__ long long block_sum(const int32_t* pool, int64_t a, i
 #pragma unroll
     for (int k = 0; k < kInFlight; ++k) s += (long long)x[k].x + x[k].y + x[k].z + x[k].w;
   }
-  for (; i < nv; i += blockDim.x) {
-    const int4 x = __ldcs(v + i);
-    s += (long long)x.x + x.y + x.z + x.w;
+  if (i < nv) {  // fewer than kInFlight left for this thread: issue them all before adding
+    int4 x[kInFlight];
+#pragma unroll
+    for (int k = 0; k < kInFlight; ++k) {
+      const int64_t j = i + k * (int64_t)blockDim.x;
+      x[k] = j < nv ? __ldcs(v + j) : make_int4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < kInFlight; ++k) s += (long long)x[k].x + x[k].y + x[k].z + x[k].w;
   }
   for (int64_t i = b4 + threadIdx.x; i < b; i += blockDim.x) s += pool[i];
   __shared__ long long red[kThreads / 32];
