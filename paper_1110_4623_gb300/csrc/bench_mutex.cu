@@ -18,7 +18,34 @@ constexpr int kNoLock = -1;     // no mutex at all: the critical-section probe (
 constexpr int kFrameOnly = -2;  // the probe's frame (acquire load, barriers, release) around an empty body
 constexpr uint32_t kGolden = 0x9E3779B1u;
 
-template <int KIND>
+// The critical section's data update: data[i] += v ^ (i * kGolden) for i < cs_words, word i on
+// thread i mod blockDim.  WIDE (more words than threads): each thread issues the loads of up to
+// kCsInFlight of its words before adding, so K words per thread cost about one L2 round trip
+// rather than K of them.  Narrow sections keep the one-word loop in a kernel of their own.
+constexpr int kCsInFlight = 4;
+template <bool WIDE>
+__device__ __forceinline__ void cs_update(uint32_t* data, uint32_t cs_words, uint32_t v) {
+  if (!WIDE) {
+    for (uint32_t i = threadIdx.x; i < cs_words; i += blockDim.x) data[i] += v ^ (i * kGolden);
+    return;
+  }
+  const uint32_t step = blockDim.x * kCsInFlight;
+  for (uint32_t base = threadIdx.x; base < cs_words; base += step) {
+    uint32_t x[kCsInFlight];
+#pragma unroll
+    for (int k = 0; k < kCsInFlight; ++k) {
+      const uint32_t j = base + k * blockDim.x;
+      x[k] = j < cs_words ? data[j] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kCsInFlight; ++k) {
+      const uint32_t j = base + k * blockDim.x;
+      if (j < cs_words) data[j] = x[k] + (v ^ (j * kGolden));
+    }
+  }
+}
+
+template <int KIND, bool WIDE>
 __global__ void __launch_bounds__(kMaxThreads, 8)
     mutex_workload_kernel(uint32_t* state, int acq, int cs_words, const uint32_t* __restrict__ delay,
                           const uint32_t* __restrict__ addend, uint32_t* data, uint32_t* total, uint32_t* grant_log,
@@ -73,7 +100,7 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
                                                      : t.ticket;
     }
     if (KIND != kFrameOnly)
-      for (uint32_t i = tid; i < (uint32_t)cs_words; i += blockDim.x) data[i] += v ^ (i * kGolden);
+      cs_update<WIDE>(data, (uint32_t)cs_words, v);
     // ---- end of critical section ----
     if (KIND >= 0) {
       gsync::mutex_unlock<KIND>(m, t);
@@ -90,18 +117,22 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
 using KernelFn = void (*)(uint32_t*, int, int, const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*,
                           uint32_t*, uint32_t*, uint32_t*);
 
-KernelFn pick(int kind) {
+template <bool WIDE>
+KernelFn pick_width(int kind) {
   switch (kind) {
-    case GSYNC_MUTEX_CAS_SPIN: return mutex_workload_kernel<GSYNC_MUTEX_CAS_SPIN>;
-    case GSYNC_MUTEX_CAS_BACKOFF: return mutex_workload_kernel<GSYNC_MUTEX_CAS_BACKOFF>;
-    case GSYNC_MUTEX_TICKET: return mutex_workload_kernel<GSYNC_MUTEX_TICKET>;
-    case GSYNC_MUTEX_SLEEP_QUEUE: return mutex_workload_kernel<GSYNC_MUTEX_SLEEP_QUEUE>;
-    case GSYNC_MUTEX_COHORT: return mutex_workload_kernel<GSYNC_MUTEX_COHORT>;
-    case GSYNC_MUTEX_RING: return mutex_workload_kernel<GSYNC_MUTEX_RING>;
-    case GSYNC_MUTEX_CLUSTER: return mutex_workload_kernel<GSYNC_MUTEX_CLUSTER>;
+    case GSYNC_MUTEX_CAS_SPIN: return mutex_workload_kernel<GSYNC_MUTEX_CAS_SPIN, WIDE>;
+    case GSYNC_MUTEX_CAS_BACKOFF: return mutex_workload_kernel<GSYNC_MUTEX_CAS_BACKOFF, WIDE>;
+    case GSYNC_MUTEX_TICKET: return mutex_workload_kernel<GSYNC_MUTEX_TICKET, WIDE>;
+    case GSYNC_MUTEX_SLEEP_QUEUE: return mutex_workload_kernel<GSYNC_MUTEX_SLEEP_QUEUE, WIDE>;
+    case GSYNC_MUTEX_COHORT: return mutex_workload_kernel<GSYNC_MUTEX_COHORT, WIDE>;
+    case GSYNC_MUTEX_RING: return mutex_workload_kernel<GSYNC_MUTEX_RING, WIDE>;
+    case GSYNC_MUTEX_CLUSTER: return mutex_workload_kernel<GSYNC_MUTEX_CLUSTER, WIDE>;
   }
   return nullptr;
 }
+
+// A critical section wider than the block runs in the kernel that batches its loads.
+KernelFn pick(int kind, bool wide) { return wide ? pick_width<true>(kind) : pick_width<false>(kind); }
 
 int check_work(const gsync_mutex_work* w) {
   if (!w || w->nblocks < 1 || w->acq < 0 || w->cs_words < 0 || w->block_threads < 32 ||
@@ -127,9 +158,14 @@ size_t round_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 namespace gsync_impl {
 int max_blocks_mutex(int kind, int block_threads, int* out) {
-  KernelFn k = pick(kind);
-  if (!k) return GSYNC_EINVAL;
-  return max_coresident(k, block_threads, 1, 0, out);
+  // both widths must fit: the grid limit is the smaller of the two
+  KernelFn kn = pick(kind, false), kw = pick(kind, true);
+  if (!kn || !kw) return GSYNC_EINVAL;
+  int n_narrow = 0, n_wide = 0;
+  if (int rc = max_coresident(kn, block_threads, 1, 0, &n_narrow)) return rc;
+  if (int rc = max_coresident(kw, block_threads, 1, 0, &n_wide)) return rc;
+  *out = n_narrow < n_wide ? n_narrow : n_wide;
+  return GSYNC_OK;
 }
 }  // namespace gsync_impl
 
@@ -139,7 +175,7 @@ extern "C" int gsync_bench_mutex(void* state, const gsync_mutex_work* w, void* s
   if (!w->addend || !w->total || !w->grant_log || !w->ticket || !w->count || !w->status ||
       (w->cs_words > 0 && !w->data))
     return GSYNC_EINVAL;
-  KernelFn k = pick(w->kind);
+  KernelFn k = pick(w->kind, w->cs_words > w->block_threads);
   if (!k) return GSYNC_EINVAL;
   return launch_coresident(k, w->nblocks, w->block_threads, launch_cluster(w), 0, (cudaStream_t)stream,
                            (uint32_t*)state, w->acq,
@@ -228,11 +264,14 @@ extern "C" int gsync_probe_cs(int cs_words, int block_threads, int iters, void* 
   GSYNC_CUDA(cudaEventCreate(&e1));
   GSYNC_CUDA(cudaEventRecord(e0, st));
   if (cs_words < 0) {  // frame only: the acquire load, barriers and release store, no body
-    mutex_workload_kernel<kFrameOnly><<<1, block_threads, 0, st>>>(nullptr, iters, 0, nullptr, add, data, total, log,
+    mutex_workload_kernel<kFrameOnly, false><<<1, block_threads, 0, st>>>(nullptr, iters, 0, nullptr, add, data, total, log,
                                                                   tick, count, status);
+  } else if (cs_words > block_threads) {  // the same body, and the same width, as the workload's
+    mutex_workload_kernel<kNoLock, true><<<1, block_threads, 0, st>>>(nullptr, iters, cs_words, nullptr, add, data,
+                                                                     total, log, tick, count, status);
   } else {
-    mutex_workload_kernel<kNoLock><<<1, block_threads, 0, st>>>(nullptr, iters, cs_words, nullptr, add, data, total,
-                                                               log, tick, count, status);
+    mutex_workload_kernel<kNoLock, false><<<1, block_threads, 0, st>>>(nullptr, iters, cs_words, nullptr, add, data,
+                                                                      total, log, tick, count, status);
   }
   GSYNC_CUDA(cudaGetLastError());
   GSYNC_CUDA(cudaEventRecord(e1, st));
