@@ -54,8 +54,11 @@ def test_contention_sweep_full_size(kind, nblocks, cs_words):
 
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("nblocks,threads,acq,cs_words", [(1, 32, 50, 7), (3, 64, 17, 33), (37, 96, 9, 1000),
-                                                            (151, 256, 5, 1025)])
+                                                            (151, 256, 5, 1025), (5, 128, 20, 128), (9, 128, 20, 129),
+                                                            (23, 256, 10, 600)])
 def test_ragged_shapes(kind, nblocks, threads, acq, cs_words):
+    # A section wider than the block (cs_words > threads) runs the kernel that batches up to
+    # four loads per thread: exactly one word per thread, one word more, and partial passes.
     check(kind, nblocks, threads, acq, cs_words, max_delay=300)
 
 
