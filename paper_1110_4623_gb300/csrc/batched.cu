@@ -138,6 +138,9 @@ __global__ void __launch_bounds__(kMaxThreads, 8) batched_kernel(Args a) {
     if (tid == 0 && !s_fail) {
       const uint32_t i = b + j * G;
       const uint32_t key = (uint32_t)a.keys[i];
+      // The addend is this block's own input: read it before the lock, so that its load (from
+      // DRAM on a launch's first touch) overlaps the wait instead of lengthening the section.
+      const int64_t add = a.adds[i];
       if (key >= (uint32_t)a.nkeys) {
         ptx::atom_or_relaxed(a.status, GSYNC_STATUS_VIOLATION);
         s_fail = 1;
@@ -164,7 +167,7 @@ __global__ void __launch_bounds__(kMaxThreads, 8) batched_kernel(Args a) {
           record_status(a.status, t.status);
           s_fail = 1;
         } else {
-          a.sum[key] += a.adds[i];
+          a.sum[key] += add;
           a.count[key] += 1u;
           unlock_by_policy(m, t);
         }
