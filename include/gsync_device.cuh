@@ -605,6 +605,21 @@ __device__ __forceinline__ void cond_signal_thread(const CondRef& cv) {
   if (sg != tk) ptx::st_relaxed(cv.signals(), sg + 1u);
 }
 
+// The two counters a signal reads.  Only holders of the mutex write them, so a snapshot that
+// thread 0 takes while it holds the mutex stays exact until it releases the mutex (waiting on
+// any condition variable releases it too).  Taking the snapshot together with the critical
+// section's own first loads puts the signal's round trip in their shadow.
+struct CondSnap {
+  uint32_t signals, tickets;
+};
+__device__ __forceinline__ CondSnap cond_snapshot_thread(const CondRef& cv) {
+  return CondSnap{ptx::ld_relaxed(cv.signals()), ptx::ld_relaxed(cv.tickets())};
+}
+// Thread 0, holding the mutex without a break since it took `snap` of cv: as cond_signal_thread.
+__device__ __forceinline__ void cond_signal_thread(const CondRef& cv, CondSnap snap) {
+  if (snap.signals != snap.tickets) ptx::st_relaxed(cv.signals(), snap.signals + 1u);
+}
+
 // Thread 0, holding the mutex: release every waiter.
 __device__ __forceinline__ void cond_broadcast_thread(const CondRef& cv) {
   ptx::st_relaxed(cv.signals(), ptx::ld_relaxed(cv.tickets()));

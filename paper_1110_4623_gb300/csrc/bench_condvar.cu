@@ -38,6 +38,9 @@ __global__ void __launch_bounds__(kMaxThreads)
   __shared__ int s_ok;
   __shared__ uint32_t s_id;
   Queue qv = {0u, 0u, 0u, 1u};  // thread 0's copy of *q while it holds the mutex
+  // ... and of the counters of the condition variable it signals (taken in the same round trip)
+  const gsync::CondRef& to_signal = producer ? not_empty : not_full;
+  gsync::CondSnap snap = {0u, 0u};
   int64_t my_sum = 0;
   uint32_t taken = 0;
   for (int i = 0; i < ops; ++i) {
@@ -51,6 +54,7 @@ __global__ void __launch_bounds__(kMaxThreads)
     int rc = GSYNC_OK;
     for (;;) {
       if (t0) {
+        snap = gsync::cond_snapshot_thread(to_signal);
         qv = *q;
         s_ok = producer ? qv.count < qv.capacity : qv.count > 0u;
       }
@@ -69,11 +73,11 @@ __global__ void __launch_bounds__(kMaxThreads)
         const uint32_t id = blockIdx.x * (uint32_t)items_per_producer + (uint32_t)i;
         buf[qv.tail % qv.capacity] = id;
         *q = Queue{qv.count + 1u, qv.head, qv.tail + 1u, qv.capacity};
-        gsync::cond_signal_thread(not_empty);
+        gsync::cond_signal_thread(not_empty, snap);
       } else {
         s_id = buf[qv.head % qv.capacity];
         *q = Queue{qv.count - 1u, qv.head + 1u, qv.tail, qv.capacity};
-        gsync::cond_signal_thread(not_full);
+        gsync::cond_signal_thread(not_full, snap);
       }
     }
     gsync::mutex_unlock<MKIND>(m, tok);
@@ -118,7 +122,9 @@ __global__ void __launch_bounds__(kMaxThreads)
     __syncthreads();
     const bool put = (i & 1) == 0;
     if (!frame_only) {
+      gsync::CondSnap snap = {0u, 0u};
       if (t0) {
+        snap = gsync::cond_snapshot_thread(put ? not_empty : not_full);
         qv = *q;
         s_ok = put ? qv.count < qv.capacity : qv.count > 0u;
       }
@@ -127,11 +133,11 @@ __global__ void __launch_bounds__(kMaxThreads)
         if (put) {
           buf[qv.tail % qv.capacity] = (uint32_t)i;
           *q = Queue{qv.count + 1u, qv.head, qv.tail + 1u, qv.capacity};
-          gsync::cond_signal_thread(not_empty);
+          gsync::cond_signal_thread(not_empty, snap);
         } else {
           s_id = buf[qv.head % qv.capacity];
           *q = Queue{qv.count - 1u, qv.head + 1u, qv.tail, qv.capacity};
-          gsync::cond_signal_thread(not_full);
+          gsync::cond_signal_thread(not_full, snap);
         }
       }
     }
