@@ -398,12 +398,17 @@ int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_backoff* backof
  *    launch and whenever a key's policy kind changes (the objects are left consistent by
  *    every completed launch otherwise).
  *  - key_class (device, nkeys bytes): class of each key, < nclasses.
- *  - policy (device, nclasses x 4 x u32): {kind (CAS_SPIN, CAS_BACKOFF, TICKET or CLUSTER;
- *    others act as TICKET), min_ns, max_ns, budget}: backoff of the CAS kind, or sleep per
- *    waiter ahead of the ticket kinds; min_ns = 0 spins without sleeping.  CLUSTER (the
- *    cluster cohort lock) applies in a cluster launch (cluster > 1) to keys below 256, whose
- *    local locks live in the blocks' shared memory, with `budget` passes per cohort (0 = the
- *    default, 64); elsewhere it acts as TICKET.  budget is ignored by the other kinds.
+ *  - policy (device, nclasses x 4 x u32): {kind (CAS_SPIN, CAS_BACKOFF, TICKET, CLUSTER or
+ *    GSYNC_BATCHED_TICKET_CARRY; others act as TICKET), min_ns, max_ns, budget}: backoff of the
+ *    CAS kind, or sleep per waiter ahead of the ticket kinds; min_ns = 0 spins without
+ *    sleeping.  CLUSTER (the cluster cohort lock) applies in a cluster launch (cluster > 1) to
+ *    keys below 256, whose local locks live in the blocks' shared memory, with `budget` passes
+ *    per cohort (0 = the default, 64); elsewhere it acts as TICKET.  budget is ignored by the
+ *    other kinds.  GSYNC_BATCHED_TICKET_CARRY is the ticket lock whose turn line carries the
+ *    key's count and sum: one 16-byte record {turn, count, sum} read by the waiter's 128-bit
+ *    acquire load and written by the holder's 128-bit release store, so a hand-off moves the
+ *    guarded data with it; a second kernel on the same stream copies such keys' count and sum
+ *    to count[] and sum[] after the launch and zeroes them in the record.
  *  - keys (device, nacq x i32), adds (device, nacq x i64); sum (device, nkeys x i64) and
  *    count (device, nkeys x u32) zeroed by the caller.
  *  - group_state (device, 128-byte aligned): ngroups x 512 bytes, zeroed before the first
@@ -414,6 +419,7 @@ int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_backoff* backof
  *    (checked on the device; a violation sets GSYNC_STATUS_CONFIG and skips the barriers).
  *  - plain_launch = 1 uses an ordinary launch after the co-residency check instead of a
  *    cooperative one (for stream capture into a CUDA graph); cluster must then be 1. */
+#define GSYNC_BATCHED_TICKET_CARRY 16u
 typedef struct gsync_batched_work {
   int32_t nkeys, nacq, nblocks, block_threads, ngroups, rounds, cluster, nclasses;
   int32_t plain_launch, reserved;
@@ -434,6 +440,7 @@ typedef struct gsync_batched_work {
   uint32_t* bad;
   uint32_t* status;
 } gsync_batched_work;
+/* Launches the batched kernel and then batched_collect_kernel (two kernels, one stream). */
 int gsync_bench_batched(const gsync_batched_work* w, void* stream);
 
 /* Persistent serving loop with continuous batching (the paper motivates its primitives

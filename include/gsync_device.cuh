@@ -148,6 +148,20 @@ __device__ __forceinline__ void atom_or_relaxed(uint32_t* p, uint32_t v) {
 __device__ __forceinline__ void atom_max_relaxed(uint32_t* p, uint32_t v) {
   asm volatile("red.relaxed.gpu.global.max.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// 128-bit acquire load and release store of one 16-byte-aligned record (two u64 halves, the
+// low half at the lower address).  A .b128 access is one memory operation, not two 64-bit
+// halves, so a reader that sees one half of a release sees the other.
+__device__ __forceinline__ void ld_acquire_b128(const void* p, uint64_t& lo, uint64_t& hi) {
+  asm volatile("{\n\t.reg .b128 t;\n\tld.acquire.gpu.global.b128 t, [%2];\n\tmov.b128 {%0, %1}, t;\n\t}"
+               : "=l"(lo), "=l"(hi)
+               : "l"(p)
+               : "memory");
+}
+__device__ __forceinline__ void st_release_b128(void* p, uint64_t lo, uint64_t hi) {
+  asm volatile("{\n\t.reg .b128 t;\n\tmov.b128 t, {%0, %1};\n\tst.release.gpu.global.b128 [%2], t;\n\t}"
+               ::"l"(lo), "l"(hi), "l"(p)
+               : "memory");
+}
 __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;

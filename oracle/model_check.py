@@ -163,6 +163,63 @@ class TicketMutex:
         raise AssertionError(pc)
 
 
+class CarryTicketMutex:
+    """Ticket mutex whose turn word carries the guarded data (the batched kernel's
+    GSYNC_BATCHED_TICKET_CARRY; a GB300 design, not in the paper).
+
+    lock: t <- fetch-and-add(ticket, 1); read the record (turn, count, sum) as one access until
+    turn = t.  The critical section adds f(t) = t + 1 to the sum it read and counts one more.
+    unlock: write the record (t + 1, count + 1, sum + f(t)) as one access.  Each holder must
+    see its predecessors' data: at entry, count = t - base and sum = the sum of f over the
+    earlier tickets (mod 2^32 here), else a violation is reported.
+    broken="split_read" reads the data first and the turn after, as two accesses (a stale
+    read); broken="turn_only" publishes the turn without the data.
+    """
+    kind, capacity, fifo = "mutex", 1, True
+
+    def __init__(self, base=0, broken=None):
+        self.base, self.broken = base & M32, broken
+
+    def _f(self, t):
+        return (t + 1) & M32
+
+    def _want_sum(self, t):
+        s, u = 0, self.base
+        while u != t:
+            s = (s + self._f(u)) & M32
+            u = inc(u)
+        return s
+
+    def init(self, nproc, ops):
+        # shared: (ticket, turn, count, sum); local: (pc, k, t, count read, sum read)
+        return (self.base, self.base, 0, 0), tuple((0, 0, 0, 0, 0) for _ in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, t, c, sm = loc
+        ticket, turn, count, total = sh
+        if pc == 0:
+            return (1, k, ticket, c, sm), (inc(ticket), turn, count, total), None
+        if pc == 1:
+            if self.broken == "split_read":  # data now, turn in the next step
+                return (4, k, t, count, total), sh, None
+            return ((PC_ENTER if turn == t else 1), k, t, count, total), sh, None
+        if pc == 4:
+            return ((PC_ENTER if turn == t else 1), k, t, c, sm), sh, None
+        if pc == PC_ENTER:
+            if c != ((t - self.base) & M32) or sm != self._want_sum(t):
+                return loc, sh, ("violation", f"ticket {t:#x} entered with count {c} and sum {sm}")
+            return (PC_EXIT, k, t, c, sm), sh, ("enter", t)
+        if pc == PC_EXIT:
+            return (2, k, t, c, sm), sh, ("exit",)
+        if pc == 2:
+            k += 1
+            nxt = ((0 if k < ops else DONE), k, t, c, sm)
+            if self.broken == "turn_only":
+                return nxt, (ticket, inc(t), count, total), None
+            return nxt, (ticket, inc(t), inc(c), (sm + self._f(t)) & M32), None
+        raise AssertionError(pc)
+
+
 class QueueMutex:
     """Sleep-waiting queue lock with one flag slot per waiter (ring of Q slots, Q a power of 2).
 

@@ -22,7 +22,8 @@ from . import runner
 HOT, WARM, COLD = 0, 1, 2
 NCLASSES = 3
 
-# (kind, min_ns, max_ns): min_ns = 0 means spin without sleeping.
+# (kind, min_ns, max_ns): min_ns = 0 means spin without sleeping.  ticket_carry is the ticket
+# lock whose turn record carries the key's count and sum through each hand-off.
 CANDIDATES = [
     ("cas_spin", 0, 0),
     ("cas_backoff", 32, 1024),
@@ -30,6 +31,8 @@ CANDIDATES = [
     ("ticket", 0, 0),
     ("ticket", 64, 2000),
     ("ticket", 256, 4000),
+    ("ticket_carry", 0, 0),
+    ("ticket_carry", 64, 2000),
 ]
 CLUSTERS = [1, 2, 4, 8]
 # Tried last, for the hot and warm classes, once a cluster size above 1 is chosen: the cluster

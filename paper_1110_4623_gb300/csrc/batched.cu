@@ -9,9 +9,9 @@
 // that belong to a barrier group also cross `rounds` group barriers spread evenly over their
 // acquisitions, with the sampled slot check of the barrier workload (partner
 // p = (j + r + 1) mod size inside the group).  The autotuner chooses, per contention class,
-// the mutex kind (spin / spin + backoff / ticket, or -- in a cluster launch -- the cluster
-// cohort lock for keys below kLocalKeys), the backoff constants (0 = pure spinning,
-// otherwise __nanosleep) and the cluster size of the group barriers.
+// the mutex kind (spin / spin + backoff / ticket, the carrying ticket lock, or -- in a cluster
+// launch -- the cluster cohort lock for keys below kLocalKeys), the backoff constants (0 = pure
+// spinning, otherwise __nanosleep) and the cluster size of the group barriers.
 #include "common.cuh"
 
 using namespace gsync_impl;
@@ -61,6 +61,52 @@ __device__ __forceinline__ void unlock_by_policy(const gsync::MutexRef& m, const
   if (m.kind == GSYNC_MUTEX_TICKET) gsync::mutex_unlock_thread<GSYNC_MUTEX_TICKET>(m, t.ticket);
   else if (m.kind == GSYNC_MUTEX_CLUSTER) gsync::mutex_unlock_thread<GSYNC_MUTEX_CLUSTER>(m, t);
   else gsync::mutex_unlock_thread<GSYNC_MUTEX_CAS_SPIN>(m, t.ticket);
+}
+
+// GSYNC_BATCHED_TICKET_CARRY: the ticket lock (take a ticket, wait for the turn, sleeping in
+// proportion to the waiters ahead) whose turn line also holds what it guards.  Line 2 of the
+// key's object is one 16-byte record {turn, count, sum}: the waiter's acquire load of the
+// turn brings the count and sum with it, and the holder's release store of the next turn
+// writes the new count and sum in the same store.  A hand-off therefore carries the data:
+// the critical section makes no L2 round trip of its own, and the release waits for no
+// earlier store.  The key's count and sum stay in the record until batched_collect_kernel
+// copies them out after the launch.
+__device__ __forceinline__ int carry_add(uint32_t* obj, const uint32_t* pol, int64_t add, uint64_t timeout_ns) {
+  uint32_t* ticket = obj + 1 * gsync::kLineWords;
+  uint32_t* rec = obj + 2 * gsync::kLineWords;
+  const uint32_t t = ptx::atom_add_relaxed(ticket, 1u);
+  gsync::Waiter w;
+  uint64_t lo, hi;
+  for (;;) {
+    ptx::ld_acquire_b128(rec, lo, hi);
+    const uint32_t ahead = t - (uint32_t)lo;
+    if (ahead == 0u) break;
+    if (int rc = w.tick(timeout_ns, obj + gsync::kHdrAbort)) return rc;
+    if (pol[1] && ahead > 1u && ahead < 0x80000000u) {
+      const uint32_t ns = (ahead - 1u) * pol[1];
+      __nanosleep(ns < pol[2] ? ns : pol[2]);
+    }
+  }
+  // critical section: count + 1 and sum + add, published with the next turn
+  const uint64_t next = (uint64_t)(t + 1u) | ((uint64_t)((uint32_t)(lo >> 32) + 1u) << 32);
+  ptx::st_release_b128(rec, next, (uint64_t)((int64_t)hi + add));
+  return GSYNC_OK;
+}
+
+// After the batched kernel: each carrying key's count and sum move from its record to count[]
+// and sum[], and the record's count and sum return to zero (its turn stays, matching the
+// ticket counter), so the next launch starts from zero like the other kinds' outputs.
+__global__ void batched_collect_kernel(Args a) {
+  const uint32_t key = blockIdx.x * blockDim.x + threadIdx.x;
+  if (key >= (uint32_t)a.nkeys) return;
+  const uint32_t cls = a.key_class[key];
+  if (a.policy[4u * (cls < (uint32_t)a.nclasses ? cls : 0u)] != GSYNC_BATCHED_TICKET_CARRY) return;
+  uint64_t* rec = (uint64_t*)(a.mutex_state + key * kMutexObjWords + 2 * gsync::kLineWords);
+  const uint64_t lo = rec[0];
+  a.count[key] = (uint32_t)(lo >> 32);
+  a.sum[key] = (int64_t)rec[1];
+  rec[0] = lo & 0xFFFFFFFFull;
+  rec[1] = 0;
 }
 
 // One crossing of the group barrier with the sampled slot check.
@@ -147,6 +193,13 @@ __global__ void __launch_bounds__(kMaxThreads, 8) batched_kernel(Args a) {
       } else {
         const uint32_t cls = a.key_class[key];
         const uint32_t* pol = a.policy + 4u * (cls < (uint32_t)a.nclasses ? cls : 0u);
+        if (pol[0] == GSYNC_BATCHED_TICKET_CARRY) {
+          const int rc = carry_add(a.mutex_state + key * kMutexObjWords, pol, add, a.timeout_ns);
+          if (rc != GSYNC_OK) {
+            record_status(a.status, rc);
+            s_fail = 1;
+          }
+        } else {
         gsync::MutexRef m;
         m.s = a.mutex_state + key * kMutexObjWords;
         const bool cohort = BKIND == GSYNC_BAR_CLUSTER && pol[0] == (uint32_t)GSYNC_MUTEX_CLUSTER && key < kLocalKeys;
@@ -170,6 +223,7 @@ __global__ void __launch_bounds__(kMaxThreads, 8) batched_kernel(Args a) {
           a.sum[key] += add;
           a.count[key] += 1u;
           unlock_by_policy(m, t);
+        }
         }
       }
     }
@@ -231,17 +285,22 @@ extern "C" int gsync_bench_batched(const gsync_batched_work* w, void* stream) {
   a.nclasses = w->nclasses;
   a.ngroups = w->ngroups;
   cudaStream_t st = (cudaStream_t)stream;
-  if (cluster > 1)
-    return launch_coresident(batched_kernel<GSYNC_BAR_CLUSTER>, w->nblocks, w->block_threads, cluster, 0, st, a);
-  if (w->plain_launch) {
+  int rc = GSYNC_OK;
+  if (cluster > 1) {
+    rc = launch_coresident(batched_kernel<GSYNC_BAR_CLUSTER>, w->nblocks, w->block_threads, cluster, 0, st, a);
+  } else if (w->plain_launch) {
     // For stream capture: an ordinary launch after the same co-residency check.  All blocks
     // are resident as long as no other kernel occupies the GPU when the graph runs.
     int maxb = 0;
-    if (int rc = max_coresident(batched_kernel<GSYNC_BAR_ATOMIC>, w->block_threads, 1, 0, &maxb)) return rc;
+    if ((rc = max_coresident(batched_kernel<GSYNC_BAR_ATOMIC>, w->block_threads, 1, 0, &maxb))) return rc;
     if (w->nblocks > maxb) return GSYNC_ENOTRESIDENT;
     batched_kernel<GSYNC_BAR_ATOMIC><<<w->nblocks, w->block_threads, 0, st>>>(a);
     GSYNC_CUDA(cudaGetLastError());
-    return GSYNC_OK;
+  } else {
+    rc = launch_coresident(batched_kernel<GSYNC_BAR_ATOMIC>, w->nblocks, w->block_threads, 1, 0, st, a);
   }
-  return launch_coresident(batched_kernel<GSYNC_BAR_ATOMIC>, w->nblocks, w->block_threads, 1, 0, st, a);
+  if (rc != GSYNC_OK) return rc;
+  batched_collect_kernel<<<(w->nkeys + 255) / 256, 256, 0, st>>>(a);
+  GSYNC_CUDA(cudaGetLastError());
+  return GSYNC_OK;
 }

@@ -19,6 +19,10 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOTRESIDENT", 3: "ETIMEDOUT", 4: "ECU
 GSYNC_STATUS_TIMEOUT, GSYNC_STATUS_ABORTED, GSYNC_STATUS_VIOLATION, GSYNC_STATUS_CONFIG = 1, 2, 4, 8
 
 MUTEX_KINDS = {"cas_spin": 0, "cas_backoff": 1, "ticket": 2, "sleep_queue": 3, "cohort": 4, "ring": 5, "cluster": 6}
+# Policy kinds of the batched kernel: the mutex kinds it runs, plus the ticket lock whose turn
+# line carries the guarded count and sum (GSYNC_BATCHED_TICKET_CARRY).
+BATCHED_TICKET_CARRY = 16
+BATCHED_POLICY_KINDS = {**MUTEX_KINDS, "ticket_carry": BATCHED_TICKET_CARRY}
 COHORT_DEFAULT_BUDGET = 64
 BARRIER_KINDS = {"atomic": 0, "flag": 1, "tree": 2, "cluster": 3, "sharded": 4, "die": 5, "split": 6, "count": 7}
 SEM_KINDS = {"ticket": 0, "spin": 1, "spin_backoff": 2, "window": 3}

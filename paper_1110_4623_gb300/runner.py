@@ -480,7 +480,7 @@ class BatchedRun:
         for entry in table:
             kind, mn, mx = entry[:3]
             budget = entry[3] if len(entry) > 3 else 0
-            flat += [G.MUTEX_KINDS[kind] if isinstance(kind, str) else int(kind), int(mn), int(mx), int(budget)]
+            flat += [G.BATCHED_POLICY_KINDS[kind] if isinstance(kind, str) else int(kind), int(mn), int(mx), int(budget)]
         self.policy.copy_(torch.tensor(flat, dtype=torch.int32))
         self.mutex_state.zero_()
         self.graph = None

@@ -72,6 +72,39 @@ def test_cluster_cohort_policy(cluster, policy):
     check(run, keys, adds, got, 23)
 
 
+@pytest.mark.parametrize("cluster,policy", [
+    (1, [("ticket_carry", 0, 0)] * 3),
+    (1, [("ticket_carry", 128, 4000)] * 3),
+    (1, [("ticket_carry", 0, 0), ("cas_backoff", 32, 1024), ("ticket", 64, 2000)]),
+    (4, [("ticket_carry", 0, 0), ("cluster", 128, 4000), ("ticket_carry", 64, 2000)])])
+def test_ticket_carry_policy(cluster, policy):
+    # The ticket lock whose turn record carries each key's count and sum, alone and beside
+    # the other kinds, twice in a row on the same objects: the second launch starts from the
+    # records the collect pass left (turns kept, counts and sums back at zero).
+    run, keys, adds = make(1_000_000 if cluster == 1 and policy[1][0] == "ticket_carry" else 200_000,
+                           cluster=cluster, policy=policy, rounds=29)
+    for _ in range(2):
+        got = run.run()
+        assert got["rc"] == 0
+        check(run, keys, adds, got, 29)
+
+
+def test_ticket_carry_policy_change_and_graph_replay():
+    # Switching a class from the plain ticket lock to the carrying one (and back) re-zeroes
+    # the objects; a captured graph of the two kernels replays exactly.
+    import torch
+    run, keys, adds = make(300_000, rounds=20, plain_launch=True, policy=[("ticket", 0, 0)] * 3)
+    check(run, keys, adds, run.run(), 20)
+    run.set_policy([("ticket_carry", 0, 0), ("ticket_carry", 64, 2000), ("cas_spin", 0, 0)])
+    run.capture()
+    for _ in range(3):
+        run.replay()
+        torch.cuda.synchronize()
+        check(run, keys, adds, run.results(), 20)
+    run.set_policy([("ticket", 0, 0)] * 3)
+    check(run, keys, adds, run.run(), 20)
+
+
 def test_graph_capture_replays_exactly():
     import torch
     run, keys, adds = make(300_000, rounds=20, plain_launch=True)

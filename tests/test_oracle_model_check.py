@@ -14,6 +14,8 @@ CORRECT = [
     ("ticket", mc.TicketMutex(), 3, 2),
     ("ticket_literal_unlock", mc.TicketMutex(literal=True), 3, 2),
     ("ticket_wrap", mc.TicketMutex(base=W), 3, 2),
+    ("ticket_carry", mc.CarryTicketMutex(), 3, 2),
+    ("ticket_carry_wrap", mc.CarryTicketMutex(base=W), 3, 2),
     ("queue", mc.QueueMutex(q=4), 3, 2),
     ("queue_wrap", mc.QueueMutex(q=4, base=W), 3, 2),
     ("queue_exact_fit", mc.QueueMutex(q=2, base=W), 2, 3),
@@ -79,6 +81,8 @@ def test_algorithm_is_safe_and_live(name, model, nproc, ops):
 BROKEN = [
     ("test_then_set", mc.SpinMutex(broken="test_then_set"), 2, 1, "critical section"),
     ("ticket_no_advance", mc.TicketMutex(broken="no_advance"), 2, 2, "final state"),
+    ("ticket_carry_split_read", mc.CarryTicketMutex(broken="split_read"), 2, 2, "entered with"),
+    ("ticket_carry_turn_only", mc.CarryTicketMutex(broken="turn_only"), 2, 2, "entered with"),
     ("ring_no_clear", mc.RingMutex(q=2, broken="no_clear"), 2, 3, "grant"),
     ("condvar_release_before_ticket", mc.CondVarQueue(P=1, C=1, broken="signal_before_ticket"), 2, 3, "deadlock"),
     ("condvar_no_recheck", mc.CondVarQueue(P=2, C=1, broken="no_recheck"), 4, 2, "buffer count"),
