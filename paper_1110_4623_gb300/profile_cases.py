@@ -50,12 +50,12 @@ def _sem(n, pairs=20, kind="ticket"):
     return lambda: G.check("gsync_bench_sem", r.launch())
 
 
-def _batched(nacq=200_000, rounds=20):
+def _batched(nacq=200_000, rounds=20, policy=None):
     from . import autotune
     keys, adds, _ = inputs.batched_inputs(nacq, 4096, 1.1)
     cls = autotune.classify_keys(keys, 4096, NB)
     r = autotune.make_run(keys, adds, 4096, NB, 64, rounds, 1, cls)
-    r.set_policy(autotune.DEFAULT_POLICY)
+    r.set_policy(policy or autotune.DEFAULT_POLICY)
     return lambda: G.check("gsync_bench_batched", r.launch())
 
 
@@ -82,6 +82,8 @@ CASES = {
     "sem_ticket_n4": lambda: _sem(4),
     "sem_window_n4": lambda: _sem(4, kind="window"),
     "batched_200k": lambda: _batched(),
+    "batched_200k_carry": lambda: _batched(policy=[("ticket_carry", 0, 0), ("ticket_carry", 64, 2000),
+                                                   ("cas_spin", 0, 0)]),
     "condvar_cohort": lambda: _condvar(),
 }
 
