@@ -300,7 +300,8 @@ int gsync_bench_barrier_static(const gsync_barrier_work* w, int param, uint64_t 
  * ticket of their group's lock: COHORT as (die << 31) | ticket, CLUSTER as (cluster << 20) |
  * ticket (ticket below 2^20).
  * Buffers (device): delay, addend, grant_log, ticket [nblocks*acq]; data [cs_words];
- * total [1]; count [nblocks]; status [1].  data, total and status must start at zero. */
+ * total [1]; count [nblocks]; status [1].  data, total and status must start at zero, and no
+ * two of the buffers may overlap. */
 typedef struct gsync_mutex_work {
   int32_t kind, nblocks, block_threads, acq, cs_words;
   int32_t cluster; /* GSYNC_MUTEX_CLUSTER: blocks per cluster (2..8, divides nblocks); else 0 or 1 */

@@ -19,28 +19,40 @@ constexpr int kFrameOnly = -2;  // the probe's frame (acquire load, barriers, re
 constexpr uint32_t kGolden = 0x9E3779B1u;
 
 // The critical section's data update: data[i] += v ^ (i * kGolden) for i < cs_words, word i on
-// thread i mod blockDim.  WIDE (more words than threads): each thread issues the loads of up to
-// kCsInFlight of its words before adding, so K words per thread cost about one L2 round trip
-// rather than K of them.  Narrow sections keep the one-word loop in a kernel of their own.
+// thread i mod blockDim.  cs_load issues a thread's first loads -- one word, or up to
+// kCsInFlight of them for a section wider than the block (WIDE) -- before thread 0's own
+// bookkeeping (total, grant log), so that thread 0 waits for one L2 round trip, not two;
+// cs_store finishes them, and a WIDE section's further passes keep kCsInFlight loads per thread
+// in flight.  Narrow sections run in a kernel of their own.
 constexpr int kCsInFlight = 4;
 template <bool WIDE>
-__device__ __forceinline__ void cs_update(uint32_t* data, uint32_t cs_words, uint32_t v) {
-  if (!WIDE) {
-    for (uint32_t i = threadIdx.x; i < cs_words; i += blockDim.x) data[i] += v ^ (i * kGolden);
-    return;
+__device__ __forceinline__ void cs_load(const uint32_t* data, uint32_t cs_words, uint32_t (&x)[kCsInFlight]) {
+#pragma unroll
+  for (int k = 0; k < (WIDE ? kCsInFlight : 1); ++k) {
+    const uint32_t j = threadIdx.x + k * blockDim.x;
+    x[k] = j < cs_words ? data[j] : 0u;
   }
+}
+template <bool WIDE>
+__device__ __forceinline__ void cs_store(uint32_t* data, uint32_t cs_words, uint32_t v, uint32_t (&x)[kCsInFlight]) {
+#pragma unroll
+  for (int k = 0; k < (WIDE ? kCsInFlight : 1); ++k) {
+    const uint32_t j = threadIdx.x + k * blockDim.x;
+    if (j < cs_words) data[j] = x[k] + (v ^ (j * kGolden));
+  }
+  if (!WIDE) return;
   const uint32_t step = blockDim.x * kCsInFlight;
-  for (uint32_t base = threadIdx.x; base < cs_words; base += step) {
-    uint32_t x[kCsInFlight];
+  for (uint32_t base = threadIdx.x + step; base < cs_words; base += step) {
+    uint32_t y[kCsInFlight];
 #pragma unroll
     for (int k = 0; k < kCsInFlight; ++k) {
       const uint32_t j = base + k * blockDim.x;
-      x[k] = j < cs_words ? data[j] : 0u;
+      y[k] = j < cs_words ? data[j] : 0u;
     }
 #pragma unroll
     for (int k = 0; k < kCsInFlight; ++k) {
       const uint32_t j = base + k * blockDim.x;
-      if (j < cs_words) data[j] = x[k] + (v ^ (j * kGolden));
+      if (j < cs_words) data[j] = y[k] + (v ^ (j * kGolden));
     }
   }
 }
@@ -85,6 +97,8 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
       __syncthreads();
     }
     // ---- critical section ----
+    uint32_t x[kCsInFlight];
+    if (KIND != kFrameOnly) cs_load<WIDE>(data, (uint32_t)cs_words, x);  // data and total never overlap
     if (KIND != kFrameOnly && tid == 0) {
       const uint32_t seq = *total;
       *total = seq + 1u;
@@ -99,8 +113,7 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
                        : KIND == GSYNC_MUTEX_CLUSTER ? ((b / gsync::ptx::cluster_nctarank()) << 20) | (t.ticket & 0xFFFFFu)
                                                      : t.ticket;
     }
-    if (KIND != kFrameOnly)
-      cs_update<WIDE>(data, (uint32_t)cs_words, v);
+    if (KIND != kFrameOnly) cs_store<WIDE>(data, (uint32_t)cs_words, v, x);
     // ---- end of critical section ----
     if (KIND >= 0) {
       gsync::mutex_unlock<KIND>(m, t);
