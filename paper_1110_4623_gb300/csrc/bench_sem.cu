@@ -36,6 +36,13 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
   uint32_t done = 0;
   for (int p = 0; p < pairs; ++p) {
     const uint32_t id = b * (uint32_t)pairs + (uint32_t)p;
+    // This pair's inputs are the block's own: read them before the wait, so that their loads
+    // overlap it instead of lengthening the critical section.
+    uint32_t hold_cycles = 0, add = 0;
+    if (KIND != kSemFrame && tid == 0) {
+      hold_cycles = hold ? hold[id] : 0u;
+      add = addend[id];
+    }
     int rc = GSYNC_OK;
     if (KIND >= 0) {
       rc = gsync::sem_wait<KIND>(s);
@@ -48,14 +55,13 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
       break;
     }
     if (KIND != kSemFrame && tid == 0) {
+      // n = 1: the plain read of total goes out with the occupancy atomic (one round trip)
+      const uint32_t t = s.n == 1u ? *total : 0u;
       const uint32_t o = gsync::ptx::atom_add_relaxed(occupancy, 1u) + 1u;
       gsync::ptx::atom_max_relaxed(max_occupancy, o);
-      if (s.n == 1u) {
-        const uint32_t t = *total;
-        *total = t + 1u;
-      }
-      if (hold) spin_cycles(hold[id]);
-      gsync::ptx::red_add_relaxed(tally, addend[id]);
+      if (s.n == 1u) *total = t + 1u;
+      if (hold) spin_cycles(hold_cycles);
+      gsync::ptx::red_add_relaxed(tally, add);
       gsync::ptx::atom_add_relaxed(occupancy, 0xFFFFFFFFu);
     }
     int rc2 = GSYNC_OK;
