@@ -228,12 +228,18 @@ class QueueMutex:
     seen by exactly one waiter.  Initial state for a first ticket `base`: tail = base,
     flag[base mod Q] = base, and every other slot holds the latest ticket below base that
     maps to it, which no pending waiter can equal.
+
+    Planted mistakes: broken="unsigned_ge" waits until flag >= t compared as plain unsigned
+    numbers (after the tickets wrap past 2^32, a slot's old value looks larger than a small
+    new ticket); broken="own_slot" makes unlock write t + 1 into the holder's own slot instead
+    of its successor's; broken="no_ring_wrap" computes the successor's slot as
+    (t mod Q) + 1 without wrapping, so the store meant for slot 0 lands past the ring.
     """
     kind, capacity, fifo = "mutex", 1, True
 
-    def __init__(self, q=4, base=0):
+    def __init__(self, q=4, base=0, broken=None):
         assert q & (q - 1) == 0
-        self.q, self.base = q, base & M32
+        self.q, self.base, self.broken = q, base & M32, broken
 
     def init(self, nproc, ops):
         assert self.q >= nproc
@@ -249,7 +255,9 @@ class QueueMutex:
         if pc == 0:
             return (1, k, sh[0], r), _set(sh, 0, inc(sh[0])), None
         if pc == 1:
-            return ((PC_ENTER if sh[1 + (t % q)] == t else 1), k, t, r), sh, None
+            f = sh[1 + (t % q)]
+            mine = f >= t if self.broken == "unsigned_ge" else f == t
+            return ((PC_ENTER if mine else 1), k, t, r), sh, None
         if pc == PC_ENTER:
             return (PC_EXIT, k, t, r), sh, ("enter", t)
         if pc == PC_EXIT:
@@ -257,7 +265,13 @@ class QueueMutex:
         if pc == 2:
             k += 1
             n = inc(t)
-            return ((0 if k < ops else DONE), k, t, r), _set(sh, 1 + (n % q), n), None
+            nxt = (0 if k < ops else DONE)
+            if self.broken == "own_slot":
+                return (nxt, k, t, r), _set(sh, 1 + (t % q), n), None
+            if self.broken == "no_ring_wrap":
+                i = (t % q) + 1
+                return (nxt, k, t, r), (sh if i == q else _set(sh, 1 + i, n)), None  # slot q: past the ring
+            return (nxt, k, t, r), _set(sh, 1 + (n % q), n), None
         raise AssertionError(pc)
 
 
@@ -480,11 +494,17 @@ class SpinSem:
     V > 1: exch(S, V - 1) and enter; V = 1 (at capacity): exch(S, 1) and retry; V = 0: retry.
     post: repeat V <- exch(S, 0) until V > 0, then exch(S, V + 1).  Backoff() after a failed
     wait attempt when UseBackoff (never in post).
+
+    Planted mistakes: broken="keep_v" makes a successful wait write back V instead of V - 1
+    (the permit is never taken); broken="post_no_inc" makes post write back V instead of
+    V + 1 (the permit is never returned); broken="full_zero" makes a wait that finds the
+    semaphore at capacity (V = 1) write back 0 instead of 1, which leaves the internal lock
+    held.
     """
     kind, fifo = "sem", False
 
-    def __init__(self, n=1, backoff=False):
-        self.capacity, self.backoff = n, backoff
+    def __init__(self, n=1, backoff=False, broken=None):
+        self.capacity, self.backoff, self.broken = n, backoff, broken
 
     def init(self, nproc, ops):
         return (self.capacity + 1,), tuple((0, 0, 0, 0) for _ in range(nproc))
@@ -500,9 +520,9 @@ class SpinSem:
                 return (2, k, S, r), (0,), None
             return (retry, k, S, r), (0,), None
         if pc == 1:
-            return (PC_ENTER, k, v, r), (v - 1,), None
+            return (PC_ENTER, k, v, r), ((v if self.broken == "keep_v" else v - 1),), None
         if pc == 2:
-            return (retry, k, v, r), (1,), None
+            return (retry, k, v, r), ((0 if self.broken == "full_zero" else 1),), None
         if pc == 7:  # Backoff()
             return (0, k, v, r), sh, None
         if pc == PC_ENTER:
@@ -515,7 +535,7 @@ class SpinSem:
             return (3, k, S, r), (0,), None
         if pc == 4:
             k += 1
-            return ((0 if k < ops else DONE), k, v, r), (v + 1,), None
+            return ((0 if k < ops else DONE), k, v, r), ((v if self.broken == "post_no_inc" else v + 1),), None
         raise AssertionError(pc)
 
 
@@ -922,11 +942,15 @@ class FlagBarrier:
 class TreeBarrier:
     """Combining-tree barrier with fan-in `fan`: a block counts itself in at its leaf; the
     last arriver at a node resets that node and counts itself in at the parent; the last
-    arriver at the root advances the release epoch, which every block polls."""
+    arriver at the root advances the release epoch, which every block polls.
+
+    Planted mistakes: broken="no_reset": the last arriver at a node never resets it, so the
+    next crossing's count overshoots the node's size; broken="release_at_leaf": the last
+    arriver at a leaf releases at once instead of climbing to the root."""
     kind = "barrier"
 
-    def __init__(self, fan=2, base=0):
-        self.fan, self.base = fan, base & M32
+    def __init__(self, fan=2, base=0, broken=None):
+        self.fan, self.base, self.broken = fan, base & M32, broken
 
     def _tree(self, nproc):
         # nodes listed level by level: (size, parent index)
@@ -961,8 +985,9 @@ class TreeBarrier:
             ev = ("arrive",) if pc == 0 else None
             return ((1 if c == size[nd] else 3), k, e, nd), _set(sh, nd, c), ev
         if pc == 1:  # last arriver at nd: reset it, go up or release
-            sh = _set(sh, nd, 0)
-            if parent[nd] < 0:
+            if self.broken != "no_reset":
+                sh = _set(sh, nd, 0)
+            if parent[nd] < 0 or self.broken == "release_at_leaf":
                 return (2, k, e, nd), sh, None
             return (4, k, e, parent[nd]), sh, None
         if pc == 2:
@@ -1038,11 +1063,15 @@ class ClusterBarrier:
     counter with a cluster epoch).  Phase 2: the cluster's leader (rank 0) arrives at a
     global two-stage atomic barrier of nproc / c leaders; every block polls the global release
     epoch.
+
+    Planted mistakes: broken="leader_early": the leader counts in at the global counter as
+    soon as it arrives itself, without waiting for its cluster; broken="all_count": every
+    block of a cluster counts in at the global counter, not only the leader.
     """
     kind = "barrier"
 
-    def __init__(self, c=2, base=0):
-        self.c, self.base = c, base & M32
+    def __init__(self, c=2, base=0, broken=None):
+        self.c, self.base, self.broken = c, base & M32, broken
 
     def init(self, nproc, ops):
         assert nproc % self.c == 0
@@ -1058,13 +1087,16 @@ class ClusterBarrier:
         CC, CE, GC, REL = cl, ncl + cl, 2 * ncl, 2 * ncl + 1
         if pc == 0:
             n = sh[CC] + 1
+            if self.broken == "leader_early" and rank == 0:
+                # counts in globally now; the cluster barrier is crossed after the release
+                return (3, k, e, ce), _set(sh, CC, n), ("arrive",)
             return ((1 if n == c else 2), k, e, ce), _set(sh, CC, n), ("arrive",)
         if pc == 1:
             sh = _set(sh, CC, 0)
             return (2, k, e, ce), _set(sh, CE, inc(sh[CE])), None
         if pc == 2:
             if sh[CE] == inc(ce):
-                return ((3 if rank == 0 else 6), k, e, inc(ce)), sh, None
+                return ((3 if rank == 0 or self.broken == "all_count" else 6), k, e, inc(ce)), sh, None
             return loc, sh, None
         if pc == 3:
             n = sh[GC] + 1

@@ -108,6 +108,24 @@ BROKEN = [
     ("split_one_copy_early", mc.SplitBarrier(S=2, R=2, broken="one_copy_early"), 3, 3, "completion"),
     ("die_no_reset", mc.DieBarrier(broken="no_reset"), 2, 4, "final state"),
     ("sharded_counts_master", mc.ShardedBarrier(shards=2, broken="counts_master"), 3, 1, "final state"),
+    # Queue lock: an unsigned poll lets a small ticket after the wrap through at once; an unlock
+    # into the holder's own slot, or a successor slot that does not wrap to 0, wakes nobody.
+    ("queue_unsigned_poll", mc.QueueMutex(q=4, base=W, broken="unsigned_ge"), 3, 2, "critical section"),
+    ("queue_own_slot", mc.QueueMutex(q=4, broken="own_slot"), 2, 2, "final state"),
+    ("queue_no_ring_wrap", mc.QueueMutex(q=2, broken="no_ring_wrap"), 2, 2, "final state"),
+    # Spin-lock semaphore: a wait that keeps the permit, a post that does not return it, and a
+    # wait at capacity that leaves the internal lock taken.
+    ("spin_sem_keep_v", mc.SpinSem(n=1, broken="keep_v"), 2, 1, "critical section"),
+    ("spin_sem_keep_v_n2", mc.SpinSem(n=2, broken="keep_v"), 3, 1, "critical section"),
+    ("spin_sem_post_no_inc", mc.SpinSem(n=1, broken="post_no_inc"), 2, 2, "final state"),
+    ("spin_sem_full_zero", mc.SpinSem(n=1, broken="full_zero"), 2, 1, "completion"),
+    # Tree barrier: a node never reset, and a leaf's last arriver that releases the grid.
+    ("tree_no_reset", mc.TreeBarrier(fan=2, broken="no_reset"), 3, 2, "final state"),
+    ("tree_release_at_leaf", mc.TreeBarrier(fan=2, broken="release_at_leaf"), 3, 1, "passed round"),
+    # Cluster barrier: a leader that counts in before its cluster has arrived, and every block
+    # counting in globally.
+    ("cluster_leader_early", mc.ClusterBarrier(c=2, broken="leader_early"), 4, 1, "passed round"),
+    ("cluster_all_count", mc.ClusterBarrier(c=2, broken="all_count"), 4, 1, "passed round"),
 ]
 
 
