@@ -4,7 +4,7 @@ One step = one pass over every row of the hot path at 1184 blocks:
   * mutex contention (the paper's 4 kinds, its ring-buffer mutex and spin-then-sleep policy,
     and the two-die cohort lock x critical sections of 0/64/1024 words, 256 threads per block,
     100 acquisitions per block, seeded delays U{0..2000} cycles),
-  * grid barriers (atomic, flag, tree, cluster 2/4/8, sharded, two-die, split, counting;
+  * grid barriers (atomic, flag, tree, cluster 2/4/8 and its counting form, sharded, two-die, split, counting;
     128 threads, 1000 rounds each),
   * counting semaphores (sleeping FA kind, n in {1, 4, 16, 64}; 128 threads, 200 pairs each,
     hold U{100..5000} cycles).
@@ -40,8 +40,11 @@ SEM_THREADS, SEM_PAIRS, SEM_COUNTS = 128, 200, (1, 4, 16, 64)
 # fastest implementation of each primitive for the GPU as the default, Section 5 "API").
 DEFAULT_MUTEX = "cluster"
 DEFAULT_BARRIER = ("count", 8)
+# cluster params: c | form << 4 (form 0: atomic stage over the leaders; 2: counting stage, the
+# rest of the cluster released by a second cluster barrier -- the fastest cluster form measured)
 BARRIERS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("cluster", 2), ("cluster", 4), ("cluster", 8),
-            ("sharded", 32), ("sharded", 8), ("die", 0), ("die", 1), ("split", 16 | 16 << 8), ("count", 0), ("count", 8)]
+            ("cluster", 4 | 2 << 4), ("cluster", 8 | 2 << 4), ("sharded", 32), ("sharded", 8), ("die", 0),
+            ("die", 1), ("split", 16 | 16 << 8), ("count", 0), ("count", 8)]
 # Backoff (min_ns, max_ns) per kind; the ticket kinds sleep min_ns per waiter ahead, capped.
 MUTEX_BACKOFF = {"cas_backoff": (16, 512), "ticket": (128, 4000), "cohort": (128, 4000), "cluster": (128, 4000)}
 MUTEX_CLUSTER = 4  # blocks per cluster of the cluster cohort lock (a sweep of 2 / 4 / 8 picked 4)
@@ -136,10 +139,27 @@ def replica_value(units_per_rank, ms_max, world):
     return units_per_rank * world / (ms_max * 1e-3)
 
 
+def br_param(kind, param):
+    """The parameter a BarrierRun of this kind actually uses (its defaults for 0)."""
+    if kind == "tree" and param == 0:
+        return 8
+    if kind == "cluster" and param == 0:
+        return 2
+    if kind == "sharded" and param == 0:
+        return min(32, NBLOCKS)
+    if kind == "split" and param == 0:
+        return 8 | 8 << 8
+    return param
+
+
 def barrier_name(kind, param):
     if kind == "flag":
         return "flag_broadcast" if param else "flag"
-    if kind in ("tree", "cluster", "sharded") or (kind == "count" and param):
+    if kind == "cluster":
+        c, form, sleep = param & 0xF, (param >> 4) & 0xF, param >> 8
+        name = f"cluster{c}" + ("", "_count", "_count_cb")[form]
+        return name + (f"_s{sleep}" if sleep else "")
+    if kind in ("tree", "sharded") or (kind == "count" and param):
         return f"{kind}{param}"
     if kind == "split":
         return f"split{param & 0xFF}x{param >> 8}"
@@ -229,6 +249,8 @@ def measure_roofline_terms(runner, inputs):
     T_cs = {K: best_placement(lambda a, K=K: runner.probe_cs(K, MUTEX_THREADS, 20000, scratch=a)["ns_per_cs"],
                               runner.G.gsync_probe_cs_scratch_bytes(K, 20000), runner)
             for K in CS_SIZES}
+    # the hardware cluster barrier, per crossing, for the cluster sizes the cluster barrier uses
+    T_cb = {c: float(np.median([runner.probe_cluster(0, c, 4000)["ns"] for _ in range(3)])) for c in (2, 4, 8)}
     rs = [runner.probe_throughput("red_add", True, False, NBLOCKS, 128, 2000)["ops_per_s"] for _ in range(3)]
     ra = [runner.probe_throughput("atomic_read", True, False, NBLOCKS, 128, 1000)["ops_per_s"] for _ in range(3)]
     # dependent chains of one thread: atomic round trip and L2 load, on a line homed on the
@@ -251,7 +273,7 @@ def measure_roofline_terms(runner, inputs):
             "L_handoff_pairs_ns": hand_ns, "T_cs_ns": T_cs,
             "T_frame_ns": T_frame, "T_cs_sem_ns": T_cs_sem, "T_frame_sem_ns": T_frame_sem,
             "R_same_red_ops_s": float(np.median(rs)), "R_same_atom_ops_s": float(np.median(ra)), "L_rt_ns": L_rt,
-            "L_ld_ns": L_ld}
+            "L_ld_ns": L_ld, "T_cluster_bar_ns": T_cb}
 
 
 def merge_terms(a, b):
@@ -262,6 +284,7 @@ def merge_terms(a, b):
     for k in ("R_same_red_ops_s", "R_same_atom_ops_s"):
         out[k] = max(a[k], b[k])
     out["T_cs_ns"] = {K: min(a["T_cs_ns"][K], b["T_cs_ns"][K]) for K in a["T_cs_ns"]}
+    out["T_cluster_bar_ns"] = {c: min(a["T_cluster_bar_ns"][c], b["T_cluster_bar_ns"][c]) for c in a["T_cluster_bar_ns"]}
     out["T_cs_sem_ns"] = {n: min(a["T_cs_sem_ns"][n], b["T_cs_sem_ns"][n]) for n in a["T_cs_sem_ns"]}
     # body = probe - frame, taken from the same measurement, then the smaller of the two
     out["T_body_ns"] = {K: min(a["T_cs_ns"][K] - a["T_frame_ns"], b["T_cs_ns"][K] - b["T_frame_ns"])
@@ -285,28 +308,64 @@ def sem_roof_ops_s(terms, n):
                n * 1e9 / (terms["L_handoff_l2_near_ns"] + max(terms["T_body_sem_ns"][n], 0.0)))
 
 
+def tree_levels(B, fan):
+    """Levels of a combining tree of fan-in `fan` over B leaves (1 for B <= fan)."""
+    levels, width = 1, -(-B // fan)
+    while width > 1:
+        width = -(-width // fan)
+        levels += 1
+    return levels
+
+
 def barrier_roof_ns(terms, kind, param, B):
-    """One atomic round trip, one hand-off, and the arrivals through the busiest atomic unit
-    (DIE: the larger die's share of the blocks, and one more round trip for the top counter),
-    plus the workload's own share of a round: the partner slot each block reads after a
-    crossing is a dependent L2 load on the critical path to its next arrival."""
-    rts = 1
-    if kind == "cluster":
-        b_eff = B / param
-    elif kind in ("sharded", "flag"):
-        b_eff = B / (param if kind == "sharded" else B)
+    """The serial steps of one crossing, each at its measured cost, plus the workload's own
+    share of a round: the partner slot each block reads after a crossing is a dependent L2 load
+    (L_ld) on the critical path to its next arrival.  A grid-wide release reaches every block
+    through L2, so the on-die L2 hand-off (L_h) bounds it; same-word arrivals serialize at the
+    atomic unit (R_same).
+      atomic : last arrival's round trip, B serialized arrivals, release hand-off
+      count  : B serialized arrivals, whose last is the release (no round trip back)
+      tree   : per level a round trip of the last arriver and fan serialized arrivals, then
+               the root's release hand-off
+      flag   : (XF) two hand-offs in series -- the last arrival flag to the master block, the
+               release flags to every block -- plus the master's second gather pass (a thread
+               watches two or three of the 16-byte flag vectors, so some need two loads)
+      sharded: two hand-offs in series (counters to the master warp, release flags to every
+               block) and B/S serialized arrivals per counter
+      cluster: the hardware cluster barrier (T_cb(c), measured), then over the B/c leaders:
+               form 0 as atomic; form 1 as count; form 2 as count plus a second cluster barrier
+      die    : B/2 arrivals per die, and with per-die counters one more round trip (the top)
+      split  : B/S per counter plus S at the top, two round trips (S > 1)"""
+    L_rt, L_h, L_ld = terms["L_rt_ns"], terms["L_handoff_l2_near_ns"], terms.get("L_ld_ns", 0.0)
+    t_atom = 1e9 / terms["R_same_atom_ops_s"]
+    if kind == "atomic":
+        ns = L_rt + B * t_atom + L_h
+    elif kind == "count":
+        ns = B * t_atom + L_h
+    elif kind == "tree":
+        fan = param
+        lv = tree_levels(B, fan)
+        ns = lv * (L_rt + fan * t_atom) + L_h
+    elif kind == "flag":
+        ns = 2 * L_h + L_ld
+    elif kind == "sharded":
+        ns = 2 * L_h + -(-B // param) * t_atom
+    elif kind == "cluster":
+        c, form = param & 0xF, (param >> 4) & 0xF
+        t_cb = terms.get("T_cluster_bar_ns", {}).get(c, 0.0)
+        leaders = B / c
+        if form == 0:
+            ns = t_cb + L_rt + leaders * t_atom + L_h
+        else:
+            ns = t_cb + leaders * t_atom + L_h + (t_cb if form == 2 else 0.0)
     elif kind == "die":
-        b_eff, rts = (B, 1) if param == 1 else (B / 2, 2)
+        ns = (L_rt + B * t_atom + L_h) if param == 1 else (2 * L_rt + B / 2 * t_atom + L_h)
     elif kind == "split":
         S = param & 0xFF
-        b_eff, rts = (-(-B // S) + S, 2) if S > 1 else (B, 1)
-    elif kind == "count":
-        b_eff, rts = B, 0  # the last arrival is the release: no round trip back to it
+        ns = (2 * L_rt + (-(-B // S) + S) * t_atom + L_h) if S > 1 else (L_rt + B * t_atom + L_h)
     else:
-        b_eff = B
-    # a grid-wide release reaches every block through L2: the on-die L2 hand-off bounds it
-    return (rts * terms["L_rt_ns"] + terms["L_handoff_l2_near_ns"] + b_eff / terms["R_same_atom_ops_s"] * 1e9
-            + terms.get("L_ld_ns", 0.0))
+        raise ValueError(kind)
+    return ns + L_ld
 
 
 # ------------------------------------------------------------------------------------------
@@ -455,17 +514,18 @@ def batched_section(G, calc, inputs, runner, autotune, terms):
     out.update({"hottest_key_acquisitions": n_hot, "roof_acq_per_s": roof, "roof_with_load_acq_per_s": roof_ld})
     results = {}
     for label, policy, cluster in (("default", autotune.DEFAULT_POLICY, 1), ("tuned", tuned["policy"], tuned["cluster"])):
-        plain = cluster == 1
+        # Without clusters the kernel is captured as an ordinary launch after the co-residency
+        # check (a cooperative launch is not captured); a cluster launch is captured as it is.
         run = autotune.make_run(keys, adds, BATCH_KEYS, NBLOCKS, BATCH_GROUPS, BATCH_ROUNDS, cluster,
-                                tuned["key_class"], BATCH_THREADS, plain_launch=plain)
+                                tuned["key_class"], BATCH_THREADS, plain_launch=cluster == 1)
         run.set_policy(policy)
-        graph = False
-        if plain:
-            try:
-                run.capture()
-                graph = True
-            except Exception:  # capture refused: time plain launches instead
-                graph = False
+        graph, capture_error = False, None
+        try:
+            run.capture()
+            graph = True
+        except Exception as exc:  # capture refused: time plain launches instead, and say why
+            capture_error = f"{type(exc).__name__}: {exc}"[:300]
+            torch.cuda.synchronize()
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ts = []
         for _ in range(3):
@@ -487,6 +547,8 @@ def batched_section(G, calc, inputs, runner, autotune, terms):
         ms = float(np.median(ts))
         results[label] = {"ms": ms, "acq_per_s": BATCH_ACQ / (ms * 1e-3), "frac": BATCH_ACQ / (ms * 1e-3) / roof,
                           "cuda_graph": graph, "cluster": cluster, "parity": "ok" if ok else "FAILED"}
+        if capture_error:
+            results[label]["capture_error"] = capture_error
     out.update(results)
     return out
 
@@ -723,7 +785,7 @@ def run_gpu(args):
     barrier = {}
     for (k, p) in step.barrier:
         ns = med[(k, p)] * 1e6 / BAR_ROUNDS
-        roof = barrier_roof_ns(terms, k, p if k in ("die", "split", "count") else max(p, 1), NBLOCKS)
+        roof = barrier_roof_ns(terms, k, br_param(k, p), NBLOCKS)
         barrier[barrier_name(k, p)] = {"ns_per_crossing": ns, "roof_ns": roof, "frac": roof / ns}
     bkey = barrier_name(*DEFAULT_BARRIER)
     sem_kinds = {}

@@ -72,7 +72,8 @@ typedef enum gsync_barrier_kind {
   GSYNC_BAR_ATOMIC = 0,  /* two-stage atomic counter + release epoch */
   GSYNC_BAR_FLAG = 1,    /* decentralized flag barrier of Xiao and Feng (XF) */
   GSYNC_BAR_TREE = 2,    /* combining tree of atomic counters, fan-in = param */
-  GSYNC_BAR_CLUSTER = 3, /* hardware cluster barrier, then one leader per cluster on a counter */
+  GSYNC_BAR_CLUSTER = 3, /* hardware cluster barrier, then one leader per cluster on a counter
+                            (param = c | form << 4 | sleep << 8; see gsync_barrier_bytes) */
   GSYNC_BAR_SHARDED = 4, /* arrivals spread over param counters, gathered by one warp (XF-style release) */
   GSYNC_BAR_DIE = 5,     /* two-die barrier: a release word per die, homed on that die; param 0:
                             a counter per die, the dies' last arrivers meet on a top counter;
@@ -154,8 +155,13 @@ int gsync_mutex_init_cluster(void* state, size_t bytes, int budget, const gsync_
  * use. */
 int gsync_device_topology(uint8_t* die_of_sm, int* ndies_out, void* stream);
 
-/* Bytes of a barrier for `nblocks` blocks.  param: fan-in (TREE, >= 2), cluster size
- * (CLUSTER, 1..8, divides nblocks), release mode (FLAG: 0 one flag per block, 1 one word;
+/* Bytes of a barrier for `nblocks` blocks.  param: fan-in (TREE, >= 2), c | form << 4 |
+ * sleep << 8 (CLUSTER: c the cluster size, 1..8, dividing nblocks; form 0: the cluster
+ * leaders meet on an atomic barrier whose release epoch every block polls; form 1: the
+ * leaders add to a growing counter, the last add is the release, and every block polls the
+ * counter; form 2: as 1, but only the leaders poll and the other blocks wait at a second
+ * hardware cluster barrier; sleep 0..1023 = ns a leader sleeps per 16 leader arrivals still
+ * missing before its first poll, forms 1 and 2), release mode (FLAG: 0 one flag per block, 1 one word;
  * FLAG takes at most 8192 blocks), number of arrival counters (SHARDED, 1..32), S | R << 8
  * (SPLIT: S arrival counters and R release copies, 1..64 each), 0 or 1 (DIE: per-die counters,
  * or one flat counter with a release word on each die), sleep | S << 16 (COUNT: sleep 0..1023 =
@@ -278,12 +284,16 @@ int gsync_probe_barrier_trace(void* state, const gsync_barrier_work* w, uint64_t
  * slot buffers live in one 128 KiB file-scope device array inside the library, which every
  * GPU that loads the library holds until the process exits.  The caller still passes the
  * outputs in `w` (chk, mix, bad, status; w->slots is ignored).
+ *  - Kinds: ATOMIC, FLAG, TREE, CLUSTER, SHARDED, SPLIT and COUNT, with `param` as for
+ *    gsync_barrier_bytes (CLUSTER takes its size from w->cluster and its form and sleep
+ *    from the other bits of `param`).  DIE
+ *    returns GSYNC_EINVAL: its init measures the die map and synchronizes the stream.
  *  - Limits: nblocks <= GSYNC_STATIC_MAX_BLOCKS (4096), and the object for (kind, nblocks,
  *    param) must fit in 96 KiB (gsync_barrier_bytes); anything larger returns GSYNC_EINVAL.
- *    `param` is the TREE fan-in or the FLAG release mode; CLUSTER takes w->cluster.
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current and caches it; make that first call
- *    before any stream capture.
+ *  - Every call looks up the array's device address (cudaGetSymbolAddress) with the
+ *    caller's device current; nothing is cached, so the address stays right after a
+ *    cudaDeviceReset.  The first call on a device (and the first after a reset) loads the
+ *    library's module there: make it before any stream capture.
  *  - Every call shares the one array and each call rewrites the object and clears the
  *    slots, so calls whose work overlaps on the GPU (other streams, other threads) race and
  *    must be serialized by the caller. */

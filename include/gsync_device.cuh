@@ -801,10 +801,19 @@ __device__ __forceinline__ int sem_post(const SemRef& s) {
 //          fire-and-forget red.release; counters only grow, so after crossing e counter s
 //          holds e x (blocks of shard s)); then release flags (one word per block, packed).
 //          Warp 0 of block 0 watches the S counters and writes the release flags.
-// CLUSTER: like ATOMIC over the cluster leaders; param = cluster size.  Its first stage is
+// CLUSTER: param = c | form << 4 | sleep << 8, c the cluster size (1..8).  Its first stage is
 //          the hardware cluster barrier, which cannot time out: every block of a cluster must
 //          make the same number of barrier_wait calls, also after one returned an error (the
-//          object's abort word makes those calls return quickly).
+//          object's abort word makes those calls return quickly).  Then, by form:
+//          0: ATOMIC over the cluster leaders (lines 1 and 3 arrival counters, line 2 the
+//             release epoch), which every block polls;
+//          1: counting over the leaders: line 1 a 64-bit counter that only grows; each leader
+//             adds 1 per crossing, and every block polls it until base + e x (n / c), so the
+//             last leader's add is the release (as COUNT); a leader sleeps `sleep` ns per 16
+//             leader arrivals still missing before its first poll;
+//          2: as 1, but only the leader polls; the other blocks of its cluster wait at a
+//             second hardware cluster barrier, which the leader reaches once it has seen the
+//             crossing complete (and they take its result from its shared memory).
 // DIE    : line 1 a flat arrival counter (registration crossings), line 2 {members of die
 //          0, members of die 1, blocks of die 0, blocks of die 1, dies with blocks}, lines
 //          3-4 the SM-to-die table; for each die d, at word offset kHdrDieOff<d> (on a 4 KB
@@ -881,6 +890,13 @@ __device__ __forceinline__ BarrierRef barrier_attach(void* state) {
       const uint64_t v = ptx::ld_relaxed_u64((const uint64_t*)b.line(2u + g));
       b.sub_base = v - v % members;
     }
+    b.epoch = 0;
+  } else if (b.kind == GSYNC_BAR_CLUSTER && ((b.param >> 4) & 0xFu) != 0u) {
+    // Counting form: rounded down to a multiple of the leaders, as for COUNT.
+    const uint32_t c = b.param & 0xFu;
+    const uint64_t P = (uint64_t)(b.n / (c ? c : 1u));
+    const uint64_t v = ptx::ld_relaxed_u64((const uint64_t*)b.line(1));
+    b.base = P ? v - v % P : v;
     b.epoch = 0;
   } else if (b.kind == GSYNC_BAR_DIE) {
     const uint32_t sm = ptx::smid();
@@ -1055,16 +1071,46 @@ __device__ __forceinline__ int barrier_wait(BarrierRef& b) {
       s_rc = rc;
     }
   } else if (KIND == GSYNC_BAR_CLUSTER) {
-    if (master) {
-      int rc = GSYNC_OK;
-      if (ptx::cluster_ctarank() == 0) {
-        rc = counter_arrive_wait(b, b.n / b.param, e1);
-      } else {
-        Waiter w;
-        while (ptx::ld_acquire(b.line(2)) != e1)
-          if ((rc = w.tick(b.timeout_ns, b.abort_word())) != GSYNC_OK) break;
+    const uint32_t form = (b.param >> 4) & 0xFu, c = b.param & 0xFu;
+    const bool leader = ptx::cluster_ctarank() == 0;
+    if (form == 0u) {
+      if (master) {
+        int rc = GSYNC_OK;
+        if (leader) {
+          rc = counter_arrive_wait(b, b.n / (c ? c : 1u), e1);
+        } else {
+          Waiter w;
+          while (ptx::ld_acquire(b.line(2)) != e1)
+            if ((rc = w.tick(b.timeout_ns, b.abort_word())) != GSYNC_OK) break;
+        }
+        s_rc = rc;
       }
-      s_rc = rc;
+    } else {
+      if (master && (leader || form == 1u)) {
+        uint64_t* cnt = (uint64_t*)b.line(1);
+        const uint64_t target = b.base + (uint64_t)e1 * (b.n / (c ? c : 1u));
+        uint64_t missing = 1;
+        if (leader) {
+          // release: orders the cluster's writes (acquired through the cluster barrier) first
+          missing = target - (ptx::atom_add_acq_rel_u64(cnt, 1ull) + 1ull);
+          const uint32_t sleep16 = (b.param >> 8) & 0x3FFu;
+          if (missing && sleep16 && missing < (1ull << 24)) {
+            const uint64_t ns = missing * sleep16 / 16u;
+            __nanosleep((uint32_t)(ns < 4000u ? ns : 4000u));
+          }
+        }
+        int rc = GSYNC_OK;
+        if (missing) {
+          Waiter w;
+          while (ptx::ld_acquire_u64(cnt) < target)
+            if ((rc = w.tick(b.timeout_ns, b.abort_word())) != GSYNC_OK) break;
+        }
+        s_rc = rc;
+      }
+      if (form == 2u) {
+        ptx::cluster_sync();  // the leader has seen the crossing complete, or given up
+        if (master && !leader) s_rc = (int)ptx::ld_relaxed_cluster((const uint32_t*)ptx::map_cluster_rank(&s_rc, 0u));
+      }
     }
   } else if (KIND == GSYNC_BAR_TREE) {
     if (master) {

@@ -28,6 +28,7 @@ The algorithms follow Section 5 ("Design") and the pseudocode of the Appendix:
   TreeBarrier   combining-tree barrier (Section 2, hierarchical barriers)
   ShardedBarrier  arrivals counted on several counters, gathered by the master block
   ClusterBarrier  barrier inside groups of c blocks, then one leader per group globally
+  ClusterCountBarrier  the same, with a growing counter over the leaders as the global stage
   DieBarrier    per-die counters and release words, a top counter between the dies
   SplitBarrier  S arrival counters under a top counter, R copies of the release word
   CountBarrier  one growing arrival counter that every block polls
@@ -1111,6 +1112,84 @@ class ClusterBarrier:
                 k += 1
                 return ((0 if k < ops else DONE), k, inc(e), ce), sh, ("pass",)
             return loc, sh, None
+        raise AssertionError(pc)
+
+
+class ClusterCountBarrier:
+    """Cluster barrier whose global stage is a counting barrier over the cluster leaders.
+
+    A block first crosses the barrier of its cluster of c consecutive blocks (the hardware
+    cluster barrier; modelled as a counter with a cluster epoch).  The cluster's leader (rank
+    0) then adds 1 to a global counter that only grows and polls it until it reaches
+    base + e x (nproc / c) for its e-th crossing: the last leader's increment is the release.
+    release="poll": the other blocks of the cluster poll the global counter too.
+    release="cluster": they wait at a second cluster barrier, which the leader reaches only
+    after it has seen the counter reach its target.
+
+    Planted mistakes: broken="off_by_one": the target is one short; broken="no_second": with
+    release="cluster", the other blocks leave without the second cluster barrier.
+    """
+    kind = "barrier"
+
+    def __init__(self, c=2, base=0, release="poll", broken=None):
+        self.c, self.base, self.release, self.broken = c, base, release, broken
+
+    def init(self, nproc, ops):
+        assert nproc % self.c == 0
+        ncl = nproc // self.c
+        # per cluster: first barrier's counter and epoch, second barrier's counter and epoch
+        sh = tuple([0] * (4 * ncl)) + (self.base * ncl,)
+        return sh, tuple((0, 0, 0, 0, 0) for _ in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        c = self.c
+        ncl = nproc // c
+        cl, rank = p // c, p % c
+        pc, k, e, ce, ce2 = loc
+        CC, CE, CC2, CE2, GC = cl, ncl + cl, 2 * ncl + cl, 3 * ncl + cl, 4 * ncl
+        second = self.release == "cluster"
+
+        def passed(sh2, e2=e + 1, ce_=ce, ce2_=ce2):
+            k2 = k + 1
+            return ((0 if k2 < ops else DONE), k2, e2, ce_, ce2_), sh2, ("pass",)
+
+        if pc == 0:  # arrive at the cluster barrier
+            n = sh[CC] + 1
+            return ((1 if n == c else 2), k, e, ce, ce2), _set(sh, CC, n), ("arrive",)
+        if pc == 1:  # last of the cluster: reset and open the cluster barrier
+            sh = _set(sh, CC, 0)
+            return (2, k, e, ce, ce2), _set(sh, CE, sh[CE] + 1), None
+        if pc == 2:
+            if sh[CE] != ce + 1:
+                return loc, sh, None
+            if rank == 0:
+                nxt = 3
+            elif second:
+                nxt = 5 if self.broken != "no_second" else 8
+            else:
+                nxt = 4
+            return (nxt, k, e, ce + 1, ce2), sh, None
+        if pc == 3:  # leader: count in on the global counter
+            return (4, k, e, ce, ce2), _set(sh, GC, sh[GC] + 1), None
+        if pc == 4:  # poll the global counter
+            target = (self.base + e + 1) * ncl - (1 if self.broken == "off_by_one" else 0)
+            if sh[GC] < target:
+                return loc, sh, None
+            if second:
+                return (5, k, e, ce, ce2), sh, None
+            return passed(sh)
+        if pc == 5:  # second cluster barrier
+            n = sh[CC2] + 1
+            return ((6 if n == c else 7), k, e, ce, ce2), _set(sh, CC2, n), None
+        if pc == 6:
+            sh = _set(sh, CC2, 0)
+            return (7, k, e, ce, ce2), _set(sh, CE2, sh[CE2] + 1), None
+        if pc == 7:
+            if sh[CE2] != ce2 + 1:
+                return loc, sh, None
+            return passed(sh, ce2_=ce2 + 1)
+        if pc == 8:  # broken: leaves without the second cluster barrier
+            return passed(sh)
         raise AssertionError(pc)
 
 

@@ -10,8 +10,6 @@
 //   sampled : thread 0 reads partner p = (b + r + 1) mod B only, folds lowbias32(slot_p) into
 //             mix and counts a stale read in bad.  This keeps the per-round work O(1) so the
 //             kernel time measures the barrier itself at large grids.
-#include <mutex>
-
 #include "common.cuh"
 
 using namespace gsync_impl;
@@ -30,7 +28,7 @@ __global__ void __launch_bounds__(kMaxThreads, FULL ? 4 : 6)
   gsync::BarrierRef bar = gsync::barrier_attach(state);
   const uint32_t B = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   if (bar.kind != (uint32_t)KIND || bar.n != B ||
-      (KIND == GSYNC_BAR_CLUSTER && gsync::ptx::cluster_nctarank() != bar.param)) {
+      (KIND == GSYNC_BAR_CLUSTER && gsync::ptx::cluster_nctarank() != (bar.param & 0xFu))) {
     if (tid == 0) gsync::ptx::atom_or_relaxed(status, GSYNC_STATUS_CONFIG);
     return;  // uniform: every block sees the same header
   }
@@ -188,22 +186,16 @@ static_assert(kStaticStateBytes % 256 == 0, "slot buffers start on a 256-byte bo
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-std::mutex g_static_mutex;
-void* g_static_address[256] = {};  // device address of g_static_scratch, per device ordinal
-
-// In host code the name g_static_scratch is only a stand-in; the kernel needs the device
-// address, looked up once per device with that device current.
+// In host code the name g_static_scratch is only a stand-in; the kernel needs the array's
+// device address, looked up here with the caller's device current.  The lookup is repeated
+// on every call rather than cached: after a cudaDeviceReset the library's module is loaded
+// again and the array may move, so an address kept from before would be stale.  The lookup
+// allocates nothing; the first one on a device (and the first after a reset) loads the
+// module there.
 int static_scratch_address(void** out) {
-  int dev = 0;
-  GSYNC_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 256) return GSYNC_EINVAL;
-  std::lock_guard<std::mutex> lock(g_static_mutex);
-  if (g_static_address[dev] == nullptr) {
-    void* p = nullptr;
-    GSYNC_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
-    g_static_address[dev] = p;
-  }
-  *out = g_static_address[dev];
+  void* p = nullptr;
+  GSYNC_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
+  *out = p;
   return GSYNC_OK;
 }
 
@@ -213,7 +205,10 @@ extern "C" int gsync_bench_barrier_static(const gsync_barrier_work* w, int param
                                           void* stream) {
   if (!w || w->nblocks < 1 || w->nblocks > GSYNC_STATIC_MAX_BLOCKS) return GSYNC_EINVAL;
   if (!w->mix || !w->bad || !w->status || (w->full && !w->chk)) return GSYNC_EINVAL;
-  const int p = w->kind == GSYNC_BAR_CLUSTER ? w->cluster : param;
+  // The two-die barrier's init measures the die map and synchronizes the stream, which the
+  // callers of this entry point cannot afford: it is refused here.
+  if (w->kind == GSYNC_BAR_DIE) return GSYNC_EINVAL;
+  const int p = w->kind == GSYNC_BAR_CLUSTER ? (param & ~0xF) | w->cluster : param;
   const size_t state_bytes = gsync_barrier_bytes(w->kind, w->nblocks, p);
   if (state_bytes == 0 || state_bytes > kStaticStateBytes) return GSYNC_EINVAL;
   void* base = nullptr;

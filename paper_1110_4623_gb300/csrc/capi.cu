@@ -285,7 +285,11 @@ size_t gsync_barrier_bytes(int kind, int nblocks, int param) {
     case GSYNC_BAR_ATOMIC: break;
     case GSYNC_BAR_FLAG: if ((param != 0 && param != 1) || nblocks > 8192) return 0; break;
     case GSYNC_BAR_TREE: if (param < 2 || param > 1024) return 0; break;
-    case GSYNC_BAR_CLUSTER: if (param < 1 || param > 8 || nblocks % param) return 0; break;
+    case GSYNC_BAR_CLUSTER: {
+      const int c = param & 0xF, form = (param >> 4) & 0xF, sleep16 = param >> 8;
+      if (param < 0 || c < 1 || c > 8 || nblocks % c || form > 2 || sleep16 > 1023) return 0;
+      break;
+    }
     case GSYNC_BAR_SHARDED: if (param < 1 || param > 32 || param > nblocks) return 0; break;
     case GSYNC_BAR_DIE: if (param != 0 && param != 1) return 0; break;
     case GSYNC_BAR_COUNT: {

@@ -111,7 +111,7 @@ class BarrierRun:
         self.bad = _zeros(nblocks)
         self.status = _zeros(1)
         self.work = G.gsync_barrier_work(self.k, nblocks, block_threads, rounds, int(full),
-                                         param if kind == "cluster" else 1,
+                                         param & 0xF if kind == "cluster" else 1,
                                          G.ptr(self.slots), G.ptr(self.chk), G.ptr(self.mix), G.ptr(self.bad),
                                          G.ptr(self.status))
 

@@ -107,6 +107,21 @@ __global__ void bounded_waits_kernel(void* sem_state, void* mutex_state, void* b
   if (threadIdx.x == 0) { rc[2] = r; ns_out[2] = gsync::ptx::globaltimer() - t0; }
 }
 
+// The cluster barrier's counting forms (1: every block polls the leaders' counter; 2: the
+// other blocks of a cluster wait at a second cluster barrier for their leader): the second
+// cluster of the grid never arrives, so the leaders' count stays short and the bounded wait
+// (1 ms) of both blocks of the first cluster must end with an error: GSYNC_ETIMEDOUT for the
+// block whose wait ran out first, GSYNC_EABORTED or GSYNC_ETIMEDOUT for the other (the first
+// marks the object aborted) -- in form 2 the leader's result reaches its cluster through the
+// leader's shared memory, so both report the leader's.
+__global__ void bounded_cluster_wait_kernel(void* bar_state, int* rc, uint64_t* ns_out) {
+  if (blockIdx.x >= 2) return;  // the second cluster (blocks 2 and 3) never arrives
+  gsync::BarrierRef bar = gsync::barrier_attach(bar_state);
+  const uint64_t t0 = gsync::ptx::globaltimer();
+  const int r = gsync::barrier_wait<GSYNC_BAR_CLUSTER>(bar, 1000000ull);
+  if (threadIdx.x == 0) { rc[blockIdx.x] = r; ns_out[blockIdx.x] = gsync::ptx::globaltimer() - t0; }
+}
+
 #define CHECK(x)                                                              \
   do {                                                                        \
     int rc_ = (int)(x);                                                       \
@@ -216,6 +231,36 @@ int main() {
       printf("FAIL bounded wait %d: rc %d after %llu ns\n", i, hrc[i], (unsigned long long)hns[i]);
       return 1;
     }
+  // The same bound in the cluster barrier's counting forms, in a launch with clusters of 2.
+  cudaFunction_t fcb;
+  CHECK(cudaGetFuncBySymbol(&fcb, (const void*)bounded_cluster_wait_kernel));
+  for (int form = 1; form <= 2; ++form) {
+    const int param = 2 | form << 4;
+    const size_t bytes = gsync_barrier_bytes(GSYNC_BAR_CLUSTER, 4, param);
+    void* bar4 = nullptr;
+    CHECK(cudaMalloc(&bar4, bytes));
+    CHECK(gsync_barrier_init(bar4, bytes, GSYNC_BAR_CLUSTER, 4, param, own, nullptr));
+    CHECK(cudaMemset(rc3, 0, 2 * sizeof(int)));
+    void* args4[] = {&bar4, &rc3, &ns3};
+    CHECK(gsync_launch_coresident((const void*)fcb, 4, threads, 0, 2, args4, nullptr));
+    CHECK(cudaDeviceSynchronize());
+    CHECK(cudaMemcpy(hrc, rc3, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+    CHECK(cudaMemcpy(hns, ns3, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    bool timed_out = false;
+    for (int i = 0; i < 2; ++i) {
+      timed_out = timed_out || hrc[i] == GSYNC_ETIMEDOUT;
+      if ((hrc[i] != GSYNC_ETIMEDOUT && hrc[i] != GSYNC_EABORTED) || hns[i] < 1000000ull || hns[i] > 200000000ull) {
+        printf("FAIL cluster barrier form %d, block %d: rc %d after %llu ns\n", form, i, hrc[i],
+               (unsigned long long)hns[i]);
+        return 1;
+      }
+    }
+    if (!timed_out || (form == 2 && hrc[0] != hrc[1])) {
+      printf("FAIL cluster barrier form %d: rc %d / %d\n", form, hrc[0], hrc[1]);
+      return 1;
+    }
+    CHECK(cudaFree(bar4));
+  }
   printf("OK %d blocks x %d rounds; %d blocks in clusters of %d x %d rounds, at most %u of %d inside; "
          "bounded waits ended after %.2f / %.2f / %.2f ms\n", B, rounds, BC, C, rounds, h2[3], n, hns[0] / 1e6,
          hns[1] / 1e6, hns[2] / 1e6);

@@ -17,7 +17,10 @@ KINDS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("tree", 2), ("cl
          ("cluster", 8), ("sharded", 32), ("sharded", 8), ("sharded", 1), ("die", 0), ("die", 1), ("split", 1 | 1 << 8),
          ("split", 1 | 16 << 8), ("split", 16 | 16 << 8), ("split", 64 | 64 << 8), ("split", 7 | 3 << 8),
          ("count", 0), ("count", 8), ("count", 1023), ("count", 8 | 16 << 16), ("count", 2 << 16),
-         ("count", 8 | 64 << 16), ("count", 7 << 16)]
+         ("count", 8 | 64 << 16), ("count", 7 << 16),
+         # the counting form of the cluster barrier (param = c | form << 4 | sleep << 8)
+         ("cluster", 2 | 1 << 4), ("cluster", 4 | 1 << 4 | 8 << 8), ("cluster", 8 | 1 << 4 | 8 << 8),
+         ("cluster", 2 | 2 << 4), ("cluster", 4 | 2 << 4 | 8 << 8), ("cluster", 8 | 2 << 4 | 1023 << 8)]
 
 
 @pytest.mark.parametrize("kind,param", KINDS)
@@ -41,7 +44,7 @@ def test_sampled_sweep_1000_rounds(kind, param, nblocks):
     # 144 with clusters of 8.
     from paper_1110_4623_gb300 import runner
     if kind == "cluster":
-        nblocks -= nblocks % param
+        nblocks -= nblocks % (param & 0xF)
     got = runner.BarrierRun(kind, nblocks, 128, 1000, full=False, param=param).run()
     want = calc.barrier_sampled(nblocks, 1000)
     assert got["rc"] == 0 and got["status"] == 0, got["status"]
@@ -51,7 +54,7 @@ def test_sampled_sweep_1000_rounds(kind, param, nblocks):
 
 @pytest.mark.parametrize("kind,param", [("atomic", 0), ("flag", 0), ("tree", 3), ("cluster", 1), ("sharded", 3),
                                         ("die", 0), ("die", 1), ("split", 5 | 3 << 8), ("count", 0),
-                                        ("count", 8 | 5 << 16)])
+                                        ("count", 8 | 5 << 16), ("cluster", 1 | 1 << 4), ("cluster", 1 | 2 << 4 | 8 << 8)])
 @pytest.mark.parametrize("nblocks,threads", [(1, 32), (2, 64), (37, 96), (151, 256)])
 def test_ragged_grids_full_fold(kind, param, nblocks, threads):
     from paper_1110_4623_gb300 import runner
@@ -70,13 +73,16 @@ def test_zero_rounds():
     assert got["rc"] == 0 and got["status"] == 0 and not got["mix"].any()
 
 
-@pytest.mark.parametrize("kind,nblocks", [("flag", 64), ("die", 64), ("die", 1184), ("die", 7), ("split", 1184),
-                                          ("count", 1184), ("count", 7)])
-def test_repeated_launches_continue_epochs(kind, nblocks):
+@pytest.mark.parametrize("kind,nblocks,param", [("flag", 64, 0), ("die", 64, 0), ("die", 1184, 0), ("die", 7, 0),
+                                                ("split", 1184, 0), ("count", 1184, 0), ("count", 7, 0),
+                                                ("cluster", 1184, 4 | 1 << 4 | 8 << 8), ("cluster", 1184, 8 | 2 << 4),
+                                                ("cluster", 7, 1 | 1 << 4)])
+def test_repeated_launches_continue_epochs(kind, nblocks, param):
     # The object keeps its epoch across launches: a second launch attaches at the new epoch
-    # (DIE: and counts its blocks per die again in its first crossing).
+    # (DIE: and counts its blocks per die again in its first crossing; the counting kinds:
+    # their counter rounded down to a multiple of the arrivals per crossing).
     from paper_1110_4623_gb300 import runner
-    br = runner.BarrierRun(kind, nblocks, 128, 501, full=False)
+    br = runner.BarrierRun(kind, nblocks, 128, 501, full=False, param=param)
     for _ in range(3):
         got = br.run()
         assert got["status"] == 0 and not got["bad"].any()

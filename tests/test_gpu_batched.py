@@ -115,6 +115,21 @@ def test_graph_capture_replays_exactly():
         check(run, keys, adds, run.results(), 20)
 
 
+@pytest.mark.parametrize("cluster", [2, 8])
+def test_cluster_launch_graph_capture_replays_exactly(cluster):
+    # The tuned configuration of the batched workload is a cluster launch (clusters of 8 for the
+    # group barriers, the carrying ticket lock): captured as it is into a CUDA graph, with the
+    # kernel that collects the carried sums, it replays exactly, launch after launch.
+    import torch
+    run, keys, adds = make(300_000, rounds=20, cluster=cluster,
+                           policy=[("ticket_carry", 0, 0), ("ticket_carry", 64, 2000), ("ticket_carry", 0, 0)])
+    run.capture()
+    for _ in range(3):
+        run.replay()
+        torch.cuda.synchronize()
+        check(run, keys, adds, run.results(), 20)
+
+
 def test_cooperative_launch_in_capture_or_refused_cleanly():
     # Either the cooperative launch captures and replays exactly, or capture is refused with
     # an error status and the context stays usable.

@@ -113,16 +113,23 @@ def test_host_buffer_entry_point():
 @pytest.mark.parametrize("nblocks,cs_words", [(1184, 0), (1184, 64), (1184, 1024), (592, 64), (16, 7)])
 def test_cluster_cohort_mutex(cluster, nblocks, cs_words):
     # The cohort protocol over thread-block clusters: the local lock lives in distributed
-    # shared memory; each cluster's grants follow its own tickets.
+    # shared memory; each cluster's grants follow its own tickets.  At 1184 blocks this is the
+    # contention sweep's full shape: 256 threads, 100 acquisitions per block, delays
+    # U{0..2000} cycles, on the inputs the bench times (their seed), with the bench's backoff.
+    from paper_1110_4623_gb300 import gsync as G
     from paper_1110_4623_gb300 import runner
     nb = nblocks - nblocks % cluster
-    delay, add = inputs.mutex_inputs(nb, 50, 31_000 + cluster + nb + cs_words)
-    got = runner.MutexRun("cluster", nb, 256, 50, cs_words, delay, add, cluster=cluster, timeout_ns=10_000_000_000,
+    acq = 100 if nb == 1184 else 50
+    seed = (inputs.mutex_seed(G.MUTEX_KINDS["cluster"], nb, cs_words) if nb == 1184
+            else 31_000 + cluster + nb + cs_words)
+    delay, add = inputs.mutex_inputs(nb, acq, seed)
+    got = runner.MutexRun("cluster", nb, 256, acq, cs_words, delay, add, cluster=cluster, timeout_ns=10_000_000_000,
                           bo=runner.backoff(min_ns=128, max_ns=4000)).run()
-    want = calc.mutex_final(nb, 50, cs_words, add)
+    want = calc.mutex_final(nb, acq, cs_words, add)
     assert got["rc"] == 0 and got["status"] == 0, got["status"]
     assert got["total"] == want["total"] and np.array_equal(got["data"], want["data"])
-    assert calc.check_grant_log(got["log"], got["ticket"], nb, 50, False, group_bits=12) == []
+    assert np.array_equal(got["count"], want["count"])
+    assert calc.check_grant_log(got["log"], got["ticket"], nb, acq, False, group_bits=12) == []
 
 
 @pytest.mark.parametrize("budget", [1, 3, 32767])

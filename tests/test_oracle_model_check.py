@@ -50,6 +50,13 @@ CORRECT = [
     ("tree_barrier_3", mc.TreeBarrier(fan=2), 3, 2),
     ("tree_barrier_4", mc.TreeBarrier(fan=2), 4, 2),
     ("cluster_barrier", mc.ClusterBarrier(c=2), 4, 2),
+    ("cluster_count_barrier_poll", mc.ClusterCountBarrier(c=2), 4, 2),
+    ("cluster_count_barrier_poll_base", mc.ClusterCountBarrier(c=2, base=3), 4, 3),
+    ("cluster_count_barrier_three_clusters", mc.ClusterCountBarrier(c=2), 6, 1),
+    ("cluster_count_barrier_c3", mc.ClusterCountBarrier(c=3), 6, 1),
+    ("cluster_count_barrier_c1", mc.ClusterCountBarrier(c=1), 3, 2),
+    ("cluster_count_barrier_second", mc.ClusterCountBarrier(c=2, release="cluster"), 4, 2),
+    ("cluster_count_barrier_second_base", mc.ClusterCountBarrier(c=2, base=2, release="cluster"), 4, 3),
     ("sharded_barrier_2", mc.ShardedBarrier(shards=2), 3, 3),
     ("sharded_barrier_3", mc.ShardedBarrier(shards=3), 4, 2),
     ("sharded_barrier_1", mc.ShardedBarrier(shards=1), 3, 2),
@@ -126,6 +133,13 @@ BROKEN = [
     # counting in globally.
     ("cluster_leader_early", mc.ClusterBarrier(c=2, broken="leader_early"), 4, 1, "passed round"),
     ("cluster_all_count", mc.ClusterBarrier(c=2, broken="all_count"), 4, 1, "passed round"),
+    # Counting form of the cluster barrier: a target one short, and blocks that skip the second
+    # cluster barrier that is meant to hold them until their leader saw the crossing complete.
+    ("cluster_count_off_by_one", mc.ClusterCountBarrier(c=2, broken="off_by_one"), 4, 1, "passed round"),
+    ("cluster_count_second_off_by_one", mc.ClusterCountBarrier(c=2, release="cluster", broken="off_by_one"), 4, 1,
+     "passed round"),
+    ("cluster_count_no_second", mc.ClusterCountBarrier(c=2, release="cluster", broken="no_second"), 4, 1,
+     "passed round"),
 ]
 
 
