@@ -105,7 +105,9 @@ def result_rows(out):
             rows.append({"section": "batched", "kind": arm, "acq_per_s": r["acq_per_s"], "frac": r.get("frac"),
                          "cluster": r["cluster"]})
     for rate, r in out.get("serving", {}).get("rates", {}).items():
-        for arm in ("persistent", "per_request_launch"):
+        for arm in ("persistent", "persistent_device_ring", "per_request_launch"):
+            if arm not in r:
+                continue
             a = r[arm]
             rows.append({"section": "serving", "kind": arm, "offered_req_s": float(rate),
                          "achieved_req_s": a["achieved_req_s"], "p50_us": a["p50_us"], "p99_us": a["p99_us"]})
@@ -640,10 +642,12 @@ def serve_section(calc, inputs, runner):
         sample = rng.choice(nreq, size=min(nreq, 300), replace=False)
         want = calc.serve_final(off[sample], ln[sample], pool)
         row = {"nreq": nreq, "chunk_values": SERVE_CHUNK}
-        for arm in ("persistent", "per_request_launch"):
+        # persistent: the ring in pinned host memory; persistent_device_ring: the ring in managed
+        # memory placed in device memory, written in place by the host
+        for arm in ("persistent", "persistent_device_ring", "per_request_launch"):
             sr = runner.ServeRun(off, ln, sched, dpool, nslots=64, nblocks=304, admitters=SERVE_ADMITTERS,
-                                 chunk_elems=SERVE_CHUNK)
-            r = sr.run() if arm == "persistent" else sr.baseline(nstreams=8)
+                                 chunk_elems=SERVE_CHUNK, ring="device" if arm == "persistent_device_ring" else "host")
+            r = sr.baseline(nstreams=8) if arm == "per_request_launch" else sr.run()
             lat = r["latency_ns"] / 1e3
             span = (sched[-1] + r["latency_ns"][-1]) / 1e9
             row[arm] = {"rc": r["rc"], "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),

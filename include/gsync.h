@@ -472,7 +472,11 @@ int gsync_bench_batched(const gsync_batched_work* w, void* stream);
  *    ctrl[32] = shutdown), res
  *    (nreq x i64) and done (nreq x u32) are caller-owned pinned host memory
  *    (cudaHostAlloc or registered); pool is device memory; offset, length, sched_ns and
- *    latency_ns are ordinary host arrays.  workspace (device, 256-byte aligned) holds
+ *    latency_ns are ordinary host arrays.  The ring may instead be managed memory
+ *    (cudaMallocManaged): on a GPU whose host reaches managed memory in place
+ *    (cudaDevAttrDirectManagedMemAccessFromHost), the call advises it to live in device
+ *    memory and to stay mapped for the host, and moves it there before it starts (the
+ *    host's stores then land in device memory, and the admitters poll it through L2).  workspace (device, 256-byte aligned) holds
  *    gsync_serve_workspace_bytes(nslots) bytes.
  *  - Requires 0 <= offset[q], 1 <= length[q], offset[q] + length[q] <= pool_elems <= 2^32,
  *    at most 32767 chunks per request, nslots <= 64, non-decreasing sched_ns.

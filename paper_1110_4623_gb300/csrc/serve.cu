@@ -2,9 +2,11 @@
 // ticket-window semaphore (the paper motivates its primitives with task queues, Section 1, and
 // names hardware enqueue/dequeue as a wish, Section 7).
 //
-// The host publishes requests into a ring of 16-byte entries in pinned host memory (each
-// entry carries its sequence number, written last with a release store).  Inside one
-// co-resident launch:
+// The host publishes requests into a ring of 16-byte entries (each entry carries its sequence
+// number, written last with a release store).  The ring is caller memory: pinned host memory,
+// which the admitters poll across the host link, or managed memory placed in device memory,
+// which the host writes in place and the admitters poll through L2.  Inside one co-resident
+// launch:
 //   * admitter blocks wait on the admission semaphore (n = number of in-flight slots), take
 //     the next request index under the ring's ticket lock, wait for that entry to appear,
 //     claim a free slot and publish the request in it (generation-tagged chunk counter,
@@ -357,6 +359,34 @@ int host_dev_ptr(void* host, void** dev) {
   return GSYNC_OK;
 }
 
+// The ring's device view.  Pinned host memory is mapped (host_dev_ptr).  A ring in managed
+// memory has one address on both sides; on a GPU whose host reaches managed memory in place
+// over a coherent link (cudaDevAttrDirectManagedMemAccessFromHost), it is advised to live in
+// device memory and to stay mapped for the host, and is moved there before the host clears it:
+// the producer's stores then cross the link into device memory, and the admitters poll it
+// through the GPU's L2 instead of across the link.
+int ring_device_ptr(void* ring, size_t bytes, cudaStream_t st, void** dev) {
+  cudaPointerAttributes attr;
+  GSYNC_CUDA(cudaPointerGetAttributes(&attr, ring));
+  if (attr.type != cudaMemoryTypeManaged) return host_dev_ptr(ring, dev);
+  int devid = 0, direct = 0;
+  GSYNC_CUDA(cudaGetDevice(&devid));
+  GSYNC_CUDA(cudaDeviceGetAttribute(&direct, cudaDevAttrDirectManagedMemAccessFromHost, devid));
+  if (direct) {
+    cudaMemLocation gpu = {};
+    gpu.type = cudaMemLocationTypeDevice;
+    gpu.id = devid;
+    cudaMemLocation cpu = {};
+    cpu.type = cudaMemLocationTypeHost;
+    GSYNC_CUDA(cudaMemAdvise(ring, bytes, cudaMemAdviseSetPreferredLocation, gpu));
+    GSYNC_CUDA(cudaMemAdvise(ring, bytes, cudaMemAdviseSetAccessedBy, cpu));
+    GSYNC_CUDA(cudaMemPrefetchAsync(ring, bytes, gpu, 0, st));
+    GSYNC_CUDA(cudaStreamSynchronize(st));
+  }
+  *dev = ring;
+  return GSYNC_OK;
+}
+
 using Clock = std::chrono::steady_clock;
 
 // Pins a host thread to one core (counted from the last core down) so that the producer and
@@ -454,6 +484,8 @@ extern "C" int gsync_serve_run(const gsync_serve_cfg* cfg, gsync_serve_buffers* 
   if (buf->publish_ns)
     for (int q = 0; q < cfg->nreq; ++q) buf->publish_ns[q] = 0;
   // Host control word ctrl[32] = shutdown; the ring starts empty (no entry has a valid seq).
+  void* d_ring = nullptr;
+  if (int rc = ring_device_ptr(buf->ring, kRingStride * (size_t)cfg->ring_slots, st, &d_ring)) return rc;
   volatile uint32_t* ctrl = buf->ctrl;
   ctrl[32] = 0;
   memset(buf->ring, 0, kRingStride * (size_t)cfg->ring_slots);
@@ -461,8 +493,7 @@ extern "C" int gsync_serve_run(const gsync_serve_cfg* cfg, gsync_serve_buffers* 
   std::atomic_thread_fence(std::memory_order_seq_cst);
 
   Args a;
-  void *d_ring, *d_ctrl, *d_res, *d_done;
-  if (int rc = host_dev_ptr(buf->ring, &d_ring)) return rc;
+  void *d_ctrl, *d_res, *d_done;
   if (int rc = host_dev_ptr((void*)buf->ctrl, &d_ctrl)) return rc;
   if (int rc = host_dev_ptr(buf->res, &d_res)) return rc;
   if (int rc = host_dev_ptr((void*)buf->done, &d_done)) return rc;

@@ -526,6 +526,49 @@ class BatchedRun:
         return out
 
 
+def _cudart():
+    """The CUDA runtime library that torch loaded (by its soname), else the toolkit's."""
+    import ctypes
+    import glob
+    names = ["libcudart.so.13", "libcudart.so"] + sorted(glob.glob("/usr/local/cuda/lib64/libcudart.so*"))
+    for name in names:
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    raise RuntimeError("no CUDA runtime library found for a managed allocation")
+
+
+class ManagedBuffer:
+    """Managed memory (cudaMallocManaged, one address for host and device), freed on collection.
+    The serving loop places a ring held here in device memory, written in place by the host."""
+
+    def __init__(self, nbytes: int):
+        import ctypes
+        self._rt = _cudart()
+        p = ctypes.c_void_p()
+        rc = self._rt.cudaMallocManaged(ctypes.byref(p), ctypes.c_size_t(nbytes), ctypes.c_uint(1))
+        if rc != 0 or not p.value:
+            raise RuntimeError(f"cudaMallocManaged({nbytes}) failed: {rc}")
+        self.ptr, self.nbytes = p.value, nbytes
+        self._handle = ctypes.c_void_p(p.value)  # kept for __del__, which may run at shutdown
+
+    def data_ptr(self) -> int:
+        return self.ptr
+
+    def free(self):
+        if getattr(self, "ptr", None):
+            torch.cuda.synchronize()
+            self._rt.cudaFree(self._handle)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # interpreter shutdown: the process exit releases the memory
+            pass
+
+
 class ServeRun:
     """The serving workload: a device value pool, request descriptors and Poisson arrival times,
     run through the persistent loop (gsync_serve_run) or one launch per request
@@ -533,7 +576,7 @@ class ServeRun:
 
     def __init__(self, offset, length, sched_ns, pool: torch.Tensor, nslots: int = 32, nblocks: int = 304,
                  admitters: int = 8, chunk_elems: int = 32768, ring_slots: int = 65536, timeout_ns: int = 0,
-                 drain_timeout_s: int = 30):
+                 drain_timeout_s: int = 30, ring: str = "host"):
         self.nreq = len(offset)
         self.offset = np.ascontiguousarray(offset, dtype=np.int64)
         self.length = np.ascontiguousarray(length, dtype=np.int64)
@@ -541,7 +584,13 @@ class ServeRun:
         self.pool = pool
         self.cfg = G.gsync_serve_cfg(self.nreq, nslots, nblocks, admitters, chunk_elems, ring_slots, 2000,
                                      drain_timeout_s, timeout_ns)
-        self.ring = torch.zeros(ring_slots * 128, dtype=torch.uint8).pin_memory()
+        # ring="host": pinned host memory, polled by the admitters across the host link;
+        # ring="device": managed memory that the loop places in device memory, written in place
+        # by the host's producer thread
+        if ring not in ("host", "device"):
+            raise ValueError(ring)
+        self.ring = (torch.zeros(ring_slots * 128, dtype=torch.uint8).pin_memory() if ring == "host"
+                     else ManagedBuffer(ring_slots * 128))
         self.ctrl = torch.zeros(64, dtype=torch.int32).pin_memory()
         self.res = torch.zeros(self.nreq, dtype=torch.int64).pin_memory()
         self.done = torch.zeros(self.nreq, dtype=torch.int32).pin_memory()

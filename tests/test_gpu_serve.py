@@ -73,3 +73,25 @@ def test_extreme_lengths(pool):
     r = runner.ServeRun(off, ln, sched, dp, nslots=2).run()
     assert r["rc"] == 0
     assert np.array_equal(r["res"], calc.serve_final(off, ln, p))
+
+
+@pytest.mark.parametrize("rate,n,kw", [(1e5, 2000, {}), (1e6, 4000, {"ring_slots": 64, "nslots": 16})])
+def test_device_resident_ring_exact(pool, rate, n, kw):
+    # The ring in managed memory that the loop places in device memory (the host's producer
+    # writes it in place): the same exact results, also when the ring wraps.
+    off, ln, p, _ = pool
+    idx = np.arange(n)
+    r = make(pool, idx, rate, ring="device", **kw).run()
+    assert r["rc"] == 0, r["stats"]
+    assert np.array_equal(r["res"], calc.serve_final(off[idx], ln[idx], p))
+    assert r["stats"][0] == n and r["stats"][2] == n and r["stats"][3] == 0
+
+
+def test_device_resident_ring_same_alone_and_in_the_mix(pool):
+    off, ln, p, _ = pool
+    idx = np.arange(300)
+    alone = make(pool, idx, 2e3, nslots=1, ring="device").run()
+    mixed = make(pool, idx, 5e6, nslots=64, ring="device").run()
+    assert alone["rc"] == 0 and mixed["rc"] == 0
+    assert np.array_equal(alone["res"], mixed["res"])
+    assert np.array_equal(mixed["res"], calc.serve_final(off[idx], ln[idx], p))
