@@ -2,10 +2,10 @@
 
 One step = one pass over every row of the hot path at 1184 blocks:
   * mutex contention (the paper's 4 kinds, its ring-buffer mutex and spin-then-sleep policy,
-    and the two-die cohort lock x critical sections of 0/64/1024 words, 256 threads per block,
+    and the two cohort locks x critical sections of 0/64/1024 words, 256 threads per block,
     100 acquisitions per block, seeded delays U{0..2000} cycles),
-  * grid barriers (atomic, flag, tree, cluster 2/4/8 and its counting form, sharded, two-die, split, counting;
-    128 threads, 1000 rounds each),
+  * grid barriers (atomic, flag, tree and its counting form, cluster 2/4/8 and its counting form,
+    sharded, two-die, split, counting; 128 threads, 1000 rounds each),
   * counting semaphores (sleeping FA kind, n in {1, 4, 16, 64}; 128 threads, 200 pairs each,
     hold U{100..5000} cycles).
 `value` is lock acquisitions per second of the library's default mutex kind over its three
@@ -42,7 +42,9 @@ DEFAULT_MUTEX = "cluster"
 DEFAULT_BARRIER = ("count", 8)
 # cluster params: c | form << 4 (form 0: atomic stage over the leaders; 2: counting stage, the
 # rest of the cluster released by a second cluster barrier -- the fastest cluster form measured)
-BARRIERS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("cluster", 2), ("cluster", 4), ("cluster", 8),
+# tree params: fan | form << 16 (form 1: counting tree, node counters that only grow)
+BARRIERS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("tree", 8 | 1 << 16), ("tree", 64 | 1 << 16),
+            ("cluster", 2), ("cluster", 4), ("cluster", 8),
             ("cluster", 4 | 2 << 4), ("cluster", 8 | 2 << 4), ("sharded", 32), ("sharded", 8), ("die", 0),
             ("die", 1), ("split", 16 | 16 << 8), ("count", 0), ("count", 8)]
 # Backoff (min_ns, max_ns) per kind; the ticket kinds sleep min_ns per waiter ahead, capped.
@@ -161,7 +163,9 @@ def barrier_name(kind, param):
         c, form, sleep = param & 0xF, (param >> 4) & 0xF, param >> 8
         name = f"cluster{c}" + ("", "_count", "_count_cb")[form]
         return name + (f"_s{sleep}" if sleep else "")
-    if kind in ("tree", "sharded") or (kind == "count" and param):
+    if kind == "tree":
+        return f"tree{param & 0xFFFF}" + ("_count" if param >> 16 else "")
+    if kind == "sharded" or (kind == "count" and param):
         return f"{kind}{param}"
     if kind == "split":
         return f"split{param & 0xFF}x{param >> 8}"
@@ -328,7 +332,7 @@ def barrier_roof_ns(terms, kind, param, B):
       atomic : last arrival's round trip, B serialized arrivals, release hand-off
       count  : B serialized arrivals, whose last is the release (no round trip back)
       tree   : per level a round trip of the last arriver and fan serialized arrivals, then
-               the root's release hand-off
+               the root's release hand-off (counting form: no round trip at the root)
       flag   : (XF) two hand-offs in series -- the last arrival flag to the master block, the
                release flags to every block -- plus the master's second gather pass (a thread
                watches two or three of the 16-byte flag vectors, so some need two loads)
@@ -345,9 +349,10 @@ def barrier_roof_ns(terms, kind, param, B):
     elif kind == "count":
         ns = B * t_atom + L_h
     elif kind == "tree":
-        fan = param
+        fan, form = param & 0xFFFF, param >> 16
         lv = tree_levels(B, fan)
-        ns = lv * (L_rt + fan * t_atom) + L_h
+        # form 1: the root's completing add is the release (no round trip back at the top)
+        ns = (lv - form) * L_rt + lv * fan * t_atom + L_h
     elif kind == "flag":
         ns = 2 * L_h + L_ld
     elif kind == "sharded":

@@ -796,7 +796,13 @@ __device__ __forceinline__ int sem_post(const SemRef& s) {
 // FLAG   : lines 1.. arrival flags (one word per block, packed), then release flags (one
 //          word per block, packed; mode 1: a single release word on its own line).  At most
 //          8192 blocks; the master block's threads gather the flags.
-// TREE   : line 1 release epoch, lines 2.. one counter line per tree node (fan-in = param).
+// TREE   : param = fan | form << 16.  Lines 2.. one counter line per tree node, level by
+//          level, the root last.  Form 0: line 1 the release epoch; the last arriver at a node
+//          resets it and counts in at the parent, and the root's last arriver advances the
+//          epoch, which every block polls.  Form 1 (counting): 64-bit node counters that only
+//          grow; the arrival that brings a node to a multiple of its size is its last one and
+//          counts in at the parent, and the root's last add is the release: every other block
+//          polls the root until base + e x (root's size).
 // SHARDED: lines 1..S: S = param arrival counters (block b counts into counter b mod S with a
 //          fire-and-forget red.release; counters only grow, so after crossing e counter s
 //          holds e x (blocks of shard s)); then release flags (one word per block, packed).
@@ -845,6 +851,7 @@ struct BarrierRef {
   uint64_t timeout_ns;
   uint32_t die, n_mine, active;  // DIE: this block's die, its die's blocks (0 = unregistered), dies
   uint64_t base, sub_base;       // COUNT: counters' values at attach (multiples of their parties)
+  uint32_t root, root_size;      // TREE counting form: the root's node index and its arrivals
   __device__ __forceinline__ uint32_t* die_line(uint32_t d, uint32_t i) const {
     return s + s[d ? kHdrDieOff1 : kHdrDieOff0] + i * kLineWords;
   }
@@ -873,6 +880,24 @@ __device__ __forceinline__ BarrierRef barrier_attach(void* state) {
     b.epoch = b.mode ? ptx::ld_relaxed(b.release_flags()) : ptx::ld_relaxed(b.release_flags() + blockIdx.x);
   } else if (b.kind == GSYNC_BAR_TREE) {
     b.epoch = ptx::ld_relaxed(b.line(1));
+    if ((b.param >> 16) != 0u) {
+      // Counting form: locate the root; its counter read here lies in [k S, k S + S - 1] (no
+      // crossing completes before this block arrives), so rounding down gives every block the
+      // same base.
+      const uint32_t fan = max(b.param & 0xFFFFu, 2u);
+      uint32_t width = b.n, total = 0;
+      for (;;) {
+        const uint32_t nodes = (width + fan - 1u) / fan;
+        total += nodes;
+        if (nodes <= 1u) break;
+        width = nodes;
+      }
+      b.root = total - 1u;
+      b.root_size = width;
+      const uint64_t v = ptx::ld_relaxed_u64((const uint64_t*)b.line(2u + b.root));
+      b.base = width ? v - v % width : v;
+      b.epoch = 0;
+    }
   } else if (b.kind == GSYNC_BAR_SPLIT) {
     b.epoch = ptx::ld_relaxed(b.line(1u + blockIdx.x % (b.param >> 8)));
   } else if (b.kind == GSYNC_BAR_COUNT) {
@@ -1112,11 +1137,41 @@ __device__ __forceinline__ int barrier_wait(BarrierRef& b) {
         if (master && !leader) s_rc = (int)ptx::ld_relaxed_cluster((const uint32_t*)ptx::map_cluster_rank(&s_rc, 0u));
       }
     }
+  } else if (KIND == GSYNC_BAR_TREE && (b.param >> 16) != 0u) {
+    if (master) {
+      // Counting combining tree: count in at the leaf; the arrival that completes a node's
+      // crossing counts in at the parent; the root's completing add is the release.
+      const uint32_t fan = max(b.param & 0xFFFFu, 2u);
+      uint32_t width = b.n, node = blockIdx.x / fan, off = 0;
+      bool released = false;
+      for (;;) {
+        const uint32_t nodes = (width + fan - 1u) / fan;
+        const uint32_t size = min(fan, width - node * fan);
+        const uint64_t now = ptx::atom_add_acq_rel_u64((uint64_t*)b.line(2u + off + node), 1ull) + 1ull;
+        if (now % size != 0u) break;  // not this node's last arrival
+        if (nodes == 1u) {
+          released = true;  // the root's last arrival: the crossing is complete
+          break;
+        }
+        off += nodes;
+        width = nodes;
+        node /= fan;
+      }
+      int rc = GSYNC_OK;
+      if (!released) {
+        const uint64_t target = b.base + (uint64_t)e1 * b.root_size;
+        const uint64_t* root = (const uint64_t*)b.line(2u + b.root);
+        Waiter w;
+        while (ptx::ld_acquire_u64(root) < target)
+          if ((rc = w.tick(b.timeout_ns, b.abort_word())) != GSYNC_OK) break;
+      }
+      s_rc = rc;
+    }
   } else if (KIND == GSYNC_BAR_TREE) {
     if (master) {
       // Combining tree: count in at the leaf; the last arriver at a node resets it and
       // counts in at the parent; the last arriver at the root advances the epoch.
-      const uint32_t fan = b.param;
+      const uint32_t fan = max(b.param & 0xFFFFu, 2u);
       uint32_t width = b.n, node = blockIdx.x / fan, off = 0;
       int rc = GSYNC_OK;
       for (;;) {

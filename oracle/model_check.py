@@ -26,6 +26,7 @@ The algorithms follow Section 5 ("Design") and the pseudocode of the Appendix:
   AtomicBarrier two-stage atomic-counter barrier (Section 5, "Barrier")
   FlagBarrier   decentralized XF flag barrier (Section 5, "Barrier")
   TreeBarrier   combining-tree barrier (Section 2, hierarchical barriers)
+  TreeCountBarrier  the same with node counters that only grow; the root's last add releases
   ShardedBarrier  arrivals counted on several counters, gathered by the master block
   ClusterBarrier  barrier inside groups of c blocks, then one leader per group globally
   ClusterCountBarrier  the same, with a growing counter over the leaders as the global stage
@@ -999,6 +1000,52 @@ class TreeBarrier:
                 k += 1
                 return ((0 if k < ops else DONE), k, inc(e), p // self.fan), sh, ("pass",)
             return loc, sh, None
+        raise AssertionError(pc)
+
+
+class TreeCountBarrier:
+    """Combining tree of fan-in `fan` whose node counters only grow.  A block counts itself in
+    at its leaf; the arrival whose fetch-and-add brings a node's counter to a multiple of the
+    node's size is that node's last one for this crossing and counts in at the parent (counters
+    start at multiples of their sizes, so no reset is needed); the root's last arrival is the
+    release.  Every other arrival polls the root until it reaches base + e x (root's size).
+
+    Planted mistakes: broken="first_climbs": the arrival whose add leaves a node at one past a
+    multiple of its size climbs, instead of the one that completes it; broken="target_short":
+    the root target is one short."""
+    kind = "barrier"
+
+    def __init__(self, fan=2, base=0, broken=None):
+        self.fan, self.base, self.broken = fan, base, broken
+
+    def init(self, nproc, ops):
+        size, _ = TreeBarrier(self.fan)._tree(nproc)
+        return tuple(self.base * z for z in size), tuple((0, 0, 0, p // self.fan) for p in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        size, parent = TreeBarrier(self.fan)._tree(nproc)
+        root = len(size) - 1
+        pc, k, e, nd = loc
+        leaf = p // self.fan
+        if pc in (0, 4):  # count in at node nd (pc 0: the leaf, the block's own arrival)
+            c = sh[nd] + 1
+            ev = ("arrive",) if pc == 0 else None
+            if self.broken == "first_climbs":
+                climbs = c % size[nd] == 1 % size[nd]
+            else:
+                climbs = c % size[nd] == 0
+            if not climbs:
+                return (3, k, e, leaf), _set(sh, nd, c), ev
+            if nd == root:
+                return (5, k, e, leaf), _set(sh, nd, c), ev  # the release itself
+            return (4, k, e, parent[nd]), _set(sh, nd, c), ev
+        if pc == 3:  # poll the root
+            target = (self.base + e + 1) * size[root] - (1 if self.broken == "target_short" else 0)
+            if sh[root] < target:
+                return loc, sh, None
+        if pc in (3, 5):
+            k2 = k + 1
+            return ((0 if k2 < ops else DONE), k2, e + 1, leaf), sh, ("pass",)
         raise AssertionError(pc)
 
 

@@ -165,7 +165,7 @@ uint32_t barrier_lines(int kind, uint32_t n, uint32_t param) {
       return 1 + fl + (param ? 1 : fl);
     }
     case GSYNC_BAR_TREE:
-      return 2 + tree_nodes(n, param);
+      return 2 + tree_nodes(n, param & 0xFFFFu);
     case GSYNC_BAR_SHARDED:
       return 1 + param + (n + 31) / 32;
     case GSYNC_BAR_DIE:
@@ -284,7 +284,11 @@ size_t gsync_barrier_bytes(int kind, int nblocks, int param) {
   switch (kind) {
     case GSYNC_BAR_ATOMIC: break;
     case GSYNC_BAR_FLAG: if ((param != 0 && param != 1) || nblocks > 8192) return 0; break;
-    case GSYNC_BAR_TREE: if (param < 2 || param > 1024) return 0; break;
+    case GSYNC_BAR_TREE: {
+      const int fan = param & 0xFFFF, form = param >> 16;
+      if (param < 0 || fan < 2 || fan > 1024 || form > 1) return 0;
+      break;
+    }
     case GSYNC_BAR_CLUSTER: {
       const int c = param & 0xF, form = (param >> 4) & 0xF, sleep16 = param >> 8;
       if (param < 0 || c < 1 || c > 8 || nblocks % c || form > 2 || sleep16 > 1023) return 0;

@@ -63,6 +63,14 @@ def test_size_queries_without_gpu(lib_path):
     # fan-in 8 over 1184 blocks: 148 + 19 + 3 + 1 nodes
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["tree"], 1184, 8) == (2 + 148 + 19 + 3 + 1) * 128
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["tree"], 16, 1) == 0
+    # the tree's counting form has the same nodes; forms above 1 and fan-ins past 1024 are refused
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["tree"], 1184, 8 | 1 << 16) == (2 + 148 + 19 + 3 + 1) * 128
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["tree"], 1184, 8 | 2 << 16) == 0
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["tree"], 1184, 1025 | 1 << 16) == 0
+    # the cluster barrier: c | form << 4 | sleep << 8
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["cluster"], 1184, 8 | 2 << 4 | 8 << 8) == 4 * 128
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["cluster"], 1184, 8 | 3 << 4) == 0
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["cluster"], 1184, 8 | 1024 << 8) == 0
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["cluster"], 1184, 8) == 4 * 128
     # two-die objects: 32 KB, room for a 4 KB page homed on each die
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["die"], 1184, 0) == 32768

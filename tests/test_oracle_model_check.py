@@ -49,6 +49,12 @@ CORRECT = [
     ("flag_barrier_wrap", mc.FlagBarrier(base=2 ** 32 - 1), 3, 3),
     ("tree_barrier_3", mc.TreeBarrier(fan=2), 3, 2),
     ("tree_barrier_4", mc.TreeBarrier(fan=2), 4, 2),
+    ("tree_count_barrier_3", mc.TreeCountBarrier(fan=2), 3, 2),
+    ("tree_count_barrier_4", mc.TreeCountBarrier(fan=2), 4, 2),
+    ("tree_count_barrier_5", mc.TreeCountBarrier(fan=2), 5, 1),
+    ("tree_count_barrier_fan3", mc.TreeCountBarrier(fan=3), 4, 2),
+    ("tree_count_barrier_base", mc.TreeCountBarrier(fan=2, base=3), 4, 3),
+    ("tree_count_barrier_one_node", mc.TreeCountBarrier(fan=4), 3, 3),
     ("cluster_barrier", mc.ClusterBarrier(c=2), 4, 2),
     ("cluster_count_barrier_poll", mc.ClusterCountBarrier(c=2), 4, 2),
     ("cluster_count_barrier_poll_base", mc.ClusterCountBarrier(c=2, base=3), 4, 3),
@@ -129,6 +135,10 @@ BROKEN = [
     # Tree barrier: a node never reset, and a leaf's last arriver that releases the grid.
     ("tree_no_reset", mc.TreeBarrier(fan=2, broken="no_reset"), 3, 2, "final state"),
     ("tree_release_at_leaf", mc.TreeBarrier(fan=2, broken="release_at_leaf"), 3, 1, "passed round"),
+    # Counting tree: the wrong arrival climbs (the first of a node's crossing, not the one that
+    # completes it), and a root target one short.
+    ("tree_count_first_climbs", mc.TreeCountBarrier(fan=2, broken="first_climbs"), 4, 2, "passed round"),
+    ("tree_count_target_short", mc.TreeCountBarrier(fan=2, broken="target_short"), 3, 1, "passed round"),
     # Cluster barrier: a leader that counts in before its cluster has arrived, and every block
     # counting in globally.
     ("cluster_leader_early", mc.ClusterBarrier(c=2, broken="leader_early"), 4, 1, "passed round"),
