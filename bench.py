@@ -64,9 +64,9 @@ BATCH_KEYS, BATCH_ACQ, BATCH_GROUPS, BATCH_ROUNDS, BATCH_THREADS = 4096, 1_000_0
 METRIC = "lock acquires/s & barrier ns at 1184 blocks vs L2-atomic roofline; p99 latency"
 # DRAM bytes per launch of the default mutex kind's workload kernel from an ncu capture, or
 # None while the kernel has changed since the last capture.
-ROOF_TRAFFIC = 1_739_179
+ROOF_TRAFFIC = 1_520_555
 ROOF_TRAFFIC_NOTE = ("DRAM bytes (read + write) per launch of the dominant kernel (cluster cohort mutex workload), "
-                     "mean over the step's three launches (CS 0/64/1024: 1.76/2.18/1.28 MB), one-pass ncu capture "
+                     "mean over the step's three launches (CS 0/64/1024: 1.46/1.38/1.72 MB), one-pass ncu capture "
                      "of the same launches in profiles/; algorithmic bytes 1.89 MB (16 B per acquisition)")
 TIMEOUT_NS = 10_000_000_000
 
