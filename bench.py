@@ -79,6 +79,7 @@ def parse():
     p.add_argument("--impl", default="gsync", choices=["gsync", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the batched and serving sections")
+    p.add_argument("--no-sweep", action="store_true", help="skip the grid-size sweep (148..1184 blocks)")
     p.add_argument("--jsonl", default=None, help="also append one JSON row per measured configuration to this file")
     return p.parse_args()
 
@@ -113,6 +114,18 @@ def result_rows(out):
             a = r[arm]
             rows.append({"section": "serving", "kind": arm, "offered_req_s": float(rate),
                          "achieved_req_s": a["achieved_req_s"], "p50_us": a["p50_us"], "p99_us": a["p99_us"]})
+    sw = out.get("sweep", {})
+    for kind, per_cs in sw.get("mutex_acq_per_s", {}).items():
+        for cs, per_b in per_cs.items():
+            for B, v in per_b.items():
+                rows.append({"section": "sweep_mutex", "kind": kind, "cs_words": int(cs), "nblocks": int(B), "acq_per_s": v})
+    for kind, per_b in sw.get("barrier_ns_per_crossing", {}).items():
+        for B, v in per_b.items():
+            rows.append({"section": "sweep_barrier", "kind": kind, "nblocks": int(B), "ns_per_crossing": v})
+    for kind, per_n in sw.get("semaphore_ops_per_s", {}).items():
+        for n, per_b in per_n.items():
+            for B, v in per_b.items():
+                rows.append({"section": "sweep_semaphore", "kind": kind, "n": int(n), "nblocks": int(B), "ops_per_s": v})
     stamp = {"clocks_sm_mhz": out.get("clocks", {}).get("sm_mhz"), "n_gpus": out.get("n_gpus")}
     return [dict(row, **stamp) for row in rows]
 
@@ -582,6 +595,85 @@ def flush_l2():
     _FLUSH[0].zero_()
 
 
+SWEEP_GRIDS = (148, 296, 592, 1184)
+SWEEP_BARRIERS = [("atomic", 0), ("flag", 0), ("tree", 8), ("tree", 64 | 1 << 16), ("cluster", 2), ("cluster", 4),
+                  ("cluster", 8), ("cluster", 8 | 2 << 4), ("count", 8)]
+
+
+def _time_launch(launch, reset, reps=3):
+    """Median device time (ms) of `reps` launches after one untimed one, L2 flushed before each."""
+    import torch
+    ts = []
+    for i in range(reps + 1):
+        reset()
+        flush_l2()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        rc = launch()
+        e.record()
+        torch.cuda.synchronize()
+        assert rc == 0, rc
+        if i:
+            ts.append(s.elapsed_time(e))
+    return float(np.median(ts))
+
+
+def sweep_section(G, calc, inputs, runner, step):
+    """Configs 2 and 3 over their grid sizes, as the paper's Section 6 curves are drawn (ops/s
+    against the number of blocks).  The mutex configurations at 148, 296 and 592 blocks (1184
+    is the timed step's), the barrier kinds at 148..1184 blocks (a cluster grid rounded down to
+    a multiple of its cluster size), both semaphore kinds at 296 and 592 blocks; each a median
+    of 3 launches with L2 flushed before each, and each result checked against the oracle."""
+    out = {"grids": list(SWEEP_GRIDS), "mutex_acq_per_s": {}, "barrier_ns_per_crossing": {}, "semaphore_ops_per_s": {},
+           "l2": "flushed (512 MiB write) before each launch", "parity": "ok"}
+    bad = []
+    for name, kind, policy, bo_ns, spin in MUTEX_CONFIGS:
+        for K in CS_SIZES:
+            row = out["mutex_acq_per_s"].setdefault(name, {}).setdefault(str(K), {})
+            for B in SWEEP_GRIDS[:-1]:
+                delay, add = inputs.mutex_inputs(B, MUTEX_ACQ, inputs.mutex_seed(G.MUTEX_KINDS[kind], B, K))
+                bo = runner.backoff(policy=policy, min_ns=bo_ns[0], max_ns=bo_ns[1], spin=spin) if bo_ns else None
+                mr = runner.MutexRun(kind, B, MUTEX_THREADS, MUTEX_ACQ, K, delay, add, bo=bo, timeout_ns=TIMEOUT_NS,
+                                     cluster=MUTEX_CLUSTER)
+                ms = _time_launch(mr.launch, mr.reset)
+                got, want = mr.results(), calc.mutex_final(B, MUTEX_ACQ, K, add)
+                if got["status"] or got["total"] != want["total"] or not np.array_equal(got["data"], want["data"]):
+                    bad.append(f"mutex {name} K={K} B={B}")
+                row[str(B)] = B * MUTEX_ACQ / (ms * 1e-3)
+    for kind, param in SWEEP_BARRIERS:
+        row = out["barrier_ns_per_crossing"].setdefault(barrier_name(kind, param), {})
+        for B in SWEEP_GRIDS:
+            nb = B - B % (param & 0xF) if kind == "cluster" else B
+            br = runner.BarrierRun(kind, nb, BAR_THREADS, BAR_ROUNDS, full=False, param=param, timeout_ns=TIMEOUT_NS)
+            ms = _time_launch(br.launch, br.status.zero_)
+            mix = br.mix.cpu().numpy().view(np.uint32)
+            if int(br.status.cpu()[0]) or br.bad.cpu().numpy().any() or \
+                    not np.array_equal(mix, calc.barrier_sampled(nb, BAR_ROUNDS)["mix"]):
+                bad.append(f"barrier {kind} {param:#x} B={nb}")
+            row[str(nb)] = ms * 1e6 / BAR_ROUNDS
+    for kind in SEM_STEP_KINDS:
+        for n in SEM_COUNTS:
+            row = out["semaphore_ops_per_s"].setdefault(kind, {}).setdefault(str(n), {})
+            for B in (296, 592):
+                hold, add = inputs.sem_inputs(B, SEM_PAIRS, inputs.SEED_SEM ^ (n << 16) ^ B)
+                sr = runner.SemRun(kind, B, SEM_THREADS, SEM_PAIRS, n, hold, add,
+                                   bo=runner.backoff(min_ns=SEM_BACKOFF[0], max_ns=SEM_BACKOFF[1]), timeout_ns=TIMEOUT_NS)
+                ms = _time_launch(sr.launch, sr.reset)
+                got, want = sr.results(), calc.sem_final(B, SEM_PAIRS, n, add)
+                if got["status"] or got["tally"] != want["tally"] or got["max_occ"] > n:
+                    bad.append(f"sem {kind} n={n} B={B}")
+                row[str(B)] = B * SEM_PAIRS / (ms * 1e-3)
+    # the 1184-block points are the timed step's
+    med = step
+    for (name, K), ms in med["mutex"].items():
+        out["mutex_acq_per_s"][name][str(K)]["1184"] = NBLOCKS * MUTEX_ACQ / (ms * 1e-3)
+    for (kind, n), ms in med["sem"].items():
+        out["semaphore_ops_per_s"][kind][str(n)]["1184"] = NBLOCKS * SEM_PAIRS / (ms * 1e-3)
+    if bad:
+        out["parity"] = bad
+    return out
+
+
 def condvar_section(calc, inputs, runner, terms):
     """Condition variables (future work in Section 7): bounded producer/consumer queue at 1184
     blocks.  Every item takes at least two lock acquisitions (the put and the take), each a
@@ -855,6 +947,10 @@ def run_gpu(args):
     if rank == 0:
         out["e2e"] = e2e
         out["condvar"] = condvar_section(calc, inputs, runner, terms)
+        if not args.no_sweep:
+            step_ms = {"mutex": {key: med[key] for key in step.mutex},
+                       "sem": {key: med[("sem",) + key] for key in step.sem}}
+            out["sweep"] = sweep_section(G, calc, inputs, runner, step_ms)
         if not args.no_batched:
             out["batched"] = batched_section(G, calc, inputs, runner, autotune, terms)
             out["serving"] = serve_section(calc, inputs, runner)

@@ -34,3 +34,18 @@ def test_rows_cover_every_measured_configuration():
 def test_rows_of_a_line_without_optional_sections():
     import bench
     assert bench.result_rows({"config": {}, "n_gpus": 1}) == []
+
+
+def test_sweep_rows():
+    import bench
+    out = {"config": {"nblocks": 1184}, "n_gpus": 1,
+           "sweep": {"mutex_acq_per_s": {"cluster": {"64": {"148": 9e5, "1184": 8.9e5}}},
+                     "barrier_ns_per_crossing": {"count8": {"148": 1700.0, "1184": 2100.0}, "cluster8": {"144": 2500.0}},
+                     "semaphore_ops_per_s": {"window": {"4": {"296": 1.5e6}}}}}
+    rows = bench.result_rows(out)
+    m = [r for r in rows if r["section"] == "sweep_mutex"]
+    assert len(m) == 2 and {r["nblocks"] for r in m} == {148, 1184} and all(r["cs_words"] == 64 for r in m)
+    b = [r for r in rows if r["section"] == "sweep_barrier"]
+    assert len(b) == 3 and {(r["kind"], r["nblocks"]) for r in b} >= {("cluster8", 144), ("count8", 148)}
+    s = [r for r in rows if r["section"] == "sweep_semaphore"]
+    assert s == [dict(s[0], section="sweep_semaphore", kind="window", n=4, nblocks=296, ops_per_s=1.5e6)]
