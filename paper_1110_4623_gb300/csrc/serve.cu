@@ -409,14 +409,28 @@ void spin_until(Clock::time_point t) {
   }
 }
 
+// Counters shared by the host threads of a run, one per cache line: the collector updates
+// `completed` while the producer (or launcher) reads it and writes `published`, and a line
+// shared between writers on different cores would bounce on every update.
+struct alignas(128) HostCounter {
+  std::atomic<int> v{0};
+};
+struct alignas(128) HostFlag {
+  std::atomic<bool> v{false};
+};
+
 // Polls completion flags in order of arrival; records the host time each flag is first seen.
+// A pass scans from the oldest incomplete request to the last one published (or launched), at
+// most 4096 of them: only requests in flight can complete, so a pass stays as short as the
+// work in flight instead of walking a fixed window of flags.
 void collect(const gsync_serve_cfg* cfg, volatile uint32_t* done, Clock::time_point t0, const int64_t* sched,
-             int64_t* lat, std::atomic<int>* completed, std::atomic<bool>* abort_flag) {
+             int64_t* lat, std::atomic<int>* completed, std::atomic<bool>* abort_flag,
+             const std::atomic<int>* published) {
   const int n = cfg->nreq;
   std::vector<char> seen(n, 0);
-  int low = 0, count = 0;
+  int low = 0, count = 0, reported = 0;
   while (count < n && !abort_flag->load(std::memory_order_relaxed)) {
-    const int hi = std::min(n, low + 4096);
+    const int hi = std::min(std::min(n, low + 4096), published->load(std::memory_order_acquire));
     for (int q = low; q < hi; ++q) {
       if (seen[q]) continue;
       if (done[q]) {
@@ -427,7 +441,10 @@ void collect(const gsync_serve_cfg* cfg, volatile uint32_t* done, Clock::time_po
       }
     }
     while (low < n && seen[low]) ++low;
-    completed->store(count, std::memory_order_release);
+    if (count != reported) {  // stored only when it moves, so readers keep the line cached
+      completed->store(count, std::memory_order_release);
+      reported = count;
+    }
   }
 }
 
@@ -520,9 +537,13 @@ extern "C" int gsync_serve_run(const gsync_serve_cfg* cfg, gsync_serve_buffers* 
   // The loop is running (or about to): publish requests on their schedule, collect completions.
   std::this_thread::sleep_for(std::chrono::microseconds(cfg->start_delay_us));
   const Clock::time_point t0 = Clock::now();
-  std::atomic<int> completed{0};
-  std::atomic<bool> abort_flag{false};
-  std::thread collector(collect, cfg, buf->done, t0, buf->sched_ns, buf->latency_ns, &completed, &abort_flag);
+  HostCounter completed_c, published_c;
+  HostFlag abort_f;
+  std::atomic<int>& completed = completed_c.v;
+  std::atomic<int>& published = published_c.v;
+  std::atomic<bool>& abort_flag = abort_f.v;
+  std::thread collector(collect, cfg, buf->done, t0, buf->sched_ns, buf->latency_ns, &completed, &abort_flag,
+                        &published);
   pin_to_core_from_end(collector, 1);
   const auto deadline = Clock::now() + std::chrono::nanoseconds(buf->sched_ns[cfg->nreq - 1]) +
                         std::chrono::seconds(cfg->drain_timeout_s);
@@ -557,6 +578,7 @@ extern "C" int gsync_serve_run(const gsync_serve_cfg* cfg, gsync_serve_buffers* 
         gsync_serve_req* e = (gsync_serve_req*)((char*)buf->ring + (size_t)(i & (cfg->ring_slots - 1)) * kRingStride);
         __atomic_store_n(&e->seq, (uint32_t)(i + 1), __ATOMIC_RELAXED);
       }
+      published.store(qe, std::memory_order_release);
       if (buf->publish_ns) {
         const int64_t t = now_ns(t0);
         for (int i = q; i < qe; ++i) buf->publish_ns[i] = t;
@@ -618,9 +640,13 @@ extern "C" int gsync_serve_baseline(const gsync_serve_cfg* cfg, gsync_serve_buff
   if (int rc = host_dev_ptr(buf->res, &d_res)) return rc;
   if (int rc = host_dev_ptr((void*)buf->done, &d_done)) return rc;
   const Clock::time_point t0 = Clock::now();
-  std::atomic<int> completed{0};
-  std::atomic<bool> abort_flag{false};
-  std::thread collector(collect, cfg, buf->done, t0, buf->sched_ns, buf->latency_ns, &completed, &abort_flag);
+  HostCounter completed_c, published_c;
+  HostFlag abort_f;
+  std::atomic<int>& completed = completed_c.v;
+  std::atomic<int>& published = published_c.v;
+  std::atomic<bool>& abort_flag = abort_f.v;
+  std::thread collector(collect, cfg, buf->done, t0, buf->sched_ns, buf->latency_ns, &completed, &abort_flag,
+                        &published);
   pin_to_core_from_end(collector, 1);
   int dev = 0;
   GSYNC_CUDA(cudaGetDevice(&dev));
@@ -638,6 +664,10 @@ extern "C" int gsync_serve_baseline(const gsync_serve_cfg* cfg, gsync_serve_buff
       segsum_kernel<<<nb, kThreads, 0, (cudaStream_t)streams[q % nstreams]>>>(
           buf->pool, buf->offset[q], len, (uint32_t)cfg->chunk_elems, acc + q, counter + 2 * q, (uint32_t)q,
           (int64_t*)d_res, (uint32_t*)d_done);
+      // The collector's scan bound, 16 launches ahead, moved once every 16 launches: a store
+      // per launch would bounce the line between this core and the collector's, and this
+      // loop is what limits the arm at high rates.
+      if ((q & 15) == 0) published.store(std::min(cfg->nreq, q + 16), std::memory_order_release);
       if (buf->publish_ns) buf->publish_ns[q] = now_ns(t0);
       if (cudaGetLastError() != cudaSuccess) {
         launch_rc.store(GSYNC_ECUDA);
