@@ -1,5 +1,6 @@
 """Seeded repetitions of the GB300 designs across shapes and parameters (cohort and cluster
-cohort mutexes, counting barrier, ticket-window semaphore, condition variables, serving loop),
+cohort mutexes, counting barrier and the counting forms of the tree and cluster barriers,
+ticket-window semaphore, condition variables, serving loop),
 each checked exactly against the oracle: a net for races that one shape per test could miss."""
 import numpy as np
 import pytest
@@ -68,6 +69,25 @@ def test_counting_barrier_repeated(i):
     got = runner.BarrierRun("count", B, 128, 300, full=True, param=param, timeout_ns=10**10).run()
     want = calc.barrier_full(B, 300)
     assert got["status"] == 0 and not got["bad"].any()
+    assert np.array_equal(got["chk"], want["chk"]) and np.array_equal(got["mix"], want["mix"])
+
+
+@pytest.mark.parametrize("i", range(24))
+def test_counting_forms_of_tree_and_cluster_barriers_repeated(i):
+    # The tree's counting form (node counters that only grow) and the cluster barrier's
+    # counting forms (leaders on a growing counter; form 2 releases the cluster through a
+    # second cluster barrier), over grids, fan-ins, cluster sizes and sleeps, full fold.
+    from paper_1110_4623_gb300 import runner
+    if i % 2:
+        c = [1, 2, 4, 8][i // 2 % 4]
+        B = [8, 64, 296, 1184][i // 2 % 4 if c != 8 else 3] // c * c
+        kind, param = "cluster", c | (1 + (i // 2) % 2) << 4 | [0, 8, 64][i % 3] << 8
+    else:
+        B = [1, 3, 64, 150, 600, 1184][i // 2 % 6]
+        kind, param = "tree", [2, 3, 8, 32, 64, 1024][i // 2 % 6] | 1 << 16
+    got = runner.BarrierRun(kind, B, 128, 300, full=True, param=param, timeout_ns=10**10).run()
+    want = calc.barrier_full(B, 300)
+    assert got["status"] == 0 and not got["bad"].any(), (kind, hex(param), B)
     assert np.array_equal(got["chk"], want["chk"]) and np.array_equal(got["mix"], want["mix"])
 
 
