@@ -71,7 +71,7 @@ typedef enum gsync_mutex_kind {
 typedef enum gsync_barrier_kind {
   GSYNC_BAR_ATOMIC = 0,  /* two-stage atomic counter + release epoch */
   GSYNC_BAR_FLAG = 1,    /* decentralized flag barrier of Xiao and Feng (XF) */
-  GSYNC_BAR_TREE = 2,    /* combining tree of atomic counters, fan-in = param */
+  GSYNC_BAR_TREE = 2,    /* combining tree of atomic counters (param = fan | form << 16) */
   GSYNC_BAR_CLUSTER = 3, /* hardware cluster barrier, then one leader per cluster on a counter
                             (param = c | form << 4 | sleep << 8; see gsync_barrier_bytes) */
   GSYNC_BAR_SHARDED = 4, /* arrivals spread over param counters, gathered by one warp (XF-style release) */
@@ -155,7 +155,11 @@ int gsync_mutex_init_cluster(void* state, size_t bytes, int budget, const gsync_
  * use. */
 int gsync_device_topology(uint8_t* die_of_sm, int* ndies_out, void* stream);
 
-/* Bytes of a barrier for `nblocks` blocks.  param: fan-in (TREE, >= 2), c | form << 4 |
+/* Bytes of a barrier for `nblocks` blocks.  param: fan | form << 16 (TREE: fan-in 2..1024;
+ * form 0: the last arriver at a node resets it and climbs, and the root's last arriver
+ * advances a release epoch that every block polls; form 1: node counters that only grow, the
+ * arrival that completes a node's crossing climbs, and the root's completing add is the
+ * release that every block polls for), c | form << 4 |
  * sleep << 8 (CLUSTER: c the cluster size, 1..8, dividing nblocks; form 0: the cluster
  * leaders meet on an atomic barrier whose release epoch every block polls; form 1: the
  * leaders add to a growing counter, the last add is the release, and every block polls the
