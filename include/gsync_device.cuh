@@ -162,6 +162,18 @@ __device__ __forceinline__ void st_release_b128(void* p, uint64_t lo, uint64_t h
                ::"l"(lo), "l"(hi), "l"(p)
                : "memory");
 }
+// Relaxed forms: the same single 16-byte access, with no ordering of other accesses.
+__device__ __forceinline__ void ld_relaxed_b128(const void* p, uint64_t& lo, uint64_t& hi) {
+  asm volatile("{\n\t.reg .b128 t;\n\tld.relaxed.gpu.global.b128 t, [%2];\n\tmov.b128 {%0, %1}, t;\n\t}"
+               : "=l"(lo), "=l"(hi)
+               : "l"(p)
+               : "memory");
+}
+__device__ __forceinline__ void st_relaxed_b128(void* p, uint64_t lo, uint64_t hi) {
+  asm volatile("{\n\t.reg .b128 t;\n\tmov.b128 t, {%0, %1};\n\tst.relaxed.gpu.global.b128 [%2], t;\n\t}"
+               ::"l"(lo), "l"(hi), "l"(p)
+               : "memory");
+}
 __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;

@@ -176,6 +176,10 @@ class CarryTicketMutex:
     earlier tickets (mod 2^32 here), else a violation is reported.
     broken="split_read" reads the data first and the turn after, as two accesses (a stale
     read); broken="turn_only" publishes the turn without the data.
+    The device reads and writes the record with relaxed 16-byte accesses.  The protocol
+    communicates only through the ticket counter and this one record, each access to it is a
+    single access, and a holder's write depends on the value its read returned.  So coherence
+    on the record orders the hand-offs as the interleavings here do, and no fence is needed.
     """
     kind, capacity, fifo = "mutex", 1, True
 

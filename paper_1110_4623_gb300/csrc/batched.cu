@@ -65,12 +65,15 @@ __device__ __forceinline__ void unlock_by_policy(const gsync::MutexRef& m, const
 
 // GSYNC_BATCHED_TICKET_CARRY: the ticket lock (take a ticket, wait for the turn, sleeping in
 // proportion to the waiters ahead) whose turn line also holds what it guards.  Line 2 of the
-// key's object is one 16-byte record {turn, count, sum}: the waiter's acquire load of the
-// turn brings the count and sum with it, and the holder's release store of the next turn
-// writes the new count and sum in the same store.  A hand-off therefore carries the data:
-// the critical section makes no L2 round trip of its own, and the release waits for no
-// earlier store.  The key's count and sum stay in the record until batched_collect_kernel
-// copies them out after the launch.
+// key's object is one 16-byte record {turn, count, sum}: the waiter's load of the turn brings
+// the count and sum with it, and the holder's store of the next turn writes the new count and
+// sum in the same store.  A hand-off therefore carries the data: the critical section makes
+// no L2 round trip of its own.  Both accesses are relaxed.  Everything the lock guards is in
+// that one 16-byte location, and a .b128 access is a single access to it, so the value a
+// holder reads is exactly the record its predecessor wrote, and the value it writes depends
+// on what it read: coherence on the one location orders the hand-offs, and no fence (no wait
+// for earlier stores, no acquire) is needed on the hand-off path.  The key's count and sum
+// stay in the record until batched_collect_kernel copies them out after the launch.
 __device__ __forceinline__ int carry_add(uint32_t* obj, const uint32_t* pol, int64_t add, uint64_t timeout_ns) {
   uint32_t* ticket = obj + 1 * gsync::kLineWords;
   uint32_t* rec = obj + 2 * gsync::kLineWords;
@@ -78,7 +81,7 @@ __device__ __forceinline__ int carry_add(uint32_t* obj, const uint32_t* pol, int
   gsync::Waiter w;
   uint64_t lo, hi;
   for (;;) {
-    ptx::ld_acquire_b128(rec, lo, hi);
+    ptx::ld_relaxed_b128(rec, lo, hi);
     const uint32_t ahead = t - (uint32_t)lo;
     if (ahead == 0u) break;
     if (int rc = w.tick(timeout_ns, obj + gsync::kHdrAbort)) return rc;
@@ -89,7 +92,7 @@ __device__ __forceinline__ int carry_add(uint32_t* obj, const uint32_t* pol, int
   }
   // critical section: count + 1 and sum + add, published with the next turn
   const uint64_t next = (uint64_t)(t + 1u) | ((uint64_t)((uint32_t)(lo >> 32) + 1u) << 32);
-  ptx::st_release_b128(rec, next, (uint64_t)((int64_t)hi + add));
+  ptx::st_relaxed_b128(rec, next, (uint64_t)((int64_t)hi + add));
   return GSYNC_OK;
 }
 

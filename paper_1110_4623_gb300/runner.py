@@ -345,7 +345,29 @@ def near_handoff(iters: int = 4000) -> dict:
         page = int(np.flatnonzero(near < far)[0])
     r = probe_pingpong(sm_a, sm_b, iters, scratch=buf[page * 4096:])
     r["page"] = page
+    r["sms"] = (sm_a, sm_b)
     return r
+
+
+def near_handoff_relaxed(iters: int = 4000) -> dict:
+    """The same near-die hand-off with a relaxed store observed by relaxed polls: no fence on
+    either side, the floor of a hand-off that orders nothing but its own location (the
+    carrying locks' hand-off, whose guarded data travel in the flag's own access)."""
+    die, nd = device_topology()
+    buf = _state(64 << 10)
+    d0 = np.flatnonzero(die == 0)
+    sm_a, sm_b = int(d0[0]), int(d0[len(d0) // 2])
+    page = 0
+    if nd == 2:
+        near = probe_rtt_by_line(sm_a, buf, 16, 4096, 8)
+        far = probe_rtt_by_line(int(np.flatnonzero(die == 1)[0]), buf, 16, 4096, 8)
+        page = int(np.flatnonzero(near < far)[0])
+    out = torch.zeros(4, dtype=torch.int64, device="cuda")
+    G.check("gsync_probe_handoff", G.gsync_probe_handoff(G.SIGNAL_MODES["st_relaxed"], G.WAIT_MODES["ld_relaxed"],
+                                                         sm_a, sm_b, iters, buf[page * 4096:], out))
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    return {"handoff_ns": o[0] / (2 * iters), "status": int(o[3]), "page": page, "sms": (sm_a, sm_b)}
 
 
 def device_topology() -> tuple[np.ndarray, int]:
