@@ -32,6 +32,7 @@ CANDIDATES = [
     ("ticket", 64, 2000),
     ("ticket", 256, 4000),
     ("ticket_carry", 0, 0),
+    ("ticket_carry", 8, 2000),
     ("ticket_carry", 64, 2000),
 ]
 CLUSTERS = [1, 2, 4, 8]
