@@ -20,6 +20,7 @@ The algorithms follow Section 5 ("Design") and the pseudocode of the Appendix:
   QueueMutex    sleep-waiting queue lock: each waiter polls its own slot of a ring of flags
   RingMutex     the paper's ring-buffer sleeping mutex (Section 5, "design alternative")
   CohortMutex   two-die cohort lock: a ticket lock per die under a global ticket lock
+  CarryCohortMutex  the cohort lock whose records carry the guarded data (batched kernel)
   CondVarQueue  condition variables (ticket and signal counters) on a bounded buffer
   SpinSem       spin-lock semaphore with optional backoff ("Spin-Lock Semaphore")
   SleepSem      sleeping (FA) semaphore ("Sleeping Semaphore")
@@ -490,6 +491,88 @@ class CohortMutex:
             pc2, k2 = finish()
             word = self.OWNED if self.broken == "owned_on_release" else 0
             return (pc2, k2, t, c), put_local(nx, inc(t), word), None
+        raise AssertionError(pc)
+
+
+class CarryCohortMutex:
+    """The cohort lock (CohortMutex) whose records carry what it guards (the batched kernel's
+    GSYNC_BATCHED_COHORT_CARRY; a GB300 design, not in the paper).
+
+    Each group d has a local ticket counter next_d and a local record (served_d, word_d,
+    sum_d), and the global lock a ticket counter gnext and a global record (gturn, gsum); each
+    record is read and written as one access.  A holder takes the sum from the record that
+    granted it the lock: the local record when word_d is OWNED (the cohort inherits the global
+    lock), else the global record once gturn shows its global ticket.  It adds its own
+    contribution, then passes the sum on in the record it releases: the local record with
+    OWNED when a local waiter is queued and the budget allows, else the global record (then the
+    local record, not OWNED).  A ghost total, updated as each holder leaves, checks that every
+    holder enters with the sum of all earlier contributions.
+    broken="global_reads_local": a holder granted by the global lock takes the sum from its
+    local record; broken="pass_without_add": a local pass carries the sum the holder entered
+    with, without its own contribution.
+    """
+    kind, capacity, fifo = "mutex", 1, False
+    OWNED = 0x80000000
+
+    def __init__(self, budget=2, groups=2, broken=None):
+        self.budget, self.broken = budget, broken
+        self.base = 0
+        self.dies = groups
+
+    def init(self, nproc, ops):
+        # (next_d, served_d, word_d, sum_d) per group; (gnext, gturn, gsum); the ghost total
+        return (0, 0, 0, 0) * self.dies + (0, 0, 0) + (0,), tuple((0, 0, 0, 0, 0) for _ in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, t, c, s = loc
+        d = p % self.dies
+        nx, sv, wd, sd = sh[4 * d:4 * d + 4]
+        G = 4 * self.dies
+        gnext, gturn, gsum, truth = sh[G], sh[G + 1], sh[G + 2], sh[G + 3]
+        f = (p + 1 + 16 * k) & M32  # this acquisition's contribution
+
+        def put_local(rec):
+            return sh[:4 * d] + (nx,) + rec + sh[4 * d + 4:]
+
+        def finish():
+            k2 = k + 1
+            return (0 if k2 < ops else DONE), k2
+
+        if pc == 0:
+            return (1, k, nx, c, s), sh[:4 * d] + (inc(nx), sv, wd, sd) + sh[4 * d + 4:], None
+        if pc == 1:  # one read of the local record
+            if sv != t:
+                return loc, sh, None
+            if wd & self.OWNED:
+                return (PC_ENTER, k, t, wd & ~self.OWNED & M32, sd), sh, None
+            return (2, k, t, c, s), sh, None
+        if pc == 2:
+            return (3, k, t, gnext & 0xFFFF, s), sh[:G] + (inc(gnext), gturn, gsum, truth), None
+        if pc == 3:  # one read of the global record
+            if (gturn & 0xFFFF) != c:
+                return loc, sh, None
+            return (PC_ENTER, k, t, c, sd if self.broken == "global_reads_local" else gsum), sh, None
+        if pc == PC_ENTER:
+            if s != truth:
+                return loc, sh, ("violation", f"block {p} entered with sum {s}, expected {truth}")
+            return (PC_EXIT, k, t, c, s), sh, ("enter", (d, t))
+        if pc == PC_EXIT:
+            return (4, k, t, c, s), sh[:G + 3] + ((truth + f) & M32,), ("exit",)
+        if pc == 4:
+            passes = (c >> 16) & 0x7FFF
+            waiter = nx != inc(t)
+            return ((5 if waiter and passes + 1 < self.budget else 6), k, t, c, s), sh, None
+        if pc == 5:  # pass within the group: the local record carries the sum
+            passes, g = (c >> 16) & 0x7FFF, c & 0xFFFF
+            out = s if self.broken == "pass_without_add" else (s + f) & M32
+            pc2, k2 = finish()
+            return (pc2, k2, t, c, s), put_local((inc(t), self.OWNED | ((passes + 1) << 16) | g, out)), None
+        if pc == 6:  # release the global lock: the global record carries the sum
+            g = c & 0xFFFF
+            return (7, k, t, c, s), sh[:G + 1] + ((g + 1) & 0xFFFF, (s + f) & M32) + sh[G + 3:], None
+        if pc == 7:
+            pc2, k2 = finish()
+            return (pc2, k2, t, c, s), put_local((inc(t), 0, (s + f) & M32)), None
         raise AssertionError(pc)
 
 

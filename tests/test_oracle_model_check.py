@@ -30,6 +30,10 @@ CORRECT = [
     ("cohort_budget_3", mc.CohortMutex(budget=3), 3, 2),
     ("cohort_wrap", mc.CohortMutex(budget=2, base=W, gbase=0xFFFE), 3, 2),
     ("cohort_three_groups", mc.CohortMutex(budget=2, groups=3), 4, 2),
+    ("cohort_carry_budget_2", mc.CarryCohortMutex(budget=2), 3, 2),
+    ("cohort_carry_budget_1", mc.CarryCohortMutex(budget=1), 4, 1),
+    ("cohort_carry_budget_3", mc.CarryCohortMutex(budget=3), 3, 2),
+    ("cohort_carry_three_groups", mc.CarryCohortMutex(budget=2, groups=3), 4, 1),
     ("spin_sem_1", mc.SpinSem(n=1), 3, 2),
     ("spin_sem_2", mc.SpinSem(n=2), 3, 2),
     ("spin_sem_2_backoff", mc.SpinSem(n=2, backoff=True), 3, 2),
@@ -108,6 +112,10 @@ BROKEN = [
     ("cohort3_owned_on_release", mc.CohortMutex(broken="owned_on_release", groups=3), 3, 2, "critical section"),
     ("cohort3_pass_always", mc.CohortMutex(broken="pass_always", groups=3), 3, 2, "final state"),
     ("cohort3_skip_ticket", mc.CohortMutex(broken="skip_ticket", groups=3), 4, 2, "local ticket"),
+    # Carrying cohort lock: a holder granted by the global lock that takes the local record's
+    # sum, and a local pass that does not add the holder's own contribution.
+    ("cohort_carry_global_reads_local", mc.CarryCohortMutex(broken="global_reads_local"), 3, 2, "entered with"),
+    ("cohort_carry_pass_without_add", mc.CarryCohortMutex(broken="pass_without_add"), 3, 2, "entered with"),
     ("sleep_sem_turn_ge", mc.SleepSem(n=1, broken="turn_ge"), 3, 1, "critical section"),
     ("window_sem_ge", mc.WindowSem(n=2, broken="window_ge"), 3, 1, "critical section"),
     ("barrier_no_wait", mc.AtomicBarrier(broken="no_wait"), 3, 1, "passed round"),
