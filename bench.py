@@ -517,9 +517,10 @@ def e2e_mutex(G, inputs, kind, reps=3):
 def batched_section(G, calc, inputs, runner, autotune, terms):
     """Autotunes the batched many-mutex workload, then times its CUDA-graph replay.  Roofline:
     the hottest key's acquisitions are serial, each at least one L2 hand-off (the per-key locks
-    are L2 locks: the on-die hand-off bounds them).  The carrying ticket lock's hand-off is a
-    relaxed 16-byte store seen by relaxed polls, with no fence, so the strict roof charges the
-    fence-free near-die hand-off: acq/s <= nacq / (n_hot * L_handoff_relaxed_near).  Reported
+    are L2 locks: the on-die hand-off bounds them).  The carrying locks' hand-off is a relaxed
+    16-byte store seen by relaxed polls, with no fence, and the carrying cohort lock's passes
+    stay on one die, so the strict roof charges the fence-free near-die hand-off:
+    acq/s <= nacq / (n_hot * L_handoff_relaxed_near).  Reported
     beside it: the roof with a release/acquire hand-off (what a lock that orders other data
     pays), and with a dependent L2 load added (a lock whose critical section loads the key's
     sum and count)."""
@@ -535,8 +536,8 @@ def batched_section(G, calc, inputs, runner, autotune, terms):
            "autotune_s": tune_s, "trials": len(tuned["trials"]), "l2": "flushed (512 MiB write) before each timed run"}
     n_hot = int(np.bincount(np.asarray(keys, dtype=np.int64), minlength=BATCH_KEYS).max())
     # The hottest key's acquisitions form one serial chain of at least one L2 hand-off each (the
-    # carrying ticket lock moves the guarded data with a fence-free hand-off, so no load and no
-    # fence is added).  The looser bounds -- a release/acquire hand-off, and that plus one
+    # carrying locks move the guarded data with a fence-free hand-off, so no load and no fence
+    # is added).  The looser bounds -- a release/acquire hand-off, and that plus one
     # dependent load per acquisition (the critical section of the other kinds) -- are reported
     # beside it.
     roof = BATCH_ACQ / (n_hot * terms["L_handoff_relaxed_near_ns"] * 1e-9)

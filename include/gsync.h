@@ -413,17 +413,23 @@ int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_backoff* backof
  *    launch and whenever a key's policy kind changes (the objects are left consistent by
  *    every completed launch otherwise).
  *  - key_class (device, nkeys bytes): class of each key, < nclasses.
- *  - policy (device, nclasses x 4 x u32): {kind (CAS_SPIN, CAS_BACKOFF, TICKET, CLUSTER or
- *    GSYNC_BATCHED_TICKET_CARRY; others act as TICKET), min_ns, max_ns, budget}: backoff of the
- *    CAS kind, or sleep per waiter ahead of the ticket kinds; min_ns = 0 spins without
- *    sleeping.  CLUSTER (the cluster cohort lock) applies in a cluster launch (cluster > 1) to
+ *  - policy (device, nclasses x 4 x u32): {kind (CAS_SPIN, CAS_BACKOFF, TICKET, CLUSTER,
+ *    GSYNC_BATCHED_TICKET_CARRY or GSYNC_BATCHED_COHORT_CARRY; others act as TICKET), min_ns,
+ *    max_ns, budget}: backoff of the CAS kind, or sleep per waiter ahead of the ticket kinds;
+ *    min_ns = 0 spins without sleeping.  CLUSTER (the cluster cohort lock) applies in a cluster launch (cluster > 1) to
  *    keys below 256, whose local locks live in the blocks' shared memory, with `budget` passes
  *    per cohort (0 = the default, 64); elsewhere it acts as TICKET.  budget is ignored by the
  *    other kinds.  GSYNC_BATCHED_TICKET_CARRY is the ticket lock whose turn line carries the
- *    key's count and sum: one 16-byte record {turn, count, sum} read by the waiter's 128-bit
- *    acquire load and written by the holder's 128-bit release store, so a hand-off moves the
+ *    key's count and sum: one 16-byte record {turn, count, sum} read by the waiter's relaxed
+ *    128-bit load and written by the holder's relaxed 128-bit store, so a hand-off moves the
  *    guarded data with it; a second kernel on the same stream copies such keys' count and sum
  *    to count[] and sum[] after the launch and zeroes them in the record.
+ *    GSYNC_BATCHED_COHORT_CARRY is the two-die cohort lock with carrying records (a record
+ *    {served, cohort word, sum} per die on a page homed on that die, and a global record
+ *    {turn, -, sum}), `budget` passes inside a die per cohort (0 = the default, 64).  It
+ *    applies to keys below ncohort, whose objects are in cohort_state; other keys of such a
+ *    class use GSYNC_BATCHED_TICKET_CARRY.  The second kernel moves their count and sum out
+ *    and returns their counters and records to zero.
  *  - keys (device, nacq x i32), adds (device, nacq x i64); sum (device, nkeys x i64) and
  *    count (device, nkeys x u32) zeroed by the caller.
  *  - group_state (device, 128-byte aligned): ngroups x 512 bytes, zeroed before the first
@@ -433,11 +439,17 @@ int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_backoff* backof
  *    for the groups: every group must start at and span a multiple of `cluster` blocks
  *    (checked on the device; a violation sets GSYNC_STATUS_CONFIG and skips the barriers).
  *  - plain_launch = 1 uses an ordinary launch after the co-residency check instead of a
- *    cooperative one (for stream capture into a CUDA graph); cluster must then be 1. */
+ *    cooperative one (for stream capture into a CUDA graph); cluster must then be 1.
+ *  - cohort_state (device, 128-byte aligned; may be NULL when ncohort = 0): ncohort objects
+ *    of 32768 bytes, object k for key k, each initialised by gsync_mutex_init_cohort (its
+ *    budget is not used: the class policy's is) before the first launch and again whenever a
+ *    key's policy kind changes.  ncohort < 0, or > 0 with cohort_state NULL or unaligned,
+ *    returns GSYNC_EINVAL; values above nkeys act as nkeys. */
 #define GSYNC_BATCHED_TICKET_CARRY 16u
+#define GSYNC_BATCHED_COHORT_CARRY 17u
 typedef struct gsync_batched_work {
   int32_t nkeys, nacq, nblocks, block_threads, ngroups, rounds, cluster, nclasses;
-  int32_t plain_launch, reserved;
+  int32_t plain_launch, ncohort;
   uint64_t timeout_ns;
   void* mutex_state;
   const uint8_t* key_class;
@@ -454,6 +466,7 @@ typedef struct gsync_batched_work {
   uint32_t* mix;
   uint32_t* bad;
   uint32_t* status;
+  void* cohort_state;
 } gsync_batched_work;
 /* Launches the batched kernel and then batched_collect_kernel (two kernels, one stream). */
 int gsync_bench_batched(const gsync_batched_work* w, void* stream);

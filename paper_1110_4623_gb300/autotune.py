@@ -23,7 +23,9 @@ HOT, WARM, COLD = 0, 1, 2
 NCLASSES = 3
 
 # (kind, min_ns, max_ns): min_ns = 0 means spin without sleeping.  ticket_carry is the ticket
-# lock whose turn record carries the key's count and sum through each hand-off.
+# lock whose turn record carries the key's count and sum through each hand-off; cohort_carry
+# the two-die cohort lock with carrying records (the hottest keys only, the rest of the class
+# on ticket_carry).
 CANDIDATES = [
     ("cas_spin", 0, 0),
     ("cas_backoff", 32, 1024),
@@ -34,6 +36,7 @@ CANDIDATES = [
     ("ticket_carry", 0, 0),
     ("ticket_carry", 8, 2000),
     ("ticket_carry", 64, 2000),
+    ("cohort_carry", 0, 0),
 ]
 CLUSTERS = [1, 2, 4, 8]
 # Tried last, for the hot and warm classes, once a cluster size above 1 is chosen: the cluster
@@ -67,10 +70,10 @@ def _time(run: runner.BatchedRun, reps: int = 2) -> float:
 
 
 def make_run(keys, adds, nkeys, nblocks, ngroups, rounds, cluster, key_class, block_threads=128, seed=I.SEED_BATCHED,
-             plain_launch=False):
+             plain_launch=False, ncohort=128):
     _, sizes = I.barrier_group_sizes(ngroups, 2, 256, nblocks, seed=seed, multiple=cluster)
     return runner.BatchedRun(keys, adds, nkeys, nblocks, sizes, rounds, key_class, NCLASSES,
-                             block_threads=block_threads, cluster=cluster, plain_launch=plain_launch)
+                             block_threads=block_threads, cluster=cluster, plain_launch=plain_launch, ncohort=ncohort)
 
 
 def tune(keys, adds, nkeys: int, nblocks: int, ngroups: int, rounds: int, block_threads: int = 128,

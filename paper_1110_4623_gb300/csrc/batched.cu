@@ -9,9 +9,10 @@
 // that belong to a barrier group also cross `rounds` group barriers spread evenly over their
 // acquisitions, with the sampled slot check of the barrier workload (partner
 // p = (j + r + 1) mod size inside the group).  The autotuner chooses, per contention class,
-// the mutex kind (spin / spin + backoff / ticket, the carrying ticket lock, or -- in a cluster
-// launch -- the cluster cohort lock for keys below kLocalKeys), the backoff constants (0 = pure
-// spinning, otherwise __nanosleep) and the cluster size of the group barriers.
+// the mutex kind (spin / spin + backoff / ticket, the carrying ticket or two-die cohort lock,
+// or -- in a cluster launch -- the cluster cohort lock for keys below kLocalKeys), the backoff
+// constants (0 = pure spinning, otherwise __nanosleep) and the cluster size of the group
+// barriers.
 #include "common.cuh"
 
 using namespace gsync_impl;
@@ -44,9 +45,13 @@ struct Args {
   uint32_t* mix;
   uint32_t* bad;
   uint32_t* status;
+  uint32_t* cohort_state;
   uint64_t timeout_ns;
-  int32_t nkeys, nacq, rounds, nclasses, ngroups;
+  int32_t nkeys, nacq, rounds, nclasses, ngroups, ncohort;
 };
+
+// Per-key two-die cohort objects (gsync_mutex_init_cohort's layout and placement).
+constexpr uint32_t kCohortObjWords = 32u * 1024u / 4u;
 
 __device__ __forceinline__ gsync::Token lock_by_policy(const gsync::MutexRef& m) {
   switch (m.kind) {
@@ -96,14 +101,125 @@ __device__ __forceinline__ int carry_add(uint32_t* obj, const uint32_t* pol, int
   return GSYNC_OK;
 }
 
+// Word offset of die d's local lock in a cohort object, or 0 when the object was not set up
+// by gsync_mutex_init_cohort (then the key is refused instead of using stray lines).
+__device__ __forceinline__ uint32_t cohort_local_offset(const uint32_t* obj, uint32_t d) {
+  const uint32_t off = __ldg(obj + (d ? gsync::kHdrDieOff1 : gsync::kHdrDieOff0));
+  const bool ok = (__ldg(obj + gsync::kHdrMagic) & 0xFFu) == (uint32_t)GSYNC_MUTEX_COHORT &&
+                  off >= 5u * gsync::kLineWords && off + 2u * gsync::kLineWords <= kCohortObjWords;
+  return ok ? off : 0u;
+}
+
+// GSYNC_BATCHED_COHORT_CARRY: the two-die cohort lock (a ticket lock per die, on a 4 KB page
+// homed on that die, under a global ticket lock) with carrying records.  Each die's turn line
+// holds one 16-byte record {served ticket, cohort word, sum}, the global turn line one record
+// {turn, -, sum}.  The holder takes the sum from the record that granted it the lock: its
+// die's record when the cohort word says the die already holds the global lock, else the
+// global record once the global turn reaches its global ticket.  It passes sum + add on in the
+// record it releases: its die's record, with the global lock kept by the die, while a waiter of
+// its die is queued and fewer than `budget` passes were made in a row; else the global record
+// and then its die's record without the cohort bit.  A pass inside a die never leaves the die.
+// Each record is read and written as one relaxed 128-bit access and a holder's sum comes only
+// from the record that granted it the lock, so, as in carry_add, coherence on that one location
+// orders each hand-off and no fence is needed.  The die's ticket counter is read beside each
+// poll that may see the grant (the first, and those after one that found a single holder
+// ahead): the counter only grows, so a waiter seen in any read is still queued at the
+// release, and one not seen finds the global lock released and queues for it.  The last
+// acquisition has no waiter behind it and so releases the global lock: after the launch the
+// global record holds the key's sum, and the dies' ticket counters add up to its count.
+__device__ __forceinline__ int cohort_carry_add(uint32_t* obj, uint32_t die, const uint32_t* pol, int64_t add,
+                                                uint64_t timeout_ns) {
+  const uint32_t off = cohort_local_offset(obj, die);
+  if (off == 0u) return GSYNC_EINVAL;
+  uint32_t* local = obj + off;
+  uint32_t* lnext = local;
+  uint32_t* lrec = local + gsync::kLineWords;
+  uint32_t* gnext = obj + 1 * gsync::kLineWords;
+  uint32_t* grec = obj + 2 * gsync::kLineWords;
+  const uint32_t budget = pol[3] ? min(pol[3], 32767u) : (uint32_t)GSYNC_COHORT_DEFAULT_BUDGET;
+  const uint32_t t = ptx::atom_add_relaxed(lnext, 1u);
+  gsync::Waiter w;
+  uint64_t lo, hi;
+  uint32_t seen = t + 1u, prev_ahead = 1u;  // t + 1: no waiter known behind this ticket
+  for (;;) {
+    // Only a poll that may see the grant reads the counter beside it.
+    if (prev_ahead <= 1u) seen = ptx::ld_relaxed(lnext);
+    ptx::ld_relaxed_b128(lrec, lo, hi);
+    const uint32_t ahead = t - (uint32_t)lo;
+    if (ahead == 0u) break;
+    prev_ahead = ahead;
+    if (int rc = w.tick(timeout_ns, obj + gsync::kHdrAbort)) return rc;
+    if (pol[1] && ahead > 1u && ahead < 0x80000000u) {
+      const uint32_t ns = (ahead - 1u) * pol[1];
+      __nanosleep(ns < pol[2] ? ns : pol[2]);
+    }
+  }
+  uint32_t word = (uint32_t)(lo >> 32);
+  int64_t sum = (int64_t)hi;
+  if (word & gsync::kCohortOwned) {
+    word &= ~gsync::kCohortOwned;
+  } else {
+    // First of a cohort: queue for the global lock (at most one waiter per die).
+    const uint32_t g = ptx::atom_add_relaxed(gnext, 1u) & 0xFFFFu;
+    for (;;) {
+      seen = ptx::ld_relaxed(lnext);
+      ptx::ld_relaxed_b128(grec, lo, hi);
+      if (((uint32_t)lo & 0xFFFFu) == g) break;
+      if (int rc = w.tick(timeout_ns, obj + gsync::kHdrAbort)) return rc;
+      if (pol[1]) __nanosleep(pol[1]);
+    }
+    word = g;
+    sum = (int64_t)hi;
+  }
+  // critical section: sum + add, published with the hand-off
+  sum += add;
+  const uint32_t passes = (word >> 16) & 0x7FFFu, g = word & 0xFFFFu;
+  if (passes + 1u < budget && seen != t + 1u) {
+    const uint32_t w2 = gsync::kCohortOwned | ((passes + 1u) << 16) | g;
+    ptx::st_relaxed_b128(lrec, (uint64_t)(t + 1u) | ((uint64_t)w2 << 32), (uint64_t)sum);
+  } else {
+    ptx::st_relaxed_b128(grec, (uint64_t)((g + 1u) & 0xFFFFu), (uint64_t)sum);
+    ptx::st_relaxed_b128(lrec, (uint64_t)(t + 1u), (uint64_t)sum);
+  }
+  return GSYNC_OK;
+}
+
+__device__ __forceinline__ bool uses_cohort_carry(const Args& a, const uint32_t* pol, uint32_t key) {
+  return pol[0] == GSYNC_BATCHED_COHORT_CARRY && key < (uint32_t)a.ncohort;
+}
+
 // After the batched kernel: each carrying key's count and sum move from its record to count[]
 // and sum[], and the record's count and sum return to zero (its turn stays, matching the
-// ticket counter), so the next launch starts from zero like the other kinds' outputs.
+// ticket counter), so the next launch starts from zero like the other kinds' outputs.  A
+// cohort-carrying key's count is the sum of its dies' ticket counters and its sum is in the
+// global record; its counters, turns and records all return to zero.
 __global__ void batched_collect_kernel(Args a) {
   const uint32_t key = blockIdx.x * blockDim.x + threadIdx.x;
   if (key >= (uint32_t)a.nkeys) return;
   const uint32_t cls = a.key_class[key];
-  if (a.policy[4u * (cls < (uint32_t)a.nclasses ? cls : 0u)] != GSYNC_BATCHED_TICKET_CARRY) return;
+  const uint32_t* pol = a.policy + 4u * (cls < (uint32_t)a.nclasses ? cls : 0u);
+  if (uses_cohort_carry(a, pol, key)) {
+    uint32_t* obj = a.cohort_state + (size_t)key * kCohortObjWords;
+    const uint32_t off[2] = {cohort_local_offset(obj, 0u), cohort_local_offset(obj, 1u)};
+    if (off[0] == 0u || off[1] == 0u) return;  // refused by the batched kernel already
+    uint32_t n = 0;
+    for (uint32_t d = 0; d < 2u; ++d) {
+      uint32_t* local = obj + off[d];
+      n += local[0];
+      local[0] = 0u;
+      uint64_t* lrec = (uint64_t*)(local + gsync::kLineWords);
+      lrec[0] = 0;
+      lrec[1] = 0;
+    }
+    uint64_t* grec = (uint64_t*)(obj + 2 * gsync::kLineWords);
+    a.count[key] = n;
+    a.sum[key] = (int64_t)grec[1];
+    obj[1 * gsync::kLineWords] = 0u;
+    grec[0] = 0;
+    grec[1] = 0;
+    return;
+  }
+  if (pol[0] != GSYNC_BATCHED_TICKET_CARRY && pol[0] != GSYNC_BATCHED_COHORT_CARRY) return;
   uint64_t* rec = (uint64_t*)(a.mutex_state + key * kMutexObjWords + 2 * gsync::kLineWords);
   const uint64_t lo = rec[0];
   a.count[key] = (uint32_t)(lo >> 32);
@@ -144,6 +260,12 @@ __global__ void __launch_bounds__(kMaxThreads, 8) batched_kernel(Args a) {
         local_locks[i].turn = 0ull;
       }
     ptx::cluster_sync();
+  }
+  // The die of this block's SM, from the die table every cohort object carries.
+  uint32_t die = 0;
+  if (a.ncohort > 0 && tid == 0) {
+    const uint32_t sm = ptx::smid();
+    die = sm < gsync::kMaxSmIds && ((const uint8_t*)(a.cohort_state + gsync::kDieTableWord))[sm] ? 1u : 0u;
   }
   int g = a.group_of_block[b];
   if (g >= a.ngroups) g = -1;
@@ -196,8 +318,11 @@ __global__ void __launch_bounds__(kMaxThreads, 8) batched_kernel(Args a) {
       } else {
         const uint32_t cls = a.key_class[key];
         const uint32_t* pol = a.policy + 4u * (cls < (uint32_t)a.nclasses ? cls : 0u);
-        if (pol[0] == GSYNC_BATCHED_TICKET_CARRY) {
-          const int rc = carry_add(a.mutex_state + key * kMutexObjWords, pol, add, a.timeout_ns);
+        if (pol[0] == GSYNC_BATCHED_TICKET_CARRY || pol[0] == GSYNC_BATCHED_COHORT_CARRY) {
+          const int rc = uses_cohort_carry(a, pol, key)
+                             ? cohort_carry_add(a.cohort_state + (size_t)key * kCohortObjWords, die, pol, add,
+                                                a.timeout_ns)
+                             : carry_add(a.mutex_state + key * kMutexObjWords, pol, add, a.timeout_ns);
           if (rc != GSYNC_OK) {
             record_status(a.status, rc);
             s_fail = 1;
@@ -263,6 +388,8 @@ extern "C" int gsync_bench_batched(const gsync_batched_work* w, void* stream) {
   if (w->ngroups > 0 && (!w->group_start || !w->group_size || !w->group_state || !w->slots ||
                          !aligned(w->group_state, 128)))
     return GSYNC_EINVAL;
+  if (w->ncohort < 0 || (w->ncohort > 0 && (!w->cohort_state || !aligned(w->cohort_state, 128))))
+    return GSYNC_EINVAL;
   const int cluster = w->cluster < 1 ? 1 : w->cluster;
   if (cluster > 8 || w->nblocks % cluster) return GSYNC_EINVAL;
   Args a;
@@ -281,6 +408,8 @@ extern "C" int gsync_bench_batched(const gsync_batched_work* w, void* stream) {
   a.mix = w->mix;
   a.bad = w->bad;
   a.status = w->status;
+  a.cohort_state = (uint32_t*)w->cohort_state;
+  a.ncohort = w->ncohort < w->nkeys ? w->ncohort : w->nkeys;
   a.timeout_ns = w->timeout_ns ? w->timeout_ns : 2000000000ull;
   a.nkeys = w->nkeys;
   a.nacq = w->nacq;

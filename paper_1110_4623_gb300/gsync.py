@@ -20,9 +20,12 @@ GSYNC_STATUS_TIMEOUT, GSYNC_STATUS_ABORTED, GSYNC_STATUS_VIOLATION, GSYNC_STATUS
 
 MUTEX_KINDS = {"cas_spin": 0, "cas_backoff": 1, "ticket": 2, "sleep_queue": 3, "cohort": 4, "ring": 5, "cluster": 6}
 # Policy kinds of the batched kernel: the mutex kinds it runs, plus the ticket lock whose turn
-# line carries the guarded count and sum (GSYNC_BATCHED_TICKET_CARRY).
+# line carries the guarded count and sum (GSYNC_BATCHED_TICKET_CARRY) and the two-die cohort
+# lock with carrying records (GSYNC_BATCHED_COHORT_CARRY).
 BATCHED_TICKET_CARRY = 16
-BATCHED_POLICY_KINDS = {**MUTEX_KINDS, "ticket_carry": BATCHED_TICKET_CARRY}
+BATCHED_COHORT_CARRY = 17
+BATCHED_POLICY_KINDS = {**MUTEX_KINDS, "ticket_carry": BATCHED_TICKET_CARRY,
+                        "cohort_carry": BATCHED_COHORT_CARRY}
 COHORT_DEFAULT_BUDGET = 64
 BARRIER_KINDS = {"atomic": 0, "flag": 1, "tree": 2, "cluster": 3, "sharded": 4, "die": 5, "split": 6, "count": 7}
 SEM_KINDS = {"ticket": 0, "spin": 1, "spin_backoff": 2, "window": 3}
@@ -70,11 +73,11 @@ class gsync_batched_work(ctypes.Structure):
     _fields_ = [("nkeys", ctypes.c_int32), ("nacq", ctypes.c_int32), ("nblocks", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("ngroups", ctypes.c_int32), ("rounds", ctypes.c_int32),
                 ("cluster", ctypes.c_int32), ("nclasses", ctypes.c_int32), ("plain_launch", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("timeout_ns", ctypes.c_uint64),
+                ("ncohort", ctypes.c_int32), ("timeout_ns", ctypes.c_uint64),
                 ("mutex_state", u32p), ("key_class", u32p), ("policy", u32p), ("keys", u32p), ("adds", u32p),
                 ("sum", u32p), ("count", u32p), ("group_start", u32p), ("group_size", u32p),
                 ("group_of_block", u32p), ("group_state", u32p), ("slots", u32p), ("mix", u32p), ("bad", u32p),
-                ("status", u32p)]
+                ("status", u32p), ("cohort_state", u32p)]
 
 
 class gsync_serve_req(ctypes.Structure):

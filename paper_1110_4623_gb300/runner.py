@@ -458,13 +458,18 @@ def sm_count() -> int:
     return n
 
 
+COHORT_OBJ_BYTES = 32 * 1024  # one two-die cohort object (gsync_mutex_bytes of COHORT)
+
+
 class BatchedRun:
     """The batched many-mutex workload (gsync_bench_batched): 4096 mutexes with Zipf keys,
     barrier groups, a per-class policy table; optional capture into a CUDA graph."""
 
     def __init__(self, keys: np.ndarray, adds: np.ndarray, nkeys: int, nblocks: int, group_sizes: np.ndarray,
                  rounds: int, key_class: np.ndarray, nclasses: int, block_threads: int = 128, cluster: int = 1,
-                 timeout_ns: int = 10_000_000_000, plain_launch: bool = False):
+                 timeout_ns: int = 10_000_000_000, plain_launch: bool = False, ncohort: int = 128):
+        """ncohort: how many of the lowest keys (the hottest, for Zipf keys) get a two-die cohort
+        object for the cohort_carry policy kind (32 KB each)."""
         from .inputs import group_layout
         self.nkeys, self.nacq, self.nblocks = nkeys, len(keys), nblocks
         self.group_sizes = np.asarray(group_sizes, dtype=np.int32)
@@ -487,17 +492,21 @@ class BatchedRun:
         self.mix = _zeros(nblocks)
         self.bad = _zeros(nblocks)
         self.status = _zeros(1)
+        self.ncohort = max(0, min(int(ncohort), nkeys))
+        self.cohort_state = torch.zeros(max(self.ncohort, 1) * COHORT_OBJ_BYTES, dtype=torch.uint8, device="cuda")
         self.work = G.gsync_batched_work(nkeys, self.nacq, nblocks, block_threads, ng, rounds, cluster, nclasses,
-                                         int(plain_launch), 0, timeout_ns, G.ptr(self.mutex_state),
+                                         int(plain_launch), self.ncohort, timeout_ns, G.ptr(self.mutex_state),
                                          G.ptr(self.key_class), G.ptr(self.policy), G.ptr(self.keys),
                                          G.ptr(self.adds), G.ptr(self.sum), G.ptr(self.count), G.ptr(self.gstart),
                                          G.ptr(self.gsize), G.ptr(self.gob), G.ptr(self.group_state),
-                                         G.ptr(self.slots), G.ptr(self.mix), G.ptr(self.bad), G.ptr(self.status))
+                                         G.ptr(self.slots), G.ptr(self.mix), G.ptr(self.bad), G.ptr(self.status),
+                                         G.ptr(self.cohort_state))
         self.graph = None
 
     def set_policy(self, table):
-        """table: list of (kind, min_ns, max_ns[, budget]) per class (budget: the cluster cohort
-        lock's passes per cohort, 0 = default).  Zeroes the mutexes (kinds may change)."""
+        """table: list of (kind, min_ns, max_ns[, budget]) per class (budget: the cohort locks'
+        passes per cohort, 0 = default).  Zeroes the mutexes (kinds may change) and, when a
+        class uses cohort_carry, places and initialises the cohort objects."""
         flat = []
         for entry in table:
             kind, mn, mx = entry[:3]
@@ -505,6 +514,11 @@ class BatchedRun:
             flat += [G.BATCHED_POLICY_KINDS[kind] if isinstance(kind, str) else int(kind), int(mn), int(mx), int(budget)]
         self.policy.copy_(torch.tensor(flat, dtype=torch.int32))
         self.mutex_state.zero_()
+        if G.BATCHED_COHORT_CARRY in flat[0::4]:
+            base = G.ptr(self.cohort_state)
+            for k in range(self.ncohort):
+                G.check("gsync_mutex_init_cohort",
+                        G.gsync_mutex_init_cohort(base + k * COHORT_OBJ_BYTES, COHORT_OBJ_BYTES, 1))
         self.graph = None
 
     def reset(self):

@@ -18,11 +18,12 @@ def _gpu():
     require_gpu()
 
 
-def make(nacq, cluster=1, rounds=100, policy=None, plain_launch=False):
+def make(nacq, cluster=1, rounds=100, policy=None, plain_launch=False, ncohort=64):
     from paper_1110_4623_gb300 import autotune
     keys, adds, _ = inputs.batched_inputs(nacq, NKEYS, 1.1)
     cls = autotune.classify_keys(keys, NKEYS, NB)
-    run = autotune.make_run(keys, adds, NKEYS, NB, 64, rounds, cluster, cls, plain_launch=plain_launch)
+    run = autotune.make_run(keys, adds, NKEYS, NB, 64, rounds, cluster, cls, plain_launch=plain_launch,
+                            ncohort=ncohort)
     run.set_policy(policy or autotune.DEFAULT_POLICY)
     return run, keys, adds
 
@@ -87,6 +88,43 @@ def test_ticket_carry_policy(cluster, policy):
         got = run.run()
         assert got["rc"] == 0
         check(run, keys, adds, got, 29)
+
+
+@pytest.mark.parametrize("cluster,policy,nacq,ncohort", [
+    (1, [("cohort_carry", 0, 0)] * 3, 1_000_000, 64),
+    (8, [("cohort_carry", 0, 0), ("cohort_carry", 8, 2000), ("ticket_carry", 0, 0)], 1_000_000, 64),
+    (1, [("cohort_carry", 0, 0, 1), ("cohort_carry", 64, 2000, 3), ("cas_spin", 0, 0)], 200_000, 64),
+    (4, [("cohort_carry", 0, 0, 32767), ("cluster", 128, 4000), ("ticket", 64, 2000)], 200_000, 64),
+    (1, [("cohort_carry", 0, 0)] * 3, 200_000, 1),
+    (2, [("cohort_carry", 0, 0)] * 3, 200_000, 0)])
+def test_cohort_carry_policy(cluster, policy, nacq, ncohort):
+    # The two-die cohort lock with carrying records on the hottest keys (keys below ncohort;
+    # the rest of such a class use the carrying ticket lock): budgets 1 (every holder releases
+    # the global lock), 3, the default and the maximum; beside the other kinds; one cohort
+    # object, and none.  Twice in a row on the same objects: the collect pass returns every
+    # counter and record to zero.
+    run, keys, adds = make(nacq, cluster=cluster, policy=policy, rounds=31, ncohort=ncohort)
+    for _ in range(2):
+        got = run.run()
+        assert got["rc"] == 0
+        check(run, keys, adds, got, 31)
+
+
+def test_cohort_carry_graph_replay_and_policy_change():
+    # Captured with clusters of 8 (the tuned launch's shape) and replayed; then the hot class
+    # moves to the carrying ticket lock and back, which re-initialises the cohort objects.
+    import torch
+    pol = [("cohort_carry", 0, 0), ("cohort_carry", 8, 2000), ("ticket_carry", 0, 0)]
+    run, keys, adds = make(300_000, rounds=20, cluster=8, policy=pol)
+    run.capture()
+    for _ in range(3):
+        run.replay()
+        torch.cuda.synchronize()
+        check(run, keys, adds, run.results(), 20)
+    run.set_policy([("ticket_carry", 0, 0)] * 3)
+    check(run, keys, adds, run.run(), 20)
+    run.set_policy(pol)
+    check(run, keys, adds, run.run(), 20)
 
 
 def test_ticket_carry_policy_change_and_graph_replay():
@@ -160,3 +198,16 @@ def test_misaligned_cluster_groups_are_refused_on_device():
     assert got["rc"] == 0 and got["status"] & G.GSYNC_STATUS_CONFIG
     want = calc.batched_final(keys, adds, NKEYS)
     assert np.array_equal(got["sum"], want["sum"])  # the lock work still completes
+
+
+def test_cohort_objects_argument_checks():
+    # A negative cohort count, or cohort objects asked for without a (128-byte aligned) buffer,
+    # is refused before anything launches.
+    from paper_1110_4623_gb300 import gsync as G
+    run, _, _ = make(10_000, rounds=2)
+    base = G.ptr(run.cohort_state)
+    for n, ptr in ((-1, base), (4, None), (4, base + 64)):
+        w = G.gsync_batched_work.from_buffer_copy(run.work)
+        w.ncohort, w.cohort_state = n, ptr
+        assert G.gsync_bench_batched(w) == G.GSYNC_EINVAL, (n, ptr)
+    assert run.run()["rc"] == 0
