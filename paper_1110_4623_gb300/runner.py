@@ -330,44 +330,54 @@ def probe_cluster(op: int, cluster: int, iters: int = 2000) -> dict:
     return {"ns": per, "status": int(o[3])}
 
 
-def near_handoff(iters: int = 4000) -> dict:
-    """The shortest SM-to-SM hand-off on this GPU: a ping-pong between two SMs of one die on
-    flag lines homed on that die (found with the topology probes).  On a one-die GPU, any pair."""
-    die, nd = device_topology()
-    buf = _state(64 << 10)
+def _near_pair() -> tuple[int, int]:
+    """Two SMs of die 0 (any two SMs on a one-die GPU)."""
+    die, _ = device_topology()
     d0 = np.flatnonzero(die == 0)
-    sm_a, sm_b = int(d0[0]), int(d0[len(d0) // 2])
-    page = 0
-    if nd == 2:
-        # first 4 KB page homed on die 0: nearer to an SM of die 0 than to one of die 1
-        near = probe_rtt_by_line(sm_a, buf, 16, 4096, 8)
-        far = probe_rtt_by_line(int(np.flatnonzero(die == 1)[0]), buf, 16, 4096, 8)
-        page = int(np.flatnonzero(near < far)[0])
-    r = probe_pingpong(sm_a, sm_b, iters, scratch=buf[page * 4096:])
-    r["page"] = page
+    return int(d0[0]), int(d0[len(d0) // 2])
+
+
+def _fastest_page(measure, pages: int) -> dict:
+    """The fastest of `measure(flag_lines)` over `pages` consecutive 4 KB pages of one buffer
+    (line homes alternate between the dies by page, so some page is homed on the pair's own
+    die); the result dict gets its page."""
+    buf = _state((pages + 1) * 4096)
+    best = None
+    for page in range(pages):
+        r = measure(buf[page * 4096:])
+        r["page"] = page
+        if r["status"] == 0 and (best is None or r["handoff_ns"] < best["handoff_ns"]):
+            best = r
+    return best if best is not None else r
+
+
+def near_handoff(iters: int = 4000, pages: int = 8) -> dict:
+    """The shortest SM-to-SM hand-off on this GPU: a release/acquire ping-pong between two SMs
+    of one die, at the fastest of `pages` page placements of the flag lines (the placement
+    homed on that die)."""
+    sm_a, sm_b = _near_pair()
+    r = _fastest_page(lambda lines: probe_pingpong(sm_a, sm_b, iters, scratch=lines), pages)
     r["sms"] = (sm_a, sm_b)
     return r
 
 
-def near_handoff_relaxed(iters: int = 4000) -> dict:
+def near_handoff_relaxed(iters: int = 4000, pages: int = 8) -> dict:
     """The same near-die hand-off with a relaxed store observed by relaxed polls: no fence on
     either side, the floor of a hand-off that orders nothing but its own location (the
     carrying locks' hand-off, whose guarded data travel in the flag's own access)."""
-    die, nd = device_topology()
-    buf = _state(64 << 10)
-    d0 = np.flatnonzero(die == 0)
-    sm_a, sm_b = int(d0[0]), int(d0[len(d0) // 2])
-    page = 0
-    if nd == 2:
-        near = probe_rtt_by_line(sm_a, buf, 16, 4096, 8)
-        far = probe_rtt_by_line(int(np.flatnonzero(die == 1)[0]), buf, 16, 4096, 8)
-        page = int(np.flatnonzero(near < far)[0])
-    out = torch.zeros(4, dtype=torch.int64, device="cuda")
-    G.check("gsync_probe_handoff", G.gsync_probe_handoff(G.SIGNAL_MODES["st_relaxed"], G.WAIT_MODES["ld_relaxed"],
-                                                         sm_a, sm_b, iters, buf[page * 4096:], out))
-    torch.cuda.synchronize()
-    o = out.cpu().numpy()
-    return {"handoff_ns": o[0] / (2 * iters), "status": int(o[3]), "page": page, "sms": (sm_a, sm_b)}
+    sm_a, sm_b = _near_pair()
+
+    def measure(lines):
+        out = torch.zeros(4, dtype=torch.int64, device="cuda")
+        G.check("gsync_probe_handoff", G.gsync_probe_handoff(G.SIGNAL_MODES["st_relaxed"], G.WAIT_MODES["ld_relaxed"],
+                                                             sm_a, sm_b, iters, lines, out))
+        torch.cuda.synchronize()
+        o = out.cpu().numpy()
+        return {"handoff_ns": o[0] / (2 * iters), "status": int(o[3])}
+
+    r = _fastest_page(measure, pages)
+    r["sms"] = (sm_a, sm_b)
+    return r
 
 
 def device_topology() -> tuple[np.ndarray, int]:
