@@ -414,8 +414,8 @@ int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_backoff* backof
  *    every completed launch otherwise).
  *  - key_class (device, nkeys bytes): class of each key, < nclasses.
  *  - policy (device, nclasses x 4 x u32): {kind (CAS_SPIN, CAS_BACKOFF, TICKET, CLUSTER,
- *    GSYNC_BATCHED_TICKET_CARRY or GSYNC_BATCHED_COHORT_CARRY; others act as TICKET), min_ns,
- *    max_ns, budget}: backoff of the CAS kind, or sleep per waiter ahead of the ticket kinds;
+ *    GSYNC_BATCHED_TICKET_CARRY, GSYNC_BATCHED_COHORT_CARRY or GSYNC_BATCHED_CLUSTER_CARRY;
+ *    others act as TICKET), min_ns, max_ns, budget}: backoff of the CAS kind, or sleep per waiter ahead of the ticket kinds;
  *    min_ns = 0 spins without sleeping.  CLUSTER (the cluster cohort lock) applies in a cluster launch (cluster > 1) to
  *    keys below 256, whose local locks live in the blocks' shared memory, with `budget` passes
  *    per cohort (0 = the default, 64); elsewhere it acts as TICKET.  budget is ignored by the
@@ -429,7 +429,13 @@ int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_backoff* backof
  *    {turn, -, sum}), `budget` passes inside a die per cohort (0 = the default, 64).  It
  *    applies to keys below ncohort, whose objects are in cohort_state; other keys of such a
  *    class use GSYNC_BATCHED_TICKET_CARRY.  The second kernel moves their count and sum out
- *    and returns their counters and records to zero.
+ *    and returns their counters and records to zero.  GSYNC_BATCHED_CLUSTER_CARRY is the
+ *    same carrying cohort protocol with the thread-block cluster as the group: in a cluster
+ *    launch (cluster > 1), keys below 256 keep the cluster's ticket counter and record in
+ *    the shared memory of the cluster's block 0 and pass the lock inside the cluster through
+ *    distributed shared memory; the key's own object holds the global ticket and record.  The
+ *    launch adds each cluster's count to count[] as it ends, and the second kernel moves the
+ *    sum out.  Elsewhere it acts as GSYNC_BATCHED_TICKET_CARRY.
  *  - keys (device, nacq x i32), adds (device, nacq x i64); sum (device, nkeys x i64) and
  *    count (device, nkeys x u32) zeroed by the caller.
  *  - group_state (device, 128-byte aligned): ngroups x 512 bytes, zeroed before the first
@@ -447,6 +453,7 @@ int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_backoff* backof
  *    returns GSYNC_EINVAL; values above nkeys act as nkeys. */
 #define GSYNC_BATCHED_TICKET_CARRY 16u
 #define GSYNC_BATCHED_COHORT_CARRY 17u
+#define GSYNC_BATCHED_CLUSTER_CARRY 18u
 typedef struct gsync_batched_work {
   int32_t nkeys, nacq, nblocks, block_threads, ngroups, rounds, cluster, nclasses;
   int32_t plain_launch, ncohort;
@@ -645,7 +652,9 @@ int gsync_probe_handoff(int signal_mode, int wait_mode, int sm_a, int sm_b, int 
  * op 0: every thread runs `iters` hardware cluster barriers (out[0] / iters per barrier);
  * op 1: ranks 0 and cluster-1 ping-pong a flag in each other's shared memory with
  *       st.release.cluster / ld.acquire.cluster; op 2: the same with remote mbarrier arrives
- *       and mbarrier.try_wait (hand-off = out[0] / (2 * iters)).  out (device, 4 x u64):
+ *       and mbarrier.try_wait; op 3: as op 1 with a 16-byte record written and polled with
+ *       relaxed 128-bit accesses, no fence (hand-off = out[0] / (2 * iters) for ops 1-3).
+ *       cluster < 2 with op > 0, or op outside 0..3, returns GSYNC_EINVAL.  out (device, 4 x u64):
  *       out[0] elapsed ns, out[3] status (0 ok, 1 timed out after 1 s). */
 int gsync_probe_cluster(int op, int cluster, int iters, uint64_t* out, void* stream);
 

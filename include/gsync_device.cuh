@@ -222,6 +222,19 @@ __device__ __forceinline__ uint64_t ld_acquire_cluster_u64(const uint64_t* p) {
 __device__ __forceinline__ void st_release_cluster_u64(uint64_t* p, uint64_t v) {
   asm volatile("st.release.cluster.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+// One 16-byte record in the shared memory of a cluster block, read or written as one relaxed
+// 128-bit access at cluster scope (generic address from mapa).
+__device__ __forceinline__ void ld_relaxed_cluster_b128(const void* p, uint64_t& lo, uint64_t& hi) {
+  asm volatile("{\n\t.reg .b128 t;\n\tld.relaxed.cluster.b128 t, [%2];\n\tmov.b128 {%0, %1}, t;\n\t}"
+               : "=l"(lo), "=l"(hi)
+               : "l"(p)
+               : "memory");
+}
+__device__ __forceinline__ void st_relaxed_cluster_b128(void* p, uint64_t lo, uint64_t hi) {
+  asm volatile("{\n\t.reg .b128 t;\n\tmov.b128 t, {%0, %1};\n\tst.relaxed.cluster.b128 [%2], t;\n\t}"
+               ::"l"(lo), "l"(hi), "l"(p)
+               : "memory");
+}
 // Hardware barrier over every thread of every block of the cluster.  The non-.aligned
 // forms let threads of a warp arrive from divergent paths.
 __device__ __forceinline__ void cluster_sync() {

@@ -25,9 +25,17 @@ constexpr int kMaxThreads = 256;
 // barrier a header line, two arrival counters (by epoch parity) and the release epoch.
 constexpr uint32_t kMutexObjWords = 3 * gsync::kLineWords;
 constexpr uint32_t kBarObjWords = 4 * gsync::kLineWords;
-// Keys below this may use the cluster cohort lock: their local locks live in a table in each
-// block's shared memory (16 bytes a key); the per-key object's lines 1-2 are the global lock.
+// Keys below this may use the cluster locks (the cluster cohort lock and its carrying form):
+// their local locks live in a table in the shared memory of each cluster's block 0 (32 bytes a
+// key); the per-key object's lines 1-2 are the global lock.
 constexpr uint32_t kLocalKeys = 256;
+
+// A key's local lock in a cluster launch: the cluster cohort lock's {ticket, turn}, and for
+// the carrying form the same ticket counter with a 16-byte record {served, cohort word, sum}.
+struct __align__(16) LocalSlot {
+  gsync::ClusterLocal cl;
+  uint64_t rec[2];
+};
 
 struct Args {
   uint32_t* mutex_state;
@@ -47,7 +55,7 @@ struct Args {
   uint32_t* status;
   uint32_t* cohort_state;
   uint64_t timeout_ns;
-  int32_t nkeys, nacq, rounds, nclasses, ngroups, ncohort;
+  int32_t nkeys, nacq, rounds, nclasses, ngroups, ncohort, clustered;
 };
 
 // Per-key two-die cohort objects (gsync_mutex_init_cohort's layout and placement).
@@ -188,6 +196,72 @@ __device__ __forceinline__ bool uses_cohort_carry(const Args& a, const uint32_t*
   return pol[0] == GSYNC_BATCHED_COHORT_CARRY && key < (uint32_t)a.ncohort;
 }
 
+// GSYNC_BATCHED_CLUSTER_CARRY: the cohort protocol of cohort_carry_add with the thread-block
+// cluster as the group.  The group's ticket counter and record are the key's LocalSlot in the
+// shared memory of the cluster's block 0, reached through distributed shared memory with
+// relaxed cluster-scope accesses (a 128-bit record access is one access there too); the global
+// ticket and record are lines 1 and 2 of the key's object, as in cohort_carry_add.  A pass
+// inside the cluster never touches L2.  The local counters die with the launch, so the
+// kernel's end adds each cluster's count of the key's acquisitions to count[].
+__device__ __forceinline__ int cluster_carry_add(LocalSlot* slot, uint32_t* obj, const uint32_t* pol, int64_t add,
+                                                 uint64_t timeout_ns) {
+  uint32_t* lnext = &slot->cl.next;
+  uint64_t* lrec = slot->rec;
+  uint32_t* gnext = obj + 1 * gsync::kLineWords;
+  uint32_t* grec = obj + 2 * gsync::kLineWords;
+  const uint32_t budget = pol[3] ? min(pol[3], 32767u) : (uint32_t)GSYNC_COHORT_DEFAULT_BUDGET;
+  const uint32_t t = ptx::atom_add_relaxed_cluster(lnext, 1u);
+  gsync::Waiter w;
+  uint64_t lo, hi;
+  uint32_t seen = t + 1u, prev_ahead = 1u;  // t + 1: no waiter known behind this ticket
+  for (;;) {
+    if (prev_ahead <= 1u) seen = ptx::ld_relaxed_cluster(lnext);
+    ptx::ld_relaxed_cluster_b128(lrec, lo, hi);
+    const uint32_t ahead = t - (uint32_t)lo;
+    if (ahead == 0u) break;
+    prev_ahead = ahead;
+    if (int rc = w.tick(timeout_ns, obj + gsync::kHdrAbort)) return rc;
+    if (pol[1] && ahead > 1u && ahead < 0x80000000u) {
+      const uint32_t ns = (ahead - 1u) * pol[1];
+      __nanosleep(ns < pol[2] ? ns : pol[2]);
+    }
+  }
+  uint32_t word = (uint32_t)(lo >> 32);
+  int64_t sum = (int64_t)hi;
+  if (word & gsync::kCohortOwned) {
+    word &= ~gsync::kCohortOwned;
+  } else {
+    // First of a cohort: queue for the global lock (at most one waiter per cluster).
+    const uint32_t g = ptx::atom_add_relaxed(gnext, 1u) & 0xFFFFu;
+    for (;;) {
+      seen = ptx::ld_relaxed_cluster(lnext);
+      ptx::ld_relaxed_b128(grec, lo, hi);
+      if (((uint32_t)lo & 0xFFFFu) == g) break;
+      if (int rc = w.tick(timeout_ns, obj + gsync::kHdrAbort)) return rc;
+      if (pol[1]) __nanosleep(pol[1]);
+    }
+    word = g;
+    sum = (int64_t)hi;
+  }
+  // critical section: sum + add, published with the hand-off
+  sum += add;
+  const uint32_t passes = (word >> 16) & 0x7FFFu, g = word & 0xFFFFu;
+  if (passes + 1u < budget && seen != t + 1u) {
+    const uint32_t w2 = gsync::kCohortOwned | ((passes + 1u) << 16) | g;
+    ptx::st_relaxed_cluster_b128(lrec, (uint64_t)(t + 1u) | ((uint64_t)w2 << 32), (uint64_t)sum);
+  } else {
+    ptx::st_relaxed_b128(grec, (uint64_t)((g + 1u) & 0xFFFFu), (uint64_t)sum);
+    ptx::st_relaxed_cluster_b128(lrec, (uint64_t)(t + 1u), (uint64_t)sum);
+  }
+  return GSYNC_OK;
+}
+
+// Whether a key runs the cluster carrying lock in this launch (cluster launch, key below
+// kLocalKeys); such a key's other launches' kinds and the collect pass must agree on it.
+__device__ __forceinline__ bool uses_cluster_carry(const Args& a, const uint32_t* pol, uint32_t key) {
+  return pol[0] == GSYNC_BATCHED_CLUSTER_CARRY && a.clustered && key < kLocalKeys;
+}
+
 // After the batched kernel: each carrying key's count and sum move from its record to count[]
 // and sum[], and the record's count and sum return to zero (its turn stays, matching the
 // ticket counter), so the next launch starts from zero like the other kinds' outputs.  A
@@ -219,7 +293,19 @@ __global__ void batched_collect_kernel(Args a) {
     grec[1] = 0;
     return;
   }
-  if (pol[0] != GSYNC_BATCHED_TICKET_CARRY && pol[0] != GSYNC_BATCHED_COHORT_CARRY) return;
+  if (uses_cluster_carry(a, pol, key)) {
+    // count[] already holds the clusters' counts; the global record holds the sum
+    uint32_t* obj = a.mutex_state + key * kMutexObjWords;
+    uint64_t* grec = (uint64_t*)(obj + 2 * gsync::kLineWords);
+    a.sum[key] = (int64_t)grec[1];
+    obj[1 * gsync::kLineWords] = 0u;
+    grec[0] = 0;
+    grec[1] = 0;
+    return;
+  }
+  if (pol[0] != GSYNC_BATCHED_TICKET_CARRY && pol[0] != GSYNC_BATCHED_COHORT_CARRY &&
+      pol[0] != GSYNC_BATCHED_CLUSTER_CARRY)
+    return;
   uint64_t* rec = (uint64_t*)(a.mutex_state + key * kMutexObjWords + 2 * gsync::kLineWords);
   const uint64_t lo = rec[0];
   a.count[key] = (uint32_t)(lo >> 32);
@@ -244,20 +330,25 @@ __device__ __forceinline__ int group_cross(gsync::BarrierRef& bar, uint32_t* gsl
   return rc;
 }
 
-template <int BKIND>
-__global__ void __launch_bounds__(kMaxThreads, 8) batched_kernel(Args a) {
+// MAXT: the largest block the instantiation runs.  Eight blocks per SM leave 32 registers a
+// thread at 256 threads and 64 at 128; the 128-thread instantiation keeps thread 0's lock
+// paths out of local memory (no spills).
+template <int BKIND, int MAXT>
+__global__ void __launch_bounds__(MAXT, 8) batched_kernel(Args a) {
   const uint32_t G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   __shared__ int s_fail;
   if (tid == 0) s_fail = 0;
   // The cluster cohort lock's local locks (one per key below kLocalKeys; block 0 of each
   // cluster holds the ones in use).  Initialised before any block of the cluster can use them,
   // and kept alive by the cluster barrier at the end of the kernel.
-  __shared__ gsync::ClusterLocal local_locks[BKIND == GSYNC_BAR_CLUSTER ? kLocalKeys : 1];
+  __shared__ LocalSlot local_locks[BKIND == GSYNC_BAR_CLUSTER ? kLocalKeys : 1];
   if (BKIND == GSYNC_BAR_CLUSTER) {
     if (ptx::cluster_ctarank() == 0)
       for (uint32_t i = tid; i < kLocalKeys; i += blockDim.x) {
-        local_locks[i].next = 0u;
-        local_locks[i].turn = 0ull;
+        local_locks[i].cl.next = 0u;
+        local_locks[i].cl.turn = 0ull;
+        local_locks[i].rec[0] = 0ull;
+        local_locks[i].rec[1] = 0ull;
       }
     ptx::cluster_sync();
   }
@@ -318,11 +409,16 @@ __global__ void __launch_bounds__(kMaxThreads, 8) batched_kernel(Args a) {
       } else {
         const uint32_t cls = a.key_class[key];
         const uint32_t* pol = a.policy + 4u * (cls < (uint32_t)a.nclasses ? cls : 0u);
-        if (pol[0] == GSYNC_BATCHED_TICKET_CARRY || pol[0] == GSYNC_BATCHED_COHORT_CARRY) {
-          const int rc = uses_cohort_carry(a, pol, key)
-                             ? cohort_carry_add(a.cohort_state + (size_t)key * kCohortObjWords, die, pol, add,
-                                                a.timeout_ns)
-                             : carry_add(a.mutex_state + key * kMutexObjWords, pol, add, a.timeout_ns);
+        if (pol[0] == GSYNC_BATCHED_TICKET_CARRY || pol[0] == GSYNC_BATCHED_COHORT_CARRY ||
+            pol[0] == GSYNC_BATCHED_CLUSTER_CARRY) {
+          int rc;
+          if (BKIND == GSYNC_BAR_CLUSTER && uses_cluster_carry(a, pol, key))
+            rc = cluster_carry_add(ptx::map_cluster_rank(&local_locks[key], 0u), a.mutex_state + key * kMutexObjWords,
+                                   pol, add, a.timeout_ns);
+          else if (uses_cohort_carry(a, pol, key))
+            rc = cohort_carry_add(a.cohort_state + (size_t)key * kCohortObjWords, die, pol, add, a.timeout_ns);
+          else
+            rc = carry_add(a.mutex_state + key * kMutexObjWords, pol, add, a.timeout_ns);
           if (rc != GSYNC_OK) {
             record_status(a.status, rc);
             s_fail = 1;
@@ -335,7 +431,7 @@ __global__ void __launch_bounds__(kMaxThreads, 8) batched_kernel(Args a) {
                         : pol[0] <= (uint32_t)GSYNC_MUTEX_TICKET ? pol[0] : (uint32_t)GSYNC_MUTEX_TICKET;
         // cohort budget (fourth policy word, 0 = the default), kept as budget - 1
         m.qmask = cohort ? (pol[3] ? min(pol[3], 32767u) : (uint32_t)GSYNC_COHORT_DEFAULT_BUDGET) - 1u : 0u;
-        m.cl = cohort ? ptx::map_cluster_rank(&local_locks[key], 0u) : nullptr;
+        m.cl = cohort ? ptx::map_cluster_rank(&local_locks[key].cl, 0u) : nullptr;
         m.local = nullptr;
         m.die = 0;
         m.bo.policy = GSYNC_BACKOFF_EXPONENTIAL;
@@ -373,7 +469,34 @@ __global__ void __launch_bounds__(kMaxThreads, 8) batched_kernel(Args a) {
     a.mix[b] = mix;
     a.bad[b] = bad;
   }
-  if (BKIND == GSYNC_BAR_CLUSTER) ptx::cluster_sync();  // block 0's local locks outlive every user
+  if (BKIND == GSYNC_BAR_CLUSTER) {
+    ptx::cluster_sync();  // block 0's local locks outlive every user
+    // The cluster carrying lock's acquisitions of each key, counted by its local ticket.
+    if (ptx::cluster_ctarank() == 0)
+      for (uint32_t key = tid; key < kLocalKeys && key < (uint32_t)a.nkeys; key += blockDim.x) {
+        const uint32_t cls = a.key_class[key];
+        const uint32_t* pol = a.policy + 4u * (cls < (uint32_t)a.nclasses ? cls : 0u);
+        const uint32_t n = local_locks[key].cl.next;
+        if (n && uses_cluster_carry(a, pol, key)) ptx::red_add_relaxed(a.count + key, n);
+      }
+  }
+}
+
+template <int MAXT>
+int launch_batched(const gsync_batched_work* w, int cluster, const Args& a, cudaStream_t st) {
+  if (cluster > 1)
+    return launch_coresident(batched_kernel<GSYNC_BAR_CLUSTER, MAXT>, w->nblocks, w->block_threads, cluster, 0, st, a);
+  if (w->plain_launch) {
+    // For stream capture: an ordinary launch after the same co-residency check.  All blocks
+    // are resident as long as no other kernel occupies the GPU when the graph runs.
+    int maxb = 0;
+    if (int rc = max_coresident(batched_kernel<GSYNC_BAR_ATOMIC, MAXT>, w->block_threads, 1, 0, &maxb)) return rc;
+    if (w->nblocks > maxb) return GSYNC_ENOTRESIDENT;
+    batched_kernel<GSYNC_BAR_ATOMIC, MAXT><<<w->nblocks, w->block_threads, 0, st>>>(a);
+    GSYNC_CUDA(cudaGetLastError());
+    return GSYNC_OK;
+  }
+  return launch_coresident(batched_kernel<GSYNC_BAR_ATOMIC, MAXT>, w->nblocks, w->block_threads, 1, 0, st, a);
 }
 
 }  // namespace
@@ -410,6 +533,7 @@ extern "C" int gsync_bench_batched(const gsync_batched_work* w, void* stream) {
   a.status = w->status;
   a.cohort_state = (uint32_t*)w->cohort_state;
   a.ncohort = w->ncohort < w->nkeys ? w->ncohort : w->nkeys;
+  a.clustered = w->cluster > 1 ? 1 : 0;
   a.timeout_ns = w->timeout_ns ? w->timeout_ns : 2000000000ull;
   a.nkeys = w->nkeys;
   a.nacq = w->nacq;
@@ -417,20 +541,8 @@ extern "C" int gsync_bench_batched(const gsync_batched_work* w, void* stream) {
   a.nclasses = w->nclasses;
   a.ngroups = w->ngroups;
   cudaStream_t st = (cudaStream_t)stream;
-  int rc = GSYNC_OK;
-  if (cluster > 1) {
-    rc = launch_coresident(batched_kernel<GSYNC_BAR_CLUSTER>, w->nblocks, w->block_threads, cluster, 0, st, a);
-  } else if (w->plain_launch) {
-    // For stream capture: an ordinary launch after the same co-residency check.  All blocks
-    // are resident as long as no other kernel occupies the GPU when the graph runs.
-    int maxb = 0;
-    if ((rc = max_coresident(batched_kernel<GSYNC_BAR_ATOMIC>, w->block_threads, 1, 0, &maxb))) return rc;
-    if (w->nblocks > maxb) return GSYNC_ENOTRESIDENT;
-    batched_kernel<GSYNC_BAR_ATOMIC><<<w->nblocks, w->block_threads, 0, st>>>(a);
-    GSYNC_CUDA(cudaGetLastError());
-  } else {
-    rc = launch_coresident(batched_kernel<GSYNC_BAR_ATOMIC>, w->nblocks, w->block_threads, 1, 0, st, a);
-  }
+  const int rc = w->block_threads <= 128 ? launch_batched<128>(w, cluster, a, st)
+                                          : launch_batched<kMaxThreads>(w, cluster, a, st);
   if (rc != GSYNC_OK) return rc;
   batched_collect_kernel<<<(w->nkeys + 255) / 256, 256, 0, st>>>(a);
   GSYNC_CUDA(cudaGetLastError());

@@ -114,6 +114,21 @@ __device__ __forceinline__ uint32_t ld_cluster_acquire(uint32_t addr) {
   return v;
 }
 
+// One 16-byte record in a cluster block's shared memory, read and written as one relaxed
+// 128-bit access (the record of a lock whose hand-off carries its data).
+__device__ __forceinline__ void st_cluster_relaxed_b128(uint32_t addr, uint64_t lo, uint64_t hi) {
+  asm volatile("{\n\t.reg .b128 t;\n\tmov.b128 t, {%1, %2};\n\tst.relaxed.cluster.shared::cluster.b128 [%0], t;\n\t}"
+               ::"r"(addr), "l"(lo), "l"(hi) : "memory");
+}
+
+__device__ __forceinline__ uint64_t ld_cluster_relaxed_b128_lo(uint32_t addr) {
+  uint64_t lo, hi;
+  asm volatile("{\n\t.reg .b128 t;\n\tld.relaxed.cluster.shared::cluster.b128 t, [%2];\n\tmov.b128 {%0, %1}, t;\n\t}"
+               : "=l"(lo), "=l"(hi) : "r"(addr) : "memory");
+  (void)hi;
+  return lo;
+}
+
 __device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
 }
@@ -137,15 +152,19 @@ __device__ __forceinline__ bool mbar_try_wait_parity(uint32_t addr, uint32_t par
 // op 0: every thread of every block runs `iters` hardware cluster barriers.
 // op 1: ranks 0 and c-1 ping-pong a flag in each other's shared memory (release/acquire).
 // op 2: ranks 0 and c-1 ping-pong remote mbarrier arrivals (hardware wait).
+// op 3: as op 1 with a 16-byte record in each other's shared memory, written and polled with
+//       relaxed 128-bit accesses (no fence on either side).
 // out[0] = elapsed ns of the loop on rank 0 (per op: out[0] / iters; per hand-off for
-// ops 1 and 2: out[0] / (2 * iters)); out[3] = status.
+// ops 1-3: out[0] / (2 * iters)); out[3] = status.
 __global__ void probe_cluster_kernel(int op, int iters, uint64_t* out) {
   __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(16) uint64_t rec[2];
   __shared__ uint32_t flag;
   const uint32_t rank = ptx::cluster_ctarank(), n = ptx::cluster_nctarank();
   const uint32_t peer = rank == 0 ? n - 1 : 0;
   if (threadIdx.x == 0) {
     flag = 0;
+    rec[0] = rec[1] = 0;
     mbar_init(smem_addr(&mbar), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -159,15 +178,20 @@ __global__ void probe_cluster_kernel(int op, int iters, uint64_t* out) {
     const uint64_t deadline = t0 + kDeadlineNs;
     const uint32_t my_flag = smem_addr(&flag), peer_flag = map_rank(my_flag, peer);
     const uint32_t my_mbar = smem_addr(&mbar), peer_mbar = map_rank(my_mbar, peer);
+    const uint32_t my_rec = smem_addr(rec), peer_rec = map_rank(my_rec, peer);
     for (int i = 1; i <= iters && status == 0; ++i) {
       const bool serve = rank == 0;
       if (serve) {
         if (op == 1) st_cluster_release(peer_flag, (uint32_t)i);
+        else if (op == 3) st_cluster_relaxed_b128(peer_rec, (uint64_t)i, (uint64_t)i);
         else mbar_remote_arrive(peer_mbar);
       }
       uint32_t polls = 0;
       if (op == 1) {
         while (ld_cluster_acquire(my_flag) != (uint32_t)i)
+          if ((++polls & 63u) == 0 && ptx::globaltimer() > deadline) { status = 1; break; }
+      } else if (op == 3) {
+        while (ld_cluster_relaxed_b128_lo(my_rec) != (uint64_t)i)
           if ((++polls & 63u) == 0 && ptx::globaltimer() > deadline) { status = 1; break; }
       } else {
         while (!mbar_try_wait_parity(my_mbar, (uint32_t)((i - 1) & 1)))
@@ -175,6 +199,7 @@ __global__ void probe_cluster_kernel(int op, int iters, uint64_t* out) {
       }
       if (!serve && status == 0) {
         if (op == 1) st_cluster_release(peer_flag, (uint32_t)i);
+        else if (op == 3) st_cluster_relaxed_b128(peer_rec, (uint64_t)i, (uint64_t)i);
         else mbar_remote_arrive(peer_mbar);
       }
     }
@@ -232,7 +257,7 @@ extern "C" int gsync_probe_handoff(int signal_mode, int wait_mode, int sm_a, int
 }
 
 extern "C" int gsync_probe_cluster(int op, int cluster, int iters, uint64_t* out, void* stream) {
-  if (op < 0 || op > 2 || cluster < 1 || cluster > 8 || iters < 1 || !out || (op > 0 && cluster < 2))
+  if (op < 0 || op > 3 || cluster < 1 || cluster > 8 || iters < 1 || !out || (op > 0 && cluster < 2))
     return GSYNC_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   GSYNC_CUDA(cudaMemsetAsync(out, 0, 4 * sizeof(uint64_t), st));

@@ -18,12 +18,12 @@ def _gpu():
     require_gpu()
 
 
-def make(nacq, cluster=1, rounds=100, policy=None, plain_launch=False, ncohort=64):
+def make(nacq, cluster=1, rounds=100, policy=None, plain_launch=False, ncohort=64, block_threads=128):
     from paper_1110_4623_gb300 import autotune
     keys, adds, _ = inputs.batched_inputs(nacq, NKEYS, 1.1)
     cls = autotune.classify_keys(keys, NKEYS, NB)
-    run = autotune.make_run(keys, adds, NKEYS, NB, 64, rounds, cluster, cls, plain_launch=plain_launch,
-                            ncohort=ncohort)
+    run = autotune.make_run(keys, adds, NKEYS, NB, 64, rounds, cluster, cls, block_threads=block_threads,
+                            plain_launch=plain_launch, ncohort=ncohort)
     run.set_policy(policy or autotune.DEFAULT_POLICY)
     return run, keys, adds
 
@@ -108,6 +108,45 @@ def test_cohort_carry_policy(cluster, policy, nacq, ncohort):
         got = run.run()
         assert got["rc"] == 0
         check(run, keys, adds, got, 31)
+
+
+@pytest.mark.parametrize("cluster,policy,nacq", [
+    (8, [("cluster_carry", 0, 0), ("cluster_carry", 8, 2000), ("ticket_carry", 0, 0)], 1_000_000),
+    (2, [("cluster_carry", 0, 0, 1), ("cohort_carry", 0, 0), ("cas_spin", 0, 0)], 200_000),
+    (4, [("cluster_carry", 64, 2000, 3), ("cluster", 128, 4000), ("cluster_carry", 0, 0, 32767)], 200_000),
+    (1, [("cluster_carry", 0, 0)] * 3, 200_000)])  # no clusters: the carrying ticket lock
+def test_cluster_carry_policy(cluster, policy, nacq):
+    # The carrying cohort lock over thread-block clusters for keys below 256 (its local ticket
+    # and record in block 0's shared memory; the rest fall back to the carrying ticket lock):
+    # budgets 1, 3, the default and the maximum, beside the other kinds, twice in a row.
+    run, keys, adds = make(nacq, cluster=cluster, policy=policy, rounds=27)
+    for _ in range(2):
+        got = run.run()
+        assert got["rc"] == 0
+        check(run, keys, adds, got, 27)
+
+
+@pytest.mark.parametrize("threads", [32, 160, 256])
+@pytest.mark.parametrize("cluster", [1, 8])
+def test_block_sizes(threads, cluster):
+    # Blocks of up to 128 threads run the instantiation with 64 registers a thread, larger
+    # ones the one with 32; both, with every carrying kind and the plain kinds beside them.
+    pol = [("cluster_carry", 0, 0), ("cohort_carry", 8, 2000), ("ticket", 64, 2000)]
+    run, keys, adds = make(200_000, cluster=cluster, policy=pol, rounds=19, block_threads=threads)
+    got = run.run()
+    assert got["rc"] == 0
+    check(run, keys, adds, got, 19)
+
+
+def test_cluster_carry_graph_replay():
+    import torch
+    run, keys, adds = make(300_000, rounds=20, cluster=8,
+                           policy=[("cluster_carry", 0, 0), ("ticket", 0, 0), ("cohort_carry", 0, 0)])
+    run.capture()
+    for _ in range(3):
+        run.replay()
+        torch.cuda.synchronize()
+        check(run, keys, adds, run.results(), 20)
 
 
 def test_cohort_carry_graph_replay_and_policy_change():

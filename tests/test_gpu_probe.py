@@ -66,3 +66,18 @@ def test_cs_probe():
     a = runner.probe_cs(0, 256, 5000)["ns_per_cs"]
     b = runner.probe_cs(1024, 256, 5000)["ns_per_cs"]
     assert 0 < a and 0 < b
+
+
+@pytest.mark.parametrize("cluster", [2, 8])
+def test_cluster_handoff_probes(cluster):
+    # The hardware cluster barrier and the three hand-offs through distributed shared memory
+    # (release/acquire flag, remote mbarrier arrive, relaxed 128-bit record) run and report
+    # sane times; malformed requests are refused.
+    from paper_1110_4623_gb300 import gsync as G, runner
+    import torch
+    for op in (0, 1, 2, 3):
+        r = runner.probe_cluster(op, cluster, 1000)
+        assert r["status"] == 0 and 10 < r["ns"] < 20_000, (op, r)
+    out = torch.zeros(4, dtype=torch.int64, device="cuda")
+    assert G.gsync_probe_cluster(4, cluster, 10, out) == G.GSYNC_EINVAL
+    assert G.gsync_probe_cluster(3, 1, 10, out) == G.GSYNC_EINVAL
