@@ -21,6 +21,7 @@ The algorithms follow Section 5 ("Design") and the pseudocode of the Appendix:
   RingMutex     the paper's ring-buffer sleeping mutex (Section 5, "design alternative")
   CohortMutex   two-die cohort lock: a ticket lock per die under a global ticket lock
   CarryCohortMutex  the cohort lock whose records carry the guarded data (batched kernel)
+  CarryHierMutex    the same over three levels: cluster, die and global (batched kernel)
   CondVarQueue  condition variables (ticket and signal counters) on a bounded buffer
   SpinSem       spin-lock semaphore with optional backoff ("Spin-Lock Semaphore")
   SleepSem      sleeping (FA) semaphore ("Sleeping Semaphore")
@@ -573,6 +574,117 @@ class CarryCohortMutex:
         if pc == 7:
             pc2, k2 = finish()
             return (pc2, k2, t, c, s), put_local((inc(t), 0, (s + f) & M32)), None
+        raise AssertionError(pc)
+
+
+class CarryHierMutex:
+    """Three-level carrying cohort lock (the batched kernel's GSYNC_BATCHED_CLUSTER_DIE_CARRY;
+    a GB300 design, not in the paper): a ticket lock per cluster, under a ticket lock per die,
+    under a global ticket lock, every level with a record that carries the guarded sum.
+
+    Block p belongs to cluster cluster_of[p], cluster c to die die_of[c].  Records: a
+    cluster's (served, word, sum), whose word, when owned, carries the die ticket, the global
+    ticket and the pass counts of the cohorts above; a die's (served, word, sum), whose word,
+    when owned, carries the global ticket and the die's pass count; the global (turn, sum).
+    Served tickets and the global turn are compared in 16 bits, as on the device.  A holder
+    takes the sum from the record that granted it the lock.  It releases to the next waiter of
+    its cluster (record owned, the die and global locks kept) while one is queued and the
+    cluster budget allows; else to the next waiter of its die (the die record owned, the global
+    lock kept), then releases its cluster; else it releases the global lock, then its die, then
+    its cluster.  A ghost total checks that every holder enters with the sum of all earlier
+    contributions.
+    broken="die_pass_keeps_cluster": a die pass leaves the cluster record owned, so the
+    cluster's next waiter also enters; broken="die_grant_reads_cluster": a holder granted at
+    the die level takes the sum from its cluster record; broken="global_skips_die": a global
+    release leaves the die lock held.
+    """
+    kind, capacity, fifo = "mutex", 1, False
+    M16 = 0xFFFF
+
+    def __init__(self, cluster_of=(0, 0, 1), die_of=(0, 0), cbudget=2, dbudget=2, base=0, broken=None):
+        self.cluster_of, self.die_of = tuple(cluster_of), tuple(die_of)
+        self.cbudget, self.dbudget, self.base, self.broken = cbudget, dbudget, base, broken
+        self.nc, self.nd = len(self.die_of), max(self.die_of) + 1
+
+    def init(self, nproc, ops):
+        b = self.base
+        cl = (b, b & self.M16, None, 0) * self.nc
+        dl = (b, b & self.M16, None, 0) * self.nd
+        return cl + dl + (b, b & self.M16, 0) + (0,), tuple((0, 0, 0, 0, 0, 0, 0, 0) for _ in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, tc, td, cp, dp, g, s = loc
+        c = self.cluster_of[p]
+        d = self.die_of[c]
+        C0, D0 = 4 * c, 4 * self.nc + 4 * d
+        G = 4 * self.nc + 4 * self.nd
+        cnext, cserved, cword, csum = sh[C0:C0 + 4]
+        dnext, dserved, dword, dsum = sh[D0:D0 + 4]
+        gnext, gturn, gsum, truth = sh[G:G + 4]
+        f = (p + 1 + 16 * k) & M32
+        out = (s + f) & M32
+
+        def put(i, rec):
+            return sh[:i] + rec + sh[i + len(rec):]
+
+        def finish():
+            k2 = k + 1
+            return (0 if k2 < ops else DONE), k2
+
+        if pc == 0:  # cluster ticket
+            return (1, k, cnext, td, cp, dp, g, s), put(C0, (inc(cnext),)), None
+        if pc == 1:  # one read of the cluster record
+            if cserved != tc & self.M16:
+                return loc, sh, None
+            if cword is not None:  # the cluster holds the die lock
+                _, cp2, dp2, td2, g2 = cword
+                return (PC_ENTER, k, tc, td2, cp2, dp2, g2, csum), sh, None
+            return (2, k, tc, td, 0, dp, g, s), sh, None
+        if pc == 2:  # die ticket
+            return (3, k, tc, dnext, cp, dp, g, s), put(D0, (inc(dnext),)), None
+        if pc == 3:  # one read of the die record
+            if dserved != td & self.M16:
+                return loc, sh, None
+            if dword is not None:  # the die holds the global lock
+                _, dp2, g2 = dword
+                s2 = csum if self.broken == "die_grant_reads_cluster" else dsum
+                return (PC_ENTER, k, tc, td, 0, dp2, g2, s2), sh, None
+            return (4, k, tc, td, 0, 0, g, s), sh, None
+        if pc == 4:  # global ticket
+            return (5, k, tc, td, cp, dp, gnext & self.M16, s), put(G, (inc(gnext),)), None
+        if pc == 5:  # one read of the global record
+            if gturn != g:
+                return loc, sh, None
+            return (PC_ENTER, k, tc, td, 0, 0, g, gsum), sh, None
+        if pc == PC_ENTER:
+            if s != truth:
+                return loc, sh, ("violation", f"block {p} entered with sum {s}, expected {truth}")
+            return (PC_EXIT, k, tc, td, cp, dp, g, s), sh, ("enter", (c, tc))
+        if pc == PC_EXIT:
+            return (6, k, tc, td, cp, dp, g, s), put(G + 3, ((truth + f) & M32,)), ("exit",)
+        if pc == 6:  # a waiter of this cluster?
+            waiter = cnext != inc(tc)
+            return ((7 if waiter and cp + 1 < self.cbudget else 8), k, tc, td, cp, dp, g, s), sh, None
+        if pc == 7:  # pass within the cluster: the die and global locks stay
+            pc2, k2 = finish()
+            rec = (inc(tc) & self.M16, ("own", cp + 1, dp, td, g), out)
+            return (pc2, k2, tc, td, cp, dp, g, s), put(C0 + 1, rec), None
+        if pc == 8:  # a waiter of this die?
+            waiter = dnext != inc(td)
+            return ((9 if waiter and dp + 1 < self.dbudget else 10), k, tc, td, cp, dp, g, s), sh, None
+        if pc == 9:  # pass within the die: the global lock stays
+            return (11, k, tc, td, cp, dp, g, s), put(D0 + 1, (inc(td) & self.M16, ("own", dp + 1, g), out)), None
+        if pc == 10:  # release the global lock
+            nxt = 11 if self.broken == "global_skips_die" else 12
+            return (nxt, k, tc, td, cp, dp, g, s), put(G + 1, ((g + 1) & self.M16, out)), None
+        if pc == 12:
+            return (11, k, tc, td, cp, dp, g, s), put(D0 + 1, (inc(td) & self.M16, None, out)), None
+        if pc == 11:  # release the cluster
+            pc2, k2 = finish()
+            word = cword if self.broken == "die_pass_keeps_cluster" and cword is not None else None
+            if self.broken == "die_pass_keeps_cluster" and word is None:
+                word = ("own", cp + 1, dp, td, g)
+            return (pc2, k2, tc, td, cp, dp, g, s), put(C0 + 1, (inc(tc) & self.M16, word, out)), None
         raise AssertionError(pc)
 
 
