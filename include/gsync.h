@@ -414,8 +414,8 @@ int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_backoff* backof
  *    every completed launch otherwise).
  *  - key_class (device, nkeys bytes): class of each key, < nclasses.
  *  - policy (device, nclasses x 4 x u32): {kind (CAS_SPIN, CAS_BACKOFF, TICKET, CLUSTER,
- *    GSYNC_BATCHED_TICKET_CARRY, GSYNC_BATCHED_COHORT_CARRY or GSYNC_BATCHED_CLUSTER_CARRY;
- *    others act as TICKET), min_ns, max_ns, budget}: backoff of the CAS kind, or sleep per waiter ahead of the ticket kinds;
+ *    GSYNC_BATCHED_TICKET_CARRY, GSYNC_BATCHED_COHORT_CARRY, GSYNC_BATCHED_CLUSTER_CARRY or
+ *    GSYNC_BATCHED_CLUSTER_DIE_CARRY; others act as TICKET), min_ns, max_ns, budget}: backoff of the CAS kind, or sleep per waiter ahead of the ticket kinds;
  *    min_ns = 0 spins without sleeping.  CLUSTER (the cluster cohort lock) applies in a cluster launch (cluster > 1) to
  *    keys below 256, whose local locks live in the blocks' shared memory, with `budget` passes
  *    per cohort (0 = the default, 64); elsewhere it acts as TICKET.  budget is ignored by the
@@ -436,6 +436,13 @@ int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_backoff* backof
  *    distributed shared memory; the key's own object holds the global ticket and record.  The
  *    launch adds each cluster's count to count[] as it ends, and the second kernel moves the
  *    sum out.  Elsewhere it acts as GSYNC_BATCHED_TICKET_CARRY.
+ *    GSYNC_BATCHED_CLUSTER_DIE_CARRY nests the two: cluster cohorts under die cohorts (on
+ *    the die's page of the key's cohort object) under the global lock (the cohort object's
+ *    lines 1-2), for keys below 256 and below ncohort in a cluster launch.  Its cluster level
+ *    is an MCS queue whose holder pushes the record into its successor's shared memory.
+ *    `budget` bounds the passes at both levels (at most 127 in a cluster, 255 on a die).
+ *    The launch adds each block's count to count[] as it ends.  Elsewhere it acts as
+ *    GSYNC_BATCHED_TICKET_CARRY.
  *  - keys (device, nacq x i32), adds (device, nacq x i64); sum (device, nkeys x i64) and
  *    count (device, nkeys x u32) zeroed by the caller.
  *  - group_state (device, 128-byte aligned): ngroups x 512 bytes, zeroed before the first
@@ -454,6 +461,7 @@ int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_backoff* backof
 #define GSYNC_BATCHED_TICKET_CARRY 16u
 #define GSYNC_BATCHED_COHORT_CARRY 17u
 #define GSYNC_BATCHED_CLUSTER_CARRY 18u
+#define GSYNC_BATCHED_CLUSTER_DIE_CARRY 19u
 typedef struct gsync_batched_work {
   int32_t nkeys, nacq, nblocks, block_threads, ngroups, rounds, cluster, nclasses;
   int32_t plain_launch, ncohort;
@@ -652,9 +660,11 @@ int gsync_probe_handoff(int signal_mode, int wait_mode, int sm_a, int sm_b, int 
  * op 0: every thread runs `iters` hardware cluster barriers (out[0] / iters per barrier);
  * op 1: ranks 0 and cluster-1 ping-pong a flag in each other's shared memory with
  *       st.release.cluster / ld.acquire.cluster; op 2: the same with remote mbarrier arrives
- *       and mbarrier.try_wait; op 3: as op 1 with a 16-byte record written and polled with
- *       relaxed 128-bit accesses, no fence (hand-off = out[0] / (2 * iters) for ops 1-3).
- *       cluster < 2 with op > 0, or op outside 0..3, returns GSYNC_EINVAL.  out (device, 4 x u64):
+ *       and mbarrier.try_wait; op 3: as op 1 with a 16-byte record written into the peer's
+ *       shared memory and polled in one's own, relaxed 128-bit accesses, no fence; op 4: the
+ *       same pulled (each writes its own record and polls the peer's); hand-off =
+ *       out[0] / (2 * iters) for ops 1-4.  cluster < 2 with op > 0, or op outside 0..4,
+ *       returns GSYNC_EINVAL.  out (device, 4 x u64):
  *       out[0] elapsed ns, out[3] status (0 ok, 1 timed out after 1 s). */
 int gsync_probe_cluster(int op, int cluster, int iters, uint64_t* out, void* stream);
 

@@ -222,6 +222,24 @@ __device__ __forceinline__ uint64_t ld_acquire_cluster_u64(const uint64_t* p) {
 __device__ __forceinline__ void st_release_cluster_u64(uint64_t* p, uint64_t v) {
   asm volatile("st.release.cluster.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+__device__ __forceinline__ uint32_t atom_exch_relaxed_cluster(uint32_t* p, uint32_t v) {
+  uint32_t r;
+  asm volatile("atom.relaxed.cluster.exch.b32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
+  return r;
+}
+__device__ __forceinline__ uint32_t atom_cas_relaxed_cluster(uint32_t* p, uint32_t cmp, uint32_t v) {
+  uint32_t r;
+  asm volatile("atom.relaxed.cluster.cas.b32 %0, [%1], %2, %3;" : "=r"(r) : "l"(p), "r"(cmp), "r"(v) : "memory");
+  return r;
+}
+__device__ __forceinline__ uint64_t ld_relaxed_cluster_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.cluster.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_cluster_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.cluster.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 // One 16-byte record in the shared memory of a cluster block, read or written as one relaxed
 // 128-bit access at cluster scope (generic address from mapa).
 __device__ __forceinline__ void ld_relaxed_cluster_b128(const void* p, uint64_t& lo, uint64_t& hi) {

@@ -21,7 +21,8 @@ The algorithms follow Section 5 ("Design") and the pseudocode of the Appendix:
   RingMutex     the paper's ring-buffer sleeping mutex (Section 5, "design alternative")
   CohortMutex   two-die cohort lock: a ticket lock per die under a global ticket lock
   CarryCohortMutex  the cohort lock whose records carry the guarded data (batched kernel)
-  CarryHierMutex    the same over three levels: cluster, die and global (batched kernel)
+  CarryMcsHierMutex the same over three levels: an MCS queue per cluster, a ticket lock per
+                    die, a global ticket lock (batched kernel)
   CondVarQueue  condition variables (ticket and signal counters) on a bounded buffer
   SpinSem       spin-lock semaphore with optional backoff ("Spin-Lock Semaphore")
   SleepSem      sleeping (FA) semaphore ("Sleeping Semaphore")
@@ -577,114 +578,158 @@ class CarryCohortMutex:
         raise AssertionError(pc)
 
 
-class CarryHierMutex:
+class CarryMcsHierMutex:
     """Three-level carrying cohort lock (the batched kernel's GSYNC_BATCHED_CLUSTER_DIE_CARRY;
-    a GB300 design, not in the paper): a ticket lock per cluster, under a ticket lock per die,
-    under a global ticket lock, every level with a record that carries the guarded sum.
+    a GB300 design, not in the paper): an MCS queue (Mellor-Crummey and Scott, 1991) per
+    cluster, under a ticket lock per die, under a global ticket lock, every level passing the
+    guarded sum in its records.
 
-    Block p belongs to cluster cluster_of[p], cluster c to die die_of[c].  Records: a
-    cluster's (served, word, sum), whose word, when owned, carries the die ticket, the global
-    ticket and the pass counts of the cohorts above; a die's (served, word, sum), whose word,
-    when owned, carries the global ticket and the die's pass count; the global (turn, sum).
-    Served tickets and the global turn are compared in 16 bits, as on the device.  A holder
-    takes the sum from the record that granted it the lock.  It releases to the next waiter of
-    its cluster (record owned, the die and global locks kept) while one is queued and the
-    cluster budget allows; else to the next waiter of its die (the die record owned, the global
-    lock kept), then releases its cluster; else it releases the global lock, then its die, then
-    its cluster.  A ghost total checks that every holder enters with the sum of all earlier
-    contributions.
-    broken="die_pass_keeps_cluster": a die pass leaves the cluster record owned, so the
-    cluster's next waiter also enters; broken="die_grant_reads_cluster": a holder granted at
-    the die level takes the sum from its cluster record; broken="global_skips_die": a global
-    release leaves the die lock held.
+    The cluster's tail holds (block, seq) of the last block to queue, or None when the cluster
+    lock is free.  A block queues with seq = its own count of queueings plus one: it swaps
+    itself into the tail; if the tail was None it holds the cluster lock at once (not owned:
+    it continues at the die level); else it links itself into its predecessor's node, link =
+    (block, seq, predecessor's seq), and polls its own node's record until the record's seq is
+    its own.  A holder passes the lock by writing (successor's seq, owned word or None, sum)
+    into its successor's node: the successor is the one whose link names the holder's current
+    seq.  Without a successor it swaps the tail back to None if the tail still names it, and
+    otherwise waits for the link.  Records and links are never reset: every one is checked
+    against the seq it must carry.  Block p belongs to cluster cluster_of[p], cluster c to die
+    die_of[c].  A die has a ticket counter and a record (served, word, sum) whose word, when
+    owned, carries the global ticket and the die's pass count; the global lock a ticket counter
+    and a record (turn, sum).  An owned cluster record carries the die ticket, the global ticket
+    and both pass counts.  Served tickets, the global turn and record seqs are compared in 16
+    bits, as on the device.  A holder takes the sum from the record that granted it the lock.
+    It passes to its linked successor while the cluster budget allows; else to the next
+    waiting cluster of its die (the die record owned) while the die budget allows, then frees
+    its cluster; else it releases the global lock, then its die, then its cluster.  A ghost
+    total checks that every holder enters with the sum of all earlier contributions.
+    broken="no_seq_check": a block takes any record in its node as its grant;
+    broken="stale_link": a holder trusts a link left by an earlier round; broken="no_cas": a
+    holder without a linked successor leaves the tail as it is.
     """
     kind, capacity, fifo = "mutex", 1, False
     M16 = 0xFFFF
 
-    def __init__(self, cluster_of=(0, 0, 1), die_of=(0, 0), cbudget=2, dbudget=2, base=0, broken=None):
+    def __init__(self, cluster_of=(0, 0, 1), die_of=(0, 0), cbudget=2, dbudget=2, broken=None):
         self.cluster_of, self.die_of = tuple(cluster_of), tuple(die_of)
-        self.cbudget, self.dbudget, self.base, self.broken = cbudget, dbudget, base, broken
+        self.cbudget, self.dbudget, self.broken = cbudget, dbudget, broken
         self.nc, self.nd = len(self.die_of), max(self.die_of) + 1
 
     def init(self, nproc, ops):
-        b = self.base
-        cl = (b, b & self.M16, None, 0) * self.nc
-        dl = (b, b & self.M16, None, 0) * self.nd
-        return cl + dl + (b, b & self.M16, 0) + (0,), tuple((0, 0, 0, 0, 0, 0, 0, 0) for _ in range(nproc))
+        nodes = (None, None) * nproc                  # (link, record) per block
+        tails = (None,) * self.nc
+        dl = (0, 0, None, 0) * self.nd                # (next, served, word, sum) per die
+        # loc: pc, k, seq, succ, td, cp, dp, g, s
+        return nodes + tails + dl + (0, 0, 0) + (0,), tuple((0, 0, 0, None, 0, 0, 0, 0, 0) for _ in range(nproc))
 
     def step(self, p, loc, sh, nproc, ops):
-        pc, k, tc, td, cp, dp, g, s = loc
+        pc, k, seq, succ, td, cp, dp, g, s = loc
         c = self.cluster_of[p]
         d = self.die_of[c]
-        C0, D0 = 4 * c, 4 * self.nc + 4 * d
-        G = 4 * self.nc + 4 * self.nd
-        cnext, cserved, cword, csum = sh[C0:C0 + 4]
+        N0 = 0
+        T0 = 2 * nproc
+        D0 = T0 + self.nc + 4 * d
+        G = T0 + self.nc + 4 * self.nd
+        link, rec = sh[N0 + 2 * p], sh[N0 + 2 * p + 1]
+        tail = sh[T0 + c]
         dnext, dserved, dword, dsum = sh[D0:D0 + 4]
         gnext, gturn, gsum, truth = sh[G:G + 4]
         f = (p + 1 + 16 * k) & M32
         out = (s + f) & M32
 
-        def put(i, rec):
-            return sh[:i] + rec + sh[i + len(rec):]
+        def put(i, vals):
+            return sh[:i] + vals + sh[i + len(vals):]
 
-        def finish():
+        def L(**kw):
+            v = dict(pc=pc, k=k, seq=seq, succ=succ, td=td, cp=cp, dp=dp, g=g, s=s)
+            v.update(kw)
+            return (v["pc"], v["k"], v["seq"], v["succ"], v["td"], v["cp"], v["dp"], v["g"], v["s"])
+
+        def finish(**kw):
             k2 = k + 1
-            return (0 if k2 < ops else DONE), k2
+            return L(pc=(0 if k2 < ops else DONE), k=k2, succ=None, **kw)
 
-        if pc == 0:  # cluster ticket
-            return (1, k, cnext, td, cp, dp, g, s), put(C0, (inc(cnext),)), None
-        if pc == 1:  # one read of the cluster record
-            if cserved != tc & self.M16:
+        def linked():  # the successor named by this block's link for its current seq
+            if link is None:
+                return None
+            sp, sseq, pseq = link
+            if pseq != seq and self.broken != "stale_link":
+                return None
+            return (sp, sseq)
+
+        if pc == 0:  # swap into the tail
+            seq2 = seq + 1
+            if tail is None:
+                return L(pc=2, seq=seq2, cp=0), put(T0 + c, ((p, seq2),)), None
+            return L(pc=1, seq=seq2, succ=tail), put(T0 + c, ((p, seq2),)), None
+        if pc == 1:  # link into the predecessor's node (succ holds the predecessor here)
+            pp, pseq = succ
+            return L(pc=20, succ=None), put(N0 + 2 * pp, ((p, seq, pseq),)), None
+        if pc == 20:  # poll this block's own record
+            if rec is None or (rec[0] != seq & self.M16 and self.broken != "no_seq_check"):
                 return loc, sh, None
-            if cword is not None:  # the cluster holds the die lock
-                _, cp2, dp2, td2, g2 = cword
-                return (PC_ENTER, k, tc, td2, cp2, dp2, g2, csum), sh, None
-            return (2, k, tc, td, 0, dp, g, s), sh, None
+            _, word, rsum = rec
+            if word is not None:
+                _, cp2, dp2, td2, g2 = word
+                return L(pc=PC_ENTER, cp=cp2, dp=dp2, td=td2, g=g2, s=rsum), sh, None
+            return L(pc=2, cp=0), sh, None
         if pc == 2:  # die ticket
-            return (3, k, tc, dnext, cp, dp, g, s), put(D0, (inc(dnext),)), None
-        if pc == 3:  # one read of the die record
+            return L(pc=3, td=dnext), put(D0, (inc(dnext),)), None
+        if pc == 3:
             if dserved != td & self.M16:
                 return loc, sh, None
-            if dword is not None:  # the die holds the global lock
+            if dword is not None:
                 _, dp2, g2 = dword
-                s2 = csum if self.broken == "die_grant_reads_cluster" else dsum
-                return (PC_ENTER, k, tc, td, 0, dp2, g2, s2), sh, None
-            return (4, k, tc, td, 0, 0, g, s), sh, None
+                return L(pc=PC_ENTER, cp=0, dp=dp2, g=g2, s=dsum), sh, None
+            return L(pc=4, cp=0, dp=0), sh, None
         if pc == 4:  # global ticket
-            return (5, k, tc, td, cp, dp, gnext & self.M16, s), put(G, (inc(gnext),)), None
-        if pc == 5:  # one read of the global record
+            return L(pc=5, g=gnext & self.M16), put(G, (inc(gnext),)), None
+        if pc == 5:
             if gturn != g:
                 return loc, sh, None
-            return (PC_ENTER, k, tc, td, 0, 0, g, gsum), sh, None
+            return L(pc=PC_ENTER, cp=0, dp=0, s=gsum), sh, None
         if pc == PC_ENTER:
             if s != truth:
                 return loc, sh, ("violation", f"block {p} entered with sum {s}, expected {truth}")
-            return (PC_EXIT, k, tc, td, cp, dp, g, s), sh, ("enter", (c, tc))
+            return L(pc=PC_EXIT), sh, ("enter", (c, seq))
         if pc == PC_EXIT:
-            return (6, k, tc, td, cp, dp, g, s), put(G + 3, ((truth + f) & M32,)), ("exit",)
-        if pc == 6:  # a waiter of this cluster?
-            waiter = cnext != inc(tc)
-            return ((7 if waiter and cp + 1 < self.cbudget else 8), k, tc, td, cp, dp, g, s), sh, None
-        if pc == 7:  # pass within the cluster: the die and global locks stay
-            pc2, k2 = finish()
-            rec = (inc(tc) & self.M16, ("own", cp + 1, dp, td, g), out)
-            return (pc2, k2, tc, td, cp, dp, g, s), put(C0 + 1, rec), None
+            return L(pc=6), put(G + 3, ((truth + f) & M32,)), ("exit",)
+        if pc == 6:  # one read of this block's link
+            nxt = linked()
+            if nxt is not None and cp + 1 < self.cbudget:
+                return L(pc=7, succ=nxt), sh, None
+            return L(pc=8, succ=nxt), sh, None
+        if pc == 7:  # pass within the cluster: push an owned record to the successor
+            sp, sseq = succ
+            word = ("own", cp + 1, dp, td & self.M16, g)
+            return finish(), put(N0 + 2 * sp + 1, ((sseq & self.M16, word, out),)), None
         if pc == 8:  # a waiter of this die?
             waiter = dnext != inc(td)
-            return ((9 if waiter and dp + 1 < self.dbudget else 10), k, tc, td, cp, dp, g, s), sh, None
-        if pc == 9:  # pass within the die: the global lock stays
-            return (11, k, tc, td, cp, dp, g, s), put(D0 + 1, (inc(td) & self.M16, ("own", dp + 1, g), out)), None
-        if pc == 10:  # release the global lock
-            nxt = 11 if self.broken == "global_skips_die" else 12
-            return (nxt, k, tc, td, cp, dp, g, s), put(G + 1, ((g + 1) & self.M16, out)), None
+            return L(pc=(9 if waiter and dp + 1 < self.dbudget else 10)), sh, None
+        if pc == 9:  # pass within the die
+            return L(pc=11), put(D0 + 1, (inc(td) & self.M16, ("own", dp + 1, g), out)), None
+        if pc == 10:  # release the global lock, then the die
+            return L(pc=12), put(G + 1, ((g + 1) & self.M16, out)), None
         if pc == 12:
-            return (11, k, tc, td, cp, dp, g, s), put(D0 + 1, (inc(td) & self.M16, None, out)), None
-        if pc == 11:  # release the cluster
-            pc2, k2 = finish()
-            word = cword if self.broken == "die_pass_keeps_cluster" and cword is not None else None
-            if self.broken == "die_pass_keeps_cluster" and word is None:
-                word = ("own", cp + 1, dp, td, g)
-            return (pc2, k2, tc, td, cp, dp, g, s), put(C0 + 1, (inc(tc) & self.M16, word, out)), None
+            return L(pc=11), put(D0 + 1, (inc(td) & self.M16, None, out)), None
+        if pc == 11:  # release the cluster: push a record that is not owned, or free the tail
+            nxt = succ if succ is not None else linked()
+            if nxt is not None:
+                sp, sseq = nxt
+                return finish(), put(N0 + 2 * sp + 1, ((sseq & self.M16, None, out),)), None
+            return L(pc=13), sh, None
+        if pc == 13:  # compare-and-swap the tail back to None
+            if tail == (p, seq) or self.broken == "no_cas":
+                if self.broken == "no_cas":
+                    return finish(), sh, None
+                return finish(), put(T0 + c, (None,)), None
+            return L(pc=14), sh, None
+        if pc == 14:  # a successor swapped in: wait for its link
+            nxt = linked()
+            if nxt is None:
+                return loc, sh, None
+            sp, sseq = nxt
+            return finish(), put(N0 + 2 * sp + 1, ((sseq & self.M16, None, out),)), None
         raise AssertionError(pc)
 
 

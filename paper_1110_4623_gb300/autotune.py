@@ -40,8 +40,8 @@ CANDIDATES = [
 ]
 CLUSTERS = [1, 2, 4, 8]
 # Tried last, for the hot and warm classes, once a cluster size above 1 is chosen: the cluster
-# cohort lock and its carrying form (keys below 256) need a cluster launch.
-CLUSTER_CANDIDATES = [("cluster", 128, 4000), ("cluster_carry", 0, 0)]
+# cohort lock and the carrying locks over clusters (keys below 256) need a cluster launch.
+CLUSTER_CANDIDATES = [("cluster", 128, 4000), ("cluster_carry", 0, 0), ("cluster_die_carry", 0, 0)]
 DEFAULT_POLICY = [("ticket", 0, 0)] * NCLASSES
 
 

@@ -25,13 +25,16 @@ constexpr int kMaxThreads = 256;
 // barrier a header line, two arrival counters (by epoch parity) and the release epoch.
 constexpr uint32_t kMutexObjWords = 3 * gsync::kLineWords;
 constexpr uint32_t kBarObjWords = 4 * gsync::kLineWords;
-// Keys below this may use the cluster locks (the cluster cohort lock and its carrying form):
-// their local locks live in a table in the shared memory of each cluster's block 0 (32 bytes a
-// key); the per-key object's lines 1-2 are the global lock.
+// Keys below this may use the cluster locks (the cluster cohort lock and the carrying locks
+// over clusters): their local locks live in a table in each block's shared memory (32 bytes a
+// key).
 constexpr uint32_t kLocalKeys = 256;
 
-// A key's local lock in a cluster launch: the cluster cohort lock's {ticket, turn}, and for
-// the carrying form the same ticket counter with a 16-byte record {served, cohort word, sum}.
+// A key's slot in a cluster launch.  The cluster cohort lock uses block 0's {ticket, turn};
+// the carrying lock over clusters block 0's ticket and a 16-byte record {served, cohort word,
+// sum}; the three-level carrying lock the tail in block 0's ticket word, and in every block
+// its own MCS node: the link (in `turn`), the pushed record, and its count of queueings (in
+// `pad`).
 struct __align__(16) LocalSlot {
   gsync::ClusterLocal cl;
   uint64_t rec[2];
@@ -262,6 +265,150 @@ __device__ __forceinline__ bool uses_cluster_carry(const Args& a, const uint32_t
   return pol[0] == GSYNC_BATCHED_CLUSTER_CARRY && a.clustered && key < kLocalKeys;
 }
 
+// GSYNC_BATCHED_CLUSTER_DIE_CARRY: the carrying cohort protocol over three levels -- the
+// cluster, the die (ticket and record on the cohort object's page homed on this block's die)
+// and the global lock (lines 1-2 of the cohort object).  The cluster level is an MCS queue
+// (Mellor-Crummey and Scott, 1991) in distributed shared memory: a block swaps itself into
+// the tail in block 0's slot, links itself into its predecessor's node, and polls a record in
+// its own shared memory, which its predecessor writes when it passes the lock (a push: one
+// remote store, no remote poll).  A holder takes the sum from the record that granted it the
+// lock and releases, in order of preference: to its linked successor in the cluster (the
+// record owned: the die and global locks stay with the cluster); to the next waiting cluster
+// of its die (the die record owned: the global lock stays with the die), then frees its
+// cluster; or it releases the global lock, then its die, then its cluster.  Nothing is reset
+// between rounds: a block's node carries its own sequence number of queueings on the key, and
+// every link and pushed record is checked against it.  An owned cluster record carries what
+// its cohort's last holder needs: lo = seq:16 | owned:1 | cluster passes:7 | die passes:8 |
+// die ticket:16 | global ticket:16, hi = sum.  The die record is {served, owned:1 | die
+// passes:15 | global ticket:16, sum} and the global record {turn, -, sum}; served tickets and
+// the global turn are compared in 16 bits (fewer than 2^15 waiters at either level).  Every
+// access to a record is one relaxed 128-bit access, so, as in cohort_carry_add, no fence is
+// needed.
+constexpr uint64_t kClusterOwned = 1ull << 16;
+
+__device__ __forceinline__ bool uses_hier_carry(const Args& a, const uint32_t* pol, uint32_t key) {
+  return pol[0] == GSYNC_BATCHED_CLUSTER_DIE_CARRY && a.clustered && key < kLocalKeys && key < (uint32_t)a.ncohort;
+}
+
+__device__ __forceinline__ int hier_carry_add(LocalSlot* slot, uint32_t* obj, uint32_t die, const uint32_t* pol,
+                                              int64_t add, uint64_t timeout_ns) {
+  const uint32_t off = cohort_local_offset(obj, die);
+  if (off == 0u) return GSYNC_EINVAL;
+  uint32_t* dnext = obj + off;
+  uint32_t* drec = dnext + gsync::kLineWords;
+  uint32_t* gnext = obj + 1 * gsync::kLineWords;
+  uint32_t* grec = obj + 2 * gsync::kLineWords;
+  const uint32_t b = pol[3] ? pol[3] : (uint32_t)GSYNC_COHORT_DEFAULT_BUDGET;
+  const uint32_t cbudget = min(b, 127u), dbudget = min(b, 255u);
+  // The cluster level: an MCS queue.  The tail (block 0's slot) names the last block to queue
+  // as (rank + 1) | seq << 4; each block's own slot holds its node: the link its successor
+  // writes, (rank, seq << 4, the holder's seq << 32), and the record its predecessor pushes.
+  const uint32_t me = ptx::cluster_ctarank();
+  uint32_t* tailp = &ptx::map_cluster_rank(slot, 0u)->cl.next;
+  uint64_t* mylink = &slot->cl.turn;
+  const uint32_t seq = ++slot->cl.pad;  // this block's queueings on the key (plain: only this thread)
+  const uint32_t mine = (me + 1u) | (seq << 4);
+  const uint32_t prev = ptx::atom_exch_relaxed_cluster(tailp, mine);
+  gsync::Waiter w;
+  uint64_t lo = 0, hi = 0;
+  uint32_t seen_d = 0u;
+  bool asked_d = false, owned = false;
+  if (prev != 0u) {
+    LocalSlot* ps = ptx::map_cluster_rank(slot, (prev & 0xFu) - 1u);
+    ptx::st_relaxed_cluster_u64(&ps->cl.turn, (uint64_t)me | ((uint64_t)seq << 4) | ((uint64_t)(prev >> 4) << 32));
+    seen_d = ptx::ld_relaxed(dnext);  // consumed only at the release, and only if past the die ticket
+    asked_d = true;
+    for (uint32_t polls = 1;; ++polls) {
+      ptx::ld_relaxed_cluster_b128(slot->rec, lo, hi);  // this block's own shared memory
+      if ((((uint32_t)lo ^ seq) & 0xFFFFu) == 0u) break;
+      if ((polls & 31u) == 0u)
+        if (int rc = w.tick(timeout_ns, obj + gsync::kHdrAbort)) return rc;
+    }
+    owned = (lo & kClusterOwned) != 0u;
+  }
+  uint32_t cp, dp, td, g;
+  int64_t sum;
+  if (owned) {
+    cp = (uint32_t)(lo >> 17) & 0x7Fu;
+    dp = (uint32_t)(lo >> 24) & 0xFFu;
+    td = (uint32_t)(lo >> 32) & 0xFFFFu;
+    g = (uint32_t)(lo >> 48) & 0xFFFFu;
+    sum = (int64_t)hi;
+  } else {
+    // First of a cluster cohort: queue at the die level (at most one waiter per cluster).
+    cp = 0u;
+    td = ptx::atom_add_relaxed(dnext, 1u);
+    uint32_t prev_d = 1u;
+    for (;;) {
+      if (prev_d <= 1u) seen_d = ptx::ld_relaxed(dnext);
+      ptx::ld_relaxed_b128(drec, lo, hi);
+      const uint32_t ahead = (td - (uint32_t)lo) & 0xFFFFu;
+      if (ahead == 0u) break;
+      prev_d = ahead;
+      if (int rc = w.tick(timeout_ns, obj + gsync::kHdrAbort)) return rc;
+    }
+    asked_d = true;
+    const uint32_t dword = (uint32_t)(lo >> 32);
+    if (dword & gsync::kCohortOwned) {
+      dp = (dword >> 16) & 0x7FFFu;
+      g = dword & 0xFFFFu;
+      sum = (int64_t)hi;
+    } else {
+      // First of a die cohort: queue for the global lock (at most one waiter per die).
+      dp = 0u;
+      g = ptx::atom_add_relaxed(gnext, 1u) & 0xFFFFu;
+      for (;;) {
+        seen_d = ptx::ld_relaxed(dnext);
+        ptx::ld_relaxed_b128(grec, lo, hi);
+        if (((uint32_t)lo & 0xFFFFu) == g) break;
+        if (int rc = w.tick(timeout_ns, obj + gsync::kHdrAbort)) return rc;
+      }
+      sum = (int64_t)hi;
+    }
+    td &= 0xFFFFu;
+  }
+  // critical section: sum + add, published with the hand-off
+  sum += add;
+  const uint64_t s = (uint64_t)sum;
+  uint64_t link = ptx::ld_relaxed_cluster_u64(mylink);
+  bool linked = (uint32_t)(link >> 32) == seq;
+  if (linked && cp + 1u < cbudget) {
+    LocalSlot* ss = ptx::map_cluster_rank(slot, (uint32_t)link & 0xFu);
+    const uint64_t rec = (uint64_t)(((uint32_t)link >> 4) & 0xFFFFu) | kClusterOwned | ((uint64_t)(cp + 1u) << 17) |
+                         ((uint64_t)dp << 24) | ((uint64_t)td << 32) | ((uint64_t)g << 48);
+    ptx::st_relaxed_cluster_b128(ss->rec, rec, s);
+    return GSYNC_OK;
+  }
+  // Another cluster of this die waits iff the die counter is past td + 1 (a read made before
+  // this cohort's die ticket was taken is behind it and says nothing: read again).
+  uint32_t behind = (seen_d - (td + 1u)) & 0xFFFFu;
+  if (!asked_d || behind >= 0x8000u) behind = (ptx::ld_relaxed(dnext) - (td + 1u)) & 0xFFFFu;
+  if (dp + 1u < dbudget && behind != 0u && behind < 0x8000u) {
+    const uint32_t dw = gsync::kCohortOwned | ((dp + 1u) << 16) | g;
+    ptx::st_relaxed_b128(drec, (uint64_t)((td + 1u) & 0xFFFFu) | ((uint64_t)dw << 32), s);
+  } else {
+    ptx::st_relaxed_b128(grec, (uint64_t)((g + 1u) & 0xFFFFu), s);
+    ptx::st_relaxed_b128(drec, (uint64_t)((td + 1u) & 0xFFFFu), s);
+  }
+  // Free the cluster level: push a record that is not owned to the successor, or swap the
+  // tail back to empty; a block that swapped in meanwhile links itself shortly: wait for it.
+  if (!linked) {
+    link = ptx::ld_relaxed_cluster_u64(mylink);
+    linked = (uint32_t)(link >> 32) == seq;
+  }
+  if (!linked) {
+    if (ptx::atom_cas_relaxed_cluster(tailp, mine, 0u) == mine) return GSYNC_OK;
+    for (;;) {
+      link = ptx::ld_relaxed_cluster_u64(mylink);
+      if ((uint32_t)(link >> 32) == seq) break;
+      if (int rc = w.tick(timeout_ns, obj + gsync::kHdrAbort)) return rc;
+    }
+  }
+  LocalSlot* ss = ptx::map_cluster_rank(slot, (uint32_t)link & 0xFu);
+  ptx::st_relaxed_cluster_b128(ss->rec, (uint64_t)(((uint32_t)link >> 4) & 0xFFFFu), s);
+  return GSYNC_OK;
+}
+
 // After the batched kernel: each carrying key's count and sum move from its record to count[]
 // and sum[], and the record's count and sum return to zero (its turn stays, matching the
 // ticket counter), so the next launch starts from zero like the other kinds' outputs.  A
@@ -293,6 +440,26 @@ __global__ void batched_collect_kernel(Args a) {
     grec[1] = 0;
     return;
   }
+  if (uses_hier_carry(a, pol, key)) {
+    // count[] already holds the clusters' counts; the cohort object's global record holds the
+    // sum; its global and die counters and records return to zero
+    uint32_t* obj = a.cohort_state + (size_t)key * kCohortObjWords;
+    const uint32_t off[2] = {cohort_local_offset(obj, 0u), cohort_local_offset(obj, 1u)};
+    if (off[0] == 0u || off[1] == 0u) return;  // refused by the batched kernel already
+    for (uint32_t d = 0; d < 2u; ++d) {
+      uint32_t* local = obj + off[d];
+      local[0] = 0u;
+      uint64_t* drec = (uint64_t*)(local + gsync::kLineWords);
+      drec[0] = 0;
+      drec[1] = 0;
+    }
+    uint64_t* grec = (uint64_t*)(obj + 2 * gsync::kLineWords);
+    a.sum[key] = (int64_t)grec[1];
+    obj[1 * gsync::kLineWords] = 0u;
+    grec[0] = 0;
+    grec[1] = 0;
+    return;
+  }
   if (uses_cluster_carry(a, pol, key)) {
     // count[] already holds the clusters' counts; the global record holds the sum
     uint32_t* obj = a.mutex_state + key * kMutexObjWords;
@@ -304,7 +471,7 @@ __global__ void batched_collect_kernel(Args a) {
     return;
   }
   if (pol[0] != GSYNC_BATCHED_TICKET_CARRY && pol[0] != GSYNC_BATCHED_COHORT_CARRY &&
-      pol[0] != GSYNC_BATCHED_CLUSTER_CARRY)
+      pol[0] != GSYNC_BATCHED_CLUSTER_CARRY && pol[0] != GSYNC_BATCHED_CLUSTER_DIE_CARRY)
     return;
   uint64_t* rec = (uint64_t*)(a.mutex_state + key * kMutexObjWords + 2 * gsync::kLineWords);
   const uint64_t lo = rec[0];
@@ -343,13 +510,13 @@ __global__ void __launch_bounds__(MAXT, 8) batched_kernel(Args a) {
   // and kept alive by the cluster barrier at the end of the kernel.
   __shared__ LocalSlot local_locks[BKIND == GSYNC_BAR_CLUSTER ? kLocalKeys : 1];
   if (BKIND == GSYNC_BAR_CLUSTER) {
-    if (ptx::cluster_ctarank() == 0)
-      for (uint32_t i = tid; i < kLocalKeys; i += blockDim.x) {
-        local_locks[i].cl.next = 0u;
-        local_locks[i].cl.turn = 0ull;
-        local_locks[i].rec[0] = 0ull;
-        local_locks[i].rec[1] = 0ull;
-      }
+    for (uint32_t i = tid; i < kLocalKeys; i += blockDim.x) {
+      local_locks[i].cl.next = 0u;
+      local_locks[i].cl.pad = 0u;
+      local_locks[i].cl.turn = 0ull;
+      local_locks[i].rec[0] = 0ull;
+      local_locks[i].rec[1] = 0ull;
+    }
     ptx::cluster_sync();
   }
   // The die of this block's SM, from the die table every cohort object carries.
@@ -410,9 +577,12 @@ __global__ void __launch_bounds__(MAXT, 8) batched_kernel(Args a) {
         const uint32_t cls = a.key_class[key];
         const uint32_t* pol = a.policy + 4u * (cls < (uint32_t)a.nclasses ? cls : 0u);
         if (pol[0] == GSYNC_BATCHED_TICKET_CARRY || pol[0] == GSYNC_BATCHED_COHORT_CARRY ||
-            pol[0] == GSYNC_BATCHED_CLUSTER_CARRY) {
+            pol[0] == GSYNC_BATCHED_CLUSTER_CARRY || pol[0] == GSYNC_BATCHED_CLUSTER_DIE_CARRY) {
           int rc;
-          if (BKIND == GSYNC_BAR_CLUSTER && uses_cluster_carry(a, pol, key))
+          if (BKIND == GSYNC_BAR_CLUSTER && uses_hier_carry(a, pol, key))
+            rc = hier_carry_add(&local_locks[key], a.cohort_state + (size_t)key * kCohortObjWords, die, pol, add,
+                                a.timeout_ns);
+          else if (BKIND == GSYNC_BAR_CLUSTER && uses_cluster_carry(a, pol, key))
             rc = cluster_carry_add(ptx::map_cluster_rank(&local_locks[key], 0u), a.mutex_state + key * kMutexObjWords,
                                    pol, add, a.timeout_ns);
           else if (uses_cohort_carry(a, pol, key))
@@ -471,14 +641,16 @@ __global__ void __launch_bounds__(MAXT, 8) batched_kernel(Args a) {
   }
   if (BKIND == GSYNC_BAR_CLUSTER) {
     ptx::cluster_sync();  // block 0's local locks outlive every user
-    // The cluster carrying lock's acquisitions of each key, counted by its local ticket.
-    if (ptx::cluster_ctarank() == 0)
-      for (uint32_t key = tid; key < kLocalKeys && key < (uint32_t)a.nkeys; key += blockDim.x) {
-        const uint32_t cls = a.key_class[key];
-        const uint32_t* pol = a.policy + 4u * (cls < (uint32_t)a.nclasses ? cls : 0u);
-        const uint32_t n = local_locks[key].cl.next;
-        if (n && uses_cluster_carry(a, pol, key)) ptx::red_add_relaxed(a.count + key, n);
-      }
+    // The cluster carrying locks' acquisitions of each key: counted by the cluster's ticket
+    // (block 0's slot), or by each block's own queueings on the MCS level.
+    const bool rank0 = ptx::cluster_ctarank() == 0;
+    for (uint32_t key = tid; key < kLocalKeys && key < (uint32_t)a.nkeys; key += blockDim.x) {
+      const uint32_t cls = a.key_class[key];
+      const uint32_t* pol = a.policy + 4u * (cls < (uint32_t)a.nclasses ? cls : 0u);
+      const uint32_t n = uses_hier_carry(a, pol, key) ? local_locks[key].cl.pad
+                         : rank0 && uses_cluster_carry(a, pol, key) ? local_locks[key].cl.next : 0u;
+      if (n) ptx::red_add_relaxed(a.count + key, n);
+    }
   }
 }
 

@@ -153,9 +153,12 @@ __device__ __forceinline__ bool mbar_try_wait_parity(uint32_t addr, uint32_t par
 // op 1: ranks 0 and c-1 ping-pong a flag in each other's shared memory (release/acquire).
 // op 2: ranks 0 and c-1 ping-pong remote mbarrier arrivals (hardware wait).
 // op 3: as op 1 with a 16-byte record in each other's shared memory, written and polled with
-//       relaxed 128-bit accesses (no fence on either side).
+//       relaxed 128-bit accesses (no fence on either side): the writer pushes into the
+//       poller's shared memory, and the poller polls its own.
+// op 4: as op 3, pulled: each rank writes the record in its own shared memory and polls the
+//       peer's (the form of a lock whose record lives in one block that every waiter polls).
 // out[0] = elapsed ns of the loop on rank 0 (per op: out[0] / iters; per hand-off for
-// ops 1-3: out[0] / (2 * iters)); out[3] = status.
+// ops 1-4: out[0] / (2 * iters)); out[3] = status.
 __global__ void probe_cluster_kernel(int op, int iters, uint64_t* out) {
   __shared__ __align__(8) uint64_t mbar;
   __shared__ __align__(16) uint64_t rec[2];
@@ -184,14 +187,16 @@ __global__ void probe_cluster_kernel(int op, int iters, uint64_t* out) {
       if (serve) {
         if (op == 1) st_cluster_release(peer_flag, (uint32_t)i);
         else if (op == 3) st_cluster_relaxed_b128(peer_rec, (uint64_t)i, (uint64_t)i);
+        else if (op == 4) st_cluster_relaxed_b128(my_rec, (uint64_t)i, (uint64_t)i);
         else mbar_remote_arrive(peer_mbar);
       }
       uint32_t polls = 0;
       if (op == 1) {
         while (ld_cluster_acquire(my_flag) != (uint32_t)i)
           if ((++polls & 63u) == 0 && ptx::globaltimer() > deadline) { status = 1; break; }
-      } else if (op == 3) {
-        while (ld_cluster_relaxed_b128_lo(my_rec) != (uint64_t)i)
+      } else if (op == 3 || op == 4) {
+        const uint32_t poll_rec = op == 3 ? my_rec : peer_rec;
+        while (ld_cluster_relaxed_b128_lo(poll_rec) != (uint64_t)i)
           if ((++polls & 63u) == 0 && ptx::globaltimer() > deadline) { status = 1; break; }
       } else {
         while (!mbar_try_wait_parity(my_mbar, (uint32_t)((i - 1) & 1)))
@@ -200,6 +205,7 @@ __global__ void probe_cluster_kernel(int op, int iters, uint64_t* out) {
       if (!serve && status == 0) {
         if (op == 1) st_cluster_release(peer_flag, (uint32_t)i);
         else if (op == 3) st_cluster_relaxed_b128(peer_rec, (uint64_t)i, (uint64_t)i);
+        else if (op == 4) st_cluster_relaxed_b128(my_rec, (uint64_t)i, (uint64_t)i);
         else mbar_remote_arrive(peer_mbar);
       }
     }
@@ -257,7 +263,7 @@ extern "C" int gsync_probe_handoff(int signal_mode, int wait_mode, int sm_a, int
 }
 
 extern "C" int gsync_probe_cluster(int op, int cluster, int iters, uint64_t* out, void* stream) {
-  if (op < 0 || op > 3 || cluster < 1 || cluster > 8 || iters < 1 || !out || (op > 0 && cluster < 2))
+  if (op < 0 || op > 4 || cluster < 1 || cluster > 8 || iters < 1 || !out || (op > 0 && cluster < 2))
     return GSYNC_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   GSYNC_CUDA(cudaMemsetAsync(out, 0, 4 * sizeof(uint64_t), st));

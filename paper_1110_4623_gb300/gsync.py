@@ -21,13 +21,16 @@ GSYNC_STATUS_TIMEOUT, GSYNC_STATUS_ABORTED, GSYNC_STATUS_VIOLATION, GSYNC_STATUS
 MUTEX_KINDS = {"cas_spin": 0, "cas_backoff": 1, "ticket": 2, "sleep_queue": 3, "cohort": 4, "ring": 5, "cluster": 6}
 # Policy kinds of the batched kernel: the mutex kinds it runs, plus the ticket lock whose turn
 # line carries the guarded count and sum (GSYNC_BATCHED_TICKET_CARRY), and the cohort locks
-# with carrying records over the two dies (GSYNC_BATCHED_COHORT_CARRY) and over thread-block
-# clusters (GSYNC_BATCHED_CLUSTER_CARRY).
+# with carrying records over the two dies (GSYNC_BATCHED_COHORT_CARRY), over thread-block
+# clusters (GSYNC_BATCHED_CLUSTER_CARRY), and over clusters within dies
+# (GSYNC_BATCHED_CLUSTER_DIE_CARRY).
 BATCHED_TICKET_CARRY = 16
 BATCHED_COHORT_CARRY = 17
 BATCHED_CLUSTER_CARRY = 18
+BATCHED_CLUSTER_DIE_CARRY = 19
 BATCHED_POLICY_KINDS = {**MUTEX_KINDS, "ticket_carry": BATCHED_TICKET_CARRY,
-                        "cohort_carry": BATCHED_COHORT_CARRY, "cluster_carry": BATCHED_CLUSTER_CARRY}
+                        "cohort_carry": BATCHED_COHORT_CARRY, "cluster_carry": BATCHED_CLUSTER_CARRY,
+                        "cluster_die_carry": BATCHED_CLUSTER_DIE_CARRY}
 COHORT_DEFAULT_BUDGET = 64
 BARRIER_KINDS = {"atomic": 0, "flag": 1, "tree": 2, "cluster": 3, "sharded": 4, "die": 5, "split": 6, "count": 7}
 SEM_KINDS = {"ticket": 0, "spin": 1, "spin_backoff": 2, "window": 3}

@@ -516,7 +516,8 @@ class BatchedRun:
     def set_policy(self, table):
         """table: list of (kind, min_ns, max_ns[, budget]) per class (budget: the cohort locks'
         passes per cohort, 0 = default).  Zeroes the mutexes (kinds may change) and, when a
-        class uses cohort_carry, places and initialises the cohort objects."""
+        class uses cohort_carry or cluster_die_carry, places and initialises the cohort
+        objects."""
         flat = []
         for entry in table:
             kind, mn, mx = entry[:3]
@@ -524,7 +525,7 @@ class BatchedRun:
             flat += [G.BATCHED_POLICY_KINDS[kind] if isinstance(kind, str) else int(kind), int(mn), int(mx), int(budget)]
         self.policy.copy_(torch.tensor(flat, dtype=torch.int32))
         self.mutex_state.zero_()
-        if G.BATCHED_COHORT_CARRY in flat[0::4]:
+        if {G.BATCHED_COHORT_CARRY, G.BATCHED_CLUSTER_DIE_CARRY} & set(flat[0::4]):
             base = G.ptr(self.cohort_state)
             for k in range(self.ncohort):
                 G.check("gsync_mutex_init_cohort",

@@ -126,13 +126,32 @@ def test_cluster_carry_policy(cluster, policy, nacq):
         check(run, keys, adds, got, 27)
 
 
+@pytest.mark.parametrize("cluster,policy,nacq,ncohort", [
+    (8, [("cluster_die_carry", 0, 0), ("cluster_die_carry", 8, 2000), ("ticket_carry", 0, 0)], 1_000_000, 128),
+    (2, [("cluster_die_carry", 0, 0, 1), ("cluster_carry", 0, 0), ("cas_spin", 0, 0)], 200_000, 64),
+    (4, [("cluster_die_carry", 0, 0, 3), ("cohort_carry", 0, 0), ("cluster_die_carry", 64, 2000, 32767)],
+     200_000, 128),
+    (8, [("cluster_die_carry", 0, 0)] * 3, 200_000, 1),
+    (1, [("cluster_die_carry", 0, 0)] * 3, 200_000, 64)])  # no clusters: the carrying ticket lock
+def test_cluster_die_carry_policy(cluster, policy, nacq, ncohort):
+    # The carrying lock over three levels (cluster, die, global) for keys below 256 and below
+    # ncohort in a cluster launch, the rest on the carrying ticket lock: budgets 1, 3, the
+    # default and the maximum (127 passes in a cluster, 255 on a die), beside the other kinds,
+    # one cohort object, no clusters; twice in a row on the same objects.
+    run, keys, adds = make(nacq, cluster=cluster, policy=policy, rounds=23, ncohort=ncohort)
+    for _ in range(2):
+        got = run.run()
+        assert got["rc"] == 0
+        check(run, keys, adds, got, 23)
+
+
 @pytest.mark.parametrize("threads", [32, 160, 256])
 @pytest.mark.parametrize("cluster", [1, 8])
 def test_block_sizes(threads, cluster):
     # Blocks of up to 128 threads run the instantiation with 64 registers a thread, larger
     # ones the one with 32; both, with every carrying kind and the plain kinds beside them.
-    pol = [("cluster_carry", 0, 0), ("cohort_carry", 8, 2000), ("ticket", 64, 2000)]
-    run, keys, adds = make(200_000, cluster=cluster, policy=pol, rounds=19, block_threads=threads)
+    pol = [("cluster_die_carry", 0, 0), ("cluster_carry", 0, 0), ("cohort_carry", 8, 2000)]
+    run, keys, adds = make(200_000, cluster=cluster, policy=pol, rounds=19, block_threads=threads, ncohort=256)
     got = run.run()
     assert got["rc"] == 0
     check(run, keys, adds, got, 19)
@@ -141,7 +160,7 @@ def test_block_sizes(threads, cluster):
 def test_cluster_carry_graph_replay():
     import torch
     run, keys, adds = make(300_000, rounds=20, cluster=8,
-                           policy=[("cluster_carry", 0, 0), ("ticket", 0, 0), ("cohort_carry", 0, 0)])
+                           policy=[("cluster_die_carry", 0, 0), ("cluster_carry", 0, 0), ("cohort_carry", 0, 0)])
     run.capture()
     for _ in range(3):
         run.replay()

@@ -70,14 +70,14 @@ def test_cs_probe():
 
 @pytest.mark.parametrize("cluster", [2, 8])
 def test_cluster_handoff_probes(cluster):
-    # The hardware cluster barrier and the three hand-offs through distributed shared memory
-    # (release/acquire flag, remote mbarrier arrive, relaxed 128-bit record) run and report
-    # sane times; malformed requests are refused.
+    # The hardware cluster barrier and the hand-offs through distributed shared memory
+    # (release/acquire flag, remote mbarrier arrive, relaxed 128-bit record pushed and pulled)
+    # run and report sane times; malformed requests are refused.
     from paper_1110_4623_gb300 import gsync as G, runner
     import torch
-    for op in (0, 1, 2, 3):
+    for op in (0, 1, 2, 3, 4):
         r = runner.probe_cluster(op, cluster, 1000)
         assert r["status"] == 0 and 10 < r["ns"] < 20_000, (op, r)
     out = torch.zeros(4, dtype=torch.int64, device="cuda")
-    assert G.gsync_probe_cluster(4, cluster, 10, out) == G.GSYNC_EINVAL
+    assert G.gsync_probe_cluster(5, cluster, 10, out) == G.GSYNC_EINVAL
     assert G.gsync_probe_cluster(3, 1, 10, out) == G.GSYNC_EINVAL

@@ -34,13 +34,14 @@ CORRECT = [
     ("cohort_carry_budget_1", mc.CarryCohortMutex(budget=1), 4, 1),
     ("cohort_carry_budget_3", mc.CarryCohortMutex(budget=3), 3, 2),
     ("cohort_carry_three_groups", mc.CarryCohortMutex(budget=2, groups=3), 4, 1),
-    ("hier_carry_one_die", mc.CarryHierMutex(cluster_of=(0, 0, 1), die_of=(0, 0)), 3, 2),
-    ("hier_carry_two_dies", mc.CarryHierMutex(cluster_of=(0, 0, 1), die_of=(0, 1)), 3, 2),
-    ("hier_carry_three_clusters", mc.CarryHierMutex(cluster_of=(0, 1, 2), die_of=(0, 0, 1)), 3, 2),
-    ("hier_carry_four_blocks", mc.CarryHierMutex(cluster_of=(0, 0, 1, 2), die_of=(0, 0, 1)), 4, 1),
-    ("hier_carry_budget_1", mc.CarryHierMutex(cbudget=1, dbudget=1), 3, 2),
-    ("hier_carry_budgets_3_1", mc.CarryHierMutex(cbudget=3, dbudget=1), 3, 2),
-    ("hier_carry_wrap_16", mc.CarryHierMutex(base=0x1FFFE), 3, 2),
+    ("hier_carry_one_die", mc.CarryMcsHierMutex(cluster_of=(0, 0, 1), die_of=(0, 0)), 3, 2),
+    ("hier_carry_one_cluster", mc.CarryMcsHierMutex(cluster_of=(0, 0, 0), die_of=(0,)), 3, 2),
+    ("hier_carry_two_dies", mc.CarryMcsHierMutex(cluster_of=(0, 0, 1), die_of=(0, 1)), 3, 2),
+    ("hier_carry_three_clusters", mc.CarryMcsHierMutex(cluster_of=(0, 1, 2), die_of=(0, 0, 1)), 3, 2),
+    ("hier_carry_four_blocks", mc.CarryMcsHierMutex(cluster_of=(0, 0, 1, 1), die_of=(0, 1)), 4, 1),
+    ("hier_carry_budget_1", mc.CarryMcsHierMutex(cbudget=1, dbudget=1), 3, 2),
+    ("hier_carry_cluster_budget_3", mc.CarryMcsHierMutex(cluster_of=(0, 0, 0), die_of=(0,), cbudget=3), 3, 2),
+    ("hier_carry_three_rounds", mc.CarryMcsHierMutex(cluster_of=(0, 0), die_of=(0,)), 2, 3),
     ("spin_sem_1", mc.SpinSem(n=1), 3, 2),
     ("spin_sem_2", mc.SpinSem(n=2), 3, 2),
     ("spin_sem_2_backoff", mc.SpinSem(n=2, backoff=True), 3, 2),
@@ -123,12 +124,13 @@ BROKEN = [
     # sum, and a local pass that does not add the holder's own contribution.
     ("cohort_carry_global_reads_local", mc.CarryCohortMutex(broken="global_reads_local"), 3, 2, "entered with"),
     ("cohort_carry_pass_without_add", mc.CarryCohortMutex(broken="pass_without_add"), 3, 2, "entered with"),
-    # Three-level carrying lock: a die pass that leaves the cluster record owned (two
-    # holders), a die-level grant that takes the cluster record's sum, and a global release
-    # that leaves the die lock held.
-    ("hier_carry_die_pass_keeps_cluster", mc.CarryHierMutex(broken="die_pass_keeps_cluster"), 3, 2, "entered with"),
-    ("hier_carry_die_grant_reads_cluster", mc.CarryHierMutex(broken="die_grant_reads_cluster"), 3, 2, "entered with"),
-    ("hier_carry_global_skips_die", mc.CarryHierMutex(broken="global_skips_die"), 3, 2, "final state"),
+    # Three-level carrying lock: a waiter that takes any record in its node as its grant, a
+    # holder that trusts a link left by an earlier round, and a holder without a linked
+    # successor that leaves the tail naming itself.
+    ("hier_carry_no_seq_check", mc.CarryMcsHierMutex(broken="no_seq_check"), 3, 2, "entered with"),
+    ("hier_carry_stale_link", mc.CarryMcsHierMutex(broken="stale_link"), 3, 2, "cannot reach completion"),
+    ("hier_carry_no_cas", mc.CarryMcsHierMutex(cluster_of=(0, 0, 0), die_of=(0,), broken="no_cas"), 3, 2,
+     "cannot reach completion"),
     ("sleep_sem_turn_ge", mc.SleepSem(n=1, broken="turn_ge"), 3, 1, "critical section"),
     ("window_sem_ge", mc.WindowSem(n=2, broken="window_ge"), 3, 1, "critical section"),
     ("barrier_no_wait", mc.AtomicBarrier(broken="no_wait"), 3, 1, "passed round"),
