@@ -201,6 +201,11 @@ def measure_all(nblocks: int = 1184, quick: bool = False) -> dict:
         "near": ext["handoff_near_ns"], "far": ext["handoff_far_ns"],
         "dsmem": {str(c): runner.probe_cluster(1, c, n_hand)["ns"] for c in CLUSTER_SIZES},
         "mbarrier": {str(c): runner.probe_cluster(2, c, n_hand)["ns"] for c in CLUSTER_SIZES},
+        # a relaxed 16-byte record with no fence, pushed into the peer's shared memory or
+        # pulled from one's own (the hand-offs of the carrying locks over clusters)
+        "dsmem_relaxed_push": {str(c): runner.probe_cluster(3, c, n_hand)["ns"] for c in CLUSTER_SIZES},
+        "dsmem_relaxed_pull": {str(c): runner.probe_cluster(4, c, n_hand)["ns"] for c in CLUSTER_SIZES},
+        "relaxed_near": runner.near_handoff_relaxed(n_hand)["handoff_ns"],
         "host": runner.probe_host_pingpong(200 if quick else 2000)["handoff_ns"],
     }
     out["cluster_barrier_ns"] = {str(c): runner.probe_cluster(0, c, n_hand)["ns"] for c in (1,) + CLUSTER_SIZES}

@@ -81,6 +81,8 @@ def test_machine_description_cli(tmp_path):
     hand = d["handoff_ns"]
     assert hand["near"] > 0 and hand["far"] > 0 and hand["host"] > 0
     assert all(v > 0 for v in list(hand["dsmem"].values()) + list(hand["mbarrier"].values()))
+    assert all(v > 0 for v in list(hand["dsmem_relaxed_push"].values()) + list(hand["dsmem_relaxed_pull"].values()))
+    assert hand["relaxed_near"] > 0
     assert all(v > 0 for v in d["cluster_barrier_ns"].values()) and all(v > 0 for v in d["fence_ns"].values())
     assert list(d["nanosleep_ns"]) == [str(n) for n in machine.SLEEP_NS]
     assert d["nanosleep_ns"]["8000"] > d["nanosleep_ns"]["100"]
