@@ -38,7 +38,7 @@ BAR_THREADS, BAR_ROUNDS = 128, 1000
 SEM_THREADS, SEM_PAIRS, SEM_COUNTS = 128, 200, (1, 4, 16, 64)
 # Library defaults for GB300, chosen from 1184-block sweeps (the paper's API serves the
 # fastest implementation of each primitive for the GPU as the default, Section 5 "API").
-DEFAULT_MUTEX = "cluster"
+DEFAULT_MUTEX = "cluster_mcs"
 DEFAULT_BARRIER = ("count", 8)
 # cluster params: c | form << 4 (form 0: atomic stage over the leaders; 2: counting stage, the
 # rest of the cluster released by a second cluster barrier -- the fastest cluster form measured)
@@ -48,14 +48,25 @@ BARRIERS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("tree", 8 | 1
             ("cluster", 4 | 2 << 4), ("cluster", 8 | 2 << 4), ("sharded", 32), ("sharded", 8), ("die", 0),
             ("die", 1), ("split", 16 | 16 << 8), ("count", 0), ("count", 8)]
 # Backoff (min_ns, max_ns) per kind; the ticket kinds sleep min_ns per waiter ahead, capped.
-MUTEX_BACKOFF = {"cas_backoff": (16, 512), "ticket": (128, 4000), "cohort": (128, 4000), "cluster": (128, 4000)}
-MUTEX_CLUSTER = 4  # blocks per cluster of the cluster cohort lock (a sweep of 2 / 4 / 8 picked 4)
+MUTEX_BACKOFF = {"cas_backoff": (16, 512), "ticket": (128, 4000), "cohort": (128, 4000), "cluster": (128, 4000),
+                 "cluster_mcs": (128, 4000)}
+# Blocks per cluster of the cluster cohort locks (sweeps of 2 / 4 / 8 picked 4 for the ticket
+# form and 8 for the MCS form).
+MUTEX_CLUSTERS = {"cluster": 4, "cluster_mcs": 8}
+
+
+def mutex_cluster(kind):
+    return MUTEX_CLUSTERS.get(kind, 0)
+
+
+
 # The measured mutex configurations: (name, kind, backoff policy, (min_ns, max_ns), spin).
 # cas_spin_then_sleep is Section 5's futex stand-in: the CAS lock spins, then backs off.
 MUTEX_CONFIGS = [("cas_spin", "cas_spin", 0, None, 0), ("cas_backoff", "cas_backoff", 0, (16, 512), 0),
                  ("cas_spin_then_sleep", "cas_backoff", 2, (16, 512), 32), ("ticket", "ticket", 0, (128, 4000), 0),
                  ("sleep_queue", "sleep_queue", 0, None, 0), ("ring", "ring", 0, None, 0),
-                 ("cohort", "cohort", 0, (128, 4000), 0), ("cluster", "cluster", 0, (128, 4000), 0)]
+                 ("cohort", "cohort", 0, (128, 4000), 0), ("cluster", "cluster", 0, (128, 4000), 0),
+                 ("cluster_mcs", "cluster_mcs", 0, (128, 4000), 0)]
 SEM_BACKOFF = (16, 2000)
 SEM_STEP_KINDS = ("window", "ticket")  # the library's default (the ticket window), then the paper's FA semaphore
 DEFAULT_SEM = "window"
@@ -64,10 +75,9 @@ BATCH_KEYS, BATCH_ACQ, BATCH_GROUPS, BATCH_ROUNDS, BATCH_THREADS = 4096, 1_000_0
 METRIC = "lock acquires/s & barrier ns at 1184 blocks vs L2-atomic roofline; p99 latency"
 # DRAM bytes per launch of the default mutex kind's workload kernel from an ncu capture, or
 # None while the kernel has changed since the last capture.
-ROOF_TRAFFIC = 1_520_555
-ROOF_TRAFFIC_NOTE = ("DRAM bytes (read + write) per launch of the dominant kernel (cluster cohort mutex workload), "
-                     "mean over the step's three launches (CS 0/64/1024: 1.46/1.38/1.72 MB), one-pass ncu capture "
-                     "of the same launches in profiles/; algorithmic bytes 1.89 MB (16 B per acquisition)")
+ROOF_TRAFFIC = None
+ROOF_TRAFFIC_NOTE = ("not yet captured for the MCS cluster cohort lock's workload kernel (the default since the "
+                     "last capture); algorithmic bytes 1.89 MB per launch (16 B per acquisition)")
 TIMEOUT_NS = 10_000_000_000
 
 
@@ -415,7 +425,7 @@ class GpuStep:
                 delay, add = inputs.mutex_inputs(NBLOCKS, MUTEX_ACQ, inputs.mutex_seed(G.MUTEX_KINDS[kind], NBLOCKS, K))
                 bo = runner.backoff(policy=policy, min_ns=bo_ns[0], max_ns=bo_ns[1], spin=spin) if bo_ns else None
                 self.mutex[(name, K)] = (runner.MutexRun(kind, NBLOCKS, MUTEX_THREADS, MUTEX_ACQ, K, delay, add, bo=bo,
-                                                         timeout_ns=TIMEOUT_NS, cluster=MUTEX_CLUSTER), add)
+                                                         timeout_ns=TIMEOUT_NS, cluster=mutex_cluster(kind)), add)
         self.barrier = {(k, p): runner.BarrierRun(k, NBLOCKS, BAR_THREADS, BAR_ROUNDS, full=False, param=p,
                                                   timeout_ns=TIMEOUT_NS) for k, p in BARRIERS}
         self.sem = {}
@@ -500,7 +510,7 @@ def e2e_mutex(G, inputs, kind, reps=3):
                 for nm, sz in (("data", max(K, 1)), ("total", 1), ("log", n), ("ticket", n), ("count", NBLOCKS),
                                ("status", 1))}
         w = G.gsync_mutex_work(G.MUTEX_KINDS[kind], NBLOCKS, MUTEX_THREADS, MUTEX_ACQ, K,
-                               MUTEX_CLUSTER if kind == "cluster" else 0, hd.data_ptr(),
+                               mutex_cluster(kind), hd.data_ptr(),
                                ha.data_ptr(), outs["data"].data_ptr(), outs["total"].data_ptr(),
                                outs["log"].data_ptr(), outs["ticket"].data_ptr(), outs["count"].data_ptr(),
                                outs["status"].data_ptr())
@@ -643,7 +653,8 @@ def sweep_section(G, calc, inputs, runner, step):
     """Configs 2 and 3 over their grid sizes, as the paper's Section 6 curves are drawn (ops/s
     against the number of blocks).  The mutex configurations at 148, 296 and 592 blocks (1184
     is the timed step's), the barrier kinds at 148..1184 blocks (a cluster grid rounded down to
-    a multiple of its cluster size), both semaphore kinds at 296 and 592 blocks; each a median
+    a multiple of its cluster size, for the cluster mutexes too: 144 blocks in clusters of 8 at
+    148), both semaphore kinds at 296 and 592 blocks; each a median
     of 3 launches with L2 flushed before each, and each result checked against the oracle."""
     out = {"grids": list(SWEEP_GRIDS), "mutex_acq_per_s": {}, "barrier_ns_per_crossing": {}, "semaphore_ops_per_s": {},
            "l2": "flushed (512 MiB write) before each launch", "parity": "ok"}
@@ -652,15 +663,17 @@ def sweep_section(G, calc, inputs, runner, step):
         for K in CS_SIZES:
             row = out["mutex_acq_per_s"].setdefault(name, {}).setdefault(str(K), {})
             for B in SWEEP_GRIDS[:-1]:
-                delay, add = inputs.mutex_inputs(B, MUTEX_ACQ, inputs.mutex_seed(G.MUTEX_KINDS[kind], B, K))
+                c = mutex_cluster(kind)
+                nb = B - B % c if c else B  # a cluster grid rounded down to a multiple of its cluster size
+                delay, add = inputs.mutex_inputs(nb, MUTEX_ACQ, inputs.mutex_seed(G.MUTEX_KINDS[kind], nb, K))
                 bo = runner.backoff(policy=policy, min_ns=bo_ns[0], max_ns=bo_ns[1], spin=spin) if bo_ns else None
-                mr = runner.MutexRun(kind, B, MUTEX_THREADS, MUTEX_ACQ, K, delay, add, bo=bo, timeout_ns=TIMEOUT_NS,
-                                     cluster=MUTEX_CLUSTER)
+                mr = runner.MutexRun(kind, nb, MUTEX_THREADS, MUTEX_ACQ, K, delay, add, bo=bo, timeout_ns=TIMEOUT_NS,
+                                     cluster=c)
                 ms = _time_launch(mr.launch, mr.reset)
-                got, want = mr.results(), calc.mutex_final(B, MUTEX_ACQ, K, add)
+                got, want = mr.results(), calc.mutex_final(nb, MUTEX_ACQ, K, add)
                 if got["status"] or got["total"] != want["total"] or not np.array_equal(got["data"], want["data"]):
-                    bad.append(f"mutex {name} K={K} B={B}")
-                row[str(B)] = B * MUTEX_ACQ / (ms * 1e-3)
+                    bad.append(f"mutex {name} K={K} B={nb}")
+                row[str(nb)] = nb * MUTEX_ACQ / (ms * 1e-3)
     for kind, param in SWEEP_BARRIERS:
         row = out["barrier_ns_per_crossing"].setdefault(barrier_name(kind, param), {})
         for B in SWEEP_GRIDS:
@@ -715,10 +728,11 @@ def condvar_section(calc, inputs, runner, terms):
                        f"per producer, queue capacity {CV_CAPACITY}, one mutex + two condition variables",
            "roof_items_per_s": roof, "T_cs_cv_ns": t_cs, "T_frame_cv_ns": t_frame, "mutex": {},
            "l2": "flushed (512 MiB write) before each timed run"}
-    for mutex, bo in (("ticket", (64, 2000)), ("cohort", (128, 4000)), ("cluster", (128, 4000))):
+    for mutex, bo in (("ticket", (64, 2000)), ("cohort", (128, 4000)), ("cluster", (128, 4000)),
+                      ("cluster_mcs", (128, 4000))):
         run = runner.CondVarRun(CV_PRODUCERS, CV_CONSUMERS, CV_ITEMS, CV_CAPACITY, value,
                                 bo=runner.backoff(min_ns=bo[0], max_ns=bo[1]), mutex=mutex,
-                                cluster=MUTEX_CLUSTER if mutex == "cluster" else 0)
+                                cluster=mutex_cluster(mutex))
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ms, ok = [], True
         for _ in range(4):
@@ -933,7 +947,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded SplitMix64 delays/addends/hold times)",
         "config": {"workload": f"mutex contention, {NBLOCKS} blocks x {MUTEX_THREADS} threads"
-                               f"{f' in clusters of {MUTEX_CLUSTER}' if DEFAULT_MUTEX == 'cluster' else ''}, {MUTEX_ACQ} "
+                               f"{f' in clusters of {mutex_cluster(DEFAULT_MUTEX)}' if mutex_cluster(DEFAULT_MUTEX) else ''}, {MUTEX_ACQ} "
                                f"acquisitions/block, CS {list(CS_SIZES)} int32 words, delays U{{0..2000}} cycles; "
                                f"+ barriers ({BAR_ROUNDS} rounds) and semaphores ({SEM_PAIRS} pairs) at {NBLOCKS} blocks",
                    "default_mutex": f"{DEFAULT_MUTEX} (backoff {MUTEX_BACKOFF.get(DEFAULT_MUTEX)} ns)",

@@ -62,9 +62,13 @@ typedef enum gsync_mutex_kind {
   GSYNC_MUTEX_RING = 5,        /* the paper's ring-buffer sleeping mutex (Section 5, design
                                   alternative): a waiter writes its block id at the ring's
                                   end and polls the head pointer and the entry it names */
-  GSYNC_MUTEX_CLUSTER = 6      /* cohort lock over thread-block clusters: a ticket lock per
+  GSYNC_MUTEX_CLUSTER = 6,     /* cohort lock over thread-block clusters: a ticket lock per
                                   cluster in distributed shared memory under a global ticket
                                   lock; needs a cluster launch (see gsync_mutex_init_cluster) */
+  GSYNC_MUTEX_CLUSTER_MCS = 7  /* the same with an MCS queue per cluster: each waiter spins in
+                                  its own shared memory and its predecessor pushes the grant
+                                  into it; needs a cluster launch (see
+                                  gsync_mutex_init_cluster_mcs) */
 } gsync_mutex_kind;
 
 /* Barrier kinds (Section 5, "Barrier"). */
@@ -147,6 +151,15 @@ int gsync_mutex_init_cohort(void* state, size_t bytes, int budget, const gsync_b
  * (gsync_launch_coresident with cluster > 1).  budget 1..32767; asynchronous on `stream`. */
 int gsync_mutex_init_cluster(void* state, size_t bytes, int budget, const gsync_backoff* backoff,
                              uint64_t timeout_ns, void* stream);
+
+/* Cluster MCS mutex (GSYNC_MUTEX_CLUSTER_MCS): the cluster cohort lock whose local lock is an
+ * MCS queue (Mellor-Crummey and Scott, 1991).  Each block's node is a gsync::McsNode the kernel
+ * declares __shared__ and hands to gsync::mutex_attach_cluster_mcs at its start (all threads);
+ * the kernel calls gsync::mutex_cluster_end() before exiting and is launched with clusters.
+ * A waiter spins on its own node; its predecessor writes the grant into it.  state holds the
+ * global ticket lock (3 lines); budget 1..32767 as for CLUSTER; asynchronous on `stream`. */
+int gsync_mutex_init_cluster_mcs(void* state, size_t bytes, int budget, const gsync_backoff* backoff,
+                                 uint64_t timeout_ns, void* stream);
 
 /* The device's SM-to-die map: die_of_sm (host, >= sm_count bytes) receives 0 or 1 per SM id
  * (die 0 = the SMs near a fixed line of the library's static memory), *ndies_out 1 or 2.
@@ -318,7 +331,7 @@ int gsync_bench_barrier_static(const gsync_barrier_work* w, int param, uint64_t 
  * two of the buffers may overlap. */
 typedef struct gsync_mutex_work {
   int32_t kind, nblocks, block_threads, acq, cs_words;
-  int32_t cluster; /* GSYNC_MUTEX_CLUSTER: blocks per cluster (2..8, divides nblocks); else 0 or 1 */
+  int32_t cluster; /* CLUSTER, CLUSTER_MCS: blocks per cluster (2..8, divides nblocks); else 0 or 1 */
   const uint32_t* delay;
   const uint32_t* addend;
   uint32_t* data;
@@ -374,9 +387,9 @@ int gsync_bench_sem(void* state, const gsync_sem_work* w, void* stream);
  * status bits as for the other workloads. */
 typedef struct gsync_condvar_work {
   int32_t producers, consumers, items_per_producer, capacity, block_threads;
-  int32_t mutex_kind; /* the queue's mutex: GSYNC_MUTEX_TICKET, GSYNC_MUTEX_COHORT or
-                         GSYNC_MUTEX_CLUSTER */
-  int32_t cluster;    /* GSYNC_MUTEX_CLUSTER: blocks per cluster, 2..8, dividing producers +
+  int32_t mutex_kind; /* the queue's mutex: GSYNC_MUTEX_TICKET, GSYNC_MUTEX_COHORT,
+                         GSYNC_MUTEX_CLUSTER or GSYNC_MUTEX_CLUSTER_MCS */
+  int32_t cluster;    /* CLUSTER, CLUSTER_MCS: blocks per cluster, 2..8, dividing producers +
                          consumers (0 = 4); ignored by the other kinds */
   const uint32_t* value;
   uint32_t* seen;

@@ -327,11 +327,24 @@ __device__ __forceinline__ uint64_t header_timeout(const uint32_t* s) {
 // CLUSTER: the same protocol with the thread-block cluster as the group: lines 1-2 hold the
 //   global ticket lock and each cluster's local lock is a ClusterLocal in the shared memory
 //   of the cluster's block 0 (see mutex_attach_cluster).
+// CLUSTER_MCS: lines 1-2 the global ticket lock; the cluster's local lock is an MCS queue of
+//   McsNode, one in each block's shared memory (see mutex_attach_cluster_mcs).
 // The local lock of a CLUSTER mutex, declared __shared__ by the kernel.
 struct ClusterLocal {
   uint32_t next;
   uint32_t pad;
   uint64_t turn;  // {served ticket (low 32), cohort word (high 32)}
+};
+// CLUSTER_MCS: each block's node of the cluster's MCS queue, declared __shared__ by the kernel
+// (see mutex_attach_cluster_mcs).  Block 0's `tail` names the last block to queue; every
+// block's `link` is written by its successor and `rec` by its predecessor, and `seq` counts
+// the block's own queueings (only its thread 0 touches it).
+struct McsNode {
+  uint32_t tail;  // block 0 only: (rank + 1) | seq << 4 of the last block to queue, 0 = free
+  uint32_t seq;
+  uint64_t link;  // successor's rank | successor's seq << 4 | this block's seq << 32
+  uint64_t rec;   // the grant: seq (bits 0-15) | owned (16) | passes (17-31) | global ticket (32-47)
+  uint64_t pad;
 };
 
 struct MutexRef {
@@ -342,6 +355,8 @@ struct MutexRef {
   uint32_t* local;  // COHORT: this block's die's local lock (counter line, then turn line)
   uint32_t die;     // COHORT: the die of this block's SM (0 or 1)
   ClusterLocal* cl; // CLUSTER: the cluster's local lock (in block 0's shared memory)
+  McsNode* mcs;     // CLUSTER_MCS: this block's own node
+  uint32_t* mcs_tail;  // CLUSTER_MCS: the cluster's tail (in block 0's shared memory)
   __device__ __forceinline__ uint32_t* lockw() const { return s + 1 * kLineWords; }
   __device__ __forceinline__ uint32_t* turn() const { return s + 2 * kLineWords; }
   __device__ __forceinline__ uint32_t* flag(uint32_t t) const { return s + (3 + (t & qmask)) * kLineWords; }
@@ -363,6 +378,8 @@ __device__ __forceinline__ MutexRef mutex_attach(void* state) {
   m.timeout_ns = header_timeout(m.s);
   m.local = nullptr;
   m.cl = nullptr;
+  m.mcs = nullptr;
+  m.mcs_tail = nullptr;
   m.die = 0;
   if (m.kind == GSYNC_MUTEX_COHORT) {
     const uint32_t sm = ptx::smid();
@@ -390,6 +407,24 @@ __device__ __forceinline__ MutexRef mutex_attach_cluster(void* state, ClusterLoc
 }
 __device__ __forceinline__ void mutex_cluster_end() { ptx::cluster_sync(); }
 
+// CLUSTER_MCS mutex: every thread of every block of the (cluster-launched) grid calls this at
+// the kernel's start with the same __shared__ McsNode; each block clears its own node, and the
+// hardware cluster barrier makes the nodes ready before anyone queues.  The kernel must call
+// mutex_cluster_end() before any of its blocks exits (its node is written by its neighbours).
+__device__ __forceinline__ MutexRef mutex_attach_cluster_mcs(void* state, McsNode* node) {
+  MutexRef m = mutex_attach(state);
+  if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
+    node->tail = 0u;
+    node->seq = 0u;
+    node->link = 0ull;
+    node->rec = 0ull;
+  }
+  m.mcs = node;
+  m.mcs_tail = &ptx::map_cluster_rank(node, 0u)->tail;
+  ptx::cluster_sync();
+  return m;
+}
+
 // Result of a lock: the status, the ticket the holder needs to unlock, and (COHORT) the
 // cohort word -- passes within the die so far (bits 30..16) and the global ticket (15..0) --
 // and the die's ticket counter as read right after the lock was taken.
@@ -406,6 +441,8 @@ enum : uint32_t { kRingEmpty = 0xFFFFFFFFu };
 // COHORT local turn word: bit 31 of the high half says the cohort already holds the global
 // lock (the next local holder inherits it instead of queueing for it).
 enum : uint32_t { kCohortOwned = 0x80000000u };
+// CLUSTER_MCS record: bit 16 says the cluster already holds the global lock.
+constexpr uint64_t kMcsOwned = 1ull << 16;
 
 // Master-thread lock.  Returns the ticket (ticket kinds) in tok.ticket.
 template <int KIND>
@@ -489,6 +526,32 @@ __device__ __forceinline__ Token mutex_lock_thread(const MutexRef& m) {
       if (m.bo.min_ns) __nanosleep(m.bo.min_ns);
     }
     return {GSYNC_OK, t, g, ptx::ld_relaxed_cluster(&m.cl->next)};
+  } else if (KIND == GSYNC_MUTEX_CLUSTER_MCS) {
+    // The cohort protocol with an MCS queue (Mellor-Crummey and Scott, 1991) as the cluster's
+    // local lock: swap this block into the cluster's tail, link into the predecessor's node,
+    // and spin on a record in this block's own shared memory, which the predecessor pushes
+    // with a cluster-scope release.  Nothing is reset between rounds: the node's link and
+    // record carry sequence numbers (this block's count of queueings) and are checked
+    // against them.  A grant that is not owned (or a free queue) sends the block on to the
+    // global ticket lock, as in CLUSTER.
+    const uint32_t me = ptx::cluster_ctarank();
+    const uint32_t seq = ++m.mcs->seq;
+    const uint32_t prev = ptx::atom_exch_relaxed_cluster(m.mcs_tail, (me + 1u) | (seq << 4));
+    if (prev != 0u) {
+      McsNode* pn = ptx::map_cluster_rank(m.mcs, (prev & 0xFu) - 1u);
+      ptx::st_relaxed_cluster_u64(&pn->link, (uint64_t)me | ((uint64_t)seq << 4) | ((uint64_t)(prev >> 4) << 32));
+      uint64_t r;
+      while ((((uint32_t)(r = ptx::ld_acquire_cluster_u64(&m.mcs->rec))) ^ seq) & 0xFFFFu) {
+        if (int rc = w.tick(m.timeout_ns, m.abort_word())) return {rc, seq, 0u};
+      }
+      if (r & kMcsOwned) return {GSYNC_OK, seq, (uint32_t)(r >> 32) | (((uint32_t)(r >> 17) & 0x7FFFu) << 16), 0u};
+    }
+    const uint32_t g = ptx::atom_add_relaxed(m.lockw(), 1u) & 0xFFFFu;
+    while ((ptx::ld_acquire(m.turn()) & 0xFFFFu) != g) {
+      if (int rc = w.tick(m.timeout_ns, m.abort_word())) return {rc, seq, 0u};
+      if (m.bo.min_ns) __nanosleep(m.bo.min_ns);
+    }
+    return {GSYNC_OK, seq, g, 0u};
   } else if (KIND == GSYNC_MUTEX_RING) {
     // Ring-buffer sleeping mutex (Section 5, design alternative): claim the ring's end with a
     // fetch-and-add on the tail, write this block's id there, then poll the head pointer and
@@ -552,6 +615,30 @@ __device__ __forceinline__ void mutex_unlock_thread(const MutexRef& m, const Tok
       ptx::st_release(m.turn(), (g + 1u) & 0xFFFFu);
       ptx::st_release_cluster_u64(&m.cl->turn, (uint64_t)(ticket + 1u));
     }
+  } else if (KIND == GSYNC_MUTEX_CLUSTER_MCS) {
+    // Pass to the linked successor (owned: the global lock stays with the cluster) while the
+    // budget allows; else release the global lock, then free the cluster's queue: push a
+    // record that is not owned to the successor, or swap the tail back to empty if it still
+    // names this block, or else wait (bounded) for the successor that swapped in to link.
+    const uint32_t passes = (tok.cohort >> 16) & 0x7FFFu, g = tok.cohort & 0xFFFFu, seq = ticket;
+    uint64_t link = ptx::ld_relaxed_cluster_u64(&m.mcs->link);
+    bool linked = (uint32_t)(link >> 32) == seq;
+    if (linked && pass_local && passes + 1u < m.budget()) {
+      McsNode* sn = ptx::map_cluster_rank(m.mcs, (uint32_t)link & 0xFu);
+      ptx::st_release_cluster_u64(&sn->rec, (uint64_t)(((uint32_t)link >> 4) & 0xFFFFu) | kMcsOwned |
+                                                ((uint64_t)(passes + 1u) << 17) | ((uint64_t)g << 32));
+      return;
+    }
+    ptx::st_release(m.turn(), (g + 1u) & 0xFFFFu);
+    if (!linked) {
+      const uint32_t mine = (ptx::cluster_ctarank() + 1u) | (seq << 4);
+      if (ptx::atom_cas_relaxed_cluster(m.mcs_tail, mine, 0u) == mine) return;
+      Waiter w;
+      while ((uint32_t)((link = ptx::ld_relaxed_cluster_u64(&m.mcs->link)) >> 32) != seq)
+        if (w.tick(m.timeout_ns, m.abort_word())) return;  // the successor times out in turn
+    }
+    McsNode* sn = ptx::map_cluster_rank(m.mcs, (uint32_t)link & 0xFu);
+    ptx::st_relaxed_cluster_u64(&sn->rec, (uint64_t)(((uint32_t)link >> 4) & 0xFFFFu));
   } else if (KIND == GSYNC_MUTEX_RING) {
     // Clear this block's entry before moving the head past it, so that no block can match
     // its own id left over from an earlier lap of the ring.
@@ -565,7 +652,8 @@ __device__ __forceinline__ void mutex_unlock_thread(const MutexRef& m, const Tok
 // Ticket-only form for the kinds whose unlock needs nothing but the ticket.
 template <int KIND>
 __device__ __forceinline__ void mutex_unlock_thread(const MutexRef& m, uint32_t ticket) {
-  static_assert(KIND != GSYNC_MUTEX_COHORT && KIND != GSYNC_MUTEX_CLUSTER, "a cohort unlock needs the whole Token");
+  static_assert(KIND != GSYNC_MUTEX_COHORT && KIND != GSYNC_MUTEX_CLUSTER && KIND != GSYNC_MUTEX_CLUSTER_MCS,
+                "a cohort unlock needs the whole Token");
   mutex_unlock_thread<KIND>(m, Token{GSYNC_OK, ticket, 0u, 0u});
 }
 
@@ -642,7 +730,7 @@ __device__ __forceinline__ int cond_wait_thread(const CondRef& cv, const MutexRe
   // the lock only to wait in turn, keeping it from the blocks that could signal.  A die holds
   // half the grid, of mixed roles, and the two-die cohort lock keeps passing within the die
   // (measured faster on the producer/consumer workload; the cluster lock gains ~25 % here).
-  mutex_unlock_thread<MKIND>(m, tok, MKIND != GSYNC_MUTEX_CLUSTER);
+  mutex_unlock_thread<MKIND>(m, tok, MKIND != GSYNC_MUTEX_CLUSTER && MKIND != GSYNC_MUTEX_CLUSTER_MCS);
   Waiter w;
   uint32_t sleep_ns = cv.bo.min_ns;
   while (!after(ptx::ld_acquire(cv.signals()), t)) {

@@ -20,6 +20,7 @@ The algorithms follow Section 5 ("Design") and the pseudocode of the Appendix:
   QueueMutex    sleep-waiting queue lock: each waiter polls its own slot of a ring of flags
   RingMutex     the paper's ring-buffer sleeping mutex (Section 5, "design alternative")
   CohortMutex   two-die cohort lock: a ticket lock per die under a global ticket lock
+  McsCohortMutex    the cluster cohort lock with an MCS queue per cluster (pushed grants)
   CarryCohortMutex  the cohort lock whose records carry the guarded data (batched kernel)
   CarryMcsHierMutex the same over three levels: an MCS queue per cluster, a ticket lock per
                     die, a global ticket lock (batched kernel)
@@ -730,6 +731,124 @@ class CarryMcsHierMutex:
                 return loc, sh, None
             sp, sseq = nxt
             return finish(), put(N0 + 2 * sp + 1, ((sseq & self.M16, None, out),)), None
+        raise AssertionError(pc)
+
+
+class McsCohortMutex:
+    """Cluster cohort lock whose local level is an MCS queue (Mellor-Crummey and Scott, 1991)
+    with pushed grants: the mutex kind GSYNC_MUTEX_CLUSTER_MCS (a GB300 design, not in the
+    paper).  The global level is a ticket lock, as in CohortMutex.
+
+    The cluster's tail holds (block, seq) of the last block to queue, or None when the cluster
+    lock is free.  A block queues with seq = its own count of queueings plus one: it swaps
+    itself into the tail; if the tail was None it holds the cluster lock (not owned) and takes
+    a global ticket; else it links itself into its predecessor's node, link = (block, seq,
+    predecessor's seq), and polls its own node's record until the record's seq is its own.  The
+    holder passes the lock by writing (successor's seq, owned word or None) into its linked
+    successor's node: owned (the global lock stays with the cluster) while the budget allows,
+    else it releases the global lock first and pushes a record that is not owned.  Without a
+    linked successor it releases the global lock and swaps the tail back to None if the tail
+    still names it, else waits for the link.  Records and links are checked against the seq
+    they carry and never reset.  Mutual exclusion is checked on the critical section.
+    broken="no_seq_check", "stale_link" and "no_cas" as in CarryMcsHierMutex;
+    broken="owned_after_release": a holder that released the global lock still pushes an
+    owned record.
+    """
+    kind, capacity, fifo = "mutex", 1, False
+    M16 = 0xFFFF
+
+    def __init__(self, cluster_of=(0, 0, 1), budget=2, broken=None):
+        self.cluster_of, self.budget, self.broken = tuple(cluster_of), budget, broken
+        self.nc = max(self.cluster_of) + 1
+
+    def init(self, nproc, ops):
+        # nodes (link, record) per block; tails per cluster; (gnext, gturn)
+        return (None, None) * nproc + (None,) * self.nc + (0, 0), \
+            tuple((0, 0, 0, None, 0, 0) for _ in range(nproc))
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, seq, succ, cp, g = loc
+        c = self.cluster_of[p]
+        T0 = 2 * nproc
+        G = T0 + self.nc
+        link, rec = sh[2 * p], sh[2 * p + 1]
+        tail = sh[T0 + c]
+        gnext, gturn = sh[G], sh[G + 1]
+
+        def put(i, vals):
+            return sh[:i] + vals + sh[i + len(vals):]
+
+        def L(**kw):
+            v = dict(pc=pc, k=k, seq=seq, succ=succ, cp=cp, g=g)
+            v.update(kw)
+            return (v["pc"], v["k"], v["seq"], v["succ"], v["cp"], v["g"])
+
+        def finish():
+            k2 = k + 1
+            return L(pc=(0 if k2 < ops else DONE), k=k2, succ=None)
+
+        def linked():
+            if link is None:
+                return None
+            sp, sseq, pseq = link
+            if pseq != seq and self.broken != "stale_link":
+                return None
+            return (sp, sseq)
+
+        if pc == 0:  # swap into the tail
+            seq2 = seq + 1
+            if tail is None:
+                return L(pc=2, seq=seq2, cp=0), put(T0 + c, ((p, seq2),)), None
+            return L(pc=1, seq=seq2, succ=tail), put(T0 + c, ((p, seq2),)), None
+        if pc == 1:  # link into the predecessor's node
+            pp, pseq = succ
+            return L(pc=20, succ=None), put(2 * pp, ((p, seq, pseq),)), None
+        if pc == 20:  # poll this block's own record
+            if rec is None or (rec[0] != seq & self.M16 and self.broken != "no_seq_check"):
+                return loc, sh, None
+            if rec[1] is not None:
+                _, cp2, g2 = rec[1]
+                return L(pc=PC_ENTER, cp=cp2, g=g2), sh, None
+            return L(pc=2, cp=0), sh, None
+        if pc == 2:  # global ticket
+            return L(pc=3, g=gnext & self.M16), put(G, (inc(gnext),)), None
+        if pc == 3:
+            if gturn & self.M16 != g:
+                return loc, sh, None
+            return L(pc=PC_ENTER, cp=0), sh, None
+        if pc == PC_ENTER:
+            return L(pc=PC_EXIT), sh, ("enter", None)
+        if pc == PC_EXIT:
+            return L(pc=6), sh, ("exit",)
+        if pc == 6:  # one read of this block's link
+            nxt = linked()
+            if nxt is not None and cp + 1 < self.budget:
+                return L(pc=7, succ=nxt), sh, None
+            return L(pc=10, succ=nxt), sh, None
+        if pc == 7:  # pass within the cluster: the global lock stays
+            sp, sseq = succ
+            return finish(), put(2 * sp + 1, ((sseq & self.M16, ("own", cp + 1, g)),)), None
+        if pc == 10:  # release the global lock
+            return L(pc=11), put(G + 1, (inc(gturn),)), None
+        if pc == 11:  # free the cluster: push a record that is not owned, or free the tail
+            nxt = succ if succ is not None else linked()
+            if nxt is not None:
+                sp, sseq = nxt
+                word = ("own", cp + 1, g) if self.broken == "owned_after_release" else None
+                return finish(), put(2 * sp + 1, ((sseq & self.M16, word),)), None
+            return L(pc=13), sh, None
+        if pc == 13:
+            if self.broken == "no_cas":
+                return finish(), sh, None
+            if tail == (p, seq):
+                return finish(), put(T0 + c, (None,)), None
+            return L(pc=14), sh, None
+        if pc == 14:
+            nxt = linked()
+            if nxt is None:
+                return loc, sh, None
+            sp, sseq = nxt
+            return finish(), put(2 * sp + 1, ((sseq & self.M16, None),)), None
         raise AssertionError(pc)
 
 

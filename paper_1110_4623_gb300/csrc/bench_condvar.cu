@@ -28,6 +28,9 @@ __global__ void __launch_bounds__(kMaxThreads)
   if (MKIND == GSYNC_MUTEX_CLUSTER) {
     __shared__ gsync::ClusterLocal cluster_lock;
     m = gsync::mutex_attach_cluster(mutex_state, &cluster_lock);
+  } else if (MKIND == GSYNC_MUTEX_CLUSTER_MCS) {
+    __shared__ gsync::McsNode node;
+    m = gsync::mutex_attach_cluster_mcs(mutex_state, &node);
   } else {
     m = gsync::mutex_attach(mutex_state);
   }
@@ -97,7 +100,8 @@ __global__ void __launch_bounds__(kMaxThreads)
     sum[c] = my_sum;
     count[c] = taken;
   }
-  if (MKIND == GSYNC_MUTEX_CLUSTER) gsync::mutex_cluster_end();  // block 0's shared lock outlives every user
+  // the cluster's shared memory (block 0's lock, or every block's node) outlives every user
+  if (MKIND == GSYNC_MUTEX_CLUSTER || MKIND == GSYNC_MUTEX_CLUSTER_MCS) gsync::mutex_cluster_end();
 }
 
 size_t round_up(size_t n) { return (n + 255) & ~(size_t)255; }
@@ -155,7 +159,7 @@ __global__ void __launch_bounds__(kMaxThreads)
 // The mutex sits first in the workspace and takes the largest of the kinds' sizes.
 size_t mutex_region() {
   size_t n = 0;
-  for (int kind : {GSYNC_MUTEX_TICKET, GSYNC_MUTEX_COHORT, GSYNC_MUTEX_CLUSTER}) {
+  for (int kind : {GSYNC_MUTEX_TICKET, GSYNC_MUTEX_COHORT, GSYNC_MUTEX_CLUSTER, GSYNC_MUTEX_CLUSTER_MCS}) {
     const size_t k = gsync_mutex_bytes(kind, 1);
     n = k > n ? k : n;
   }
@@ -176,12 +180,10 @@ extern "C" int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_back
   const int64_t items = (int64_t)w->producers * w->items_per_producer;
   if (items > (1ll << 30) || items % w->consumers) return GSYNC_EINVAL;
   if (!w->value || !w->seen || !w->sum || !w->count || !w->status) return GSYNC_EINVAL;
-  if (w->mutex_kind != GSYNC_MUTEX_TICKET && w->mutex_kind != GSYNC_MUTEX_COHORT &&
-      w->mutex_kind != GSYNC_MUTEX_CLUSTER)
-    return GSYNC_EINVAL;
-  const int cluster = w->mutex_kind != GSYNC_MUTEX_CLUSTER ? 1 : w->cluster ? w->cluster : 4;
-  if ((w->mutex_kind == GSYNC_MUTEX_CLUSTER && (cluster < 2 || cluster > 8)) || (w->producers + w->consumers) % cluster)
-    return GSYNC_EINVAL;
+  const bool clustered = w->mutex_kind == GSYNC_MUTEX_CLUSTER || w->mutex_kind == GSYNC_MUTEX_CLUSTER_MCS;
+  if (w->mutex_kind != GSYNC_MUTEX_TICKET && w->mutex_kind != GSYNC_MUTEX_COHORT && !clustered) return GSYNC_EINVAL;
+  const int cluster = !clustered ? 1 : w->cluster ? w->cluster : 4;
+  if ((clustered && (cluster < 2 || cluster > 8)) || (w->producers + w->consumers) % cluster) return GSYNC_EINVAL;
   const size_t need = gsync_bench_condvar_workspace_bytes(w->capacity);
   if (need == 0 || !workspace || workspace_bytes < need || !aligned(workspace, 256)) return GSYNC_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
@@ -201,9 +203,10 @@ extern "C" int gsync_bench_condvar(const gsync_condvar_work* w, const gsync_back
   GSYNC_CUDA(cudaMemcpyAsync(q, &q0, sizeof q0, cudaMemcpyHostToDevice, st));
   GSYNC_CUDA(cudaStreamSynchronize(st));  // q0 lives on this stack frame
   const int items_per_consumer = (int)(items / w->consumers);
-  auto kernel = w->mutex_kind == GSYNC_MUTEX_COHORT    ? condvar_workload_kernel<GSYNC_MUTEX_COHORT>
-                : w->mutex_kind == GSYNC_MUTEX_CLUSTER ? condvar_workload_kernel<GSYNC_MUTEX_CLUSTER>
-                                                       : condvar_workload_kernel<GSYNC_MUTEX_TICKET>;
+  auto kernel = w->mutex_kind == GSYNC_MUTEX_COHORT        ? condvar_workload_kernel<GSYNC_MUTEX_COHORT>
+                : w->mutex_kind == GSYNC_MUTEX_CLUSTER     ? condvar_workload_kernel<GSYNC_MUTEX_CLUSTER>
+                : w->mutex_kind == GSYNC_MUTEX_CLUSTER_MCS ? condvar_workload_kernel<GSYNC_MUTEX_CLUSTER_MCS>
+                                                           : condvar_workload_kernel<GSYNC_MUTEX_TICKET>;
   return launch_coresident(kernel, w->producers + w->consumers, w->block_threads, cluster, 0, st, mstate, nf, ne, q, buf,
                            w->producers, w->items_per_producer, items_per_consumer, w->value, w->seen, w->sum,
                            w->count, w->status, w->acquisitions);

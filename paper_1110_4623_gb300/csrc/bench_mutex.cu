@@ -68,6 +68,9 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
   if (KIND == GSYNC_MUTEX_CLUSTER) {
     __shared__ gsync::ClusterLocal cluster_lock;
     m = gsync::mutex_attach_cluster(state, &cluster_lock);
+  } else if (KIND == GSYNC_MUTEX_CLUSTER_MCS) {
+    __shared__ gsync::McsNode node;
+    m = gsync::mutex_attach_cluster_mcs(state, &node);
   } else if (KIND >= 0) {
     m = gsync::mutex_attach(state);
   }
@@ -108,10 +111,12 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
         gsync::ptx::atom_or_relaxed(status, GSYNC_STATUS_VIOLATION);
       }
       // COHORT: tickets are per die; bit 31 records the die so the host can check each
-      // die's grants in ticket order.
-      ticket_out[id] = KIND == GSYNC_MUTEX_COHORT    ? (m.die << 31) | (t.ticket & 0x7FFFFFFFu)
-                       : KIND == GSYNC_MUTEX_CLUSTER ? ((b / gsync::ptx::cluster_nctarank()) << 20) | (t.ticket & 0xFFFFFu)
-                                                     : t.ticket;
+      // die's grants in ticket order.  CLUSTER_MCS has no cluster-wide ticket (its queue order
+      // is the order of the tail swaps): it records none.
+      ticket_out[id] = KIND == GSYNC_MUTEX_COHORT        ? (m.die << 31) | (t.ticket & 0x7FFFFFFFu)
+                       : KIND == GSYNC_MUTEX_CLUSTER     ? ((b / gsync::ptx::cluster_nctarank()) << 20) | (t.ticket & 0xFFFFFu)
+                       : KIND == GSYNC_MUTEX_CLUSTER_MCS ? 0xFFFFFFFFu
+                                                         : t.ticket;
     }
     if (KIND != kFrameOnly) cs_store<WIDE>(data, (uint32_t)cs_words, v, x);
     // ---- end of critical section ----
@@ -124,7 +129,8 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
     ++done;
   }
   if (tid == 0) count[b] = done;
-  if (KIND == GSYNC_MUTEX_CLUSTER) gsync::mutex_cluster_end();  // block 0's shared lock outlives every user
+  // the cluster's shared memory (block 0's lock, or every block's node) outlives every user
+  if (KIND == GSYNC_MUTEX_CLUSTER || KIND == GSYNC_MUTEX_CLUSTER_MCS) gsync::mutex_cluster_end();
 }
 
 using KernelFn = void (*)(uint32_t*, int, int, const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*,
@@ -140,6 +146,7 @@ KernelFn pick_width(int kind) {
     case GSYNC_MUTEX_COHORT: return mutex_workload_kernel<GSYNC_MUTEX_COHORT, WIDE>;
     case GSYNC_MUTEX_RING: return mutex_workload_kernel<GSYNC_MUTEX_RING, WIDE>;
     case GSYNC_MUTEX_CLUSTER: return mutex_workload_kernel<GSYNC_MUTEX_CLUSTER, WIDE>;
+    case GSYNC_MUTEX_CLUSTER_MCS: return mutex_workload_kernel<GSYNC_MUTEX_CLUSTER_MCS, WIDE>;
   }
   return nullptr;
 }
@@ -152,7 +159,7 @@ int check_work(const gsync_mutex_work* w) {
       w->block_threads > kMaxThreads || w->block_threads % 32)
     return GSYNC_EINVAL;
   if ((uint64_t)w->nblocks * (uint64_t)w->acq >= (1ull << 31)) return GSYNC_EINVAL;
-  if (w->kind == GSYNC_MUTEX_CLUSTER) {
+  if (w->kind == GSYNC_MUTEX_CLUSTER || w->kind == GSYNC_MUTEX_CLUSTER_MCS) {
     // cluster ids and tickets must fit the recorded (cluster << 20) | ticket
     if (w->cluster < 2 || w->cluster > 8 || w->nblocks % w->cluster || w->nblocks / w->cluster > 4096 ||
         (uint64_t)w->cluster * (uint64_t)w->acq >= (1ull << 20))
@@ -163,7 +170,9 @@ int check_work(const gsync_mutex_work* w) {
   return GSYNC_OK;
 }
 
-int launch_cluster(const gsync_mutex_work* w) { return w->kind == GSYNC_MUTEX_CLUSTER ? w->cluster : 1; }
+int launch_cluster(const gsync_mutex_work* w) {
+  return w->kind == GSYNC_MUTEX_CLUSTER || w->kind == GSYNC_MUTEX_CLUSTER_MCS ? w->cluster : 1;
+}
 
 size_t round_up(size_t x) { return (x + 255) & ~(size_t)255; }
 

@@ -187,7 +187,7 @@ extern "C" {
 int gsync_last_cuda_error(void) { return g_last_cuda_error; }
 
 size_t gsync_mutex_bytes(int kind, int max_waiters) {
-  if (kind < GSYNC_MUTEX_CAS_SPIN || kind > GSYNC_MUTEX_CLUSTER || max_waiters < 1) return 0;
+  if (kind < GSYNC_MUTEX_CAS_SPIN || kind > GSYNC_MUTEX_CLUSTER_MCS || max_waiters < 1) return 0;
   if (max_waiters > (1 << 24)) return 0;
   if (kind == GSYNC_MUTEX_COHORT) return kCohortBytes;
   const bool queued = kind == GSYNC_MUTEX_SLEEP_QUEUE || kind == GSYNC_MUTEX_RING;
@@ -235,6 +235,17 @@ int place_on_dies(void* state, InitSpec& spec, cudaStream_t st) {
   return GSYNC_OK;
 }
 
+// CLUSTER and CLUSTER_MCS: the header and the global ticket lock (3 lines).
+int init_cluster_kind(uint32_t kind, void* state, size_t bytes, int budget, const gsync_backoff* backoff,
+                      uint64_t timeout_ns, void* stream) {
+  if (!state || !aligned(state, kLine) || bytes < 3 * kLine || budget < 1 || budget > 32767) return GSYNC_EINVAL;
+  if (backoff && backoff->policy > GSYNC_BACKOFF_SPIN_THEN_SLEEP) return GSYNC_EINVAL;
+  InitSpec spec;
+  fill_header(spec, kPrimMutex, kind, 0, (uint32_t)budget, backoff, timeout_ns, 0);
+  spec.nwords = 3 * kLine / 4;
+  return launch_init(state, bytes, spec, (cudaStream_t)stream);
+}
+
 }  // namespace
 
 extern "C" {
@@ -252,12 +263,12 @@ int gsync_mutex_init_cohort(void* state, size_t bytes, int budget, const gsync_b
 
 int gsync_mutex_init_cluster(void* state, size_t bytes, int budget, const gsync_backoff* backoff, uint64_t timeout_ns,
                              void* stream) {
-  if (!state || !aligned(state, kLine) || bytes < 3 * kLine || budget < 1 || budget > 32767) return GSYNC_EINVAL;
-  if (backoff && backoff->policy > GSYNC_BACKOFF_SPIN_THEN_SLEEP) return GSYNC_EINVAL;
-  InitSpec spec;
-  fill_header(spec, kPrimMutex, GSYNC_MUTEX_CLUSTER, 0, (uint32_t)budget, backoff, timeout_ns, 0);
-  spec.nwords = 3 * kLine / 4;
-  return launch_init(state, bytes, spec, (cudaStream_t)stream);
+  return init_cluster_kind(GSYNC_MUTEX_CLUSTER, state, bytes, budget, backoff, timeout_ns, stream);
+}
+
+int gsync_mutex_init_cluster_mcs(void* state, size_t bytes, int budget, const gsync_backoff* backoff,
+                                 uint64_t timeout_ns, void* stream) {
+  return init_cluster_kind(GSYNC_MUTEX_CLUSTER_MCS, state, bytes, budget, backoff, timeout_ns, stream);
 }
 
 int gsync_mutex_init(void* state, size_t bytes, int kind, int max_waiters, const gsync_backoff* backoff,
@@ -269,6 +280,8 @@ int gsync_mutex_init(void* state, size_t bytes, int kind, int max_waiters, const
     return gsync_mutex_init_cohort(state, bytes, GSYNC_COHORT_DEFAULT_BUDGET, backoff, timeout_ns, stream);
   if (kind == GSYNC_MUTEX_CLUSTER)
     return gsync_mutex_init_cluster(state, bytes, GSYNC_COHORT_DEFAULT_BUDGET, backoff, timeout_ns, stream);
+  if (kind == GSYNC_MUTEX_CLUSTER_MCS)
+    return gsync_mutex_init_cluster_mcs(state, bytes, GSYNC_COHORT_DEFAULT_BUDGET, backoff, timeout_ns, stream);
   const bool queued = kind == GSYNC_MUTEX_SLEEP_QUEUE || kind == GSYNC_MUTEX_RING;
   const uint32_t q = queued ? pow2_at_least((uint32_t)max_waiters) : 0;
   InitSpec spec;

@@ -18,7 +18,8 @@ GSYNC_OK, GSYNC_EINVAL, GSYNC_ENOTRESIDENT, GSYNC_ETIMEDOUT, GSYNC_ECUDA, GSYNC_
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOTRESIDENT", 3: "ETIMEDOUT", 4: "ECUDA", 5: "EABORTED"}
 GSYNC_STATUS_TIMEOUT, GSYNC_STATUS_ABORTED, GSYNC_STATUS_VIOLATION, GSYNC_STATUS_CONFIG = 1, 2, 4, 8
 
-MUTEX_KINDS = {"cas_spin": 0, "cas_backoff": 1, "ticket": 2, "sleep_queue": 3, "cohort": 4, "ring": 5, "cluster": 6}
+MUTEX_KINDS = {"cas_spin": 0, "cas_backoff": 1, "ticket": 2, "sleep_queue": 3, "cohort": 4, "ring": 5, "cluster": 6,
+               "cluster_mcs": 7}
 # Policy kinds of the batched kernel: the mutex kinds it runs, plus the ticket lock whose turn
 # line carries the guarded count and sum (GSYNC_BATCHED_TICKET_CARRY), and the cohort locks
 # with carrying records over the two dies (GSYNC_BATCHED_COHORT_CARRY), over thread-block
@@ -115,6 +116,8 @@ _SIG = {
     "gsync_device_topology": (ctypes.c_int, [u32p, ctypes.POINTER(ctypes.c_int), u32p]),
     "gsync_mutex_init_cluster": (ctypes.c_int, [u32p, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(gsync_backoff),
                                                 ctypes.c_uint64, u32p]),
+    "gsync_mutex_init_cluster_mcs": (ctypes.c_int, [u32p, ctypes.c_size_t, ctypes.c_int,
+                                                    ctypes.POINTER(gsync_backoff), ctypes.c_uint64, u32p]),
     "gsync_check_coresident": (ctypes.c_int, [u32p, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_int,
                                               ctypes.POINTER(ctypes.c_int)]),
     "gsync_launch_coresident": (ctypes.c_int, [u32p, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_int, u32p,
@@ -278,6 +281,11 @@ def gsync_mutex_init_cohort(state, nbytes, budget, backoff=None, timeout_ns=0, s
 def gsync_mutex_init_cluster(state, nbytes, budget, backoff=None, timeout_ns=0, stream=None) -> int:
     bo = ctypes.byref(backoff) if backoff is not None else None
     return lib().gsync_mutex_init_cluster(ptr(state), nbytes, budget, bo, timeout_ns, stream_handle(stream))
+
+
+def gsync_mutex_init_cluster_mcs(state, nbytes, budget, backoff=None, timeout_ns=0, stream=None) -> int:
+    bo = ctypes.byref(backoff) if backoff is not None else None
+    return lib().gsync_mutex_init_cluster_mcs(ptr(state), nbytes, budget, bo, timeout_ns, stream_handle(stream))
 
 
 def gsync_device_topology(die_of_sm, stream=None) -> tuple[int, int]:

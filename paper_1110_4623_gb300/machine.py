@@ -116,8 +116,10 @@ WINDOW_RTT_FRACTION = 0.25
 def design_extended(params: dict, ext: dict, nblocks: int = 1184) -> dict:
     """The Section 4 choice, then the GB300 extensions: a cohort lock on a two-die part whose
     cross-die hand-off is DIE_GAP_NS slower (mutex_without_clusters), and over thread-block
-    clusters when a hand-off through distributed shared memory beats the on-die L2 one and the
-    kernel can launch in clusters (mutex); the counting barrier when `nblocks` serialized
+    clusters when a hand-off through distributed shared memory (a flag pushed into the peer's
+    shared memory) beats the on-die L2 one and the kernel can launch in clusters (mutex: the
+    cluster cohort lock whose MCS queue pushes each grant that way); the counting barrier
+    when `nblocks` serialized
     same-word atomics cost less than the two hand-offs of the flag barrier's extra stage; the
     ticket-window semaphore when an atomic round trip exceeds WINDOW_RTT_FRACTION of the
     on-die hand-off."""
@@ -126,7 +128,7 @@ def design_extended(params: dict, ext: dict, nblocks: int = 1184) -> dict:
         choice["mutex"] = "cohort"
     choice["mutex_without_clusters"] = choice["mutex"]
     if ext.get("handoff_dsmem_ns", float("inf")) < ext["handoff_near_ns"]:
-        choice["mutex"] = "cluster"
+        choice["mutex"] = "cluster_mcs"
     if nblocks * ext["atomic_same_ns"] < 2.0 * ext["handoff_near_ns"]:
         choice["barrier"] = "count"
     if ext.get("atomic_rtt_ns", 0.0) > WINDOW_RTT_FRACTION * ext["handoff_near_ns"]:

@@ -143,7 +143,7 @@ class MutexRun:
                  delay: np.ndarray | None, addend: np.ndarray, bo: G.gsync_backoff | None = None,
                  timeout_ns: int = 0, budget: int | None = None, cluster: int = 8):
         self.kind, self.k = kind, G.MUTEX_KINDS[kind]
-        self.cluster = cluster if kind == "cluster" else 0
+        self.cluster = cluster if kind in ("cluster", "cluster_mcs") else 0
         self.nblocks, self.acq, self.cs_words = nblocks, acq, cs_words
         self.bo = bo
         n = nblocks * acq
@@ -152,6 +152,9 @@ class MutexRun:
         if budget is not None and kind == "cluster":
             G.check("gsync_mutex_init_cluster", G.gsync_mutex_init_cluster(self.state, self.nbytes, budget, bo,
                                                                           timeout_ns))
+        elif budget is not None and kind == "cluster_mcs":
+            G.check("gsync_mutex_init_cluster_mcs", G.gsync_mutex_init_cluster_mcs(self.state, self.nbytes, budget, bo,
+                                                                                  timeout_ns))
         elif budget is not None:
             G.check("gsync_mutex_init_cohort", G.gsync_mutex_init_cohort(self.state, self.nbytes, budget, bo, timeout_ns))
         else:

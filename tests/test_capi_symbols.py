@@ -88,7 +88,8 @@ def test_size_queries_without_gpu(lib_path):
     # ring: header, tail, head, one line per entry (a power of two >= the waiters)
     assert G.gsync_mutex_bytes(G.MUTEX_KINDS["ring"], 1184) == (3 + 2048) * 128
     assert G.gsync_mutex_bytes(G.MUTEX_KINDS["cluster"], 4) == 3 * 128  # the global lock; local locks live in smem
-    assert G.gsync_mutex_bytes(7, 4) == 0
+    assert G.gsync_mutex_bytes(G.MUTEX_KINDS["cluster_mcs"], 4) == 3 * 128  # nodes live in smem
+    assert G.gsync_mutex_bytes(8, 4) == 0
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["cluster"], 1183, 8) == 0
     assert G.gsync_sem_bytes(0) == 4 * 128 and G.gsync_sem_bytes(3) == 4 * 128 and G.gsync_sem_bytes(4) == 0
     assert G.gsync_bench_mutex_workspace_bytes(2, 1184, 100, 1024) > 4 * 1184 * 100 * 4

@@ -44,21 +44,24 @@ def test_producer_consumer_on_the_cohort_lock(producers, consumers, items, capac
     check(producers, consumers, items, capacity, mutex="cohort", bo=runner.backoff(min_ns=128, max_ns=4000))
 
 
+@pytest.mark.parametrize("mutex", ["cluster", "cluster_mcs"])
 @pytest.mark.parametrize("producers,consumers,items,capacity,cluster", [
     (1, 1, 100, 1, 2), (592, 592, 100, 16, 4), (592, 592, 100, 1, 8), (16, 4, 20, 3, 4), (37, 11, 33, 5, 2)])
-def test_producer_consumer_on_the_cluster_lock(producers, consumers, items, capacity, cluster):
+def test_producer_consumer_on_the_cluster_lock(mutex, producers, consumers, items, capacity, cluster):
     # Clusters mix producer and consumer blocks wherever producers is not a multiple of the
-    # cluster size; the cohort passes the mutex between them inside the cluster.
+    # cluster size; the cohort passes the mutex between them inside the cluster (through block
+    # 0's ticket lock, or the MCS queue's pushed grants).
     from paper_1110_4623_gb300 import runner
-    check(producers, consumers, items, capacity, mutex="cluster", cluster=cluster,
+    check(producers, consumers, items, capacity, mutex=mutex, cluster=cluster,
           bo=runner.backoff(min_ns=128, max_ns=4000))
 
 
-def test_cluster_lock_needs_a_cluster_size_that_divides_the_grid():
+@pytest.mark.parametrize("mutex", ["cluster", "cluster_mcs"])
+def test_cluster_lock_needs_a_cluster_size_that_divides_the_grid(mutex):
     from paper_1110_4623_gb300 import gsync as G
     from paper_1110_4623_gb300 import runner
     for bad in (1, 3, 16):  # not a cluster, does not divide 8 blocks, above 8
-        r = runner.CondVarRun(4, 4, 4, 4, np.zeros(16, np.uint32), mutex="cluster", cluster=bad)
+        r = runner.CondVarRun(4, 4, 4, 4, np.zeros(16, np.uint32), mutex=mutex, cluster=bad)
         assert r.launch() == G.GSYNC_EINVAL
 
 

@@ -50,7 +50,7 @@ def test_extended_abstraction_measured_on_this_gpu():
         params = machine.abstraction(machine.measure_table(1184, 128, 1000, reps=1))
         got = machine.design_extended(params, ext)
         assert got["mutex_without_clusters"] == "cohort"
-        assert got["mutex"] == ("cluster" if ext["handoff_dsmem_ns"] < ext["handoff_near_ns"] else "cohort")
+        assert got["mutex"] == ("cluster_mcs" if ext["handoff_dsmem_ns"] < ext["handoff_near_ns"] else "cohort")
         window = ext["atomic_rtt_ns"] > machine.WINDOW_RTT_FRACTION * ext["handoff_near_ns"]
         assert got["sem_high"] == ("window" if window else machine.design(params)["sem_high"])
 
@@ -86,4 +86,4 @@ def test_machine_description_cli(tmp_path):
     assert all(v > 0 for v in d["cluster_barrier_ns"].values()) and all(v > 0 for v in d["fence_ns"].values())
     assert list(d["nanosleep_ns"]) == [str(n) for n in machine.SLEEP_NS]
     assert d["nanosleep_ns"]["8000"] > d["nanosleep_ns"]["100"]
-    assert d["design_extended"]["mutex"] in ("cluster", "cohort", "ticket", "cas_backoff")
+    assert d["design_extended"]["mutex"] in ("cluster_mcs", "cohort", "ticket", "cas_backoff")

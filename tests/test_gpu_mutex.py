@@ -143,6 +143,53 @@ def test_cluster_cohort_budgets(budget):
     assert calc.check_grant_log(got["log"], got["ticket"], 1184, 20, False, group_bits=12) == []
 
 
+@pytest.mark.parametrize("cluster", [2, 4, 8])
+@pytest.mark.parametrize("nblocks,cs_words", [(1184, 0), (1184, 64), (1184, 1024), (592, 64), (16, 7), (8, 1025)])
+def test_cluster_mcs_mutex(cluster, nblocks, cs_words):
+    # The cluster cohort lock with an MCS queue per cluster (grants pushed into each waiter's
+    # own shared memory), at the contention sweep's full shape and on ragged ones; its queue
+    # order is the order of the tail swaps, so no ticket order is recorded.
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    nb = nblocks - nblocks % cluster
+    acq = 100 if nb == 1184 else 50
+    seed = (inputs.mutex_seed(G.MUTEX_KINDS["cluster_mcs"], nb, cs_words) if nb == 1184
+            else 32_000 + cluster + nb + cs_words)
+    delay, add = inputs.mutex_inputs(nb, acq, seed)
+    got = runner.MutexRun("cluster_mcs", nb, 256, acq, cs_words, delay, add, cluster=cluster,
+                          timeout_ns=10_000_000_000, bo=runner.backoff(min_ns=128, max_ns=4000)).run()
+    want = calc.mutex_final(nb, acq, cs_words, add)
+    assert got["rc"] == 0 and got["status"] == 0, got["status"]
+    assert got["total"] == want["total"] and np.array_equal(got["data"], want["data"])
+    assert np.array_equal(got["count"], want["count"])
+    assert calc.check_grant_log(got["log"], None, nb, acq, False) == []
+
+
+@pytest.mark.parametrize("budget", [1, 2, 3, 32767])
+def test_cluster_mcs_budgets_and_reuse(budget):
+    # Budgets from "always release the global lock" to the maximum, and the same object and
+    # launch run twice: nodes live in shared memory and start afresh, the global lock goes on.
+    from paper_1110_4623_gb300 import runner
+    delay, add = inputs.mutex_inputs(1184, 20, 42_000 + budget, max_delay=300)
+    mr = runner.MutexRun("cluster_mcs", 1184, 256, 20, 64, delay, add, cluster=8, budget=budget,
+                         timeout_ns=10_000_000_000)
+    want = calc.mutex_final(1184, 20, 64, add)
+    for _ in range(2):
+        got = mr.run()
+        assert got["rc"] == 0 and got["status"] == 0 and np.array_equal(got["data"], want["data"])
+        assert calc.check_grant_log(got["log"], None, 1184, 20, False) == []
+
+
+def test_cluster_mcs_mutex_needs_a_cluster_size():
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    delay, add = inputs.mutex_inputs(64, 2, 5)
+    mr = runner.MutexRun("cluster_mcs", 64, 128, 2, 8, delay, add, cluster=8)
+    for bad in (1, 3, 16):  # not a cluster, does not divide 64, above 8
+        mr.work.cluster = bad
+        assert mr.launch() == G.GSYNC_EINVAL
+
+
 def test_cluster_mutex_needs_a_cluster_size():
     from paper_1110_4623_gb300 import gsync as G
     from paper_1110_4623_gb300 import runner

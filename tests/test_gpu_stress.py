@@ -1,7 +1,7 @@
 """Seeded repetitions of the GB300 designs across shapes and parameters (cohort and cluster
-cohort mutexes, counting barrier and the counting forms of the tree and cluster barriers,
-ticket-window semaphore, condition variables, serving loop),
-each checked exactly against the oracle: a net for races that one shape per test could miss."""
+cohort mutexes in both forms, counting barrier and the counting forms of the tree and cluster
+barriers, ticket-window semaphore, condition variables, serving loop), each checked exactly
+against the oracle: a net for races that one shape per test could miss."""
 import numpy as np
 import pytest
 
@@ -44,6 +44,23 @@ def test_cluster_mutex_repeated(i):
     want = calc.mutex_final(B, 20, K, add)
     assert got["status"] == 0 and got["total"] == want["total"] and np.array_equal(got["data"], want["data"])
     assert calc.check_grant_log(got["log"], got["ticket"], B, 20, False, group_bits=12) == []
+
+
+@pytest.mark.parametrize("i", range(30))
+def test_cluster_mcs_mutex_repeated(i):
+    # The MCS form of the cluster cohort lock over grids, sections, budgets, delays and sleeps
+    # (its queue order is the tail swaps', so only the grant log's validity is checked).
+    from paper_1110_4623_gb300 import runner
+    c = [8, 2, 4][i % 3]
+    B = [16, 296, 592, 1184, 1184][i % 5] // c * c
+    K = [0, 64, 1024, 7][i % 4]
+    budget = [1, 2, 64, 4096, 32767][i % 5]
+    delay, add = inputs.mutex_inputs(B, 20, 21_000 + i, max_delay=[0, 300, 2000][i % 3])
+    got = runner.MutexRun("cluster_mcs", B, 256, 20, K, delay, add, budget=budget, cluster=c, timeout_ns=10**10,
+                          bo=runner.backoff(min_ns=[0, 128][i % 2], max_ns=4000)).run()
+    want = calc.mutex_final(B, 20, K, add)
+    assert got["status"] == 0 and got["total"] == want["total"] and np.array_equal(got["data"], want["data"])
+    assert calc.check_grant_log(got["log"], None, B, 20, False) == []
 
 
 @pytest.mark.parametrize("i", range(30))
@@ -96,8 +113,9 @@ def test_condvar_repeated(i):
     from paper_1110_4623_gb300 import runner
     P, C, items = [(1, 1, 50), (8, 8, 20), (100, 50, 10), (592, 592, 40), (1100, 100, 10)][i % 5]
     v = inputs.condvar_inputs(P * items, 777 + i)
-    mutex = ["ticket", "cohort", "cluster"][i % 3]  # every grid here is even: clusters of 2 fit
-    got = runner.CondVarRun(P, C, items, [1, 2, 16, 64][i % 4], v, mutex=mutex, cluster=2 if mutex == "cluster" else 0,
+    mutex = ["ticket", "cohort", "cluster", "cluster_mcs"][i % 4]  # every grid here is even: clusters of 2 fit
+    got = runner.CondVarRun(P, C, items, [1, 2, 16, 64][i % 4], v, mutex=mutex,
+                            cluster=2 if mutex in ("cluster", "cluster_mcs") else 0,
                             bo=runner.backoff(min_ns=[0, 64][i % 2], max_ns=2000)).run()
     want = calc.condvar_final(v, P, items, C)
     assert got["rc"] == 0 and got["status"] == 0

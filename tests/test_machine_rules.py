@@ -36,7 +36,7 @@ def test_paper_machines_keep_the_paper_choice():
 def test_gb300_measurements_pick_cohort_and_count():
     params = machine.abstraction(times("tesla"))  # the atomic:volatile class GB300 falls in
     got = machine.design_extended(params, GB300, nblocks=1184)
-    assert got["mutex"] == "cluster" and got["mutex_without_clusters"] == "cohort" and got["barrier"] == "count"
+    assert got["mutex"] == "cluster_mcs" and got["mutex_without_clusters"] == "cohort" and got["barrier"] == "count"
     assert got["sem_low"] == got["sem_high"] == "window"
 
 
@@ -47,7 +47,7 @@ def test_each_extension_needs_its_own_condition():
     assert got["mutex"] == machine.design(params)["mutex"] and got["barrier"] == "count"
     # 4096 blocks x 0.64 ns = 2.6 us > 2 x 477 ns: the flag barrier's extra stage is cheaper
     got = machine.design_extended(params, GB300, nblocks=4096)
-    assert got["mutex"] == "cluster" and got["barrier"] == machine.design(params)["barrier"]
+    assert got["mutex"] == "cluster_mcs" and got["barrier"] == machine.design(params)["barrier"]
     # a cluster hand-off no faster than the on-die one: the die cohort stays the choice
     got = machine.design_extended(params, dict(GB300, handoff_dsmem_ns=500.0))
     assert got["mutex"] == "cohort"

@@ -30,6 +30,13 @@ CORRECT = [
     ("cohort_budget_3", mc.CohortMutex(budget=3), 3, 2),
     ("cohort_wrap", mc.CohortMutex(budget=2, base=W, gbase=0xFFFE), 3, 2),
     ("cohort_three_groups", mc.CohortMutex(budget=2, groups=3), 4, 2),
+    ("mcs_cohort_one_cluster", mc.McsCohortMutex(cluster_of=(0, 0, 0)), 3, 2),
+    ("mcs_cohort_two_clusters", mc.McsCohortMutex(cluster_of=(0, 0, 1)), 3, 2),
+    ("mcs_cohort_three_clusters", mc.McsCohortMutex(cluster_of=(0, 1, 2)), 3, 2),
+    ("mcs_cohort_four_blocks", mc.McsCohortMutex(cluster_of=(0, 0, 1, 1)), 4, 1),
+    ("mcs_cohort_budget_1", mc.McsCohortMutex(budget=1), 3, 2),
+    ("mcs_cohort_budget_3", mc.McsCohortMutex(cluster_of=(0, 0, 0), budget=3), 3, 2),
+    ("mcs_cohort_three_rounds", mc.McsCohortMutex(cluster_of=(0, 0)), 2, 3),
     ("cohort_carry_budget_2", mc.CarryCohortMutex(budget=2), 3, 2),
     ("cohort_carry_budget_1", mc.CarryCohortMutex(budget=1), 4, 1),
     ("cohort_carry_budget_3", mc.CarryCohortMutex(budget=3), 3, 2),
@@ -124,6 +131,12 @@ BROKEN = [
     # sum, and a local pass that does not add the holder's own contribution.
     ("cohort_carry_global_reads_local", mc.CarryCohortMutex(broken="global_reads_local"), 3, 2, "entered with"),
     ("cohort_carry_pass_without_add", mc.CarryCohortMutex(broken="pass_without_add"), 3, 2, "entered with"),
+    # MCS cluster cohort lock: the same three mistakes, and an owned record pushed after the
+    # holder released the global lock.
+    ("mcs_cohort_no_seq_check", mc.McsCohortMutex(broken="no_seq_check"), 3, 2, "critical section"),
+    ("mcs_cohort_stale_link", mc.McsCohortMutex(broken="stale_link"), 3, 2, "cannot reach completion"),
+    ("mcs_cohort_no_cas", mc.McsCohortMutex(cluster_of=(0, 0, 0), broken="no_cas"), 3, 2, "cannot reach completion"),
+    ("mcs_cohort_owned_after_release", mc.McsCohortMutex(broken="owned_after_release"), 3, 2, "critical section"),
     # Three-level carrying lock: a waiter that takes any record in its node as its grant, a
     # holder that trusts a link left by an earlier round, and a holder without a linked
     # successor that leaves the tail naming itself.
