@@ -42,11 +42,16 @@ __global__ void user_kernel(void* bar_state, void* mutex_state, uint32_t* slots,
   }
 }
 
+// MKIND: the cluster cohort lock in its ticket form (GSYNC_MUTEX_CLUSTER) or its MCS form
+// (GSYNC_MUTEX_CLUSTER_MCS, the GB300 default), each attached its own way.
+template <int MKIND>
 __global__ void user_kernel_cluster(void* bar_state, void* mutex_state, void* sem_state, uint32_t* slots,
                                     uint32_t* counter, uint32_t* bad, uint32_t* occ, int rounds) {
   __shared__ gsync::ClusterLocal cluster_lock;
+  __shared__ gsync::McsNode node;
   gsync::BarrierRef bar = gsync::barrier_attach(bar_state);
-  const gsync::MutexRef m = gsync::mutex_attach_cluster(mutex_state, &cluster_lock);
+  const gsync::MutexRef m = MKIND == GSYNC_MUTEX_CLUSTER_MCS ? gsync::mutex_attach_cluster_mcs(mutex_state, &node)
+                                                             : gsync::mutex_attach_cluster(mutex_state, &cluster_lock);
   const gsync::SemRef s = gsync::sem_attach(sem_state);
   const uint32_t b = blockIdx.x, B = gridDim.x;
   bool ok = true;
@@ -61,13 +66,13 @@ __global__ void user_kernel_cluster(void* bar_state, void* mutex_state, void* se
       const uint32_t p = (b + (uint32_t)r + 1u) % B;
       if (buf[p] != (uint32_t)r * B + p) atomicAdd(bad, 1u);
     }
-    gsync::Token t = gsync::mutex_lock<GSYNC_MUTEX_CLUSTER>(m);
+    gsync::Token t = gsync::mutex_lock<MKIND>(m);
     if (t.status != GSYNC_OK) {
       ok = false;
       break;
     }
     if (threadIdx.x == 0) *counter = *counter + 1u;  // plain read-modify-write under the mutex
-    gsync::mutex_unlock<GSYNC_MUTEX_CLUSTER>(m, t);
+    gsync::mutex_unlock<MKIND>(m, t);
     if (gsync::sem_wait<GSYNC_SEM_WINDOW>(s) != GSYNC_OK) {
       ok = false;
       break;
@@ -80,7 +85,7 @@ __global__ void user_kernel_cluster(void* bar_state, void* mutex_state, void* se
     gsync::sem_post<GSYNC_SEM_WINDOW>(s);
   }
   if (!ok && threadIdx.x == 0) atomicAdd(bad, 1u);
-  gsync::mutex_cluster_end();  // block 0's local lock outlives every user in the cluster
+  gsync::mutex_cluster_end();  // the cluster's shared memory outlives every user in it
 }
 
 // The per-call wait bounds: block 0 takes the semaphore's only permit and then waits for a
@@ -167,39 +172,49 @@ int main() {
     return 1;
   }
 
-  // The GB300 defaults in a cluster launch.
-  cudaFunction_t fc;
-  CHECK(cudaGetFuncBySymbol(&fc, (const void*)user_kernel_cluster));
-  const int C = 4, n = 4;
-  int maxc = 0;
-  CHECK(gsync_check_coresident((const void*)fc, C, threads, 0, C, &maxc));
-  const int BC = (maxc < 1184 ? maxc : 1184) / C * C;
-  void *bar2 = nullptr, *mtx2 = nullptr, *sem = nullptr;
-  uint32_t* w = nullptr;  // counter, bad, occupancy, max occupancy
-  uint32_t* slots2 = nullptr;
-  const size_t bar2_bytes = gsync_barrier_bytes(GSYNC_BAR_COUNT, BC, 8);
-  const size_t mtx2_bytes = gsync_mutex_bytes(GSYNC_MUTEX_CLUSTER, BC);
-  const size_t sem_bytes = gsync_sem_bytes(GSYNC_SEM_WINDOW);
-  CHECK(cudaMalloc(&bar2, bar2_bytes));
-  CHECK(cudaMalloc(&mtx2, mtx2_bytes));
-  CHECK(cudaMalloc(&sem, sem_bytes));
-  CHECK(cudaMalloc(&w, 4 * sizeof(uint32_t)));
-  CHECK(cudaMalloc(&slots2, 2 * BC * sizeof(uint32_t)));
-  CHECK(cudaMemset(w, 0, 4 * sizeof(uint32_t)));
-  CHECK(gsync_barrier_init(bar2, bar2_bytes, GSYNC_BAR_COUNT, BC, 8, 0, nullptr));
-  CHECK(gsync_mutex_init(mtx2, mtx2_bytes, GSYNC_MUTEX_CLUSTER, BC, &bo, 0, nullptr));
-  gsync_backoff sbo = {GSYNC_BACKOFF_EXPONENTIAL, 16, 2000, 0};
-  CHECK(gsync_sem_init(sem, sem_bytes, GSYNC_SEM_WINDOW, n, &sbo, 0, nullptr));
-  uint32_t *cnt2 = w, *bad2 = w + 1, *occ = w + 2;
-  void* args2[] = {&bar2, &mtx2, &sem, &slots2, &cnt2, &bad2, &occ, &r};
-  CHECK(gsync_launch_coresident((const void*)fc, BC, threads, 0, C, args2, nullptr));
-  CHECK(cudaDeviceSynchronize());
-  uint32_t h2[4];
-  CHECK(cudaMemcpy(h2, w, sizeof h2, cudaMemcpyDeviceToHost));
-  if (h2[1] != 0 || h2[0] != (uint32_t)BC * rounds || h2[2] != 0 || h2[3] < 1 || h2[3] > (uint32_t)n) {
-    printf("FAIL cluster kernel: counter %u (want %u), bad %u, occupancy %u, max %u (n %d)\n", h2[0],
-           (uint32_t)BC * rounds, h2[1], h2[2], h2[3], n);
-    return 1;
+  // The GB300 defaults in a cluster launch: the counting barrier, the ticket-window semaphore,
+  // and the cluster cohort lock in its ticket form (clusters of 4) and its MCS form (clusters
+  // of 8, the default).
+  int cl_blocks[2] = {0, 0};
+  uint32_t cl_max[2] = {0u, 0u};
+  for (int form = 0; form < 2; ++form) {
+    const int mkind = form ? GSYNC_MUTEX_CLUSTER_MCS : GSYNC_MUTEX_CLUSTER;
+    cudaFunction_t fc;
+    CHECK(cudaGetFuncBySymbol(&fc, form ? (const void*)user_kernel_cluster<GSYNC_MUTEX_CLUSTER_MCS>
+                                        : (const void*)user_kernel_cluster<GSYNC_MUTEX_CLUSTER>));
+    const int C = form ? 8 : 4, n = 4;
+    int maxc = 0;
+    CHECK(gsync_check_coresident((const void*)fc, C, threads, 0, C, &maxc));
+    const int BC = (maxc < 1184 ? maxc : 1184) / C * C;
+    void *bar2 = nullptr, *mtx2 = nullptr, *sem = nullptr;
+    uint32_t* w = nullptr;  // counter, bad, occupancy, max occupancy
+    uint32_t* slots2 = nullptr;
+    const size_t bar2_bytes = gsync_barrier_bytes(GSYNC_BAR_COUNT, BC, 8);
+    const size_t mtx2_bytes = gsync_mutex_bytes(mkind, BC);
+    const size_t sem_bytes = gsync_sem_bytes(GSYNC_SEM_WINDOW);
+    CHECK(cudaMalloc(&bar2, bar2_bytes));
+    CHECK(cudaMalloc(&mtx2, mtx2_bytes));
+    CHECK(cudaMalloc(&sem, sem_bytes));
+    CHECK(cudaMalloc(&w, 4 * sizeof(uint32_t)));
+    CHECK(cudaMalloc(&slots2, 2 * BC * sizeof(uint32_t)));
+    CHECK(cudaMemset(w, 0, 4 * sizeof(uint32_t)));
+    CHECK(gsync_barrier_init(bar2, bar2_bytes, GSYNC_BAR_COUNT, BC, 8, 0, nullptr));
+    CHECK(gsync_mutex_init(mtx2, mtx2_bytes, mkind, BC, &bo, 0, nullptr));
+    gsync_backoff sbo = {GSYNC_BACKOFF_EXPONENTIAL, 16, 2000, 0};
+    CHECK(gsync_sem_init(sem, sem_bytes, GSYNC_SEM_WINDOW, n, &sbo, 0, nullptr));
+    uint32_t *cnt2 = w, *bad2 = w + 1, *occ = w + 2;
+    void* args2[] = {&bar2, &mtx2, &sem, &slots2, &cnt2, &bad2, &occ, &r};
+    CHECK(gsync_launch_coresident((const void*)fc, BC, threads, 0, C, args2, nullptr));
+    CHECK(cudaDeviceSynchronize());
+    uint32_t h2[4];
+    CHECK(cudaMemcpy(h2, w, sizeof h2, cudaMemcpyDeviceToHost));
+    if (h2[1] != 0 || h2[0] != (uint32_t)BC * rounds || h2[2] != 0 || h2[3] < 1 || h2[3] > (uint32_t)n) {
+      printf("FAIL cluster kernel (mutex kind %d): counter %u (want %u), bad %u, occupancy %u, max %u (n %d)\n",
+             mkind, h2[0], (uint32_t)BC * rounds, h2[1], h2[2], h2[3], n);
+      return 1;
+    }
+    cl_blocks[form] = BC;
+    cl_max[form] = h2[3];
   }
 
   // Per-call wait bounds: each second wait must end with GSYNC_ETIMEDOUT after ~1 ms (the
@@ -261,8 +276,8 @@ int main() {
     }
     CHECK(cudaFree(bar4));
   }
-  printf("OK %d blocks x %d rounds; %d blocks in clusters of %d x %d rounds, at most %u of %d inside; "
-         "bounded waits ended after %.2f / %.2f / %.2f ms\n", B, rounds, BC, C, rounds, h2[3], n, hns[0] / 1e6,
-         hns[1] / 1e6, hns[2] / 1e6);
+  printf("OK %d blocks x %d rounds; in clusters (ticket form, MCS form): %d / %d blocks, at most %u / %u of 4 "
+         "inside; bounded waits ended after %.2f / %.2f / %.2f ms\n", B, rounds, cl_blocks[0], cl_blocks[1],
+         cl_max[0], cl_max[1], hns[0] / 1e6, hns[1] / 1e6, hns[2] / 1e6);
   return 0;
 }
