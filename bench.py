@@ -46,7 +46,7 @@ DEFAULT_BARRIER = ("count", 8)
 BARRIERS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("tree", 8 | 1 << 16), ("tree", 64 | 1 << 16),
             ("cluster", 2), ("cluster", 4), ("cluster", 8),
             ("cluster", 4 | 2 << 4), ("cluster", 8 | 2 << 4), ("sharded", 32), ("sharded", 8), ("die", 0),
-            ("die", 1), ("split", 16 | 16 << 8), ("count", 0), ("count", 8)]
+            ("die", 1), ("split", 16 | 16 << 8), ("count", 0), ("count", 8), ("exchange", 8)]
 # Backoff (min_ns, max_ns) per kind; the ticket kinds sleep min_ns per waiter ahead, capped.
 MUTEX_BACKOFF = {"cas_backoff": (16, 512), "ticket": (128, 4000), "cohort": (128, 4000), "cluster": (128, 4000),
                  "cluster_mcs": (128, 4000)}
@@ -190,7 +190,7 @@ def barrier_name(kind, param):
         return name + (f"_s{sleep}" if sleep else "")
     if kind == "tree":
         return f"tree{param & 0xFFFF}" + ("_count" if param >> 16 else "")
-    if kind == "sharded" or (kind == "count" and param):
+    if kind == "sharded" or (kind in ("count", "exchange") and param):
         return f"{kind}{param}"
     if kind == "split":
         return f"split{param & 0xFF}x{param >> 8}"
@@ -378,13 +378,18 @@ def barrier_roof_ns(terms, kind, param, B):
       cluster: the hardware cluster barrier (T_cb(c), measured), then over the B/c leaders:
                form 0 as atomic; form 1 as count; form 2 as count plus a second cluster barrier
       die    : B/2 arrivals per die, and with per-die counters one more round trip (the top)
-      split  : B/S per counter plus S at the top, two round trips (S > 1)"""
+      split  : B/S per counter plus S at the top, two round trips (S > 1)
+      exchange: as count, but the arrival has no fence and the pollers' loads are relaxed, so
+               the hand-off is the fence-free one (L_handoff_relaxed_near); the partner value
+               is one load of its record (L_ld)"""
     L_rt, L_h, L_ld = terms["L_rt_ns"], terms["L_handoff_l2_near_ns"], terms.get("L_ld_ns", 0.0)
     t_atom = 1e9 / terms["R_same_atom_ops_s"]
     if kind == "atomic":
         ns = L_rt + B * t_atom + L_h
     elif kind == "count":
         ns = B * t_atom + L_h
+    elif kind == "exchange":
+        ns = B * t_atom + terms.get("L_handoff_relaxed_near_ns", L_h)
     elif kind == "tree":
         fan, form = param & 0xFFFF, param >> 16
         lv = tree_levels(B, fan)
@@ -630,7 +635,7 @@ def flush_l2():
 
 SWEEP_GRIDS = (148, 296, 592, 1184)
 SWEEP_BARRIERS = [("atomic", 0), ("flag", 0), ("tree", 8), ("tree", 64 | 1 << 16), ("cluster", 2), ("cluster", 4),
-                  ("cluster", 8), ("cluster", 8 | 2 << 4), ("count", 8)]
+                  ("cluster", 8), ("cluster", 8 | 2 << 4), ("count", 8), ("exchange", 8)]
 
 
 def _time_launch(launch, reset, reps=3):

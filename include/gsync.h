@@ -84,8 +84,12 @@ typedef enum gsync_barrier_kind {
                             param 1: one flat counter */
   GSYNC_BAR_SPLIT = 6,   /* S arrival counters under a top counter, R copies of the release
                             word (param = S | R << 8) */
-  GSYNC_BAR_COUNT = 7    /* a growing 64-bit arrival counter that every block polls: the last
+  GSYNC_BAR_COUNT = 7,   /* a growing 64-bit arrival counter that every block polls: the last
                             arrival is the release (no epoch word); optionally two levels */
+  GSYNC_BAR_EXCHANGE = 8 /* the counting barrier whose arrivals carry one 64-bit value per
+                            block, read by any block after the crossing (gsync::barrier_exchange
+                            and barrier_exchange_read): no fence, and only the exchanged values
+                            are ordered; param = the sleep of COUNT (0..1023) */
 } gsync_barrier_kind;
 
 /* Semaphore kinds (Section 5, "Semaphore"; Appendix, spin-lock and sleeping semaphores). */
@@ -301,10 +305,11 @@ int gsync_probe_barrier_trace(void* state, const gsync_barrier_work* w, uint64_t
  * slot buffers live in one 128 KiB file-scope device array inside the library, which every
  * GPU that loads the library holds until the process exits.  The caller still passes the
  * outputs in `w` (chk, mix, bad, status; w->slots is ignored).
- *  - Kinds: ATOMIC, FLAG, TREE, CLUSTER, SHARDED, SPLIT and COUNT, with `param` as for
- *    gsync_barrier_bytes (CLUSTER takes its size from w->cluster and its form and sleep
- *    from the other bits of `param`).  DIE
- *    returns GSYNC_EINVAL: its init measures the die map and synchronizes the stream.
+ *  - Kinds: ATOMIC, FLAG, TREE, CLUSTER, SHARDED, SPLIT, COUNT and EXCHANGE, with `param`
+ *    as for gsync_barrier_bytes (CLUSTER takes its size from w->cluster and its form and
+ *    sleep from the other bits of `param`; EXCHANGE carries the slot values in its records
+ *    and does not use the slot buffers).  DIE returns GSYNC_EINVAL: its init measures the die
+ *    map and synchronizes the stream.
  *  - Limits: nblocks <= GSYNC_STATIC_MAX_BLOCKS (4096), and the object for (kind, nblocks,
  *    param) must fit in 96 KiB (gsync_barrier_bytes); anything larger returns GSYNC_EINVAL.
  *  - Every call looks up the array's device address (cudaGetSymbolAddress) with the

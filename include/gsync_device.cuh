@@ -84,6 +84,11 @@ __device__ __forceinline__ uint64_t atom_add_acq_rel_u64(uint64_t* p, uint64_t v
   asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(v) : "memory");
   return r;
 }
+__device__ __forceinline__ uint64_t atom_add_relaxed_u64(uint64_t* p, uint64_t v) {
+  uint64_t r;
+  asm volatile("atom.relaxed.gpu.global.add.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(v) : "memory");
+  return r;
+}
 __device__ __forceinline__ void red_add_release_u64(uint64_t* p, uint64_t v) {
   asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -1031,7 +1036,7 @@ __device__ __forceinline__ BarrierRef barrier_attach(void* state) {
     }
   } else if (b.kind == GSYNC_BAR_SPLIT) {
     b.epoch = ptx::ld_relaxed(b.line(1u + blockIdx.x % (b.param >> 8)));
-  } else if (b.kind == GSYNC_BAR_COUNT) {
+  } else if (b.kind == GSYNC_BAR_COUNT || b.kind == GSYNC_BAR_EXCHANGE) {
     // No crossing can complete before every block has attached and arrived, so the counter
     // read here lies in [k P, k P + P - 1] for its P parties per crossing: rounding down
     // gives every block the same base (and every block of a sub-counter the same sub-base).
@@ -1178,6 +1183,7 @@ __device__ __forceinline__ int counter_arrive_wait(const BarrierRef& b, uint32_t
 
 template <int KIND>
 __device__ __forceinline__ int barrier_wait(BarrierRef& b) {
+  static_assert(KIND != GSYNC_BAR_EXCHANGE, "the exchange barrier crosses with barrier_exchange");
   __shared__ int s_rc;
   const bool master = threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0;
   const uint32_t e1 = b.epoch + 1u;
@@ -1421,6 +1427,71 @@ __device__ __forceinline__ int barrier_wait(BarrierRef& b) {
   const int rc = s_rc;
   b.epoch = e1;
   return rc;
+}
+
+// EXCHANGE: the counting barrier whose arrivals carry one 64-bit value per block -- a barrier
+// and an all-gather in one (a GB300 design; the paper's barriers publish data through memory
+// written before a fenced arrival).  Line 1 is the growing counter; from line 2, one 16-byte
+// record {global epoch, value} per block and epoch parity.  A block's arrival writes its
+// record with one relaxed 128-bit store and counts in with a relaxed fetch-and-add: no fence,
+// so the device may make the two visible in either order.  After the crossing, a reader polls
+// a block's record until it shows the crossing's epoch; a 128-bit access is one access, so the
+// value it then holds is the one published for that crossing.  Records alternate by epoch
+// parity: a block rewrites its record of parity e mod 2 for crossing e + 2 only after passing
+// e + 1, which every reader of crossing e reaches only after its reads.  The global epoch
+// (base / n + crossings since attach) keeps growing across launches, so a record left by an
+// earlier launch never matches.  The crossing orders the exchanged values only: writes a
+// block made to other memory before it are not published -- GSYNC_BAR_COUNT does that.
+__device__ __forceinline__ uint64_t* exchange_record(const BarrierRef& b, uint64_t epoch, uint32_t blk) {
+  return (uint64_t*)b.line(2) + 2u * ((uint32_t)(epoch & 1u) * b.n + blk);
+}
+
+// All threads of the block: publish `value` (thread 0's) for this crossing and cross.
+__device__ __forceinline__ int barrier_exchange(BarrierRef& b, uint64_t value) {
+  __shared__ int s_rc;
+  const bool master = threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0;
+  const uint32_t e1 = b.epoch + 1u;
+  __syncthreads();
+  if (master) {
+    const uint64_t ge = b.base / b.n + e1;
+    uint64_t* counter = (uint64_t*)b.line(1);
+    ptx::st_relaxed_b128(exchange_record(b, ge, blockIdx.x), ge, value);
+    const uint64_t target = b.base + (uint64_t)e1 * b.n;
+    const uint64_t missing = target - (ptx::atom_add_relaxed_u64(counter, 1ull) + 1ull);
+    const uint32_t sleep16 = b.param & 0x3FFu;
+    int rc = GSYNC_OK;
+    if (missing) {
+      if (sleep16 && missing < (1ull << 24)) {
+        const uint64_t ns = missing * sleep16 / 16u;
+        __nanosleep((uint32_t)(ns < 4000u ? ns : 4000u));
+      }
+      Waiter w;
+      while (ptx::ld_relaxed_u64(counter) < target)
+        if ((rc = w.tick(b.timeout_ns, b.abort_word())) != GSYNC_OK) break;
+    }
+    s_rc = rc;
+  }
+  __syncthreads();
+  const int rc = s_rc;
+  b.epoch = e1;
+  return rc;
+}
+
+// Any thread, after barrier_exchange returned GSYNC_OK: the value block `blk` published for
+// that crossing (polls its record, bounded).  Must complete before the block's next crossing.
+__device__ __forceinline__ int barrier_exchange_read(const BarrierRef& b, uint32_t blk, uint64_t& value) {
+  if (blk >= b.n) return GSYNC_EINVAL;
+  const uint64_t ge = b.base / b.n + b.epoch;
+  const uint64_t* rec = exchange_record(b, ge, blk);
+  Waiter w;
+  uint64_t lo, hi;
+  for (;;) {
+    ptx::ld_relaxed_b128(rec, lo, hi);
+    if (lo == ge) break;
+    if (int rc = w.tick(b.timeout_ns, b.abort_word())) return rc;
+  }
+  value = hi;
+  return GSYNC_OK;
 }
 
 // barrier_wait with a wait bound for this call (ns) instead of the object's own; on expiry

@@ -37,6 +37,7 @@ The algorithms follow Section 5 ("Design") and the pseudocode of the Appendix:
   DieBarrier    per-die counters and release words, a top counter between the dies
   SplitBarrier  S arrival counters under a top counter, R copies of the release word
   CountBarrier  one growing arrival counter that every block polls
+  ExchangeBarrier  the counting barrier whose arrivals carry one value per block, no fence
 Mutation variants with a planted mistake (`broken=...`) exist so that tests can show the
 checker catches each kind of error.
 """
@@ -1093,6 +1094,65 @@ class CountBarrier:
                 return loc, sh, None
             k += 1
             return ((0 if k < ops else DONE), k, e, r), sh, ("pass",)
+        raise AssertionError(pc)
+
+
+class ExchangeBarrier:
+    """Exchange barrier: the counting barrier whose arrival carries one value per block (a
+    barrier and an all-gather in one; GSYNC_BAR_EXCHANGE, a GB300 design, not in the paper).
+
+    For its e-th crossing block p writes a record (epoch, value) into slot (epoch mod 2, p) and
+    adds 1 to the counter; there is no fence, so the device may make the two visible in either
+    order: `late[p]` makes block p count in before its record is written.  The block polls the
+    counter until it reaches (base + e) x B, then reads its partner's record of the same parity,
+    polling until the record shows the crossing's epoch, and must find the value its partner
+    published for it (value(q, epoch) = 16 q + epoch).  Records alternate by epoch parity: a
+    block rewrites slot (e mod 2, p) for crossing e + 2 only after passing crossing e + 1, which
+    needs every reader of crossing e to have arrived at e + 1.
+    broken="single_buffer": one record per block (a fast block overwrites the record a slow one
+    still has to read); broken="no_epoch_check": a reader takes the record without checking its
+    epoch; broken="off_by_one": a block waits for one arrival less.
+    """
+    kind = "barrier"
+
+    def __init__(self, base=0, late=(), broken=None):
+        self.base, self.late, self.broken = base, tuple(late), broken
+
+    def init(self, nproc, ops):
+        recs = ((self.base, 0),) * (2 * nproc)  # (epoch, value) per (parity, block)
+        return (self.base * nproc,) + recs, tuple((0, 0, 0, 0) for _ in range(nproc))
+
+    def slot(self, epoch, q, nproc):
+        return 1 + (0 if self.broken == "single_buffer" else (epoch & 1) * nproc) + q
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, k, e, r = loc
+        count = sh[0]
+        late = p < len(self.late) and self.late[p]
+        ge = self.base + e + 1  # the epoch of the crossing this block is making (pc 0..2)
+        if pc == 0:
+            if late:
+                return (1, k, e, r), _set(sh, 0, count + 1), ("arrive",)
+            return (1, k, e, r), _set(sh, self.slot(ge, p, nproc), (ge, 16 * p + ge)), None
+        if pc == 1:
+            if late:
+                return (2, k, e + 1, r), _set(sh, self.slot(ge, p, nproc), (ge, 16 * p + ge)), None
+            return (2, k, e + 1, r), _set(sh, 0, count + 1), ("arrive",)
+        if pc == 2:
+            target = (self.base + e) * nproc - (1 if self.broken == "off_by_one" else 0)
+            if count < target:
+                return loc, sh, None
+            return (3, k, e, r), sh, ("pass",)
+        if pc == 3:  # the partner's record of this crossing
+            ep = self.base + e
+            q = (p + k + 1) % nproc
+            rep, val = sh[self.slot(ep, q, nproc)]
+            if rep != ep and self.broken != "no_epoch_check":
+                return loc, sh, None
+            if val != 16 * q + ep:
+                return loc, sh, ("violation", f"block {p} read {val} from block {q} at epoch {ep}")
+            k += 1
+            return ((0 if k < ops else DONE), k, e, r), sh, None
         raise AssertionError(pc)
 
 

@@ -10,6 +10,9 @@
 //   sampled : thread 0 reads partner p = (b + r + 1) mod B only, folds lowbias32(slot_p) into
 //             mix and counts a stale read in bad.  This keeps the per-round work O(1) so the
 //             kernel time measures the barrier itself at large grids.
+// EXCHANGE carries each block's slot value in its arrival instead: the block publishes r * B + b
+// with barrier_exchange and reads the others' values with barrier_exchange_read (the slot
+// buffers are not used); the results are the same.
 #include "common.cuh"
 
 using namespace gsync_impl;
@@ -34,12 +37,31 @@ __global__ void __launch_bounds__(kMaxThreads, FULL ? 4 : 6)
   }
   __shared__ uint32_t red_x[kMaxThreads / 32], red_s[kMaxThreads / 32], red_b[kMaxThreads / 32];
   uint32_t mix = 0, bad = 0;
+  constexpr bool kExchange = KIND == GSYNC_BAR_EXCHANGE;
+  // The value of slot j this round: the slot buffer, or block j's exchange record.
+  auto slot = [&](const uint32_t* buf, uint32_t j, uint32_t& nb) -> uint32_t {
+    if constexpr (kExchange) {
+      uint64_t v = 0;
+      if (gsync::barrier_exchange_read(bar, j, v) != GSYNC_OK) {
+        ++nb;
+        return 0xFFFFFFFFu;
+      }
+      return (uint32_t)v;
+    } else {
+      return buf[j];
+    }
+  };
   for (int r = 0; r < rounds; ++r) {
     uint32_t* buf = slots + (uint32_t)(r & 1) * B;
     const uint32_t rb = (uint32_t)r * B;
-    if (tid == 0) buf[b] = rb + b;
+    if (!kExchange && tid == 0) buf[b] = rb + b;
     if (TRACE && tid == 0) trace[2u * ((uint64_t)b * (uint32_t)rounds + (uint32_t)r)] = gsync::ptx::globaltimer();
-    const int rc = gsync::barrier_wait<KIND>(bar);
+    int rc;
+    if constexpr (kExchange) {
+      rc = gsync::barrier_exchange(bar, rb + b);
+    } else {
+      rc = gsync::barrier_wait<KIND>(bar);
+    }
     if (TRACE && tid == 0) trace[2u * ((uint64_t)b * (uint32_t)rounds + (uint32_t)r) + 1u] = gsync::ptx::globaltimer();
     if (rc != GSYNC_OK) {
       if (tid == 0) record_status(status, rc);
@@ -52,7 +74,7 @@ __global__ void __launch_bounds__(kMaxThreads, FULL ? 4 : 6)
     if (FULL) {
       uint32_t x = 0, s = 0, nb = 0;
       for (uint32_t j = tid; j < B; j += blockDim.x) {
-        const uint32_t v = buf[j];
+        const uint32_t v = slot(buf, j, nb);
         x ^= v;
         s += lowbias32(v);
         nb += v != rb + j;
@@ -83,7 +105,7 @@ __global__ void __launch_bounds__(kMaxThreads, FULL ? 4 : 6)
       }
     } else if (tid == 0) {
       const uint32_t p = (b + (uint32_t)r + 1u) % B;
-      const uint32_t v = buf[p];
+      const uint32_t v = slot(buf, p, bad);
       mix = rotl32(mix, 5) ^ lowbias32(v);
       bad += v != rb + p;
     }
@@ -106,6 +128,7 @@ KernelFn pick(int kind, int full) {
     case GSYNC_BAR_DIE: return full ? barrier_workload_kernel<GSYNC_BAR_DIE, true> : barrier_workload_kernel<GSYNC_BAR_DIE, false>;
     case GSYNC_BAR_SPLIT: return full ? barrier_workload_kernel<GSYNC_BAR_SPLIT, true> : barrier_workload_kernel<GSYNC_BAR_SPLIT, false>;
     case GSYNC_BAR_COUNT: return full ? barrier_workload_kernel<GSYNC_BAR_COUNT, true> : barrier_workload_kernel<GSYNC_BAR_COUNT, false>;
+    case GSYNC_BAR_EXCHANGE: return full ? barrier_workload_kernel<GSYNC_BAR_EXCHANGE, true> : barrier_workload_kernel<GSYNC_BAR_EXCHANGE, false>;
   }
   return nullptr;
 }
@@ -120,6 +143,7 @@ KernelFn pick_trace(int kind) {
     case GSYNC_BAR_DIE: return barrier_workload_kernel<GSYNC_BAR_DIE, false, true>;
     case GSYNC_BAR_SPLIT: return barrier_workload_kernel<GSYNC_BAR_SPLIT, false, true>;
     case GSYNC_BAR_COUNT: return barrier_workload_kernel<GSYNC_BAR_COUNT, false, true>;
+    case GSYNC_BAR_EXCHANGE: return barrier_workload_kernel<GSYNC_BAR_EXCHANGE, false, true>;
   }
   return nullptr;
 }

@@ -176,6 +176,8 @@ uint32_t barrier_lines(int kind, uint32_t n, uint32_t param) {
       const uint32_t S = (param >> 16) & 0x7Fu;
       return 2 + (S > 1 ? S : 0);
     }
+    case GSYNC_BAR_EXCHANGE:
+      return 2 + (2 * n * 16 + kLine - 1) / kLine;  // counter, then 2 x n 16-byte records
   }
   return 0;
 }
@@ -314,6 +316,7 @@ size_t gsync_barrier_bytes(int kind, int nblocks, int param) {
       if (param < 0 || sleep16 > 1023 || S > 64) return 0;
       break;
     }
+    case GSYNC_BAR_EXCHANGE: if (param < 0 || param > 1023) return 0; break;
     case GSYNC_BAR_SPLIT: {
       const int S = param & 0xFF, R = param >> 8;
       if (param < 0 || S < 1 || S > 64 || R < 1 || R > 64) return 0;

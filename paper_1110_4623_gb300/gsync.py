@@ -33,7 +33,8 @@ BATCHED_POLICY_KINDS = {**MUTEX_KINDS, "ticket_carry": BATCHED_TICKET_CARRY,
                         "cohort_carry": BATCHED_COHORT_CARRY, "cluster_carry": BATCHED_CLUSTER_CARRY,
                         "cluster_die_carry": BATCHED_CLUSTER_DIE_CARRY}
 COHORT_DEFAULT_BUDGET = 64
-BARRIER_KINDS = {"atomic": 0, "flag": 1, "tree": 2, "cluster": 3, "sharded": 4, "die": 5, "split": 6, "count": 7}
+BARRIER_KINDS = {"atomic": 0, "flag": 1, "tree": 2, "cluster": 3, "sharded": 4, "die": 5, "split": 6, "count": 7,
+                 "exchange": 8}
 SEM_KINDS = {"ticket": 0, "spin": 1, "spin_backoff": 2, "window": 3}
 BACKOFF_EXPONENTIAL, BACKOFF_LINEAR_CYCLIC, BACKOFF_SPIN_THEN_SLEEP = 0, 1, 2
 PROBE_OPS = {"volatile_load": 0, "volatile_store": 1, "atomic_read": 2, "atomic_write": 3,

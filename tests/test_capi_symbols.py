@@ -81,6 +81,10 @@ def test_size_queries_without_gpu(lib_path):
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["split"], 1184, 65 | 8 << 8) == 0
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["split"], 1184, 16) == 0  # R = 0
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["count"], 1184, 0) == 2 * 128
+    # exchange: header, counter, then two 16-byte records per block
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["exchange"], 1184, 8) == (2 + 296) * 128
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["exchange"], 5, 0) == (2 + 2) * 128
+    assert G.gsync_barrier_bytes(G.BARRIER_KINDS["exchange"], 1184, 1024) == 0
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["count"], 1184, 1024) == 0
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["count"], 1184, 8 | 16 << 16) == (2 + 16) * 128
     assert G.gsync_barrier_bytes(G.BARRIER_KINDS["count"], 1184, 8 | 65 << 16) == 0

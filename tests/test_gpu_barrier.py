@@ -22,7 +22,9 @@ KINDS = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("tree", 2), ("cl
          ("cluster", 2 | 1 << 4), ("cluster", 4 | 1 << 4 | 8 << 8), ("cluster", 8 | 1 << 4 | 8 << 8),
          ("cluster", 2 | 2 << 4), ("cluster", 4 | 2 << 4 | 8 << 8), ("cluster", 8 | 2 << 4 | 1023 << 8),
          # the counting form of the tree (param = fan | 1 << 16)
-         ("tree", 2 | 1 << 16), ("tree", 8 | 1 << 16), ("tree", 32 | 1 << 16), ("tree", 1024 | 1 << 16)]
+         ("tree", 2 | 1 << 16), ("tree", 8 | 1 << 16), ("tree", 32 | 1 << 16), ("tree", 1024 | 1 << 16),
+         # the exchange barrier: the slot values carried in the arrivals (param = the sleep)
+         ("exchange", 0), ("exchange", 8), ("exchange", 1023)]
 
 
 @pytest.mark.parametrize("kind,param", KINDS)
@@ -57,7 +59,7 @@ def test_sampled_sweep_1000_rounds(kind, param, nblocks):
 @pytest.mark.parametrize("kind,param", [("atomic", 0), ("flag", 0), ("tree", 3), ("cluster", 1), ("sharded", 3),
                                         ("die", 0), ("die", 1), ("split", 5 | 3 << 8), ("count", 0),
                                         ("count", 8 | 5 << 16), ("cluster", 1 | 1 << 4), ("cluster", 1 | 2 << 4 | 8 << 8),
-                                        ("tree", 3 | 1 << 16)])
+                                        ("tree", 3 | 1 << 16), ("exchange", 8)])
 @pytest.mark.parametrize("nblocks,threads", [(1, 32), (2, 64), (37, 96), (151, 256)])
 def test_ragged_grids_full_fold(kind, param, nblocks, threads):
     from paper_1110_4623_gb300 import runner
@@ -80,7 +82,7 @@ def test_zero_rounds():
                                                 ("split", 1184, 0), ("count", 1184, 0), ("count", 7, 0),
                                                 ("cluster", 1184, 4 | 1 << 4 | 8 << 8), ("cluster", 1184, 8 | 2 << 4),
                                                 ("cluster", 7, 1 | 1 << 4), ("tree", 1184, 8 | 1 << 16),
-                                                ("tree", 7, 3 | 1 << 16)])
+                                                ("tree", 7, 3 | 1 << 16), ("exchange", 1184, 8), ("exchange", 7, 0)])
 def test_repeated_launches_continue_epochs(kind, nblocks, param):
     # The object keeps its epoch across launches: a second launch attaches at the new epoch
     # (DIE: and counts its blocks per die again in its first crossing; the counting kinds:

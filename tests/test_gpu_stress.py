@@ -1,6 +1,6 @@
 """Seeded repetitions of the GB300 designs across shapes and parameters (cohort and cluster
 cohort mutexes in both forms, counting barrier and the counting forms of the tree and cluster
-barriers, ticket-window semaphore, condition variables, serving loop), each checked exactly
+barriers, the exchange barrier, ticket-window semaphore, condition variables, serving loop), each checked exactly
 against the oracle: a net for races that one shape per test could miss."""
 import numpy as np
 import pytest
@@ -106,6 +106,25 @@ def test_counting_forms_of_tree_and_cluster_barriers_repeated(i):
     want = calc.barrier_full(B, 300)
     assert got["status"] == 0 and not got["bad"].any(), (kind, hex(param), B)
     assert np.array_equal(got["chk"], want["chk"]) and np.array_equal(got["mix"], want["mix"])
+
+
+@pytest.mark.parametrize("i", range(16))
+def test_exchange_barrier_repeated(i):
+    # The exchange barrier (slot values carried in fence-free arrivals) over grids and sleeps,
+    # in the full fold (every block reads every record each round) and the sampled one, and
+    # launched twice on the same object (global epochs keep growing).
+    from paper_1110_4623_gb300 import runner
+    B = [1, 2, 7, 64, 150, 296, 600, 1184][i % 8]
+    param = [0, 8, 64, 1023][i % 4]
+    full = B <= 296 or i % 2 == 0
+    br = runner.BarrierRun("exchange", B, [32, 128, 256][i % 3], 200, full=full, param=param, timeout_ns=10**10)
+    for _ in range(2):
+        got = br.run()
+        assert got["status"] == 0 and not got["bad"].any(), (B, param, full)
+        want = calc.barrier_full(B, 200) if full else calc.barrier_sampled(B, 200)
+        assert np.array_equal(got["mix"], want["mix"])
+        if full:
+            assert np.array_equal(got["chk"], want["chk"])
 
 
 @pytest.mark.parametrize("i", range(20))

@@ -87,6 +87,10 @@ CORRECT = [
     ("sharded_barrier_1", mc.ShardedBarrier(shards=1), 3, 2),
     ("sharded_barrier_wrap", mc.ShardedBarrier(shards=2, base=2 ** 32 - 1), 3, 3),
     ("count_barrier", mc.CountBarrier(), 4, 3),
+    ("exchange_in_order", mc.ExchangeBarrier(), 3, 3),
+    ("exchange_counts_in_first", mc.ExchangeBarrier(late=(True, True, True)), 3, 3),
+    ("exchange_mixed_orders", mc.ExchangeBarrier(late=(True, False, True)), 3, 3),
+    ("exchange_base", mc.ExchangeBarrier(base=5, late=(False, True)), 2, 4),
     ("count_barrier_base", mc.CountBarrier(base=5), 3, 4),
     ("count_barrier_two_level", mc.CountBarrier(S=2), 4, 3),
     ("count_barrier_two_level_3", mc.CountBarrier(S=3, base=2), 4, 3),
@@ -144,6 +148,12 @@ BROKEN = [
     ("hier_carry_stale_link", mc.CarryMcsHierMutex(broken="stale_link"), 3, 2, "cannot reach completion"),
     ("hier_carry_no_cas", mc.CarryMcsHierMutex(cluster_of=(0, 0, 0), die_of=(0,), broken="no_cas"), 3, 2,
      "cannot reach completion"),
+    # Exchange barrier: one record per block instead of two by parity (a fast block overwrites
+    # one still to be read), a reader that skips the epoch check (it can take last round's
+    # value while the new record is in flight), a target one short.
+    ("exchange_single_buffer", mc.ExchangeBarrier(broken="single_buffer"), 3, 3, "cannot reach completion"),
+    ("exchange_no_epoch_check", mc.ExchangeBarrier(late=(True, False, True), broken="no_epoch_check"), 3, 3, "read"),
+    ("exchange_off_by_one", mc.ExchangeBarrier(broken="off_by_one"), 3, 3, "passed round"),
     ("sleep_sem_turn_ge", mc.SleepSem(n=1, broken="turn_ge"), 3, 1, "critical section"),
     ("window_sem_ge", mc.WindowSem(n=2, broken="window_ge"), 3, 1, "critical section"),
     ("barrier_no_wait", mc.AtomicBarrier(broken="no_wait"), 3, 1, "passed round"),

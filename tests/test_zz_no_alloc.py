@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 ACCEPTED = [("atomic", 0), ("flag", 0), ("flag", 1), ("tree", 8), ("tree", 2), ("cluster", 2), ("cluster", 4),
             ("cluster", 8), ("sharded", 8), ("sharded", 32), ("split", 16 | 16 << 8), ("split", 4 | 2 << 8),
             ("count", 0), ("count", 8), ("count", 8 | 4 << 16), ("cluster", 4 | 1 << 4 | 8 << 8),
-            ("cluster", 8 | 2 << 4), ("tree", 8 | 1 << 16)]
+            ("cluster", 8 | 2 << 4), ("tree", 8 | 1 << 16), ("exchange", 8)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -78,7 +78,8 @@ def test_each_call_finds_another_kind_in_the_array():
     # 64-bit counter past zero, flag epochs.  Each call must rewrite all of it for its own kind.
     seq = [("tree", 2, 96), ("count", 8, 96), ("flag", 0, 96), ("sharded", 8, 64), ("count", 8 | 4 << 16, 64),
            ("atomic", 0, 96), ("cluster", 4, 96), ("split", 4 | 2 << 8, 64), ("cluster", 2 | 1 << 4, 96),
-           ("tree", 8, 64), ("cluster", 4 | 2 << 4 | 8 << 8, 64), ("tree", 2 | 1 << 16, 96), ("count", 0, 96)]
+           ("tree", 8, 64), ("cluster", 4 | 2 << 4 | 8 << 8, 64), ("tree", 2 | 1 << 16, 96), ("count", 0, 96),
+           ("exchange", 8, 96), ("exchange", 0, 64), ("count", 8, 96), ("exchange", 8, 96)]
     rounds = 300
     for kind, param, nblocks in seq:
         rc, got = static_call(kind, nblocks, 128, rounds, param)
