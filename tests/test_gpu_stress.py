@@ -1,7 +1,7 @@
 """Seeded repetitions of the GB300 designs across shapes and parameters (cohort and cluster
 cohort mutexes in both forms, counting barrier and the counting forms of the tree and cluster
-barriers, the exchange barrier, ticket-window semaphore, condition variables, serving loop), each checked exactly
-against the oracle: a net for races that one shape per test could miss."""
+barriers, the exchange barrier, ticket-window semaphore, condition variables, serving loop),
+each checked exactly against the oracle: a net for races that one shape per test could miss."""
 import numpy as np
 import pytest
 
