@@ -78,7 +78,9 @@ def make_run(keys, adds, nkeys, nblocks, ngroups, rounds, cluster, key_class, bl
 
 def tune(keys, adds, nkeys: int, nblocks: int, ngroups: int, rounds: int, block_threads: int = 128,
          reps: int = 2) -> dict:
-    """Coordinate descent over the classes' policies, then over the group cluster size."""
+    """Coordinate descent over the classes' policies, then over the group cluster size, then,
+    at every cluster size above 1, over the cluster-only kinds for the hot and warm classes;
+    the fastest combination wins."""
     key_class = classify_keys(keys, nkeys, nblocks)
     policy = list(DEFAULT_POLICY)
     trials = []
@@ -102,18 +104,27 @@ def tune(keys, adds, nkeys: int, nblocks: int, ngroups: int, rounds: int, block_
         trials.append({"class": None, "policy": None, "cluster": c, "ms": ms})
         if best_cluster[0] is None or ms < best_cluster[0]:
             best_cluster = (ms, c)
-    if best_cluster[1] > 1:
-        r = make_run(keys, adds, nkeys, nblocks, ngroups, rounds, best_cluster[1], key_class, block_threads)
+    # The cluster-only kinds (the cluster cohort lock, the carrying locks over clusters) depend
+    # on the cluster size as much as the group barriers do: try them at every size above 1.
+    best = (best_cluster[0], best_cluster[1], list(policy))
+    for c in CLUSTERS:
+        if c == 1:
+            continue
+        r = make_run(keys, adds, nkeys, nblocks, ngroups, rounds, c, key_class, block_threads)
+        pol_c = list(policy)
+        ms_c = next(t["ms"] for t in trials if t["class"] is None and t["cluster"] == c)
         for cls in (HOT, WARM):
             for cand in CLUSTER_CANDIDATES:
-                trial = list(policy)
+                trial = list(pol_c)
                 trial[cls] = cand
                 r.set_policy(trial)
                 ms = _time(r, reps)
-                trials.append({"class": cls, "policy": cand, "cluster": best_cluster[1], "ms": ms})
-                if ms < best_cluster[0]:
-                    best_cluster = (ms, best_cluster[1])
-                    policy[cls] = cand
+                trials.append({"class": cls, "policy": cand, "cluster": c, "ms": ms})
+                if ms < ms_c:
+                    ms_c, pol_c = ms, trial
+        if ms_c < best[0]:
+            best = (ms_c, c, pol_c)
+    best_cluster, policy = (best[0], best[1]), best[2]
     return {"policy": policy, "cluster": best_cluster[1], "best_ms": best_cluster[0],
             "class_sizes": [int((key_class == c).sum()) for c in range(NCLASSES)], "trials": trials,
             "key_class": key_class}
