@@ -987,6 +987,7 @@ struct BarrierRef {
   uint64_t timeout_ns;
   uint32_t die, n_mine, active;  // DIE: this block's die, its die's blocks (0 = unregistered), dies
   uint64_t base, sub_base;       // COUNT: counters' values at attach (multiples of their parties)
+  uint64_t epoch_base;           // EXCHANGE: the global epoch at attach (base / n)
   uint32_t root, root_size;      // TREE counting form: the root's node index and its arrivals
   __device__ __forceinline__ uint32_t* die_line(uint32_t d, uint32_t i) const {
     return s + s[d ? kHdrDieOff1 : kHdrDieOff0] + i * kLineWords;
@@ -1044,6 +1045,7 @@ __device__ __forceinline__ BarrierRef barrier_attach(void* state) {
     const uint64_t P = S > 1u ? (uint64_t)min(S, b.n) : (uint64_t)b.n;
     const uint64_t c = ptx::ld_relaxed_u64((const uint64_t*)b.line(1));
     b.base = c - c % P;
+    b.epoch_base = b.base / P;
     b.sub_base = 0;
     if (S > 1u) {
       const uint32_t g = blockIdx.x % S;
@@ -1439,7 +1441,7 @@ __device__ __forceinline__ int barrier_wait(BarrierRef& b) {
 // value it then holds is the one published for that crossing.  Records alternate by epoch
 // parity: a block rewrites its record of parity e mod 2 for crossing e + 2 only after passing
 // e + 1, which every reader of crossing e reaches only after its reads.  The global epoch
-// (base / n + crossings since attach) keeps growing across launches, so a record left by an
+// (epoch_base + crossings since attach) keeps growing across launches, so a record left by an
 // earlier launch never matches.  The crossing orders the exchanged values only: writes a
 // block made to other memory before it are not published -- GSYNC_BAR_COUNT does that.
 __device__ __forceinline__ uint64_t* exchange_record(const BarrierRef& b, uint64_t epoch, uint32_t blk) {
@@ -1453,7 +1455,7 @@ __device__ __forceinline__ int barrier_exchange(BarrierRef& b, uint64_t value) {
   const uint32_t e1 = b.epoch + 1u;
   __syncthreads();
   if (master) {
-    const uint64_t ge = b.base / b.n + e1;
+    const uint64_t ge = b.epoch_base + e1;
     uint64_t* counter = (uint64_t*)b.line(1);
     ptx::st_relaxed_b128(exchange_record(b, ge, blockIdx.x), ge, value);
     const uint64_t target = b.base + (uint64_t)e1 * b.n;
@@ -1481,7 +1483,7 @@ __device__ __forceinline__ int barrier_exchange(BarrierRef& b, uint64_t value) {
 // that crossing (polls its record, bounded).  Must complete before the block's next crossing.
 __device__ __forceinline__ int barrier_exchange_read(const BarrierRef& b, uint32_t blk, uint64_t& value) {
   if (blk >= b.n) return GSYNC_EINVAL;
-  const uint64_t ge = b.base / b.n + b.epoch;
+  const uint64_t ge = b.epoch_base + b.epoch;
   const uint64_t* rec = exchange_record(b, ge, blk);
   Waiter w;
   uint64_t lo, hi;
