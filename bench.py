@@ -953,13 +953,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "acq/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded SplitMix64 delays/addends/hold times)",
-        "config": {"workload": f"mutex contention, {NBLOCKS} blocks x {MUTEX_THREADS} threads"
-                               f"{f' in clusters of {mutex_cluster(DEFAULT_MUTEX)}' if mutex_cluster(DEFAULT_MUTEX) else ''}, {MUTEX_ACQ} "
-                               f"acquisitions/block, CS {list(CS_SIZES)} int32 words, delays U{{0..2000}} cycles; "
-                               f"+ barriers ({BAR_ROUNDS} rounds) and semaphores ({SEM_PAIRS} pairs) at {NBLOCKS} blocks",
-                   "default_mutex": f"{DEFAULT_MUTEX} (backoff {MUTEX_BACKOFF.get(DEFAULT_MUTEX)} ns)",
-                   "default_barrier": bkey, "nblocks": NBLOCKS,
-                   "l2": "flushed (512 MiB write) before every timed step", "parallelism": f"replicas x{world}"},
+        "config": step_config(world),
         "roofline": {"bound": "l2_handoff_latency", "achieved": value / world, "peak": peak, "unit": "acq/s",
                      "frac": (value / world) / peak, "traffic": ROOF_TRAFFIC,
                      "traffic_note": ROOF_TRAFFIC_NOTE,
@@ -1011,6 +1005,18 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+def step_config(world):
+    """The workload the bench line is quoted on; both arms print it."""
+    c = mutex_cluster(DEFAULT_MUTEX)
+    return {"workload": f"mutex contention, {NBLOCKS} blocks x {MUTEX_THREADS} threads"
+                        f"{f' in clusters of {c}' if c else ''}, {MUTEX_ACQ} "
+                        f"acquisitions/block, CS {list(CS_SIZES)} int32 words, delays U{{0..2000}} cycles; "
+                        f"+ barriers ({BAR_ROUNDS} rounds) and semaphores ({SEM_PAIRS} pairs) at {NBLOCKS} blocks",
+            "default_mutex": f"{DEFAULT_MUTEX} (backoff {MUTEX_BACKOFF.get(DEFAULT_MUTEX)} ns)",
+            "default_barrier": barrier_name(*DEFAULT_BARRIER), "nblocks": NBLOCKS,
+            "l2": "flushed (512 MiB write) before every timed step", "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -1029,8 +1035,7 @@ def run_reference(args):
     out = {"metric": METRIC, "impl": "reference", "value": value, "unit": "acq/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-           "config": {"workload": f"mutex contention, {NBLOCKS} blocks, {MUTEX_ACQ} acquisitions/block, CS "
-                                  f"{list(CS_SIZES)} words ({DEFAULT_MUTEX})", "nblocks": NBLOCKS},
+           "config": step_config(world),
            "cpu_baseline": {"value": value, "unit": "acq/s", "cores": base["cores"], "kind": "oracle",
                             "sample": base["sample"]},
            "e2e": {"value": value, "unit": "acq/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
