@@ -3,8 +3,8 @@
 // grids are launched through the library's co-residency gate.
 //   user_kernel: the counting barrier and the two-die cohort mutex, a plain launch.
 //   user_kernel_cluster: the GB300 defaults -- the counting barrier, the cluster cohort mutex
-//     (its local lock in the kernel's shared memory) and the ticket-window semaphore -- in a
-//     launch with clusters of 4.
+//     (its local lock, or each block's MCS node, in the kernel's shared memory) and the
+//     ticket-window semaphore -- in launches with clusters of 4 and 8.
 //   bounded_waits_kernel: the per-call wait bounds of sem_wait, mutex_lock and barrier_wait.
 // Checked exactly: every round of the barrier sees every block's value of that round, a
 // counter updated with plain loads and stores under the mutex ends at blocks x rounds, and

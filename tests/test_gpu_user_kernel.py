@@ -1,6 +1,7 @@
 """The library used the way a CUDA C++ program uses it: its own kernels call the device
 primitives (counting barrier, cohort mutex; and the GB300 defaults -- counting barrier, cluster
-cohort mutex, ticket-window semaphore -- in a cluster launch), the objects come from the C ABI,
+cohort mutex in both forms, ticket-window semaphore -- in cluster launches), the objects come
+from the C ABI,
 and the grids are launched through gsync_launch_coresident.  The program
 (tests/cuda/user_kernel.cu) checks its own results exactly and prints OK."""
 import os
