@@ -1448,8 +1448,10 @@ __device__ __forceinline__ uint64_t* exchange_record(const BarrierRef& b, uint64
   return (uint64_t*)b.line(2) + 2u * ((uint32_t)(epoch & 1u) * b.n + blk);
 }
 
-// All threads of the block: publish `value` (thread 0's) for this crossing and cross.
+// All threads of the block: publish `value` (thread 0's) for this crossing and cross.  An
+// object of another kind returns GSYNC_EINVAL without crossing.
 __device__ __forceinline__ int barrier_exchange(BarrierRef& b, uint64_t value) {
+  if (b.kind != GSYNC_BAR_EXCHANGE) return GSYNC_EINVAL;  // uniform: every thread reads the same header
   __shared__ int s_rc;
   const bool master = threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0;
   const uint32_t e1 = b.epoch + 1u;
@@ -1482,7 +1484,7 @@ __device__ __forceinline__ int barrier_exchange(BarrierRef& b, uint64_t value) {
 // Any thread, after barrier_exchange returned GSYNC_OK: the value block `blk` published for
 // that crossing (polls its record, bounded).  Must complete before the block's next crossing.
 __device__ __forceinline__ int barrier_exchange_read(const BarrierRef& b, uint32_t blk, uint64_t& value) {
-  if (blk >= b.n) return GSYNC_EINVAL;
+  if (b.kind != GSYNC_BAR_EXCHANGE || blk >= b.n) return GSYNC_EINVAL;
   const uint64_t ge = b.epoch_base + b.epoch;
   const uint64_t* rec = exchange_record(b, ge, blk);
   Waiter w;
