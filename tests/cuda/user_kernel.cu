@@ -5,6 +5,7 @@
 //   user_kernel_cluster: the GB300 defaults -- the counting barrier, the cluster cohort mutex
 //     (its local lock, or each block's MCS node, in the kernel's shared memory) and the
 //     ticket-window semaphore -- in launches with clusters of 4 and 8.
+//   user_kernel_exchange: the exchange barrier as an all-gather, over two launches.
 //   bounded_waits_kernel: the per-call wait bounds of sem_wait, mutex_lock and barrier_wait.
 // Checked exactly: every round of the barrier sees every block's value of that round, a
 // counter updated with plain loads and stores under the mutex ends at blocks x rounds, and
@@ -86,6 +87,26 @@ __global__ void user_kernel_cluster(void* bar_state, void* mutex_state, void* se
   }
   if (!ok && threadIdx.x == 0) atomicAdd(bad, 1u);
   gsync::mutex_cluster_end();  // the cluster's shared memory outlives every user in it
+}
+
+// The exchange barrier as an all-gather: each round every block publishes one value and reads
+// two others' (its right neighbour's and block 0's) after the crossing.
+__global__ void user_kernel_exchange(void* bar_state, uint32_t* bad, int rounds) {
+  gsync::BarrierRef bar = gsync::barrier_attach(bar_state);
+  const uint32_t b = blockIdx.x, B = gridDim.x;
+  for (int r = 0; r < rounds; ++r) {
+    const uint64_t mine = ((uint64_t)r << 32) | (b * 7u + 1u);
+    if (gsync::barrier_exchange(bar, mine) != GSYNC_OK) {
+      if (threadIdx.x == 0) atomicAdd(bad, 1u);
+      return;
+    }
+    if (threadIdx.x < 2) {
+      const uint32_t q = threadIdx.x == 0 ? (b + 1u) % B : 0u;
+      uint64_t v = 0;
+      const int rc = gsync::barrier_exchange_read(bar, q, v);
+      if (rc != GSYNC_OK || v != (((uint64_t)r << 32) | (q * 7u + 1u))) atomicAdd(bad, 1u);
+    }
+  }
 }
 
 // The per-call wait bounds: block 0 takes the semaphore's only permit and then waits for a
@@ -170,6 +191,32 @@ int main() {
   if (h[1] != 0 || h[0] != (uint32_t)B * rounds) {
     printf("FAIL counter %u (want %u), bad %u\n", h[0], (uint32_t)B * rounds, h[1]);
     return 1;
+  }
+
+  // The exchange barrier on the same grid.
+  {
+    cudaFunction_t fx;
+    CHECK(cudaGetFuncBySymbol(&fx, (const void*)user_kernel_exchange));
+    int maxx = 0;
+    CHECK(gsync_check_coresident((const void*)fx, 1, threads, 0, 1, &maxx));
+    const int BX = maxx < 1184 ? maxx : 1184;
+    void* xbar = nullptr;
+    const size_t xbytes = gsync_barrier_bytes(GSYNC_BAR_EXCHANGE, BX, 8);
+    CHECK(cudaMalloc(&xbar, xbytes));
+    CHECK(gsync_barrier_init(xbar, xbytes, GSYNC_BAR_EXCHANGE, BX, 8, 0, nullptr));
+    CHECK(cudaMemset(bad, 0, sizeof(uint32_t)));
+    void* xargs[] = {&xbar, &bad, &r};
+    for (int launch = 0; launch < 2; ++launch) {  // the second launch continues the epochs
+      CHECK(gsync_launch_coresident((const void*)fx, BX, threads, 0, 1, xargs, nullptr));
+      CHECK(cudaDeviceSynchronize());
+    }
+    uint32_t hb = 0;
+    CHECK(cudaMemcpy(&hb, bad, sizeof hb, cudaMemcpyDeviceToHost));
+    if (hb != 0) {
+      printf("FAIL exchange kernel: %u bad reads\n", hb);
+      return 1;
+    }
+    CHECK(cudaFree(xbar));
   }
 
   // The GB300 defaults in a cluster launch: the counting barrier, the ticket-window semaphore,
