@@ -41,6 +41,25 @@ def test_lock_that_is_never_released_times_out(kind, line, value):
     assert ok["status"] == 0 and ok["total"] == 256
 
 
+# The cluster forms compare the low 16 bits of the global turn with a cluster head's ticket:
+# 0x8000 is a turn that none of the 256 acquisitions' tickets reaches.  The heads wait on the
+# global lock; the blocks queued behind them in the cluster (on the shared-memory ticket or on
+# the MCS queue) wait on a grant their head never passes.  Every wait must end.
+@pytest.mark.parametrize("kind", ["cluster", "cluster_mcs"])
+def test_cluster_lock_whose_global_turn_is_never_reached_times_out(kind):
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    delay, add = inputs.mutex_inputs(64, 4, 1, max_delay=0)
+    mr = runner.MutexRun(kind, 64, 128, 4, 8, delay, add, timeout_ns=200_000_000, cluster=8)
+    mr.state.view(torch.int32)[2 * 32] = 0x8000
+    got = mr.run()
+    assert got["rc"] == 0 and got["status"] & G.GSYNC_STATUS_TIMEOUT
+    assert got["total"] == 0 and not got["count"].any()
+    assert G.gsync_object_abort_flag(mr.state)[1] != 0
+    ok = runner.MutexRun(kind, 64, 128, 4, 8, delay, add, cluster=8).run()
+    assert ok["status"] == 0 and ok["total"] == 256
+
+
 @pytest.mark.parametrize("kind", ["atomic", "cluster"])
 def test_barrier_that_can_never_complete_times_out(kind):
     from paper_1110_4623_gb300 import gsync as G
@@ -90,6 +109,25 @@ def test_watchdog_aborts_a_lock_that_is_never_released():
     assert got["status"] & G.GSYNC_STATUS_ABORTED and got["total"] == 0
     assert G.gsync_object_abort_flag(mr.state)[1] & 2  # set by the host
     ok = runner.MutexRun("ticket", 64, 128, 4, 8, delay, add).run()
+    assert ok["status"] == 0 and ok["total"] == 256
+
+
+def test_watchdog_aborts_a_cluster_queue_lock():
+    # Heads wait on a global turn that is never reached, their MCS successors on records that
+    # are never pushed; the watchdog's abort must end both kinds of wait.
+    from paper_1110_4623_gb300 import gsync as G
+    from paper_1110_4623_gb300 import runner
+    delay, add = inputs.mutex_inputs(64, 4, 2, max_delay=0)
+    mr = runner.MutexRun("cluster_mcs", 64, 128, 4, 8, delay, add, timeout_ns=3_000_000_000, cluster=8)
+    mr.reset()
+    mr.state.view(torch.int32)[2 * 32] = 0x8000
+    wd = runner.Watchdog([mr.state], 0.1)
+    assert mr.launch() == 0
+    fired, elapsed = _timed_watch(wd)
+    got = mr.results()
+    assert fired and elapsed < 1.5, elapsed
+    assert got["status"] & G.GSYNC_STATUS_ABORTED and got["total"] == 0
+    ok = runner.MutexRun("cluster_mcs", 64, 128, 4, 8, delay, add, cluster=8).run()
     assert ok["status"] == 0 and ok["total"] == 256
 
 
