@@ -611,7 +611,7 @@ def batched_section(G, calc, inputs, runner, autotune, terms):
     return out
 
 
-SERVE_POOL = 128 << 20           # 512 MB of int32 values (4x the L2)
+SERVE_POOL = 256 << 20           # 1 GiB of int32 values (8x the L2)
 SERVE_RATES = (1e3, 1e4, 1e5, 1e6)
 SERVE_SECONDS, SERVE_MAX_REQ = 0.5, 100_000
 SERVE_CHUNK = 8192                # values per chunk (one block's share), both arms
