@@ -633,7 +633,18 @@ def flush_l2():
     _FLUSH[0].zero_()
 
 
-SWEEP_GRIDS = (148, 296, 592, 1184)
+# The paper draws its Section 6 curves from one block up to the most the GPU holds; the
+# configurations' own grids start at 148 (one block per SM).
+SWEEP_SMALL = (1, 2, 4, 8, 16, 32, 64)
+SWEEP_GRIDS = SWEEP_SMALL + (148, 296, 592, 1184)
+SWEEP_SEM_GRIDS = SWEEP_SMALL + (296, 592)
+
+
+def sweep_grid(B, c):
+    """The grid a sweep point of B blocks runs: rounded down to a multiple of the cluster size c
+    for a cluster launch (0: no such grid, the point is skipped)."""
+    return B - B % c if c else B
+
 SWEEP_BARRIERS = [("atomic", 0), ("flag", 0), ("tree", 8), ("tree", 64 | 1 << 16), ("cluster", 2), ("cluster", 4),
                   ("cluster", 8), ("cluster", 8 | 2 << 4), ("count", 8), ("exchange", 8)]
 
@@ -658,11 +669,12 @@ def _time_launch(launch, reset, reps=3):
 
 def sweep_section(G, calc, inputs, runner, step):
     """Configs 2 and 3 over their grid sizes, as the paper's Section 6 curves are drawn (ops/s
-    against the number of blocks).  The mutex configurations at 148, 296 and 592 blocks (1184
-    is the timed step's), the barrier kinds at 148..1184 blocks (a cluster grid rounded down to
-    a multiple of its cluster size, for the cluster mutexes too: 144 blocks in clusters of 8 at
-    148), both semaphore kinds at 296 and 592 blocks; each a median
-    of 3 launches with L2 flushed before each, and each result checked against the oracle."""
+    against the number of blocks, from one block up).  The mutex configurations at 1..64 and
+    148, 296 and 592 blocks (1184 is the timed step's), the barrier kinds at 1..64 and
+    148..1184 blocks, both semaphore kinds at 1..64, 296 and 592 blocks.  A cluster grid is
+    rounded down to a multiple of its cluster size (144 blocks in clusters of 8 at 148), and a
+    point smaller than one cluster is skipped.  Each point is a median of 3 launches with L2
+    flushed before each, and each result is checked against the oracle."""
     out = {"grids": list(SWEEP_GRIDS), "mutex_acq_per_s": {}, "barrier_ns_per_crossing": {}, "semaphore_ops_per_s": {},
            "l2": "flushed (512 MiB write) before each launch", "parity": "ok"}
     bad = []
@@ -671,7 +683,9 @@ def sweep_section(G, calc, inputs, runner, step):
             row = out["mutex_acq_per_s"].setdefault(name, {}).setdefault(str(K), {})
             for B in SWEEP_GRIDS[:-1]:
                 c = mutex_cluster(kind)
-                nb = B - B % c if c else B  # a cluster grid rounded down to a multiple of its cluster size
+                nb = sweep_grid(B, c)
+                if not nb or str(nb) in row:
+                    continue
                 delay, add = inputs.mutex_inputs(nb, MUTEX_ACQ, inputs.mutex_seed(G.MUTEX_KINDS[kind], nb, K))
                 bo = runner.backoff(policy=policy, min_ns=bo_ns[0], max_ns=bo_ns[1], spin=spin) if bo_ns else None
                 mr = runner.MutexRun(kind, nb, MUTEX_THREADS, MUTEX_ACQ, K, delay, add, bo=bo, timeout_ns=TIMEOUT_NS,
@@ -684,7 +698,9 @@ def sweep_section(G, calc, inputs, runner, step):
     for kind, param in SWEEP_BARRIERS:
         row = out["barrier_ns_per_crossing"].setdefault(barrier_name(kind, param), {})
         for B in SWEEP_GRIDS:
-            nb = B - B % (param & 0xF) if kind == "cluster" else B
+            nb = sweep_grid(B, param & 0xF if kind == "cluster" else 0)
+            if not nb or str(nb) in row:
+                continue
             br = runner.BarrierRun(kind, nb, BAR_THREADS, BAR_ROUNDS, full=False, param=param, timeout_ns=TIMEOUT_NS)
             ms = _time_launch(br.launch, br.status.zero_)
             mix = br.mix.cpu().numpy().view(np.uint32)
@@ -695,7 +711,7 @@ def sweep_section(G, calc, inputs, runner, step):
     for kind in SEM_STEP_KINDS:
         for n in SEM_COUNTS:
             row = out["semaphore_ops_per_s"].setdefault(kind, {}).setdefault(str(n), {})
-            for B in (296, 592):
+            for B in SWEEP_SEM_GRIDS:
                 hold, add = inputs.sem_inputs(B, SEM_PAIRS, inputs.SEED_SEM ^ (n << 16) ^ B)
                 sr = runner.SemRun(kind, B, SEM_THREADS, SEM_PAIRS, n, hold, add,
                                    bo=runner.backoff(min_ns=SEM_BACKOFF[0], max_ns=SEM_BACKOFF[1]), timeout_ns=TIMEOUT_NS)
