@@ -102,9 +102,23 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
     // ---- critical section ----
     uint32_t x[kCsInFlight];
     if (KIND != kFrameOnly) cs_load<WIDE>(data, (uint32_t)cs_words, x);  // data and total never overlap
+    uint32_t seq = 0;
     if (KIND != kFrameOnly && tid == 0) {
-      const uint32_t seq = *total;
+      seq = *total;
       *total = seq + 1u;
+    }
+    if (KIND != kFrameOnly) cs_store<WIDE>(data, (uint32_t)cs_words, v, x);
+    // ---- end of critical section ----
+    if (KIND >= 0) {
+      gsync::mutex_unlock<KIND>(m, t);
+    } else {
+      __syncthreads();
+      if (tid == 0) gsync::ptx::st_release(status + 32, id);  // the release store of an unlock
+    }
+    // The grant log and the ticket record are this acquisition's own slots, which only the
+    // host reads after the launch: written after the release, their stores' acknowledgements
+    // stay off the hand-off path (the release waits only for the section's own stores).
+    if (KIND != kFrameOnly && tid == 0) {
       if (seq < n) {
         grant_log[seq] = id;
       } else {
@@ -117,14 +131,6 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
                        : KIND == GSYNC_MUTEX_CLUSTER     ? ((b / gsync::ptx::cluster_nctarank()) << 20) | (t.ticket & 0xFFFFFu)
                        : KIND == GSYNC_MUTEX_CLUSTER_MCS ? 0xFFFFFFFFu
                                                          : t.ticket;
-    }
-    if (KIND != kFrameOnly) cs_store<WIDE>(data, (uint32_t)cs_words, v, x);
-    // ---- end of critical section ----
-    if (KIND >= 0) {
-      gsync::mutex_unlock<KIND>(m, t);
-    } else {
-      __syncthreads();
-      if (tid == 0) gsync::ptx::st_release(status + 32, id);  // the release store of an unlock
     }
     ++done;
   }
