@@ -75,9 +75,9 @@ BATCH_KEYS, BATCH_ACQ, BATCH_GROUPS, BATCH_ROUNDS, BATCH_THREADS = 4096, 1_000_0
 METRIC = "lock acquires/s & barrier ns at 1184 blocks vs L2-atomic roofline; p99 latency"
 # DRAM bytes per launch of the default mutex kind's workload kernel from an ncu capture, or
 # None while the kernel has changed since the last capture.
-ROOF_TRAFFIC = 1_606_059
+ROOF_TRAFFIC = 1_676_459
 ROOF_TRAFFIC_NOTE = ("DRAM bytes (read + write) per launch of the dominant kernel (the MCS cluster cohort mutex "
-                     "workload, clusters of 8), mean over the step's three launches (CS 0/64/1024: 1.49/1.71/1.61 MB), "
+                     "workload, clusters of 8), mean over the step's three launches (CS 0/64/1024: 1.73/2.10/1.20 MB), "
                      "one-pass ncu capture of the same launches in profiles/; algorithmic bytes 1.89 MB "
                      "(16 B per acquisition)")
 TIMEOUT_NS = 10_000_000_000
