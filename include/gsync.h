@@ -324,11 +324,12 @@ int gsync_bench_barrier_static(const gsync_barrier_work* w, int param, uint64_t 
                                void* stream);
 
 /* Mutex workload.  Block b makes `acq` acquisitions (id = b*acq + a): it waits delay[id]
- * SM cycles, locks, and inside the critical section its thread 0 appends id to
- * grant_log[total] and increments total (plain load/store), records the lock ticket in
- * ticket[id] (0xFFFFFFFF for the CAS kinds), and its threads add addend[id] XOR
- * (i * 0x9E3779B1) to data[i] for every i < cs_words (plain loads/stores); then it unlocks.
- * count[b] receives the number of completed acquisitions.  The per-group kinds record a
+ * SM cycles, locks, and inside the critical section its thread 0 reads total (the position
+ * of this grant) and increments it (plain load/store), and its threads add addend[id] XOR
+ * (i * 0x9E3779B1) to data[i] for every i < cs_words (plain loads/stores); then it unlocks,
+ * and thread 0 writes id to grant_log[position] and the lock ticket to ticket[id]
+ * (0xFFFFFFFF for the CAS kinds and CLUSTER_MCS): each is the grant's own slot, read by the
+ * host only after the launch, so neither needs the lock.  count[b] receives the number of completed acquisitions.  The per-group kinds record a
  * ticket of their group's lock: COHORT as (die << 31) | ticket, CLUSTER as (cluster << 20) |
  * ticket (ticket below 2^20).
  * Buffers (device): delay, addend, grant_log, ticket [nblocks*acq]; data [cs_words];

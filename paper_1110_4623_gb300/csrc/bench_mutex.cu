@@ -1,12 +1,13 @@
 // Mutex workload (Section 6, "Results": each block runs a loop of lock/unlock pairs).
 //
 // Block b makes `acq` acquisitions (id = b * acq + a).  Before each lock its master thread
-// waits delay[id] SM cycles; inside the critical section thread 0 appends id to the grant
-// log at position `total` and increments `total` with a plain load and store, and the
-// block's threads add addend[id] ^ (i * 0x9E3779B1) to data[i] for i < cs_words with plain
-// loads and stores.  Broken exclusion loses updates to total/data or corrupts the log; the
-// fair kinds also record their ticket so the host can check grants follow ticket order
-// (the cohort lock: each die's grants follow that die's tickets).
+// waits delay[id] SM cycles; inside the critical section thread 0 reads `total` (the grant's
+// position) and increments it with a plain load and store, and the block's threads add
+// addend[id] ^ (i * 0x9E3779B1) to data[i] for i < cs_words with plain loads and stores.
+// After the unlock thread 0 writes id into the grant log at that position.  Broken exclusion
+// loses updates to total/data or repeats a position in the log; the fair kinds also record
+// their ticket so the host can check grants follow ticket order (the cohort lock: each die's
+// grants follow that die's tickets).
 #include "common.cuh"
 
 using namespace gsync_impl;
@@ -21,7 +22,7 @@ constexpr uint32_t kGolden = 0x9E3779B1u;
 // The critical section's data update: data[i] += v ^ (i * kGolden) for i < cs_words, word i on
 // thread i mod blockDim.  cs_load issues a thread's first loads -- one word, or up to
 // kCsInFlight of them for a section wider than the block (WIDE) -- before thread 0's own
-// bookkeeping (total, grant log), so that thread 0 waits for one L2 round trip, not two;
+// bookkeeping (the read and write of total), so that thread 0 waits for one L2 round trip, not two;
 // cs_store finishes them, and a WIDE section's further passes keep kCsInFlight loads per thread
 // in flight.  Narrow sections run in a kernel of their own.
 constexpr int kCsInFlight = 4;
