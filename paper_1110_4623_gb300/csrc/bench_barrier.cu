@@ -51,10 +51,23 @@ __global__ void __launch_bounds__(kMaxThreads, FULL ? 4 : 6)
       return buf[j];
     }
   };
+  // Sampled fold with slot buffers: the partner read of round r is folded in round r + 1,
+  // after that round's slot store has been issued, so the read's round trip and the store's
+  // acknowledgement (which the next arrival's release waits for) overlap instead of following
+  // one another.  The read is still ordered before the next arrival by that release, so no
+  // block can overwrite the slot before it is read.
+  constexpr bool kDeferFold = !FULL && !kExchange;
+  uint32_t pend_v = 0, pend_want = 0;
+  bool pend = false;
   for (int r = 0; r < rounds; ++r) {
     uint32_t* buf = slots + (uint32_t)(r & 1) * B;
     const uint32_t rb = (uint32_t)r * B;
     if (!kExchange && tid == 0) buf[b] = rb + b;
+    if (kDeferFold && tid == 0 && pend) {
+      mix = rotl32(mix, 5) ^ lowbias32(pend_v);
+      bad += pend_v != pend_want;
+      pend = false;
+    }
     if (TRACE && tid == 0) trace[2u * ((uint64_t)b * (uint32_t)rounds + (uint32_t)r)] = gsync::ptx::globaltimer();
     int rc;
     if constexpr (kExchange) {
@@ -106,9 +119,19 @@ __global__ void __launch_bounds__(kMaxThreads, FULL ? 4 : 6)
     } else if (tid == 0) {
       const uint32_t p = (b + (uint32_t)r + 1u) % B;
       const uint32_t v = slot(buf, p, bad);
-      mix = rotl32(mix, 5) ^ lowbias32(v);
-      bad += v != rb + p;
+      if constexpr (kDeferFold) {
+        pend_v = v;
+        pend_want = rb + p;
+        pend = true;
+      } else {
+        mix = rotl32(mix, 5) ^ lowbias32(v);
+        bad += v != rb + p;
+      }
     }
+  }
+  if (kDeferFold && tid == 0 && pend) {
+    mix = rotl32(mix, 5) ^ lowbias32(pend_v);
+    bad += pend_v != pend_want;
   }
   if (tid == 0) {
     mix_out[b] = mix;
