@@ -2,10 +2,10 @@
 // pairs; Section 5: at most n blocks inside the critical section at once).
 //
 // Block b makes `pairs` wait/post pairs (id = b * pairs + p).  Inside, thread 0 counts itself
-// into `occupancy` with an atomic add and raises `max_occupancy` (the capacity invariant,
-// checked on the host), increments `total` with a plain load/store when n == 1 (exclusion
-// makes it exact), holds for hold[id] SM cycles, adds addend[id] to `tally` atomically and
-// counts itself out of `occupancy` before posting.
+// into `occupancy` with an atomic add (and, when n == 1, reads `total`), holds for hold[id]
+// SM cycles, then raises `max_occupancy` to its count (the capacity invariant, checked on the
+// host), stores total + 1 when n == 1 (exclusion makes the plain load/store exact), adds
+// addend[id] to `tally` atomically and counts itself out of `occupancy` before posting.
 #include "common.cuh"
 
 using namespace gsync_impl;
@@ -55,12 +55,14 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
       break;
     }
     if (KIND != kSemFrame && tid == 0) {
-      // n = 1: the plain read of total goes out with the occupancy atomic (one round trip)
+      // n = 1: the plain read of total goes out with the occupancy atomic (one round trip).
+      // The hold starts at once: their round trip overlaps it, and only what needs their
+      // values -- the running maximum and total's store -- comes after the hold.
       const uint32_t t = s.n == 1u ? *total : 0u;
       const uint32_t o = gsync::ptx::atom_add_relaxed(occupancy, 1u) + 1u;
+      if (hold) spin_cycles(hold_cycles);
       gsync::ptx::atom_max_relaxed(max_occupancy, o);
       if (s.n == 1u) *total = t + 1u;
-      if (hold) spin_cycles(hold_cycles);
       gsync::ptx::red_add_relaxed(tally, add);
       gsync::ptx::atom_add_relaxed(occupancy, 0xFFFFFFFFu);
     }
