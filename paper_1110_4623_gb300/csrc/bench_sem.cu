@@ -1,11 +1,12 @@
 // Counting-semaphore workload (Section 6, "Results": each block runs a loop of wait/post
 // pairs; Section 5: at most n blocks inside the critical section at once).
 //
-// Block b makes `pairs` wait/post pairs (id = b * pairs + p).  Inside, thread 0 counts itself
-// into `occupancy` with an atomic add (and, when n == 1, reads `total`), holds for hold[id]
-// SM cycles, then raises `max_occupancy` to its count (the capacity invariant, checked on the
-// host), stores total + 1 when n == 1 (exclusion makes the plain load/store exact), adds
-// addend[id] to `tally` atomically and counts itself out of `occupancy` before posting.
+// Block b makes `pairs` wait/post pairs (id = b * pairs + p).  Inside, for hold[id] SM cycles
+// from entry, thread 0 counts itself into `occupancy` with an atomic add, raises
+// `max_occupancy` to its count (the capacity invariant, checked on the host), increments
+// `total` with a plain load/store when n == 1 (exclusion makes it exact) and adds addend[id]
+// to `tally` atomically; at the end of the hold it counts itself out of `occupancy`, then
+// posts.
 #include "common.cuh"
 
 using namespace gsync_impl;
@@ -16,6 +17,15 @@ constexpr int kMaxThreads = 256;
 
 constexpr int kNoSem = -1;     // no semaphore at all: the critical-section probe
 constexpr int kSemFrame = -2;  // the probe's frame around an empty critical section
+// Cycles into the hold after which thread 0 does the section's bookkeeping: longer than an
+// L2 round trip to either die (~0.4 us at 2 GHz), so the values it needs have returned.
+constexpr uint32_t kBookkeepCycles = 1024;
+
+// Spin until `cycles` SM cycles have passed since h0 (clock64 at the hold's start).
+__device__ __forceinline__ void spin_until(long long h0, uint32_t cycles) {
+  while (clock64() - h0 < (long long)cycles) {
+  }
+}
 
 template <int KIND>
 __global__ void __launch_bounds__(kMaxThreads, 8)
@@ -55,15 +65,18 @@ __global__ void __launch_bounds__(kMaxThreads, 8)
       break;
     }
     if (KIND != kSemFrame && tid == 0) {
-      // n = 1: the plain read of total goes out with the occupancy atomic (one round trip).
-      // The hold starts at once: their round trip overlaps it, and only what needs their
-      // values -- the running maximum and total's store -- comes after the hold.
+      // The hold (hold[id] cycles from entry) starts at once.  n = 1: the plain read of total
+      // goes out with the occupancy atomic, and their round trip overlaps the hold's first
+      // kBookkeepCycles; then the running maximum, total's store and the tally go out
+      // mid-hold, so that at the post only the occupancy decrement is still in flight.
+      const long long h0 = clock64();
       const uint32_t t = s.n == 1u ? *total : 0u;
       const uint32_t o = gsync::ptx::atom_add_relaxed(occupancy, 1u) + 1u;
-      if (hold) spin_cycles(hold_cycles);
+      spin_until(h0, min(hold_cycles, kBookkeepCycles));
       gsync::ptx::atom_max_relaxed(max_occupancy, o);
       if (s.n == 1u) *total = t + 1u;
       gsync::ptx::red_add_relaxed(tally, add);
+      spin_until(h0, hold_cycles);
       gsync::ptx::atom_add_relaxed(occupancy, 0xFFFFFFFFu);
     }
     int rc2 = GSYNC_OK;
