@@ -52,7 +52,9 @@ __global__ void __launch_bounds__(kMaxThreads)
       if (t0) record_status(status, tok.status);
       break;
     }
-    if (t0 && acquisitions) ptx::red_add_relaxed(acquisitions, 1u);  // fire-and-forget: no round trip
+    // Acquisitions of the mutex in this round (the lock, and one per wait that takes it again),
+    // counted after the unlock so that the release does not wait for the count's store.
+    uint32_t acq_round = 1u;
     // wait while the buffer is full (producer) or empty (consumer); re-test after each wake
     int rc = GSYNC_OK;
     for (;;) {
@@ -65,10 +67,13 @@ __global__ void __launch_bounds__(kMaxThreads)
       if (s_ok) break;
       rc = gsync::cond_wait<MKIND>(producer ? not_full : not_empty, m, tok);
       if (rc != GSYNC_OK) break;
-      if (t0 && acquisitions) ptx::red_add_relaxed(acquisitions, 1u);  // the wait took the mutex again
+      ++acq_round;  // the wait took the mutex again
     }
     if (rc != GSYNC_OK) {
-      if (t0) record_status(status, rc);
+      if (t0) {
+        record_status(status, rc);
+        if (acquisitions) ptx::red_add_relaxed(acquisitions, acq_round);
+      }
       break;  // the mutex is not held after a failed wait
     }
     if (t0) {
@@ -84,6 +89,7 @@ __global__ void __launch_bounds__(kMaxThreads)
       }
     }
     gsync::mutex_unlock<MKIND>(m, tok);
+    if (t0 && acquisitions) ptx::red_add_relaxed(acquisitions, acq_round);
     if (!producer && t0) {
       const uint32_t id = s_id;
       if (id < (uint32_t)(producers * items_per_producer)) {
