@@ -17,8 +17,9 @@ constexpr int kMaxThreads = 256;
 
 constexpr int kNoSem = -1;     // no semaphore at all: the critical-section probe
 constexpr int kSemFrame = -2;  // the probe's frame around an empty critical section
-// Cycles into the hold after which thread 0 does the section's bookkeeping: longer than an
-// L2 round trip to either die (~0.4 us at 2 GHz), so the values it needs have returned.
+// Cycles into the hold after which thread 0 does the section's bookkeeping: ~0.5 us at the
+// 2.07 GHz clock, longer than an L2 round trip to a line on either die (0.2-0.4 us), so the
+// values it needs have returned (a hold shorter than this does it at the hold's end).
 constexpr uint32_t kBookkeepCycles = 1024;
 
 // Spin until `cycles` SM cycles have passed since h0 (clock64 at the hold's start).
