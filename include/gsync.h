@@ -358,9 +358,10 @@ int gsync_bench_mutex_host(const gsync_mutex_work* w, const gsync_backoff* backo
                            void* workspace, size_t workspace_bytes, void* stream);
 
 /* Semaphore workload.  Block b makes `pairs` wait/post pairs (id = b*pairs + p); inside,
- * thread 0 counts itself into `occupancy` (atomic), raises max_occupancy, increments total
- * with a plain load/store when the initial count is 1, holds for hold[id] SM cycles, adds
- * addend[id] to tally (atomic) and counts itself out before posting.
+ * for hold[id] SM cycles from its entry, thread 0 counts itself into `occupancy` (atomic),
+ * raises max_occupancy, increments total with a plain load/store when the initial count is
+ * 1 and adds addend[id] to tally (atomic); at the end of the hold it counts itself out, then
+ * posts.
  * Buffers (device): hold, addend [nblocks*pairs]; occupancy, max_occupancy, total, tally,
  * status [1] (zeroed by the caller); count [nblocks]. */
 typedef struct gsync_sem_work {
@@ -645,8 +646,8 @@ int gsync_probe_cs(int cs_words, int block_threads, int iters, void* scratch, ui
 size_t gsync_probe_cs_scratch_bytes(int cs_words, int iters);
 
 /* Semaphore critical-section probe (the semaphore roofline's T_cs): one block runs the
- * semaphore workload's critical section -- occupancy bookkeeping, hold[p] SM cycles, the
- * tally -- framed like a hand-off (an acquire load and a barrier before it, a barrier and a
+ * semaphore workload's critical section -- hold[p] SM cycles with the occupancy bookkeeping
+ * and the tally inside them -- framed like a hand-off (an acquire load and a barrier before it, a barrier and a
  * release fence and store after it) for p < iters, with no semaphore.  hold, addend
  * (device) hold >= iters entries (hold may be NULL: no hold; both NULL: the frame alone,
  * with an empty critical section).  scratch (device, 256-byte aligned, 1024 bytes).
