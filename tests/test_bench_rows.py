@@ -49,3 +49,14 @@ def test_sweep_rows():
     assert len(b) == 3 and {(r["kind"], r["nblocks"]) for r in b} >= {("cluster8", 144), ("count8", 148)}
     s = [r for r in rows if r["section"] == "sweep_semaphore"]
     assert s == [dict(s[0], section="sweep_semaphore", kind="window", n=4, nblocks=296, ops_per_s=1.5e6)]
+
+
+def test_sweep_grids_start_at_one_block_and_round_cluster_grids_down():
+    import bench
+    assert bench.SWEEP_GRIDS[0] == 1 and bench.SWEEP_GRIDS[-1] == bench.NBLOCKS
+    assert list(bench.SWEEP_GRIDS) == sorted(set(bench.SWEEP_GRIDS))
+    assert bench.sweep_grid(148, 0) == 148 and bench.sweep_grid(148, 8) == 144 and bench.sweep_grid(148, 4) == 148
+    assert bench.sweep_grid(4, 8) == 0 and bench.sweep_grid(8, 8) == 8 and bench.sweep_grid(1, 0) == 1
+    # every cluster grid the sweep runs divides into whole clusters
+    for c in (2, 4, 8):
+        assert all(bench.sweep_grid(B, c) % c == 0 for B in bench.SWEEP_GRIDS)
