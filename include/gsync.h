@@ -541,8 +541,9 @@ int gsync_bench_batched(const gsync_batched_work* w, void* stream);
  * aligned, gsync_serve_baseline_workspace_bytes(nreq) bytes. */
 /* One ring entry (16 bytes), at the start of its own 128-byte line of the ring (entry i at
  * byte 128 * i).  Request q is in the ring when seq == seq_check == q + 1; the host writes
- * len, off and seq_check first and seq last with a release store, and the device reads the
- * entry with one 16-byte acquire load. */
+ * the entry as two aligned 8-byte stores, {seq, len} and {off, seq_check}, each single-copy
+ * atomic, with no fence between them, and the device reads the entry with one 16-byte acquire
+ * load: both sequence numbers current means both halves are. */
 typedef struct gsync_serve_req {
   uint32_t seq;
   uint32_t len;

@@ -3,7 +3,7 @@
 // names hardware enqueue/dequeue as a wish, Section 7).
 //
 // The host publishes requests into a ring of 16-byte entries (each entry carries its sequence
-// number, written last with a release store).  The ring is caller memory: pinned host memory,
+// number twice, one copy in each of its two 8-byte halves, each half written with one store).  The ring is caller memory: pinned host memory,
 // which the admitters poll across the host link, or managed memory placed in device memory,
 // which the host writes in place and the admitters poll through L2.  Inside one co-resident
 // launch:
@@ -22,6 +22,7 @@
 // The per-request-launch baseline runs the same chunked segmented sum as one kernel launch
 // per request and completes it the same way (result and flag in pinned host memory).
 #include <pthread.h>
+#include <stddef.h>
 #include <sched.h>
 #include <string.h>
 #include <unistd.h>
@@ -42,6 +43,11 @@ constexpr int kThreads = 256;
 // Ring entries sit one per 128-byte line, so the host writing entry q never touches a line
 // that an admitter polls for another entry.
 constexpr size_t kRingStride = 128;
+static_assert(sizeof(gsync_serve_req) == 16 && offsetof(gsync_serve_req, seq) == 0 &&
+                  offsetof(gsync_serve_req, len) == 4 && offsetof(gsync_serve_req, off) == 8 &&
+                  offsetof(gsync_serve_req, seq_check) == 12,
+              "the producer writes an entry as two 8-byte halves {seq, len} and {off, seq_check}");
+static_assert(__BYTE_ORDER__ == __ORDER_LITTLE_ENDIAN__, "the entry halves are packed little-endian");
 // The active mask is kept in kMaskCopies copies on separate lines (set and cleared in all,
 // read from one per worker) to spread the workers' polling.
 constexpr uint32_t kMaskCopies = 4;
@@ -550,10 +556,13 @@ extern "C" int gsync_serve_run(const gsync_serve_cfg* cfg, gsync_serve_buffers* 
   // The producer runs on its own pinned core too; this thread only waits.
   std::atomic<int> prod_rc{GSYNC_OK};
   std::thread producer([&]() {
-    // Publishes every request whose time has come in one batch: the entries' bodies, one
-    // release fence, then their sequence numbers.  A store to a line the device is polling
-    // waits for that line's copy to be invalidated (~1 us over the C2C link), so one fence
-    // per batch instead of one per entry keeps the producer on schedule at high rates.
+    // Publishes every request whose time has come in one batch.  Each entry is written with
+    // two aligned 8-byte stores, {seq, len} and {off, seq_check}, and no fence: each store is
+    // single-copy atomic, so an entry whose seq and seq_check both read q + 1 holds request
+    // q's len and off whatever order the two stores became visible in (a reader that sees
+    // one half of an older lap's entry finds that half's sequence number stale).  One
+    // write per half, with nothing to wait for between them, keeps the producer on schedule
+    // where its stores cross the host link into device memory.
     int q = 0;
     while (q < cfg->nreq) {
       spin_until(t0 + std::chrono::nanoseconds(buf->sched_ns[q]));
@@ -568,15 +577,11 @@ extern "C" int gsync_serve_run(const gsync_serve_cfg* cfg, gsync_serve_buffers* 
         }
       }
       for (int i = q; i < qe; ++i) {
-        gsync_serve_req* e = (gsync_serve_req*)((char*)buf->ring + (size_t)(i & (cfg->ring_slots - 1)) * kRingStride);
-        e->len = (uint32_t)buf->length[i];
-        e->off = (uint32_t)buf->offset[i];
-        e->seq_check = (uint32_t)(i + 1);
-      }
-      std::atomic_thread_fence(std::memory_order_release);
-      for (int i = q; i < qe; ++i) {
-        gsync_serve_req* e = (gsync_serve_req*)((char*)buf->ring + (size_t)(i & (cfg->ring_slots - 1)) * kRingStride);
-        __atomic_store_n(&e->seq, (uint32_t)(i + 1), __ATOMIC_RELAXED);
+        uint64_t* e = (uint64_t*)((char*)buf->ring + (size_t)(i & (cfg->ring_slots - 1)) * kRingStride);
+        const uint64_t seq = (uint32_t)(i + 1);
+        // little-endian layout of gsync_serve_req: seq | len << 32, then off | seq_check << 32
+        __atomic_store_n(e, seq | ((uint64_t)(uint32_t)buf->length[i] << 32), __ATOMIC_RELAXED);
+        __atomic_store_n(e + 1, (uint64_t)(uint32_t)buf->offset[i] | (seq << 32), __ATOMIC_RELAXED);
       }
       published.store(qe, std::memory_order_release);
       if (buf->publish_ns) {
