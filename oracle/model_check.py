@@ -38,6 +38,7 @@ The algorithms follow Section 5 ("Design") and the pseudocode of the Appendix:
   SplitBarrier  S arrival counters under a top counter, R copies of the release word
   CountBarrier  one growing arrival counter that every block polls
   ExchangeBarrier  the counting barrier whose arrivals carry one value per block, no fence
+  RingPublish   the serving ring's entry, written as two single-copy-atomic halves, no fence
 Mutation variants with a planted mistake (`broken=...`) exist so that tests can show the
 checker catches each kind of error.
 """
@@ -1666,6 +1667,58 @@ class ClusterCountBarrier:
 # --------------------------------------------------------------------------------------------
 # Explorer
 # --------------------------------------------------------------------------------------------
+
+
+class RingPublish:
+    """The serving ring's entry publication (the persistent serving loop; not in the paper).
+
+    Block 0 is the host's producer, block 1 an admitter, over one ring slot that every request
+    reuses.  The producer writes request i as two halves, lo = (seq, len) and hi = (off,
+    seq_check), each one atomic store, in either order (`hi_first`) and with no fence, and
+    reuses the slot only after the admitter has taken request i - 1.  The admitter reads the two
+    halves with two separate reads (`read_hi_first` picks the order) and takes the entry when
+    both sequence numbers equal i + 1; it must then hold request i's len (10 + i) and off
+    (20 + i).
+    broken="one_check": the admitter checks seq alone (a half of the previous lap slips in);
+    broken="no_reuse_wait": the producer overwrites the slot before the admitter took the
+    previous request (that request is lost and the admitter waits forever).
+    """
+    kind = "mutex"
+    capacity = 1
+    fifo = False
+
+    def __init__(self, hi_first=False, read_hi_first=False, broken=None):
+        self.hi_first, self.read_hi_first, self.broken = hi_first, read_hi_first, broken
+
+    def init(self, nproc, ops):
+        # shared: (lo, hi, requests taken); the slot starts empty (sequence numbers 0)
+        locs = tuple((0, 0, None) if p < 2 else (DONE, 0, None) for p in range(nproc))
+        return ((0, -1), (-1, 0), 0), locs
+
+    def step(self, p, loc, sh, nproc, ops):
+        pc, i, seen = loc
+        lo, hi, taken = sh
+        if p == 0:  # producer
+            new_lo, new_hi = (i + 1, 10 + i), (20 + i, i + 1)
+            if pc == 0:
+                if taken < i and self.broken != "no_reuse_wait":
+                    return loc, sh, None
+                first = (lo, new_hi, taken) if self.hi_first else (new_lo, hi, taken)
+                return (1, i, None), first, None
+            second = (new_lo, hi, taken) if self.hi_first else (lo, new_hi, taken)
+            i += 1
+            return ((0 if i < ops else DONE), i, None), second, None
+        # admitter
+        if pc == 0:
+            return (1, i, hi if self.read_hi_first else lo), sh, None
+        got_lo, got_hi = (lo, seen) if self.read_hi_first else (seen, hi)
+        (seq, ln), (off, chk) = got_lo, got_hi
+        if seq != i + 1 or (chk != i + 1 and self.broken != "one_check"):
+            return (0, i, None), sh, None  # not published yet: poll again
+        if ln != 10 + i or off != 20 + i:
+            return loc, sh, ("violation", f"request {i} taken with len {ln}, off {off}")
+        i += 1
+        return ((0 if i < ops else DONE), i, None), (lo, hi, i), None
 
 
 def _ghost0(model, nproc):

@@ -104,6 +104,11 @@ CORRECT = [
     ("die_barrier_uneven", mc.DieBarrier(layout=(0, 0, 1)), 3, 4),
     ("die_barrier_one_die", mc.DieBarrier(layout=(1, 1, 1)), 3, 3),
     ("die_barrier_wrap", mc.DieBarrier(base=2 ** 32 - 2), 3, 4),
+    # the serving ring's entry: both write orders of its two halves, both read orders
+    ("ring_publish_lo_first", mc.RingPublish(), 2, 3),
+    ("ring_publish_hi_first", mc.RingPublish(hi_first=True), 2, 3),
+    ("ring_publish_read_hi_first", mc.RingPublish(read_hi_first=True), 2, 3),
+    ("ring_publish_both_hi_first", mc.RingPublish(hi_first=True, read_hi_first=True), 2, 4),
 ]
 
 
@@ -154,6 +159,11 @@ BROKEN = [
     ("exchange_single_buffer", mc.ExchangeBarrier(broken="single_buffer"), 3, 3, "cannot reach completion"),
     ("exchange_no_epoch_check", mc.ExchangeBarrier(late=(True, False, True), broken="no_epoch_check"), 3, 3, "read"),
     ("exchange_off_by_one", mc.ExchangeBarrier(broken="off_by_one"), 3, 3, "passed round"),
+    # Serving ring: an admitter that checks one sequence number (the other half may still be
+    # the previous lap's), and a producer that reuses the slot before its request was taken.
+    ("ring_publish_one_check", mc.RingPublish(broken="one_check"), 2, 3, "taken with"),
+    ("ring_publish_one_check_read_hi", mc.RingPublish(read_hi_first=True, broken="one_check"), 2, 3, "taken with"),
+    ("ring_publish_no_reuse_wait", mc.RingPublish(broken="no_reuse_wait"), 2, 3, "cannot reach completion"),
     ("sleep_sem_turn_ge", mc.SleepSem(n=1, broken="turn_ge"), 3, 1, "critical section"),
     ("window_sem_ge", mc.WindowSem(n=2, broken="window_ge"), 3, 1, "critical section"),
     ("barrier_no_wait", mc.AtomicBarrier(broken="no_wait"), 3, 1, "passed round"),
