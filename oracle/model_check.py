@@ -39,6 +39,7 @@ The algorithms follow Section 5 ("Design") and the pseudocode of the Appendix:
   CountBarrier  one growing arrival counter that every block polls
   ExchangeBarrier  the counting barrier whose arrivals carry one value per block, no fence
   RingPublish   the serving ring's entry, written as two single-copy-atomic halves, no fence
+  ServeSlot     a serving slot: generation-tagged chunk claims by fetch-and-add, reuse
 Mutation variants with a planted mistake (`broken=...`) exist so that tests can show the
 checker catches each kind of error.
 """
@@ -1719,6 +1720,113 @@ class RingPublish:
             return loc, sh, ("violation", f"request {i} taken with len {ln}, off {off}")
         i += 1
         return ((0 if i < ops else DONE), i, None), (lo, hi, i), None
+
+
+class ServeSlot:
+    """One slot of the persistent serving loop (not in the paper): an admitter publishes
+    requests into the slot one after another, and workers claim the requests' chunks.
+
+    Block 0 is the admitter.  For request r it takes the free slot (compare-and-swap of the
+    state 0 -> 1), reads the generation and writes generation + 1, the chunk count NCH[r], the
+    done count 0 and the accumulator 0, resets the claim counter to (generation, chunk 0),
+    publishes the slot (state 2) and sets its bit in the active mask.  Blocks 1.. are workers.
+    A worker that finds the bit set claims with one fetch-and-add on the (generation, chunk)
+    counter, then reads (state, generation, chunk count) in one access: the claim is taken when
+    the slot is active in the claim's generation and the chunk exists, dropped when the slot
+    has moved on or the chunk is past the last, and waits while the slot is being set up.  The
+    worker that takes the last chunk clears the bit.  A taken chunk adds its value (1 << chunk)
+    to the accumulator and counts itself done; the block whose count completes the request
+    reads the accumulator, which must hold every chunk, frees the slot (state 0) and counts
+    the request completed.  Workers stop once every request is completed.  Each shared access
+    is one step (sequential consistency).  The counter's chunk field stops growing one past the
+    largest chunk count (a 16-bit field on the device, which the few claims made between a
+    last chunk's hand-out and the clearing of the bit cannot carry into the generation).
+    broken="no_gen_check": a worker takes any claim whose chunk exists in the active request,
+    whatever the claim's generation (a chunk is then processed twice);
+    broken="no_done_reset": the admitter leaves the done count of the previous request (the
+    next request never completes).
+    """
+    kind = "mutex"
+    capacity = 1 << 30
+    fifo = False
+
+    def __init__(self, nch=(1, 2), broken=None):
+        self.nch, self.broken = tuple(nch), broken
+
+    def init(self, nproc, ops):
+        # shared: state, gen, nchunks, claim counter (gen, chunk), done, acc, completed, active
+        # bit, and a ghost: the (generation, chunk) pairs processed so far
+        sh = (0, 0, 0, (0, 0), 0, 0, 0, 0, frozenset())
+        return sh, tuple((0, 0, 0, 0) for _ in range(nproc))
+
+    @staticmethod
+    def _put(sh, i, v):
+        return sh[:i] + (v,) + sh[i + 1:]
+
+    def step(self, p, loc, sh, nproc, ops):
+        state, gen, nch, ctr, done, acc, completed, active, seen = sh
+        pc, a, b, c = loc
+        put = self._put
+        R = len(self.nch)
+        if p == 0:  # admitter; a = request, b = its generation
+            if pc == 0:
+                if state != 0:
+                    return loc, sh, None
+                return (1, a, b, c), put(sh, 0, 1), None
+            if pc == 1:
+                return (2, a, gen + 1, c), sh, None
+            if pc == 2:
+                return (3, a, b, c), put(sh, 1, b), None
+            if pc == 3:
+                return (4, a, b, c), put(sh, 2, self.nch[a]), None
+            if pc == 4:
+                return (5, a, b, c), put(sh, 4, done if self.broken == "no_done_reset" else 0), None
+            if pc == 5:
+                return (6, a, b, c), put(sh, 5, 0), None
+            if pc == 6:
+                return (7, a, b, c), put(sh, 3, (b, 0)), None
+            if pc == 7:
+                return (8, a, b, c), put(sh, 0, 2), None
+            a += 1
+            return ((0 if a < R else DONE), a, 0, 0), put(sh, 7, 1), None
+        # worker; a, b = the claim's (generation, chunk), c = the request's chunk count
+        if pc == 0:
+            if completed == R:
+                return (DONE, 0, 0, 0), sh, None
+            return (10, 0, 0, 0), sh, None
+        if pc == 10:
+            return ((1 if active else 0), 0, 0, 0), sh, None
+        if pc == 1:
+            g, k = ctr
+            # the chunk field stops at max(NCH) + 1: every claim past a request's last chunk is
+            # dropped alike, and the bound keeps the state space finite
+            return (2, g, k, 0), put(sh, 3, (g, min(k + 1, max(self.nch) + 1))), None
+        if pc == 2:
+            g, k = a, b
+            if state == 2 and (gen == g or self.broken == "no_gen_check"):
+                if k >= nch:
+                    return (0, 0, 0, 0), sh, None  # past the last chunk: dropped
+                return (3, gen, k, nch), sh, None
+            if gen > g or (gen == g and state == 0):
+                return (0, 0, 0, 0), sh, None  # the slot has moved on: dropped
+            return loc, sh, None  # generation g is being set up: wait
+        if pc == 3:  # the last chunk handed out: the slot leaves the active mask
+            if b + 1 == c:
+                return (4, a, b, c), put(sh, 7, 0), None
+            return (4, a, b, c), sh, None
+        if pc == 4:
+            if (a, b) in seen:
+                return loc, sh, ("violation", f"chunk {b} of generation {a} processed twice")
+            return (5, a, b, c), put(put(sh, 5, acc | (1 << b)), 8, seen | {(a, b)}), None
+        if pc == 5:
+            return ((6 if done + 1 == c else 0), a, b, c), put(sh, 4, done + 1), None
+        if pc == 6:
+            if acc != (1 << c) - 1:
+                return loc, sh, ("violation", f"generation {a} completed with chunks {acc:#b} of {c}")
+            return (7, a, b, c), sh, None
+        if pc == 7:
+            return (8, a, b, c), put(sh, 0, 0), None
+        return (0, 0, 0, 0), put(sh, 6, completed + 1), None
 
 
 def _ghost0(model, nproc):

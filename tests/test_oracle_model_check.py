@@ -109,6 +109,11 @@ CORRECT = [
     ("ring_publish_hi_first", mc.RingPublish(hi_first=True), 2, 3),
     ("ring_publish_read_hi_first", mc.RingPublish(read_hi_first=True), 2, 3),
     ("ring_publish_both_hi_first", mc.RingPublish(hi_first=True, read_hi_first=True), 2, 4),
+    # a serving slot reused by requests of 1 and 2 chunks, two and three workers
+    ("serve_slot_1_2", mc.ServeSlot(nch=(1, 2)), 3, 1),
+    ("serve_slot_2_1", mc.ServeSlot(nch=(2, 1)), 3, 1),
+    ("serve_slot_1_2_1", mc.ServeSlot(nch=(1, 2, 1)), 3, 1),
+    ("serve_slot_three_workers", mc.ServeSlot(nch=(1, 2)), 4, 1),
 ]
 
 
@@ -164,6 +169,11 @@ BROKEN = [
     ("ring_publish_one_check", mc.RingPublish(broken="one_check"), 2, 3, "taken with"),
     ("ring_publish_one_check_read_hi", mc.RingPublish(read_hi_first=True, broken="one_check"), 2, 3, "taken with"),
     ("ring_publish_no_reuse_wait", mc.RingPublish(broken="no_reuse_wait"), 2, 3, "cannot reach completion"),
+    # Serving slot: a worker that ignores its claim's generation (an over-claim of the last
+    # request becomes a second claim of a chunk of the next), and an admitter that does not
+    # reset the done count (the next request completes with a chunk missing).
+    ("serve_slot_no_gen_check", mc.ServeSlot(nch=(1, 2), broken="no_gen_check"), 3, 1, "processed twice"),
+    ("serve_slot_no_done_reset", mc.ServeSlot(nch=(1, 2), broken="no_done_reset"), 3, 1, "completed with"),
     ("sleep_sem_turn_ge", mc.SleepSem(n=1, broken="turn_ge"), 3, 1, "critical section"),
     ("window_sem_ge", mc.WindowSem(n=2, broken="window_ge"), 3, 1, "critical section"),
     ("barrier_no_wait", mc.AtomicBarrier(broken="no_wait"), 3, 1, "passed round"),
