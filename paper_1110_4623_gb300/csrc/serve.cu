@@ -3,9 +3,10 @@
 // names hardware enqueue/dequeue as a wish, Section 7).
 //
 // The host publishes requests into a ring of 16-byte entries (each entry carries its sequence
-// number twice, one copy in each of its two 8-byte halves, each half written with one store).  The ring is caller memory: pinned host memory,
-// which the admitters poll across the host link, or managed memory placed in device memory,
-// which the host writes in place and the admitters poll through L2.  Inside one co-resident
+// number twice, one copy in each of its two 8-byte halves, each half written with one store).
+// The ring is caller memory: pinned host memory, which the admitters poll across the host
+// link, or managed memory placed in device memory, which the host writes in place and the
+// admitters poll through L2.  Inside one co-resident
 // launch:
 //   * admitter blocks wait on the admission semaphore (n = number of in-flight slots), take
 //     the next request index under the ring's ticket lock, wait for that entry to appear,
